@@ -1,0 +1,168 @@
+/*
+ * stokes.h -- C ABI of libstokes_gb300, a single-GPU (GB300, sm_103a) solver
+ * for the variable-density, variable-viscosity staggered-grid Stokes system
+ *
+ *     M x = b,   M = [ A  G ]      A = theta rho - L_mu,   theta = 1/dt
+ *                    [ -D 0 ]
+ *
+ * of Cai, Nonaka, Bell, Griffith & Donev, "Efficient Variable-Coefficient
+ * Finite-Volume Stokes Solvers" (arXiv:1308.4605), Eq. Saddle_sys of Sec. 2
+ * with the MAC discretisation of Sec. 3.1, solved by GMRES (Sec. 3.2, Sec. 4)
+ * preconditioned by the block preconditioners P1..P5 of Sec. 2, each of
+ * which applies one geometric-multigrid V-cycle (App. C) to the velocity and
+ * to the pressure subproblem.
+ *
+ * Data layout (all arrays are caller-owned DEVICE memory, FP64, contiguous):
+ *   cell arrays   nz * ny * nx doubles, x fastest (nz = 1 in 2D);
+ *                 cell (i,j,k) is centred at ((i+1/2)h, (j+1/2)h, (k+1/2)h).
+ *   face arrays   one per velocity component a; same shape except that the
+ *                 extent along axis a is n_a + 1 when axis a has walls (faces
+ *                 0 and n_a lie on the walls; the library writes zeros there
+ *                 and ignores what it finds there) and n_a when it is
+ *                 periodic.  Face i of component a lies at x_a = i h.
+ * Right-hand side convention (Eq. Saddle_sys):  b_u = rho u^n / dt + f,
+ * b_p = -g where g is the prescribed velocity divergence.
+ *
+ * Every call returns STK_OK (0) or a negative STK_ERR_* code; the message of
+ * the last failure on a handle is returned by stk_last_error.  Calls are
+ * asynchronous on the given stream (a cudaStream_t passed as void*, NULL for
+ * the legacy default stream) except stk_create, stk_destroy,
+ * stk_set_coefficients (which validates its inputs) and stk_solve (which
+ * returns when the solve is finished and info is written).
+ * The library owns all workspace (multigrid hierarchy, Krylov basis) and
+ * allocates it in stk_create / stk_set_coefficients / the first stk_solve.
+ * A handle is used from one host thread at a time.
+ */
+#ifndef STOKES_GB300_H
+#define STOKES_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* boundary condition codes, one per side: x_lo, x_hi, y_lo, y_hi, z_lo, z_hi
+ * (Sec. 3.1: periodic, no-slip u = 0, free-slip u.n = 0 with zero tangential
+ * stress).  Periodic must be set on both sides of an axis. */
+#define STK_PERIODIC 0
+#define STK_NOSLIP   1
+#define STK_FREESLIP 2
+
+/* return codes */
+#define STK_OK                 0
+#define STK_ERR_ARG           -1  /* bad argument (null pointer, bad code)       */
+#define STK_ERR_SIZE          -2  /* n_a not a power of two >= 2                 */
+#define STK_ERR_CUDA          -3  /* a CUDA runtime call failed                  */
+#define STK_ERR_NOT_CONVERGED -4  /* maxit reached; x holds the last iterate     */
+#define STK_ERR_NONFINITE     -5  /* NaN/Inf in coefficients or in the iteration */
+#define STK_ERR_TIMEOUT       -6  /* a bounded device wait expired               */
+#define STK_ERR_STATE         -7  /* coefficients not set                        */
+
+/* preconditioners (Sec. 2.1-2.4) */
+#define STK_P1 1  /* projection, Eq. P1_practical        */
+#define STK_P2 2  /* lower triangular, Eq. CC_Pre_lower  */
+#define STK_P3 3  /* upper triangular, Eq. CC_Pre_upper  */
+#define STK_P4 4  /* block diagonal, Eq. CC_Pre_diagonal */
+#define STK_P5 5  /* Uzawa-like, Sec. 2.4                */
+
+/* precision of the solve */
+#define STK_FP64  0  /* left-preconditioned GMRES(m), everything in FP64 (Sec. 3.2)      */
+#define STK_MIXED 1  /* flexible GMRES(m) in FP64 around an FP32 preconditioner (Sec. 4) */
+
+typedef struct stk_handle stk_handle;
+
+typedef struct {
+    int    precond;    /* STK_P1..STK_P5                                            */
+    int    restart;    /* GMRES restart length m (paper: 10, Sec. 4.2.2), 1..32     */
+    double rtol;       /* stop when ||b - M x||_2 <= rtol ||b||_2                   */
+    int    maxit;      /* maximum number of Arnoldi steps                           */
+    int    precision;  /* STK_FP64 or STK_MIXED                                     */
+    int    nu;         /* smoothing sweeps before and after the coarse correction (2) */
+    int    ncoarse;    /* sweeps on the coarsest level (8, App. C)                  */
+} stk_solver_params;
+
+typedef struct {
+    int    iterations;     /* Arnoldi steps (= applications of M and of P^{-1})     */
+    int    restarts;       /* GMRES cycles                                           */
+    int    converged;      /* 1 when ||b - M x|| <= rtol ||b||                       */
+    int    status;         /* return code of the solve                               */
+    double true_residual;  /* final ||b - M x|| / ||b|| (computed in FP64)           */
+    double est_residual;   /* last Arnoldi residual estimate                         */
+    double scalar_vcycles; /* cost proxy of Sec. 4: d per velocity, 1 per pressure V-cycle */
+    double solve_ms;       /* wall time of the solve on the stream                   */
+} stk_solve_info;
+
+/* Default parameters: P1, m = 10, rtol = 1e-10, maxit = 1000, FP64, nu = 2,
+ * ncoarse = 8 (Sec. 4.1.1, 4.1.2, 4.2.2, App. C). */
+void stk_default_params(stk_solver_params* p);
+
+/* Create a grid of dim (2 or 3) dimensions with n[0..dim-1] cells per axis,
+ * spacing h > 0 and boundary codes bc[0..2*dim-1].  Each n_a must be a power
+ * of two >= 2 so that coarsening by 2 reaches 2 cells along the shortest
+ * axis (App. C).  Uses the current CUDA device.  *out is NULL on failure. */
+int stk_create(int dim, const int* n, double h, const int* bc, stk_handle** out);
+
+/* Free the handle and every device allocation it owns. */
+int stk_destroy(stk_handle* h);
+
+/* Message of the last failure on h (h may be NULL for a failed stk_create). */
+const char* stk_last_error(const stk_handle* h);
+
+/* Number of doubles in the face array of component a (0 <= a < dim) and in a
+ * cell array. */
+long long stk_face_length(const stk_handle* h, int a);
+long long stk_cell_length(const stk_handle* h);
+
+/* Set the cell-centred density rho > 0 and viscosity mu >= 0 (device arrays,
+ * copied) and dt (theta = 1/dt; dt = +INFINITY gives steady flow, theta = 0).
+ * Builds the face densities (Sec. 3.1: mean of the two adjacent cells), the
+ * node/edge viscosities (mean of the surrounding in-domain cells) and the
+ * coarse-level coefficients of the velocity and pressure multigrid hierarchy
+ * (App. C), in FP64 and FP32.  Synchronises the stream.  Returns
+ * STK_ERR_NONFINITE / STK_ERR_ARG for non-finite or non-positive inputs. */
+int stk_set_coefficients(stk_handle* h, const double* rho, const double* mu, double dt,
+                         void* stream);
+
+/* y = M x  (Eq. Saddle_sys): y_u = theta rho_f x_u - L_mu x_u + G x_p and
+ * y_p = -D x_u, with the stress-form viscous operator of Eq. div_stress.
+ * x_u[a], y_u[a] are face arrays, x_p, y_p cell arrays; y must not alias x. */
+int stk_apply_operator(stk_handle* h, const double* const* x_u, const double* x_p,
+                       double* const* y_u, double* y_p, void* stream);
+
+/* x = P^{-1} b for which = STK_P1..STK_P5 (Sec. 2.1-2.4) in FP64: one velocity
+ * V-cycle per velocity subsolve, one pressure V-cycle per pressure subsolve,
+ * zero initial guesses (Sec. 3.2), S~^{-1} = -theta L~_rho^{-1} + 2 mu
+ * (Eq. Schur_app_varDen_varVis).  The mean of every Poisson right-hand side
+ * and of x_p is removed. */
+int stk_apply_preconditioner(stk_handle* h, int which, const double* const* b_u,
+                             const double* b_p, double* const* x_u, double* x_p,
+                             void* stream);
+
+/* One velocity V-cycle for A x = r (x = A~^{-1} r, zero initial guess, App. C)
+ * and one pressure V-cycle for L_rho x = r (x = L~_rho^{-1} r), in FP64. */
+int stk_velocity_vcycle(stk_handle* h, const double* const* r_u, double* const* x_u,
+                        void* stream);
+int stk_pressure_vcycle(stk_handle* h, const double* r_p, double* x_p, void* stream);
+
+/* Solve M x = b with restarted GMRES (Sec. 3.2, Sec. 4).  x_u, x_p hold the
+ * initial guess on entry and the solution on exit.  info may be NULL.
+ * Returns STK_OK, STK_ERR_NOT_CONVERGED (x holds the last iterate) or an
+ * error code.  Synchronises the stream. */
+int stk_solve(stk_handle* h, const stk_solver_params* params, const double* const* b_u,
+              const double* b_p, double* const* x_u, double* x_p, stk_solve_info* info,
+              void* stream);
+
+/* Per-kernel timing of the calls above with CUDA events on the call's
+ * stream.  stk_profile(h, 1) starts collecting (and clears), 0 stops.
+ * stk_profile_read returns, for kernel family k (0 <= k < STK_NPROF), its
+ * name, its number of launches, its summed device time in ms and the
+ * algorithmic bytes it moved (reads of every input word and writes of every
+ * output word, once per launch).  Returns -1 when k is out of range. */
+#define STK_NPROF 16
+int stk_profile(stk_handle* h, int enable);
+int stk_profile_read(stk_handle* h, int k, const char** name, long long* launches,
+                     double* ms, double* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STOKES_GB300_H */

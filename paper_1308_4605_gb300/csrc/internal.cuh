@@ -1,0 +1,129 @@
+// Internal declarations shared by the translation units of libstokes_gb300.
+//
+// Geometry of one multigrid level of the staggered (MAC) grid, Sec. 3.1 of
+// Cai et al., arXiv:1308.4605.  A velocity vector is stored "packed": the
+// face arrays of components x, y[, z] one after the other (x fastest in each);
+// a Stokes vector appends the cell array.  Wall faces are stored as zeros.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+namespace stk {
+
+constexpr int PERIODIC = 0, NOSLIP = 1, FREESLIP = 2;
+
+struct Geom {
+    int dim;
+    int n[3];        // cells per axis (n[2] = 1 in 2D)
+    int per[3];      // 1 if the axis is periodic
+    int bclo[3];     // boundary code of the low side of each axis
+    int bchi[3];
+    int fe[3][3];    // extents (x, y, z) of the face array of component a
+    int ee[3][3];    // extents of the edge array of pair p: 0=(x,y) 1=(x,z) 2=(y,z)
+    int foff[3];     // offset of component a in a packed velocity vector
+    int fsize[3];
+    int esize[3];
+    int nvel;        // length of a packed velocity vector
+    int ncell;
+    double h, ih, ih2;
+};
+
+// Coefficients of one level (precision T).  alpha = theta rho_f and
+// beta = 1/rho_f (coarsened by face averaging) are packed face vectors with
+// zeros on wall faces; mu_e are the node (2D) / edge (3D) viscosities with
+// zeros on free-slip walls and on edges lying on two walls; invd_u, invd_p
+// are the inverse diagonals of A and L_rho.
+template <typename T>
+struct Coef {
+    T* alpha;
+    T* beta;
+    T* mu_c;
+    T* mu_e[3];
+    T* invd_u;
+    T* invd_p;
+};
+
+// ---- launch wrappers (kernels.cu); all asynchronous on `s` -------------------
+
+// coefficients
+void launch_fine_coefficients(const Geom& g, const double* rho, const double* mu, double theta,
+                              Coef<double> C, cudaStream_t s);
+void launch_coarsen_coefficients(const Geom& gf, Coef<double> Cf, const Geom& gc, Coef<double> Cc,
+                                 cudaStream_t s);
+void launch_inverse_diagonals(const Geom& g, Coef<double> C, cudaStream_t s);
+void launch_convert_coefficients(const Geom& g, Coef<double> C, Coef<float> Cf, cudaStream_t s);
+
+// y = M x (packed Stokes vectors); input precision TV, output double
+template <typename TV>
+void launch_stokes_matvec(const Geom& g, Coef<double> C, const TV* x, double* y, cudaStream_t s);
+// r = b - M x
+void launch_stokes_residual(const Geom& g, Coef<double> C, const double* x, const double* b,
+                            double* r, cudaStream_t s);
+
+// multigrid (precision T)
+template <typename T>
+void launch_vel_gs_colour(const Geom& g, Coef<T> C, int comp, int parity, T* phi, const T* rhs,
+                          cudaStream_t s);
+template <typename T>
+void launch_vel_residual(const Geom& g, Coef<T> C, const T* phi, const T* rhs, T* res,
+                         cudaStream_t s);
+template <typename T>
+void launch_vel_restrict(const Geom& gf, const T* res, const Geom& gc, T* rhs_c, cudaStream_t s);
+template <typename T>
+void launch_vel_prolong_add(const Geom& gc, const T* phi_c, const Geom& gf, T* phi_f,
+                            cudaStream_t s);
+template <typename T>
+void launch_cell_gs_colour(const Geom& g, Coef<T> C, int parity, T* phi, const T* rhs,
+                           cudaStream_t s);
+template <typename T>
+void launch_cell_residual(const Geom& g, Coef<T> C, const T* phi, const T* rhs, T* res,
+                          cudaStream_t s);
+template <typename T>
+void launch_cell_restrict(const Geom& gf, const T* res, const Geom& gc, T* rhs_c, cudaStream_t s);
+template <typename T>
+void launch_cell_prolong_add(const Geom& gc, const T* phi_c, const Geom& gf, T* phi_f,
+                             cudaStream_t s);
+
+// preconditioner algebra (precision T)
+template <typename T>  // bc = D u + bp
+void launch_div_plus(const Geom& g, const T* u, const T* bp, T* bc, cudaStream_t s);
+template <typename T>  // out = u - beta G p (beta may be null: out = u - G p)
+void launch_sub_grad(const Geom& g, const T* beta, const T* u, const T* p, T* out, cudaStream_t s);
+template <typename T>  // out = b - G p - A u
+void launch_vel_correction_rhs(const Geom& g, Coef<T> C, const T* b, const T* p, const T* u,
+                               T* out, cudaStream_t s);
+template <typename T>  // xp = theta phi - 2 mu bc  (phi may be null)
+void launch_schur_combine(int n, double theta, const T* phi, const T* mu, const T* bc, T* xp,
+                          cudaStream_t s);
+
+// reductions with a fixed block count: deterministic results
+constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
+constexpr int RED_THREADS = 256;
+template <typename T>  // out[0] = sum x  (scratch >= RED_BLOCKS doubles)
+void launch_sum(int n, const T* x, double* scratch, double* out, cudaStream_t s);
+template <typename T>  // x -= (*sum) / n
+void launch_sub_mean(int n, T* x, const double* sum, cudaStream_t s);
+template <typename T>  // out = in - (*sum)/n
+void launch_copy_sub_mean(int n, const T* in, T* out, const double* sum, cudaStream_t s);
+// h[i] = <w, V_i> for i <= j and h[j+1] = <w, w>;  V = array of j+1 device pointers
+void launch_multidot(int n, int j, const double* const* V, const double* w, double* scratch,
+                     double* h, cudaStream_t s);
+// w -= sum_i h[i] V_i (i <= j), then out[0] = <w, w>
+void launch_update_norm(int n, int j, const double* const* V, const double* h, double* w,
+                        double* scratch, double* out, cudaStream_t s);
+// x += sum_i y[i] V_i (i < k); V of precision TV
+template <typename TV>
+void launch_combine(int n, int k, const TV* const* V, const double* y, double* x, cudaStream_t s);
+// x *= 1 / sqrt(*nrm2)
+void launch_scale_inv_sqrt(int n, double* x, const double* nrm2, cudaStream_t s);
+void launch_scale(int n, double* x, double a, cudaStream_t s);
+template <typename T>  // y += a x
+void launch_axpy(int n, T a, const T* x, T* y, cudaStream_t s);
+template <typename TA, typename TB>
+void launch_convert(int n, const TA* a, TB* b, cudaStream_t s);
+// out[0] = number of non-finite entries, out[1] = number of entries <= 0
+void launch_check_fields(int n, const double* rho, const double* mu, double* scratch, double* out,
+                         cudaStream_t s);
+
+}  // namespace stk

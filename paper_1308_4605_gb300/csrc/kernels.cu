@@ -1,0 +1,1033 @@
+// CUDA kernels of libstokes_gb300 (sm_103a): the staggered-grid Stokes
+// operator, the App. C multigrid components and the Krylov vector kernels.
+//
+// Reference: Cai, Nonaka, Bell, Griffith & Donev, "Efficient
+// Variable-Coefficient Finite-Volume Stokes Solvers", arXiv:1308.4605.
+//   Sec. 3.1  D, G, L_mu (Eq. div_stress), face density, node/edge viscosity
+//   App. C    multicolour Gauss-Seidel, restriction, prolongation, coarse
+//             coefficients
+//
+// Conventions (see internal.cuh): packed face vectors, wall faces stored as
+// zeros and never written with anything else; face i of component a lies on
+// the low-a side of cell i.  Every stencil below is evaluated only on faces
+// that carry an unknown, so no index ever leaves its array.
+#include "internal.cuh"
+
+#include <cmath>
+
+namespace stk {
+
+namespace {
+
+constexpr int TPB = 256;
+
+__host__ __device__ __forceinline__ int wrapm(int i, int n) {
+    return i < 0 ? i + n : (i >= n ? i - n : i);
+}
+__device__ __forceinline__ int fidx(const Geom& g, int a, const int q[3]) {
+    return g.foff[a] + (q[2] * g.fe[a][1] + q[1]) * g.fe[a][0] + q[0];
+}
+__device__ __forceinline__ int cidx(const Geom& g, const int q[3]) {
+    return (q[2] * g.n[1] + q[1]) * g.n[0] + q[0];
+}
+__device__ __forceinline__ int eidx(const Geom& g, int p, const int q[3]) {
+    return (q[2] * g.ee[p][1] + q[1]) * g.ee[p][0] + q[0];
+}
+__device__ __forceinline__ void decode(int t, const int e[3], int q[3]) {
+    q[0] = t % e[0];
+    int r = t / e[0];
+    q[1] = r % e[1];
+    q[2] = r / e[1];
+}
+__device__ __forceinline__ bool wall_face(const Geom& g, int a, const int q[3]) {
+    return !g.per[a] && (q[a] == 0 || q[a] == g.n[a]);
+}
+__device__ __forceinline__ int step(const Geom& g, int ax, int i, int d) {
+    return g.per[ax] ? wrapm(i + d, g.n[ax]) : i + d;
+}
+
+template <typename T> __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
+
+// (L_mu phi)_A and the diagonal of A at the interior A-face q
+// (Eq. div_stress with the wall closures of Sec. 3.1).  phi is a packed
+// velocity vector of precision TV; arithmetic in T.
+template <int DIM, int A, typename T, typename TV>
+__device__ __forceinline__ T viscous_face(const Geom& g, const Coef<T>& C, const int q[3],
+                                          const TV* __restrict__ phi, T& dsum) {
+    const T ih = T(g.ih), ih2 = T(g.ih2);
+    int qp[3] = {q[0], q[1], q[2]};
+    int qm[3] = {q[0], q[1], q[2]};
+    qp[A] = step(g, A, q[A], 1);
+    qm[A] = step(g, A, q[A], -1);
+    const T pa = T(phi[fidx(g, A, q)]);
+    const T pp = T(phi[fidx(g, A, qp)]);
+    const T pm = T(phi[fidx(g, A, qm)]);
+    // normal stress 2 mu du_A/dx_A at the two cells on either side of the face
+    const T mh = ld(C.mu_c + cidx(g, q));
+    const T ml = ld(C.mu_c + cidx(g, qm));
+    T L = T(2) * ih2 * (mh * (pp - pa) - ml * (pa - pm));
+    dsum = T(2) * ih2 * (mh + ml);
+#pragma unroll
+    for (int B = 0; B < DIM; ++B) {
+        if (B == A) continue;
+        const int P = A + B - 1;   // edge pair index of {A, B}
+        const bool wlo = !g.per[B] && q[B] == 0;
+        const bool whi = !g.per[B] && q[B] == g.n[B] - 1;
+        int qe[3] = {q[0], q[1], q[2]};
+        qe[B] = step(g, B, q[B], 1);
+        const T mlo = ld(C.mu_e[P] + eidx(g, P, q));
+        const T mhi = ld(C.mu_e[P] + eidx(g, P, qe));
+        T dlo, dhi;
+        if (wlo) {
+            dlo = T(2) * pa * ih;          // (phi - 0) / (h/2)
+        } else {
+            int qb[3] = {q[0], q[1], q[2]};
+            qb[B] = step(g, B, q[B], -1);
+            dlo = (pa - T(phi[fidx(g, A, qb)])) * ih;
+        }
+        if (whi) {
+            dhi = T(-2) * pa * ih;
+        } else {
+            dhi = (T(phi[fidx(g, A, qe)]) - pa) * ih;
+        }
+        // d phi_B / dx_A on the two edges: B-faces in A-cells q[A] and q[A]-1
+        int r1[3] = {q[0], q[1], q[2]};
+        int r0[3] = {q[0], q[1], q[2]};
+        r0[A] = qm[A];
+        int r3[3] = {qe[0], qe[1], qe[2]};
+        int r2[3] = {qe[0], qe[1], qe[2]};
+        r2[A] = qm[A];
+        const T xlo = (T(phi[fidx(g, B, r1)]) - T(phi[fidx(g, B, r0)])) * ih;
+        const T xhi = (T(phi[fidx(g, B, r3)]) - T(phi[fidx(g, B, r2)])) * ih;
+        L += ih * (mhi * (dhi + xhi) - mlo * (dlo + xlo));
+        dsum += ih2 * ((whi ? T(2) : T(1)) * mhi + (wlo ? T(2) : T(1)) * mlo);
+    }
+    return L;
+}
+
+// (L_rho phi) at cell q and its diagonal; beta = 0 on wall faces.
+template <int DIM, typename T, typename TV>
+__device__ __forceinline__ T poisson_cell(const Geom& g, const Coef<T>& C, const int q[3],
+                                          const TV* __restrict__ phi, T& diag) {
+    const T ih2 = T(g.ih2);
+    const T pc = T(phi[cidx(g, q)]);
+    T L = T(0);
+    diag = T(0);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        int fh[3] = {q[0], q[1], q[2]};
+        fh[a] = g.per[a] ? wrapm(q[a] + 1, g.n[a]) : q[a] + 1;
+        const T bh = ld(C.beta + fidx(g, a, fh));
+        const T bl = ld(C.beta + fidx(g, a, q));
+        int ch[3] = {q[0], q[1], q[2]};
+        int cl[3] = {q[0], q[1], q[2]};
+        ch[a] = g.per[a] ? wrapm(q[a] + 1, g.n[a]) : min(q[a] + 1, g.n[a] - 1);
+        cl[a] = g.per[a] ? wrapm(q[a] - 1, g.n[a]) : max(q[a] - 1, 0);
+        L += ih2 * (bh * (T(phi[cidx(g, ch)]) - pc) - bl * (pc - T(phi[cidx(g, cl)])));
+        diag -= ih2 * (bh + bl);
+    }
+    return L;
+}
+
+// Block ranges: blocks [start[s], start[s+1]) serve segment s.
+struct Segs {
+    int start[5];
+    int nseg;
+};
+
+inline Segs face_segs(const Geom& g, bool with_cells) {
+    Segs s{};
+    int b = 0;
+    for (int a = 0; a < g.dim; ++a) {
+        s.start[a] = b;
+        b += (g.fsize[a] + TPB - 1) / TPB;
+    }
+    s.nseg = g.dim;
+    if (with_cells) {
+        s.start[g.dim] = b;
+        b += (g.ncell + TPB - 1) / TPB;
+        s.nseg = g.dim + 1;
+    }
+    s.start[s.nseg] = b;
+    return s;
+}
+
+__device__ __forceinline__ int seg_of(const Segs& s, int blk, int& local) {
+    int k = 0;
+    while (k + 1 < s.nseg && blk >= s.start[k + 1]) ++k;
+    local = (blk - s.start[k]) * blockDim.x + threadIdx.x;
+    return k;
+}
+
+// ------------------------------------------------------------------ coefficients
+__global__ void k_fine_faces(Geom g, const double* __restrict__ rho, double theta,
+                             double* alpha, double* beta) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.nvel) return;
+    int a = 0;
+    while (a + 1 < g.dim && t >= g.foff[a + 1]) ++a;
+    int q[3];
+    decode(t - g.foff[a], g.fe[a], q);
+    if (wall_face(g, a, q)) {
+        alpha[t] = 0.0;
+        beta[t] = 0.0;
+        return;
+    }
+    int qm[3] = {q[0], q[1], q[2]};
+    qm[a] = step(g, a, q[a], -1);
+    double rf = 0.5 * (rho[cidx(g, q)] + rho[cidx(g, qm)]);
+    alpha[t] = theta * rf;
+    beta[t] = 1.0 / rf;
+}
+
+// Node (2D) / edge (3D) viscosity: mean of the in-domain cells around the
+// edge, zero on free-slip walls and on edges lying on two walls.
+__global__ void k_fine_edges(Geom g, int p, int a, int b, const double* __restrict__ mu,
+                             double* mu_e) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.esize[p]) return;
+    int q[3];
+    decode(t, g.ee[p], q);
+    double acc = 0.0;
+    int cnt = 0;
+    for (int da = -1; da <= 0; ++da)
+        for (int db = -1; db <= 0; ++db) {
+            int c[3] = {q[0], q[1], q[2]};
+            c[a] += da;
+            c[b] += db;
+            bool ok = true;
+            const int axes[2] = {a, b};
+            for (int m = 0; m < 2; ++m) {
+                const int ax = axes[m];
+                if (g.per[ax]) c[ax] = wrapm(c[ax], g.n[ax]);
+                else if (c[ax] < 0 || c[ax] >= g.n[ax]) ok = false;
+            }
+            if (ok) {
+                acc += mu[cidx(g, c)];
+                ++cnt;
+            }
+        }
+    double v = cnt ? acc / cnt : 0.0;
+    bool wa = !g.per[a] && (q[a] == 0 || q[a] == g.n[a]);
+    bool wb = !g.per[b] && (q[b] == 0 || q[b] == g.n[b]);
+    if (wa && wb) v = 0.0;
+    if (wa && ((q[a] == 0 && g.bclo[a] == FREESLIP) || (q[a] == g.n[a] && g.bchi[a] == FREESLIP)))
+        v = 0.0;
+    if (wb && ((q[b] == 0 && g.bclo[b] == FREESLIP) || (q[b] == g.n[b] && g.bchi[b] == FREESLIP)))
+        v = 0.0;
+    mu_e[t] = v;
+}
+
+// Coarse face coefficients: mean of the overlying fine faces (App. C).
+__global__ void k_coarsen_faces(Geom gf, Geom gc, const double* __restrict__ af,
+                                const double* __restrict__ bf, double* ac, double* bcoef) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= gc.nvel) return;
+    int a = 0;
+    while (a + 1 < gc.dim && t >= gc.foff[a + 1]) ++a;
+    int Q[3];
+    decode(t - gc.foff[a], gc.fe[a], Q);
+    double sa = 0.0, sb = 0.0;
+    int cnt = 0;
+    int tb[2], nt = 0;
+    for (int b = 0; b < gc.dim; ++b)
+        if (b != a) tb[nt++] = b;
+    for (int m = 0; m < (1 << nt); ++m) {
+        int q[3] = {2 * Q[0], 2 * Q[1], gc.dim == 3 ? 2 * Q[2] : 0};
+        for (int k = 0; k < nt; ++k) q[tb[k]] += (m >> k) & 1;
+        int f = fidx(gf, a, q);
+        sa += af[f];
+        sb += bf[f];
+        ++cnt;
+    }
+    ac[t] = sa / cnt;
+    bcoef[t] = sb / cnt;
+}
+
+__global__ void k_coarsen_cells(Geom gf, Geom gc, const double* __restrict__ mf, double* mc) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= gc.ncell) return;
+    int Q[3];
+    decode(t, gc.n, Q);
+    double s = 0.0;
+    int nz = gc.dim == 3 ? 2 : 1;
+    for (int dz = 0; dz < nz; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+                int q[3] = {2 * Q[0] + dx, 2 * Q[1] + dy, (gc.dim == 3 ? 2 * Q[2] : 0) + dz};
+                s += mf[cidx(gf, q)];
+            }
+    mc[t] = s / (gc.dim == 3 ? 8.0 : 4.0);
+}
+
+// Coarse node viscosity by injection (2D); coarse edge viscosity as the mean
+// of the two overlying fine edges (3D), App. C.
+__global__ void k_coarsen_edges(Geom gf, Geom gc, int p, int c, const double* __restrict__ ef,
+                                double* ec) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= gc.esize[p]) return;
+    int Q[3];
+    decode(t, gc.ee[p], Q);
+    if (gc.dim == 2) {
+        int q[3] = {2 * Q[0], 2 * Q[1], 0};
+        ec[t] = ef[eidx(gf, p, q)];
+    } else {
+        int q[3] = {2 * Q[0], 2 * Q[1], 2 * Q[2]};
+        double v = ef[eidx(gf, p, q)];
+        q[c] += 1;
+        v += ef[eidx(gf, p, q)];
+        ec[t] = 0.5 * v;
+    }
+}
+
+template <int DIM>
+__global__ void k_inverse_diagonals(Geom g, Coef<double> C, Segs sg) {
+    int t;
+    int s = seg_of(sg, blockIdx.x, t);
+    int q[3];
+    if (s == DIM) {
+        if (t >= g.ncell) return;
+        decode(t, g.n, q);
+        double d;
+        double dummy = 0.0;
+        (void)dummy;
+        poisson_cell<DIM, double, double>(g, C, q, C.beta, d);   // phi unused for diag
+        C.invd_p[t] = d != 0.0 ? 1.0 / d : 0.0;
+        return;
+    }
+    if (t >= g.fsize[s]) return;
+    decode(t, g.fe[s], q);
+    int f = g.foff[s] + t;
+    if (wall_face(g, s, q)) {
+        C.invd_u[f] = 0.0;
+        return;
+    }
+    double dsum = 0.0;
+    if (s == 0) viscous_face<DIM, 0, double, double>(g, C, q, C.alpha, dsum);
+    else if (s == 1) viscous_face<DIM, 1, double, double>(g, C, q, C.alpha, dsum);
+    else viscous_face<DIM, DIM == 3 ? 2 : 1, double, double>(g, C, q, C.alpha, dsum);
+    double d = C.alpha[f] + dsum;
+    C.invd_u[f] = d != 0.0 ? 1.0 / d : 0.0;
+}
+
+template <typename TA, typename TB>
+__global__ void k_convert(int n, const TA* __restrict__ a, TB* __restrict__ b) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) b[t] = TB(a[t]);
+}
+
+// ----------------------------------------------------------------- Stokes matvec
+// y_u = alpha x_u - L_mu x_u + G x_p on unknown faces (0 on wall faces),
+// y_p = -D x_u on cells (Eq. Saddle_sys).
+template <int DIM, typename TV>
+__global__ void k_stokes_matvec(Geom g, Coef<double> C, Segs sg, const TV* __restrict__ x,
+                                const double* __restrict__ b, double* __restrict__ y) {
+    int t;
+    int s = seg_of(sg, blockIdx.x, t);
+    int q[3];
+    const TV* xp = x + g.nvel;
+    if (s == DIM) {
+        if (t >= g.ncell) return;
+        decode(t, g.n, q);
+        double div = 0.0;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            int qh[3] = {q[0], q[1], q[2]};
+            qh[a] = step(g, a, q[a], 1);
+            div += (double(x[fidx(g, a, qh)]) - double(x[fidx(g, a, q)])) * g.ih;
+        }
+        int c = g.nvel + t;
+        y[c] = b ? b[c] + div : -div;
+        return;
+    }
+    if (t >= g.fsize[s]) return;
+    decode(t, g.fe[s], q);
+    int f = g.foff[s] + t;
+    if (wall_face(g, s, q)) {
+        y[f] = 0.0;
+        return;
+    }
+    double dsum, L;
+    if (s == 0) L = viscous_face<DIM, 0, double, TV>(g, C, q, x, dsum);
+    else if (s == 1) L = viscous_face<DIM, 1, double, TV>(g, C, q, x, dsum);
+    else L = viscous_face<DIM, DIM == 3 ? 2 : 1, double, TV>(g, C, q, x, dsum);
+    int qm[3] = {q[0], q[1], q[2]};
+    qm[s] = step(g, s, q[s], -1);
+    double grad = (double(xp[cidx(g, q)]) - double(xp[cidx(g, qm)])) * g.ih;
+    double Mx = ld(C.alpha + f) * double(x[f]) - L + grad;
+    y[f] = b ? b[f] - Mx : Mx;
+}
+
+// ------------------------------------------------------------------- multigrid
+// One colour of the staggered Gauss-Seidel smoother (App. C): every A-face
+// with (i + j + k) % 2 == parity gets phi += D^{-1} (rhs - A phi).
+template <int DIM, int A, typename T>
+__global__ void k_vel_gs(Geom g, Coef<T> C, int parity, T* __restrict__ phi,
+                         const T* __restrict__ rhs) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e0 = g.fe[A][0];
+    const int half = (e0 + 1) >> 1;
+    if (t >= half * g.fe[A][1] * g.fe[A][2]) return;
+    int q[3];
+    q[0] = t % half;
+    int r = t / half;
+    q[1] = r % g.fe[A][1];
+    q[2] = r / g.fe[A][1];
+    q[0] = 2 * q[0] + ((q[1] + q[2] + parity) & 1);
+    if (q[0] >= e0 || wall_face(g, A, q)) return;
+    T dsum;
+    T L = viscous_face<DIM, A, T, T>(g, C, q, phi, dsum);
+    int f = fidx(g, A, q);
+    T p = phi[f];
+    T res = rhs[f] - (ld(C.alpha + f) * p - L);
+    phi[f] = p + res * ld(C.invd_u + f);
+}
+
+template <int DIM, typename T>
+__global__ void k_vel_residual(Geom g, Coef<T> C, Segs sg, const T* __restrict__ phi,
+                               const T* __restrict__ rhs, T* __restrict__ res) {
+    int t;
+    int s = seg_of(sg, blockIdx.x, t);
+    if (t >= g.fsize[s]) return;
+    int q[3];
+    decode(t, g.fe[s], q);
+    int f = g.foff[s] + t;
+    if (wall_face(g, s, q)) {
+        res[f] = T(0);
+        return;
+    }
+    T dsum, L;
+    if (s == 0) L = viscous_face<DIM, 0, T, T>(g, C, q, phi, dsum);
+    else if (s == 1) L = viscous_face<DIM, 1, T, T>(g, C, q, phi, dsum);
+    else L = viscous_face<DIM, DIM == 3 ? 2 : 1, T, T>(g, C, q, phi, dsum);
+    res[f] = rhs[f] - (ld(C.alpha + f) * phi[f] - L);
+}
+
+// 6-point (2D) / 12-point (3D) face restriction (App. C).
+template <int DIM, typename T>
+__global__ void k_vel_restrict(Geom gf, Geom gc, Segs sg, const T* __restrict__ res,
+                               T* __restrict__ rc) {
+    int t;
+    int a = seg_of(sg, blockIdx.x, t);
+    if (t >= gc.fsize[a]) return;
+    int Q[3];
+    decode(t, gc.fe[a], Q);
+    int f = gc.foff[a] + t;
+    if (wall_face(gc, a, Q)) {
+        rc[f] = T(0);
+        return;
+    }
+    int tb[2], nt = 0;
+    for (int b = 0; b < DIM; ++b)
+        if (b != a) tb[nt++] = b;
+    const T wt = DIM == 3 ? T(0.25) : T(0.5);
+    T acc = T(0);
+    for (int s = -1; s <= 1; ++s) {
+        T w = (s == 0 ? T(0.5) : T(0.25)) * wt;
+        for (int m = 0; m < (1 << nt); ++m) {
+            int q[3] = {2 * Q[0], 2 * Q[1], DIM == 3 ? 2 * Q[2] : 0};
+            q[a] = step(gf, a, q[a], s);
+            for (int k = 0; k < nt; ++k) q[tb[k]] += (m >> k) & 1;
+            acc += w * res[fidx(gf, a, q)];
+        }
+    }
+    rc[f] = acc;
+}
+
+// Face prolongation and correction phi_f += P phi_c (App. C): along the face
+// normal the coarse face (even index) or the mean of the two coarse faces
+// (odd index); across, 3/4 on the own coarse cell and 1/4 on the nearer
+// neighbour, whose ghost across a wall is -phi (no-slip) or +phi (free-slip).
+template <int DIM, typename T>
+__global__ void k_vel_prolong_add(Geom gc, Geom gf, Segs sg, const T* __restrict__ pc,
+                                  T* __restrict__ pf) {
+    int t;
+    int a = seg_of(sg, blockIdx.x, t);
+    if (t >= gf.fsize[a]) return;
+    int q[3];
+    decode(t, gf.fe[a], q);
+    if (wall_face(gf, a, q)) return;
+    int ca[2];
+    T wa[2];
+    int na;
+    if ((q[a] & 1) == 0) {
+        ca[0] = q[a] >> 1;
+        wa[0] = T(1);
+        na = 1;
+    } else {
+        ca[0] = q[a] >> 1;
+        ca[1] = (q[a] + 1) >> 1;
+        if (gc.per[a] && ca[1] >= gc.n[a]) ca[1] -= gc.n[a];
+        wa[0] = wa[1] = T(0.5);
+        na = 2;
+    }
+    int tb[2], nt = 0;
+    for (int b = 0; b < DIM; ++b)
+        if (b != a) tb[nt++] = b;
+    int cj[2][2];
+    T wj[2][2];
+    for (int k = 0; k < nt; ++k) {
+        int b = tb[k];
+        int j = q[b];
+        int J = j >> 1;
+        int nb = (j & 1) ? J + 1 : J - 1;
+        T wo = T(0.75), wn = T(0.25);
+        if (nb < 0 || nb >= gc.n[b]) {
+            if (gc.per[b]) {
+                nb = wrapm(nb, gc.n[b]);
+            } else {
+                int code = nb < 0 ? gc.bclo[b] : gc.bchi[b];
+                wo += code == NOSLIP ? T(-0.25) : T(0.25);
+                wn = T(0);
+                nb = J;
+            }
+        }
+        cj[k][0] = J;
+        wj[k][0] = wo;
+        cj[k][1] = nb;
+        wj[k][1] = wn;
+    }
+    T acc = T(0);
+    for (int ia = 0; ia < na; ++ia)
+        for (int m = 0; m < (1 << nt); ++m) {
+            int Q[3] = {0, 0, 0};
+            Q[a] = ca[ia];
+            T w = wa[ia];
+            for (int k = 0; k < nt; ++k) {
+                int sel = (m >> k) & 1;
+                Q[tb[k]] = cj[k][sel];
+                w *= wj[k][sel];
+            }
+            if (w != T(0)) acc += w * pc[fidx(gc, a, Q)];
+        }
+    pf[gf.foff[a] + t] += acc;
+}
+
+// Red-black Gauss-Seidel colour for L_rho phi = rhs (App. C).
+template <int DIM, typename T>
+__global__ void k_cell_gs(Geom g, Coef<T> C, int parity, T* __restrict__ phi,
+                          const T* __restrict__ rhs) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int half = g.n[0] >> 1;
+    if (t >= half * g.n[1] * g.n[2]) return;
+    int q[3];
+    q[0] = t % half;
+    int r = t / half;
+    q[1] = r % g.n[1];
+    q[2] = r / g.n[1];
+    q[0] = 2 * q[0] + ((q[1] + q[2] + parity) & 1);
+    T d;
+    T L = poisson_cell<DIM, T, T>(g, C, q, phi, d);
+    int c = cidx(g, q);
+    phi[c] += (rhs[c] - L) * ld(C.invd_p + c);
+}
+
+template <int DIM, typename T>
+__global__ void k_cell_residual(Geom g, Coef<T> C, const T* __restrict__ phi,
+                                const T* __restrict__ rhs, T* __restrict__ res) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.ncell) return;
+    int q[3];
+    decode(t, g.n, q);
+    T d;
+    res[t] = rhs[t] - poisson_cell<DIM, T, T>(g, C, q, phi, d);
+}
+
+template <int DIM, typename T>
+__global__ void k_cell_restrict(Geom gf, Geom gc, const T* __restrict__ res, T* __restrict__ rc) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= gc.ncell) return;
+    int Q[3];
+    decode(t, gc.n, Q);
+    T s = T(0);
+    for (int dz = 0; dz < (DIM == 3 ? 2 : 1); ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+                int q[3] = {2 * Q[0] + dx, 2 * Q[1] + dy, (DIM == 3 ? 2 * Q[2] : 0) + dz};
+                s += res[cidx(gf, q)];
+            }
+    rc[t] = s * (DIM == 3 ? T(0.125) : T(0.25));
+}
+
+template <int DIM, typename T>
+__global__ void k_cell_prolong_add(Geom gc, Geom gf, const T* __restrict__ pc, T* __restrict__ pf) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= gf.ncell) return;
+    int q[3];
+    decode(t, gf.n, q);
+    int Q[3] = {q[0] >> 1, q[1] >> 1, DIM == 3 ? q[2] >> 1 : 0};
+    pf[t] += pc[cidx(gc, Q)];
+}
+
+// -------------------------------------------------------- preconditioner algebra
+template <int DIM, typename T>
+__global__ void k_div_plus(Geom g, const T* __restrict__ u, const T* __restrict__ bp,
+                           T* __restrict__ bc) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.ncell) return;
+    int q[3];
+    decode(t, g.n, q);
+    T div = T(0);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        int qh[3] = {q[0], q[1], q[2]};
+        qh[a] = step(g, a, q[a], 1);
+        div += (u[fidx(g, a, qh)] - u[fidx(g, a, q)]) * T(g.ih);
+    }
+    bc[t] = div + (bp ? bp[t] : T(0));
+}
+
+template <int DIM, typename T>
+__global__ void k_sub_grad(Geom g, Segs sg, const T* __restrict__ beta, const T* __restrict__ u,
+                           const T* __restrict__ p, T* __restrict__ out) {
+    int t;
+    int a = seg_of(sg, blockIdx.x, t);
+    if (t >= g.fsize[a]) return;
+    int q[3];
+    decode(t, g.fe[a], q);
+    int f = g.foff[a] + t;
+    if (wall_face(g, a, q)) {
+        out[f] = T(0);
+        return;
+    }
+    int qm[3] = {q[0], q[1], q[2]};
+    qm[a] = step(g, a, q[a], -1);
+    T grad = (p[cidx(g, q)] - p[cidx(g, qm)]) * T(g.ih);
+    out[f] = u[f] - (beta ? beta[f] : T(1)) * grad;
+}
+
+template <int DIM, typename T>
+__global__ void k_vel_correction_rhs(Geom g, Coef<T> C, Segs sg, const T* __restrict__ b,
+                                     const T* __restrict__ p, const T* __restrict__ u,
+                                     T* __restrict__ out) {
+    int t;
+    int s = seg_of(sg, blockIdx.x, t);
+    if (t >= g.fsize[s]) return;
+    int q[3];
+    decode(t, g.fe[s], q);
+    int f = g.foff[s] + t;
+    if (wall_face(g, s, q)) {
+        out[f] = T(0);
+        return;
+    }
+    T dsum, L;
+    if (s == 0) L = viscous_face<DIM, 0, T, T>(g, C, q, u, dsum);
+    else if (s == 1) L = viscous_face<DIM, 1, T, T>(g, C, q, u, dsum);
+    else L = viscous_face<DIM, DIM == 3 ? 2 : 1, T, T>(g, C, q, u, dsum);
+    int qm[3] = {q[0], q[1], q[2]};
+    qm[s] = step(g, s, q[s], -1);
+    T grad = (p[cidx(g, q)] - p[cidx(g, qm)]) * T(g.ih);
+    out[f] = b[f] - grad - (ld(C.alpha + f) * u[f] - L);
+}
+
+template <typename T>
+__global__ void k_schur_combine(int n, double theta, const T* __restrict__ phi,
+                                const T* __restrict__ mu, const T* __restrict__ bc,
+                                T* __restrict__ xp) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    T v = -T(2) * mu[t] * bc[t];
+    if (phi) v += T(theta) * phi[t];
+    xp[t] = v;
+}
+
+// ------------------------------------------------------------------ reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        r = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    return r;   // valid in thread 0
+}
+
+template <typename T>
+__global__ void k_sum_partials(int n, const T* __restrict__ x, double* part) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        s += double(x[i]);
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// out[k] = sum over RED_BLOCKS partials part[k * RED_BLOCKS + b], fixed order.
+__global__ void k_final(int nk, const double* __restrict__ part, double* out) {
+    __shared__ double sh[32];
+    for (int k = 0; k < nk; ++k) {
+        double s = 0.0;
+        for (int b = threadIdx.x; b < RED_BLOCKS; b += blockDim.x) s += part[k * RED_BLOCKS + b];
+        s = block_sum(s, sh);
+        if (threadIdx.x == 0) out[k] = s;
+    }
+}
+
+template <typename T>
+__global__ void k_sub_mean(int n, T* x, const double* __restrict__ sum) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) x[t] -= T(*sum / n);
+}
+
+template <typename T>
+__global__ void k_copy_sub_mean(int n, const T* __restrict__ in, T* out,
+                                const double* __restrict__ sum) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) out[t] = in[t] - T(*sum / n);
+}
+
+constexpr int MAXV = 33;
+struct PtrArr {
+    const void* p[MAXV];
+};
+
+__global__ void k_multidot(int n, int j, PtrArr V, const double* __restrict__ w, double* part) {
+    __shared__ double sh[32];
+    double acc[MAXV + 1];
+#pragma unroll
+    for (int i = 0; i <= MAXV; ++i) acc[i] = 0.0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        double wv = w[t];
+#pragma unroll
+        for (int i = 0; i < MAXV; ++i)
+            if (i <= j) acc[i] += wv * static_cast<const double*>(V.p[i])[t];
+        acc[MAXV] += wv * wv;
+    }
+#pragma unroll
+    for (int i = 0; i < MAXV; ++i) {
+        if (i <= j) {
+            double s = block_sum(acc[i], sh);
+            if (threadIdx.x == 0) part[i * RED_BLOCKS + blockIdx.x] = s;
+        }
+    }
+    double s = block_sum(acc[MAXV], sh);
+    if (threadIdx.x == 0) part[(j + 1) * RED_BLOCKS + blockIdx.x] = s;
+}
+
+__global__ void k_update_norm(int n, int j, PtrArr V, const double* __restrict__ h, double* w,
+                              double* part) {
+    __shared__ double sh[32];
+    double hh[MAXV];
+#pragma unroll
+    for (int i = 0; i < MAXV; ++i) hh[i] = i <= j ? h[i] : 0.0;
+    double s = 0.0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        double wv = w[t];
+#pragma unroll
+        for (int i = 0; i < MAXV; ++i)
+            if (i <= j) wv -= hh[i] * static_cast<const double*>(V.p[i])[t];
+        w[t] = wv;
+        s += wv * wv;
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+template <typename TV>
+__global__ void k_combine(int n, int k, PtrArr V, const double* __restrict__ y, double* x) {
+    double yy[MAXV];
+#pragma unroll
+    for (int i = 0; i < MAXV; ++i) yy[i] = i < k ? y[i] : 0.0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        double acc = x[t];
+#pragma unroll
+        for (int i = 0; i < MAXV; ++i)
+            if (i < k) acc += yy[i] * double(static_cast<const TV*>(V.p[i])[t]);
+        x[t] = acc;
+    }
+}
+
+__global__ void k_scale_inv_sqrt(int n, double* x, const double* __restrict__ nrm2) {
+    double s = 1.0 / sqrt(*nrm2);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
+        x[t] *= s;
+}
+
+template <typename T>
+__global__ void k_axpy(int n, T a, const T* __restrict__ x, T* __restrict__ y) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) y[t] += a * x[t];
+}
+
+__global__ void k_scale(int n, double* x, double a) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
+        x[t] *= a;
+}
+
+__global__ void k_check_fields(int n, const double* __restrict__ rho, const double* __restrict__ mu,
+                               double* part) {
+    __shared__ double sh[32];
+    double bad = 0.0, nonpos = 0.0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        double r = rho[t], m = mu[t];
+        if (!isfinite(r) || !isfinite(m)) bad += 1.0;
+        else if (r <= 0.0 || m < 0.0) nonpos += 1.0;
+    }
+    double s = block_sum(bad, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+    s = block_sum(nonpos, sh);
+    if (threadIdx.x == 0) part[RED_BLOCKS + blockIdx.x] = s;
+}
+
+inline int nblk(long long n) { return (int)((n + TPB - 1) / TPB); }
+
+}  // namespace
+
+// ============================================================== launch wrappers
+void launch_fine_coefficients(const Geom& g, const double* rho, const double* mu, double theta,
+                              Coef<double> C, cudaStream_t s) {
+    k_fine_faces<<<nblk(g.nvel), TPB, 0, s>>>(g, rho, theta, C.alpha, C.beta);
+    cudaMemcpyAsync(C.mu_c, mu, sizeof(double) * g.ncell, cudaMemcpyDeviceToDevice, s);
+    for (int a = 0; a < g.dim; ++a)
+        for (int b = a + 1; b < g.dim; ++b) {
+            int p = a + b - 1;
+            k_fine_edges<<<nblk(g.esize[p]), TPB, 0, s>>>(g, p, a, b, mu, C.mu_e[p]);
+        }
+}
+
+void launch_coarsen_coefficients(const Geom& gf, Coef<double> Cf, const Geom& gc, Coef<double> Cc,
+                                 cudaStream_t s) {
+    k_coarsen_faces<<<nblk(gc.nvel), TPB, 0, s>>>(gf, gc, Cf.alpha, Cf.beta, Cc.alpha, Cc.beta);
+    k_coarsen_cells<<<nblk(gc.ncell), TPB, 0, s>>>(gf, gc, Cf.mu_c, Cc.mu_c);
+    for (int a = 0; a < gc.dim; ++a)
+        for (int b = a + 1; b < gc.dim; ++b) {
+            int p = a + b - 1;
+            int c = 3 - a - b;
+            k_coarsen_edges<<<nblk(gc.esize[p]), TPB, 0, s>>>(gf, gc, p, c, Cf.mu_e[p], Cc.mu_e[p]);
+        }
+}
+
+void launch_inverse_diagonals(const Geom& g, Coef<double> C, cudaStream_t s) {
+    Segs sg = face_segs(g, true);
+    if (g.dim == 2) k_inverse_diagonals<2><<<sg.start[sg.nseg], TPB, 0, s>>>(g, C, sg);
+    else k_inverse_diagonals<3><<<sg.start[sg.nseg], TPB, 0, s>>>(g, C, sg);
+}
+
+template <typename TA, typename TB>
+void launch_convert(int n, const TA* a, TB* b, cudaStream_t s) {
+    if (n > 0) k_convert<TA, TB><<<nblk(n), TPB, 0, s>>>(n, a, b);
+}
+
+void launch_convert_coefficients(const Geom& g, Coef<double> C, Coef<float> F, cudaStream_t s) {
+    launch_convert(g.nvel, C.alpha, F.alpha, s);
+    launch_convert(g.nvel, C.beta, F.beta, s);
+    launch_convert(g.ncell, C.mu_c, F.mu_c, s);
+    for (int p = 0; p < 3; ++p)
+        if (g.esize[p] > 0 && C.mu_e[p]) launch_convert(g.esize[p], C.mu_e[p], F.mu_e[p], s);
+    launch_convert(g.nvel, C.invd_u, F.invd_u, s);
+    launch_convert(g.ncell, C.invd_p, F.invd_p, s);
+}
+
+template <typename TV>
+void launch_stokes_matvec(const Geom& g, Coef<double> C, const TV* x, double* y, cudaStream_t s) {
+    Segs sg = face_segs(g, true);
+    if (g.dim == 2) k_stokes_matvec<2, TV><<<sg.start[sg.nseg], TPB, 0, s>>>(g, C, sg, x, nullptr, y);
+    else k_stokes_matvec<3, TV><<<sg.start[sg.nseg], TPB, 0, s>>>(g, C, sg, x, nullptr, y);
+}
+
+void launch_stokes_residual(const Geom& g, Coef<double> C, const double* x, const double* b,
+                            double* r, cudaStream_t s) {
+    Segs sg = face_segs(g, true);
+    if (g.dim == 2) k_stokes_matvec<2, double><<<sg.start[sg.nseg], TPB, 0, s>>>(g, C, sg, x, b, r);
+    else k_stokes_matvec<3, double><<<sg.start[sg.nseg], TPB, 0, s>>>(g, C, sg, x, b, r);
+}
+
+template <typename T>
+void launch_vel_gs_colour(const Geom& g, Coef<T> C, int comp, int parity, T* phi, const T* rhs,
+                          cudaStream_t s) {
+    int nthreads = ((g.fe[comp][0] + 1) / 2) * g.fe[comp][1] * g.fe[comp][2];
+    int nb = nblk(nthreads);
+    if (g.dim == 2) {
+        if (comp == 0) k_vel_gs<2, 0, T><<<nb, TPB, 0, s>>>(g, C, parity, phi, rhs);
+        else k_vel_gs<2, 1, T><<<nb, TPB, 0, s>>>(g, C, parity, phi, rhs);
+    } else {
+        if (comp == 0) k_vel_gs<3, 0, T><<<nb, TPB, 0, s>>>(g, C, parity, phi, rhs);
+        else if (comp == 1) k_vel_gs<3, 1, T><<<nb, TPB, 0, s>>>(g, C, parity, phi, rhs);
+        else k_vel_gs<3, 2, T><<<nb, TPB, 0, s>>>(g, C, parity, phi, rhs);
+    }
+}
+
+template <typename T>
+void launch_vel_residual(const Geom& g, Coef<T> C, const T* phi, const T* rhs, T* res,
+                         cudaStream_t s) {
+    Segs sg = face_segs(g, false);
+    if (g.dim == 2) k_vel_residual<2, T><<<sg.start[sg.nseg], TPB, 0, s>>>(g, C, sg, phi, rhs, res);
+    else k_vel_residual<3, T><<<sg.start[sg.nseg], TPB, 0, s>>>(g, C, sg, phi, rhs, res);
+}
+
+template <typename T>
+void launch_vel_restrict(const Geom& gf, const T* res, const Geom& gc, T* rc, cudaStream_t s) {
+    Segs sg = face_segs(gc, false);
+    if (gf.dim == 2) k_vel_restrict<2, T><<<sg.start[sg.nseg], TPB, 0, s>>>(gf, gc, sg, res, rc);
+    else k_vel_restrict<3, T><<<sg.start[sg.nseg], TPB, 0, s>>>(gf, gc, sg, res, rc);
+}
+
+template <typename T>
+void launch_vel_prolong_add(const Geom& gc, const T* pc, const Geom& gf, T* pf, cudaStream_t s) {
+    Segs sg = face_segs(gf, false);
+    if (gf.dim == 2) k_vel_prolong_add<2, T><<<sg.start[sg.nseg], TPB, 0, s>>>(gc, gf, sg, pc, pf);
+    else k_vel_prolong_add<3, T><<<sg.start[sg.nseg], TPB, 0, s>>>(gc, gf, sg, pc, pf);
+}
+
+template <typename T>
+void launch_cell_gs_colour(const Geom& g, Coef<T> C, int parity, T* phi, const T* rhs,
+                           cudaStream_t s) {
+    int nb = nblk((g.n[0] / 2) * g.n[1] * g.n[2]);
+    if (g.dim == 2) k_cell_gs<2, T><<<nb, TPB, 0, s>>>(g, C, parity, phi, rhs);
+    else k_cell_gs<3, T><<<nb, TPB, 0, s>>>(g, C, parity, phi, rhs);
+}
+
+template <typename T>
+void launch_cell_residual(const Geom& g, Coef<T> C, const T* phi, const T* rhs, T* res,
+                          cudaStream_t s) {
+    if (g.dim == 2) k_cell_residual<2, T><<<nblk(g.ncell), TPB, 0, s>>>(g, C, phi, rhs, res);
+    else k_cell_residual<3, T><<<nblk(g.ncell), TPB, 0, s>>>(g, C, phi, rhs, res);
+}
+
+template <typename T>
+void launch_cell_restrict(const Geom& gf, const T* res, const Geom& gc, T* rc, cudaStream_t s) {
+    if (gf.dim == 2) k_cell_restrict<2, T><<<nblk(gc.ncell), TPB, 0, s>>>(gf, gc, res, rc);
+    else k_cell_restrict<3, T><<<nblk(gc.ncell), TPB, 0, s>>>(gf, gc, res, rc);
+}
+
+template <typename T>
+void launch_cell_prolong_add(const Geom& gc, const T* pc, const Geom& gf, T* pf, cudaStream_t s) {
+    if (gf.dim == 2) k_cell_prolong_add<2, T><<<nblk(gf.ncell), TPB, 0, s>>>(gc, gf, pc, pf);
+    else k_cell_prolong_add<3, T><<<nblk(gf.ncell), TPB, 0, s>>>(gc, gf, pc, pf);
+}
+
+template <typename T>
+void launch_div_plus(const Geom& g, const T* u, const T* bp, T* bc, cudaStream_t s) {
+    if (g.dim == 2) k_div_plus<2, T><<<nblk(g.ncell), TPB, 0, s>>>(g, u, bp, bc);
+    else k_div_plus<3, T><<<nblk(g.ncell), TPB, 0, s>>>(g, u, bp, bc);
+}
+
+template <typename T>
+void launch_sub_grad(const Geom& g, const T* beta, const T* u, const T* p, T* out, cudaStream_t s) {
+    Segs sg = face_segs(g, false);
+    if (g.dim == 2) k_sub_grad<2, T><<<sg.start[sg.nseg], TPB, 0, s>>>(g, sg, beta, u, p, out);
+    else k_sub_grad<3, T><<<sg.start[sg.nseg], TPB, 0, s>>>(g, sg, beta, u, p, out);
+}
+
+template <typename T>
+void launch_vel_correction_rhs(const Geom& g, Coef<T> C, const T* b, const T* p, const T* u,
+                               T* out, cudaStream_t s) {
+    Segs sg = face_segs(g, false);
+    if (g.dim == 2)
+        k_vel_correction_rhs<2, T><<<sg.start[sg.nseg], TPB, 0, s>>>(g, C, sg, b, p, u, out);
+    else
+        k_vel_correction_rhs<3, T><<<sg.start[sg.nseg], TPB, 0, s>>>(g, C, sg, b, p, u, out);
+}
+
+template <typename T>
+void launch_schur_combine(int n, double theta, const T* phi, const T* mu, const T* bc, T* xp,
+                          cudaStream_t s) {
+    k_schur_combine<T><<<nblk(n), TPB, 0, s>>>(n, theta, phi, mu, bc, xp);
+}
+
+template <typename T>
+void launch_sum(int n, const T* x, double* scratch, double* out, cudaStream_t s) {
+    k_sum_partials<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, x, scratch);
+    k_final<<<1, RED_THREADS, 0, s>>>(1, scratch, out);
+}
+
+template <typename T>
+void launch_sub_mean(int n, T* x, const double* sum, cudaStream_t s) {
+    k_sub_mean<T><<<nblk(n), TPB, 0, s>>>(n, x, sum);
+}
+
+template <typename T>
+void launch_copy_sub_mean(int n, const T* in, T* out, const double* sum, cudaStream_t s) {
+    k_copy_sub_mean<T><<<nblk(n), TPB, 0, s>>>(n, in, out, sum);
+}
+
+void launch_multidot(int n, int j, const double* const* V, const double* w, double* scratch,
+                     double* h, cudaStream_t s) {
+    PtrArr pa{};
+    for (int i = 0; i <= j; ++i) pa.p[i] = V[i];
+    k_multidot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, j, pa, w, scratch);
+    k_final<<<1, RED_THREADS, 0, s>>>(j + 2, scratch, h);
+}
+
+void launch_update_norm(int n, int j, const double* const* V, const double* h, double* w,
+                        double* scratch, double* out, cudaStream_t s) {
+    PtrArr pa{};
+    for (int i = 0; i <= j; ++i) pa.p[i] = V[i];
+    k_update_norm<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, j, pa, h, w, scratch);
+    k_final<<<1, RED_THREADS, 0, s>>>(1, scratch, out);
+}
+
+template <typename TV>
+void launch_combine(int n, int k, const TV* const* V, const double* y, double* x, cudaStream_t s) {
+    PtrArr pa{};
+    for (int i = 0; i < k; ++i) pa.p[i] = V[i];
+    k_combine<TV><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, k, pa, y, x);
+}
+
+void launch_scale_inv_sqrt(int n, double* x, const double* nrm2, cudaStream_t s) {
+    k_scale_inv_sqrt<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, x, nrm2);
+}
+
+template <typename T>
+void launch_axpy(int n, T a, const T* x, T* y, cudaStream_t s) {
+    k_axpy<T><<<nblk(n), TPB, 0, s>>>(n, a, x, y);
+}
+
+void launch_scale(int n, double* x, double a, cudaStream_t s) {
+    k_scale<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, x, a);
+}
+
+void launch_check_fields(int n, const double* rho, const double* mu, double* scratch, double* out,
+                         cudaStream_t s) {
+    k_check_fields<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, rho, mu, scratch);
+    k_final<<<1, RED_THREADS, 0, s>>>(2, scratch, out);
+}
+
+// explicit instantiations
+#define STK_INST(T)                                                                                \
+    template void launch_vel_gs_colour<T>(const Geom&, Coef<T>, int, int, T*, const T*,          \
+                                          cudaStream_t);                                           \
+    template void launch_vel_residual<T>(const Geom&, Coef<T>, const T*, const T*, T*,           \
+                                         cudaStream_t);                                            \
+    template void launch_vel_restrict<T>(const Geom&, const T*, const Geom&, T*, cudaStream_t);  \
+    template void launch_vel_prolong_add<T>(const Geom&, const T*, const Geom&, T*,              \
+                                            cudaStream_t);                                         \
+    template void launch_cell_gs_colour<T>(const Geom&, Coef<T>, int, T*, const T*,              \
+                                           cudaStream_t);                                          \
+    template void launch_cell_residual<T>(const Geom&, Coef<T>, const T*, const T*, T*,          \
+                                          cudaStream_t);                                           \
+    template void launch_cell_restrict<T>(const Geom&, const T*, const Geom&, T*, cudaStream_t); \
+    template void launch_cell_prolong_add<T>(const Geom&, const T*, const Geom&, T*,             \
+                                             cudaStream_t);                                        \
+    template void launch_div_plus<T>(const Geom&, const T*, const T*, T*, cudaStream_t);         \
+    template void launch_sub_grad<T>(const Geom&, const T*, const T*, const T*, T*,              \
+                                     cudaStream_t);                                                \
+    template void launch_vel_correction_rhs<T>(const Geom&, Coef<T>, const T*, const T*,         \
+                                               const T*, T*, cudaStream_t);                        \
+    template void launch_schur_combine<T>(int, double, const T*, const T*, const T*, T*,         \
+                                          cudaStream_t);                                           \
+    template void launch_sum<T>(int, const T*, double*, double*, cudaStream_t);                  \
+    template void launch_sub_mean<T>(int, T*, const double*, cudaStream_t);                      \
+    template void launch_copy_sub_mean<T>(int, const T*, T*, const double*, cudaStream_t);       \
+    template void launch_combine<T>(int, int, const T* const*, const double*, double*,           \
+                                    cudaStream_t);                                                 \
+    template void launch_stokes_matvec<T>(const Geom&, Coef<double>, const T*, double*,          \
+                                          cudaStream_t);                                           \
+    template void launch_axpy<T>(int, T, const T*, T*, cudaStream_t);
+STK_INST(double)
+STK_INST(float)
+#undef STK_INST
+template void launch_convert<double, float>(int, const double*, float*, cudaStream_t);
+template void launch_convert<float, double>(int, const float*, double*, cudaStream_t);
+
+}  // namespace stk

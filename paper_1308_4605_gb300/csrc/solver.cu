@@ -1,0 +1,984 @@
+// Host side of libstokes_gb300: the multigrid hierarchy, the V-cycles
+// (App. C), the block preconditioners P1..P5 (Sec. 2), restarted GMRES
+// (Sec. 3.2) and flexible GMRES with an FP32 preconditioner (Sec. 4), and the
+// C ABI declared in include/stokes.h.
+//
+// Reference: Cai, Nonaka, Bell, Griffith & Donev, arXiv:1308.4605.
+#include "internal.cuh"
+#include "../../include/stokes.h"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace stk;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct ProfRec {
+    int cat;
+    double bytes;
+    cudaEvent_t a, b;
+};
+
+const char* kProfNames[STK_NPROF] = {
+    "stokes_matvec",    "vel_smooth_colour", "vel_residual",  "vel_restrict",
+    "vel_prolong_add",  "cell_smooth_colour", "cell_residual", "cell_restrict",
+    "cell_prolong_add", "precond_algebra",   "mean_removal",  "arnoldi_multidot",
+    "arnoldi_update",   "krylov_combine",    "convert",       "other"};
+
+enum {
+    PF_MATVEC = 0, PF_VSMOOTH, PF_VRES, PF_VRESTR, PF_VPROL, PF_CSMOOTH, PF_CRES, PF_CRESTR,
+    PF_CPROL, PF_ALG, PF_MEAN, PF_MDOT, PF_UPD, PF_COMB, PF_CONV, PF_OTHER
+};
+
+template <typename T>
+struct Work {            // multigrid work vectors of one level
+    T *phi_u, *rhs_u, *res_u, *phi_p, *rhs_p, *res_p;
+};
+
+struct Level {
+    Geom g;
+    Coef<double> cd;
+    Coef<float> cf;
+    Work<double> wd;
+    Work<float> wf;
+};
+
+template <typename T>
+struct PBuf {            // level-0 buffers of the preconditioner in precision T
+    T* in;               // packed Stokes input (mixed form: converted Krylov vector)
+    T* bc;               // cell: D x* + b_p
+    T* tmpu;             // velocity temporary
+    T* xs;               // velocity x*
+};
+
+}  // namespace
+
+struct stk_handle {
+    int device = 0;
+    int dim = 0;
+    std::vector<Level> lev;
+    double theta = 0.0;
+    bool coef_set = false;
+    std::string err;
+    std::vector<void*> allocs;
+    PBuf<double> pd{};
+    PBuf<float> pf{};
+    int m_alloc = 0;
+    std::vector<double*> V;
+    std::vector<float*> Z;
+    double *bk = nullptr, *xk = nullptr, *tmp = nullptr;
+    double* red = nullptr;    // reduction scratch (RED_BLOCKS * 36 doubles)
+    double* dsc = nullptr;    // device scalars
+    double* hpin = nullptr;   // pinned host staging
+    bool prof = false;
+    std::vector<ProfRec> recs;
+    std::vector<cudaEvent_t> evpool;
+    size_t evnext = 0;
+    long long plaunch[STK_NPROF] = {};
+    double pms[STK_NPROF] = {}, pbytes[STK_NPROF] = {};
+};
+
+namespace {
+
+constexpr int NDSC = 128;     // device scalar slots
+// slots of h->dsc
+constexpr int DS_SUM = 0;     // mean removal sums
+constexpr int DS_H = 8;       // Arnoldi column h[0..m+1]
+constexpr int DS_N2 = 48;     // norms
+constexpr int DS_Y = 64;      // least-squares solution y
+
+int fail(stk_handle* h, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    else g_create_error = buf;
+    return code;
+}
+
+#define CK(call)                                                                       \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return fail(h, STK_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));     \
+    } while (0)
+
+#define CKL()                                                                          \
+    do {                                                                               \
+        cudaError_t e_ = cudaGetLastError();                                           \
+        if (e_ != cudaSuccess)                                                         \
+            return fail(h, STK_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(stk_handle* h, T** p, size_t n) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, sizeof(T) * (n ? n : 1));
+    if (e != cudaSuccess) return e;
+    h->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return cudaMemset(q, 0, sizeof(T) * (n ? n : 1));
+}
+
+Geom make_geom(int dim, const int n[3], double hh, const int bc[6]) {
+    Geom g{};
+    g.dim = dim;
+    for (int a = 0; a < 3; ++a) {
+        g.n[a] = a < dim ? n[a] : 1;
+        g.per[a] = a < dim ? (bc[2 * a] == STK_PERIODIC) : 1;
+        g.bclo[a] = a < dim ? bc[2 * a] : STK_PERIODIC;
+        g.bchi[a] = a < dim ? bc[2 * a + 1] : STK_PERIODIC;
+    }
+    int off = 0;
+    for (int a = 0; a < 3; ++a) {
+        for (int c = 0; c < 3; ++c) g.fe[a][c] = g.n[c] + ((c == a && !g.per[a]) ? 1 : 0);
+        g.fsize[a] = a < dim ? g.fe[a][0] * g.fe[a][1] * g.fe[a][2] : 0;
+        g.foff[a] = off;
+        off += g.fsize[a];
+    }
+    g.nvel = off;
+    g.ncell = g.n[0] * g.n[1] * g.n[2];
+    const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
+    for (int p = 0; p < 3; ++p) {
+        for (int c = 0; c < 3; ++c)
+            g.ee[p][c] = g.n[c] + (((c == pa[p] || c == pb[p]) && !g.per[c]) ? 1 : 0);
+        g.esize[p] = pb[p] < dim ? g.ee[p][0] * g.ee[p][1] * g.ee[p][2] : 0;
+    }
+    g.h = hh;
+    g.ih = 1.0 / hh;
+    g.ih2 = 1.0 / (hh * hh);
+    return g;
+}
+
+// -------------------------------------------------------------------- profiling
+struct Scope {
+    stk_handle* h;
+    ProfRec rec{};
+    cudaStream_t s;
+    Scope(stk_handle* h_, int cat, double bytes, cudaStream_t s_) : h(h_), s(s_) {
+        if (!h->prof) return;
+        rec.cat = cat;
+        rec.bytes = bytes;
+        rec.a = next_event();
+        rec.b = next_event();
+        cudaEventRecord(rec.a, s);
+    }
+    ~Scope() {
+        if (!h->prof) return;
+        cudaEventRecord(rec.b, s);
+        h->recs.push_back(rec);
+    }
+    cudaEvent_t next_event() {
+        if (h->evnext >= h->evpool.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            h->evpool.push_back(e);
+        }
+        return h->evpool[h->evnext++];
+    }
+};
+
+void prof_flush(stk_handle* h) {
+    if (h->recs.empty()) return;
+    cudaDeviceSynchronize();
+    for (auto& r : h->recs) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        h->plaunch[r.cat] += 1;
+        h->pms[r.cat] += ms;
+        h->pbytes[r.cat] += r.bytes;
+    }
+    h->recs.clear();
+    h->evnext = 0;
+}
+
+// Algorithmic bytes of one launch: every input word read once, every output
+// word written once.
+double esum(const Geom& g) { return double(g.esize[0]) + g.esize[1] + g.esize[2]; }
+template <typename T>
+double bytes_vel_colour(const Geom& g, int a) {
+    double e = 0;
+    for (int b = 0; b < g.dim; ++b)
+        if (b != a) e += g.esize[a + b - 1];
+    // half of comp a: rhs, alpha, invd read and phi written; phi of all
+    // components, mu_c and the edge viscosities of comp a read
+    return sizeof(T) * (2.0 * g.fsize[a] + g.nvel + g.ncell + e);
+}
+template <typename T>
+double bytes_vel_residual(const Geom& g) {   // phi, rhs, alpha read; res written
+    return sizeof(T) * (4.0 * g.nvel + g.ncell + esum(g));
+}
+template <typename T>
+double bytes_cell_colour(const Geom& g) {    // half: rhs, invd, write; phi, beta all
+    return sizeof(T) * (1.5 * g.ncell + g.ncell + g.nvel);
+}
+double bytes_matvec(const Geom& g, int in_size) {
+    return in_size * double(g.nvel + g.ncell) + 8.0 * (2.0 * g.nvel + 2.0 * g.ncell + esum(g));
+}
+
+// --------------------------------------------------------------------- V-cycles
+template <typename T> Coef<T> coef_of(const Level& L);
+template <> Coef<double> coef_of<double>(const Level& L) { return L.cd; }
+template <> Coef<float> coef_of<float>(const Level& L) { return L.cf; }
+template <typename T> Work<T> work_of(const Level& L);
+template <> Work<double> work_of<double>(const Level& L) { return L.wd; }
+template <> Work<float> work_of<float>(const Level& L) { return L.wf; }
+template <typename T> PBuf<T>& pbuf_of(stk_handle* h);
+template <> PBuf<double>& pbuf_of<double>(stk_handle* h) { return h->pd; }
+template <> PBuf<float>& pbuf_of<float>(stk_handle* h) { return h->pf; }
+
+struct MGParams {
+    int nu = 2;
+    int ncoarse = 8;
+};
+
+template <typename T>
+void vel_sweeps(stk_handle* h, const Level& L, int nsweep, T* phi, const T* rhs, cudaStream_t s) {
+    Coef<T> C = coef_of<T>(L);
+    for (int it = 0; it < nsweep; ++it)
+        for (int a = 0; a < L.g.dim; ++a)
+            for (int par = 0; par < 2; ++par) {
+                Scope sc(h, PF_VSMOOTH, bytes_vel_colour<T>(L.g, a), s);
+                launch_vel_gs_colour<T>(L.g, C, a, par, phi, rhs, s);
+            }
+}
+
+template <typename T>
+void cell_sweeps(stk_handle* h, const Level& L, int nsweep, T* phi, const T* rhs, cudaStream_t s) {
+    Coef<T> C = coef_of<T>(L);
+    for (int it = 0; it < nsweep; ++it)
+        for (int par = 0; par < 2; ++par) {
+            Scope sc(h, PF_CSMOOTH, bytes_cell_colour<T>(L.g), s);
+            launch_cell_gs_colour<T>(L.g, C, par, phi, rhs, s);
+        }
+}
+
+// One velocity V-cycle for A phi = rhs with phi = 0 initially (App. C).
+// Level l reads rhs (level 0: caller's vector) and writes phi.
+template <typename T>
+void vcycle_vel(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp, cudaStream_t s) {
+    const Level& L = h->lev[l];
+    Work<T> W = work_of<T>(L);
+    cudaMemsetAsync(phi, 0, sizeof(T) * L.g.nvel, s);
+    if (l + 1 == (int)h->lev.size()) {
+        vel_sweeps<T>(h, L, mp.ncoarse, phi, rhs, s);
+        return;
+    }
+    const Level& Lc = h->lev[l + 1];
+    Work<T> Wc = work_of<T>(Lc);
+    vel_sweeps<T>(h, L, mp.nu, phi, rhs, s);
+    {
+        Scope sc(h, PF_VRES, bytes_vel_residual<T>(L.g), s);
+        launch_vel_residual<T>(L.g, coef_of<T>(L), phi, rhs, W.res_u, s);
+    }
+    {
+        Scope sc(h, PF_VRESTR, sizeof(T) * (L.g.nvel + Lc.g.nvel), s);
+        launch_vel_restrict<T>(L.g, W.res_u, Lc.g, Wc.rhs_u, s);
+    }
+    vcycle_vel<T>(h, l + 1, Wc.rhs_u, Wc.phi_u, mp, s);
+    {
+        Scope sc(h, PF_VPROL, sizeof(T) * (2.0 * L.g.nvel + Lc.g.nvel), s);
+        launch_vel_prolong_add<T>(Lc.g, Wc.phi_u, L.g, phi, s);
+    }
+    vel_sweeps<T>(h, L, mp.nu, phi, rhs, s);
+}
+
+// One pressure V-cycle for L_rho phi = rhs with phi = 0 initially (App. C).
+template <typename T>
+void vcycle_cell(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp, cudaStream_t s) {
+    const Level& L = h->lev[l];
+    Work<T> W = work_of<T>(L);
+    cudaMemsetAsync(phi, 0, sizeof(T) * L.g.ncell, s);
+    if (l + 1 == (int)h->lev.size()) {
+        cell_sweeps<T>(h, L, mp.ncoarse, phi, rhs, s);
+        return;
+    }
+    const Level& Lc = h->lev[l + 1];
+    Work<T> Wc = work_of<T>(Lc);
+    cell_sweeps<T>(h, L, mp.nu, phi, rhs, s);
+    {
+        Scope sc(h, PF_CRES, sizeof(T) * (3.0 * L.g.ncell + L.g.nvel), s);
+        launch_cell_residual<T>(L.g, coef_of<T>(L), phi, rhs, W.res_p, s);
+    }
+    {
+        Scope sc(h, PF_CRESTR, sizeof(T) * (L.g.ncell + Lc.g.ncell), s);
+        launch_cell_restrict<T>(L.g, W.res_p, Lc.g, Wc.rhs_p, s);
+    }
+    vcycle_cell<T>(h, l + 1, Wc.rhs_p, Wc.phi_p, mp, s);
+    {
+        Scope sc(h, PF_CPROL, sizeof(T) * (2.0 * L.g.ncell + Lc.g.ncell), s);
+        launch_cell_prolong_add<T>(Lc.g, Wc.phi_p, L.g, phi, s);
+    }
+    cell_sweeps<T>(h, L, mp.nu, phi, rhs, s);
+}
+
+// phi = L~_rho^{-1} (r - mean r): the Poisson right-hand side is projected
+// onto mean-zero vectors (the constant null space of L_rho, Sec. 3.2).
+template <typename T>
+void poisson_solve(stk_handle* h, const T* r, T* phi, const MGParams& mp, cudaStream_t s) {
+    const Level& L = h->lev[0];
+    Work<T> W = work_of<T>(L);
+    {
+        Scope sc(h, PF_MEAN, 2.0 * sizeof(T) * L.g.ncell, s);
+        launch_sum<T>(L.g.ncell, r, h->red, h->dsc + DS_SUM, s);
+        launch_copy_sub_mean<T>(L.g.ncell, r, W.rhs_p, h->dsc + DS_SUM, s);
+    }
+    vcycle_cell<T>(h, 0, W.rhs_p, phi, mp, s);
+}
+
+template <typename T>
+void remove_mean(stk_handle* h, T* x, cudaStream_t s) {
+    const Level& L = h->lev[0];
+    Scope sc(h, PF_MEAN, 3.0 * sizeof(T) * L.g.ncell, s);
+    launch_sum<T>(L.g.ncell, x, h->red, h->dsc + DS_SUM + 1, s);
+    launch_sub_mean<T>(L.g.ncell, x, h->dsc + DS_SUM + 1, s);
+}
+
+// x = P^{-1} b, Sec. 2.1-2.4; b, x packed Stokes vectors of precision T.
+template <typename T>
+void apply_precond(stk_handle* h, int which, const T* b, T* x, const MGParams& mp, cudaStream_t s) {
+    const Level& L = h->lev[0];
+    const Geom& g = L.g;
+    Coef<T> C = coef_of<T>(L);
+    Work<T> W = work_of<T>(L);
+    PBuf<T>& B = pbuf_of<T>(h);
+    const T* bu = b;
+    const T* bp = b + g.nvel;
+    T* xu = x;
+    T* xp = x + g.nvel;
+    const double th = h->theta;
+    const bool pois = th != 0.0;
+    const double alg_cell = sizeof(T) * 3.0 * g.ncell + sizeof(T) * g.nvel;
+    switch (which) {
+    case STK_P1: {
+        vcycle_vel<T>(h, 0, bu, B.xs, mp, s);
+        { Scope sc(h, PF_ALG, alg_cell, s); launch_div_plus<T>(g, B.xs, bp, B.bc, s); }
+        poisson_solve<T>(h, B.bc, W.phi_p, mp, s);
+        {
+            Scope sc(h, PF_ALG, sizeof(T) * (3.0 * g.nvel + g.ncell), s);
+            launch_sub_grad<T>(g, C.beta, B.xs, W.phi_p, xu, s);
+        }
+        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, th, W.phi_p, C.mu_c, B.bc, xp, s); }
+        break;
+    }
+    case STK_P2: {
+        vcycle_vel<T>(h, 0, bu, xu, mp, s);
+        { Scope sc(h, PF_ALG, alg_cell, s); launch_div_plus<T>(g, xu, bp, B.bc, s); }
+        if (pois) poisson_solve<T>(h, B.bc, W.phi_p, mp, s);
+        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, th, pois ? W.phi_p : nullptr, C.mu_c, B.bc, xp, s); }
+        break;
+    }
+    case STK_P3: {
+        if (pois) poisson_solve<T>(h, bp, W.phi_p, mp, s);
+        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, th, pois ? W.phi_p : nullptr, C.mu_c, bp, xp, s); }
+        {
+            Scope sc(h, PF_ALG, sizeof(T) * (2.0 * g.nvel + g.ncell), s);
+            launch_sub_grad<T>(g, (const T*)nullptr, bu, xp, B.tmpu, s);
+        }
+        vcycle_vel<T>(h, 0, B.tmpu, xu, mp, s);
+        break;
+    }
+    case STK_P4: {
+        vcycle_vel<T>(h, 0, bu, xu, mp, s);
+        if (pois) poisson_solve<T>(h, bp, W.phi_p, mp, s);
+        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, th, pois ? W.phi_p : nullptr, C.mu_c, bp, xp, s); }
+        break;
+    }
+    default: {  // STK_P5
+        vcycle_vel<T>(h, 0, bu, B.xs, mp, s);
+        { Scope sc(h, PF_ALG, alg_cell, s); launch_div_plus<T>(g, B.xs, bp, B.bc, s); }
+        if (pois) poisson_solve<T>(h, B.bc, W.phi_p, mp, s);
+        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, th, pois ? W.phi_p : nullptr, C.mu_c, B.bc, xp, s); }
+        {
+            Scope sc(h, PF_ALG, bytes_vel_residual<T>(g), s);
+            launch_vel_correction_rhs<T>(g, C, bu, xp, B.xs, B.tmpu, s);
+        }
+        vcycle_vel<T>(h, 0, B.tmpu, xu, mp, s);
+        { Scope sc(h, PF_ALG, 3.0 * sizeof(T) * g.nvel, s); launch_axpy<T>(g.nvel, T(1), B.xs, xu, s); }
+        break;
+    }
+    }
+    remove_mean<T>(h, xp, s);
+}
+
+double scalar_vcycles(const stk_handle* h, int which) {
+    double d = h->dim;
+    double p = h->theta != 0.0 ? 1.0 : 0.0;
+    if (which == STK_P1) return d + 1.0;
+    if (which == STK_P5) return 2.0 * d + p;
+    return d + p;
+}
+
+int nstokes(const stk_handle* h) { return h->lev[0].g.nvel + h->lev[0].g.ncell; }
+
+int check_ptrs(stk_handle* h, const void* const* u, const void* p) {
+    if (!u || !p) return fail(h, STK_ERR_ARG, "null array pointer");
+    for (int a = 0; a < h->dim; ++a)
+        if (!u[a]) return fail(h, STK_ERR_ARG, "null face array %d", a);
+    return STK_OK;
+}
+
+// gather caller's face/cell arrays into a packed vector and back
+int gather(stk_handle* h, const double* const* u, const double* p, double* packed, cudaStream_t s) {
+    const Geom& g = h->lev[0].g;
+    for (int a = 0; a < g.dim; ++a)
+        CK(cudaMemcpyAsync(packed + g.foff[a], u[a], sizeof(double) * g.fsize[a],
+                           cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(packed + g.nvel, p, sizeof(double) * g.ncell, cudaMemcpyDeviceToDevice, s));
+    return STK_OK;
+}
+
+int scatter(stk_handle* h, const double* packed, double* const* u, double* p, cudaStream_t s) {
+    const Geom& g = h->lev[0].g;
+    for (int a = 0; a < g.dim; ++a)
+        CK(cudaMemcpyAsync(u[a], packed + g.foff[a], sizeof(double) * g.fsize[a],
+                           cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(p, packed + g.nvel, sizeof(double) * g.ncell, cudaMemcpyDeviceToDevice, s));
+    return STK_OK;
+}
+
+int ensure_krylov(stk_handle* h, int m) {
+    if (m <= h->m_alloc) return STK_OK;
+    const int n = nstokes(h);
+    for (int i = (int)h->V.size(); i < m + 1; ++i) {
+        double* v;
+        CK(dalloc(h, &v, n));
+        h->V.push_back(v);
+    }
+    for (int i = (int)h->Z.size(); i < m; ++i) {
+        float* z;
+        CK(dalloc(h, &z, n));
+        h->Z.push_back(z);
+    }
+    h->m_alloc = m;
+    return STK_OK;
+}
+
+// Givens rotation helpers on the host: H is (m+1) x m column-major in hc
+struct Arnoldi {
+    int m;
+    std::vector<double> H, cs, sn, g;
+    explicit Arnoldi(int m_) : m(m_), H((m_ + 1) * m_, 0.0), cs(m_), sn(m_), g(m_ + 1, 0.0) {}
+    double& at(int i, int j) { return H[j * (m + 1) + i]; }
+    // column j holds h[0..j+1]; returns |g[j+1]|
+    double add_column(int j, const double* col) {
+        for (int i = 0; i <= j + 1; ++i) at(i, j) = col[i];
+        for (int i = 0; i < j; ++i) {
+            double t = cs[i] * at(i, j) + sn[i] * at(i + 1, j);
+            at(i + 1, j) = -sn[i] * at(i, j) + cs[i] * at(i + 1, j);
+            at(i, j) = t;
+        }
+        double a = at(j, j), b = at(j + 1, j);
+        double r = std::hypot(a, b);
+        cs[j] = r == 0.0 ? 1.0 : a / r;
+        sn[j] = r == 0.0 ? 0.0 : b / r;
+        at(j, j) = cs[j] * a + sn[j] * b;
+        at(j + 1, j) = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        return std::fabs(g[j + 1]);
+    }
+    void solve(int k, double* y) {
+        for (int i = k - 1; i >= 0; --i) {
+            double s = g[i];
+            for (int c = i + 1; c < k; ++c) s -= at(i, c) * y[c];
+            y[i] = s / at(i, i);
+        }
+    }
+};
+
+// w (= V[j+1], unnormalised) is orthogonalised against V[0..j] by classical
+// Gram-Schmidt with one selective re-orthogonalisation pass; its norm
+// becomes hcol[j+1] and it is normalised.  hcol[0..j] receive the
+// projections.
+int orthogonalise(stk_handle* h, int j, cudaStream_t s, double* hcol) {
+    const int n = nstokes(h);
+    double* w = h->V[j + 1];
+    std::vector<const double*> Vp(h->V.begin(), h->V.begin() + j + 1);
+    double* hd = h->dsc + DS_H;
+    {
+        Scope sc(h, PF_MDOT, 8.0 * n * (j + 2), s);
+        launch_multidot(n, j, Vp.data(), w, h->red, hd, s);
+    }
+    {
+        Scope sc(h, PF_UPD, 8.0 * n * (j + 3), s);
+        launch_update_norm(n, j, Vp.data(), hd, w, h->red, h->dsc + DS_N2, s);
+    }
+    CK(cudaMemcpyAsync(h->hpin, hd, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h->hpin + 40, h->dsc + DS_N2, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int i = 0; i <= j; ++i) hcol[i] = h->hpin[i];
+    double before = h->hpin[j + 1];
+    double after = h->hpin[40];
+    if (!(std::isfinite(after) && std::isfinite(before)))
+        return fail(h, STK_ERR_NONFINITE, "non-finite value in the Arnoldi process");
+    if (after < 0.5 * before) {   // lost more than 1 - 1/sqrt(2) of its norm: re-orthogonalise
+        {
+            Scope sc(h, PF_MDOT, 8.0 * n * (j + 2), s);
+            launch_multidot(n, j, Vp.data(), w, h->red, hd, s);
+        }
+        {
+            Scope sc(h, PF_UPD, 8.0 * n * (j + 3), s);
+            launch_update_norm(n, j, Vp.data(), hd, w, h->red, h->dsc + DS_N2, s);
+        }
+        CK(cudaMemcpyAsync(h->hpin, hd, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(h->hpin + 40, h->dsc + DS_N2, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int i = 0; i <= j; ++i) hcol[i] += h->hpin[i];
+        after = h->hpin[40];
+    }
+    hcol[j + 1] = std::sqrt(after);
+    if (hcol[j + 1] > 0.0) {
+        Scope sc(h, PF_COMB, 16.0 * n, s);
+        launch_scale(n, w, 1.0 / hcol[j + 1], s);
+    }
+    CKL();
+    return STK_OK;
+}
+
+int norm2(stk_handle* h, const double* x, int n, cudaStream_t s, double* out) {
+    {
+        Scope sc(h, PF_MDOT, 8.0 * n, s);
+        launch_multidot(n, -1, nullptr, x, h->red, h->dsc + DS_N2 + 1, s);
+    }
+    CK(cudaMemcpyAsync(h->hpin + 41, h->dsc + DS_N2 + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *out = std::sqrt(h->hpin[41]);
+    return STK_OK;
+}
+
+// Restarted GMRES (Sec. 3.2): left-preconditioned with an FP64 preconditioner
+// (flexible = false) or flexible with an FP32 preconditioner (flexible = true,
+// Sec. 4).  Stopping rule: ||b - M x|| <= rtol ||b||, checked at the start of
+// every cycle; inside a cycle the Arnoldi estimate must fall to rtol ||b||
+// (flexible) or to its initial value times rtol ||b|| / ||b - M x|| (left).
+int gmres(stk_handle* h, const stk_solver_params& prm, stk_solve_info& info, cudaStream_t s) {
+    const Geom& g = h->lev[0].g;
+    const int n = nstokes(h);
+    const int m = prm.restart;
+    const bool flex = prm.precision == STK_MIXED;
+    MGParams mp;
+    mp.nu = prm.nu;
+    mp.ncoarse = prm.ncoarse;
+    int rc = ensure_krylov(h, m);
+    if (rc) return rc;
+    double bnorm;
+    if ((rc = norm2(h, h->bk, n, s, &bnorm))) return rc;
+    info.iterations = info.restarts = 0;
+    info.scalar_vcycles = 0.0;
+    info.converged = 0;
+    if (!std::isfinite(bnorm)) return fail(h, STK_ERR_NONFINITE, "non-finite right-hand side");
+    if (bnorm == 0.0) {
+        CK(cudaMemsetAsync(h->xk, 0, sizeof(double) * n, s));
+        info.converged = 1;
+        info.true_residual = 0.0;
+        return STK_OK;
+    }
+    const double sv = scalar_vcycles(h, prm.precond);
+    std::vector<double> hcol(m + 2), y(m);
+    while (true) {
+        {
+            Scope sc(h, PF_MATVEC, bytes_matvec(g, 8) + 8.0 * n, s);
+            launch_stokes_residual(g, h->lev[0].cd, h->xk, h->bk, h->tmp, s);
+        }
+        CKL();
+        double rnorm;
+        if ((rc = norm2(h, h->tmp, n, s, &rnorm))) return rc;
+        if (!std::isfinite(rnorm)) return fail(h, STK_ERR_NONFINITE, "non-finite residual");
+        info.true_residual = rnorm / bnorm;
+        if (info.true_residual <= prm.rtol) {
+            info.converged = 1;
+            break;
+        }
+        if (info.iterations >= prm.maxit) break;
+        double beta, target;
+        if (flex) {
+            CK(cudaMemcpyAsync(h->V[0], h->tmp, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+            beta = rnorm;
+            target = prm.rtol * bnorm;
+        } else {
+            apply_precond<double>(h, prm.precond, h->tmp, h->V[0], mp, s);
+            info.scalar_vcycles += sv;
+            CKL();
+            if ((rc = norm2(h, h->V[0], n, s, &beta))) return rc;
+            if (!std::isfinite(beta)) return fail(h, STK_ERR_NONFINITE, "non-finite preconditioned residual");
+            target = beta * (prm.rtol * bnorm / rnorm);
+        }
+        if (beta == 0.0) break;
+        {
+            Scope sc(h, PF_COMB, 16.0 * n, s);
+            launch_scale(n, h->V[0], 1.0 / beta, s);
+        }
+        Arnoldi ar(m);
+        ar.g[0] = beta;
+        int k = 0;
+        for (int j = 0; j < m && info.iterations < prm.maxit; ++j) {
+            if (flex) {
+                {
+                    Scope sc(h, PF_CONV, 12.0 * n, s);
+                    launch_convert<double, float>(n, h->V[j], h->pf.in, s);
+                }
+                apply_precond<float>(h, prm.precond, h->pf.in, h->Z[j], mp, s);
+                Scope sc(h, PF_MATVEC, bytes_matvec(g, 4), s);
+                launch_stokes_matvec<float>(g, h->lev[0].cd, h->Z[j], h->V[j + 1], s);
+            } else {
+                {
+                    Scope sc(h, PF_MATVEC, bytes_matvec(g, 8), s);
+                    launch_stokes_matvec<double>(g, h->lev[0].cd, h->V[j], h->tmp, s);
+                }
+                apply_precond<double>(h, prm.precond, h->tmp, h->V[j + 1], mp, s);
+            }
+            info.scalar_vcycles += sv;
+            CKL();
+            if ((rc = orthogonalise(h, j, s, hcol.data()))) return rc;
+            ++info.iterations;
+            k = j + 1;
+            double est = ar.add_column(j, hcol.data());
+            info.est_residual = est / bnorm;
+            if (est <= target || hcol[j + 1] == 0.0) break;
+        }
+        ++info.restarts;
+        ar.solve(k, y.data());
+        for (int i = 0; i < k; ++i)
+            if (!std::isfinite(y[i])) return fail(h, STK_ERR_NONFINITE, "non-finite GMRES update");
+        std::memcpy(h->hpin, y.data(), sizeof(double) * k);
+        CK(cudaMemcpyAsync(h->dsc + DS_Y, h->hpin, sizeof(double) * k, cudaMemcpyHostToDevice, s));
+        {
+            Scope sc(h, PF_COMB, (flex ? 4.0 : 8.0) * n * k + 16.0 * n, s);
+            if (flex) {
+                std::vector<const float*> Zp(h->Z.begin(), h->Z.begin() + k);
+                launch_combine<float>(n, k, Zp.data(), h->dsc + DS_Y, h->xk, s);
+            } else {
+                std::vector<const double*> Vp(h->V.begin(), h->V.begin() + k);
+                launch_combine<double>(n, k, Vp.data(), h->dsc + DS_Y, h->xk, s);
+            }
+        }
+        CKL();
+        CK(cudaStreamSynchronize(s));   // host staging buffer reused next cycle
+    }
+    return info.converged ? STK_OK : STK_ERR_NOT_CONVERGED;
+}
+
+bool is_pow2(int v) { return v >= 2 && (v & (v - 1)) == 0; }
+
+}  // namespace
+
+// ===================================================================== C ABI
+extern "C" {
+
+void stk_default_params(stk_solver_params* p) {
+    if (!p) return;
+    p->precond = STK_P1;
+    p->restart = 10;
+    p->rtol = 1e-10;
+    p->maxit = 1000;
+    p->precision = STK_FP64;
+    p->nu = 2;
+    p->ncoarse = 8;
+}
+
+const char* stk_last_error(const stk_handle* h) {
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+long long stk_face_length(const stk_handle* h, int a) {
+    if (!h || a < 0 || a >= h->dim) return -1;
+    return h->lev[0].g.fsize[a];
+}
+
+long long stk_cell_length(const stk_handle* h) { return h ? h->lev[0].g.ncell : -1; }
+
+int stk_create(int dim, const int* n, double hh, const int* bc, stk_handle** out) {
+    stk_handle* h = nullptr;
+    if (!out) return fail(nullptr, STK_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (dim != 2 && dim != 3) return fail(nullptr, STK_ERR_ARG, "dim must be 2 or 3");
+    if (!n || !bc) return fail(nullptr, STK_ERR_ARG, "null n or bc");
+    if (!(hh > 0.0) || !std::isfinite(hh)) return fail(nullptr, STK_ERR_ARG, "h must be > 0");
+    int nn[3] = {1, 1, 1}, bb[6] = {0, 0, 0, 0, 0, 0};
+    for (int a = 0; a < dim; ++a) {
+        nn[a] = n[a];
+        if (!is_pow2(n[a])) return fail(nullptr, STK_ERR_SIZE, "n[%d] = %d is not a power of two >= 2", a, n[a]);
+        bb[2 * a] = bc[2 * a];
+        bb[2 * a + 1] = bc[2 * a + 1];
+        for (int sd = 0; sd < 2; ++sd)
+            if (bb[2 * a + sd] < 0 || bb[2 * a + sd] > 2)
+                return fail(nullptr, STK_ERR_ARG, "bad boundary code %d", bb[2 * a + sd]);
+        if ((bb[2 * a] == STK_PERIODIC) != (bb[2 * a + 1] == STK_PERIODIC))
+            return fail(nullptr, STK_ERR_ARG, "axis %d: periodic must be set on both sides", a);
+    }
+    long long total = 1;
+    for (int a = 0; a < dim; ++a) total *= nn[a];
+    if (total * (dim + 1) > (1LL << 30)) return fail(nullptr, STK_ERR_SIZE, "grid too large");
+    h = new stk_handle();
+    cudaGetDevice(&h->device);
+    h->dim = dim;
+    int cur[3] = {nn[0], nn[1], nn[2]};
+    double hl = hh;
+    while (true) {
+        Level L{};
+        L.g = make_geom(dim, cur, hl, bb);
+        h->lev.push_back(L);
+        int mn = cur[0];
+        for (int a = 1; a < dim; ++a) mn = cur[a] < mn ? cur[a] : mn;
+        if (mn <= 2) break;
+        for (int a = 0; a < dim; ++a) cur[a] /= 2;
+        hl *= 2.0;
+    }
+#define CKC(call)                                                                   \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess) {                                                    \
+            fail(nullptr, STK_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));   \
+            stk_destroy(h);                                                         \
+            return STK_ERR_CUDA;                                                    \
+        }                                                                           \
+    } while (0)
+    for (auto& L : h->lev) {
+        const Geom& g = L.g;
+        CKC(dalloc(h, &L.cd.alpha, g.nvel));
+        CKC(dalloc(h, &L.cd.beta, g.nvel));
+        CKC(dalloc(h, &L.cd.mu_c, g.ncell));
+        CKC(dalloc(h, &L.cd.invd_u, g.nvel));
+        CKC(dalloc(h, &L.cd.invd_p, g.ncell));
+        CKC(dalloc(h, &L.cf.alpha, g.nvel));
+        CKC(dalloc(h, &L.cf.beta, g.nvel));
+        CKC(dalloc(h, &L.cf.mu_c, g.ncell));
+        CKC(dalloc(h, &L.cf.invd_u, g.nvel));
+        CKC(dalloc(h, &L.cf.invd_p, g.ncell));
+        for (int p = 0; p < 3; ++p) {
+            L.cd.mu_e[p] = nullptr;
+            L.cf.mu_e[p] = nullptr;
+            if (g.esize[p] > 0) {
+                CKC(dalloc(h, &L.cd.mu_e[p], g.esize[p]));
+                CKC(dalloc(h, &L.cf.mu_e[p], g.esize[p]));
+            }
+        }
+        CKC(dalloc(h, &L.wd.phi_u, g.nvel));
+        CKC(dalloc(h, &L.wd.rhs_u, g.nvel));
+        CKC(dalloc(h, &L.wd.res_u, g.nvel));
+        CKC(dalloc(h, &L.wd.phi_p, g.ncell));
+        CKC(dalloc(h, &L.wd.rhs_p, g.ncell));
+        CKC(dalloc(h, &L.wd.res_p, g.ncell));
+        CKC(dalloc(h, &L.wf.phi_u, g.nvel));
+        CKC(dalloc(h, &L.wf.rhs_u, g.nvel));
+        CKC(dalloc(h, &L.wf.res_u, g.nvel));
+        CKC(dalloc(h, &L.wf.phi_p, g.ncell));
+        CKC(dalloc(h, &L.wf.rhs_p, g.ncell));
+        CKC(dalloc(h, &L.wf.res_p, g.ncell));
+    }
+    const Geom& g0 = h->lev[0].g;
+    const int ns = g0.nvel + g0.ncell;
+    CKC(dalloc(h, &h->pd.in, ns));
+    CKC(dalloc(h, &h->pd.bc, g0.ncell));
+    CKC(dalloc(h, &h->pd.tmpu, g0.nvel));
+    CKC(dalloc(h, &h->pd.xs, g0.nvel));
+    CKC(dalloc(h, &h->pf.in, ns));
+    CKC(dalloc(h, &h->pf.bc, g0.ncell));
+    CKC(dalloc(h, &h->pf.tmpu, g0.nvel));
+    CKC(dalloc(h, &h->pf.xs, g0.nvel));
+    CKC(dalloc(h, &h->bk, ns));
+    CKC(dalloc(h, &h->xk, ns));
+    CKC(dalloc(h, &h->tmp, ns));
+    CKC(dalloc(h, &h->red, (size_t)RED_BLOCKS * 36));
+    CKC(dalloc(h, &h->dsc, NDSC));
+    {
+        void* p = nullptr;
+        CKC(cudaMallocHost(&p, sizeof(double) * 128));
+        h->hpin = static_cast<double*>(p);
+    }
+#undef CKC
+    *out = h;
+    return STK_OK;
+}
+
+int stk_destroy(stk_handle* h) {
+    if (!h) return STK_OK;
+    cudaDeviceSynchronize();
+    for (void* p : h->allocs) cudaFree(p);
+    if (h->hpin) cudaFreeHost(h->hpin);
+    for (auto e : h->evpool) cudaEventDestroy(e);
+    delete h;
+    return STK_OK;
+}
+
+int stk_set_coefficients(stk_handle* h, const double* rho, const double* mu, double dt,
+                         void* stream) {
+    if (!h) return STK_ERR_ARG;
+    if (!rho || !mu) return fail(h, STK_ERR_ARG, "null rho or mu");
+    if (!(dt > 0.0)) return fail(h, STK_ERR_ARG, "dt must be > 0 (+INFINITY for steady flow)");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(cudaSetDevice(h->device));
+    const Geom& g0 = h->lev[0].g;
+    launch_check_fields(g0.ncell, rho, mu, h->red, h->dsc + DS_N2, s);
+    CKL();
+    CK(cudaMemcpyAsync(h->hpin, h->dsc + DS_N2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (h->hpin[0] != 0.0) return fail(h, STK_ERR_NONFINITE, "rho or mu has %g non-finite entries", h->hpin[0]);
+    if (h->hpin[1] != 0.0) return fail(h, STK_ERR_ARG, "rho <= 0 or mu < 0 at %g cells", h->hpin[1]);
+    bool all_periodic = true;
+    for (int a = 0; a < h->dim; ++a) all_periodic = all_periodic && g0.per[a];
+    h->theta = std::isinf(dt) ? 0.0 : 1.0 / dt;
+    if (h->theta == 0.0 && all_periodic)
+        return fail(h, STK_ERR_ARG, "steady flow on an all-periodic grid (constant-velocity null space) is not supported");
+    launch_fine_coefficients(g0, rho, mu, h->theta, h->lev[0].cd, s);
+    for (size_t l = 1; l < h->lev.size(); ++l)
+        launch_coarsen_coefficients(h->lev[l - 1].g, h->lev[l - 1].cd, h->lev[l].g, h->lev[l].cd, s);
+    for (auto& L : h->lev) {
+        launch_inverse_diagonals(L.g, L.cd, s);
+        launch_convert_coefficients(L.g, L.cd, L.cf, s);
+    }
+    CKL();
+    CK(cudaStreamSynchronize(s));
+    h->coef_set = true;
+    return STK_OK;
+}
+
+int stk_apply_operator(stk_handle* h, const double* const* x_u, const double* x_p,
+                       double* const* y_u, double* y_p, void* stream) {
+    if (!h) return STK_ERR_ARG;
+    if (!h->coef_set) return fail(h, STK_ERR_STATE, "coefficients not set");
+    int rc;
+    if ((rc = check_ptrs(h, (const void* const*)x_u, x_p))) return rc;
+    if ((rc = check_ptrs(h, (const void* const*)y_u, y_p))) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(cudaSetDevice(h->device));
+    if ((rc = gather(h, x_u, x_p, h->xk, s))) return rc;
+    {
+        Scope sc(h, PF_MATVEC, bytes_matvec(h->lev[0].g, 8), s);
+        launch_stokes_matvec<double>(h->lev[0].g, h->lev[0].cd, h->xk, h->tmp, s);
+    }
+    CKL();
+    return scatter(h, h->tmp, y_u, y_p, s);
+}
+
+int stk_apply_preconditioner(stk_handle* h, int which, const double* const* b_u,
+                             const double* b_p, double* const* x_u, double* x_p, void* stream) {
+    if (!h) return STK_ERR_ARG;
+    if (!h->coef_set) return fail(h, STK_ERR_STATE, "coefficients not set");
+    if (which < STK_P1 || which > STK_P5) return fail(h, STK_ERR_ARG, "preconditioner must be 1..5");
+    int rc;
+    if ((rc = check_ptrs(h, (const void* const*)b_u, b_p))) return rc;
+    if ((rc = check_ptrs(h, (const void* const*)x_u, x_p))) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(cudaSetDevice(h->device));
+    if ((rc = gather(h, b_u, b_p, h->bk, s))) return rc;
+    MGParams mp;
+    apply_precond<double>(h, which, h->bk, h->tmp, mp, s);
+    CKL();
+    return scatter(h, h->tmp, x_u, x_p, s);
+}
+
+int stk_velocity_vcycle(stk_handle* h, const double* const* r_u, double* const* x_u,
+                        void* stream) {
+    if (!h) return STK_ERR_ARG;
+    if (!h->coef_set) return fail(h, STK_ERR_STATE, "coefficients not set");
+    if (!r_u || !x_u) return fail(h, STK_ERR_ARG, "null pointer");
+    for (int a = 0; a < h->dim; ++a)
+        if (!r_u[a] || !x_u[a]) return fail(h, STK_ERR_ARG, "null face array");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(cudaSetDevice(h->device));
+    const Geom& g = h->lev[0].g;
+    for (int a = 0; a < g.dim; ++a)
+        CK(cudaMemcpyAsync(h->bk + g.foff[a], r_u[a], sizeof(double) * g.fsize[a], cudaMemcpyDeviceToDevice, s));
+    MGParams mp;
+    vcycle_vel<double>(h, 0, h->bk, h->tmp, mp, s);
+    CKL();
+    for (int a = 0; a < g.dim; ++a)
+        CK(cudaMemcpyAsync(x_u[a], h->tmp + g.foff[a], sizeof(double) * g.fsize[a], cudaMemcpyDeviceToDevice, s));
+    return STK_OK;
+}
+
+int stk_pressure_vcycle(stk_handle* h, const double* r_p, double* x_p, void* stream) {
+    if (!h) return STK_ERR_ARG;
+    if (!h->coef_set) return fail(h, STK_ERR_STATE, "coefficients not set");
+    if (!r_p || !x_p) return fail(h, STK_ERR_ARG, "null pointer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(cudaSetDevice(h->device));
+    MGParams mp;
+    vcycle_cell<double>(h, 0, r_p, x_p, mp, s);
+    CKL();
+    return STK_OK;
+}
+
+int stk_solve(stk_handle* h, const stk_solver_params* params, const double* const* b_u,
+              const double* b_p, double* const* x_u, double* x_p, stk_solve_info* info_out,
+              void* stream) {
+    if (!h) return STK_ERR_ARG;
+    if (!h->coef_set) return fail(h, STK_ERR_STATE, "coefficients not set");
+    stk_solver_params prm;
+    stk_default_params(&prm);
+    if (params) prm = *params;
+    if (prm.precond < STK_P1 || prm.precond > STK_P5) return fail(h, STK_ERR_ARG, "preconditioner must be 1..5");
+    if (prm.restart < 1 || prm.restart > 32) return fail(h, STK_ERR_ARG, "restart must be 1..32");
+    if (!(prm.rtol > 0.0)) return fail(h, STK_ERR_ARG, "rtol must be > 0");
+    if (prm.maxit < 1) return fail(h, STK_ERR_ARG, "maxit must be >= 1");
+    if (prm.precision != STK_FP64 && prm.precision != STK_MIXED) return fail(h, STK_ERR_ARG, "bad precision");
+    if (prm.nu < 0 || prm.ncoarse < 1) return fail(h, STK_ERR_ARG, "bad sweep counts");
+    int rc;
+    if ((rc = check_ptrs(h, (const void* const*)b_u, b_p))) return rc;
+    if ((rc = check_ptrs(h, (const void* const*)x_u, x_p))) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(cudaSetDevice(h->device));
+    stk_solve_info info{};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, s));
+    if ((rc = gather(h, b_u, b_p, h->bk, s)) == STK_OK && (rc = gather(h, x_u, x_p, h->xk, s)) == STK_OK) {
+        rc = gmres(h, prm, info, s);
+        if (rc == STK_OK || rc == STK_ERR_NOT_CONVERGED) {
+            int rc2 = scatter(h, h->xk, x_u, x_p, s);
+            if (rc2) rc = rc2;
+        }
+    }
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    info.solve_ms = ms;
+    info.status = rc;
+    if (rc == STK_ERR_NOT_CONVERGED && h->err.empty())
+        h->err = "maximum number of iterations reached";
+    if (rc == STK_ERR_NOT_CONVERGED) fail(h, rc, "not converged after %d iterations (residual %.3e)", info.iterations, info.true_residual);
+    if (info_out) *info_out = info;
+    return rc;
+}
+
+int stk_profile(stk_handle* h, int enable) {
+    if (!h) return STK_ERR_ARG;
+    prof_flush(h);
+    if (enable) {
+        for (int k = 0; k < STK_NPROF; ++k) {
+            h->plaunch[k] = 0;
+            h->pms[k] = 0.0;
+            h->pbytes[k] = 0.0;
+        }
+    }
+    h->prof = enable != 0;
+    return STK_OK;
+}
+
+int stk_profile_read(stk_handle* h, int k, const char** name, long long* launches, double* ms,
+                     double* bytes) {
+    if (!h || k < 0 || k >= STK_NPROF) return -1;
+    prof_flush(h);
+    if (name) *name = kProfNames[k];
+    if (launches) *launches = h->plaunch[k];
+    if (ms) *ms = h->pms[k];
+    if (bytes) *bytes = h->pbytes[k];
+    return STK_OK;
+}
+
+}  // extern "C"

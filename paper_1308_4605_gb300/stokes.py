@@ -1,0 +1,287 @@
+"""Python binding of libstokes_gb300 (the C ABI of include/stokes.h).
+
+Argument marshalling only: every function forwards device pointers of torch
+CUDA tensors (float64, contiguous) and the current torch CUDA stream to the
+library of the same name.  There is no CPU fallback: importing this module
+raises if the shared library has not been built, and every call raises
+``StokesError`` on a non-zero return code (except ``stk_solve`` returning
+``STK_ERR_NOT_CONVERGED``, which is reported through the info record).
+
+Layouts: a cell array has shape (nz, ny, nx) (nz = 1 in 2D); the face array
+of velocity component a has the same shape with n_a + 1 entries along axis a
+when that axis has walls (wall faces hold zeros).  ``face_shape`` gives them.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libstokes_gb300.so")
+
+STK_PERIODIC, STK_NOSLIP, STK_FREESLIP = 0, 1, 2
+STK_OK = 0
+STK_ERR_ARG, STK_ERR_SIZE, STK_ERR_CUDA, STK_ERR_NOT_CONVERGED = -1, -2, -3, -4
+STK_ERR_NONFINITE, STK_ERR_TIMEOUT, STK_ERR_STATE = -5, -6, -7
+STK_P1, STK_P2, STK_P3, STK_P4, STK_P5 = 1, 2, 3, 4, 5
+STK_FP64, STK_MIXED = 0, 1
+STK_NPROF = 16
+
+
+class StokesError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"stokes error {code}: {msg}")
+        self.code = code
+
+
+class stk_solver_params(ctypes.Structure):
+    _fields_ = [("precond", ctypes.c_int), ("restart", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("maxit", ctypes.c_int), ("precision", ctypes.c_int), ("nu", ctypes.c_int),
+                ("ncoarse", ctypes.c_int)]
+
+
+class stk_solve_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("converged", ctypes.c_int), ("status", ctypes.c_int),
+                ("true_residual", ctypes.c_double), ("est_residual", ctypes.c_double),
+                ("scalar_vcycles", ctypes.c_double), ("solve_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1308_4605_gb300.build`"
+                          " (there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    D = ctypes.c_double
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "stk_default_params": (None, [ctypes.POINTER(stk_solver_params)]),
+        "stk_create": (I, [I, ctypes.POINTER(I), D, ctypes.POINTER(I), ctypes.POINTER(P)]),
+        "stk_destroy": (I, [P]),
+        "stk_last_error": (ctypes.c_char_p, [P]),
+        "stk_face_length": (ctypes.c_longlong, [P, I]),
+        "stk_cell_length": (ctypes.c_longlong, [P]),
+        "stk_set_coefficients": (I, [P, P, P, D, P]),
+        "stk_apply_operator": (I, [P, PP, P, PP, P, P]),
+        "stk_apply_preconditioner": (I, [P, I, PP, P, PP, P, P]),
+        "stk_velocity_vcycle": (I, [P, PP, PP, P]),
+        "stk_pressure_vcycle": (I, [P, P, P, P]),
+        "stk_solve": (I, [P, ctypes.POINTER(stk_solver_params), PP, P, PP, P,
+                          ctypes.POINTER(stk_solve_info), P]),
+        "stk_profile": (I, [P, I]),
+        "stk_profile_read": (I, [P, I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong),
+                                 ctypes.POINTER(D), ctypes.POINTER(D)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+EXPORTED = ["stk_default_params", "stk_create", "stk_destroy", "stk_last_error", "stk_face_length",
+            "stk_cell_length", "stk_set_coefficients", "stk_apply_operator",
+            "stk_apply_preconditioner", "stk_velocity_vcycle", "stk_pressure_vcycle", "stk_solve",
+            "stk_profile", "stk_profile_read"]
+
+
+def library():
+    return _lib
+
+
+def _check(h, rc):
+    if rc != STK_OK:
+        msg = _lib.stk_last_error(h)
+        raise StokesError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t, numel=None, dtype=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if t.dtype != (dtype or torch.float64):
+        raise TypeError(f"expected {dtype or torch.float64}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"expected {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _ptrs(ts, lengths):
+    arr = (ctypes.c_void_p * 3)()
+    for a, (t, n) in enumerate(zip(ts, lengths)):
+        arr[a] = _ptr(t, n).value
+    return arr
+
+
+def face_shape(n, bc, a):
+    ext = list(n) + [1] * (3 - len(n))
+    if bc[2 * a] != STK_PERIODIC:
+        ext[a] += 1
+    return (ext[2], ext[1], ext[0])
+
+
+# ------------------------------------------------------------- C ABI mirrors
+def stk_default_params():
+    p = stk_solver_params()
+    _lib.stk_default_params(ctypes.byref(p))
+    return p
+
+
+def stk_create(dim, n, h, bc):
+    nn = (ctypes.c_int * 3)(*(list(n) + [1] * (3 - len(n))))
+    bb = (ctypes.c_int * 6)(*(list(bc) + [0] * (6 - len(bc))))
+    out = ctypes.c_void_p()
+    _check(None, _lib.stk_create(int(dim), nn, float(h), bb, ctypes.byref(out)))
+    return out
+
+
+def stk_destroy(h):
+    return _check(h, _lib.stk_destroy(h))
+
+
+def stk_last_error(h):
+    m = _lib.stk_last_error(h)
+    return m.decode() if m else ""
+
+
+def stk_face_length(h, a):
+    return int(_lib.stk_face_length(h, a))
+
+
+def stk_cell_length(h):
+    return int(_lib.stk_cell_length(h))
+
+
+def _lengths(h, dim):
+    return [stk_face_length(h, a) for a in range(dim)], stk_cell_length(h)
+
+
+def stk_set_coefficients(h, rho, mu, dt, stream=None):
+    nc = stk_cell_length(h)
+    return _check(h, _lib.stk_set_coefficients(h, _ptr(rho, nc), _ptr(mu, nc), float(dt),
+                                               _stream(stream)))
+
+
+def stk_apply_operator(h, x_u, x_p, y_u, y_p, stream=None):
+    fl, nc = _lengths(h, len(x_u))
+    return _check(h, _lib.stk_apply_operator(h, _ptrs(x_u, fl), _ptr(x_p, nc), _ptrs(y_u, fl),
+                                             _ptr(y_p, nc), _stream(stream)))
+
+
+def stk_apply_preconditioner(h, which, b_u, b_p, x_u, x_p, stream=None):
+    fl, nc = _lengths(h, len(b_u))
+    return _check(h, _lib.stk_apply_preconditioner(h, int(which), _ptrs(b_u, fl), _ptr(b_p, nc),
+                                                   _ptrs(x_u, fl), _ptr(x_p, nc), _stream(stream)))
+
+
+def stk_velocity_vcycle(h, r_u, x_u, stream=None):
+    fl, _ = _lengths(h, len(r_u))
+    return _check(h, _lib.stk_velocity_vcycle(h, _ptrs(r_u, fl), _ptrs(x_u, fl), _stream(stream)))
+
+
+def stk_pressure_vcycle(h, r_p, x_p, stream=None):
+    nc = stk_cell_length(h)
+    return _check(h, _lib.stk_pressure_vcycle(h, _ptr(r_p, nc), _ptr(x_p, nc), _stream(stream)))
+
+
+def stk_solve(h, params, b_u, b_p, x_u, x_p, stream=None):
+    """Returns the info record as a dict; raises unless converged or
+    STK_ERR_NOT_CONVERGED."""
+    fl, nc = _lengths(h, len(b_u))
+    info = stk_solve_info()
+    rc = _lib.stk_solve(h, ctypes.byref(params), _ptrs(b_u, fl), _ptr(b_p, nc), _ptrs(x_u, fl),
+                        _ptr(x_p, nc), ctypes.byref(info), _stream(stream))
+    if rc not in (STK_OK, STK_ERR_NOT_CONVERGED):
+        _check(h, rc)
+    return info.as_dict()
+
+
+def stk_profile(h, enable):
+    return _check(h, _lib.stk_profile(h, int(enable)))
+
+
+def stk_profile_read(h, k):
+    name = ctypes.c_char_p()
+    launches = ctypes.c_longlong()
+    ms = ctypes.c_double()
+    nbytes = ctypes.c_double()
+    rc = _lib.stk_profile_read(h, int(k), ctypes.byref(name), ctypes.byref(launches),
+                               ctypes.byref(ms), ctypes.byref(nbytes))
+    if rc != 0:
+        raise StokesError(rc, "profile index out of range")
+    return {"name": name.value.decode(), "launches": launches.value, "ms": ms.value,
+            "bytes": nbytes.value}
+
+
+# ------------------------------------------------------------ convenience
+class StokesSolver:
+    """Owns one stk_handle; methods take/return torch CUDA tensors."""
+
+    def __init__(self, dim, n, bc, h=1.0):
+        self.dim = int(dim)
+        self.n = tuple(list(n) + [1] * (3 - len(n)))
+        self.bc = tuple(list(bc) + [0] * (6 - len(bc)))
+        self.h = float(h)
+        self.handle = stk_create(dim, n, h, bc)
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            stk_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def face_shape(self, a):
+        return face_shape(self.n, self.bc, a)
+
+    def cell_shape(self):
+        return (self.n[2], self.n[1], self.n[0])
+
+    def zeros(self, device="cuda"):
+        import torch
+        u = [torch.zeros(self.face_shape(a), dtype=torch.float64, device=device) for a in range(self.dim)]
+        p = torch.zeros(self.cell_shape(), dtype=torch.float64, device=device)
+        return u, p
+
+    def set_coefficients(self, rho, mu, theta):
+        dt = math.inf if theta == 0.0 else 1.0 / theta
+        stk_set_coefficients(self.handle, rho, mu, dt)
+
+    def apply_operator(self, x_u, x_p):
+        y_u, y_p = self.zeros(x_p.device)
+        stk_apply_operator(self.handle, x_u, x_p, y_u, y_p)
+        return y_u, y_p
+
+    def apply_preconditioner(self, which, b_u, b_p):
+        x_u, x_p = self.zeros(b_p.device)
+        stk_apply_preconditioner(self.handle, which, b_u, b_p, x_u, x_p)
+        return x_u, x_p
+
+    def solve(self, b_u, b_p, x_u=None, x_p=None, **kw):
+        p = stk_default_params()
+        for k, v in kw.items():
+            setattr(p, k, v)
+        if x_u is None:
+            x_u, x_p = self.zeros(b_p.device)
+        info = stk_solve(self.handle, p, b_u, b_p, x_u, x_p)
+        return x_u, x_p, info
