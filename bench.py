@@ -1,0 +1,392 @@
+#!/usr/bin/env python3
+"""Benchmark: time to a relative true residual of 1e-10 for the staggered
+variable-coefficient Stokes system on one GB300, through libstokes_gb300.
+
+One step = set the coefficients (face densities, node/edge viscosities, the
+FP64 and FP32 multigrid hierarchy) and solve M x = b from x = 0 to
+||b - M x|| <= 1e-10 ||b|| with GMRES(10) and the workload's preconditioner.
+
+Default workload: 3D unsteady Stokes on 128^3 periodic cells, rho contrast
+1e2 and mu contrast 1e3 from seeded smooth log-normal fields, theta = 1
+(viscous CFL number 1), forcing f ~ N(0,1) and mean-free g ~ N(0,1), P1.
+Inputs are larger than L2 (8.4M unknowns: b and x alone are 134 MB, the FP64
+Krylov basis 740 MB) and L2 is flushed by writing 256 MB between steps.
+
+Forms: "fp64" (left-preconditioned GMRES, all FP64; the line's value) and
+"mixed" (flexible GMRES in FP64 around an FP32 preconditioner; reported
+beside it).  `--impl reference` times the FP64 CPU oracle instead.
+
+Multi-GPU: replicas only (each rank solves its own copy; value = max over
+ranks of the per-solve time).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Stokes time-to-1e-10 residual & GMRES iters; V-cycle/matvec HBM GB/s vs peak"
+UNIT = "ms"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "c5", "bubble2d", "bubble3d"])
+    ap.add_argument("--n", type=int, default=0, help="override the grid size")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def make_problem(name, n):
+    from paper_1308_4605_gb300 import workloads as wl
+    if name == "c3":
+        return wl.config_c3(n or 128), {"workload": f"3d_unsteady_periodic_{n or 128}^3",
+                                         "rho_contrast": 1e2, "mu_contrast": 1e3, "precond": "P1"}
+    if name == "c2":
+        return wl.config_c2(n or 512), {"workload": f"2d_steady_noslip_20_inclusions_mu1e4_{n or 512}^2",
+                                         "precond": "P2"}
+    if name == "c1":
+        return wl.config_c1(n or 32), {"workload": f"2d_unsteady_periodic_{n or 32}^2", "precond": "P1"}
+    if name == "c5":
+        return wl.config_c5(n or 64), {"workload": f"3d_steady_noslip_{n or 64}^3", "precond": "P2"}
+    if name == "bubble2d":
+        return wl.bubble(2, n or 512), {"workload": f"bubble_2d_r100_steady_{n or 512}^2", "precond": "P1"}
+    return wl.bubble(3, n or 128), {"workload": f"bubble_3d_r100_steady_{n or 128}^3", "precond": "P1"}
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- oracle arm
+def oracle_time_to_solution(pr, gpu_iterations=None, budget_s=20.0):
+    """Time the FP64 CPU oracle on a bounded sample of the workload.
+
+    The sample is the same generator at the largest size whose setup and a
+    few GMRES(10) iterations fit the budget (64^3 for the 128^3 workload,
+    full size for small 2D workloads); the time to solution is
+    setup + iterations * time per iteration, scaled by the ratio of unknowns
+    to the full size.  Returns (ms, description, cores)."""
+    import numpy as np
+    from oracle import assemble as asm
+    from oracle import krylov
+    from oracle.grid import Grid
+    from oracle.precond import Preconditioner
+    from paper_1308_4605_gb300 import workloads as wl
+
+    full_unknowns = (pr.dim + 1) * int(np.prod(pr.n))
+    n_full = pr.n[0]
+    n = n_full
+    while n > 8 and (pr.dim + 1) * n ** pr.dim > (2_200_000 if pr.dim == 3 else 1_100_000):
+        n //= 2
+    if pr.name.startswith("3d_unsteady_periodic"):
+        spr = wl.config_c3(n)
+    elif pr.name.startswith("3d_steady_noslip"):
+        spr = wl.config_c5(n)
+    elif pr.name.startswith("2d_steady_noslip_inclusions"):
+        spr = wl.config_c2(n)
+    elif pr.name.startswith("2d_unsteady_periodic"):
+        spr = wl.config_c1(n)
+    else:
+        spr = pr if n == n_full else wl.bubble(pr.dim, n)
+    g = Grid(spr.dim, spr.n, spr.h, spr.bc)
+    t0 = time.perf_counter()
+    M = asm.stokes_from_fields(g, spr.rho, spr.mu, spr.theta)
+    P = Preconditioner(g, spr.rho, spr.mu, spr.theta, spr.precond)
+    t_setup = time.perf_counter() - t0
+    b = g.pack(spr.b_u, spr.b_p)
+    k = 3
+    t0 = time.perf_counter()
+    _, info = krylov.gmres(lambda v: M @ v, P, b, rtol=1e-30, maxit=k)
+    t_iter = (time.perf_counter() - t0) / max(info["iterations"], 1)
+    iters = gpu_iterations if gpu_iterations else 30
+    scale = full_unknowns / ((spr.dim + 1) * int(np.prod(spr.n)))
+    ms = (t_setup + iters * t_iter) * scale * 1e3
+    desc = (f"oracle (scipy.sparse, FP64) setup + {k} GMRES(10) iterations of the same generator at "
+            f"{'x'.join(map(str, spr.n[:spr.dim]))} ({t_setup:.1f} s setup, {t_iter:.2f} s/iteration), "
+            f"time to solution = setup + {iters} iterations (the GPU's count), scaled x{scale:.0f} to "
+            f"{'x'.join(map(str, pr.n[:pr.dim]))} unknowns")
+    return ms, desc, 1
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    pr, cfg = make_problem(args.workload, args.n)
+    times = []
+    desc = ""
+    for i in range(args.warmup + args.steps):
+        ms, desc, cores = oracle_time_to_solution(pr)
+        if i >= args.warmup:
+            times.append(ms)
+    v = statistics.mean(times)
+    cfg = dict(cfg, l2="oracle on host cores")
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1308_4605_gb300 import stokes as S
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    pr, cfg = make_problem(args.workload, args.n)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    rho, mu = t(pr.rho), t(pr.mu)
+    b_u = [t(x) for x in pr.b_u]
+    b_p = t(pr.b_p)
+    solver = S.StokesSolver(pr.dim, pr.n[:pr.dim], pr.bc[:2 * pr.dim], pr.h)
+    x_u, x_p = solver.zeros(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def params(precision):
+        p = S.stk_default_params()
+        p.precond = pr.precond
+        p.rtol = 1e-10
+        p.maxit = 3000
+        p.precision = precision
+        return p
+
+    def step(precision):
+        solver.set_coefficients(rho, mu, pr.theta)
+        for v in x_u:
+            v.zero_()
+        x_p.zero_()
+        return S.stk_solve(solver.handle, params(precision), b_u, b_p, x_u, x_p)
+
+    def timed(precision, k):
+        times, infos = [], []
+        for _ in range(k):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = step(precision)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            infos.append(info)
+        return times, infos
+
+    for _ in range(args.warmup):
+        step(S.STK_FP64)
+        step(S.STK_MIXED)
+    torch.cuda.synchronize()
+
+    clk = ClockSampler(local)
+    clk.start()
+    barrier()
+    torch.cuda.synchronize()
+    k0 = S.stk_kernel_launches(solver.handle)
+    t_wall = time.perf_counter()
+    times64, infos64 = timed(S.STK_FP64, args.steps)
+    barrier()
+    torch.cuda.synchronize()
+    wall64 = time.perf_counter() - t_wall
+    launches = S.stk_kernel_launches(solver.handle) - k0
+    times_mx, infos_mx = timed(S.STK_MIXED, args.steps)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+
+    ms64 = statistics.mean(times64)
+    ms_mx = statistics.mean(times_mx)
+    if world > 1:
+        tt = torch.tensor([ms64, ms_mx], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms64, ms_mx = tt.tolist()
+
+    # ---- end to end through the C ABI from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_in = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in
+                [pr.rho, pr.mu] + list(pr.b_u) + [pr.b_p]]
+        h_out = [torch.empty(v.shape, dtype=torch.float64).pin_memory() for v in x_u + [x_p]]
+        d_in = [rho, mu] + b_u + [b_p]
+        h2d = sum(v.numel() * 8 for v in h_in)
+        d2h = sum(v.numel() * 8 for v in h_out)
+        et = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for d, hh in zip(d_in, h_in):
+                d.copy_(hh, non_blocking=True)
+            step(S.STK_FP64)
+            for hh, d in zip(h_out, x_u + [x_p]):
+                hh.copy_(d, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            et.append(e0.elapsed_time(e1))
+        e2e = {"value": statistics.mean(et), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    # ---- per-kernel device time (CUDA events on the solve's stream), one
+    # extra FP64 step and one extra mixed step after the timed ones
+    def profile(precision):
+        S.stk_profile(solver.handle, 1)
+        flush.fill_(1.0)
+        step(precision)
+        fam = [S.stk_profile_read(solver.handle, k) for k in range(S.STK_NPROF)]
+        S.stk_profile(solver.handle, 0)
+        return [f for f in fam if f["launches"] > 0]
+
+    fam64 = profile(S.STK_FP64)
+    fam_mx = profile(S.STK_MIXED)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs")
+    peak_note = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    dom = max(fam64, key=lambda f: f["ms"])
+    achieved = dom["bytes"] / (dom["ms"] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                "peak_source": peak_note,
+                "avg_launch_us": dom["ms"] * 1e3 / dom["launches"],
+                "bytes_per_launch": dom["bytes"] / dom["launches"]}
+
+    def fam_table(fams, total):
+        return {f["name"]: {"launches": f["launches"], "ms": round(f["ms"], 4),
+                            "share": round(f["ms"] / total, 4),
+                            "GBps": round(f["bytes"] / max(f["ms"], 1e-9) / 1e6, 1)} for f in fams}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cms, desc, cores = oracle_time_to_solution(pr, infos64[0]["iterations"])
+            cpu = {"value": cms, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+        except Exception as e:  # the baseline is informative only
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+
+    line = {
+        "metric": METRIC, "value": ms64, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(cfg, l2="flushed between steps (256 MB write); inputs > L2",
+                       parallelism="replicas" if world > 1 else "single GPU"),
+        "gmres_iterations": infos64[0]["iterations"],
+        "true_residual": max(i["true_residual"] for i in infos64),
+        "scalar_vcycles": infos64[0]["scalar_vcycles"],
+        "forms": {
+            "fp64": {"ms": ms64, "iterations": infos64[0]["iterations"],
+                     "true_residual": max(i["true_residual"] for i in infos64)},
+            "mixed_fp32_precond": {"ms": ms_mx, "iterations": infos_mx[0]["iterations"],
+                                   "true_residual": max(i["true_residual"] for i in infos_mx),
+                                   "speedup_vs_fp64": ms64 / ms_mx},
+        },
+        "roofline": roofline,
+        "kernels_fp64": fam_table(fam64, sum(f["ms"] for f in fam64)),
+        "kernels_mixed": fam_table(fam_mx, sum(f["ms"] for f in fam_mx)),
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "wall_s_fp64_steps": wall64,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    solver.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -159,6 +159,8 @@ int stk_solve(stk_handle* h, const stk_solver_params* params, const double* cons
  * output word, once per launch).  Returns -1 when k is out of range. */
 #define STK_NPROF 16
 int stk_profile(stk_handle* h, int enable);
+/* Number of CUDA kernels this handle has launched since it was created. */
+long long stk_kernel_launches(const stk_handle* h);
 int stk_profile_read(stk_handle* h, int k, const char** name, long long* launches,
                      double* ms, double* bytes);
 

@@ -78,6 +78,7 @@ struct stk_handle {
     double* dsc = nullptr;    // device scalars
     double* hpin = nullptr;   // pinned host staging
     bool prof = false;
+    long long nkern = 0;      // kernels launched by this handle
     std::vector<ProfRec> recs;
     std::vector<cudaEvent_t> evpool;
     size_t evnext = 0;
@@ -164,7 +165,8 @@ struct Scope {
     stk_handle* h;
     ProfRec rec{};
     cudaStream_t s;
-    Scope(stk_handle* h_, int cat, double bytes, cudaStream_t s_) : h(h_), s(s_) {
+    Scope(stk_handle* h_, int cat, double bytes, cudaStream_t s_, int kernels = 1) : h(h_), s(s_) {
+        h->nkern += kernels;
         if (!h->prof) return;
         rec.cat = cat;
         rec.bytes = bytes;
@@ -328,7 +330,7 @@ void poisson_solve(stk_handle* h, const T* r, T* phi, const MGParams& mp, cudaSt
     const Level& L = h->lev[0];
     Work<T> W = work_of<T>(L);
     {
-        Scope sc(h, PF_MEAN, 2.0 * sizeof(T) * L.g.ncell, s);
+        Scope sc(h, PF_MEAN, 2.0 * sizeof(T) * L.g.ncell, s, 3);
         launch_sum<T>(L.g.ncell, r, h->red, h->dsc + DS_SUM, s);
         launch_copy_sub_mean<T>(L.g.ncell, r, W.rhs_p, h->dsc + DS_SUM, s);
     }
@@ -338,7 +340,7 @@ void poisson_solve(stk_handle* h, const T* r, T* phi, const MGParams& mp, cudaSt
 template <typename T>
 void remove_mean(stk_handle* h, T* x, cudaStream_t s) {
     const Level& L = h->lev[0];
-    Scope sc(h, PF_MEAN, 3.0 * sizeof(T) * L.g.ncell, s);
+    Scope sc(h, PF_MEAN, 3.0 * sizeof(T) * L.g.ncell, s, 3);
     launch_sum<T>(L.g.ncell, x, h->red, h->dsc + DS_SUM + 1, s);
     launch_sub_mean<T>(L.g.ncell, x, h->dsc + DS_SUM + 1, s);
 }
@@ -506,11 +508,11 @@ int orthogonalise(stk_handle* h, int j, cudaStream_t s, double* hcol) {
     std::vector<const double*> Vp(h->V.begin(), h->V.begin() + j + 1);
     double* hd = h->dsc + DS_H;
     {
-        Scope sc(h, PF_MDOT, 8.0 * n * (j + 2), s);
+        Scope sc(h, PF_MDOT, 8.0 * n * (j + 2), s, 2);
         launch_multidot(n, j, Vp.data(), w, h->red, hd, s);
     }
     {
-        Scope sc(h, PF_UPD, 8.0 * n * (j + 3), s);
+        Scope sc(h, PF_UPD, 8.0 * n * (j + 3), s, 2);
         launch_update_norm(n, j, Vp.data(), hd, w, h->red, h->dsc + DS_N2, s);
     }
     CK(cudaMemcpyAsync(h->hpin, hd, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
@@ -523,11 +525,11 @@ int orthogonalise(stk_handle* h, int j, cudaStream_t s, double* hcol) {
         return fail(h, STK_ERR_NONFINITE, "non-finite value in the Arnoldi process");
     if (after < 0.5 * before) {   // lost more than 1 - 1/sqrt(2) of its norm: re-orthogonalise
         {
-            Scope sc(h, PF_MDOT, 8.0 * n * (j + 2), s);
+            Scope sc(h, PF_MDOT, 8.0 * n * (j + 2), s, 2);
             launch_multidot(n, j, Vp.data(), w, h->red, hd, s);
         }
         {
-            Scope sc(h, PF_UPD, 8.0 * n * (j + 3), s);
+            Scope sc(h, PF_UPD, 8.0 * n * (j + 3), s, 2);
             launch_update_norm(n, j, Vp.data(), hd, w, h->red, h->dsc + DS_N2, s);
         }
         CK(cudaMemcpyAsync(h->hpin, hd, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s));
@@ -547,7 +549,7 @@ int orthogonalise(stk_handle* h, int j, cudaStream_t s, double* hcol) {
 
 int norm2(stk_handle* h, const double* x, int n, cudaStream_t s, double* out) {
     {
-        Scope sc(h, PF_MDOT, 8.0 * n, s);
+        Scope sc(h, PF_MDOT, 8.0 * n, s, 2);
         launch_multidot(n, -1, nullptr, x, h->red, h->dsc + DS_N2 + 1, s);
     }
     CK(cudaMemcpyAsync(h->hpin + 41, h->dsc + DS_N2 + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -969,6 +971,8 @@ int stk_profile(stk_handle* h, int enable) {
     h->prof = enable != 0;
     return STK_OK;
 }
+
+long long stk_kernel_launches(const stk_handle* h) { return h ? h->nkern : -1; }
 
 int stk_profile_read(stk_handle* h, int k, const char** name, long long* launches, double* ms,
                      double* bytes) {

@@ -75,6 +75,7 @@ def _load():
         "stk_solve": (I, [P, ctypes.POINTER(stk_solver_params), PP, P, PP, P,
                           ctypes.POINTER(stk_solve_info), P]),
         "stk_profile": (I, [P, I]),
+        "stk_kernel_launches": (ctypes.c_longlong, [P]),
         "stk_profile_read": (I, [P, I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong),
                                  ctypes.POINTER(D), ctypes.POINTER(D)]),
     }
@@ -89,7 +90,7 @@ _lib = _load()
 EXPORTED = ["stk_default_params", "stk_create", "stk_destroy", "stk_last_error", "stk_face_length",
             "stk_cell_length", "stk_set_coefficients", "stk_apply_operator",
             "stk_apply_preconditioner", "stk_velocity_vcycle", "stk_pressure_vcycle", "stk_solve",
-            "stk_profile", "stk_profile_read"]
+            "stk_profile", "stk_profile_read", "stk_kernel_launches"]
 
 
 def library():
@@ -214,6 +215,10 @@ def stk_solve(h, params, b_u, b_p, x_u, x_p, stream=None):
 
 def stk_profile(h, enable):
     return _check(h, _lib.stk_profile(h, int(enable)))
+
+
+def stk_kernel_launches(h):
+    return int(_lib.stk_kernel_launches(h))
 
 
 def stk_profile_read(h, k):
