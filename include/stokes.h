@@ -164,6 +164,33 @@ long long stk_kernel_launches(const stk_handle* h);
 int stk_profile_read(stk_handle* h, int k, const char** name, long long* launches,
                      double* ms, double* bytes);
 
+/* Pressure V-cycle for callers that cannot allocate device memory.
+ * (No counterpart in the paper: this is a deployment variant of
+ * stk_pressure_vcycle.)  Callers whose device memory is wholly owned by another
+ * allocator, or whose loop cannot afford the implicit synchronisation of
+ * cudaMalloc, cannot create an stk_handle; this call needs none.  It computes
+ * x_p = L~_rho^{-1} r_p, one V-cycle with zero initial guess for
+ * D (1/rho_f) G x = r (App. C), exactly as stk_pressure_vcycle does on a handle
+ * whose coefficients were set from the same rho, for the grid (dim, n, h, bc)
+ * described as in stk_create.  rho, r_p (inputs) and x_p (output) are
+ * caller-owned device cell arrays.
+ * Workspace: a file-scope device array of 2,097,152 doubles (16 MiB) that every
+ * GPU loading this library holds until the process exits; grids needing more
+ * (about 6 doubles per cell: 2D up to 512^2, 3D up to 64^3 fit) are rejected
+ * with STK_ERR_SIZE before any device work.  No cudaMalloc, cudaFree or other
+ * allocating call is made.  The first call on each device looks up the
+ * array's device address (with that device current), so make that first call
+ * before any stream capture.  All calls on a device share that device's one
+ * array and leave their workspace in it; each call writes every value it
+ * later reads, so a call does not depend on what an earlier call left.  Calls
+ * whose work overlaps on the same GPU (issued on different streams, or from
+ * different host threads, without ordering between them) race on the array:
+ * serialise them.  Returns STK_OK, STK_ERR_ARG, STK_ERR_SIZE or STK_ERR_CUDA
+ * (no message is recorded for stk_last_error). */
+int stk_pressure_vcycle_noalloc(int dim, const int* n, double h, const int* bc,
+                                const double* rho, const double* r_p, double* x_p,
+                                void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -76,6 +76,7 @@ def _load():
                           ctypes.POINTER(stk_solve_info), P]),
         "stk_profile": (I, [P, I]),
         "stk_kernel_launches": (ctypes.c_longlong, [P]),
+        "stk_pressure_vcycle_noalloc": (I, [I, ctypes.POINTER(I), D, ctypes.POINTER(I), P, P, P, P]),
         "stk_profile_read": (I, [P, I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong),
                                  ctypes.POINTER(D), ctypes.POINTER(D)]),
     }
@@ -90,7 +91,7 @@ _lib = _load()
 EXPORTED = ["stk_default_params", "stk_create", "stk_destroy", "stk_last_error", "stk_face_length",
             "stk_cell_length", "stk_set_coefficients", "stk_apply_operator",
             "stk_apply_preconditioner", "stk_velocity_vcycle", "stk_pressure_vcycle", "stk_solve",
-            "stk_profile", "stk_profile_read", "stk_kernel_launches"]
+            "stk_profile", "stk_profile_read", "stk_kernel_launches", "stk_pressure_vcycle_noalloc"]
 
 
 def library():
@@ -215,6 +216,18 @@ def stk_solve(h, params, b_u, b_p, x_u, x_p, stream=None):
 
 def stk_profile(h, enable):
     return _check(h, _lib.stk_profile(h, int(enable)))
+
+
+def stk_pressure_vcycle_noalloc(dim, n, h, bc, rho, r_p, x_p, stream=None):
+    """One pressure V-cycle without any device allocation (see stokes.h)."""
+    nn = (ctypes.c_int * 3)(*(list(n) + [1] * (3 - len(n))))
+    bb = (ctypes.c_int * 6)(*(list(bc) + [0] * (6 - len(bc))))
+    ncell = int(nn[0]) * int(nn[1]) * int(nn[2])
+    rc = _lib.stk_pressure_vcycle_noalloc(int(dim), nn, float(h), bb, _ptr(rho, ncell),
+                                          _ptr(r_p, ncell), _ptr(x_p, ncell), _stream(stream))
+    if rc != STK_OK:
+        raise StokesError(rc, "stk_pressure_vcycle_noalloc failed")
+    return rc
 
 
 def stk_kernel_launches(h):
