@@ -163,9 +163,8 @@ def _mg_rate(g, which):
 @pytest.mark.parametrize("which", ["velocity", "pressure"])
 @pytest.mark.parametrize("dim,n", [(2, (64, 64)), (3, (16, 16, 16))])
 def test_vcycle_reduces_residual_tenfold(which, dim, n):
-    """Sec. 4.1.1: with 2 sweeps, V-cycles reduce the residual of the
-    constant-coefficient steady no-slip subproblems by an order of magnitude
-    per cycle.  Read as: geometric mean of the first six reductions <= 0.1 and
+    """Sec. 4.1.1: with 2 sweeps, each V-cycle cuts the residual of the
+    constant-coefficient steady no-slip subproblems by a factor of ten.  Read as: geometric mean of the first six reductions <= 0.1 and
     no single cycle worse than 0.15 (the 3D velocity cycle settles near 0.12)."""
     g = Grid(dim, n, 1.0, (NOSLIP,) * 6)
     rates = _mg_rate(g, which)
