@@ -100,6 +100,8 @@ void launch_schur_combine(int n, double theta, const T* phi, const T* mu, const 
 // reductions with a fixed block count: deterministic results
 constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
 constexpr int RED_THREADS = 256;
+constexpr int KRY_BLOCKS = 1216;  // 8 x 152 SMs: grid of the Krylov kernels (krylov.cu)
+constexpr int RED_SCRATCH = KRY_BLOCKS * 36;   // doubles of reduction scratch
 template <typename T>  // out[0] = sum x  (scratch >= RED_BLOCKS doubles)
 void launch_sum(int n, const T* x, double* scratch, double* out, cudaStream_t s);
 template <typename T>  // x -= (*sum) / n

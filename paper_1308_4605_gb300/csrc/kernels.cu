@@ -686,82 +686,10 @@ __global__ void k_copy_sub_mean(int n, const T* __restrict__ in, T* out,
     if (t < n) out[t] = in[t] - T(*sum / n);
 }
 
-constexpr int MAXV = 33;
-struct PtrArr {
-    const void* p[MAXV];
-};
-
-__global__ void k_multidot(int n, int j, PtrArr V, const double* __restrict__ w, double* part) {
-    __shared__ double sh[32];
-    double acc[MAXV + 1];
-#pragma unroll
-    for (int i = 0; i <= MAXV; ++i) acc[i] = 0.0;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-        double wv = w[t];
-#pragma unroll
-        for (int i = 0; i < MAXV; ++i)
-            if (i <= j) acc[i] += wv * static_cast<const double*>(V.p[i])[t];
-        acc[MAXV] += wv * wv;
-    }
-#pragma unroll
-    for (int i = 0; i < MAXV; ++i) {
-        if (i <= j) {
-            double s = block_sum(acc[i], sh);
-            if (threadIdx.x == 0) part[i * RED_BLOCKS + blockIdx.x] = s;
-        }
-    }
-    double s = block_sum(acc[MAXV], sh);
-    if (threadIdx.x == 0) part[(j + 1) * RED_BLOCKS + blockIdx.x] = s;
-}
-
-__global__ void k_update_norm(int n, int j, PtrArr V, const double* __restrict__ h, double* w,
-                              double* part) {
-    __shared__ double sh[32];
-    double hh[MAXV];
-#pragma unroll
-    for (int i = 0; i < MAXV; ++i) hh[i] = i <= j ? h[i] : 0.0;
-    double s = 0.0;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-        double wv = w[t];
-#pragma unroll
-        for (int i = 0; i < MAXV; ++i)
-            if (i <= j) wv -= hh[i] * static_cast<const double*>(V.p[i])[t];
-        w[t] = wv;
-        s += wv * wv;
-    }
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
-}
-
-template <typename TV>
-__global__ void k_combine(int n, int k, PtrArr V, const double* __restrict__ y, double* x) {
-    double yy[MAXV];
-#pragma unroll
-    for (int i = 0; i < MAXV; ++i) yy[i] = i < k ? y[i] : 0.0;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-        double acc = x[t];
-#pragma unroll
-        for (int i = 0; i < MAXV; ++i)
-            if (i < k) acc += yy[i] * double(static_cast<const TV*>(V.p[i])[t]);
-        x[t] = acc;
-    }
-}
-
-__global__ void k_scale_inv_sqrt(int n, double* x, const double* __restrict__ nrm2) {
-    double s = 1.0 / sqrt(*nrm2);
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
-        x[t] *= s;
-}
-
 template <typename T>
 __global__ void k_axpy(int n, T a, const T* __restrict__ x, T* __restrict__ y) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) y[t] += a * x[t];
-}
-
-__global__ void k_scale(int n, double* x, double a) {
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
-        x[t] *= a;
 }
 
 __global__ void k_check_fields(int n, const double* __restrict__ rho, const double* __restrict__ mu,
@@ -951,40 +879,9 @@ void launch_copy_sub_mean(int n, const T* in, T* out, const double* sum, cudaStr
     k_copy_sub_mean<T><<<nblk(n), TPB, 0, s>>>(n, in, out, sum);
 }
 
-void launch_multidot(int n, int j, const double* const* V, const double* w, double* scratch,
-                     double* h, cudaStream_t s) {
-    PtrArr pa{};
-    for (int i = 0; i <= j; ++i) pa.p[i] = V[i];
-    k_multidot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, j, pa, w, scratch);
-    k_final<<<1, RED_THREADS, 0, s>>>(j + 2, scratch, h);
-}
-
-void launch_update_norm(int n, int j, const double* const* V, const double* h, double* w,
-                        double* scratch, double* out, cudaStream_t s) {
-    PtrArr pa{};
-    for (int i = 0; i <= j; ++i) pa.p[i] = V[i];
-    k_update_norm<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, j, pa, h, w, scratch);
-    k_final<<<1, RED_THREADS, 0, s>>>(1, scratch, out);
-}
-
-template <typename TV>
-void launch_combine(int n, int k, const TV* const* V, const double* y, double* x, cudaStream_t s) {
-    PtrArr pa{};
-    for (int i = 0; i < k; ++i) pa.p[i] = V[i];
-    k_combine<TV><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, k, pa, y, x);
-}
-
-void launch_scale_inv_sqrt(int n, double* x, const double* nrm2, cudaStream_t s) {
-    k_scale_inv_sqrt<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, x, nrm2);
-}
-
 template <typename T>
 void launch_axpy(int n, T a, const T* x, T* y, cudaStream_t s) {
     k_axpy<T><<<nblk(n), TPB, 0, s>>>(n, a, x, y);
-}
-
-void launch_scale(int n, double* x, double a, cudaStream_t s) {
-    k_scale<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, x, a);
 }
 
 void launch_check_fields(int n, const double* rho, const double* mu, double* scratch, double* out,
@@ -1019,8 +916,6 @@ void launch_check_fields(int n, const double* rho, const double* mu, double* scr
     template void launch_sum<T>(int, const T*, double*, double*, cudaStream_t);                  \
     template void launch_sub_mean<T>(int, T*, const double*, cudaStream_t);                      \
     template void launch_copy_sub_mean<T>(int, const T*, T*, const double*, cudaStream_t);       \
-    template void launch_combine<T>(int, int, const T* const*, const double*, double*,           \
-                                    cudaStream_t);                                                 \
     template void launch_stokes_matvec<T>(const Geom&, Coef<double>, const T*, double*,          \
                                           cudaStream_t);                                           \
     template void launch_axpy<T>(int, T, const T*, T*, cudaStream_t);

@@ -1,0 +1,226 @@
+// Krylov vector kernels of the GMRES core (Sec. 3.2): classical Gram-Schmidt
+// projections (one multi-dot pass), the update w -= sum h_i v_i fused with
+// ||w||^2, the solution update x += sum y_i z_i and scalings.
+//
+// These are streaming kernels over packed Stokes vectors of N doubles.  The
+// number of basis vectors is a template parameter (dispatched at run time),
+// loads are 16-byte, the grid is a fixed KRY_BLOCKS blocks (8 per SM) and
+// every reduction sums its block partials in a fixed order, so results are
+// bitwise reproducible.  On GB300 the FP64 FMA rate (about 1.2 TFLOP/s) caps a
+// pass at about one FMA per 8 bytes read.
+#include "internal.cuh"
+
+namespace stk {
+namespace {
+
+constexpr int KT = 256;
+constexpr int MAXV = 33;
+
+struct PtrArr {
+    const void* p[MAXV];
+};
+
+__device__ __forceinline__ double wsum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Reduce NV per-thread values over the block; value i of block b goes to
+// part[i * KRY_BLOCKS + b].
+template <int NV>
+__device__ __forceinline__ void block_sums(const double (&v)[NV], double* part) {
+    __shared__ double sh[NV][KT / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        double s = wsum(v[i]);
+        if (lane == 0) sh[i][w] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < KT / 32; ++k) s += sh[threadIdx.x][k];
+        part[threadIdx.x * KRY_BLOCKS + blockIdx.x] = s;
+    }
+}
+
+// out[k] = sum_b part[k * KRY_BLOCKS + b], one block per k, fixed order.
+__global__ void __launch_bounds__(KT) k_final_multi(const double* __restrict__ part, double* out) {
+    __shared__ double sh[KT / 32];
+    const int k = blockIdx.x;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < KRY_BLOCKS; b += KT) s += part[k * KRY_BLOCKS + b];
+    s = wsum(s);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = 0.0;
+#pragma unroll
+        for (int i = 0; i < KT / 32; ++i) r += sh[i];
+        out[k] = r;
+    }
+}
+
+// h[i] = <w, V_i> (i <= J) and h[J+1] = <w, w>
+template <int J>
+__global__ void __launch_bounds__(KT) k_mdot(int n, PtrArr V, const double* __restrict__ w,
+                                              double* __restrict__ part) {
+    double acc[J + 2];
+#pragma unroll
+    for (int i = 0; i < J + 2; ++i) acc[i] = 0.0;
+    const int n2 = n >> 1;
+    const double2* w2 = reinterpret_cast<const double2*>(w);
+    for (int t = blockIdx.x * KT + threadIdx.x; t < n2; t += KRY_BLOCKS * KT) {
+        const double2 a = w2[t];
+#pragma unroll
+        for (int i = 0; i <= J; ++i) {
+            const double2 v = reinterpret_cast<const double2*>(V.p[i])[t];
+            acc[i] = fma(a.x, v.x, acc[i]);
+            acc[i] = fma(a.y, v.y, acc[i]);
+        }
+        acc[J + 1] = fma(a.x, a.x, acc[J + 1]);
+        acc[J + 1] = fma(a.y, a.y, acc[J + 1]);
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        const double a = w[n - 1];
+#pragma unroll
+        for (int i = 0; i <= J; ++i) acc[i] = fma(a, static_cast<const double*>(V.p[i])[n - 1], acc[i]);
+        acc[J + 1] = fma(a, a, acc[J + 1]);
+    }
+    block_sums<J + 2>(acc, part);
+}
+
+// w -= sum_{i <= J} h[i] V_i, then ||w||^2
+template <int J>
+__global__ void __launch_bounds__(KT) k_upd(int n, PtrArr V, const double* __restrict__ h,
+                                             double* __restrict__ w, double* __restrict__ part) {
+    double hh[J + 1];
+#pragma unroll
+    for (int i = 0; i <= J; ++i) hh[i] = h[i];
+    double s[1] = {0.0};
+    const int n2 = n >> 1;
+    double2* w2 = reinterpret_cast<double2*>(w);
+    for (int t = blockIdx.x * KT + threadIdx.x; t < n2; t += KRY_BLOCKS * KT) {
+        double2 a = w2[t];
+#pragma unroll
+        for (int i = 0; i <= J; ++i) {
+            const double2 v = reinterpret_cast<const double2*>(V.p[i])[t];
+            a.x = fma(-hh[i], v.x, a.x);
+            a.y = fma(-hh[i], v.y, a.y);
+        }
+        w2[t] = a;
+        s[0] = fma(a.x, a.x, s[0]);
+        s[0] = fma(a.y, a.y, s[0]);
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        double a = w[n - 1];
+#pragma unroll
+        for (int i = 0; i <= J; ++i) a = fma(-hh[i], static_cast<const double*>(V.p[i])[n - 1], a);
+        w[n - 1] = a;
+        s[0] = fma(a, a, s[0]);
+    }
+    block_sums<1>(s, part);
+}
+
+template <typename TV> struct Vec2;
+template <> struct Vec2<double> { using type = double2; };
+template <> struct Vec2<float> { using type = float2; };
+
+// x += sum_{i < K} y[i] V_i
+template <int K, typename TV>
+__global__ void __launch_bounds__(KT) k_comb(int n, PtrArr V, const double* __restrict__ y,
+                                              double* __restrict__ x) {
+    using V2 = typename Vec2<TV>::type;
+    double yy[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) yy[i] = y[i];
+    const int n2 = n >> 1;
+    double2* x2 = reinterpret_cast<double2*>(x);
+    for (int t = blockIdx.x * KT + threadIdx.x; t < n2; t += KRY_BLOCKS * KT) {
+        double2 a = x2[t];
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            const V2 v = reinterpret_cast<const V2*>(V.p[i])[t];
+            a.x = fma(yy[i], double(v.x), a.x);
+            a.y = fma(yy[i], double(v.y), a.y);
+        }
+        x2[t] = a;
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        double a = x[n - 1];
+#pragma unroll
+        for (int i = 0; i < K; ++i) a = fma(yy[i], double(static_cast<const TV*>(V.p[i])[n - 1]), a);
+        x[n - 1] = a;
+    }
+}
+
+__global__ void __launch_bounds__(KT) k_scal(int n, double* __restrict__ x, double a,
+                                             const double* __restrict__ nrm2) {
+    const double s = nrm2 ? 1.0 / sqrt(*nrm2) : a;
+    for (int t = blockIdx.x * KT + threadIdx.x; t < n; t += KRY_BLOCKS * KT) x[t] *= s;
+}
+
+PtrArr pack(const void* const* V, int k) {
+    PtrArr pa{};
+    for (int i = 0; i < k; ++i) pa.p[i] = V[i];
+    return pa;
+}
+
+}  // namespace
+
+#define STK_J_CASES(X) \
+    X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) \
+    X(16) X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29) X(30) X(31)
+
+void launch_multidot(int n, int j, const double* const* V, const double* w, double* scratch,
+                     double* h, cudaStream_t s) {
+    PtrArr pa = pack(reinterpret_cast<const void* const*>(V), j + 1);
+    switch (j) {
+    case -1: k_mdot<-1><<<KRY_BLOCKS, KT, 0, s>>>(n, pa, w, scratch); break;
+#define X(J) case J: k_mdot<J><<<KRY_BLOCKS, KT, 0, s>>>(n, pa, w, scratch); break;
+    STK_J_CASES(X)
+#undef X
+    default: return;
+    }
+    k_final_multi<<<j + 2, KT, 0, s>>>(scratch, h);
+}
+
+void launch_update_norm(int n, int j, const double* const* V, const double* h, double* w,
+                        double* scratch, double* out, cudaStream_t s) {
+    PtrArr pa = pack(reinterpret_cast<const void* const*>(V), j + 1);
+    switch (j) {
+#define X(J) case J: k_upd<J><<<KRY_BLOCKS, KT, 0, s>>>(n, pa, h, w, scratch); break;
+    STK_J_CASES(X)
+#undef X
+    default: return;
+    }
+    k_final_multi<<<1, KT, 0, s>>>(scratch, out);
+}
+
+template <typename TV>
+void launch_combine(int n, int k, const TV* const* V, const double* y, double* x, cudaStream_t s) {
+    PtrArr pa = pack(reinterpret_cast<const void* const*>(V), k);
+    switch (k - 1) {
+#define X(J) case J: k_comb<J + 1, TV><<<KRY_BLOCKS, KT, 0, s>>>(n, pa, y, x); break;
+    STK_J_CASES(X)
+#undef X
+    default: return;
+    }
+}
+
+void launch_scale_inv_sqrt(int n, double* x, const double* nrm2, cudaStream_t s) {
+    k_scal<<<KRY_BLOCKS, KT, 0, s>>>(n, x, 0.0, nrm2);
+}
+
+void launch_scale(int n, double* x, double a, cudaStream_t s) {
+    k_scal<<<KRY_BLOCKS, KT, 0, s>>>(n, x, a, nullptr);
+}
+
+template void launch_combine<double>(int, int, const double* const*, const double*, double*,
+                                     cudaStream_t);
+template void launch_combine<float>(int, int, const float* const*, const double*, double*,
+                                    cudaStream_t);
+
+}  // namespace stk

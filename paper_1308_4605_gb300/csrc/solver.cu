@@ -11,7 +11,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 using namespace stk;
@@ -79,6 +81,19 @@ struct stk_handle {
     double* hpin = nullptr;   // pinned host staging
     bool prof = false;
     long long nkern = 0;      // kernels launched by this handle
+    // CUDA graphs of preconditioner applications, keyed by
+    // (which, sizeof(T), input, output, nu, ncoarse, profiling)
+    struct GraphEntry {
+        cudaGraphExec_t exec = nullptr;
+        long long kernels = 0;
+        std::vector<ProfRec> recs;   // event pairs captured inside (profiling)
+    };
+    std::map<std::tuple<int, int, const void*, void*, int, int, int>, GraphEntry> graphs;
+    bool use_graphs = true;
+    bool capturing = false;
+    long long cap_kernels = 0;
+    std::vector<ProfRec> caprecs;
+    cudaStream_t cap = nullptr;    // private stream used for capture only
     std::vector<ProfRec> recs;
     std::vector<cudaEvent_t> evpool;
     size_t evnext = 0;
@@ -166,20 +181,32 @@ struct Scope {
     ProfRec rec{};
     cudaStream_t s;
     Scope(stk_handle* h_, int cat, double bytes, cudaStream_t s_, int kernels = 1) : h(h_), s(s_) {
-        h->nkern += kernels;
+        if (h->capturing) h->cap_kernels += kernels;
+        else h->nkern += kernels;
         if (!h->prof) return;
         rec.cat = cat;
         rec.bytes = bytes;
         rec.a = next_event();
         rec.b = next_event();
-        cudaEventRecord(rec.a, s);
+        record(rec.a);
     }
     ~Scope() {
         if (!h->prof) return;
-        cudaEventRecord(rec.b, s);
-        h->recs.push_back(rec);
+        record(rec.b);
+        if (h->capturing) h->caprecs.push_back(rec);
+        else h->recs.push_back(rec);
+    }
+    void record(cudaEvent_t e) {
+        // inside a capture, an external record makes a timing event node
+        if (h->capturing) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+        else cudaEventRecord(e, s);
     }
     cudaEvent_t next_event() {
+        if (h->capturing) {   // events recorded by graph nodes belong to the graph
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            return e;
+        }
         if (h->evnext >= h->evpool.size()) {
             cudaEvent_t e;
             cudaEventCreate(&e);
@@ -412,6 +439,60 @@ void apply_precond(stk_handle* h, int which, const T* b, T* x, const MGParams& m
     remove_mean<T>(h, xp, s);
 }
 
+void clear_graphs(stk_handle* h) {
+    if (h->graphs.empty()) return;
+    cudaDeviceSynchronize();   // no launch of these graphs may still be in flight
+    for (auto& kv : h->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        for (auto& r : kv.second.recs) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+    }
+    h->graphs.clear();
+}
+
+// x = P^{-1} b through a CUDA graph captured on first use (one graph per
+// preconditioner, precision and buffer pair), so that the ~10^2 kernels of
+// the V-cycles are submitted with one launch.
+template <typename T>
+int run_precond(stk_handle* h, int which, const T* b, T* x, const MGParams& mp, cudaStream_t s) {
+    if (!h->use_graphs) {
+        apply_precond<T>(h, which, b, x, mp, s);
+        CKL();
+        return STK_OK;
+    }
+    auto key = std::make_tuple(which, (int)sizeof(T), (const void*)b, (void*)x, mp.nu, mp.ncoarse,
+                               h->prof ? 1 : 0);
+    auto it = h->graphs.find(key);
+    if (it == h->graphs.end()) {
+        stk_handle::GraphEntry e;
+        CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+        h->capturing = true;
+        h->cap_kernels = 0;
+        h->caprecs.clear();
+        apply_precond<T>(h, which, b, x, mp, h->cap);
+        h->capturing = false;
+        cudaGraph_t g = nullptr;
+        cudaError_t ec = cudaStreamEndCapture(h->cap, &g);
+        if (ec != cudaSuccess) return fail(h, STK_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ec));
+        ec = cudaGraphInstantiate(&e.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ec != cudaSuccess) return fail(h, STK_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ec));
+        e.kernels = h->cap_kernels;
+        e.recs = h->caprecs;
+        h->caprecs.clear();
+        it = h->graphs.emplace(key, std::move(e)).first;
+    }
+    CK(cudaGraphLaunch(it->second.exec, s));
+    h->nkern += it->second.kernels;
+    if (h->prof) {   // read the graph's event pairs before its next launch
+        h->recs.insert(h->recs.end(), it->second.recs.begin(), it->second.recs.end());
+        prof_flush(h);
+    }
+    return STK_OK;
+}
+
 double scalar_vcycles(const stk_handle* h, int which) {
     double d = h->dim;
     double p = h->theta != 0.0 ? 1.0 : 0.0;
@@ -608,9 +689,8 @@ int gmres(stk_handle* h, const stk_solver_params& prm, stk_solve_info& info, cud
             beta = rnorm;
             target = prm.rtol * bnorm;
         } else {
-            apply_precond<double>(h, prm.precond, h->tmp, h->V[0], mp, s);
+            if ((rc = run_precond<double>(h, prm.precond, h->tmp, h->V[0], mp, s))) return rc;
             info.scalar_vcycles += sv;
-            CKL();
             if ((rc = norm2(h, h->V[0], n, s, &beta))) return rc;
             if (!std::isfinite(beta)) return fail(h, STK_ERR_NONFINITE, "non-finite preconditioned residual");
             target = beta * (prm.rtol * bnorm / rnorm);
@@ -629,15 +709,19 @@ int gmres(stk_handle* h, const stk_solver_params& prm, stk_solve_info& info, cud
                     Scope sc(h, PF_CONV, 12.0 * n, s);
                     launch_convert<double, float>(n, h->V[j], h->pf.in, s);
                 }
-                apply_precond<float>(h, prm.precond, h->pf.in, h->Z[j], mp, s);
-                Scope sc(h, PF_MATVEC, bytes_matvec(g, 4), s);
-                launch_stokes_matvec<float>(g, h->lev[0].cd, h->Z[j], h->V[j + 1], s);
+                if ((rc = run_precond<float>(h, prm.precond, h->pf.in, h->Z[j], mp, s))) return rc;
+                {   // the FP64 matvec of the FP32 direction z_j (converted once)
+                    Scope sc(h, PF_CONV, 12.0 * n, s);
+                    launch_convert<float, double>(n, h->Z[j], h->tmp, s);
+                }
+                Scope sc(h, PF_MATVEC, bytes_matvec(g, 8), s);
+                launch_stokes_matvec<double>(g, h->lev[0].cd, h->tmp, h->V[j + 1], s);
             } else {
                 {
                     Scope sc(h, PF_MATVEC, bytes_matvec(g, 8), s);
                     launch_stokes_matvec<double>(g, h->lev[0].cd, h->V[j], h->tmp, s);
                 }
-                apply_precond<double>(h, prm.precond, h->tmp, h->V[j + 1], mp, s);
+                if ((rc = run_precond<double>(h, prm.precond, h->tmp, h->V[j + 1], mp, s))) return rc;
             }
             info.scalar_vcycles += sv;
             CKL();
@@ -791,13 +875,14 @@ int stk_create(int dim, const int* n, double hh, const int* bc, stk_handle** out
     CKC(dalloc(h, &h->bk, ns));
     CKC(dalloc(h, &h->xk, ns));
     CKC(dalloc(h, &h->tmp, ns));
-    CKC(dalloc(h, &h->red, (size_t)RED_BLOCKS * 36));
+    CKC(dalloc(h, &h->red, (size_t)RED_SCRATCH));
     CKC(dalloc(h, &h->dsc, NDSC));
     {
         void* p = nullptr;
         CKC(cudaMallocHost(&p, sizeof(double) * 128));
         h->hpin = static_cast<double*>(p);
     }
+    CKC(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
 #undef CKC
     *out = h;
     return STK_OK;
@@ -806,6 +891,8 @@ int stk_create(int dim, const int* n, double hh, const int* bc, stk_handle** out
 int stk_destroy(stk_handle* h) {
     if (!h) return STK_OK;
     cudaDeviceSynchronize();
+    clear_graphs(h);
+    if (h->cap) cudaStreamDestroy(h->cap);
     for (void* p : h->allocs) cudaFree(p);
     if (h->hpin) cudaFreeHost(h->hpin);
     for (auto e : h->evpool) cudaEventDestroy(e);
@@ -829,6 +916,7 @@ int stk_set_coefficients(stk_handle* h, const double* rho, const double* mu, dou
     if (h->hpin[1] != 0.0) return fail(h, STK_ERR_ARG, "rho <= 0 or mu < 0 at %g cells", h->hpin[1]);
     bool all_periodic = true;
     for (int a = 0; a < h->dim; ++a) all_periodic = all_periodic && g0.per[a];
+    clear_graphs(h);   // the graphs bake in the Poisson solve (theta != 0) or not
     h->theta = std::isinf(dt) ? 0.0 : 1.0 / dt;
     if (h->theta == 0.0 && all_periodic)
         return fail(h, STK_ERR_ARG, "steady flow on an all-periodic grid (constant-velocity null space) is not supported");
