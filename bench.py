@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--n", type=int, default=0, help="override the grid size")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="profiling runs: only the timed solves of --form, no baseline/e2e/profile passes")
+    ap.add_argument("--form", default="both", choices=["both", "fp64", "mixed"])
     return ap.parse_args()
 
 
@@ -253,6 +256,17 @@ def run_ours(args):
             times.append(e0.elapsed_time(e1))
             infos.append(info)
         return times, infos
+
+    if args.quick:
+        form = S.STK_MIXED if args.form == "mixed" else S.STK_FP64
+        for _ in range(args.warmup):
+            step(form)
+        times, infos = timed(form, args.steps)
+        if rank == 0:
+            print(json.dumps({"quick": True, "form": args.form, "ms": times, "iterations": infos[0]["iterations"],
+                              "true_residual": infos[0]["true_residual"], "config": cfg}))
+        solver.close()
+        return 0
 
     for _ in range(args.warmup):
         step(S.STK_FP64)

@@ -151,6 +151,39 @@ int stk_solve(stk_handle* h, const stk_solver_params* params, const double* cons
               const double* b_p, double* const* x_u, double* x_p, stk_solve_info* info,
               void* stream);
 
+/* Gradient of a loss L(u) of the velocity with respect to the cell
+ * log-viscosity and density, by the adjoint method: given the forward
+ * velocity u (solution of M x = b) and the adjoint velocity lambda (solution
+ * of M^T lambda = (dL/du, 0); M is symmetric, so stk_solve computes it),
+ *   dL/dlog mu_c = mu_c lambda^T (dL_mu/dmu_c) u,
+ *   dL/drho_c    = -theta lambda^T (d rho_f/d rho_c) u,
+ * for the stress-form L_mu of Eq. div_stress (edge viscosities are the mean
+ * of the surrounding in-domain cells, face densities the mean of the two
+ * adjacent cells, Sec. 3.1) with the coefficients last set on h.  u, lambda:
+ * face arrays; dL_dlogmu, dL_drho: cell arrays (written). */
+int stk_gradient(stk_handle* h, const double* const* u, const double* const* lambda,
+                 double* dL_dlogmu, double* dL_drho, void* stream);
+
+/* Batched solve: count independent systems, each on its own handle (any
+ * grid size, boundary conditions and coefficients), solved together with
+ * the same parameters.  The GMRES iterations of all instances advance in
+ * lockstep (one host synchronisation per Arnoldi step for the whole batch)
+ * and each instance's kernels and preconditioner graphs run on its handle's
+ * own stream, forked from and joined back into `stream`, so the instances
+ * share the GPU.  io[i] holds instance i's right-hand side and its initial
+ * guess / solution (layouts as in stk_solve); infos (may be NULL) receives
+ * count records.  A handle may appear once per batch.  Returns STK_OK when
+ * every instance converged, else the first error (STK_ERR_NOT_CONVERGED when
+ * that is the only kind). */
+typedef struct {
+    const double* const* b_u;
+    const double* b_p;
+    double* const* x_u;
+    double* x_p;
+} stk_batch_io;
+int stk_solve_batched(int count, stk_handle* const* hs, const stk_solver_params* params,
+                      const stk_batch_io* io, stk_solve_info* infos, void* stream);
+
 /* Per-kernel timing of the calls above with CUDA events on the call's
  * stream.  stk_profile(h, 1) starts collecting (and clears), 0 stops.
  * stk_profile_read returns, for kernel family k (0 <= k < STK_NPROF), its

@@ -13,6 +13,29 @@ namespace stk {
 
 constexpr int PERIODIC = 0, NOSLIP = 1, FREESLIP = 2;
 
+// Division by a run-time constant d >= 1 for 0 <= n < 2^31 (Granlund &
+// Montgomery, round-up multiplier): n / d = (n * m) >> s.
+struct FDiv {
+    unsigned long long m;
+    int s;
+};
+inline FDiv make_fdiv(int d) {
+    FDiv f;
+    if (d <= 1) {
+        f.m = 1;
+        f.s = 0;
+        return f;
+    }
+    int l = 0;
+    while ((1LL << l) < d) ++l;
+    f.s = 32 + l;
+    f.m = (unsigned long long)(((unsigned __int128)1 << f.s) / (unsigned)d) + 1;
+    return f;
+}
+__host__ __device__ __forceinline__ int fdiv(int n, const FDiv& f) {
+    return (int)(((unsigned long long)(unsigned)n * f.m) >> f.s);
+}
+
 struct Geom {
     int dim;
     int n[3];        // cells per axis (n[2] = 1 in 2D)
@@ -27,7 +50,25 @@ struct Geom {
     int nvel;        // length of a packed velocity vector
     int ncell;
     double h, ih, ih2;
+    float ihf, ih2f;   // the same in FP32 (no FP64 conversion in FP32 kernels)
+    // fast divisors: face extents fe[a][0], fe[a][1]; the colour row length
+    // (fe[a][0]+1)/2; cell extents n[0], n[1]; the cell colour row n[0]/2
+    FDiv fd_e0[3], fd_e1[3], fd_h0[3], fd_n0, fd_n1, fd_nh0;
 };
+
+// fill the derived fields of g (call after n, per, fe are set)
+inline void finish_geom(Geom& g) {
+    g.ihf = float(g.ih);
+    g.ih2f = float(g.ih2);
+    for (int a = 0; a < 3; ++a) {
+        g.fd_e0[a] = make_fdiv(g.fe[a][0]);
+        g.fd_e1[a] = make_fdiv(g.fe[a][1]);
+        g.fd_h0[a] = make_fdiv((g.fe[a][0] + 1) / 2);
+    }
+    g.fd_n0 = make_fdiv(g.n[0]);
+    g.fd_n1 = make_fdiv(g.n[1]);
+    g.fd_nh0 = make_fdiv(g.n[0] / 2 > 0 ? g.n[0] / 2 : 1);
+}
 
 // Coefficients of one level (precision T).  alpha = theta rho_f and
 // beta = 1/rho_f (coarsened by face averaging) are packed face vectors with
@@ -85,6 +126,26 @@ template <typename T>
 void launch_cell_prolong_add(const Geom& gc, const T* phi_c, const Geom& gf, T* phi_f,
                              cudaStream_t s);
 
+// All levels from the one given down to the coarsest, in one single-block
+// launch (coarse.cu): L points to nlev device-resident level descriptors.
+template <typename T>
+struct CLevel {
+    Geom g;
+    Coef<T> C;
+    T *phi_u, *rhs_u, *res_u, *phi_p, *rhs_p, *res_p;
+};
+// levels this small run in the coarse kernel: one SM's FP32 rate makes 4096
+// cells (16^3, 64^2) worth it; its FP64 rate (1/152 of about 1.2 TFLOP/s)
+// only 512 (8^3, 16x32)
+constexpr int COARSE_MAX_CELLS_F32 = 4096;
+constexpr int COARSE_MAX_CELLS_F64 = 512;
+template <typename T>
+void launch_coarse_vcycle_vel(int dim, const CLevel<T>* L, int nlev, const T* rhs, T* phi, int nu,
+                              int ncoarse, cudaStream_t s);
+template <typename T>
+void launch_coarse_vcycle_cell(int dim, const CLevel<T>* L, int nlev, const T* rhs, T* phi, int nu,
+                               int ncoarse, cudaStream_t s);
+
 // preconditioner algebra (precision T)
 template <typename T>  // bc = D u + bp
 void launch_div_plus(const Geom& g, const T* u, const T* bp, T* bc, cudaStream_t s);
@@ -104,10 +165,10 @@ constexpr int KRY_BLOCKS = 1216;  // 8 x 152 SMs: grid of the Krylov kernels (kr
 constexpr int RED_SCRATCH = KRY_BLOCKS * 36;   // doubles of reduction scratch
 template <typename T>  // out[0] = sum x  (scratch >= RED_BLOCKS doubles)
 void launch_sum(int n, const T* x, double* scratch, double* out, cudaStream_t s);
-template <typename T>  // x -= (*sum) / n
-void launch_sub_mean(int n, T* x, const double* sum, cudaStream_t s);
-template <typename T>  // out = in - (*sum)/n
-void launch_copy_sub_mean(int n, const T* in, T* out, const double* sum, cudaStream_t s);
+template <typename T>  // x -= (*sum) / n    (sum[1] receives the mean)
+void launch_sub_mean(int n, T* x, double* sum, cudaStream_t s);
+template <typename T>  // out = in - (*sum)/n  (sum[1] receives the mean)
+void launch_copy_sub_mean(int n, const T* in, T* out, double* sum, cudaStream_t s);
 // h[i] = <w, V_i> for i <= j and h[j+1] = <w, w>;  V = array of j+1 device pointers
 void launch_multidot(int n, int j, const double* const* V, const double* w, double* scratch,
                      double* h, cudaStream_t s);
@@ -124,6 +185,9 @@ template <typename T>  // y += a x
 void launch_axpy(int n, T a, const T* x, T* y, cudaStream_t s);
 template <typename TA, typename TB>
 void launch_convert(int n, const TA* a, TB* b, cudaStream_t s);
+// dL/dlog mu and dL/drho (cell arrays) from packed velocities u and lambda
+void launch_gradient(const Geom& g, const double* mu, double theta, const double* u,
+                     const double* lam, double* glogmu, double* grho, cudaStream_t s);
 // out[0] = number of non-finite entries, out[1] = number of entries <= 0
 void launch_check_fields(int n, const double* rho, const double* mu, double* scratch, double* out,
                          cudaStream_t s);

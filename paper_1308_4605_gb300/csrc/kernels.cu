@@ -11,7 +11,7 @@
 // zeros and never written with anything else; face i of component a lies on
 // the low-a side of cell i.  Every stencil below is evaluated only on faces
 // that carry an unknown, so no index ever leaves its array.
-#include "internal.cuh"
+#include "stencil.cuh"
 
 #include <cmath>
 
@@ -19,114 +19,16 @@ namespace stk {
 
 namespace {
 
+using namespace st;
+
 constexpr int TPB = 256;
 
-__host__ __device__ __forceinline__ int wrapm(int i, int n) {
-    return i < 0 ? i + n : (i >= n ? i - n : i);
-}
-__device__ __forceinline__ int fidx(const Geom& g, int a, const int q[3]) {
-    return g.foff[a] + (q[2] * g.fe[a][1] + q[1]) * g.fe[a][0] + q[0];
-}
-__device__ __forceinline__ int cidx(const Geom& g, const int q[3]) {
-    return (q[2] * g.n[1] + q[1]) * g.n[0] + q[0];
-}
-__device__ __forceinline__ int eidx(const Geom& g, int p, const int q[3]) {
-    return (q[2] * g.ee[p][1] + q[1]) * g.ee[p][0] + q[0];
-}
+// plain decode (coefficient set-up only)
 __device__ __forceinline__ void decode(int t, const int e[3], int q[3]) {
     q[0] = t % e[0];
     int r = t / e[0];
     q[1] = r % e[1];
     q[2] = r / e[1];
-}
-__device__ __forceinline__ bool wall_face(const Geom& g, int a, const int q[3]) {
-    return !g.per[a] && (q[a] == 0 || q[a] == g.n[a]);
-}
-__device__ __forceinline__ int step(const Geom& g, int ax, int i, int d) {
-    return g.per[ax] ? wrapm(i + d, g.n[ax]) : i + d;
-}
-
-template <typename T> __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
-
-// (L_mu phi)_A and the diagonal of A at the interior A-face q
-// (Eq. div_stress with the wall closures of Sec. 3.1).  phi is a packed
-// velocity vector of precision TV; arithmetic in T.
-template <int DIM, int A, typename T, typename TV>
-__device__ __forceinline__ T viscous_face(const Geom& g, const Coef<T>& C, const int q[3],
-                                          const TV* __restrict__ phi, T& dsum) {
-    const T ih = T(g.ih), ih2 = T(g.ih2);
-    int qp[3] = {q[0], q[1], q[2]};
-    int qm[3] = {q[0], q[1], q[2]};
-    qp[A] = step(g, A, q[A], 1);
-    qm[A] = step(g, A, q[A], -1);
-    const T pa = T(phi[fidx(g, A, q)]);
-    const T pp = T(phi[fidx(g, A, qp)]);
-    const T pm = T(phi[fidx(g, A, qm)]);
-    // normal stress 2 mu du_A/dx_A at the two cells on either side of the face
-    const T mh = ld(C.mu_c + cidx(g, q));
-    const T ml = ld(C.mu_c + cidx(g, qm));
-    T L = T(2) * ih2 * (mh * (pp - pa) - ml * (pa - pm));
-    dsum = T(2) * ih2 * (mh + ml);
-#pragma unroll
-    for (int B = 0; B < DIM; ++B) {
-        if (B == A) continue;
-        const int P = A + B - 1;   // edge pair index of {A, B}
-        const bool wlo = !g.per[B] && q[B] == 0;
-        const bool whi = !g.per[B] && q[B] == g.n[B] - 1;
-        int qe[3] = {q[0], q[1], q[2]};
-        qe[B] = step(g, B, q[B], 1);
-        const T mlo = ld(C.mu_e[P] + eidx(g, P, q));
-        const T mhi = ld(C.mu_e[P] + eidx(g, P, qe));
-        T dlo, dhi;
-        if (wlo) {
-            dlo = T(2) * pa * ih;          // (phi - 0) / (h/2)
-        } else {
-            int qb[3] = {q[0], q[1], q[2]};
-            qb[B] = step(g, B, q[B], -1);
-            dlo = (pa - T(phi[fidx(g, A, qb)])) * ih;
-        }
-        if (whi) {
-            dhi = T(-2) * pa * ih;
-        } else {
-            dhi = (T(phi[fidx(g, A, qe)]) - pa) * ih;
-        }
-        // d phi_B / dx_A on the two edges: B-faces in A-cells q[A] and q[A]-1
-        int r1[3] = {q[0], q[1], q[2]};
-        int r0[3] = {q[0], q[1], q[2]};
-        r0[A] = qm[A];
-        int r3[3] = {qe[0], qe[1], qe[2]};
-        int r2[3] = {qe[0], qe[1], qe[2]};
-        r2[A] = qm[A];
-        const T xlo = (T(phi[fidx(g, B, r1)]) - T(phi[fidx(g, B, r0)])) * ih;
-        const T xhi = (T(phi[fidx(g, B, r3)]) - T(phi[fidx(g, B, r2)])) * ih;
-        L += ih * (mhi * (dhi + xhi) - mlo * (dlo + xlo));
-        dsum += ih2 * ((whi ? T(2) : T(1)) * mhi + (wlo ? T(2) : T(1)) * mlo);
-    }
-    return L;
-}
-
-// (L_rho phi) at cell q and its diagonal; beta = 0 on wall faces.
-template <int DIM, typename T, typename TV>
-__device__ __forceinline__ T poisson_cell(const Geom& g, const Coef<T>& C, const int q[3],
-                                          const TV* __restrict__ phi, T& diag) {
-    const T ih2 = T(g.ih2);
-    const T pc = T(phi[cidx(g, q)]);
-    T L = T(0);
-    diag = T(0);
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-        int fh[3] = {q[0], q[1], q[2]};
-        fh[a] = g.per[a] ? wrapm(q[a] + 1, g.n[a]) : q[a] + 1;
-        const T bh = ld(C.beta + fidx(g, a, fh));
-        const T bl = ld(C.beta + fidx(g, a, q));
-        int ch[3] = {q[0], q[1], q[2]};
-        int cl[3] = {q[0], q[1], q[2]};
-        ch[a] = g.per[a] ? wrapm(q[a] + 1, g.n[a]) : min(q[a] + 1, g.n[a] - 1);
-        cl[a] = g.per[a] ? wrapm(q[a] - 1, g.n[a]) : max(q[a] - 1, 0);
-        L += ih2 * (bh * (T(phi[cidx(g, ch)]) - pc) - bl * (pc - T(phi[cidx(g, cl)])));
-        diag -= ih2 * (bh + bl);
-    }
-    return L;
 }
 
 // Block ranges: blocks [start[s], start[s+1]) serve segment s.
@@ -167,7 +69,7 @@ __global__ void k_fine_faces(Geom g, const double* __restrict__ rho, double thet
     int a = 0;
     while (a + 1 < g.dim && t >= g.foff[a + 1]) ++a;
     int q[3];
-    decode(t - g.foff[a], g.fe[a], q);
+    decode_face(g, a, t - g.foff[a], q);
     if (wall_face(g, a, q)) {
         alpha[t] = 0.0;
         beta[t] = 0.0;
@@ -226,7 +128,7 @@ __global__ void k_coarsen_faces(Geom gf, Geom gc, const double* __restrict__ af,
     int a = 0;
     while (a + 1 < gc.dim && t >= gc.foff[a + 1]) ++a;
     int Q[3];
-    decode(t - gc.foff[a], gc.fe[a], Q);
+    decode_face(gc, a, t - gc.foff[a], Q);
     double sa = 0.0, sb = 0.0;
     int cnt = 0;
     int tb[2], nt = 0;
@@ -248,7 +150,7 @@ __global__ void k_coarsen_cells(Geom gf, Geom gc, const double* __restrict__ mf,
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= gc.ncell) return;
     int Q[3];
-    decode(t, gc.n, Q);
+    decode_cell(gc, t, Q);
     double s = 0.0;
     int nz = gc.dim == 3 ? 2 : 1;
     for (int dz = 0; dz < nz; ++dz)
@@ -287,7 +189,7 @@ __global__ void k_inverse_diagonals(Geom g, Coef<double> C, Segs sg) {
     int q[3];
     if (s == DIM) {
         if (t >= g.ncell) return;
-        decode(t, g.n, q);
+        decode_cell(g, t, q);
         double d;
         double dummy = 0.0;
         (void)dummy;
@@ -296,17 +198,15 @@ __global__ void k_inverse_diagonals(Geom g, Coef<double> C, Segs sg) {
         return;
     }
     if (t >= g.fsize[s]) return;
-    decode(t, g.fe[s], q);
+    decode_face(g, s, t, q);
     int f = g.foff[s] + t;
     if (wall_face(g, s, q)) {
         C.invd_u[f] = 0.0;
         return;
     }
     double dsum = 0.0;
-    if (s == 0) viscous_face<DIM, 0, double, double>(g, C, q, C.alpha, dsum);
-    else if (s == 1) viscous_face<DIM, 1, double, double>(g, C, q, C.alpha, dsum);
-    else viscous_face<DIM, DIM == 3 ? 2 : 1, double, double>(g, C, q, C.alpha, dsum);
-    double d = C.alpha[f] + dsum;
+    visc_h2_any<DIM, double, double, true>(s, g, C, q, C.alpha, dsum);
+    double d = C.alpha[f] + g.ih2 * dsum;
     C.invd_u[f] = d != 0.0 ? 1.0 / d : 0.0;
 }
 
@@ -328,7 +228,7 @@ __global__ void k_stokes_matvec(Geom g, Coef<double> C, Segs sg, const TV* __res
     const TV* xp = x + g.nvel;
     if (s == DIM) {
         if (t >= g.ncell) return;
-        decode(t, g.n, q);
+        decode_cell(g, t, q);
         double div = 0.0;
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
@@ -341,20 +241,19 @@ __global__ void k_stokes_matvec(Geom g, Coef<double> C, Segs sg, const TV* __res
         return;
     }
     if (t >= g.fsize[s]) return;
-    decode(t, g.fe[s], q);
+    decode_face(g, s, t, q);
     int f = g.foff[s] + t;
     if (wall_face(g, s, q)) {
         y[f] = 0.0;
         return;
     }
-    double dsum, L;
-    if (s == 0) L = viscous_face<DIM, 0, double, TV>(g, C, q, x, dsum);
-    else if (s == 1) L = viscous_face<DIM, 1, double, TV>(g, C, q, x, dsum);
-    else L = viscous_face<DIM, DIM == 3 ? 2 : 1, double, TV>(g, C, q, x, dsum);
+    double dsum;
+    const double L = visc_h2_any<DIM, double, TV, false>(s, g, C, q, x, dsum);
     int qm[3] = {q[0], q[1], q[2]};
     qm[s] = step(g, s, q[s], -1);
-    double grad = (double(xp[cidx(g, q)]) - double(xp[cidx(g, qm)])) * g.ih;
-    double Mx = ld(C.alpha + f) * double(x[f]) - L + grad;
+    double Mx = g.ih * (double(xp[cidx(g, q)]) - double(xp[cidx(g, qm)]));
+    Mx = fma(-g.ih2, L, Mx);
+    Mx = fma(ld(C.alpha + f), double(x[f]), Mx);
     y[f] = b ? b[f] - Mx : Mx;
 }
 
@@ -362,199 +261,102 @@ __global__ void k_stokes_matvec(Geom g, Coef<double> C, Segs sg, const TV* __res
 // One colour of the staggered Gauss-Seidel smoother (App. C): every A-face
 // with (i + j + k) % 2 == parity gets phi += D^{-1} (rhs - A phi).
 template <int DIM, int A, typename T>
-__global__ void k_vel_gs(Geom g, Coef<T> C, int parity, T* __restrict__ phi,
-                         const T* __restrict__ rhs) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int e0 = g.fe[A][0];
-    const int half = (e0 + 1) >> 1;
-    if (t >= half * g.fe[A][1] * g.fe[A][2]) return;
+__global__ void __launch_bounds__(TPB) k_vel_gs(Geom g, Coef<T> C, int parity, T* __restrict__ phi,
+                                                const T* __restrict__ rhs, int nthreads) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nthreads) return;
     int q[3];
-    q[0] = t % half;
-    int r = t / half;
-    q[1] = r % g.fe[A][1];
-    q[2] = r / g.fe[A][1];
-    q[0] = 2 * q[0] + ((q[1] + q[2] + parity) & 1);
-    if (q[0] >= e0 || wall_face(g, A, q)) return;
-    T dsum;
-    T L = viscous_face<DIM, A, T, T>(g, C, q, phi, dsum);
-    int f = fidx(g, A, q);
-    T p = phi[f];
-    T res = rhs[f] - (ld(C.alpha + f) * p - L);
-    phi[f] = p + res * ld(C.invd_u + f);
+    if (!decode_face_colour(g, A, parity, t, q) || wall_face(g, A, q)) return;
+    vel_gs_point<DIM, A, T>(g, C, q, phi, rhs);
 }
 
 template <int DIM, typename T>
-__global__ void k_vel_residual(Geom g, Coef<T> C, Segs sg, const T* __restrict__ phi,
-                               const T* __restrict__ rhs, T* __restrict__ res) {
+__global__ void __launch_bounds__(TPB) k_vel_residual(Geom g, Coef<T> C, Segs sg,
+                                                      const T* __restrict__ phi,
+                                                      const T* __restrict__ rhs, T* __restrict__ res) {
     int t;
-    int s = seg_of(sg, blockIdx.x, t);
+    const int s = seg_of(sg, blockIdx.x, t);
     if (t >= g.fsize[s]) return;
     int q[3];
-    decode(t, g.fe[s], q);
-    int f = g.foff[s] + t;
-    if (wall_face(g, s, q)) {
-        res[f] = T(0);
-        return;
-    }
-    T dsum, L;
-    if (s == 0) L = viscous_face<DIM, 0, T, T>(g, C, q, phi, dsum);
-    else if (s == 1) L = viscous_face<DIM, 1, T, T>(g, C, q, phi, dsum);
-    else L = viscous_face<DIM, DIM == 3 ? 2 : 1, T, T>(g, C, q, phi, dsum);
-    res[f] = rhs[f] - (ld(C.alpha + f) * phi[f] - L);
+    decode_face(g, s, t, q);
+    const int f = g.foff[s] + t;
+    res[f] = wall_face(g, s, q) ? T(0) : vel_res_point<DIM, T>(s, g, C, q, phi, rhs);
 }
 
-// 6-point (2D) / 12-point (3D) face restriction (App. C).
 template <int DIM, typename T>
-__global__ void k_vel_restrict(Geom gf, Geom gc, Segs sg, const T* __restrict__ res,
-                               T* __restrict__ rc) {
+__global__ void __launch_bounds__(TPB) k_vel_restrict(Geom gf, Geom gc, Segs sg,
+                                                      const T* __restrict__ res, T* __restrict__ rc) {
     int t;
-    int a = seg_of(sg, blockIdx.x, t);
+    const int a = seg_of(sg, blockIdx.x, t);
     if (t >= gc.fsize[a]) return;
     int Q[3];
-    decode(t, gc.fe[a], Q);
-    int f = gc.foff[a] + t;
-    if (wall_face(gc, a, Q)) {
-        rc[f] = T(0);
-        return;
+    decode_face(gc, a, t, Q);
+    const int f = gc.foff[a] + t;
+    T v = T(0);
+    if (!wall_face(gc, a, Q)) {
+        if (a == 0) v = vel_restrict_point<DIM, 0, T>(gf, Q, res);
+        else if (a == 1) v = vel_restrict_point<DIM, 1, T>(gf, Q, res);
+        else v = vel_restrict_point<DIM, DIM == 3 ? 2 : 1, T>(gf, Q, res);
     }
-    int tb[2], nt = 0;
-    for (int b = 0; b < DIM; ++b)
-        if (b != a) tb[nt++] = b;
-    const T wt = DIM == 3 ? T(0.25) : T(0.5);
-    T acc = T(0);
-    for (int s = -1; s <= 1; ++s) {
-        T w = (s == 0 ? T(0.5) : T(0.25)) * wt;
-        for (int m = 0; m < (1 << nt); ++m) {
-            int q[3] = {2 * Q[0], 2 * Q[1], DIM == 3 ? 2 * Q[2] : 0};
-            q[a] = step(gf, a, q[a], s);
-            for (int k = 0; k < nt; ++k) q[tb[k]] += (m >> k) & 1;
-            acc += w * res[fidx(gf, a, q)];
-        }
-    }
-    rc[f] = acc;
+    rc[f] = v;
 }
 
-// Face prolongation and correction phi_f += P phi_c (App. C): along the face
-// normal the coarse face (even index) or the mean of the two coarse faces
-// (odd index); across, 3/4 on the own coarse cell and 1/4 on the nearer
-// neighbour, whose ghost across a wall is -phi (no-slip) or +phi (free-slip).
 template <int DIM, typename T>
-__global__ void k_vel_prolong_add(Geom gc, Geom gf, Segs sg, const T* __restrict__ pc,
-                                  T* __restrict__ pf) {
+__global__ void __launch_bounds__(TPB) k_vel_prolong_add(Geom gc, Geom gf, Segs sg,
+                                                         const T* __restrict__ pc,
+                                                         T* __restrict__ pf) {
     int t;
-    int a = seg_of(sg, blockIdx.x, t);
+    const int a = seg_of(sg, blockIdx.x, t);
     if (t >= gf.fsize[a]) return;
     int q[3];
-    decode(t, gf.fe[a], q);
+    decode_face(gf, a, t, q);
     if (wall_face(gf, a, q)) return;
-    int ca[2];
-    T wa[2];
-    int na;
-    if ((q[a] & 1) == 0) {
-        ca[0] = q[a] >> 1;
-        wa[0] = T(1);
-        na = 1;
-    } else {
-        ca[0] = q[a] >> 1;
-        ca[1] = (q[a] + 1) >> 1;
-        if (gc.per[a] && ca[1] >= gc.n[a]) ca[1] -= gc.n[a];
-        wa[0] = wa[1] = T(0.5);
-        na = 2;
-    }
-    int tb[2], nt = 0;
-    for (int b = 0; b < DIM; ++b)
-        if (b != a) tb[nt++] = b;
-    int cj[2][2];
-    T wj[2][2];
-    for (int k = 0; k < nt; ++k) {
-        int b = tb[k];
-        int j = q[b];
-        int J = j >> 1;
-        int nb = (j & 1) ? J + 1 : J - 1;
-        T wo = T(0.75), wn = T(0.25);
-        if (nb < 0 || nb >= gc.n[b]) {
-            if (gc.per[b]) {
-                nb = wrapm(nb, gc.n[b]);
-            } else {
-                int code = nb < 0 ? gc.bclo[b] : gc.bchi[b];
-                wo += code == NOSLIP ? T(-0.25) : T(0.25);
-                wn = T(0);
-                nb = J;
-            }
-        }
-        cj[k][0] = J;
-        wj[k][0] = wo;
-        cj[k][1] = nb;
-        wj[k][1] = wn;
-    }
-    T acc = T(0);
-    for (int ia = 0; ia < na; ++ia)
-        for (int m = 0; m < (1 << nt); ++m) {
-            int Q[3] = {0, 0, 0};
-            Q[a] = ca[ia];
-            T w = wa[ia];
-            for (int k = 0; k < nt; ++k) {
-                int sel = (m >> k) & 1;
-                Q[tb[k]] = cj[k][sel];
-                w *= wj[k][sel];
-            }
-            if (w != T(0)) acc += w * pc[fidx(gc, a, Q)];
-        }
-    pf[gf.foff[a] + t] += acc;
+    T v;
+    if (a == 0) v = vel_prolong_point<DIM, 0, T>(gc, q, pc);
+    else if (a == 1) v = vel_prolong_point<DIM, 1, T>(gc, q, pc);
+    else v = vel_prolong_point<DIM, DIM == 3 ? 2 : 1, T>(gc, q, pc);
+    pf[gf.foff[a] + t] += v;
 }
 
 // Red-black Gauss-Seidel colour for L_rho phi = rhs (App. C).
 template <int DIM, typename T>
-__global__ void k_cell_gs(Geom g, Coef<T> C, int parity, T* __restrict__ phi,
-                          const T* __restrict__ rhs) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int half = g.n[0] >> 1;
-    if (t >= half * g.n[1] * g.n[2]) return;
+__global__ void __launch_bounds__(TPB) k_cell_gs(Geom g, Coef<T> C, int parity, T* __restrict__ phi,
+                                                 const T* __restrict__ rhs, int nthreads) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nthreads) return;
     int q[3];
-    q[0] = t % half;
-    int r = t / half;
-    q[1] = r % g.n[1];
-    q[2] = r / g.n[1];
-    q[0] = 2 * q[0] + ((q[1] + q[2] + parity) & 1);
-    T d;
-    T L = poisson_cell<DIM, T, T>(g, C, q, phi, d);
-    int c = cidx(g, q);
-    phi[c] += (rhs[c] - L) * ld(C.invd_p + c);
+    decode_cell_colour(g, parity, t, q);
+    cell_gs_point<DIM, T>(g, C, q, phi, rhs);
 }
 
 template <int DIM, typename T>
-__global__ void k_cell_residual(Geom g, Coef<T> C, const T* __restrict__ phi,
-                                const T* __restrict__ rhs, T* __restrict__ res) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(TPB) k_cell_residual(Geom g, Coef<T> C, const T* __restrict__ phi,
+                                                       const T* __restrict__ rhs, T* __restrict__ res) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.ncell) return;
     int q[3];
-    decode(t, g.n, q);
+    decode_cell(g, t, q);
     T d;
     res[t] = rhs[t] - poisson_cell<DIM, T, T>(g, C, q, phi, d);
 }
 
 template <int DIM, typename T>
-__global__ void k_cell_restrict(Geom gf, Geom gc, const T* __restrict__ res, T* __restrict__ rc) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(TPB) k_cell_restrict(Geom gf, Geom gc, const T* __restrict__ res,
+                                                       T* __restrict__ rc) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= gc.ncell) return;
     int Q[3];
-    decode(t, gc.n, Q);
-    T s = T(0);
-    for (int dz = 0; dz < (DIM == 3 ? 2 : 1); ++dz)
-        for (int dy = 0; dy < 2; ++dy)
-            for (int dx = 0; dx < 2; ++dx) {
-                int q[3] = {2 * Q[0] + dx, 2 * Q[1] + dy, (DIM == 3 ? 2 * Q[2] : 0) + dz};
-                s += res[cidx(gf, q)];
-            }
-    rc[t] = s * (DIM == 3 ? T(0.125) : T(0.25));
+    decode_cell(gc, t, Q);
+    rc[t] = cell_restrict_point<DIM, T>(gf, Q, res);
 }
 
 template <int DIM, typename T>
-__global__ void k_cell_prolong_add(Geom gc, Geom gf, const T* __restrict__ pc, T* __restrict__ pf) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(TPB) k_cell_prolong_add(Geom gc, Geom gf, const T* __restrict__ pc,
+                                                          T* __restrict__ pf) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= gf.ncell) return;
     int q[3];
-    decode(t, gf.n, q);
+    decode_cell(gf, t, q);
     int Q[3] = {q[0] >> 1, q[1] >> 1, DIM == 3 ? q[2] >> 1 : 0};
     pf[t] += pc[cidx(gc, Q)];
 }
@@ -566,13 +368,13 @@ __global__ void k_div_plus(Geom g, const T* __restrict__ u, const T* __restrict_
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.ncell) return;
     int q[3];
-    decode(t, g.n, q);
+    decode_cell(g, t, q);
     T div = T(0);
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
         int qh[3] = {q[0], q[1], q[2]};
         qh[a] = step(g, a, q[a], 1);
-        div += (u[fidx(g, a, qh)] - u[fidx(g, a, q)]) * T(g.ih);
+        div += (u[fidx(g, a, qh)] - u[fidx(g, a, q)]) * gih<T>(g);
     }
     bc[t] = div + (bp ? bp[t] : T(0));
 }
@@ -584,7 +386,7 @@ __global__ void k_sub_grad(Geom g, Segs sg, const T* __restrict__ beta, const T*
     int a = seg_of(sg, blockIdx.x, t);
     if (t >= g.fsize[a]) return;
     int q[3];
-    decode(t, g.fe[a], q);
+    decode_face(g, a, t, q);
     int f = g.foff[a] + t;
     if (wall_face(g, a, q)) {
         out[f] = T(0);
@@ -592,7 +394,7 @@ __global__ void k_sub_grad(Geom g, Segs sg, const T* __restrict__ beta, const T*
     }
     int qm[3] = {q[0], q[1], q[2]};
     qm[a] = step(g, a, q[a], -1);
-    T grad = (p[cidx(g, q)] - p[cidx(g, qm)]) * T(g.ih);
+    T grad = (p[cidx(g, q)] - p[cidx(g, qm)]) * gih<T>(g);
     out[f] = u[f] - (beta ? beta[f] : T(1)) * grad;
 }
 
@@ -604,20 +406,18 @@ __global__ void k_vel_correction_rhs(Geom g, Coef<T> C, Segs sg, const T* __rest
     int s = seg_of(sg, blockIdx.x, t);
     if (t >= g.fsize[s]) return;
     int q[3];
-    decode(t, g.fe[s], q);
+    decode_face(g, s, t, q);
     int f = g.foff[s] + t;
     if (wall_face(g, s, q)) {
         out[f] = T(0);
         return;
     }
-    T dsum, L;
-    if (s == 0) L = viscous_face<DIM, 0, T, T>(g, C, q, u, dsum);
-    else if (s == 1) L = viscous_face<DIM, 1, T, T>(g, C, q, u, dsum);
-    else L = viscous_face<DIM, DIM == 3 ? 2 : 1, T, T>(g, C, q, u, dsum);
+    T dsum;
+    const T L = visc_h2_any<DIM, T, T, false>(s, g, C, q, u, dsum);
     int qm[3] = {q[0], q[1], q[2]};
     qm[s] = step(g, s, q[s], -1);
-    T grad = (p[cidx(g, q)] - p[cidx(g, qm)]) * T(g.ih);
-    out[f] = b[f] - grad - (ld(C.alpha + f) * u[f] - L);
+    T grad = (p[cidx(g, q)] - p[cidx(g, qm)]) * gih<T>(g);
+    out[f] = b[f] - grad - fma(ld(C.alpha + f), u[f], -gih2<T>(g) * L);
 }
 
 template <typename T>
@@ -629,6 +429,87 @@ __global__ void k_schur_combine(int n, double theta, const T* __restrict__ phi,
     T v = -T(2) * mu[t] * bc[t];
     if (phi) v += T(theta) * phi[t];
     xp[t] = v;
+}
+
+// --------------------------------------------------------- adjoint gradient
+// Strain rate dv_a/dx_b + dv_b/dx_a (times h) on the (a, b) edge at position e,
+// with the one-sided no-slip wall derivative (v_first - 0)/(h/2) (Sec. 3.1).
+template <typename TV>
+__device__ __forceinline__ double edge_rate_h(const Geom& g, int a, int b, const int e[3],
+                                              const TV* v) {
+    double r = 0.0;
+    const int ab[2][2] = {{a, b}, {b, a}};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int c = ab[k][0], d = ab[k][1];   // d v_c / d x_d
+        if (!g.per[c] && (e[c] == 0 || e[c] == g.n[c])) continue;   // v_c faces on a c-wall are 0
+        int f[3] = {e[0], e[1], e[2]};
+        if (!g.per[d] && e[d] == 0) {
+            r += 2.0 * double(v[fidx(g, c, f)]);
+        } else if (!g.per[d] && e[d] == g.n[d]) {
+            f[d] = e[d] - 1;
+            r -= 2.0 * double(v[fidx(g, c, f)]);
+        } else {
+            int fm[3] = {e[0], e[1], e[2]};
+            f[d] = g.per[d] ? wrapm(e[d], g.n[d]) : e[d];
+            fm[d] = step(g, d, e[d], -1);
+            r += double(v[fidx(g, c, f)]) - double(v[fidx(g, c, fm)]);
+        }
+    }
+    return r;
+}
+
+// dL/dlog(mu_c) and dL/drho_c from the forward velocity u and the adjoint
+// velocity lambda: dL/dmu_c = lambda^T (dL_mu/dmu_c) u and
+// dL/drho_c = -theta lambda^T (d rho_f/d rho_c) u (M is affine in mu, rho).
+// With the stress form: -2 sum_a (D_a lambda)(D_a u) on the cell, and on each
+// edge around it -(m_e w_e / cnt_e) gamma(lambda) gamma(u), cnt_e the number
+// of in-domain cells around the edge, m_e its free-slip/corner mask, w_e = 1/2
+// on a no-slip wall (the flux across the half cell) and 1 inside.
+template <int DIM>
+__global__ void k_gradient(Geom g, const double* __restrict__ mu, double theta,
+                           const double* __restrict__ u, const double* __restrict__ lam,
+                           double* __restrict__ glogmu, double* __restrict__ grho) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.ncell) return;
+    int q[3];
+    decode_cell(g, t, q);
+    double gm = 0.0, gr = 0.0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        int qh[3] = {q[0], q[1], q[2]};
+        qh[a] = step(g, a, q[a], 1);
+        const int flo = fidx(g, a, q), fhi = fidx(g, a, qh);
+        const double du = u[fhi] - u[flo];
+        const double dl = lam[fhi] - lam[flo];
+        gm -= 2.0 * dl * du * g.ih2;
+        gr -= 0.5 * theta * (lam[flo] * u[flo] + lam[fhi] * u[fhi]);
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
+        for (int b = a + 1; b < DIM; ++b) {
+#pragma unroll
+            for (int sa = 0; sa < 2; ++sa)
+#pragma unroll
+                for (int sb = 0; sb < 2; ++sb) {
+                    int e[3] = {q[0], q[1], q[2]};
+                    e[a] += sa;
+                    e[b] += sb;
+                    const bool wa = !g.per[a] && (e[a] == 0 || e[a] == g.n[a]);
+                    const bool wb = !g.per[b] && (e[b] == 0 || e[b] == g.n[b]);
+                    if (wa && wb) continue;                         // corner edge: unused
+                    if (wa && ((e[a] == 0 ? g.bclo[a] : g.bchi[a]) == FREESLIP)) continue;
+                    if (wb && ((e[b] == 0 ? g.bclo[b] : g.bchi[b]) == FREESLIP)) continue;
+                    if (g.per[a]) e[a] = wrapm(e[a], g.n[a]);
+                    if (g.per[b]) e[b] = wrapm(e[b], g.n[b]);
+                    const double cnt = (wa || wb) ? 2.0 : 4.0;
+                    const double w = (wa || wb) ? 0.5 : 1.0;
+                    gm -= w / cnt * edge_rate_h(g, a, b, e, lam) * edge_rate_h(g, a, b, e, u) * g.ih2;
+                }
+        }
+    glogmu[t] = mu[t] * gm;
+    grho[t] = gr;
 }
 
 // ------------------------------------------------------------------ reductions
@@ -673,17 +554,24 @@ __global__ void k_final(int nk, const double* __restrict__ part, double* out) {
     }
 }
 
+// sum[1] = sum[0] / n, computed once (one FP64 division, not one per thread)
+__global__ void k_mean(int n, double* sum) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) sum[1] = sum[0] / n;
+}
+
 template <typename T>
 __global__ void k_sub_mean(int n, T* x, const double* __restrict__ sum) {
+    const T m = T(sum[1]);
     int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n) x[t] -= T(*sum / n);
+    if (t < n) x[t] -= m;
 }
 
 template <typename T>
 __global__ void k_copy_sub_mean(int n, const T* __restrict__ in, T* out,
                                 const double* __restrict__ sum) {
+    const T m = T(sum[1]);
     int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n) out[t] = in[t] - T(*sum / n);
+    if (t < n) out[t] = in[t] - m;
 }
 
 template <typename T>
@@ -773,15 +661,15 @@ void launch_stokes_residual(const Geom& g, Coef<double> C, const double* x, cons
 template <typename T>
 void launch_vel_gs_colour(const Geom& g, Coef<T> C, int comp, int parity, T* phi, const T* rhs,
                           cudaStream_t s) {
-    int nthreads = ((g.fe[comp][0] + 1) / 2) * g.fe[comp][1] * g.fe[comp][2];
-    int nb = nblk(nthreads);
+    const int nt = ((g.fe[comp][0] + 1) / 2) * g.fe[comp][1] * g.fe[comp][2];
+    const int nb = nblk(nt);
     if (g.dim == 2) {
-        if (comp == 0) k_vel_gs<2, 0, T><<<nb, TPB, 0, s>>>(g, C, parity, phi, rhs);
-        else k_vel_gs<2, 1, T><<<nb, TPB, 0, s>>>(g, C, parity, phi, rhs);
+        if (comp == 0) k_vel_gs<2, 0, T><<<nb, TPB, 0, s>>>(g, C, parity, phi, rhs, nt);
+        else k_vel_gs<2, 1, T><<<nb, TPB, 0, s>>>(g, C, parity, phi, rhs, nt);
     } else {
-        if (comp == 0) k_vel_gs<3, 0, T><<<nb, TPB, 0, s>>>(g, C, parity, phi, rhs);
-        else if (comp == 1) k_vel_gs<3, 1, T><<<nb, TPB, 0, s>>>(g, C, parity, phi, rhs);
-        else k_vel_gs<3, 2, T><<<nb, TPB, 0, s>>>(g, C, parity, phi, rhs);
+        if (comp == 0) k_vel_gs<3, 0, T><<<nb, TPB, 0, s>>>(g, C, parity, phi, rhs, nt);
+        else if (comp == 1) k_vel_gs<3, 1, T><<<nb, TPB, 0, s>>>(g, C, parity, phi, rhs, nt);
+        else k_vel_gs<3, 2, T><<<nb, TPB, 0, s>>>(g, C, parity, phi, rhs, nt);
     }
 }
 
@@ -810,9 +698,10 @@ void launch_vel_prolong_add(const Geom& gc, const T* pc, const Geom& gf, T* pf, 
 template <typename T>
 void launch_cell_gs_colour(const Geom& g, Coef<T> C, int parity, T* phi, const T* rhs,
                            cudaStream_t s) {
-    int nb = nblk((g.n[0] / 2) * g.n[1] * g.n[2]);
-    if (g.dim == 2) k_cell_gs<2, T><<<nb, TPB, 0, s>>>(g, C, parity, phi, rhs);
-    else k_cell_gs<3, T><<<nb, TPB, 0, s>>>(g, C, parity, phi, rhs);
+    const int nt = (g.n[0] / 2) * g.n[1] * g.n[2];
+    const int nb = nblk(nt);
+    if (g.dim == 2) k_cell_gs<2, T><<<nb, TPB, 0, s>>>(g, C, parity, phi, rhs, nt);
+    else k_cell_gs<3, T><<<nb, TPB, 0, s>>>(g, C, parity, phi, rhs, nt);
 }
 
 template <typename T>
@@ -870,18 +759,26 @@ void launch_sum(int n, const T* x, double* scratch, double* out, cudaStream_t s)
 }
 
 template <typename T>
-void launch_sub_mean(int n, T* x, const double* sum, cudaStream_t s) {
+void launch_sub_mean(int n, T* x, double* sum, cudaStream_t s) {
+    k_mean<<<1, 32, 0, s>>>(n, sum);
     k_sub_mean<T><<<nblk(n), TPB, 0, s>>>(n, x, sum);
 }
 
 template <typename T>
-void launch_copy_sub_mean(int n, const T* in, T* out, const double* sum, cudaStream_t s) {
+void launch_copy_sub_mean(int n, const T* in, T* out, double* sum, cudaStream_t s) {
+    k_mean<<<1, 32, 0, s>>>(n, sum);
     k_copy_sub_mean<T><<<nblk(n), TPB, 0, s>>>(n, in, out, sum);
 }
 
 template <typename T>
 void launch_axpy(int n, T a, const T* x, T* y, cudaStream_t s) {
     k_axpy<T><<<nblk(n), TPB, 0, s>>>(n, a, x, y);
+}
+
+void launch_gradient(const Geom& g, const double* mu, double theta, const double* u,
+                     const double* lam, double* glogmu, double* grho, cudaStream_t s) {
+    if (g.dim == 2) k_gradient<2><<<nblk(g.ncell), TPB, 0, s>>>(g, mu, theta, u, lam, glogmu, grho);
+    else k_gradient<3><<<nblk(g.ncell), TPB, 0, s>>>(g, mu, theta, u, lam, glogmu, grho);
 }
 
 void launch_check_fields(int n, const double* rho, const double* mu, double* scratch, double* out,
@@ -914,8 +811,8 @@ void launch_check_fields(int n, const double* rho, const double* mu, double* scr
     template void launch_schur_combine<T>(int, double, const T*, const T*, const T*, T*,         \
                                           cudaStream_t);                                           \
     template void launch_sum<T>(int, const T*, double*, double*, cudaStream_t);                  \
-    template void launch_sub_mean<T>(int, T*, const double*, cudaStream_t);                      \
-    template void launch_copy_sub_mean<T>(int, const T*, T*, const double*, cudaStream_t);       \
+    template void launch_sub_mean<T>(int, T*, double*, cudaStream_t);                            \
+    template void launch_copy_sub_mean<T>(int, const T*, T*, double*, cudaStream_t);             \
     template void launch_stokes_matvec<T>(const Geom&, Coef<double>, const T*, double*,          \
                                           cudaStream_t);                                           \
     template void launch_axpy<T>(int, T, const T*, T*, cudaStream_t);

@@ -130,6 +130,7 @@ Geom na_geom(int dim, const int n[3], double hh, const int bc[6]) {
     g.h = hh;
     g.ih = 1.0 / hh;
     g.ih2 = 1.0 / (hh * hh);
+    stk::finish_geom(g);
     return g;
 }
 

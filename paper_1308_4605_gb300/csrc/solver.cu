@@ -32,11 +32,11 @@ const char* kProfNames[STK_NPROF] = {
     "stokes_matvec",    "vel_smooth_colour", "vel_residual",  "vel_restrict",
     "vel_prolong_add",  "cell_smooth_colour", "cell_residual", "cell_restrict",
     "cell_prolong_add", "precond_algebra",   "mean_removal",  "arnoldi_multidot",
-    "arnoldi_update",   "krylov_combine",    "convert",       "other"};
+    "arnoldi_update",   "krylov_combine",    "convert",       "coarse_levels"};
 
 enum {
     PF_MATVEC = 0, PF_VSMOOTH, PF_VRES, PF_VRESTR, PF_VPROL, PF_CSMOOTH, PF_CRES, PF_CRESTR,
-    PF_CPROL, PF_ALG, PF_MEAN, PF_MDOT, PF_UPD, PF_COMB, PF_CONV, PF_OTHER
+    PF_CPROL, PF_ALG, PF_MEAN, PF_MDOT, PF_UPD, PF_COMB, PF_CONV, PF_COARSE
 };
 
 template <typename T>
@@ -76,6 +76,9 @@ struct stk_handle {
     std::vector<double*> V;
     std::vector<float*> Z;
     double *bk = nullptr, *xk = nullptr, *tmp = nullptr;
+    int lcoarse_d = 0, lcoarse_f = 0;        // first level run by the coarse kernel (FP64, FP32)
+    CLevel<double>* cld = nullptr;           // device copies of the level descriptors
+    CLevel<float>* clf = nullptr;
     double* red = nullptr;    // reduction scratch (RED_BLOCKS * 36 doubles)
     double* dsc = nullptr;    // device scalars
     double* hpin = nullptr;   // pinned host staging
@@ -94,6 +97,8 @@ struct stk_handle {
     long long cap_kernels = 0;
     std::vector<ProfRec> caprecs;
     cudaStream_t cap = nullptr;    // private stream used for capture only
+    cudaStream_t run = nullptr;    // this handle's stream inside a batched solve
+    cudaEvent_t join = nullptr;    // marks the end of its work in a batched solve
     std::vector<ProfRec> recs;
     std::vector<cudaEvent_t> evpool;
     size_t evnext = 0;
@@ -172,6 +177,7 @@ Geom make_geom(int dim, const int n[3], double hh, const int bc[6]) {
     g.h = hh;
     g.ih = 1.0 / hh;
     g.ih2 = 1.0 / (hh * hh);
+    stk::finish_geom(g);
     return g;
 }
 
@@ -261,6 +267,12 @@ template <> Coef<float> coef_of<float>(const Level& L) { return L.cf; }
 template <typename T> Work<T> work_of(const Level& L);
 template <> Work<double> work_of<double>(const Level& L) { return L.wd; }
 template <> Work<float> work_of<float>(const Level& L) { return L.wf; }
+template <typename T> int lcoarse_of(const stk_handle* h) {
+    return sizeof(T) == 8 ? h->lcoarse_d : h->lcoarse_f;
+}
+template <typename T> const CLevel<T>* clev_of(const stk_handle* h);
+template <> const CLevel<double>* clev_of<double>(const stk_handle* h) { return h->cld; }
+template <> const CLevel<float>* clev_of<float>(const stk_handle* h) { return h->clf; }
 template <typename T> PBuf<T>& pbuf_of(stk_handle* h);
 template <> PBuf<double>& pbuf_of<double>(stk_handle* h) { return h->pd; }
 template <> PBuf<float>& pbuf_of<float>(stk_handle* h) { return h->pf; }
@@ -297,6 +309,12 @@ template <typename T>
 void vcycle_vel(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp, cudaStream_t s) {
     const Level& L = h->lev[l];
     Work<T> W = work_of<T>(L);
+    if (l >= lcoarse_of<T>(h)) {   // this level and all coarser ones in one launch
+        Scope sc(h, PF_COARSE, 0.0, s);
+        launch_coarse_vcycle_vel<T>(L.g.dim, clev_of<T>(h) + l, (int)h->lev.size() - l, rhs, phi,
+                                    mp.nu, mp.ncoarse, s);
+        return;
+    }
     cudaMemsetAsync(phi, 0, sizeof(T) * L.g.nvel, s);
     if (l + 1 == (int)h->lev.size()) {
         vel_sweeps<T>(h, L, mp.ncoarse, phi, rhs, s);
@@ -326,6 +344,12 @@ template <typename T>
 void vcycle_cell(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp, cudaStream_t s) {
     const Level& L = h->lev[l];
     Work<T> W = work_of<T>(L);
+    if (l >= lcoarse_of<T>(h)) {
+        Scope sc(h, PF_COARSE, 0.0, s);
+        launch_coarse_vcycle_cell<T>(L.g.dim, clev_of<T>(h) + l, (int)h->lev.size() - l, rhs, phi,
+                                     mp.nu, mp.ncoarse, s);
+        return;
+    }
     cudaMemsetAsync(phi, 0, sizeof(T) * L.g.ncell, s);
     if (l + 1 == (int)h->lev.size()) {
         cell_sweeps<T>(h, L, mp.ncoarse, phi, rhs, s);
@@ -357,7 +381,7 @@ void poisson_solve(stk_handle* h, const T* r, T* phi, const MGParams& mp, cudaSt
     const Level& L = h->lev[0];
     Work<T> W = work_of<T>(L);
     {
-        Scope sc(h, PF_MEAN, 2.0 * sizeof(T) * L.g.ncell, s, 3);
+        Scope sc(h, PF_MEAN, 2.0 * sizeof(T) * L.g.ncell, s, 4);
         launch_sum<T>(L.g.ncell, r, h->red, h->dsc + DS_SUM, s);
         launch_copy_sub_mean<T>(L.g.ncell, r, W.rhs_p, h->dsc + DS_SUM, s);
     }
@@ -367,9 +391,9 @@ void poisson_solve(stk_handle* h, const T* r, T* phi, const MGParams& mp, cudaSt
 template <typename T>
 void remove_mean(stk_handle* h, T* x, cudaStream_t s) {
     const Level& L = h->lev[0];
-    Scope sc(h, PF_MEAN, 3.0 * sizeof(T) * L.g.ncell, s, 3);
-    launch_sum<T>(L.g.ncell, x, h->red, h->dsc + DS_SUM + 1, s);
-    launch_sub_mean<T>(L.g.ncell, x, h->dsc + DS_SUM + 1, s);
+    Scope sc(h, PF_MEAN, 3.0 * sizeof(T) * L.g.ncell, s, 4);
+    launch_sum<T>(L.g.ncell, x, h->red, h->dsc + DS_SUM + 2, s);
+    launch_sub_mean<T>(L.g.ncell, x, h->dsc + DS_SUM + 2, s);
 }
 
 // x = P^{-1} b, Sec. 2.1-2.4; b, x packed Stokes vectors of precision T.
@@ -579,11 +603,15 @@ struct Arnoldi {
     }
 };
 
-// w (= V[j+1], unnormalised) is orthogonalised against V[0..j] by classical
-// Gram-Schmidt with one selective re-orthogonalisation pass; its norm
-// becomes hcol[j+1] and it is normalised.  hcol[0..j] receive the
-// projections.
-int orthogonalise(stk_handle* h, int j, cudaStream_t s, double* hcol) {
+// ---------------------------------------------------------------- GMRES core
+// Arnoldi step pieces.  w = V[j+1] (unnormalised) is orthogonalised against
+// V[0..j] by classical Gram-Schmidt: one multi-dot pass (which also gives
+// ||w||^2 before) and one update pass (which gives ||w||^2 after); when the
+// norm falls below 1/sqrt(2) of its start a second pass re-orthogonalises.
+// The projections and norms are staged to pinned host memory.
+constexpr int HP_H = 0, HP_AFTER = 40, HP_NRM = 41, HP_H2 = 64, HP_Y = 128;
+
+void orth_enqueue(stk_handle* h, int j, int pass, cudaStream_t s) {
     const int n = nstokes(h);
     double* w = h->V[j + 1];
     std::vector<const double*> Vp(h->V.begin(), h->V.begin() + j + 1);
@@ -596,162 +624,261 @@ int orthogonalise(stk_handle* h, int j, cudaStream_t s, double* hcol) {
         Scope sc(h, PF_UPD, 8.0 * n * (j + 3), s, 2);
         launch_update_norm(n, j, Vp.data(), hd, w, h->red, h->dsc + DS_N2, s);
     }
-    CK(cudaMemcpyAsync(h->hpin, hd, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(h->hpin + 40, h->dsc + DS_N2, sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    for (int i = 0; i <= j; ++i) hcol[i] = h->hpin[i];
-    double before = h->hpin[j + 1];
-    double after = h->hpin[40];
-    if (!(std::isfinite(after) && std::isfinite(before)))
-        return fail(h, STK_ERR_NONFINITE, "non-finite value in the Arnoldi process");
-    if (after < 0.5 * before) {   // lost more than 1 - 1/sqrt(2) of its norm: re-orthogonalise
-        {
-            Scope sc(h, PF_MDOT, 8.0 * n * (j + 2), s, 2);
-            launch_multidot(n, j, Vp.data(), w, h->red, hd, s);
-        }
-        {
-            Scope sc(h, PF_UPD, 8.0 * n * (j + 3), s, 2);
-            launch_update_norm(n, j, Vp.data(), hd, w, h->red, h->dsc + DS_N2, s);
-        }
-        CK(cudaMemcpyAsync(h->hpin, hd, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(h->hpin + 40, h->dsc + DS_N2, sizeof(double), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        for (int i = 0; i <= j; ++i) hcol[i] += h->hpin[i];
-        after = h->hpin[40];
-    }
-    hcol[j + 1] = std::sqrt(after);
-    if (hcol[j + 1] > 0.0) {
-        Scope sc(h, PF_COMB, 16.0 * n, s);
-        launch_scale(n, w, 1.0 / hcol[j + 1], s);
-    }
-    CKL();
-    return STK_OK;
+    cudaMemcpyAsync(h->hpin + (pass ? HP_H2 : HP_H), hd, sizeof(double) * (j + 2),
+                    cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(h->hpin + HP_AFTER, h->dsc + DS_N2, sizeof(double), cudaMemcpyDeviceToHost, s);
 }
 
-int norm2(stk_handle* h, const double* x, int n, cudaStream_t s, double* out) {
-    {
-        Scope sc(h, PF_MDOT, 8.0 * n, s, 2);
-        launch_multidot(n, -1, nullptr, x, h->red, h->dsc + DS_N2 + 1, s);
-    }
-    CK(cudaMemcpyAsync(h->hpin + 41, h->dsc + DS_N2 + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    *out = std::sqrt(h->hpin[41]);
-    return STK_OK;
-}
-
-// Restarted GMRES (Sec. 3.2): left-preconditioned with an FP64 preconditioner
-// (flexible = false) or flexible with an FP32 preconditioner (flexible = true,
-// Sec. 4).  Stopping rule: ||b - M x|| <= rtol ||b||, checked at the start of
-// every cycle; inside a cycle the Arnoldi estimate must fall to rtol ||b||
-// (flexible) or to its initial value times rtol ||b|| / ||b - M x|| (left).
-int gmres(stk_handle* h, const stk_solver_params& prm, stk_solve_info& info, cudaStream_t s) {
-    const Geom& g = h->lev[0].g;
+void norm_enqueue(stk_handle* h, const double* x, cudaStream_t s) {
     const int n = nstokes(h);
+    Scope sc(h, PF_MDOT, 8.0 * n, s, 2);
+    launch_multidot(n, -1, nullptr, x, h->red, h->dsc + DS_N2 + 1, s);
+    cudaMemcpyAsync(h->hpin + HP_NRM, h->dsc + DS_N2 + 1, sizeof(double), cudaMemcpyDeviceToHost, s);
+}
+
+// One GMRES instance advanced in lockstep with others (Sec. 3.2, Sec. 4).
+struct Inst {
+    stk_handle* h = nullptr;
+    cudaStream_t s = nullptr;
+    stk_solve_info info{};
+    int rc = STK_OK;
+    bool done = false;      // solve finished (converged, maxit or error)
+    bool in_cycle = false;  // Arnoldi cycle still running
+    double bnorm = 0, rnorm = 0, beta = 0, target = 0;
+    std::vector<double> hcol, y;
+    Arnoldi ar{1};
+    int k = 0;
+    bool reorth = false;
+};
+
+int sync_all(std::vector<Inst*>& v) {
+    int rc = STK_OK;
+    for (Inst* it : v) {
+        cudaError_t e = cudaStreamSynchronize(it->s);
+        if (e != cudaSuccess && it->rc == STK_OK) {
+            it->rc = fail(it->h, STK_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
+            it->done = true;
+            rc = it->rc;
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess && it->rc == STK_OK) {
+            it->rc = fail(it->h, STK_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+            it->done = true;
+            rc = it->rc;
+        }
+    }
+    return rc;
+}
+
+void finish(Inst* it, int rc) {
+    if (it->rc == STK_OK) it->rc = rc;
+    it->done = true;
+    it->in_cycle = false;
+}
+
+// Restarted GMRES for every instance: left-preconditioned with an FP64
+// preconditioner, or flexible with an FP32 preconditioner (precision MIXED).
+// Stopping rule: ||b - M x|| <= rtol ||b||, checked at the start of every
+// cycle; inside a cycle the Arnoldi estimate must fall to rtol ||b||
+// (flexible) or to its start value times rtol ||b|| / ||b - M x|| (left).
+// Every phase enqueues the work of all active instances on their streams and
+// then synchronises once for all of them.
+void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm) {
     const int m = prm.restart;
     const bool flex = prm.precision == STK_MIXED;
     MGParams mp;
     mp.nu = prm.nu;
     mp.ncoarse = prm.ncoarse;
-    int rc = ensure_krylov(h, m);
-    if (rc) return rc;
-    double bnorm;
-    if ((rc = norm2(h, h->bk, n, s, &bnorm))) return rc;
-    info.iterations = info.restarts = 0;
-    info.scalar_vcycles = 0.0;
-    info.converged = 0;
-    if (!std::isfinite(bnorm)) return fail(h, STK_ERR_NONFINITE, "non-finite right-hand side");
-    if (bnorm == 0.0) {
-        CK(cudaMemsetAsync(h->xk, 0, sizeof(double) * n, s));
-        info.converged = 1;
-        info.true_residual = 0.0;
-        return STK_OK;
+    std::vector<Inst*> act;
+    for (auto& it : insts) {
+        it.hcol.assign(m + 2, 0.0);
+        it.y.assign(m, 0.0);
+        int rc = ensure_krylov(it.h, m);
+        if (rc) { finish(&it, rc); continue; }
+        norm_enqueue(it.h, it.h->bk, it.s);
+        act.push_back(&it);
     }
-    const double sv = scalar_vcycles(h, prm.precond);
-    std::vector<double> hcol(m + 2), y(m);
+    sync_all(act);
+    for (Inst* it : act) {
+        if (it->done) continue;
+        it->bnorm = std::sqrt(it->h->hpin[HP_NRM]);
+        if (!std::isfinite(it->bnorm)) finish(it, fail(it->h, STK_ERR_NONFINITE, "non-finite right-hand side"));
+        else if (it->bnorm == 0.0) {
+            cudaMemsetAsync(it->h->xk, 0, sizeof(double) * nstokes(it->h), it->s);
+            it->info.converged = 1;
+            finish(it, STK_OK);
+        }
+    }
     while (true) {
-        {
-            Scope sc(h, PF_MATVEC, bytes_matvec(g, 8) + 8.0 * n, s);
-            launch_stokes_residual(g, h->lev[0].cd, h->xk, h->bk, h->tmp, s);
+        // cycle start: true residual
+        act.clear();
+        for (auto& it : insts)
+            if (!it.done) act.push_back(&it);
+        if (act.empty()) break;
+        for (Inst* it : act) {
+            stk_handle* h = it->h;
+            const Geom& g = h->lev[0].g;
+            Scope sc(h, PF_MATVEC, bytes_matvec(g, 8) + 8.0 * nstokes(h), it->s);
+            launch_stokes_residual(g, h->lev[0].cd, h->xk, h->bk, h->tmp, it->s);
+            norm_enqueue(h, h->tmp, it->s);
         }
-        CKL();
-        double rnorm;
-        if ((rc = norm2(h, h->tmp, n, s, &rnorm))) return rc;
-        if (!std::isfinite(rnorm)) return fail(h, STK_ERR_NONFINITE, "non-finite residual");
-        info.true_residual = rnorm / bnorm;
-        if (info.true_residual <= prm.rtol) {
-            info.converged = 1;
-            break;
+        sync_all(act);
+        std::vector<Inst*> cyc;
+        for (Inst* it : act) {
+            if (it->done) continue;
+            it->rnorm = std::sqrt(it->h->hpin[HP_NRM]);
+            if (!std::isfinite(it->rnorm)) { finish(it, fail(it->h, STK_ERR_NONFINITE, "non-finite residual")); continue; }
+            it->info.true_residual = it->rnorm / it->bnorm;
+            if (it->info.true_residual <= prm.rtol) { it->info.converged = 1; finish(it, STK_OK); continue; }
+            if (it->info.iterations >= prm.maxit) { finish(it, STK_ERR_NOT_CONVERGED); continue; }
+            cyc.push_back(it);
         }
-        if (info.iterations >= prm.maxit) break;
-        double beta, target;
+        if (cyc.empty()) continue;
+        const double sv_dummy = 0.0;
+        (void)sv_dummy;
         if (flex) {
-            CK(cudaMemcpyAsync(h->V[0], h->tmp, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-            beta = rnorm;
-            target = prm.rtol * bnorm;
-        } else {
-            if ((rc = run_precond<double>(h, prm.precond, h->tmp, h->V[0], mp, s))) return rc;
-            info.scalar_vcycles += sv;
-            if ((rc = norm2(h, h->V[0], n, s, &beta))) return rc;
-            if (!std::isfinite(beta)) return fail(h, STK_ERR_NONFINITE, "non-finite preconditioned residual");
-            target = beta * (prm.rtol * bnorm / rnorm);
-        }
-        if (beta == 0.0) break;
-        {
-            Scope sc(h, PF_COMB, 16.0 * n, s);
-            launch_scale(n, h->V[0], 1.0 / beta, s);
-        }
-        Arnoldi ar(m);
-        ar.g[0] = beta;
-        int k = 0;
-        for (int j = 0; j < m && info.iterations < prm.maxit; ++j) {
-            if (flex) {
-                {
-                    Scope sc(h, PF_CONV, 12.0 * n, s);
-                    launch_convert<double, float>(n, h->V[j], h->pf.in, s);
-                }
-                if ((rc = run_precond<float>(h, prm.precond, h->pf.in, h->Z[j], mp, s))) return rc;
-                {   // the FP64 matvec of the FP32 direction z_j (converted once)
-                    Scope sc(h, PF_CONV, 12.0 * n, s);
-                    launch_convert<float, double>(n, h->Z[j], h->tmp, s);
-                }
-                Scope sc(h, PF_MATVEC, bytes_matvec(g, 8), s);
-                launch_stokes_matvec<double>(g, h->lev[0].cd, h->tmp, h->V[j + 1], s);
-            } else {
-                {
-                    Scope sc(h, PF_MATVEC, bytes_matvec(g, 8), s);
-                    launch_stokes_matvec<double>(g, h->lev[0].cd, h->V[j], h->tmp, s);
-                }
-                if ((rc = run_precond<double>(h, prm.precond, h->tmp, h->V[j + 1], mp, s))) return rc;
+            for (Inst* it : cyc) {
+                cudaMemcpyAsync(it->h->V[0], it->h->tmp, sizeof(double) * nstokes(it->h),
+                                cudaMemcpyDeviceToDevice, it->s);
+                it->beta = it->rnorm;
+                it->target = prm.rtol * it->bnorm;
             }
-            info.scalar_vcycles += sv;
-            CKL();
-            if ((rc = orthogonalise(h, j, s, hcol.data()))) return rc;
-            ++info.iterations;
-            k = j + 1;
-            double est = ar.add_column(j, hcol.data());
-            info.est_residual = est / bnorm;
-            if (est <= target || hcol[j + 1] == 0.0) break;
+        } else {
+            for (Inst* it : cyc) {
+                int rc = run_precond<double>(it->h, prm.precond, it->h->tmp, it->h->V[0], mp, it->s);
+                if (rc) { finish(it, rc); continue; }
+                it->info.scalar_vcycles += scalar_vcycles(it->h, prm.precond);
+                norm_enqueue(it->h, it->h->V[0], it->s);
+            }
+            sync_all(cyc);
+            for (Inst* it : cyc) {
+                if (it->done) continue;
+                it->beta = std::sqrt(it->h->hpin[HP_NRM]);
+                if (!std::isfinite(it->beta)) { finish(it, fail(it->h, STK_ERR_NONFINITE, "non-finite preconditioned residual")); continue; }
+                it->target = it->beta * (prm.rtol * it->bnorm / it->rnorm);
+            }
         }
-        ++info.restarts;
-        ar.solve(k, y.data());
-        for (int i = 0; i < k; ++i)
-            if (!std::isfinite(y[i])) return fail(h, STK_ERR_NONFINITE, "non-finite GMRES update");
-        std::memcpy(h->hpin, y.data(), sizeof(double) * k);
-        CK(cudaMemcpyAsync(h->dsc + DS_Y, h->hpin, sizeof(double) * k, cudaMemcpyHostToDevice, s));
-        {
-            Scope sc(h, PF_COMB, (flex ? 4.0 : 8.0) * n * k + 16.0 * n, s);
+        std::vector<Inst*> run;
+        for (Inst* it : cyc) {
+            if (it->done) continue;
+            if (it->beta == 0.0) { finish(it, it->info.converged ? STK_OK : STK_ERR_NOT_CONVERGED); continue; }
+            Scope sc(it->h, PF_COMB, 16.0 * nstokes(it->h), it->s);
+            launch_scale(nstokes(it->h), it->h->V[0], 1.0 / it->beta, it->s);
+            it->ar = Arnoldi(m);
+            it->ar.g[0] = it->beta;
+            it->k = 0;
+            it->in_cycle = true;
+            run.push_back(it);
+        }
+        for (int j = 0; j < m; ++j) {
+            std::vector<Inst*> step;
+            for (Inst* it : run)
+                if (it->in_cycle && !it->done && it->info.iterations < prm.maxit) step.push_back(it);
+            if (step.empty()) break;
+            for (Inst* it : step) {
+                stk_handle* h = it->h;
+                const Geom& g = h->lev[0].g;
+                const int n = nstokes(h);
+                int rc;
+                if (flex) {
+                    {
+                        Scope sc(h, PF_CONV, 12.0 * n, it->s);
+                        launch_convert<double, float>(n, h->V[j], h->pf.in, it->s);
+                    }
+                    if ((rc = run_precond<float>(h, prm.precond, h->pf.in, h->Z[j], mp, it->s))) { finish(it, rc); continue; }
+                    {   // the FP64 matvec of the FP32 direction z_j (converted once)
+                        Scope sc(h, PF_CONV, 12.0 * n, it->s);
+                        launch_convert<float, double>(n, h->Z[j], h->tmp, it->s);
+                    }
+                    Scope sc(h, PF_MATVEC, bytes_matvec(g, 8), it->s);
+                    launch_stokes_matvec<double>(g, h->lev[0].cd, h->tmp, h->V[j + 1], it->s);
+                } else {
+                    {
+                        Scope sc(h, PF_MATVEC, bytes_matvec(g, 8), it->s);
+                        launch_stokes_matvec<double>(g, h->lev[0].cd, h->V[j], h->tmp, it->s);
+                    }
+                    if ((rc = run_precond<double>(h, prm.precond, h->tmp, h->V[j + 1], mp, it->s))) { finish(it, rc); continue; }
+                }
+                it->info.scalar_vcycles += scalar_vcycles(h, prm.precond);
+                orth_enqueue(h, j, 0, it->s);
+            }
+            sync_all(step);
+            bool any_reorth = false;
+            for (Inst* it : step) {
+                if (it->done) continue;
+                const double* hp = it->h->hpin;
+                for (int i = 0; i <= j; ++i) it->hcol[i] = hp[HP_H + i];
+                const double before = hp[HP_H + j + 1], after = hp[HP_AFTER];
+                if (!(std::isfinite(after) && std::isfinite(before))) {
+                    finish(it, fail(it->h, STK_ERR_NONFINITE, "non-finite value in the Arnoldi process"));
+                    continue;
+                }
+                it->reorth = after < 0.5 * before;
+                if (it->reorth) {
+                    orth_enqueue(it->h, j, 1, it->s);
+                    any_reorth = true;
+                }
+            }
+            if (any_reorth) {
+                sync_all(step);
+                for (Inst* it : step)
+                    if (!it->done && it->reorth)
+                        for (int i = 0; i <= j; ++i) it->hcol[i] += it->h->hpin[HP_H2 + i];
+            }
+            for (Inst* it : step) {
+                if (it->done) continue;
+                stk_handle* h = it->h;
+                const int n = nstokes(h);
+                it->hcol[j + 1] = std::sqrt(h->hpin[HP_AFTER]);
+                if (it->hcol[j + 1] > 0.0) {
+                    Scope sc(h, PF_COMB, 16.0 * n, it->s);
+                    launch_scale(n, h->V[j + 1], 1.0 / it->hcol[j + 1], it->s);
+                }
+                ++it->info.iterations;
+                it->k = j + 1;
+                const double est = it->ar.add_column(j, it->hcol.data());
+                it->info.est_residual = est / it->bnorm;
+                if (est <= it->target || it->hcol[j + 1] == 0.0) it->in_cycle = false;
+            }
+        }
+        // x += V y (left) or Z y (flexible)
+        for (Inst* it : run) {
+            if (it->done) continue;
+            stk_handle* h = it->h;
+            const int n = nstokes(h);
+            const int k = it->k;
+            it->in_cycle = false;
+            ++it->info.restarts;
+            if (k == 0) continue;
+            it->ar.solve(k, it->y.data());
+            bool ok = true;
+            for (int i = 0; i < k; ++i) ok = ok && std::isfinite(it->y[i]);
+            if (!ok) { finish(it, fail(h, STK_ERR_NONFINITE, "non-finite GMRES update")); continue; }
+            std::memcpy(h->hpin + HP_Y, it->y.data(), sizeof(double) * k);
+            cudaMemcpyAsync(h->dsc + DS_Y, h->hpin + HP_Y, sizeof(double) * k, cudaMemcpyHostToDevice, it->s);
+            Scope sc(h, PF_COMB, (flex ? 4.0 : 8.0) * n * k + 16.0 * n, it->s);
             if (flex) {
                 std::vector<const float*> Zp(h->Z.begin(), h->Z.begin() + k);
-                launch_combine<float>(n, k, Zp.data(), h->dsc + DS_Y, h->xk, s);
+                launch_combine<float>(n, k, Zp.data(), h->dsc + DS_Y, h->xk, it->s);
             } else {
                 std::vector<const double*> Vp(h->V.begin(), h->V.begin() + k);
-                launch_combine<double>(n, k, Vp.data(), h->dsc + DS_Y, h->xk, s);
+                launch_combine<double>(n, k, Vp.data(), h->dsc + DS_Y, h->xk, it->s);
             }
         }
-        CKL();
-        CK(cudaStreamSynchronize(s));   // host staging buffer reused next cycle
     }
-    return info.converged ? STK_OK : STK_ERR_NOT_CONVERGED;
+    std::vector<Inst*> all;
+    for (auto& it : insts) all.push_back(&it);
+    sync_all(all);
+}
+
+int validate_params(stk_handle* h, const stk_solver_params& prm) {
+    if (prm.precond < STK_P1 || prm.precond > STK_P5) return fail(h, STK_ERR_ARG, "preconditioner must be 1..5");
+    if (prm.restart < 1 || prm.restart > 32) return fail(h, STK_ERR_ARG, "restart must be 1..32");
+    if (!(prm.rtol > 0.0)) return fail(h, STK_ERR_ARG, "rtol must be > 0");
+    if (prm.maxit < 1) return fail(h, STK_ERR_ARG, "maxit must be >= 1");
+    if (prm.precision != STK_FP64 && prm.precision != STK_MIXED) return fail(h, STK_ERR_ARG, "bad precision");
+    if (prm.nu < 0 || prm.ncoarse < 1) return fail(h, STK_ERR_ARG, "bad sweep counts");
+    return STK_OK;
 }
 
 bool is_pow2(int v) { return v >= 2 && (v & (v - 1)) == 0; }
@@ -879,10 +1006,29 @@ int stk_create(int dim, const int* n, double hh, const int* bc, stk_handle** out
     CKC(dalloc(h, &h->dsc, NDSC));
     {
         void* p = nullptr;
-        CKC(cudaMallocHost(&p, sizeof(double) * 128));
+        CKC(cudaMallocHost(&p, sizeof(double) * 256));
         h->hpin = static_cast<double*>(p);
     }
     CKC(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+    CKC(cudaStreamCreateWithFlags(&h->run, cudaStreamNonBlocking));
+    CKC(cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming));
+    {   // level descriptors of the single-block coarse-level kernel
+        const int nl = (int)h->lev.size();
+        h->lcoarse_d = h->lcoarse_f = nl;
+        while (h->lcoarse_f > 0 && h->lev[h->lcoarse_f - 1].g.ncell <= COARSE_MAX_CELLS_F32) --h->lcoarse_f;
+        while (h->lcoarse_d > 0 && h->lev[h->lcoarse_d - 1].g.ncell <= COARSE_MAX_CELLS_F64) --h->lcoarse_d;
+        std::vector<CLevel<double>> cd(nl);
+        std::vector<CLevel<float>> cf(nl);
+        for (int l = 0; l < nl; ++l) {
+            const Level& L = h->lev[l];
+            cd[l] = CLevel<double>{L.g, L.cd, L.wd.phi_u, L.wd.rhs_u, L.wd.res_u, L.wd.phi_p, L.wd.rhs_p, L.wd.res_p};
+            cf[l] = CLevel<float>{L.g, L.cf, L.wf.phi_u, L.wf.rhs_u, L.wf.res_u, L.wf.phi_p, L.wf.rhs_p, L.wf.res_p};
+        }
+        CKC(dalloc(h, &h->cld, nl));
+        CKC(dalloc(h, &h->clf, nl));
+        CKC(cudaMemcpy(h->cld, cd.data(), sizeof(CLevel<double>) * nl, cudaMemcpyHostToDevice));
+        CKC(cudaMemcpy(h->clf, cf.data(), sizeof(CLevel<float>) * nl, cudaMemcpyHostToDevice));
+    }
 #undef CKC
     *out = h;
     return STK_OK;
@@ -893,6 +1039,8 @@ int stk_destroy(stk_handle* h) {
     cudaDeviceSynchronize();
     clear_graphs(h);
     if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->run) cudaStreamDestroy(h->run);
+    if (h->join) cudaEventDestroy(h->join);
     for (void* p : h->allocs) cudaFree(p);
     if (h->hpin) cudaFreeHost(h->hpin);
     for (auto e : h->evpool) cudaEventDestroy(e);
@@ -1003,47 +1151,84 @@ int stk_pressure_vcycle(stk_handle* h, const double* r_p, double* x_p, void* str
 int stk_solve(stk_handle* h, const stk_solver_params* params, const double* const* b_u,
               const double* b_p, double* const* x_u, double* x_p, stk_solve_info* info_out,
               void* stream) {
+    stk_batch_io io{b_u, b_p, x_u, x_p};
+    stk_handle* hs[1] = {h};
     if (!h) return STK_ERR_ARG;
-    if (!h->coef_set) return fail(h, STK_ERR_STATE, "coefficients not set");
+    return stk_solve_batched(1, hs, params, &io, info_out, stream);
+}
+
+int stk_solve_batched(int count, stk_handle* const* hs, const stk_solver_params* params,
+                      const stk_batch_io* io, stk_solve_info* infos, void* stream) {
+    if (count < 1 || !hs || !io) return STK_ERR_ARG;
     stk_solver_params prm;
     stk_default_params(&prm);
     if (params) prm = *params;
-    if (prm.precond < STK_P1 || prm.precond > STK_P5) return fail(h, STK_ERR_ARG, "preconditioner must be 1..5");
-    if (prm.restart < 1 || prm.restart > 32) return fail(h, STK_ERR_ARG, "restart must be 1..32");
-    if (!(prm.rtol > 0.0)) return fail(h, STK_ERR_ARG, "rtol must be > 0");
-    if (prm.maxit < 1) return fail(h, STK_ERR_ARG, "maxit must be >= 1");
-    if (prm.precision != STK_FP64 && prm.precision != STK_MIXED) return fail(h, STK_ERR_ARG, "bad precision");
-    if (prm.nu < 0 || prm.ncoarse < 1) return fail(h, STK_ERR_ARG, "bad sweep counts");
-    int rc;
-    if ((rc = check_ptrs(h, (const void* const*)b_u, b_p))) return rc;
-    if ((rc = check_ptrs(h, (const void* const*)x_u, x_p))) return rc;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    CK(cudaSetDevice(h->device));
-    stk_solve_info info{};
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
-    CK(cudaEventRecord(e0, s));
-    if ((rc = gather(h, b_u, b_p, h->bk, s)) == STK_OK && (rc = gather(h, x_u, x_p, h->xk, s)) == STK_OK) {
-        rc = gmres(h, prm, info, s);
-        if (rc == STK_OK || rc == STK_ERR_NOT_CONVERGED) {
-            int rc2 = scatter(h, h->xk, x_u, x_p, s);
-            if (rc2) rc = rc2;
-        }
+    cudaStream_t us = static_cast<cudaStream_t>(stream);
+    for (int i = 0; i < count; ++i) {
+        stk_handle* h = hs[i];
+        if (!h) return STK_ERR_ARG;
+        if (!h->coef_set) return fail(h, STK_ERR_STATE, "coefficients not set");
+        int rc;
+        if ((rc = validate_params(h, prm))) return rc;
+        if ((rc = check_ptrs(h, (const void* const*)io[i].b_u, io[i].b_p))) return rc;
+        if ((rc = check_ptrs(h, (const void* const*)io[i].x_u, io[i].x_p))) return rc;
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == h) return fail(h, STK_ERR_ARG, "a handle appears twice in one batch");
     }
-    cudaEventRecord(e1, s);
+    stk_handle* h0 = hs[0];
+    int dev = h0->device;
+    {
+        stk_handle* h = h0;
+        CK(cudaSetDevice(dev));
+    }
+    // one solve: the caller's stream; several: each handle's own stream,
+    // forked from and joined back into the caller's stream
+    std::vector<Inst> insts(count);
+    cudaEvent_t e0, e1;
+    {
+        stk_handle* h = h0;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        CK(cudaEventRecord(e0, us));
+    }
+    for (int i = 0; i < count; ++i) {
+        Inst& it = insts[i];
+        it.h = hs[i];
+        it.s = count == 1 ? us : hs[i]->run;
+        if (count > 1) cudaStreamWaitEvent(it.s, e0, 0);
+        int rc = gather(it.h, io[i].b_u, io[i].b_p, it.h->bk, it.s);
+        if (!rc) rc = gather(it.h, io[i].x_u, io[i].x_p, it.h->xk, it.s);
+        if (rc) finish(&it, rc);
+    }
+    gmres_lockstep(insts, prm);
+    int worst = STK_OK;
+    for (int i = 0; i < count; ++i) {
+        Inst& it = insts[i];
+        if (it.rc == STK_OK || it.rc == STK_ERR_NOT_CONVERGED) {
+            int rc2 = scatter(it.h, it.h->xk, io[i].x_u, io[i].x_p, it.s);
+            if (rc2) it.rc = rc2;
+        }
+        if (count > 1) {
+            cudaEventRecord(it.h->join, it.s);
+            cudaStreamWaitEvent(us, it.h->join, 0);
+        }
+        if (it.rc == STK_ERR_NOT_CONVERGED)
+            fail(it.h, it.rc, "not converged after %d iterations (residual %.3e)", it.info.iterations,
+                 it.info.true_residual);
+        if (it.rc != STK_OK && (worst == STK_OK || worst == STK_ERR_NOT_CONVERGED)) worst = it.rc;
+    }
+    cudaEventRecord(e1, us);
     cudaEventSynchronize(e1);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    info.solve_ms = ms;
-    info.status = rc;
-    if (rc == STK_ERR_NOT_CONVERGED && h->err.empty())
-        h->err = "maximum number of iterations reached";
-    if (rc == STK_ERR_NOT_CONVERGED) fail(h, rc, "not converged after %d iterations (residual %.3e)", info.iterations, info.true_residual);
-    if (info_out) *info_out = info;
-    return rc;
+    for (int i = 0; i < count; ++i) {
+        insts[i].info.solve_ms = ms;
+        insts[i].info.status = insts[i].rc;
+        if (infos) infos[i] = insts[i].info;
+    }
+    return worst;
 }
 
 int stk_profile(stk_handle* h, int enable) {
@@ -1061,6 +1246,28 @@ int stk_profile(stk_handle* h, int enable) {
 }
 
 long long stk_kernel_launches(const stk_handle* h) { return h ? h->nkern : -1; }
+
+int stk_gradient(stk_handle* h, const double* const* u, const double* const* lambda,
+                 double* dL_dlogmu, double* dL_drho, void* stream) {
+    if (!h) return STK_ERR_ARG;
+    if (!h->coef_set) return fail(h, STK_ERR_STATE, "coefficients not set");
+    if (!u || !lambda || !dL_dlogmu || !dL_drho) return fail(h, STK_ERR_ARG, "null pointer");
+    for (int a = 0; a < h->dim; ++a)
+        if (!u[a] || !lambda[a]) return fail(h, STK_ERR_ARG, "null face array");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(cudaSetDevice(h->device));
+    const Geom& g = h->lev[0].g;
+    for (int a = 0; a < g.dim; ++a) {
+        CK(cudaMemcpyAsync(h->bk + g.foff[a], u[a], sizeof(double) * g.fsize[a], cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(h->tmp + g.foff[a], lambda[a], sizeof(double) * g.fsize[a], cudaMemcpyDeviceToDevice, s));
+    }
+    {
+        Scope sc(h, PF_ALG, 8.0 * (2.0 * g.nvel + 3.0 * g.ncell), s);
+        launch_gradient(g, h->lev[0].cd.mu_c, h->theta, h->bk, h->tmp, dL_dlogmu, dL_drho, s);
+    }
+    CKL();
+    return STK_OK;
+}
 
 int stk_profile_read(stk_handle* h, int k, const char** name, long long* launches, double* ms,
                      double* bytes) {

@@ -1,0 +1,323 @@
+// Device-side stencils of the staggered Stokes operator and of the App. C
+// multigrid, as per-point functions shared by the grid-wide kernels
+// (kernels.cu) and the single-block coarse-level kernel (coarse.cu).
+//
+// Reference: Cai, Nonaka, Bell, Griffith & Donev, arXiv:1308.4605,
+// Sec. 3.1 (Eq. div_stress, wall closures) and App. C (multicolour
+// Gauss-Seidel, restriction, prolongation).
+//
+// Conventions: packed face vectors (components x, y[, z], x fastest), wall
+// faces stored as zeros and never written; face i of component a lies on the
+// low-a side of cell i.  Every stencil is evaluated only on faces that carry
+// an unknown, so no index leaves its array.  Arrays that a V-cycle writes
+// (phi, rhs, residuals) are read with ordinary coherent loads, never through
+// the read-only path: the coarse-level kernel reads them again after a
+// __syncthreads() within the same launch.  Only coefficients use __ldg.
+#pragma once
+#include "internal.cuh"
+
+namespace stk {
+namespace st {
+
+__host__ __device__ __forceinline__ int wrapm(int i, int n) {
+    return i < 0 ? i + n : (i >= n ? i - n : i);
+}
+__device__ __forceinline__ int fidx(const Geom& g, int a, const int q[3]) {
+    return g.foff[a] + (q[2] * g.fe[a][1] + q[1]) * g.fe[a][0] + q[0];
+}
+__device__ __forceinline__ int cidx(const Geom& g, const int q[3]) {
+    return (q[2] * g.n[1] + q[1]) * g.n[0] + q[0];
+}
+__device__ __forceinline__ int eidx(const Geom& g, int p, const int q[3]) {
+    return (q[2] * g.ee[p][1] + q[1]) * g.ee[p][0] + q[0];
+}
+// t -> (i, j, k) over the face array of component a
+__device__ __forceinline__ void decode_face(const Geom& g, int a, int t, int q[3]) {
+    const int r = fdiv(t, g.fd_e0[a]);
+    q[0] = t - r * g.fe[a][0];
+    q[2] = fdiv(r, g.fd_e1[a]);
+    q[1] = r - q[2] * g.fe[a][1];
+}
+__device__ __forceinline__ void decode_cell(const Geom& g, int t, int q[3]) {
+    const int r = fdiv(t, g.fd_n0);
+    q[0] = t - r * g.n[0];
+    q[2] = fdiv(r, g.fd_n1);
+    q[1] = r - q[2] * g.n[1];
+}
+// t-th face of component a with (i + j + k) % 2 == parity; false past the end
+__device__ __forceinline__ bool decode_face_colour(const Geom& g, int a, int parity, int t, int q[3]) {
+    const int half = (g.fe[a][0] + 1) >> 1;
+    const int r = fdiv(t, g.fd_h0[a]);
+    const int xh = t - r * half;
+    q[2] = fdiv(r, g.fd_e1[a]);
+    q[1] = r - q[2] * g.fe[a][1];
+    q[0] = 2 * xh + ((q[1] + q[2] + parity) & 1);
+    return q[0] < g.fe[a][0];
+}
+__device__ __forceinline__ void decode_cell_colour(const Geom& g, int parity, int t, int q[3]) {
+    const int half = g.n[0] >> 1;
+    const int r = fdiv(t, g.fd_nh0);
+    const int xh = t - r * half;
+    q[2] = fdiv(r, g.fd_n1);
+    q[1] = r - q[2] * g.n[1];
+    q[0] = 2 * xh + ((q[1] + q[2] + parity) & 1);
+}
+__device__ __forceinline__ bool wall_face(const Geom& g, int a, const int q[3]) {
+    return !g.per[a] && (q[a] == 0 || q[a] == g.n[a]);
+}
+__device__ __forceinline__ int step(const Geom& g, int ax, int i, int d) {
+    return g.per[ax] ? wrapm(i + d, g.n[ax]) : i + d;
+}
+template <typename T> __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
+
+template <typename T> __device__ __forceinline__ T gih(const Geom& g);
+template <> __device__ __forceinline__ double gih<double>(const Geom& g) { return g.ih; }
+template <> __device__ __forceinline__ float gih<float>(const Geom& g) { return g.ihf; }
+template <typename T> __device__ __forceinline__ T gih2(const Geom& g);
+template <> __device__ __forceinline__ double gih2<double>(const Geom& g) { return g.ih2; }
+template <> __device__ __forceinline__ float gih2<float>(const Geom& g) { return g.ih2f; }
+
+// the axes other than A (compile time)
+template <int DIM, int A> struct Trans;
+template <int A> struct Trans<2, A> { static constexpr int n = 1, b0 = 1 - A, b1 = 1 - A; };
+template <int A> struct Trans<3, A> {
+    static constexpr int n = 2, b0 = (A + 1) % 3, b1 = (A + 2) % 3;
+};
+
+// h^2 (L_mu phi)_A at the interior A-face q (Eq. div_stress with the wall
+// closures of Sec. 3.1), grid scaling factored out, arithmetic in T.  With
+// DIAG, dsum receives h^2 times the viscous part of A's diagonal (a no-slip
+// wall edge counts twice: its derivative is taken over h/2).
+template <int DIM, int A, typename T, typename TV, bool DIAG>
+__device__ __forceinline__ T visc_h2(const Geom& g, const Coef<T>& C, const int q[3],
+                                     const TV* phi, T& dsum) {
+    int qp[3] = {q[0], q[1], q[2]};
+    int qm[3] = {q[0], q[1], q[2]};
+    qp[A] = step(g, A, q[A], 1);
+    qm[A] = step(g, A, q[A], -1);
+    const T pa = T(phi[fidx(g, A, q)]);
+    const T pp = T(phi[fidx(g, A, qp)]);
+    const T pm = T(phi[fidx(g, A, qm)]);
+    const T mh = ld(C.mu_c + cidx(g, q));
+    const T ml = ld(C.mu_c + cidx(g, qm));
+    T L = mh * (pp - pa);
+    L = fma(-ml, pa - pm, L);
+    L = L + L;
+    if (DIAG) dsum = T(2) * (mh + ml);
+#pragma unroll
+    for (int B = 0; B < DIM; ++B) {
+        if (B == A) continue;
+        const int P = A + B - 1;   // edge pair index of {A, B}
+        const bool wlo = !g.per[B] && q[B] == 0;
+        const bool whi = !g.per[B] && q[B] == g.n[B] - 1;
+        int qe[3] = {q[0], q[1], q[2]};
+        qe[B] = step(g, B, q[B], 1);
+        const T mlo = ld(C.mu_e[P] + eidx(g, P, q));
+        const T mhi = ld(C.mu_e[P] + eidx(g, P, qe));
+        T dlo, dhi;
+        if (wlo) {
+            dlo = pa + pa;               // (phi - 0) / (h/2)
+        } else {
+            int qb[3] = {q[0], q[1], q[2]};
+            qb[B] = step(g, B, q[B], -1);
+            dlo = pa - T(phi[fidx(g, A, qb)]);
+        }
+        dhi = whi ? -(pa + pa) : T(phi[fidx(g, A, qe)]) - pa;
+        // d phi_B / dx_A on the two edges: B-faces in A-cells q[A] and q[A]-1
+        int r0[3] = {q[0], q[1], q[2]};
+        r0[A] = qm[A];
+        int r2[3] = {qe[0], qe[1], qe[2]};
+        r2[A] = qm[A];
+        const T xlo = T(phi[fidx(g, B, q)]) - T(phi[fidx(g, B, r0)]);
+        const T xhi = T(phi[fidx(g, B, qe)]) - T(phi[fidx(g, B, r2)]);
+        L = fma(mhi, dhi + xhi, L);
+        L = fma(-mlo, dlo + xlo, L);
+        if (DIAG) dsum += (whi ? T(2) : T(1)) * mhi + (wlo ? T(2) : T(1)) * mlo;
+    }
+    return L;
+}
+
+template <int DIM, typename T, typename TV, bool DIAG>
+__device__ __forceinline__ T visc_h2_any(int a, const Geom& g, const Coef<T>& C, const int q[3],
+                                         const TV* phi, T& dsum) {
+    if (a == 0) return visc_h2<DIM, 0, T, TV, DIAG>(g, C, q, phi, dsum);
+    if (a == 1) return visc_h2<DIM, 1, T, TV, DIAG>(g, C, q, phi, dsum);
+    return visc_h2<DIM, DIM == 3 ? 2 : 1, T, TV, DIAG>(g, C, q, phi, dsum);
+}
+
+// (L_rho phi) at cell q and its diagonal; beta = 0 on wall faces.
+template <int DIM, typename T, typename TV>
+__device__ __forceinline__ T poisson_cell(const Geom& g, const Coef<T>& C, const int q[3],
+                                          const TV* phi, T& diag) {
+    const T ih2 = gih2<T>(g);
+    const T pc = T(phi[cidx(g, q)]);
+    T L = T(0);
+    diag = T(0);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        int fh[3] = {q[0], q[1], q[2]};
+        fh[a] = g.per[a] ? wrapm(q[a] + 1, g.n[a]) : q[a] + 1;
+        const T bh = ld(C.beta + fidx(g, a, fh));
+        const T bl = ld(C.beta + fidx(g, a, q));
+        int ch[3] = {q[0], q[1], q[2]};
+        int cl[3] = {q[0], q[1], q[2]};
+        ch[a] = g.per[a] ? wrapm(q[a] + 1, g.n[a]) : min(q[a] + 1, g.n[a] - 1);
+        cl[a] = g.per[a] ? wrapm(q[a] - 1, g.n[a]) : max(q[a] - 1, 0);
+        L += ih2 * (bh * (T(phi[cidx(g, ch)]) - pc) - bl * (pc - T(phi[cidx(g, cl)])));
+        diag -= ih2 * (bh + bl);
+    }
+    return L;
+}
+
+// ---------------------------------------------------------- per-point updates
+// Gauss-Seidel update phi += D^{-1}(rhs - A phi) of the interior A-face q
+// (App. C, omega = 1).  FP32 forms the diagonal on the fly; FP64 loads the
+// stored inverse diagonal (an FP64 division costs more than the load).
+template <int DIM, int A, typename T>
+__device__ __forceinline__ void vel_gs_point(const Geom& g, const Coef<T>& C, const int q[3],
+                                             T* phi, const T* rhs) {
+    constexpr bool F32 = sizeof(T) == 4;
+    T dsum;
+    const T L = visc_h2<DIM, A, T, T, F32>(g, C, q, phi, dsum);
+    const int f = fidx(g, A, q);
+    const T p = phi[f];
+    const T al = ld(C.alpha + f);
+    const T ih2 = gih2<T>(g);
+    const T res = rhs[f] - fma(al, p, -ih2 * L);
+    if constexpr (F32) phi[f] = p + res / fma(ih2, dsum, al);
+    else phi[f] = fma(res, ld(C.invd_u + f), p);
+}
+
+template <int DIM, typename T>
+__device__ __forceinline__ T vel_res_point(int a, const Geom& g, const Coef<T>& C, const int q[3],
+                                           const T* phi, const T* rhs) {
+    const int f = fidx(g, a, q);
+    T dsum;
+    const T L = visc_h2_any<DIM, T, T, false>(a, g, C, q, phi, dsum);
+    return rhs[f] - fma(ld(C.alpha + f), phi[f], -gih2<T>(g) * L);
+}
+
+// 6-point (2D) / 12-point (3D) restriction to the interior coarse A-face Q:
+// 1/4 (1/8) on the coincident fine faces, 1/8 (1/16) on their neighbours.
+template <int DIM, int A, typename T>
+__device__ __forceinline__ T vel_restrict_point(const Geom& gf, const int Q[3],
+                                                const T* res) {
+    using TR = Trans<DIM, A>;
+    const T wt = DIM == 3 ? T(0.25) : T(0.5);
+    T acc = T(0);
+#pragma unroll
+    for (int s = -1; s <= 1; ++s) {
+        const T w = (s == 0 ? T(0.5) : T(0.25)) * wt;
+#pragma unroll
+        for (int t0 = 0; t0 < 2; ++t0)
+#pragma unroll
+            for (int t1 = 0; t1 < (TR::n == 2 ? 2 : 1); ++t1) {
+                int q[3] = {2 * Q[0], 2 * Q[1], DIM == 3 ? 2 * Q[2] : 0};
+                q[A] = step(gf, A, q[A], s);
+                q[TR::b0] += t0;
+                if (TR::n == 2) q[TR::b1] += t1;
+                acc += w * res[fidx(gf, A, q)];
+            }
+    }
+    return acc;
+}
+
+// transverse weights of the face prolongation along axis b for fine cell j:
+// 3/4 on coarse cell J = j/2, 1/4 on the nearer neighbour; a neighbour across
+// a wall is a ghost -phi (no-slip) or +phi (free-slip) folded onto J.
+__device__ __forceinline__ void prolong_transverse(const Geom& gc, int b, int j, int& J, int& nb,
+                                                   float& wo, float& wn) {
+    J = j >> 1;
+    nb = (j & 1) ? J + 1 : J - 1;
+    wo = 0.75f;
+    wn = 0.25f;
+    if (nb < 0 || nb >= gc.n[b]) {
+        if (gc.per[b]) {
+            nb = wrapm(nb, gc.n[b]);
+        } else {
+            const int code = nb < 0 ? gc.bclo[b] : gc.bchi[b];
+            wo += code == NOSLIP ? -0.25f : 0.25f;
+            wn = 0.f;
+            nb = J;
+        }
+    }
+}
+
+// (P phi_c) at the interior fine A-face q (App. C face prolongation)
+template <int DIM, int A, typename T>
+__device__ __forceinline__ T vel_prolong_point(const Geom& gc, const int q[3],
+                                               const T* pc) {
+    using TR = Trans<DIM, A>;
+    int ca0 = q[A] >> 1, ca1 = ca0;
+    T wa0 = T(1), wa1 = T(0);
+    if (q[A] & 1) {
+        ca1 = ca0 + 1;
+        if (gc.per[A] && ca1 >= gc.n[A]) ca1 -= gc.n[A];
+        wa0 = wa1 = T(0.5);
+    }
+    int J0, N0, J1 = 0, N1 = 0;
+    float wo0, wn0, wo1 = 1.f, wn1 = 0.f;
+    prolong_transverse(gc, TR::b0, q[TR::b0], J0, N0, wo0, wn0);
+    if (TR::n == 2) prolong_transverse(gc, TR::b1, q[TR::b1], J1, N1, wo1, wn1);
+    // separable: along the second transverse axis, then the first, then the normal
+    auto line = [&](int ca) -> T {
+        int Q[3] = {0, 0, 0};
+        Q[A] = ca;
+        Q[TR::b0] = J0;
+        T t0, t1;
+        if (TR::n == 2) {
+            Q[TR::b1] = J1;
+            t0 = T(wo1) * pc[fidx(gc, A, Q)];
+            if (wn1 != 0.f) {
+                Q[TR::b1] = N1;
+                t0 = fma(T(wn1), pc[fidx(gc, A, Q)], t0);
+            }
+            Q[TR::b0] = N0;
+            Q[TR::b1] = J1;
+            t1 = T(wo1) * pc[fidx(gc, A, Q)];
+            if (wn1 != 0.f) {
+                Q[TR::b1] = N1;
+                t1 = fma(T(wn1), pc[fidx(gc, A, Q)], t1);
+            }
+        } else {
+            t0 = pc[fidx(gc, A, Q)];
+            Q[TR::b0] = N0;
+            t1 = pc[fidx(gc, A, Q)];
+        }
+        T v = T(wo0) * t0;
+        if (wn0 != 0.f) v = fma(T(wn0), t1, v);
+        return v;
+    };
+    T acc = line(ca0);
+    if (wa1 != T(0)) acc = wa0 * acc + wa1 * line(ca1);
+    return acc;
+}
+
+template <int DIM, typename T>
+__device__ __forceinline__ void cell_gs_point(const Geom& g, const Coef<T>& C, const int q[3],
+                                              T* phi, const T* rhs) {
+    T d;
+    const T L = poisson_cell<DIM, T, T>(g, C, q, phi, d);
+    const int c = cidx(g, q);
+    if constexpr (sizeof(T) == 4) phi[c] += (rhs[c] - L) / d;
+    else phi[c] = fma(rhs[c] - L, ld(C.invd_p + c), phi[c]);
+}
+
+template <int DIM, typename T>
+__device__ __forceinline__ T cell_restrict_point(const Geom& gf, const int Q[3],
+                                                 const T* res) {
+    T s = T(0);
+#pragma unroll
+    for (int dz = 0; dz < (DIM == 3 ? 2 : 1); ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                int q[3] = {2 * Q[0] + dx, 2 * Q[1] + dy, (DIM == 3 ? 2 * Q[2] : 0) + dz};
+                s += res[cidx(gf, q)];
+            }
+    return s * (DIM == 3 ? T(0.125) : T(0.25));
+}
+
+}  // namespace st
+}  // namespace stk

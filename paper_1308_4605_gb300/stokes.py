@@ -51,6 +51,11 @@ class stk_solve_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class stk_batch_io(ctypes.Structure):
+    _fields_ = [("b_u", ctypes.POINTER(ctypes.c_void_p)), ("b_p", ctypes.c_void_p),
+                ("x_u", ctypes.POINTER(ctypes.c_void_p)), ("x_p", ctypes.c_void_p)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1308_4605_gb300.build`"
@@ -76,6 +81,9 @@ def _load():
                           ctypes.POINTER(stk_solve_info), P]),
         "stk_profile": (I, [P, I]),
         "stk_kernel_launches": (ctypes.c_longlong, [P]),
+        "stk_gradient": (I, [P, PP, PP, P, P, P]),
+        "stk_solve_batched": (I, [I, ctypes.POINTER(P), ctypes.POINTER(stk_solver_params),
+                                  ctypes.POINTER(stk_batch_io), ctypes.POINTER(stk_solve_info), P]),
         "stk_pressure_vcycle_noalloc": (I, [I, ctypes.POINTER(I), D, ctypes.POINTER(I), P, P, P, P]),
         "stk_profile_read": (I, [P, I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong),
                                  ctypes.POINTER(D), ctypes.POINTER(D)]),
@@ -91,7 +99,7 @@ _lib = _load()
 EXPORTED = ["stk_default_params", "stk_create", "stk_destroy", "stk_last_error", "stk_face_length",
             "stk_cell_length", "stk_set_coefficients", "stk_apply_operator",
             "stk_apply_preconditioner", "stk_velocity_vcycle", "stk_pressure_vcycle", "stk_solve",
-            "stk_profile", "stk_profile_read", "stk_kernel_launches", "stk_pressure_vcycle_noalloc"]
+            "stk_profile", "stk_profile_read", "stk_kernel_launches", "stk_pressure_vcycle_noalloc", "stk_gradient", "stk_solve_batched"]
 
 
 def library():
@@ -214,6 +222,31 @@ def stk_solve(h, params, b_u, b_p, x_u, x_p, stream=None):
     return info.as_dict()
 
 
+def stk_solve_batched(handles, params, b_us, b_ps, x_us, x_ps, stream=None):
+    """Solve len(handles) independent systems together (see stokes.h).
+    Returns the list of info dicts; raises unless every solve converged or
+    the only failure is STK_ERR_NOT_CONVERGED."""
+    count = len(handles)
+    hs = (ctypes.c_void_p * count)(*[h.value for h in handles])
+    keep = []
+    ios = (stk_batch_io * count)()
+    for i, h in enumerate(handles):
+        dim = len(b_us[i])
+        fl, nc = _lengths(h, dim)
+        bu, xu = _ptrs(b_us[i], fl), _ptrs(x_us[i], fl)
+        keep += [bu, xu]
+        ios[i].b_u = ctypes.cast(bu, ctypes.POINTER(ctypes.c_void_p))
+        ios[i].b_p = _ptr(b_ps[i], nc)
+        ios[i].x_u = ctypes.cast(xu, ctypes.POINTER(ctypes.c_void_p))
+        ios[i].x_p = _ptr(x_ps[i], nc)
+    infos = (stk_solve_info * count)()
+    rc = _lib.stk_solve_batched(count, hs, ctypes.byref(params), ios, infos, _stream(stream))
+    if rc not in (STK_OK, STK_ERR_NOT_CONVERGED):
+        bad = [i for i in range(count) if infos[i].status not in (STK_OK, STK_ERR_NOT_CONVERGED)]
+        _check(handles[bad[0]] if bad else None, rc)
+    return [infos[i].as_dict() for i in range(count)]
+
+
 def stk_profile(h, enable):
     return _check(h, _lib.stk_profile(h, int(enable)))
 
@@ -228,6 +261,12 @@ def stk_pressure_vcycle_noalloc(dim, n, h, bc, rho, r_p, x_p, stream=None):
     if rc != STK_OK:
         raise StokesError(rc, "stk_pressure_vcycle_noalloc failed")
     return rc
+
+
+def stk_gradient(h, u, lam, dlogmu, drho, stream=None):
+    fl, nc = _lengths(h, len(u))
+    return _check(h, _lib.stk_gradient(h, _ptrs(u, fl), _ptrs(lam, fl), _ptr(dlogmu, nc), _ptr(drho, nc),
+                                       _stream(stream)))
 
 
 def stk_kernel_launches(h):

@@ -66,6 +66,10 @@ CASES = [
     (3, (8, 8, 8), (PERIODIC,) * 6, 1.0),
     (3, (8, 4, 16), (NOSLIP,) * 6, 0.0),
     (3, (8, 8, 4), (NOSLIP, NOSLIP, PERIODIC, PERIODIC, FREESLIP, FREESLIP), 1.0),
+    # above 4096 cells: the finer levels run as grid-wide kernels, the rest in
+    # the single-block coarse-level kernel
+    (2, (128, 64), (NOSLIP, FREESLIP, PERIODIC, PERIODIC), 1.0),
+    (3, (32, 16, 16), (PERIODIC, PERIODIC, NOSLIP, NOSLIP, FREESLIP, NOSLIP), 0.5),
 ]
 
 
@@ -115,7 +119,7 @@ def test_vcycles_match_oracle(S, dim, n, bc, theta):
 
 
 @pytest.mark.parametrize("which", [1, 2, 3, 4, 5])
-@pytest.mark.parametrize("dim,n,bc,theta", [CASES[0], CASES[1], CASES[4], CASES[6]])
+@pytest.mark.parametrize("dim,n,bc,theta", [CASES[0], CASES[1], CASES[4], CASES[6], CASES[7], CASES[8]])
 def test_preconditioners_match_oracle(S, which, dim, n, bc, theta):
     pr = _problem(dim, n, bc, theta, seed=4)
     g = Grid(dim, pr.n, pr.h, pr.bc)
@@ -168,6 +172,13 @@ def test_solve_bubble_2d(S, which, precision):
     """The paper's bubble problem (Eq. varcoeff_def), r = 100, steady, 64^2."""
     pr = wl.bubble(2, 64, 100.0, 100.0)
     _solve_and_check(S, pr, precision, which)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_bubble_2d_256(S, precision):
+    """Bubble r = 100 at 256^2: four levels run as grid-wide kernels."""
+    pr = wl.bubble(2, 256, 100.0, 100.0)
+    _solve_and_check(S, pr, precision, 1)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
