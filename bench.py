@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "c5", "bubble2d", "bubble3d"])
+    ap.add_argument("--workload", default="c3",
+                    choices=["c3", "c2", "c1", "c5", "bubble2d", "bubble3d", "c4", "c5adj"])
     ap.add_argument("--n", type=int, default=0, help="override the grid size")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -268,6 +269,9 @@ def run_ours(args):
         solver.close()
         return 0
 
+    from paper_1308_4605_gb300 import tuning
+    solver.set_coefficients(rho, mu, pr.theta)
+    schedules = {"fp64": tuning.tune(solver, S.STK_FP64), "mixed": tuning.tune(solver, S.STK_MIXED)}
     for _ in range(args.warmup):
         step(S.STK_FP64)
         step(S.STK_MIXED)
@@ -369,6 +373,7 @@ def run_ours(args):
         "config": dict(cfg, l2="flushed between steps (256 MB write); inputs > L2",
                        parallelism="replicas" if world > 1 else "single GPU"),
         "gmres_iterations": infos64[0]["iterations"],
+        "multigrid_schedules": schedules,
         "true_residual": max(i["true_residual"] for i in infos64),
         "scalar_vcycles": infos64[0]["scalar_vcycles"],
         "forms": {
@@ -395,10 +400,161 @@ def run_ours(args):
     return 0
 
 
+def run_batched(args):
+    """64 independent 2D periodic unsteady instances of {64..512}^2 (sizes
+    drawn by seed), mu contrast 1e3, P1: one after another with the FP64
+    solver, then all together with stk_solve_batched (FP64 and mixed)."""
+    import numpy as np
+    import torch
+    from paper_1308_4605_gb300 import stokes as S
+    from paper_1308_4605_gb300 import tuning
+    from paper_1308_4605_gb300 import workloads as wl
+    dev = torch.device("cuda", 0)
+    sizes = wl.config_c4_sizes()
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    solvers, bus, bps, xus, xps = [], [], [], [], []
+    for i, n in enumerate(sizes):
+        pr = wl.config_c4_instance(i, n)
+        sv = S.StokesSolver(2, pr.n[:2], pr.bc[:4], pr.h)
+        sv.set_coefficients(t(pr.rho), t(pr.mu), pr.theta)
+        tuning.tune(sv, S.STK_FP64)
+        tuning.tune(sv, S.STK_MIXED)
+        solvers.append(sv)
+        bus.append([t(x) for x in pr.b_u])
+        bps.append(t(pr.b_p))
+        xu, xp = sv.zeros(dev)
+        xus.append(xu)
+        xps.append(xp)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def params(precision):
+        p = S.stk_default_params()
+        p.precision = precision
+        p.precond = 1
+        p.maxit = 3000
+        return p
+
+    def zero():
+        for xu, xp in zip(xus, xps):
+            for v in xu:
+                v.zero_()
+            xp.zero_()
+
+    def sequential(precision):
+        zero()
+        its = []
+        for k, sv in enumerate(solvers):
+            its.append(S.stk_solve(sv.handle, params(precision), bus[k], bps[k], xus[k], xps[k]))
+        return its
+
+    def batched(precision):
+        zero()
+        return S.stk_solve_batched([sv.handle for sv in solvers], params(precision), bus, bps, xus, xps)
+
+    def timed(fn, precision, k):
+        times, infos = [], None
+        for _ in range(k):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            infos = fn(precision)
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return statistics.mean(times), infos
+
+    for _ in range(args.warmup):
+        sequential(S.STK_FP64)
+        batched(S.STK_FP64)
+        batched(S.STK_MIXED)
+    res = {}
+    for name, fn, prec in (("sequential_fp64", sequential, S.STK_FP64),
+                           ("batched_fp64", batched, S.STK_FP64),
+                           ("batched_mixed", batched, S.STK_MIXED),
+                           ("sequential_mixed", sequential, S.STK_MIXED)):
+        ms, infos = timed(fn, prec, args.steps)
+        res[name] = {"ms": ms, "iterations_total": int(sum(i["iterations"] for i in infos)),
+                     "max_true_residual": max(i["true_residual"] for i in infos),
+                     "all_converged": all(i["converged"] for i in infos)}
+    cells = int(sum(n * n for n in sizes))
+    line = {"metric": METRIC, "value": res["batched_mixed"]["ms"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["batched_mixed"]["ms"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+            "data": "synthetic",
+            "config": {"workload": f"batched_64_periodic_2d_instances_{cells}_cells",
+                       "sizes_histogram": {str(n): sizes.count(n) for n in sorted(set(sizes))},
+                       "mu_contrast": 1e3, "precond": "P1", "l2": "flushed between steps"},
+            "forms": res,
+            "speedup_batched_mixed_vs_sequential_fp64": res["sequential_fp64"]["ms"] / res["batched_mixed"]["ms"]}
+    print(json.dumps(line))
+    for sv in solvers:
+        sv.close()
+    return 0
+
+
+def run_adjoint(args):
+    """Forward + adjoint (gradient w.r.t. log mu) of the 3D steady no-slip
+    workload at n^3 (default 256), loss 1/2||u - u_t||^2, FP64 and mixed."""
+    import numpy as np
+    import torch
+    from paper_1308_4605_gb300 import adjoint
+    from paper_1308_4605_gb300 import stokes as S
+    from paper_1308_4605_gb300 import workloads as wl
+    dev = torch.device("cuda", 0)
+    n = args.n or 256
+    pr = wl.config_c5(n)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    solver = S.StokesSolver(3, pr.n, pr.bc, pr.h)
+    b_u = [t(x) for x in pr.b_u]
+    b_p = t(pr.b_p)
+    rng = np.random.default_rng(77)
+    ut = [t(rng.standard_normal(x.shape)) for x in pr.b_u]
+    rho = t(pr.rho)
+    lm0 = t(np.log(pr.mu))
+    res = {}
+    for name, precision in (("fp64", S.STK_FP64), ("mixed", S.STK_MIXED)):
+        def step():
+            lm = lm0.clone().requires_grad_(True)
+            out = adjoint.stokes_solve(solver, lm, rho, 0.0, b_u, b_p, precond=2, rtol=1e-10,
+                                       precision=precision, maxit=4000)
+            L = 0.5 * sum(((o - q) ** 2).sum() for o, q in zip(out[:3], ut))
+            L.backward()
+            return lm.grad
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            gr = step()
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        res[name] = {"ms_forward_plus_adjoint": statistics.mean(times),
+                     "grad_norm": float(torch.linalg.norm(gr))}
+    line = {"metric": METRIC, "value": res["mixed"]["ms_forward_plus_adjoint"], "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["mixed"]["ms_forward_plus_adjoint"], "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": f"adjoint_3d_steady_noslip_{n}^3", "mu_contrast": 1e2, "precond": "P2"},
+            "forms": res}
+    print(json.dumps(line))
+    solver.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "c4":
+        return run_batched(args)
+    if args.workload == "c5adj":
+        return run_adjoint(args)
     return run_ours(args)
 
 

@@ -184,6 +184,23 @@ typedef struct {
 int stk_solve_batched(int count, stk_handle* const* hs, const stk_solver_params* params,
                       const stk_batch_io* io, stk_solve_info* infos, void* stream);
 
+/* Multigrid schedule of one precision (STK_FP64: the FP64 preconditioner of
+ * left GMRES; STK_MIXED: the FP32 one of the flexible form).  Levels
+ * coarse_level and coarser run as one single-block kernel (all of their
+ * smoothing and transfers in one launch); finer levels run as grid-wide
+ * kernels, the Gauss-Seidel colours with `threads` threads per block
+ * (64, 128, 256 or 512).  The arithmetic does not depend on the schedule.
+ * stk_autotune times one velocity + one pressure V-cycle (as a captured
+ * graph) for every admissible schedule, applies the fastest and returns it;
+ * stk_set_schedule applies a known one (e.g. cached from an earlier run). */
+typedef struct {
+    int coarse_level;
+    int threads;
+} stk_schedule;
+int stk_get_schedule(const stk_handle* h, int precision, stk_schedule* out);
+int stk_set_schedule(stk_handle* h, int precision, const stk_schedule* sc);
+int stk_autotune(stk_handle* h, int precision, stk_schedule* best, void* stream);
+
 /* Per-kernel timing of the calls above with CUDA events on the call's
  * stream.  stk_profile(h, 1) starts collecting (and clears), 0 stops.
  * stk_profile_read returns, for kernel family k (0 <= k < STK_NPROF), its

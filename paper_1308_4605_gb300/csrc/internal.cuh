@@ -105,7 +105,7 @@ void launch_stokes_residual(const Geom& g, Coef<double> C, const double* x, cons
 // multigrid (precision T)
 template <typename T>
 void launch_vel_gs_colour(const Geom& g, Coef<T> C, int comp, int parity, T* phi, const T* rhs,
-                          cudaStream_t s);
+                          cudaStream_t s, int tpb = 256);   // tpb <= 512
 template <typename T>
 void launch_vel_residual(const Geom& g, Coef<T> C, const T* phi, const T* rhs, T* res,
                          cudaStream_t s);
@@ -116,7 +116,7 @@ void launch_vel_prolong_add(const Geom& gc, const T* phi_c, const Geom& gf, T* p
                             cudaStream_t s);
 template <typename T>
 void launch_cell_gs_colour(const Geom& g, Coef<T> C, int parity, T* phi, const T* rhs,
-                           cudaStream_t s);
+                           cudaStream_t s, int tpb = 256);  // tpb <= 512
 template <typename T>
 void launch_cell_residual(const Geom& g, Coef<T> C, const T* phi, const T* rhs, T* res,
                           cudaStream_t s);

@@ -261,7 +261,7 @@ __global__ void k_stokes_matvec(Geom g, Coef<double> C, Segs sg, const TV* __res
 // One colour of the staggered Gauss-Seidel smoother (App. C): every A-face
 // with (i + j + k) % 2 == parity gets phi += D^{-1} (rhs - A phi).
 template <int DIM, int A, typename T>
-__global__ void __launch_bounds__(TPB) k_vel_gs(Geom g, Coef<T> C, int parity, T* __restrict__ phi,
+__global__ void __launch_bounds__(512) k_vel_gs(Geom g, Coef<T> C, int parity, T* __restrict__ phi,
                                                 const T* __restrict__ rhs, int nthreads) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nthreads) return;
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(TPB) k_vel_prolong_add(Geom gc, Geom gf, Segs 
 
 // Red-black Gauss-Seidel colour for L_rho phi = rhs (App. C).
 template <int DIM, typename T>
-__global__ void __launch_bounds__(TPB) k_cell_gs(Geom g, Coef<T> C, int parity, T* __restrict__ phi,
+__global__ void __launch_bounds__(512) k_cell_gs(Geom g, Coef<T> C, int parity, T* __restrict__ phi,
                                                  const T* __restrict__ rhs, int nthreads) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nthreads) return;
@@ -660,16 +660,16 @@ void launch_stokes_residual(const Geom& g, Coef<double> C, const double* x, cons
 
 template <typename T>
 void launch_vel_gs_colour(const Geom& g, Coef<T> C, int comp, int parity, T* phi, const T* rhs,
-                          cudaStream_t s) {
+                          cudaStream_t s, int tpb) {
     const int nt = ((g.fe[comp][0] + 1) / 2) * g.fe[comp][1] * g.fe[comp][2];
-    const int nb = nblk(nt);
+    const int nb = (nt + tpb - 1) / tpb;
     if (g.dim == 2) {
-        if (comp == 0) k_vel_gs<2, 0, T><<<nb, TPB, 0, s>>>(g, C, parity, phi, rhs, nt);
-        else k_vel_gs<2, 1, T><<<nb, TPB, 0, s>>>(g, C, parity, phi, rhs, nt);
+        if (comp == 0) k_vel_gs<2, 0, T><<<nb, tpb, 0, s>>>(g, C, parity, phi, rhs, nt);
+        else k_vel_gs<2, 1, T><<<nb, tpb, 0, s>>>(g, C, parity, phi, rhs, nt);
     } else {
-        if (comp == 0) k_vel_gs<3, 0, T><<<nb, TPB, 0, s>>>(g, C, parity, phi, rhs, nt);
-        else if (comp == 1) k_vel_gs<3, 1, T><<<nb, TPB, 0, s>>>(g, C, parity, phi, rhs, nt);
-        else k_vel_gs<3, 2, T><<<nb, TPB, 0, s>>>(g, C, parity, phi, rhs, nt);
+        if (comp == 0) k_vel_gs<3, 0, T><<<nb, tpb, 0, s>>>(g, C, parity, phi, rhs, nt);
+        else if (comp == 1) k_vel_gs<3, 1, T><<<nb, tpb, 0, s>>>(g, C, parity, phi, rhs, nt);
+        else k_vel_gs<3, 2, T><<<nb, tpb, 0, s>>>(g, C, parity, phi, rhs, nt);
     }
 }
 
@@ -697,11 +697,11 @@ void launch_vel_prolong_add(const Geom& gc, const T* pc, const Geom& gf, T* pf, 
 
 template <typename T>
 void launch_cell_gs_colour(const Geom& g, Coef<T> C, int parity, T* phi, const T* rhs,
-                           cudaStream_t s) {
+                           cudaStream_t s, int tpb) {
     const int nt = (g.n[0] / 2) * g.n[1] * g.n[2];
-    const int nb = nblk(nt);
-    if (g.dim == 2) k_cell_gs<2, T><<<nb, TPB, 0, s>>>(g, C, parity, phi, rhs, nt);
-    else k_cell_gs<3, T><<<nb, TPB, 0, s>>>(g, C, parity, phi, rhs, nt);
+    const int nb = (nt + tpb - 1) / tpb;
+    if (g.dim == 2) k_cell_gs<2, T><<<nb, tpb, 0, s>>>(g, C, parity, phi, rhs, nt);
+    else k_cell_gs<3, T><<<nb, tpb, 0, s>>>(g, C, parity, phi, rhs, nt);
 }
 
 template <typename T>
@@ -790,14 +790,14 @@ void launch_check_fields(int n, const double* rho, const double* mu, double* scr
 // explicit instantiations
 #define STK_INST(T)                                                                                \
     template void launch_vel_gs_colour<T>(const Geom&, Coef<T>, int, int, T*, const T*,          \
-                                          cudaStream_t);                                           \
+                                          cudaStream_t, int);                                      \
     template void launch_vel_residual<T>(const Geom&, Coef<T>, const T*, const T*, T*,           \
                                          cudaStream_t);                                            \
     template void launch_vel_restrict<T>(const Geom&, const T*, const Geom&, T*, cudaStream_t);  \
     template void launch_vel_prolong_add<T>(const Geom&, const T*, const Geom&, T*,              \
                                             cudaStream_t);                                         \
     template void launch_cell_gs_colour<T>(const Geom&, Coef<T>, int, T*, const T*,              \
-                                           cudaStream_t);                                          \
+                                           cudaStream_t, int);                                     \
     template void launch_cell_residual<T>(const Geom&, Coef<T>, const T*, const T*, T*,          \
                                           cudaStream_t);                                           \
     template void launch_cell_restrict<T>(const Geom&, const T*, const Geom&, T*, cudaStream_t); \

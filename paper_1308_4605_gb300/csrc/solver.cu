@@ -77,6 +77,7 @@ struct stk_handle {
     std::vector<float*> Z;
     double *bk = nullptr, *xk = nullptr, *tmp = nullptr;
     int lcoarse_d = 0, lcoarse_f = 0;        // first level run by the coarse kernel (FP64, FP32)
+    int tpb_d = 256, tpb_f = 256;            // threads per block of the colour kernels
     CLevel<double>* cld = nullptr;           // device copies of the level descriptors
     CLevel<float>* clf = nullptr;
     double* red = nullptr;    // reduction scratch (RED_BLOCKS * 36 doubles)
@@ -270,6 +271,7 @@ template <> Work<float> work_of<float>(const Level& L) { return L.wf; }
 template <typename T> int lcoarse_of(const stk_handle* h) {
     return sizeof(T) == 8 ? h->lcoarse_d : h->lcoarse_f;
 }
+template <typename T> int tpb_of(const stk_handle* h) { return sizeof(T) == 8 ? h->tpb_d : h->tpb_f; }
 template <typename T> const CLevel<T>* clev_of(const stk_handle* h);
 template <> const CLevel<double>* clev_of<double>(const stk_handle* h) { return h->cld; }
 template <> const CLevel<float>* clev_of<float>(const stk_handle* h) { return h->clf; }
@@ -289,7 +291,7 @@ void vel_sweeps(stk_handle* h, const Level& L, int nsweep, T* phi, const T* rhs,
         for (int a = 0; a < L.g.dim; ++a)
             for (int par = 0; par < 2; ++par) {
                 Scope sc(h, PF_VSMOOTH, bytes_vel_colour<T>(L.g, a), s);
-                launch_vel_gs_colour<T>(L.g, C, a, par, phi, rhs, s);
+                launch_vel_gs_colour<T>(L.g, C, a, par, phi, rhs, s, tpb_of<T>(h));
             }
 }
 
@@ -299,7 +301,7 @@ void cell_sweeps(stk_handle* h, const Level& L, int nsweep, T* phi, const T* rhs
     for (int it = 0; it < nsweep; ++it)
         for (int par = 0; par < 2; ++par) {
             Scope sc(h, PF_CSMOOTH, bytes_cell_colour<T>(L.g), s);
-            launch_cell_gs_colour<T>(L.g, C, par, phi, rhs, s);
+            launch_cell_gs_colour<T>(L.g, C, par, phi, rhs, s, tpb_of<T>(h));
         }
 }
 
@@ -1229,6 +1231,109 @@ int stk_solve_batched(int count, stk_handle* const* hs, const stk_solver_params*
         if (infos) infos[i] = insts[i].info;
     }
     return worst;
+}
+
+int stk_get_schedule(const stk_handle* h, int precision, stk_schedule* out) {
+    if (!h || !out || (precision != STK_FP64 && precision != STK_MIXED)) return STK_ERR_ARG;
+    out->coarse_level = precision == STK_FP64 ? h->lcoarse_d : h->lcoarse_f;
+    out->threads = precision == STK_FP64 ? h->tpb_d : h->tpb_f;
+    return STK_OK;
+}
+
+int stk_set_schedule(stk_handle* h, int precision, const stk_schedule* sc) {
+    if (!h) return STK_ERR_ARG;
+    if (!sc || (precision != STK_FP64 && precision != STK_MIXED))
+        return fail(h, STK_ERR_ARG, "bad schedule arguments");
+    if (sc->coarse_level < 0 || sc->coarse_level > (int)h->lev.size())
+        return fail(h, STK_ERR_ARG, "coarse_level must be in 0..%d", (int)h->lev.size());
+    if (sc->threads != 64 && sc->threads != 128 && sc->threads != 256 && sc->threads != 512)
+        return fail(h, STK_ERR_ARG, "threads must be 64, 128, 256 or 512");
+    clear_graphs(h);
+    if (precision == STK_FP64) {
+        h->lcoarse_d = sc->coarse_level;
+        h->tpb_d = sc->threads;
+    } else {
+        h->lcoarse_f = sc->coarse_level;
+        h->tpb_f = sc->threads;
+    }
+    return STK_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// time `reps` replays of the velocity + pressure V-cycle pair in precision T
+// captured as one graph, with the current schedule
+template <typename T>
+int time_vcycles(stk_handle* h, int reps, cudaStream_t s, float* ms) {
+    PBuf<T>& B = pbuf_of<T>(h);
+    const Level& L = h->lev[0];
+    MGParams mp;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    h->capturing = true;
+    vcycle_vel<T>(h, 0, B.in, B.xs, mp, h->cap);
+    vcycle_cell<T>(h, 0, B.in + L.g.nvel, B.bc, mp, h->cap);
+    h->capturing = false;
+    CK(cudaStreamEndCapture(h->cap, &g));
+    cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(h, STK_ERR_CUDA, "autotune instantiate: %s", cudaGetErrorString(e));
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaGraphLaunch(ex, s);   // warm-up
+    cudaEventRecord(a, s);
+    for (int r = 0; r < reps; ++r) cudaGraphLaunch(ex, s);
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    cudaEventElapsedTime(ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaGraphExecDestroy(ex);
+    CKL();
+    return STK_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int stk_autotune(stk_handle* h, int precision, stk_schedule* best, void* stream) {
+    if (!h) return STK_ERR_ARG;
+    if (!h->coef_set) return fail(h, STK_ERR_STATE, "coefficients not set");
+    if (precision != STK_FP64 && precision != STK_MIXED) return fail(h, STK_ERR_ARG, "bad precision");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(cudaSetDevice(h->device));
+    const bool prof = h->prof;
+    h->prof = false;
+    stk_schedule cur;
+    stk_get_schedule(h, precision, &cur);
+    stk_schedule bs = cur;
+    float bms = 1e30f;
+    const int nl = (int)h->lev.size();
+    const int threads[3] = {128, 256, 512};
+    for (int lc = 0; lc <= nl; ++lc) {
+        // the single-block kernel only pays on small levels
+        if (lc < nl && h->lev[lc].g.ncell > 65536) continue;
+        for (int ti = 0; ti < 3; ++ti) {
+            stk_schedule c{lc, threads[ti]};
+            int rc = stk_set_schedule(h, precision, &c);
+            if (rc) { h->prof = prof; return rc; }
+            float ms = 0.f;
+            rc = precision == STK_FP64 ? time_vcycles<double>(h, 3, s, &ms)
+                                       : time_vcycles<float>(h, 3, s, &ms);
+            if (rc) { h->prof = prof; return rc; }
+            if (ms < bms) {
+                bms = ms;
+                bs = c;
+            }
+        }
+    }
+    h->prof = prof;
+    int rc = stk_set_schedule(h, precision, &bs);
+    if (best) *best = bs;
+    return rc;
 }
 
 int stk_profile(stk_handle* h, int enable) {

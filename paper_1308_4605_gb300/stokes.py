@@ -51,6 +51,10 @@ class stk_solve_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class stk_schedule(ctypes.Structure):
+    _fields_ = [("coarse_level", ctypes.c_int), ("threads", ctypes.c_int)]
+
+
 class stk_batch_io(ctypes.Structure):
     _fields_ = [("b_u", ctypes.POINTER(ctypes.c_void_p)), ("b_p", ctypes.c_void_p),
                 ("x_u", ctypes.POINTER(ctypes.c_void_p)), ("x_p", ctypes.c_void_p)]
@@ -82,6 +86,9 @@ def _load():
         "stk_profile": (I, [P, I]),
         "stk_kernel_launches": (ctypes.c_longlong, [P]),
         "stk_gradient": (I, [P, PP, PP, P, P, P]),
+        "stk_get_schedule": (I, [P, I, ctypes.POINTER(stk_schedule)]),
+        "stk_set_schedule": (I, [P, I, ctypes.POINTER(stk_schedule)]),
+        "stk_autotune": (I, [P, I, ctypes.POINTER(stk_schedule), P]),
         "stk_solve_batched": (I, [I, ctypes.POINTER(P), ctypes.POINTER(stk_solver_params),
                                   ctypes.POINTER(stk_batch_io), ctypes.POINTER(stk_solve_info), P]),
         "stk_pressure_vcycle_noalloc": (I, [I, ctypes.POINTER(I), D, ctypes.POINTER(I), P, P, P, P]),
@@ -99,7 +106,7 @@ _lib = _load()
 EXPORTED = ["stk_default_params", "stk_create", "stk_destroy", "stk_last_error", "stk_face_length",
             "stk_cell_length", "stk_set_coefficients", "stk_apply_operator",
             "stk_apply_preconditioner", "stk_velocity_vcycle", "stk_pressure_vcycle", "stk_solve",
-            "stk_profile", "stk_profile_read", "stk_kernel_launches", "stk_pressure_vcycle_noalloc", "stk_gradient", "stk_solve_batched"]
+            "stk_profile", "stk_profile_read", "stk_kernel_launches", "stk_pressure_vcycle_noalloc", "stk_gradient", "stk_solve_batched", "stk_get_schedule", "stk_set_schedule", "stk_autotune"]
 
 
 def library():
@@ -245,6 +252,23 @@ def stk_solve_batched(handles, params, b_us, b_ps, x_us, x_ps, stream=None):
         bad = [i for i in range(count) if infos[i].status not in (STK_OK, STK_ERR_NOT_CONVERGED)]
         _check(handles[bad[0]] if bad else None, rc)
     return [infos[i].as_dict() for i in range(count)]
+
+
+def stk_get_schedule(h, precision):
+    sc = stk_schedule()
+    _check(h, _lib.stk_get_schedule(h, int(precision), ctypes.byref(sc)))
+    return {"coarse_level": sc.coarse_level, "threads": sc.threads}
+
+
+def stk_set_schedule(h, precision, coarse_level, threads):
+    sc = stk_schedule(int(coarse_level), int(threads))
+    return _check(h, _lib.stk_set_schedule(h, int(precision), ctypes.byref(sc)))
+
+
+def stk_autotune(h, precision, stream=None):
+    sc = stk_schedule()
+    _check(h, _lib.stk_autotune(h, int(precision), ctypes.byref(sc), _stream(stream)))
+    return {"coarse_level": sc.coarse_level, "threads": sc.threads}
 
 
 def stk_profile(h, enable):

@@ -81,3 +81,33 @@ def test_batched_rejects_duplicate_handles(S):
     with pytest.raises(S.StokesError):
         S.stk_solve_batched([sv.handle, sv.handle], S.stk_default_params(), [bu, bu], [bp, bp], [xu, xu], [xp, xp])
     sv.close()
+
+
+def test_schedules_change_timing_not_results(S, tmp_path):
+    """Every multigrid schedule (coarse-kernel level, colour block size) gives
+    bitwise the same solution; the autotuner picks one and caches it."""
+    from paper_1308_4605_gb300 import tuning
+    pr = wl.config_c4_instance(5, 128)
+    sv = S.StokesSolver(2, pr.n[:2], pr.bc[:4], pr.h)
+    sv.set_coefficients(_t(pr.rho), _t(pr.mu), pr.theta)
+    bu = [_t(x) for x in pr.b_u]
+    bp = _t(pr.b_p)
+    ref = None
+    nlev = 7                      # 128, 64, ..., 2
+    for prec in (0, 1):
+        ref = None
+        for lc, th in ((nlev, 256), (0, 256), (2, 128), (3, 512), (4, 64)):
+            S.stk_set_schedule(sv.handle, prec, lc, th)
+            xu, xp, info = sv.solve(bu, bp, precision=prec)
+            assert info["converged"]
+            if ref is None:
+                ref = (xu, xp, info["iterations"])
+            else:
+                assert info["iterations"] == ref[2]
+                assert all(torch.equal(a, b) for a, b in zip(xu, ref[0])) and torch.equal(xp, ref[1])
+        path = str(tmp_path / "sched.json")
+        sc = tuning.tune(sv, prec, path)
+        assert 0 <= sc["coarse_level"] <= nlev and sc["threads"] in (128, 256, 512)
+        assert tuning.tune(sv, prec, path) == sc          # cache hit
+        assert S.stk_get_schedule(sv.handle, prec) == sc
+    sv.close()
