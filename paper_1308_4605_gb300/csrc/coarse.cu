@@ -153,8 +153,7 @@ __global__ void __launch_bounds__(CT) k_coarse_cell(const CLevel<T>* __restrict_
         for (int t = threadIdx.x; t < g.ncell; t += CT) {
             int q[3];
             decode_cell(g, t, q);
-            T d;
-            res[t] = rhs[t] - poisson_cell<DIM, T, T>(g, C, q, phi, d);
+            res[t] = cell_res_point<DIM, T>(g, C, q, phi, rhs);
         }
         __syncthreads();
         const Geom& gc = gsh[1];

@@ -83,6 +83,7 @@ struct Coef {
     T* mu_e[3];
     T* invd_u;
     T* invd_p;
+    T* diag_u;   // the diagonal of A itself (FP64 hierarchy only; null in FP32)
 };
 
 // ---- launch wrappers (kernels.cu); all asynchronous on `s` -------------------

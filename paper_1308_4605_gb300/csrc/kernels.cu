@@ -202,12 +202,14 @@ __global__ void k_inverse_diagonals(Geom g, Coef<double> C, Segs sg) {
     int f = g.foff[s] + t;
     if (wall_face(g, s, q)) {
         C.invd_u[f] = 0.0;
+        if (C.diag_u) C.diag_u[f] = 0.0;
         return;
     }
     double dsum = 0.0;
     visc_h2_any<DIM, double, double, true>(s, g, C, q, C.alpha, dsum);
     double d = C.alpha[f] + g.ih2 * dsum;
     C.invd_u[f] = d != 0.0 ? 1.0 / d : 0.0;
+    if (C.diag_u) C.diag_u[f] = d;
 }
 
 template <typename TA, typename TB>
@@ -248,12 +250,12 @@ __global__ void k_stokes_matvec(Geom g, Coef<double> C, Segs sg, const TV* __res
         return;
     }
     double dsum;
-    const double L = visc_h2_any<DIM, double, TV, false>(s, g, C, q, x, dsum);
+    const double N = visc_offdiag_any<DIM, double, TV, false>(s, g, C, q, x, dsum);
     int qm[3] = {q[0], q[1], q[2]};
     qm[s] = step(g, s, q[s], -1);
     double Mx = g.ih * (double(xp[cidx(g, q)]) - double(xp[cidx(g, qm)]));
-    Mx = fma(-g.ih2, L, Mx);
-    Mx = fma(ld(C.alpha + f), double(x[f]), Mx);
+    Mx = fma(-g.ih2, N, Mx);
+    Mx = fma(ld(C.diag_u + f), double(x[f]), Mx);
     y[f] = b ? b[f] - Mx : Mx;
 }
 
@@ -336,8 +338,7 @@ __global__ void __launch_bounds__(TPB) k_cell_residual(Geom g, Coef<T> C, const 
     if (t >= g.ncell) return;
     int q[3];
     decode_cell(g, t, q);
-    T d;
-    res[t] = rhs[t] - poisson_cell<DIM, T, T>(g, C, q, phi, d);
+    res[t] = cell_res_point<DIM, T>(g, C, q, phi, rhs);
 }
 
 template <int DIM, typename T>
@@ -412,12 +413,10 @@ __global__ void k_vel_correction_rhs(Geom g, Coef<T> C, Segs sg, const T* __rest
         out[f] = T(0);
         return;
     }
-    T dsum;
-    const T L = visc_h2_any<DIM, T, T, false>(s, g, C, q, u, dsum);
     int qm[3] = {q[0], q[1], q[2]};
     qm[s] = step(g, s, q[s], -1);
     T grad = (p[cidx(g, q)] - p[cidx(g, qm)]) * gih<T>(g);
-    out[f] = b[f] - grad - fma(ld(C.alpha + f), u[f], -gih2<T>(g) * L);
+    out[f] = vel_res_point<DIM, T>(s, g, C, q, u, b) - grad;
 }
 
 template <typename T>
@@ -635,6 +634,7 @@ void launch_convert(int n, const TA* a, TB* b, cudaStream_t s) {
 }
 
 void launch_convert_coefficients(const Geom& g, Coef<double> C, Coef<float> F, cudaStream_t s) {
+    // F.diag_u stays null: the FP32 kernels form the diagonal on the fly
     launch_convert(g.nvel, C.alpha, F.alpha, s);
     launch_convert(g.nvel, C.beta, F.beta, s);
     launch_convert(g.ncell, C.mu_c, F.mu_c, s);

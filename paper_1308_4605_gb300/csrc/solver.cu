@@ -965,6 +965,8 @@ int stk_create(int dim, const int* n, double hh, const int* bc, stk_handle** out
         CKC(dalloc(h, &L.cd.mu_c, g.ncell));
         CKC(dalloc(h, &L.cd.invd_u, g.nvel));
         CKC(dalloc(h, &L.cd.invd_p, g.ncell));
+        CKC(dalloc(h, &L.cd.diag_u, g.nvel));
+        L.cf.diag_u = nullptr;
         CKC(dalloc(h, &L.cf.alpha, g.nvel));
         CKC(dalloc(h, &L.cf.beta, g.nvel));
         CKC(dalloc(h, &L.cf.mu_c, g.ncell));

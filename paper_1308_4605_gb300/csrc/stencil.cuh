@@ -145,6 +145,93 @@ __device__ __forceinline__ T visc_h2_any(int a, const Geom& g, const Coef<T>& C,
     return visc_h2<DIM, DIM == 3 ? 2 : 1, T, TV, DIAG>(g, C, q, phi, dsum);
 }
 
+// The same operator split into its off-diagonal part: h^2 L_A = N - phi_A dsum,
+//   N    = 2 (mu_hi phi_A[+a] + mu_lo phi_A[-a])
+//          + sum_B mu_e,hi (phi_A[+b] + dphi_B/dx_A|hi) + mu_e,lo (phi_A[-b] - dphi_B/dx_A|lo)
+//   dsum = 2 (mu_hi + mu_lo) + sum_B (f_hi mu_e,hi + f_lo mu_e,lo),
+// with phi_A beyond a wall omitted from N (f = 2 there: the one-sided
+// derivative over h/2, Sec. 3.1; f = 1 inside).  A Gauss-Seidel step is then
+// phi_A <- (rhs + N / h^2) / (alpha + dsum / h^2) with no term in the old
+// phi_A, and the operator is A phi = diag phi_A - N / h^2.
+template <int DIM, int A, typename T, typename TV, bool DIAG>
+__device__ __forceinline__ T visc_offdiag_h2(const Geom& g, const Coef<T>& C, const int q[3],
+                                             const TV* phi, T& dsum) {
+    int qp[3] = {q[0], q[1], q[2]};
+    int qm[3] = {q[0], q[1], q[2]};
+    qp[A] = step(g, A, q[A], 1);
+    qm[A] = step(g, A, q[A], -1);
+    const T pp = T(phi[fidx(g, A, qp)]);
+    const T pm = T(phi[fidx(g, A, qm)]);
+    const T mh = ld(C.mu_c + cidx(g, q));
+    const T ml = ld(C.mu_c + cidx(g, qm));
+    T N = mh * pp;
+    N = fma(ml, pm, N);
+    N = N + N;
+    if (DIAG) dsum = T(2) * (mh + ml);
+#pragma unroll
+    for (int B = 0; B < DIM; ++B) {
+        if (B == A) continue;
+        const int P = A + B - 1;   // edge pair index of {A, B}
+        const bool wlo = !g.per[B] && q[B] == 0;
+        const bool whi = !g.per[B] && q[B] == g.n[B] - 1;
+        int qe[3] = {q[0], q[1], q[2]};
+        qe[B] = step(g, B, q[B], 1);
+        const T mlo = ld(C.mu_e[P] + eidx(g, P, q));
+        const T mhi = ld(C.mu_e[P] + eidx(g, P, qe));
+        // d phi_B / dx_A on the two edges: B-faces in A-cells q[A] and q[A]-1
+        int r0[3] = {q[0], q[1], q[2]};
+        r0[A] = qm[A];
+        int r2[3] = {qe[0], qe[1], qe[2]};
+        r2[A] = qm[A];
+        const T xlo = T(phi[fidx(g, B, q)]) - T(phi[fidx(g, B, r0)]);
+        const T xhi = T(phi[fidx(g, B, qe)]) - T(phi[fidx(g, B, r2)]);
+        T shi = xhi, slo = -xlo;
+        if (!whi) shi += T(phi[fidx(g, A, qe)]);
+        if (!wlo) {
+            int qb[3] = {q[0], q[1], q[2]};
+            qb[B] = step(g, B, q[B], -1);
+            slo += T(phi[fidx(g, A, qb)]);
+        }
+        N = fma(mhi, shi, N);
+        N = fma(mlo, slo, N);
+        if (DIAG) dsum += (whi ? T(2) : T(1)) * mhi + (wlo ? T(2) : T(1)) * mlo;
+    }
+    return N;
+}
+
+template <int DIM, typename T, typename TV, bool DIAG>
+__device__ __forceinline__ T visc_offdiag_any(int a, const Geom& g, const Coef<T>& C,
+                                              const int q[3], const TV* phi, T& dsum) {
+    if (a == 0) return visc_offdiag_h2<DIM, 0, T, TV, DIAG>(g, C, q, phi, dsum);
+    if (a == 1) return visc_offdiag_h2<DIM, 1, T, TV, DIAG>(g, C, q, phi, dsum);
+    return visc_offdiag_h2<DIM, DIM == 3 ? 2 : 1, T, TV, DIAG>(g, C, q, phi, dsum);
+}
+
+// Off-diagonal part of h^2 L_rho at cell q: Nc = sum_a (beta_hi phi[+a] +
+// beta_lo phi[-a]) and bsum = sum_a (beta_hi + beta_lo), so that
+// h^2 (L_rho phi)_q = Nc - bsum phi_q (beta = 0 on wall faces).
+template <int DIM, typename T, typename TV>
+__device__ __forceinline__ T poisson_offdiag_h2(const Geom& g, const Coef<T>& C, const int q[3],
+                                                const TV* phi, T& bsum) {
+    T N = T(0);
+    bsum = T(0);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        int fh[3] = {q[0], q[1], q[2]};
+        fh[a] = g.per[a] ? wrapm(q[a] + 1, g.n[a]) : q[a] + 1;
+        const T bh = ld(C.beta + fidx(g, a, fh));
+        const T bl = ld(C.beta + fidx(g, a, q));
+        int ch[3] = {q[0], q[1], q[2]};
+        int cl[3] = {q[0], q[1], q[2]};
+        ch[a] = g.per[a] ? wrapm(q[a] + 1, g.n[a]) : min(q[a] + 1, g.n[a] - 1);
+        cl[a] = g.per[a] ? wrapm(q[a] - 1, g.n[a]) : max(q[a] - 1, 0);
+        N = fma(bh, T(phi[cidx(g, ch)]), N);
+        N = fma(bl, T(phi[cidx(g, cl)]), N);
+        bsum += bh + bl;
+    }
+    return N;
+}
+
 // (L_rho phi) at cell q and its diagonal; beta = 0 on wall faces.
 template <int DIM, typename T, typename TV>
 __device__ __forceinline__ T poisson_cell(const Geom& g, const Coef<T>& C, const int q[3],
@@ -178,23 +265,24 @@ __device__ __forceinline__ void vel_gs_point(const Geom& g, const Coef<T>& C, co
                                              T* phi, const T* rhs) {
     constexpr bool F32 = sizeof(T) == 4;
     T dsum;
-    const T L = visc_h2<DIM, A, T, T, F32>(g, C, q, phi, dsum);
+    const T N = visc_offdiag_h2<DIM, A, T, T, F32>(g, C, q, phi, dsum);
     const int f = fidx(g, A, q);
-    const T p = phi[f];
-    const T al = ld(C.alpha + f);
     const T ih2 = gih2<T>(g);
-    const T res = rhs[f] - fma(al, p, -ih2 * L);
-    if constexpr (F32) phi[f] = p + res / fma(ih2, dsum, al);
-    else phi[f] = fma(res, ld(C.invd_u + f), p);
+    const T num = fma(ih2, N, rhs[f]);
+    if constexpr (F32) phi[f] = num / fma(ih2, dsum, ld(C.alpha + f));
+    else phi[f] = num * ld(C.invd_u + f);
 }
 
 template <int DIM, typename T>
 __device__ __forceinline__ T vel_res_point(int a, const Geom& g, const Coef<T>& C, const int q[3],
                                            const T* phi, const T* rhs) {
+    constexpr bool F32 = sizeof(T) == 4;
     const int f = fidx(g, a, q);
     T dsum;
-    const T L = visc_h2_any<DIM, T, T, false>(a, g, C, q, phi, dsum);
-    return rhs[f] - fma(ld(C.alpha + f), phi[f], -gih2<T>(g) * L);
+    const T N = visc_offdiag_any<DIM, T, T, F32>(a, g, C, q, phi, dsum);
+    const T ih2 = gih2<T>(g);
+    const T diag = F32 ? fma(ih2, dsum, ld(C.alpha + f)) : ld(C.diag_u + f);
+    return fma(ih2, N, rhs[f]) - diag * phi[f];
 }
 
 // 6-point (2D) / 12-point (3D) restriction to the interior coarse A-face Q:
@@ -296,11 +384,22 @@ __device__ __forceinline__ T vel_prolong_point(const Geom& gc, const int q[3],
 template <int DIM, typename T>
 __device__ __forceinline__ void cell_gs_point(const Geom& g, const Coef<T>& C, const int q[3],
                                               T* phi, const T* rhs) {
-    T d;
-    const T L = poisson_cell<DIM, T, T>(g, C, q, phi, d);
+    T bsum;
+    const T N = poisson_offdiag_h2<DIM, T, T>(g, C, q, phi, bsum);
     const int c = cidx(g, q);
-    if constexpr (sizeof(T) == 4) phi[c] += (rhs[c] - L) / d;
-    else phi[c] = fma(rhs[c] - L, ld(C.invd_p + c), phi[c]);
+    const T ih2 = gih2<T>(g);
+    const T num = fma(-ih2, N, rhs[c]);   // (rhs - off-diagonal part) / diag
+    if constexpr (sizeof(T) == 4) phi[c] = num / (-ih2 * bsum);
+    else phi[c] = num * ld(C.invd_p + c);
+}
+
+template <int DIM, typename T>
+__device__ __forceinline__ T cell_res_point(const Geom& g, const Coef<T>& C, const int q[3],
+                                            const T* phi, const T* rhs) {
+    T bsum;
+    const T N = poisson_offdiag_h2<DIM, T, T>(g, C, q, phi, bsum);
+    const int c = cidx(g, q);
+    return rhs[c] - gih2<T>(g) * fma(-bsum, T(phi[c]), N);
 }
 
 template <int DIM, typename T>
