@@ -202,17 +202,19 @@ int stk_set_schedule(stk_handle* h, int precision, const stk_schedule* sc);
 int stk_autotune(stk_handle* h, int precision, stk_schedule* best, void* stream);
 
 /* Per-kernel timing of the calls above with CUDA events on the call's
- * stream.  stk_profile(h, 1) starts collecting (and clears), 0 stops.
- * stk_profile_read returns, for kernel family k (0 <= k < STK_NPROF), its
- * name, its number of launches, its summed device time in ms and the
- * algorithmic bytes it moved (reads of every input word and writes of every
- * output word, once per launch).  Returns -1 when k is out of range. */
-#define STK_NPROF 16
+ * stream (event nodes inside the preconditioner graphs).  stk_profile(h, 1)
+ * starts collecting (and clears), 0 stops.  stk_profile_read returns, for
+ * kernel family k (0 <= k < STK_NPROF), its name, its number of launches, its
+ * summed device time in ms, the algorithmic bytes it moved (reads of every
+ * input word and writes of every output word, once per launch) and, for the
+ * Gauss-Seidel families, its floating-point operations.  Level-0 smoothing
+ * has families of its own.  Returns -1 when k is out of range. */
+#define STK_NPROF 20
 int stk_profile(stk_handle* h, int enable);
 /* Number of CUDA kernels this handle has launched since it was created. */
 long long stk_kernel_launches(const stk_handle* h);
 int stk_profile_read(stk_handle* h, int k, const char** name, long long* launches,
-                     double* ms, double* bytes);
+                     double* ms, double* bytes, double* flops);
 
 /* Pressure V-cycle for callers that cannot allocate device memory.
  * (No counterpart in the paper: this is a deployment variant of

@@ -25,6 +25,7 @@ thread_local std::string g_create_error;
 struct ProfRec {
     int cat;
     double bytes;
+    double flops;
     cudaEvent_t a, b;
 };
 
@@ -32,11 +33,13 @@ const char* kProfNames[STK_NPROF] = {
     "stokes_matvec",    "vel_smooth_colour", "vel_residual",  "vel_restrict",
     "vel_prolong_add",  "cell_smooth_colour", "cell_residual", "cell_restrict",
     "cell_prolong_add", "precond_algebra",   "mean_removal",  "arnoldi_multidot",
-    "arnoldi_update",   "krylov_combine",    "convert",       "coarse_levels"};
+    "arnoldi_update",   "krylov_combine",    "convert",       "coarse_levels",
+    "vel_smooth_colour_l0", "cell_smooth_colour_l0", "unused_18", "unused_19"};
 
 enum {
     PF_MATVEC = 0, PF_VSMOOTH, PF_VRES, PF_VRESTR, PF_VPROL, PF_CSMOOTH, PF_CRES, PF_CRESTR,
-    PF_CPROL, PF_ALG, PF_MEAN, PF_MDOT, PF_UPD, PF_COMB, PF_CONV, PF_COARSE
+    PF_CPROL, PF_ALG, PF_MEAN, PF_MDOT, PF_UPD, PF_COMB, PF_CONV, PF_COARSE, PF_VSMOOTH0,
+    PF_CSMOOTH0
 };
 
 template <typename T>
@@ -104,7 +107,7 @@ struct stk_handle {
     std::vector<cudaEvent_t> evpool;
     size_t evnext = 0;
     long long plaunch[STK_NPROF] = {};
-    double pms[STK_NPROF] = {}, pbytes[STK_NPROF] = {};
+    double pms[STK_NPROF] = {}, pbytes[STK_NPROF] = {}, pflops[STK_NPROF] = {};
 };
 
 namespace {
@@ -187,12 +190,15 @@ struct Scope {
     stk_handle* h;
     ProfRec rec{};
     cudaStream_t s;
-    Scope(stk_handle* h_, int cat, double bytes, cudaStream_t s_, int kernels = 1) : h(h_), s(s_) {
+    Scope(stk_handle* h_, int cat, double bytes, cudaStream_t s_, int kernels = 1,
+          double flops = 0.0)
+        : h(h_), s(s_) {
         if (h->capturing) h->cap_kernels += kernels;
         else h->nkern += kernels;
         if (!h->prof) return;
         rec.cat = cat;
         rec.bytes = bytes;
+        rec.flops = flops;
         rec.a = next_event();
         rec.b = next_event();
         record(rec.a);
@@ -232,6 +238,7 @@ void prof_flush(stk_handle* h) {
         h->plaunch[r.cat] += 1;
         h->pms[r.cat] += ms;
         h->pbytes[r.cat] += r.bytes;
+        h->pflops[r.cat] += r.flops;
     }
     h->recs.clear();
     h->evnext = 0;
@@ -284,13 +291,31 @@ struct MGParams {
     int ncoarse = 8;
 };
 
+// Floating-point operations of one Gauss-Seidel point update (adds + muls +
+// 2 x fmas), counted with ncu (sm__sass_thread_inst_executed_op_*) on the
+// 3D kernels: FP64 velocity 25, FP32 velocity 46 (the FP32 division is a
+// short FMA sequence), FP64 cell 15; the 2D velocity stencil has one
+// transverse axis instead of two (8 fewer FP64 operations).
+template <typename T>
+double flops_vel_point(int dim) {
+    if (sizeof(T) == 8) return dim == 3 ? 25.0 : 17.0;
+    return dim == 3 ? 46.0 : 38.0;
+}
+double updated_faces(const Geom& g, int a) {   // unknown a-faces of one colour
+    double n = double(g.fe[a][0]) * g.fe[a][1] * g.fe[a][2];
+    if (!g.per[a]) n -= 2.0 * double(g.fsize[a]) / g.fe[a][a];
+    return 0.5 * n;
+}
+
 template <typename T>
 void vel_sweeps(stk_handle* h, const Level& L, int nsweep, T* phi, const T* rhs, cudaStream_t s) {
     Coef<T> C = coef_of<T>(L);
+    const bool fine = &L == &h->lev[0];
     for (int it = 0; it < nsweep; ++it)
         for (int a = 0; a < L.g.dim; ++a)
             for (int par = 0; par < 2; ++par) {
-                Scope sc(h, PF_VSMOOTH, bytes_vel_colour<T>(L.g, a), s);
+                Scope sc(h, fine ? PF_VSMOOTH0 : PF_VSMOOTH, bytes_vel_colour<T>(L.g, a), s, 1,
+                         flops_vel_point<T>(L.g.dim) * updated_faces(L.g, a));
                 launch_vel_gs_colour<T>(L.g, C, a, par, phi, rhs, s, tpb_of<T>(h));
             }
 }
@@ -298,9 +323,11 @@ void vel_sweeps(stk_handle* h, const Level& L, int nsweep, T* phi, const T* rhs,
 template <typename T>
 void cell_sweeps(stk_handle* h, const Level& L, int nsweep, T* phi, const T* rhs, cudaStream_t s) {
     Coef<T> C = coef_of<T>(L);
+    const bool fine = &L == &h->lev[0];
     for (int it = 0; it < nsweep; ++it)
         for (int par = 0; par < 2; ++par) {
-            Scope sc(h, PF_CSMOOTH, bytes_cell_colour<T>(L.g), s);
+            Scope sc(h, fine ? PF_CSMOOTH0 : PF_CSMOOTH, bytes_cell_colour<T>(L.g), s, 1,
+                     (sizeof(T) == 8 ? 15.0 : 40.0) * 0.5 * L.g.ncell);
             launch_cell_gs_colour<T>(L.g, C, par, phi, rhs, s, tpb_of<T>(h));
         }
 }
@@ -1346,6 +1373,7 @@ int stk_profile(stk_handle* h, int enable) {
             h->plaunch[k] = 0;
             h->pms[k] = 0.0;
             h->pbytes[k] = 0.0;
+            h->pflops[k] = 0.0;
         }
     }
     h->prof = enable != 0;
@@ -1377,13 +1405,14 @@ int stk_gradient(stk_handle* h, const double* const* u, const double* const* lam
 }
 
 int stk_profile_read(stk_handle* h, int k, const char** name, long long* launches, double* ms,
-                     double* bytes) {
+                     double* bytes, double* flops) {
     if (!h || k < 0 || k >= STK_NPROF) return -1;
     prof_flush(h);
     if (name) *name = kProfNames[k];
     if (launches) *launches = h->plaunch[k];
     if (ms) *ms = h->pms[k];
     if (bytes) *bytes = h->pbytes[k];
+    if (flops) *flops = h->pflops[k];
     return STK_OK;
 }
 

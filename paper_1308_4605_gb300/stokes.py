@@ -26,7 +26,7 @@ STK_ERR_ARG, STK_ERR_SIZE, STK_ERR_CUDA, STK_ERR_NOT_CONVERGED = -1, -2, -3, -4
 STK_ERR_NONFINITE, STK_ERR_TIMEOUT, STK_ERR_STATE = -5, -6, -7
 STK_P1, STK_P2, STK_P3, STK_P4, STK_P5 = 1, 2, 3, 4, 5
 STK_FP64, STK_MIXED = 0, 1
-STK_NPROF = 16
+STK_NPROF = 20
 
 
 class StokesError(RuntimeError):
@@ -93,7 +93,7 @@ def _load():
                                   ctypes.POINTER(stk_batch_io), ctypes.POINTER(stk_solve_info), P]),
         "stk_pressure_vcycle_noalloc": (I, [I, ctypes.POINTER(I), D, ctypes.POINTER(I), P, P, P, P]),
         "stk_profile_read": (I, [P, I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong),
-                                 ctypes.POINTER(D), ctypes.POINTER(D)]),
+                                 ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -302,12 +302,13 @@ def stk_profile_read(h, k):
     launches = ctypes.c_longlong()
     ms = ctypes.c_double()
     nbytes = ctypes.c_double()
+    flops = ctypes.c_double()
     rc = _lib.stk_profile_read(h, int(k), ctypes.byref(name), ctypes.byref(launches),
-                               ctypes.byref(ms), ctypes.byref(nbytes))
+                               ctypes.byref(ms), ctypes.byref(nbytes), ctypes.byref(flops))
     if rc != 0:
         raise StokesError(rc, "profile index out of range")
     return {"name": name.value.decode(), "launches": launches.value, "ms": ms.value,
-            "bytes": nbytes.value}
+            "bytes": nbytes.value, "flops": flops.value}
 
 
 # ------------------------------------------------------------ convenience
