@@ -59,6 +59,7 @@ __device__ __forceinline__ void load_geom(Geom* dst, const Geom* src) {
 template <int DIM, typename T>
 __global__ void __launch_bounds__(CT) k_coarse_vel(const CLevel<T>* __restrict__ Ls, int nlev,
                                                    const T* rhs0, T* phi0, int nu, int ncoarse) {
+    pdl_entry();
     __shared__ Geom gsh[2];
     // down: pre-smoothing, residual, restriction
     for (int l = 0; l < nlev; ++l) {
@@ -133,6 +134,7 @@ __global__ void __launch_bounds__(CT) k_coarse_vel(const CLevel<T>* __restrict__
 template <int DIM, typename T>
 __global__ void __launch_bounds__(CT) k_coarse_cell(const CLevel<T>* __restrict__ Ls, int nlev,
                                                     const T* rhs0, T* phi0, int nu, int ncoarse) {
+    pdl_entry();
     __shared__ Geom gsh[2];
     for (int l = 0; l < nlev; ++l) {
         load_geom(&gsh[0], &Ls[l].g);
@@ -191,15 +193,15 @@ __global__ void __launch_bounds__(CT) k_coarse_cell(const CLevel<T>* __restrict_
 template <typename T>
 void launch_coarse_vcycle_vel(int dim, const CLevel<T>* L, int nlev, const T* rhs, T* phi, int nu,
                               int ncoarse, cudaStream_t s) {
-    if (dim == 2) k_coarse_vel<2, T><<<1, CT, 0, s>>>(L, nlev, rhs, phi, nu, ncoarse);
-    else k_coarse_vel<3, T><<<1, CT, 0, s>>>(L, nlev, rhs, phi, nu, ncoarse);
+    if (dim == 2) launch_pdl(k_coarse_vel<2, T>, dim3(1), dim3(CT), s, L, nlev, rhs, phi, nu, ncoarse);
+    else launch_pdl(k_coarse_vel<3, T>, dim3(1), dim3(CT), s, L, nlev, rhs, phi, nu, ncoarse);
 }
 
 template <typename T>
 void launch_coarse_vcycle_cell(int dim, const CLevel<T>* L, int nlev, const T* rhs, T* phi, int nu,
                                int ncoarse, cudaStream_t s) {
-    if (dim == 2) k_coarse_cell<2, T><<<1, CT, 0, s>>>(L, nlev, rhs, phi, nu, ncoarse);
-    else k_coarse_cell<3, T><<<1, CT, 0, s>>>(L, nlev, rhs, phi, nu, ncoarse);
+    if (dim == 2) launch_pdl(k_coarse_cell<2, T>, dim3(1), dim3(CT), s, L, nlev, rhs, phi, nu, ncoarse);
+    else launch_pdl(k_coarse_cell<3, T>, dim3(1), dim3(CT), s, L, nlev, rhs, phi, nu, ncoarse);
 }
 
 template void launch_coarse_vcycle_vel<double>(int, const CLevel<double>*, int, const double*,

@@ -86,6 +86,41 @@ struct Coef {
     T* diag_u;   // the diagonal of A itself (FP64 hierarchy only; null in FP32)
 };
 
+// Launch with programmatic dependent launch allowed: the kernel may be
+// scheduled while its predecessor on the stream is still running; every
+// kernel of this library starts with pdl_entry() (stencil.cuh), which lets
+// its own dependents be scheduled and then waits until the predecessor grid
+// has completed and its memory is visible.  Inside a captured graph the
+// same holds through programmatic edges.  Semantics are those of ordinary
+// stream order; only launch latency is hidden.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t s,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+// First statement of every kernel of this library: let the next kernel on
+// the stream be scheduled, then wait until the previous grid has completed
+// and its memory is visible (a no-op without programmatic dependent launch).
+__device__ __forceinline__ void pdl_entry() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// zero n elements (a kernel, so that it takes part in the launch chain)
+template <typename T>
+void launch_zero(int n, T* x, cudaStream_t s);
+
 // ---- launch wrappers (kernels.cu); all asynchronous on `s` -------------------
 
 // coefficients

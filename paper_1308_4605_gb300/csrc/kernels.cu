@@ -64,6 +64,7 @@ __device__ __forceinline__ int seg_of(const Segs& s, int blk, int& local) {
 // ------------------------------------------------------------------ coefficients
 __global__ void k_fine_faces(Geom g, const double* __restrict__ rho, double theta,
                              double* alpha, double* beta) {
+    pdl_entry();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.nvel) return;
     int a = 0;
@@ -86,6 +87,7 @@ __global__ void k_fine_faces(Geom g, const double* __restrict__ rho, double thet
 // edge, zero on free-slip walls and on edges lying on two walls.
 __global__ void k_fine_edges(Geom g, int p, int a, int b, const double* __restrict__ mu,
                              double* mu_e) {
+    pdl_entry();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.esize[p]) return;
     int q[3];
@@ -123,6 +125,7 @@ __global__ void k_fine_edges(Geom g, int p, int a, int b, const double* __restri
 // Coarse face coefficients: mean of the overlying fine faces (App. C).
 __global__ void k_coarsen_faces(Geom gf, Geom gc, const double* __restrict__ af,
                                 const double* __restrict__ bf, double* ac, double* bcoef) {
+    pdl_entry();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= gc.nvel) return;
     int a = 0;
@@ -147,6 +150,7 @@ __global__ void k_coarsen_faces(Geom gf, Geom gc, const double* __restrict__ af,
 }
 
 __global__ void k_coarsen_cells(Geom gf, Geom gc, const double* __restrict__ mf, double* mc) {
+    pdl_entry();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= gc.ncell) return;
     int Q[3];
@@ -166,6 +170,7 @@ __global__ void k_coarsen_cells(Geom gf, Geom gc, const double* __restrict__ mf,
 // of the two overlying fine edges (3D), App. C.
 __global__ void k_coarsen_edges(Geom gf, Geom gc, int p, int c, const double* __restrict__ ef,
                                 double* ec) {
+    pdl_entry();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= gc.esize[p]) return;
     int Q[3];
@@ -184,6 +189,7 @@ __global__ void k_coarsen_edges(Geom gf, Geom gc, int p, int c, const double* __
 
 template <int DIM>
 __global__ void k_inverse_diagonals(Geom g, Coef<double> C, Segs sg) {
+    pdl_entry();
     int t;
     int s = seg_of(sg, blockIdx.x, t);
     int q[3];
@@ -214,6 +220,7 @@ __global__ void k_inverse_diagonals(Geom g, Coef<double> C, Segs sg) {
 
 template <typename TA, typename TB>
 __global__ void k_convert(int n, const TA* __restrict__ a, TB* __restrict__ b) {
+    pdl_entry();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) b[t] = TB(a[t]);
 }
@@ -224,6 +231,7 @@ __global__ void k_convert(int n, const TA* __restrict__ a, TB* __restrict__ b) {
 template <int DIM, typename TV>
 __global__ void k_stokes_matvec(Geom g, Coef<double> C, Segs sg, const TV* __restrict__ x,
                                 const double* __restrict__ b, double* __restrict__ y) {
+    pdl_entry();
     int t;
     int s = seg_of(sg, blockIdx.x, t);
     int q[3];
@@ -265,6 +273,7 @@ __global__ void k_stokes_matvec(Geom g, Coef<double> C, Segs sg, const TV* __res
 template <int DIM, int A, typename T>
 __global__ void __launch_bounds__(512) k_vel_gs(Geom g, Coef<T> C, int parity, T* __restrict__ phi,
                                                 const T* __restrict__ rhs, int nthreads) {
+    pdl_entry();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nthreads) return;
     int q[3];
@@ -276,6 +285,7 @@ template <int DIM, typename T>
 __global__ void __launch_bounds__(TPB) k_vel_residual(Geom g, Coef<T> C, Segs sg,
                                                       const T* __restrict__ phi,
                                                       const T* __restrict__ rhs, T* __restrict__ res) {
+    pdl_entry();
     int t;
     const int s = seg_of(sg, blockIdx.x, t);
     if (t >= g.fsize[s]) return;
@@ -288,6 +298,7 @@ __global__ void __launch_bounds__(TPB) k_vel_residual(Geom g, Coef<T> C, Segs sg
 template <int DIM, typename T>
 __global__ void __launch_bounds__(TPB) k_vel_restrict(Geom gf, Geom gc, Segs sg,
                                                       const T* __restrict__ res, T* __restrict__ rc) {
+    pdl_entry();
     int t;
     const int a = seg_of(sg, blockIdx.x, t);
     if (t >= gc.fsize[a]) return;
@@ -307,6 +318,7 @@ template <int DIM, typename T>
 __global__ void __launch_bounds__(TPB) k_vel_prolong_add(Geom gc, Geom gf, Segs sg,
                                                          const T* __restrict__ pc,
                                                          T* __restrict__ pf) {
+    pdl_entry();
     int t;
     const int a = seg_of(sg, blockIdx.x, t);
     if (t >= gf.fsize[a]) return;
@@ -324,6 +336,7 @@ __global__ void __launch_bounds__(TPB) k_vel_prolong_add(Geom gc, Geom gf, Segs 
 template <int DIM, typename T>
 __global__ void __launch_bounds__(512) k_cell_gs(Geom g, Coef<T> C, int parity, T* __restrict__ phi,
                                                  const T* __restrict__ rhs, int nthreads) {
+    pdl_entry();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nthreads) return;
     int q[3];
@@ -334,6 +347,7 @@ __global__ void __launch_bounds__(512) k_cell_gs(Geom g, Coef<T> C, int parity, 
 template <int DIM, typename T>
 __global__ void __launch_bounds__(TPB) k_cell_residual(Geom g, Coef<T> C, const T* __restrict__ phi,
                                                        const T* __restrict__ rhs, T* __restrict__ res) {
+    pdl_entry();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.ncell) return;
     int q[3];
@@ -344,6 +358,7 @@ __global__ void __launch_bounds__(TPB) k_cell_residual(Geom g, Coef<T> C, const 
 template <int DIM, typename T>
 __global__ void __launch_bounds__(TPB) k_cell_restrict(Geom gf, Geom gc, const T* __restrict__ res,
                                                        T* __restrict__ rc) {
+    pdl_entry();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= gc.ncell) return;
     int Q[3];
@@ -354,6 +369,7 @@ __global__ void __launch_bounds__(TPB) k_cell_restrict(Geom gf, Geom gc, const T
 template <int DIM, typename T>
 __global__ void __launch_bounds__(TPB) k_cell_prolong_add(Geom gc, Geom gf, const T* __restrict__ pc,
                                                           T* __restrict__ pf) {
+    pdl_entry();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= gf.ncell) return;
     int q[3];
@@ -366,6 +382,7 @@ __global__ void __launch_bounds__(TPB) k_cell_prolong_add(Geom gc, Geom gf, cons
 template <int DIM, typename T>
 __global__ void k_div_plus(Geom g, const T* __restrict__ u, const T* __restrict__ bp,
                            T* __restrict__ bc) {
+    pdl_entry();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.ncell) return;
     int q[3];
@@ -383,6 +400,7 @@ __global__ void k_div_plus(Geom g, const T* __restrict__ u, const T* __restrict_
 template <int DIM, typename T>
 __global__ void k_sub_grad(Geom g, Segs sg, const T* __restrict__ beta, const T* __restrict__ u,
                            const T* __restrict__ p, T* __restrict__ out) {
+    pdl_entry();
     int t;
     int a = seg_of(sg, blockIdx.x, t);
     if (t >= g.fsize[a]) return;
@@ -403,6 +421,7 @@ template <int DIM, typename T>
 __global__ void k_vel_correction_rhs(Geom g, Coef<T> C, Segs sg, const T* __restrict__ b,
                                      const T* __restrict__ p, const T* __restrict__ u,
                                      T* __restrict__ out) {
+    pdl_entry();
     int t;
     int s = seg_of(sg, blockIdx.x, t);
     if (t >= g.fsize[s]) return;
@@ -423,6 +442,7 @@ template <typename T>
 __global__ void k_schur_combine(int n, double theta, const T* __restrict__ phi,
                                 const T* __restrict__ mu, const T* __restrict__ bc,
                                 T* __restrict__ xp) {
+    pdl_entry();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     T v = -T(2) * mu[t] * bc[t];
@@ -469,6 +489,7 @@ template <int DIM>
 __global__ void k_gradient(Geom g, const double* __restrict__ mu, double theta,
                            const double* __restrict__ u, const double* __restrict__ lam,
                            double* __restrict__ glogmu, double* __restrict__ grho) {
+    pdl_entry();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.ncell) return;
     int q[3];
@@ -534,6 +555,7 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 
 template <typename T>
 __global__ void k_sum_partials(int n, const T* __restrict__ x, double* part) {
+    pdl_entry();
     __shared__ double sh[32];
     double s = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -544,6 +566,7 @@ __global__ void k_sum_partials(int n, const T* __restrict__ x, double* part) {
 
 // out[k] = sum over RED_BLOCKS partials part[k * RED_BLOCKS + b], fixed order.
 __global__ void k_final(int nk, const double* __restrict__ part, double* out) {
+    pdl_entry();
     __shared__ double sh[32];
     for (int k = 0; k < nk; ++k) {
         double s = 0.0;
@@ -555,11 +578,13 @@ __global__ void k_final(int nk, const double* __restrict__ part, double* out) {
 
 // sum[1] = sum[0] / n, computed once (one FP64 division, not one per thread)
 __global__ void k_mean(int n, double* sum) {
+    pdl_entry();
     if (threadIdx.x == 0 && blockIdx.x == 0) sum[1] = sum[0] / n;
 }
 
 template <typename T>
 __global__ void k_sub_mean(int n, T* x, const double* __restrict__ sum) {
+    pdl_entry();
     const T m = T(sum[1]);
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) x[t] -= m;
@@ -568,19 +593,28 @@ __global__ void k_sub_mean(int n, T* x, const double* __restrict__ sum) {
 template <typename T>
 __global__ void k_copy_sub_mean(int n, const T* __restrict__ in, T* out,
                                 const double* __restrict__ sum) {
+    pdl_entry();
     const T m = T(sum[1]);
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) out[t] = in[t] - m;
 }
 
 template <typename T>
+__global__ void k_zero(int n, T* __restrict__ x) {
+    pdl_entry();
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) x[t] = T(0);
+}
+
+template <typename T>
 __global__ void k_axpy(int n, T a, const T* __restrict__ x, T* __restrict__ y) {
+    pdl_entry();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) y[t] += a * x[t];
 }
 
 __global__ void k_check_fields(int n, const double* __restrict__ rho, const double* __restrict__ mu,
                                double* part) {
+    pdl_entry();
     __shared__ double sh[32];
     double bad = 0.0, nonpos = 0.0;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
@@ -601,36 +635,36 @@ inline int nblk(long long n) { return (int)((n + TPB - 1) / TPB); }
 // ============================================================== launch wrappers
 void launch_fine_coefficients(const Geom& g, const double* rho, const double* mu, double theta,
                               Coef<double> C, cudaStream_t s) {
-    k_fine_faces<<<nblk(g.nvel), TPB, 0, s>>>(g, rho, theta, C.alpha, C.beta);
+    launch_pdl(k_fine_faces, dim3(nblk(g.nvel)), dim3(TPB), s, g, rho, theta, C.alpha, C.beta);
     cudaMemcpyAsync(C.mu_c, mu, sizeof(double) * g.ncell, cudaMemcpyDeviceToDevice, s);
     for (int a = 0; a < g.dim; ++a)
         for (int b = a + 1; b < g.dim; ++b) {
             int p = a + b - 1;
-            k_fine_edges<<<nblk(g.esize[p]), TPB, 0, s>>>(g, p, a, b, mu, C.mu_e[p]);
+            launch_pdl(k_fine_edges, dim3(nblk(g.esize[p])), dim3(TPB), s, g, p, a, b, mu, C.mu_e[p]);
         }
 }
 
 void launch_coarsen_coefficients(const Geom& gf, Coef<double> Cf, const Geom& gc, Coef<double> Cc,
                                  cudaStream_t s) {
-    k_coarsen_faces<<<nblk(gc.nvel), TPB, 0, s>>>(gf, gc, Cf.alpha, Cf.beta, Cc.alpha, Cc.beta);
-    k_coarsen_cells<<<nblk(gc.ncell), TPB, 0, s>>>(gf, gc, Cf.mu_c, Cc.mu_c);
+    launch_pdl(k_coarsen_faces, dim3(nblk(gc.nvel)), dim3(TPB), s, gf, gc, Cf.alpha, Cf.beta, Cc.alpha, Cc.beta);
+    launch_pdl(k_coarsen_cells, dim3(nblk(gc.ncell)), dim3(TPB), s, gf, gc, Cf.mu_c, Cc.mu_c);
     for (int a = 0; a < gc.dim; ++a)
         for (int b = a + 1; b < gc.dim; ++b) {
             int p = a + b - 1;
             int c = 3 - a - b;
-            k_coarsen_edges<<<nblk(gc.esize[p]), TPB, 0, s>>>(gf, gc, p, c, Cf.mu_e[p], Cc.mu_e[p]);
+            launch_pdl(k_coarsen_edges, dim3(nblk(gc.esize[p])), dim3(TPB), s, gf, gc, p, c, Cf.mu_e[p], Cc.mu_e[p]);
         }
 }
 
 void launch_inverse_diagonals(const Geom& g, Coef<double> C, cudaStream_t s) {
     Segs sg = face_segs(g, true);
-    if (g.dim == 2) k_inverse_diagonals<2><<<sg.start[sg.nseg], TPB, 0, s>>>(g, C, sg);
-    else k_inverse_diagonals<3><<<sg.start[sg.nseg], TPB, 0, s>>>(g, C, sg);
+    if (g.dim == 2) launch_pdl(k_inverse_diagonals<2>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg);
+    else launch_pdl(k_inverse_diagonals<3>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg);
 }
 
 template <typename TA, typename TB>
 void launch_convert(int n, const TA* a, TB* b, cudaStream_t s) {
-    if (n > 0) k_convert<TA, TB><<<nblk(n), TPB, 0, s>>>(n, a, b);
+    if (n > 0) launch_pdl(k_convert<TA, TB>, dim3(nblk(n)), dim3(TPB), s, n, a, b);
 }
 
 void launch_convert_coefficients(const Geom& g, Coef<double> C, Coef<float> F, cudaStream_t s) {
@@ -647,15 +681,15 @@ void launch_convert_coefficients(const Geom& g, Coef<double> C, Coef<float> F, c
 template <typename TV>
 void launch_stokes_matvec(const Geom& g, Coef<double> C, const TV* x, double* y, cudaStream_t s) {
     Segs sg = face_segs(g, true);
-    if (g.dim == 2) k_stokes_matvec<2, TV><<<sg.start[sg.nseg], TPB, 0, s>>>(g, C, sg, x, nullptr, y);
-    else k_stokes_matvec<3, TV><<<sg.start[sg.nseg], TPB, 0, s>>>(g, C, sg, x, nullptr, y);
+    if (g.dim == 2) launch_pdl(k_stokes_matvec<2, TV>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, x, nullptr, y);
+    else launch_pdl(k_stokes_matvec<3, TV>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, x, nullptr, y);
 }
 
 void launch_stokes_residual(const Geom& g, Coef<double> C, const double* x, const double* b,
                             double* r, cudaStream_t s) {
     Segs sg = face_segs(g, true);
-    if (g.dim == 2) k_stokes_matvec<2, double><<<sg.start[sg.nseg], TPB, 0, s>>>(g, C, sg, x, b, r);
-    else k_stokes_matvec<3, double><<<sg.start[sg.nseg], TPB, 0, s>>>(g, C, sg, x, b, r);
+    if (g.dim == 2) launch_pdl(k_stokes_matvec<2, double>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, x, b, r);
+    else launch_pdl(k_stokes_matvec<3, double>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, x, b, r);
 }
 
 template <typename T>
@@ -664,12 +698,12 @@ void launch_vel_gs_colour(const Geom& g, Coef<T> C, int comp, int parity, T* phi
     const int nt = ((g.fe[comp][0] + 1) / 2) * g.fe[comp][1] * g.fe[comp][2];
     const int nb = (nt + tpb - 1) / tpb;
     if (g.dim == 2) {
-        if (comp == 0) k_vel_gs<2, 0, T><<<nb, tpb, 0, s>>>(g, C, parity, phi, rhs, nt);
-        else k_vel_gs<2, 1, T><<<nb, tpb, 0, s>>>(g, C, parity, phi, rhs, nt);
+        if (comp == 0) launch_pdl(k_vel_gs<2, 0, T>, dim3(nb), dim3(tpb), s, g, C, parity, phi, rhs, nt);
+        else launch_pdl(k_vel_gs<2, 1, T>, dim3(nb), dim3(tpb), s, g, C, parity, phi, rhs, nt);
     } else {
-        if (comp == 0) k_vel_gs<3, 0, T><<<nb, tpb, 0, s>>>(g, C, parity, phi, rhs, nt);
-        else if (comp == 1) k_vel_gs<3, 1, T><<<nb, tpb, 0, s>>>(g, C, parity, phi, rhs, nt);
-        else k_vel_gs<3, 2, T><<<nb, tpb, 0, s>>>(g, C, parity, phi, rhs, nt);
+        if (comp == 0) launch_pdl(k_vel_gs<3, 0, T>, dim3(nb), dim3(tpb), s, g, C, parity, phi, rhs, nt);
+        else if (comp == 1) launch_pdl(k_vel_gs<3, 1, T>, dim3(nb), dim3(tpb), s, g, C, parity, phi, rhs, nt);
+        else launch_pdl(k_vel_gs<3, 2, T>, dim3(nb), dim3(tpb), s, g, C, parity, phi, rhs, nt);
     }
 }
 
@@ -677,22 +711,22 @@ template <typename T>
 void launch_vel_residual(const Geom& g, Coef<T> C, const T* phi, const T* rhs, T* res,
                          cudaStream_t s) {
     Segs sg = face_segs(g, false);
-    if (g.dim == 2) k_vel_residual<2, T><<<sg.start[sg.nseg], TPB, 0, s>>>(g, C, sg, phi, rhs, res);
-    else k_vel_residual<3, T><<<sg.start[sg.nseg], TPB, 0, s>>>(g, C, sg, phi, rhs, res);
+    if (g.dim == 2) launch_pdl(k_vel_residual<2, T>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, phi, rhs, res);
+    else launch_pdl(k_vel_residual<3, T>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, phi, rhs, res);
 }
 
 template <typename T>
 void launch_vel_restrict(const Geom& gf, const T* res, const Geom& gc, T* rc, cudaStream_t s) {
     Segs sg = face_segs(gc, false);
-    if (gf.dim == 2) k_vel_restrict<2, T><<<sg.start[sg.nseg], TPB, 0, s>>>(gf, gc, sg, res, rc);
-    else k_vel_restrict<3, T><<<sg.start[sg.nseg], TPB, 0, s>>>(gf, gc, sg, res, rc);
+    if (gf.dim == 2) launch_pdl(k_vel_restrict<2, T>, dim3(sg.start[sg.nseg]), dim3(TPB), s, gf, gc, sg, res, rc);
+    else launch_pdl(k_vel_restrict<3, T>, dim3(sg.start[sg.nseg]), dim3(TPB), s, gf, gc, sg, res, rc);
 }
 
 template <typename T>
 void launch_vel_prolong_add(const Geom& gc, const T* pc, const Geom& gf, T* pf, cudaStream_t s) {
     Segs sg = face_segs(gf, false);
-    if (gf.dim == 2) k_vel_prolong_add<2, T><<<sg.start[sg.nseg], TPB, 0, s>>>(gc, gf, sg, pc, pf);
-    else k_vel_prolong_add<3, T><<<sg.start[sg.nseg], TPB, 0, s>>>(gc, gf, sg, pc, pf);
+    if (gf.dim == 2) launch_pdl(k_vel_prolong_add<2, T>, dim3(sg.start[sg.nseg]), dim3(TPB), s, gc, gf, sg, pc, pf);
+    else launch_pdl(k_vel_prolong_add<3, T>, dim3(sg.start[sg.nseg]), dim3(TPB), s, gc, gf, sg, pc, pf);
 }
 
 template <typename T>
@@ -700,40 +734,40 @@ void launch_cell_gs_colour(const Geom& g, Coef<T> C, int parity, T* phi, const T
                            cudaStream_t s, int tpb) {
     const int nt = (g.n[0] / 2) * g.n[1] * g.n[2];
     const int nb = (nt + tpb - 1) / tpb;
-    if (g.dim == 2) k_cell_gs<2, T><<<nb, tpb, 0, s>>>(g, C, parity, phi, rhs, nt);
-    else k_cell_gs<3, T><<<nb, tpb, 0, s>>>(g, C, parity, phi, rhs, nt);
+    if (g.dim == 2) launch_pdl(k_cell_gs<2, T>, dim3(nb), dim3(tpb), s, g, C, parity, phi, rhs, nt);
+    else launch_pdl(k_cell_gs<3, T>, dim3(nb), dim3(tpb), s, g, C, parity, phi, rhs, nt);
 }
 
 template <typename T>
 void launch_cell_residual(const Geom& g, Coef<T> C, const T* phi, const T* rhs, T* res,
                           cudaStream_t s) {
-    if (g.dim == 2) k_cell_residual<2, T><<<nblk(g.ncell), TPB, 0, s>>>(g, C, phi, rhs, res);
-    else k_cell_residual<3, T><<<nblk(g.ncell), TPB, 0, s>>>(g, C, phi, rhs, res);
+    if (g.dim == 2) launch_pdl(k_cell_residual<2, T>, dim3(nblk(g.ncell)), dim3(TPB), s, g, C, phi, rhs, res);
+    else launch_pdl(k_cell_residual<3, T>, dim3(nblk(g.ncell)), dim3(TPB), s, g, C, phi, rhs, res);
 }
 
 template <typename T>
 void launch_cell_restrict(const Geom& gf, const T* res, const Geom& gc, T* rc, cudaStream_t s) {
-    if (gf.dim == 2) k_cell_restrict<2, T><<<nblk(gc.ncell), TPB, 0, s>>>(gf, gc, res, rc);
-    else k_cell_restrict<3, T><<<nblk(gc.ncell), TPB, 0, s>>>(gf, gc, res, rc);
+    if (gf.dim == 2) launch_pdl(k_cell_restrict<2, T>, dim3(nblk(gc.ncell)), dim3(TPB), s, gf, gc, res, rc);
+    else launch_pdl(k_cell_restrict<3, T>, dim3(nblk(gc.ncell)), dim3(TPB), s, gf, gc, res, rc);
 }
 
 template <typename T>
 void launch_cell_prolong_add(const Geom& gc, const T* pc, const Geom& gf, T* pf, cudaStream_t s) {
-    if (gf.dim == 2) k_cell_prolong_add<2, T><<<nblk(gf.ncell), TPB, 0, s>>>(gc, gf, pc, pf);
-    else k_cell_prolong_add<3, T><<<nblk(gf.ncell), TPB, 0, s>>>(gc, gf, pc, pf);
+    if (gf.dim == 2) launch_pdl(k_cell_prolong_add<2, T>, dim3(nblk(gf.ncell)), dim3(TPB), s, gc, gf, pc, pf);
+    else launch_pdl(k_cell_prolong_add<3, T>, dim3(nblk(gf.ncell)), dim3(TPB), s, gc, gf, pc, pf);
 }
 
 template <typename T>
 void launch_div_plus(const Geom& g, const T* u, const T* bp, T* bc, cudaStream_t s) {
-    if (g.dim == 2) k_div_plus<2, T><<<nblk(g.ncell), TPB, 0, s>>>(g, u, bp, bc);
-    else k_div_plus<3, T><<<nblk(g.ncell), TPB, 0, s>>>(g, u, bp, bc);
+    if (g.dim == 2) launch_pdl(k_div_plus<2, T>, dim3(nblk(g.ncell)), dim3(TPB), s, g, u, bp, bc);
+    else launch_pdl(k_div_plus<3, T>, dim3(nblk(g.ncell)), dim3(TPB), s, g, u, bp, bc);
 }
 
 template <typename T>
 void launch_sub_grad(const Geom& g, const T* beta, const T* u, const T* p, T* out, cudaStream_t s) {
     Segs sg = face_segs(g, false);
-    if (g.dim == 2) k_sub_grad<2, T><<<sg.start[sg.nseg], TPB, 0, s>>>(g, sg, beta, u, p, out);
-    else k_sub_grad<3, T><<<sg.start[sg.nseg], TPB, 0, s>>>(g, sg, beta, u, p, out);
+    if (g.dim == 2) launch_pdl(k_sub_grad<2, T>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, sg, beta, u, p, out);
+    else launch_pdl(k_sub_grad<3, T>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, sg, beta, u, p, out);
 }
 
 template <typename T>
@@ -741,50 +775,56 @@ void launch_vel_correction_rhs(const Geom& g, Coef<T> C, const T* b, const T* p,
                                T* out, cudaStream_t s) {
     Segs sg = face_segs(g, false);
     if (g.dim == 2)
-        k_vel_correction_rhs<2, T><<<sg.start[sg.nseg], TPB, 0, s>>>(g, C, sg, b, p, u, out);
+        launch_pdl(k_vel_correction_rhs<2, T>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, b, p, u, out);
     else
-        k_vel_correction_rhs<3, T><<<sg.start[sg.nseg], TPB, 0, s>>>(g, C, sg, b, p, u, out);
+        launch_pdl(k_vel_correction_rhs<3, T>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, b, p, u, out);
 }
 
 template <typename T>
 void launch_schur_combine(int n, double theta, const T* phi, const T* mu, const T* bc, T* xp,
                           cudaStream_t s) {
-    k_schur_combine<T><<<nblk(n), TPB, 0, s>>>(n, theta, phi, mu, bc, xp);
+    launch_pdl(k_schur_combine<T>, dim3(nblk(n)), dim3(TPB), s, n, theta, phi, mu, bc, xp);
 }
 
 template <typename T>
 void launch_sum(int n, const T* x, double* scratch, double* out, cudaStream_t s) {
-    k_sum_partials<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, x, scratch);
-    k_final<<<1, RED_THREADS, 0, s>>>(1, scratch, out);
+    launch_pdl(k_sum_partials<T>, dim3(RED_BLOCKS), dim3(RED_THREADS), s, n, x, scratch);
+    launch_pdl(k_final, dim3(1), dim3(RED_THREADS), s, 1, scratch, out);
 }
 
 template <typename T>
 void launch_sub_mean(int n, T* x, double* sum, cudaStream_t s) {
-    k_mean<<<1, 32, 0, s>>>(n, sum);
-    k_sub_mean<T><<<nblk(n), TPB, 0, s>>>(n, x, sum);
+    launch_pdl(k_mean, dim3(1), dim3(32), s, n, sum);
+    launch_pdl(k_sub_mean<T>, dim3(nblk(n)), dim3(TPB), s, n, x, sum);
 }
 
 template <typename T>
 void launch_copy_sub_mean(int n, const T* in, T* out, double* sum, cudaStream_t s) {
-    k_mean<<<1, 32, 0, s>>>(n, sum);
-    k_copy_sub_mean<T><<<nblk(n), TPB, 0, s>>>(n, in, out, sum);
+    launch_pdl(k_mean, dim3(1), dim3(32), s, n, sum);
+    launch_pdl(k_copy_sub_mean<T>, dim3(nblk(n)), dim3(TPB), s, n, in, out, sum);
+}
+
+template <typename T>
+void launch_zero(int n, T* x, cudaStream_t s) {
+    const int nb = nblk(n) < 1216 ? nblk(n) : 1216;
+    launch_pdl(k_zero<T>, dim3(nb > 0 ? nb : 1), dim3(TPB), s, n, x);
 }
 
 template <typename T>
 void launch_axpy(int n, T a, const T* x, T* y, cudaStream_t s) {
-    k_axpy<T><<<nblk(n), TPB, 0, s>>>(n, a, x, y);
+    launch_pdl(k_axpy<T>, dim3(nblk(n)), dim3(TPB), s, n, a, x, y);
 }
 
 void launch_gradient(const Geom& g, const double* mu, double theta, const double* u,
                      const double* lam, double* glogmu, double* grho, cudaStream_t s) {
-    if (g.dim == 2) k_gradient<2><<<nblk(g.ncell), TPB, 0, s>>>(g, mu, theta, u, lam, glogmu, grho);
-    else k_gradient<3><<<nblk(g.ncell), TPB, 0, s>>>(g, mu, theta, u, lam, glogmu, grho);
+    if (g.dim == 2) launch_pdl(k_gradient<2>, dim3(nblk(g.ncell)), dim3(TPB), s, g, mu, theta, u, lam, glogmu, grho);
+    else launch_pdl(k_gradient<3>, dim3(nblk(g.ncell)), dim3(TPB), s, g, mu, theta, u, lam, glogmu, grho);
 }
 
 void launch_check_fields(int n, const double* rho, const double* mu, double* scratch, double* out,
                          cudaStream_t s) {
-    k_check_fields<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, rho, mu, scratch);
-    k_final<<<1, RED_THREADS, 0, s>>>(2, scratch, out);
+    launch_pdl(k_check_fields, dim3(RED_BLOCKS), dim3(RED_THREADS), s, n, rho, mu, scratch);
+    launch_pdl(k_final, dim3(1), dim3(RED_THREADS), s, 2, scratch, out);
 }
 
 // explicit instantiations
@@ -815,7 +855,8 @@ void launch_check_fields(int n, const double* rho, const double* mu, double* scr
     template void launch_copy_sub_mean<T>(int, const T*, T*, double*, cudaStream_t);             \
     template void launch_stokes_matvec<T>(const Geom&, Coef<double>, const T*, double*,          \
                                           cudaStream_t);                                           \
-    template void launch_axpy<T>(int, T, const T*, T*, cudaStream_t);
+    template void launch_axpy<T>(int, T, const T*, T*, cudaStream_t);                            \
+    template void launch_zero<T>(int, T*, cudaStream_t);
 STK_INST(double)
 STK_INST(float)
 #undef STK_INST

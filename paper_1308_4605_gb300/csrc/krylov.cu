@@ -48,6 +48,7 @@ __device__ __forceinline__ void block_sums(const double (&v)[NV], double* part) 
 
 // out[k] = sum_b part[k * KRY_BLOCKS + b], one block per k, fixed order.
 __global__ void __launch_bounds__(KT) k_final_multi(const double* __restrict__ part, double* out) {
+    pdl_entry();
     __shared__ double sh[KT / 32];
     const int k = blockIdx.x;
     double s = 0.0;
@@ -67,6 +68,7 @@ __global__ void __launch_bounds__(KT) k_final_multi(const double* __restrict__ p
 template <int J>
 __global__ void __launch_bounds__(KT) k_mdot(int n, PtrArr V, const double* __restrict__ w,
                                               double* __restrict__ part) {
+    pdl_entry();
     double acc[J + 2];
 #pragma unroll
     for (int i = 0; i < J + 2; ++i) acc[i] = 0.0;
@@ -96,6 +98,7 @@ __global__ void __launch_bounds__(KT) k_mdot(int n, PtrArr V, const double* __re
 template <int J>
 __global__ void __launch_bounds__(KT) k_upd(int n, PtrArr V, const double* __restrict__ h,
                                              double* __restrict__ w, double* __restrict__ part) {
+    pdl_entry();
     double hh[J + 1];
 #pragma unroll
     for (int i = 0; i <= J; ++i) hh[i] = h[i];
@@ -132,6 +135,7 @@ template <> struct Vec2<float> { using type = float2; };
 template <int K, typename TV>
 __global__ void __launch_bounds__(KT) k_comb(int n, PtrArr V, const double* __restrict__ y,
                                               double* __restrict__ x) {
+    pdl_entry();
     using V2 = typename Vec2<TV>::type;
     double yy[K];
 #pragma unroll
@@ -158,6 +162,7 @@ __global__ void __launch_bounds__(KT) k_comb(int n, PtrArr V, const double* __re
 
 __global__ void __launch_bounds__(KT) k_scal(int n, double* __restrict__ x, double a,
                                              const double* __restrict__ nrm2) {
+    pdl_entry();
     const double s = nrm2 ? 1.0 / sqrt(*nrm2) : a;
     for (int t = blockIdx.x * KT + threadIdx.x; t < n; t += KRY_BLOCKS * KT) x[t] *= s;
 }
@@ -178,32 +183,32 @@ void launch_multidot(int n, int j, const double* const* V, const double* w, doub
                      double* h, cudaStream_t s) {
     PtrArr pa = pack(reinterpret_cast<const void* const*>(V), j + 1);
     switch (j) {
-    case -1: k_mdot<-1><<<KRY_BLOCKS, KT, 0, s>>>(n, pa, w, scratch); break;
-#define X(J) case J: k_mdot<J><<<KRY_BLOCKS, KT, 0, s>>>(n, pa, w, scratch); break;
+    case -1: launch_pdl(k_mdot<-1>, dim3(KRY_BLOCKS), dim3(KT), s, n, pa, w, scratch); break;
+#define X(J) case J: launch_pdl(k_mdot<J>, dim3(KRY_BLOCKS), dim3(KT), s, n, pa, w, scratch); break;
     STK_J_CASES(X)
 #undef X
     default: return;
     }
-    k_final_multi<<<j + 2, KT, 0, s>>>(scratch, h);
+    launch_pdl(k_final_multi, dim3(j + 2), dim3(KT), s, scratch, h);
 }
 
 void launch_update_norm(int n, int j, const double* const* V, const double* h, double* w,
                         double* scratch, double* out, cudaStream_t s) {
     PtrArr pa = pack(reinterpret_cast<const void* const*>(V), j + 1);
     switch (j) {
-#define X(J) case J: k_upd<J><<<KRY_BLOCKS, KT, 0, s>>>(n, pa, h, w, scratch); break;
+#define X(J) case J: launch_pdl(k_upd<J>, dim3(KRY_BLOCKS), dim3(KT), s, n, pa, h, w, scratch); break;
     STK_J_CASES(X)
 #undef X
     default: return;
     }
-    k_final_multi<<<1, KT, 0, s>>>(scratch, out);
+    launch_pdl(k_final_multi, dim3(1), dim3(KT), s, scratch, out);
 }
 
 template <typename TV>
 void launch_combine(int n, int k, const TV* const* V, const double* y, double* x, cudaStream_t s) {
     PtrArr pa = pack(reinterpret_cast<const void* const*>(V), k);
     switch (k - 1) {
-#define X(J) case J: k_comb<J + 1, TV><<<KRY_BLOCKS, KT, 0, s>>>(n, pa, y, x); break;
+#define X(J) case J: launch_pdl(k_comb<J + 1, TV>, dim3(KRY_BLOCKS), dim3(KT), s, n, pa, y, x); break;
     STK_J_CASES(X)
 #undef X
     default: return;
@@ -211,11 +216,11 @@ void launch_combine(int n, int k, const TV* const* V, const double* y, double* x
 }
 
 void launch_scale_inv_sqrt(int n, double* x, const double* nrm2, cudaStream_t s) {
-    k_scal<<<KRY_BLOCKS, KT, 0, s>>>(n, x, 0.0, nrm2);
+    launch_pdl(k_scal, dim3(KRY_BLOCKS), dim3(KT), s, n, x, 0.0, nrm2);
 }
 
 void launch_scale(int n, double* x, double a, cudaStream_t s) {
-    k_scal<<<KRY_BLOCKS, KT, 0, s>>>(n, x, a, nullptr);
+    launch_pdl(k_scal, dim3(KRY_BLOCKS), dim3(KT), s, n, x, a, nullptr);
 }
 
 template void launch_combine<double>(int, int, const double* const*, const double*, double*,

@@ -344,7 +344,7 @@ void vcycle_vel(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp, 
                                     mp.nu, mp.ncoarse, s);
         return;
     }
-    cudaMemsetAsync(phi, 0, sizeof(T) * L.g.nvel, s);
+    launch_zero<T>(L.g.nvel, phi, s);
     if (l + 1 == (int)h->lev.size()) {
         vel_sweeps<T>(h, L, mp.ncoarse, phi, rhs, s);
         return;
@@ -379,7 +379,7 @@ void vcycle_cell(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp,
                                      mp.nu, mp.ncoarse, s);
         return;
     }
-    cudaMemsetAsync(phi, 0, sizeof(T) * L.g.ncell, s);
+    launch_zero<T>(L.g.ncell, phi, s);
     if (l + 1 == (int)h->lev.size()) {
         cell_sweeps<T>(h, L, mp.ncoarse, phi, rhs, s);
         return;

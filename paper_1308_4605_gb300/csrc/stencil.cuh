@@ -70,6 +70,7 @@ __device__ __forceinline__ int step(const Geom& g, int ax, int i, int d) {
 }
 template <typename T> __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
 
+
 template <typename T> __device__ __forceinline__ T gih(const Geom& g);
 template <> __device__ __forceinline__ double gih<double>(const Geom& g) { return g.ih; }
 template <> __device__ __forceinline__ float gih<float>(const Geom& g) { return g.ihf; }
