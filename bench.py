@@ -56,6 +56,41 @@ def parse():
     return ap.parse_args()
 
 
+class Replicas:
+    """`--gpus N` under torchrun: one process per GPU, each solving its own
+    copy of the workload.  There is no collective on the data path; the
+    process group only brackets the timed region with barriers and takes the
+    maximum per-solve time over ranks."""
+
+    def __init__(self, backend):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend, init_method="env://")
+
+    def barrier(self):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max(self, values, device):
+        """Element-wise maximum of a list of floats over all ranks."""
+        if self.world == 1:
+            return list(values)
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor(values, dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return t.tolist()
+
+    def close(self):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
 def make_problem(name, n):
     from paper_1308_4605_gb300 import workloads as wl
     if name == "c3":
@@ -254,21 +289,13 @@ def run_reference(args):
 def run_ours(args):
     import numpy as np
     import torch
-    import torch.distributed as dist
-
     from paper_1308_4605_gb300 import stokes as S
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl", init_method="env://")
+    reps = Replicas("nccl")
+    world, rank, local = reps.world, reps.rank, reps.local
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
+    barrier = reps.barrier
 
     pr, cfg = make_problem(args.workload, args.n)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
@@ -345,10 +372,7 @@ def run_ours(args):
 
     ms64 = statistics.mean(times64)
     ms_mx = statistics.mean(times_mx)
-    if world > 1:
-        tt = torch.tensor([ms64, ms_mx], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms64, ms_mx = tt.tolist()
+    ms64, ms_mx = reps.max([ms64, ms_mx], dev)
 
     # ---- end to end through the C ABI from pinned host buffers
     e2e = None
@@ -440,8 +464,7 @@ def run_ours(args):
     if rank == 0:
         print(json.dumps(line))
     solver.close()
-    if world > 1:
-        dist.destroy_process_group()
+    reps.close()
     return 0
 
 
