@@ -188,14 +188,19 @@ int stk_solve_batched(int count, stk_handle* const* hs, const stk_solver_params*
  * left GMRES; STK_MIXED: the FP32 one of the flexible form).  Levels
  * coarse_level and coarser run as one single-block kernel (all of their
  * smoothing and transfers in one launch); finer levels run as grid-wide
- * kernels, the Gauss-Seidel colours with `threads` threads per block
- * (64, 128, 256 or 512).  The arithmetic does not depend on the schedule.
- * stk_autotune times one velocity + one pressure V-cycle (as a captured
- * graph) for every admissible schedule, applies the fastest and returns it;
- * stk_set_schedule applies a known one (e.g. cached from an earlier run). */
+ * kernels.  On those, levels pair_level and coarser smooth with one launch
+ * per sweep and component doing both colours (each block recomputes the
+ * red points of a one-point halo around its tile); finer levels launch once
+ * per colour with `threads` threads per block (64, 128, 256 or 512).
+ * 0 <= pair_level, coarse_level <= number of levels.  The arithmetic does
+ * not depend on the schedule.  stk_autotune times one velocity + one
+ * pressure V-cycle (as a captured graph) for every admissible schedule,
+ * applies the fastest and returns it; stk_set_schedule applies a known one
+ * (e.g. cached from an earlier run). */
 typedef struct {
     int coarse_level;
     int threads;
+    int pair_level;
 } stk_schedule;
 int stk_get_schedule(const stk_handle* h, int precision, stk_schedule* out);
 int stk_set_schedule(stk_handle* h, int precision, const stk_schedule* sc);
@@ -209,7 +214,7 @@ int stk_autotune(stk_handle* h, int precision, stk_schedule* best, void* stream)
  * input word and writes of every output word, once per launch) and, for the
  * Gauss-Seidel families, its floating-point operations.  Level-0 smoothing
  * has families of its own.  Returns -1 when k is out of range. */
-#define STK_NPROF 20
+#define STK_NPROF 24
 int stk_profile(stk_handle* h, int enable);
 /* Number of CUDA kernels this handle has launched since it was created. */
 long long stk_kernel_launches(const stk_handle* h);

@@ -150,6 +150,14 @@ void launch_vel_restrict(const Geom& gf, const T* res, const Geom& gc, T* rhs_c,
 template <typename T>
 void launch_vel_prolong_add(const Geom& gc, const T* phi_c, const Geom& gf, T* phi_f,
                             cudaStream_t s);
+// both colours of one sweep, out of place (pair.cu): velocity component
+// comp read from src (components < comp from dst) and written to dst
+template <typename T>
+void launch_vel_gs_pair(const Geom& g, Coef<T> C, int comp, const T* src, T* dst, const T* rhs,
+                        cudaStream_t s);
+template <typename T>
+void launch_cell_gs_pair(const Geom& g, Coef<T> C, const T* src, T* dst, const T* rhs,
+                         cudaStream_t s);
 template <typename T>
 void launch_cell_gs_colour(const Geom& g, Coef<T> C, int parity, T* phi, const T* rhs,
                            cudaStream_t s, int tpb = 256);  // tpb <= 512
@@ -191,7 +199,7 @@ template <typename T>  // out = b - G p - A u
 void launch_vel_correction_rhs(const Geom& g, Coef<T> C, const T* b, const T* p, const T* u,
                                T* out, cudaStream_t s);
 template <typename T>  // xp = theta phi - 2 mu bc  (phi may be null)
-void launch_schur_combine(int n, double theta, const T* phi, const T* mu, const T* bc, T* xp,
+void launch_schur_combine(int n, const double* theta, const T* phi, const T* mu, const T* bc, T* xp,
                           cudaStream_t s);
 
 // reductions with a fixed block count: deterministic results

@@ -439,14 +439,14 @@ __global__ void k_vel_correction_rhs(Geom g, Coef<T> C, Segs sg, const T* __rest
 }
 
 template <typename T>
-__global__ void k_schur_combine(int n, double theta, const T* __restrict__ phi,
+__global__ void k_schur_combine(int n, const double* __restrict__ theta, const T* __restrict__ phi,
                                 const T* __restrict__ mu, const T* __restrict__ bc,
                                 T* __restrict__ xp) {
     pdl_entry();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     T v = -T(2) * mu[t] * bc[t];
-    if (phi) v += T(theta) * phi[t];
+    if (phi) v += T(*theta) * phi[t];
     xp[t] = v;
 }
 
@@ -781,7 +781,7 @@ void launch_vel_correction_rhs(const Geom& g, Coef<T> C, const T* b, const T* p,
 }
 
 template <typename T>
-void launch_schur_combine(int n, double theta, const T* phi, const T* mu, const T* bc, T* xp,
+void launch_schur_combine(int n, const double* theta, const T* phi, const T* mu, const T* bc, T* xp,
                           cudaStream_t s) {
     launch_pdl(k_schur_combine<T>, dim3(nblk(n)), dim3(TPB), s, n, theta, phi, mu, bc, xp);
 }
@@ -848,7 +848,7 @@ void launch_check_fields(int n, const double* rho, const double* mu, double* scr
                                      cudaStream_t);                                                \
     template void launch_vel_correction_rhs<T>(const Geom&, Coef<T>, const T*, const T*,         \
                                                const T*, T*, cudaStream_t);                        \
-    template void launch_schur_combine<T>(int, double, const T*, const T*, const T*, T*,         \
+    template void launch_schur_combine<T>(int, const double*, const T*, const T*, const T*, T*,  \
                                           cudaStream_t);                                           \
     template void launch_sum<T>(int, const T*, double*, double*, cudaStream_t);                  \
     template void launch_sub_mean<T>(int, T*, double*, cudaStream_t);                            \

@@ -1,0 +1,218 @@
+// Both colours of one Gauss-Seidel sweep in one launch (App. C smoother).
+//
+// The per-colour kernels (kernels.cu) read every input array once per colour
+// and the second colour waits for a grid-wide launch boundary.  Here a block
+// owns a tile of one face (or cell) array and does both colours itself:
+//
+//   1. the red points ((i + j + k) even) of the tile and of a one-point halo
+//      around it are computed from the input values into shared memory (the
+//      halo points belong to neighbouring tiles and are recomputed, with the
+//      same arithmetic, from the same inputs);
+//   2. the black points of the tile are computed from those red values.
+//
+// The sweep is out of place: values are read from `src` and written to
+// `dst`, so no block ever reads a value that another block of the same
+// launch writes.  For the velocity, a sweep over components x, y(, z) reads
+// the components already swept from `dst` and the others from `src`; after
+// a whole sweep every component lives in `dst`, and the caller swaps the two
+// buffers.  The results equal those of the two per-colour launches: the
+// same per-point functions (stencil.cuh) with the same operands.
+#include "stencil.cuh"
+
+namespace stk {
+namespace {
+
+using namespace st;
+
+// In-range coordinate of the (unwrapped) position u along axis d of an
+// array with extent e, or -1 if there is none: periodic axes wrap once,
+// other axes end at the array.
+__device__ __forceinline__ int halo_coord(const Geom& g, int d, int u, int e) {
+    if (g.per[d]) return (u < -1 || u > e) ? -1 : wrapm(u, e);
+    return (u < 0 || u >= e) ? -1 : u;
+}
+// Shared-memory slot of in-range coordinate c of a neighbour of a tile point,
+// for a haloed tile that starts at o (tile origin - 1) and is W wide; a
+// neighbour across a periodic seam is found one period away.
+__device__ __forceinline__ int slot(int c, int o, int W, int e) {
+    int l = c - o;
+    if (l < 0) l += e;
+    else if (l >= W) l -= e;
+    return l;
+}
+
+// Velocity component A.  Tile: 2 TXC faces along x (TXC of each colour),
+// TY along y, TZ along z (3D); one thread per black point.
+template <int DIM, int A, typename T, int TXC, int TY, int TZ>
+__global__ void __launch_bounds__(TXC * TY * TZ)
+k_vel_gs_pair(Geom g, Coef<T> C, const T* src, T* dst, const T* __restrict__ rhs) {
+    pdl_entry();
+    constexpr bool F32 = sizeof(T) == 4;
+    constexpr int NT = TXC * TY * TZ;
+    constexpr int WX = 2 * TXC + 2, WY = TY + 2, WZ = DIM == 3 ? TZ + 2 : 1;
+    __shared__ T R[WZ][WY][WX];
+    const int e0 = g.fe[A][0], e1 = g.fe[A][1], e2 = g.fe[A][2];
+    const int ox = blockIdx.x * 2 * TXC - 1, oy = blockIdx.y * TY - 1;
+    const int oz = DIM == 3 ? int(blockIdx.z) * TZ - 1 : 0;
+    // components swept before A in this sweep are in dst, the others in src
+    auto pb = [&](int B, const int* r) { return T((B < A ? dst : src)[fidx(g, B, r)]); };
+
+    // 1. red points of the haloed tile, from the input values
+    {
+        auto pa = [&](const int* r) { return T(src[fidx(g, A, r)]); };
+        for (int t = threadIdx.x; t < (TXC + 1) * WY * WZ; t += NT) {
+            const int xr = t % (TXC + 1);
+            const int rr = t / (TXC + 1);
+            const int ly = rr % WY;
+            const int lz = DIM == 3 ? rr / WY : 0;
+            const int uy = oy + ly, uz = oz + lz;
+            const int lx = 2 * xr + ((ox + uy + uz) & 1);   // ox + lx + uy + uz even
+            const int ux = ox + lx;
+            R[lz][ly][lx ^ 1] = T(0);   // black slot: never read, kept finite
+            int q[3];
+            q[0] = halo_coord(g, 0, ux, e0);
+            q[1] = halo_coord(g, 1, uy, e1);
+            q[2] = DIM == 3 ? halo_coord(g, 2, uz, e2) : 0;
+            if (q[0] < 0 || q[1] < 0 || q[2] < 0) {
+                R[lz][ly][lx] = T(0);
+                continue;
+            }
+            T v = T(0);
+            if (!wall_face(g, A, q)) {
+                T dsum;
+                const T N = visc_offdiag_acc<DIM, A, T, F32>(g, C, q, pa, pb, dsum);
+                const int f = fidx(g, A, q);
+                v = vel_gs_value<T>(g, C, f, N, dsum, rhs);
+                const bool inner = lx >= 1 && lx <= 2 * TXC && ux < e0 && ly >= 1 && ly <= TY &&
+                                   uy < e1 && (DIM == 2 || (lz >= 1 && lz <= TZ && uz < e2));
+                if (inner) dst[f] = v;
+            }
+            R[lz][ly][lx] = v;   // wall faces hold 0
+        }
+    }
+    __syncthreads();
+
+    // 2. black points of the tile, from the red values in shared memory
+    const int xb = threadIdx.x % TXC;
+    const int ly = 1 + (threadIdx.x / TXC) % TY;
+    const int lz = DIM == 3 ? 1 + int(threadIdx.x) / (TXC * TY) : 0;
+    const int uy = oy + ly, uz = oz + lz;
+    const int lx = 1 + 2 * xb + ((ox + uy + uz) & 1);   // ox + lx + uy + uz odd
+    const int ux = ox + lx;
+    if (ux >= e0 || uy >= e1 || (DIM == 3 && uz >= e2)) return;
+    const int q[3] = {ux, uy, DIM == 3 ? uz : 0};
+    if (wall_face(g, A, q)) return;
+    auto pa = [&](const int* r) {
+        const int sx = slot(r[0], ox, WX, e0);
+        const int sy = slot(r[1], oy, WY, e1);
+        const int sz = DIM == 3 ? slot(r[2], oz, WZ, e2) : 0;
+        return R[sz][sy][sx];
+    };
+    T dsum;
+    const T N = visc_offdiag_acc<DIM, A, T, F32>(g, C, q, pa, pb, dsum);
+    const int f = fidx(g, A, q);
+    dst[f] = vel_gs_value<T>(g, C, f, N, dsum, rhs);
+}
+
+// Cells.  Tile: 2 TXC cells along x, TY along y, TZ along z (3D).
+template <int DIM, typename T, int TXC, int TY, int TZ>
+__global__ void __launch_bounds__(TXC * TY * TZ)
+k_cell_gs_pair(Geom g, Coef<T> C, const T* src, T* dst, const T* __restrict__ rhs) {
+    pdl_entry();
+    constexpr int NT = TXC * TY * TZ;
+    constexpr int WX = 2 * TXC + 2, WY = TY + 2, WZ = DIM == 3 ? TZ + 2 : 1;
+    __shared__ T R[WZ][WY][WX];
+    const int e0 = g.n[0], e1 = g.n[1], e2 = g.n[2];
+    const int ox = blockIdx.x * 2 * TXC - 1, oy = blockIdx.y * TY - 1;
+    const int oz = DIM == 3 ? int(blockIdx.z) * TZ - 1 : 0;
+    {
+        auto pc = [&](const int* r) { return T(src[cidx(g, r)]); };
+        for (int t = threadIdx.x; t < (TXC + 1) * WY * WZ; t += NT) {
+            const int xr = t % (TXC + 1);
+            const int rr = t / (TXC + 1);
+            const int ly = rr % WY;
+            const int lz = DIM == 3 ? rr / WY : 0;
+            const int uy = oy + ly, uz = oz + lz;
+            const int lx = 2 * xr + ((ox + uy + uz) & 1);
+            const int ux = ox + lx;
+            // the black slot is read with weight 0 by a point next to a wall
+            // (its clamped neighbour is itself), so it must hold a finite value
+            R[lz][ly][lx ^ 1] = T(0);
+            int q[3];
+            q[0] = halo_coord(g, 0, ux, e0);
+            q[1] = halo_coord(g, 1, uy, e1);
+            q[2] = DIM == 3 ? halo_coord(g, 2, uz, e2) : 0;
+            if (q[0] < 0 || q[1] < 0 || q[2] < 0) {
+                R[lz][ly][lx] = T(0);
+                continue;
+            }
+            const T v = cell_gs_value<DIM, T>(g, C, q, pc, rhs);
+            const bool inner = lx >= 1 && lx <= 2 * TXC && ux < e0 && ly >= 1 && ly <= TY &&
+                               uy < e1 && (DIM == 2 || (lz >= 1 && lz <= TZ && uz < e2));
+            if (inner) dst[cidx(g, q)] = v;
+            R[lz][ly][lx] = v;
+        }
+    }
+    __syncthreads();
+    const int xb = threadIdx.x % TXC;
+    const int ly = 1 + (threadIdx.x / TXC) % TY;
+    const int lz = DIM == 3 ? 1 + int(threadIdx.x) / (TXC * TY) : 0;
+    const int uy = oy + ly, uz = oz + lz;
+    const int lx = 1 + 2 * xb + ((ox + uy + uz) & 1);
+    const int ux = ox + lx;
+    if (ux >= e0 || uy >= e1 || (DIM == 3 && uz >= e2)) return;
+    const int q[3] = {ux, uy, DIM == 3 ? uz : 0};
+    auto pc = [&](const int* r) {
+        const int sx = slot(r[0], ox, WX, e0);
+        const int sy = slot(r[1], oy, WY, e1);
+        const int sz = DIM == 3 ? slot(r[2], oz, WZ, e2) : 0;
+        return R[sz][sy][sx];
+    };
+    dst[cidx(g, q)] = cell_gs_value<DIM, T>(g, C, q, pc, rhs);
+}
+
+// tile shapes: 3D 32 x 8 x 4 faces (512 threads), 2D 32 x 16 (256 threads)
+constexpr int P3X = 16, P3Y = 8, P3Z = 4;
+constexpr int P2X = 16, P2Y = 16;
+
+inline dim3 pair_grid(int dim, int e0, int e1, int e2) {
+    if (dim == 2) return dim3((e0 + 2 * P2X - 1) / (2 * P2X), (e1 + P2Y - 1) / P2Y, 1);
+    return dim3((e0 + 2 * P3X - 1) / (2 * P3X), (e1 + P3Y - 1) / P3Y, (e2 + P3Z - 1) / P3Z);
+}
+
+}  // namespace
+
+template <typename T>
+void launch_vel_gs_pair(const Geom& g, Coef<T> C, int comp, const T* src, T* dst, const T* rhs,
+                        cudaStream_t s) {
+    const dim3 gr = pair_grid(g.dim, g.fe[comp][0], g.fe[comp][1], g.fe[comp][2]);
+    if (g.dim == 2) {
+        const dim3 bl(P2X * P2Y);
+        if (comp == 0) launch_pdl(k_vel_gs_pair<2, 0, T, P2X, P2Y, 1>, gr, bl, s, g, C, src, dst, rhs);
+        else launch_pdl(k_vel_gs_pair<2, 1, T, P2X, P2Y, 1>, gr, bl, s, g, C, src, dst, rhs);
+    } else {
+        const dim3 bl(P3X * P3Y * P3Z);
+        if (comp == 0) launch_pdl(k_vel_gs_pair<3, 0, T, P3X, P3Y, P3Z>, gr, bl, s, g, C, src, dst, rhs);
+        else if (comp == 1) launch_pdl(k_vel_gs_pair<3, 1, T, P3X, P3Y, P3Z>, gr, bl, s, g, C, src, dst, rhs);
+        else launch_pdl(k_vel_gs_pair<3, 2, T, P3X, P3Y, P3Z>, gr, bl, s, g, C, src, dst, rhs);
+    }
+}
+
+template <typename T>
+void launch_cell_gs_pair(const Geom& g, Coef<T> C, const T* src, T* dst, const T* rhs,
+                         cudaStream_t s) {
+    const dim3 gr = pair_grid(g.dim, g.n[0], g.n[1], g.n[2]);
+    if (g.dim == 2) launch_pdl(k_cell_gs_pair<2, T, P2X, P2Y, 1>, gr, dim3(P2X * P2Y), s, g, C, src, dst, rhs);
+    else launch_pdl(k_cell_gs_pair<3, T, P3X, P3Y, P3Z>, gr, dim3(P3X * P3Y * P3Z), s, g, C, src, dst, rhs);
+}
+
+template void launch_vel_gs_pair<double>(const Geom&, Coef<double>, int, const double*, double*,
+                                         const double*, cudaStream_t);
+template void launch_vel_gs_pair<float>(const Geom&, Coef<float>, int, const float*, float*,
+                                        const float*, cudaStream_t);
+template void launch_cell_gs_pair<double>(const Geom&, Coef<double>, const double*, double*,
+                                          const double*, cudaStream_t);
+template void launch_cell_gs_pair<float>(const Geom&, Coef<float>, const float*, float*,
+                                         const float*, cudaStream_t);
+
+}  // namespace stk

@@ -34,17 +34,19 @@ const char* kProfNames[STK_NPROF] = {
     "vel_prolong_add",  "cell_smooth_colour", "cell_residual", "cell_restrict",
     "cell_prolong_add", "precond_algebra",   "mean_removal",  "arnoldi_multidot",
     "arnoldi_update",   "krylov_combine",    "convert",       "coarse_levels",
-    "vel_smooth_colour_l0", "cell_smooth_colour_l0", "unused_18", "unused_19"};
+    "vel_smooth_colour_l0", "cell_smooth_colour_l0", "vel_smooth_pair_l0", "vel_smooth_pair",
+    "cell_smooth_pair_l0", "cell_smooth_pair", "unused_22", "unused_23"};
 
 enum {
     PF_MATVEC = 0, PF_VSMOOTH, PF_VRES, PF_VRESTR, PF_VPROL, PF_CSMOOTH, PF_CRES, PF_CRESTR,
     PF_CPROL, PF_ALG, PF_MEAN, PF_MDOT, PF_UPD, PF_COMB, PF_CONV, PF_COARSE, PF_VSMOOTH0,
-    PF_CSMOOTH0
+    PF_CSMOOTH0, PF_VPAIR0, PF_VPAIR, PF_CPAIR0, PF_CPAIR
 };
 
 template <typename T>
 struct Work {            // multigrid work vectors of one level
     T *phi_u, *rhs_u, *res_u, *phi_p, *rhs_p, *res_p;
+    T *alt_u, *alt_p;    // second buffers of the out-of-place two-colour sweeps
 };
 
 struct Level {
@@ -81,6 +83,7 @@ struct stk_handle {
     double *bk = nullptr, *xk = nullptr, *tmp = nullptr;
     int lcoarse_d = 0, lcoarse_f = 0;        // first level run by the coarse kernel (FP64, FP32)
     int tpb_d = 256, tpb_f = 256;            // threads per block of the colour kernels
+    int lpair_d = 1, lpair_f = 0;            // first level smoothed by the two-colour kernels
     CLevel<double>* cld = nullptr;           // device copies of the level descriptors
     CLevel<float>* clf = nullptr;
     double* red = nullptr;    // reduction scratch (RED_BLOCKS * 36 doubles)
@@ -118,6 +121,7 @@ constexpr int DS_SUM = 0;     // mean removal sums
 constexpr int DS_H = 8;       // Arnoldi column h[0..m+1]
 constexpr int DS_N2 = 48;     // norms
 constexpr int DS_Y = 64;      // least-squares solution y
+constexpr int DS_THETA = 100; // theta = 1/dt (read by the preconditioner graphs)
 
 int fail(stk_handle* h, int code, const char* fmt, ...) {
     char buf[512];
@@ -279,6 +283,9 @@ template <typename T> int lcoarse_of(const stk_handle* h) {
     return sizeof(T) == 8 ? h->lcoarse_d : h->lcoarse_f;
 }
 template <typename T> int tpb_of(const stk_handle* h) { return sizeof(T) == 8 ? h->tpb_d : h->tpb_f; }
+template <typename T> int lpair_of(const stk_handle* h) {
+    return sizeof(T) == 8 ? h->lpair_d : h->lpair_f;
+}
 template <typename T> const CLevel<T>* clev_of(const stk_handle* h);
 template <> const CLevel<double>* clev_of<double>(const stk_handle* h) { return h->cld; }
 template <> const CLevel<float>* clev_of<float>(const stk_handle* h) { return h->clf; }
@@ -308,26 +315,64 @@ double updated_faces(const Geom& g, int a) {   // unknown a-faces of one colour
 }
 
 template <typename T>
-void vel_sweeps(stk_handle* h, const Level& L, int nsweep, T* phi, const T* rhs, cudaStream_t s) {
+double bytes_vel_pair(const Geom& g, int a) {
+    double e = 0;
+    for (int b = 0; b < g.dim; ++b)
+        if (b != a) e += g.esize[a + b - 1];
+    // comp a: rhs, alpha (or inverse diagonal) read and phi written; phi of
+    // all components, mu_c and the edge viscosities of comp a read
+    return sizeof(T) * (3.0 * g.fsize[a] + g.nvel + g.ncell + e);
+}
+
+// nsweep Gauss-Seidel sweeps of the velocity on level l.  From the level
+// lpair on, pairs of sweeps run as out-of-place two-colour kernels that
+// alternate between phi and the level's second buffer (an even count ends
+// in phi); an odd last sweep, and levels below lpair, use one launch per
+// colour in place.
+template <typename T>
+void vel_sweeps(stk_handle* h, int l, int nsweep, T* phi, const T* rhs, cudaStream_t s) {
+    const Level& L = h->lev[l];
     Coef<T> C = coef_of<T>(L);
-    const bool fine = &L == &h->lev[0];
-    for (int it = 0; it < nsweep; ++it)
+    const bool fine = l == 0;
+    const double fl = flops_vel_point<T>(L.g.dim);
+    int it = 0;
+    if (l >= lpair_of<T>(h)) {
+        T* buf[2] = {phi, work_of<T>(L).alt_u};
+        for (; it < (nsweep & ~1); ++it)
+            for (int a = 0; a < L.g.dim; ++a) {
+                Scope sc(h, fine ? PF_VPAIR0 : PF_VPAIR, bytes_vel_pair<T>(L.g, a), s, 1,
+                         2.0 * fl * updated_faces(L.g, a));
+                launch_vel_gs_pair<T>(L.g, C, a, buf[it & 1], buf[(it + 1) & 1], rhs, s);
+            }
+    }
+    for (; it < nsweep; ++it)
         for (int a = 0; a < L.g.dim; ++a)
             for (int par = 0; par < 2; ++par) {
                 Scope sc(h, fine ? PF_VSMOOTH0 : PF_VSMOOTH, bytes_vel_colour<T>(L.g, a), s, 1,
-                         flops_vel_point<T>(L.g.dim) * updated_faces(L.g, a));
+                         fl * updated_faces(L.g, a));
                 launch_vel_gs_colour<T>(L.g, C, a, par, phi, rhs, s, tpb_of<T>(h));
             }
 }
 
 template <typename T>
-void cell_sweeps(stk_handle* h, const Level& L, int nsweep, T* phi, const T* rhs, cudaStream_t s) {
+void cell_sweeps(stk_handle* h, int l, int nsweep, T* phi, const T* rhs, cudaStream_t s) {
+    const Level& L = h->lev[l];
     Coef<T> C = coef_of<T>(L);
-    const bool fine = &L == &h->lev[0];
-    for (int it = 0; it < nsweep; ++it)
+    const bool fine = l == 0;
+    const double fl = (sizeof(T) == 8 ? 15.0 : 40.0) * 0.5 * L.g.ncell;
+    int it = 0;
+    if (l >= lpair_of<T>(h)) {
+        T* buf[2] = {phi, work_of<T>(L).alt_p};
+        for (; it < (nsweep & ~1); ++it) {
+            // rhs and inverse diagonal read, phi read and written, beta read
+            Scope sc(h, fine ? PF_CPAIR0 : PF_CPAIR, sizeof(T) * (4.0 * L.g.ncell + L.g.nvel), s,
+                     1, 2.0 * fl);
+            launch_cell_gs_pair<T>(L.g, C, buf[it & 1], buf[(it + 1) & 1], rhs, s);
+        }
+    }
+    for (; it < nsweep; ++it)
         for (int par = 0; par < 2; ++par) {
-            Scope sc(h, fine ? PF_CSMOOTH0 : PF_CSMOOTH, bytes_cell_colour<T>(L.g), s, 1,
-                     (sizeof(T) == 8 ? 15.0 : 40.0) * 0.5 * L.g.ncell);
+            Scope sc(h, fine ? PF_CSMOOTH0 : PF_CSMOOTH, bytes_cell_colour<T>(L.g), s, 1, fl);
             launch_cell_gs_colour<T>(L.g, C, par, phi, rhs, s, tpb_of<T>(h));
         }
 }
@@ -346,12 +391,12 @@ void vcycle_vel(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp, 
     }
     launch_zero<T>(L.g.nvel, phi, s);
     if (l + 1 == (int)h->lev.size()) {
-        vel_sweeps<T>(h, L, mp.ncoarse, phi, rhs, s);
+        vel_sweeps<T>(h, l, mp.ncoarse, phi, rhs, s);
         return;
     }
     const Level& Lc = h->lev[l + 1];
     Work<T> Wc = work_of<T>(Lc);
-    vel_sweeps<T>(h, L, mp.nu, phi, rhs, s);
+    vel_sweeps<T>(h, l, mp.nu, phi, rhs, s);
     {
         Scope sc(h, PF_VRES, bytes_vel_residual<T>(L.g), s);
         launch_vel_residual<T>(L.g, coef_of<T>(L), phi, rhs, W.res_u, s);
@@ -365,7 +410,7 @@ void vcycle_vel(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp, 
         Scope sc(h, PF_VPROL, sizeof(T) * (2.0 * L.g.nvel + Lc.g.nvel), s);
         launch_vel_prolong_add<T>(Lc.g, Wc.phi_u, L.g, phi, s);
     }
-    vel_sweeps<T>(h, L, mp.nu, phi, rhs, s);
+    vel_sweeps<T>(h, l, mp.nu, phi, rhs, s);
 }
 
 // One pressure V-cycle for L_rho phi = rhs with phi = 0 initially (App. C).
@@ -381,12 +426,12 @@ void vcycle_cell(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp,
     }
     launch_zero<T>(L.g.ncell, phi, s);
     if (l + 1 == (int)h->lev.size()) {
-        cell_sweeps<T>(h, L, mp.ncoarse, phi, rhs, s);
+        cell_sweeps<T>(h, l, mp.ncoarse, phi, rhs, s);
         return;
     }
     const Level& Lc = h->lev[l + 1];
     Work<T> Wc = work_of<T>(Lc);
-    cell_sweeps<T>(h, L, mp.nu, phi, rhs, s);
+    cell_sweeps<T>(h, l, mp.nu, phi, rhs, s);
     {
         Scope sc(h, PF_CRES, sizeof(T) * (3.0 * L.g.ncell + L.g.nvel), s);
         launch_cell_residual<T>(L.g, coef_of<T>(L), phi, rhs, W.res_p, s);
@@ -400,7 +445,7 @@ void vcycle_cell(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp,
         Scope sc(h, PF_CPROL, sizeof(T) * (2.0 * L.g.ncell + Lc.g.ncell), s);
         launch_cell_prolong_add<T>(Lc.g, Wc.phi_p, L.g, phi, s);
     }
-    cell_sweeps<T>(h, L, mp.nu, phi, rhs, s);
+    cell_sweeps<T>(h, l, mp.nu, phi, rhs, s);
 }
 
 // phi = L~_rho^{-1} (r - mean r): the Poisson right-hand side is projected
@@ -437,8 +482,7 @@ void apply_precond(stk_handle* h, int which, const T* b, T* x, const MGParams& m
     const T* bp = b + g.nvel;
     T* xu = x;
     T* xp = x + g.nvel;
-    const double th = h->theta;
-    const bool pois = th != 0.0;
+    const bool pois = h->theta != 0.0;
     const double alg_cell = sizeof(T) * 3.0 * g.ncell + sizeof(T) * g.nvel;
     switch (which) {
     case STK_P1: {
@@ -449,19 +493,19 @@ void apply_precond(stk_handle* h, int which, const T* b, T* x, const MGParams& m
             Scope sc(h, PF_ALG, sizeof(T) * (3.0 * g.nvel + g.ncell), s);
             launch_sub_grad<T>(g, C.beta, B.xs, W.phi_p, xu, s);
         }
-        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, th, W.phi_p, C.mu_c, B.bc, xp, s); }
+        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, h->dsc + DS_THETA, W.phi_p, C.mu_c, B.bc, xp, s); }
         break;
     }
     case STK_P2: {
         vcycle_vel<T>(h, 0, bu, xu, mp, s);
         { Scope sc(h, PF_ALG, alg_cell, s); launch_div_plus<T>(g, xu, bp, B.bc, s); }
         if (pois) poisson_solve<T>(h, B.bc, W.phi_p, mp, s);
-        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, th, pois ? W.phi_p : nullptr, C.mu_c, B.bc, xp, s); }
+        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, h->dsc + DS_THETA, pois ? W.phi_p : nullptr, C.mu_c, B.bc, xp, s); }
         break;
     }
     case STK_P3: {
         if (pois) poisson_solve<T>(h, bp, W.phi_p, mp, s);
-        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, th, pois ? W.phi_p : nullptr, C.mu_c, bp, xp, s); }
+        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, h->dsc + DS_THETA, pois ? W.phi_p : nullptr, C.mu_c, bp, xp, s); }
         {
             Scope sc(h, PF_ALG, sizeof(T) * (2.0 * g.nvel + g.ncell), s);
             launch_sub_grad<T>(g, (const T*)nullptr, bu, xp, B.tmpu, s);
@@ -472,14 +516,14 @@ void apply_precond(stk_handle* h, int which, const T* b, T* x, const MGParams& m
     case STK_P4: {
         vcycle_vel<T>(h, 0, bu, xu, mp, s);
         if (pois) poisson_solve<T>(h, bp, W.phi_p, mp, s);
-        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, th, pois ? W.phi_p : nullptr, C.mu_c, bp, xp, s); }
+        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, h->dsc + DS_THETA, pois ? W.phi_p : nullptr, C.mu_c, bp, xp, s); }
         break;
     }
     default: {  // STK_P5
         vcycle_vel<T>(h, 0, bu, B.xs, mp, s);
         { Scope sc(h, PF_ALG, alg_cell, s); launch_div_plus<T>(g, B.xs, bp, B.bc, s); }
         if (pois) poisson_solve<T>(h, B.bc, W.phi_p, mp, s);
-        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, th, pois ? W.phi_p : nullptr, C.mu_c, B.bc, xp, s); }
+        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, h->dsc + DS_THETA, pois ? W.phi_p : nullptr, C.mu_c, B.bc, xp, s); }
         {
             Scope sc(h, PF_ALG, bytes_vel_residual<T>(g), s);
             launch_vel_correction_rhs<T>(g, C, bu, xp, B.xs, B.tmpu, s);
@@ -638,7 +682,7 @@ struct Arnoldi {
 // ||w||^2 before) and one update pass (which gives ||w||^2 after); when the
 // norm falls below 1/sqrt(2) of its start a second pass re-orthogonalises.
 // The projections and norms are staged to pinned host memory.
-constexpr int HP_H = 0, HP_AFTER = 40, HP_NRM = 41, HP_H2 = 64, HP_Y = 128;
+constexpr int HP_H = 0, HP_AFTER = 40, HP_NRM = 41, HP_H2 = 64, HP_Y = 128, HP_THETA = 250;
 
 void orth_enqueue(stk_handle* h, int j, int pass, cudaStream_t s) {
     const int n = nstokes(h);
@@ -1013,12 +1057,16 @@ int stk_create(int dim, const int* n, double hh, const int* bc, stk_handle** out
         CKC(dalloc(h, &L.wd.phi_p, g.ncell));
         CKC(dalloc(h, &L.wd.rhs_p, g.ncell));
         CKC(dalloc(h, &L.wd.res_p, g.ncell));
+        CKC(dalloc(h, &L.wd.alt_u, g.nvel));
+        CKC(dalloc(h, &L.wd.alt_p, g.ncell));
         CKC(dalloc(h, &L.wf.phi_u, g.nvel));
         CKC(dalloc(h, &L.wf.rhs_u, g.nvel));
         CKC(dalloc(h, &L.wf.res_u, g.nvel));
         CKC(dalloc(h, &L.wf.phi_p, g.ncell));
         CKC(dalloc(h, &L.wf.rhs_p, g.ncell));
         CKC(dalloc(h, &L.wf.res_p, g.ncell));
+        CKC(dalloc(h, &L.wf.alt_u, g.nvel));
+        CKC(dalloc(h, &L.wf.alt_p, g.ncell));
     }
     const Geom& g0 = h->lev[0].g;
     const int ns = g0.nvel + g0.ncell;
@@ -1095,10 +1143,17 @@ int stk_set_coefficients(stk_handle* h, const double* rho, const double* mu, dou
     if (h->hpin[1] != 0.0) return fail(h, STK_ERR_ARG, "rho <= 0 or mu < 0 at %g cells", h->hpin[1]);
     bool all_periodic = true;
     for (int a = 0; a < h->dim; ++a) all_periodic = all_periodic && g0.per[a];
-    clear_graphs(h);   // the graphs bake in the Poisson solve (theta != 0) or not
-    h->theta = std::isinf(dt) ? 0.0 : 1.0 / dt;
-    if (h->theta == 0.0 && all_periodic)
+    const double theta = std::isinf(dt) ? 0.0 : 1.0 / dt;
+    if (theta == 0.0 && all_periodic)
         return fail(h, STK_ERR_ARG, "steady flow on an all-periodic grid (constant-velocity null space) is not supported");
+    // The preconditioner graphs hold pointers only (coefficients and theta
+    // are read from device memory), except that they contain the Poisson
+    // solve or not: rebuild them only when theta changes between zero and
+    // non-zero.
+    if (!h->coef_set || (theta != 0.0) != (h->theta != 0.0)) clear_graphs(h);
+    h->theta = theta;
+    h->hpin[HP_THETA] = theta;
+    CK(cudaMemcpyAsync(h->dsc + DS_THETA, h->hpin + HP_THETA, sizeof(double), cudaMemcpyHostToDevice, s));
     launch_fine_coefficients(g0, rho, mu, h->theta, h->lev[0].cd, s);
     for (size_t l = 1; l < h->lev.size(); ++l)
         launch_coarsen_coefficients(h->lev[l - 1].g, h->lev[l - 1].cd, h->lev[l].g, h->lev[l].cd, s);
@@ -1266,6 +1321,7 @@ int stk_get_schedule(const stk_handle* h, int precision, stk_schedule* out) {
     if (!h || !out || (precision != STK_FP64 && precision != STK_MIXED)) return STK_ERR_ARG;
     out->coarse_level = precision == STK_FP64 ? h->lcoarse_d : h->lcoarse_f;
     out->threads = precision == STK_FP64 ? h->tpb_d : h->tpb_f;
+    out->pair_level = precision == STK_FP64 ? h->lpair_d : h->lpair_f;
     return STK_OK;
 }
 
@@ -1277,13 +1333,17 @@ int stk_set_schedule(stk_handle* h, int precision, const stk_schedule* sc) {
         return fail(h, STK_ERR_ARG, "coarse_level must be in 0..%d", (int)h->lev.size());
     if (sc->threads != 64 && sc->threads != 128 && sc->threads != 256 && sc->threads != 512)
         return fail(h, STK_ERR_ARG, "threads must be 64, 128, 256 or 512");
+    if (sc->pair_level < 0 || sc->pair_level > (int)h->lev.size())
+        return fail(h, STK_ERR_ARG, "pair_level must be in 0..%d", (int)h->lev.size());
     clear_graphs(h);
     if (precision == STK_FP64) {
         h->lcoarse_d = sc->coarse_level;
         h->tpb_d = sc->threads;
+        h->lpair_d = sc->pair_level;
     } else {
         h->lcoarse_f = sc->coarse_level;
         h->tpb_f = sc->threads;
+        h->lpair_f = sc->pair_level;
     }
     return STK_OK;
 }
@@ -1345,19 +1405,25 @@ int stk_autotune(stk_handle* h, int precision, stk_schedule* best, void* stream)
     for (int lc = 0; lc <= nl; ++lc) {
         // the single-block kernel only pays on small levels
         if (lc < nl && h->lev[lc].g.ncell > 65536) continue;
-        for (int ti = 0; ti < 3; ++ti) {
-            stk_schedule c{lc, threads[ti]};
-            int rc = stk_set_schedule(h, precision, &c);
-            if (rc) { h->prof = prof; return rc; }
-            float ms = 0.f;
-            rc = precision == STK_FP64 ? time_vcycles<double>(h, 3, s, &ms)
-                                       : time_vcycles<float>(h, 3, s, &ms);
-            if (rc) { h->prof = prof; return rc; }
-            if (ms < bms) {
-                bms = ms;
-                bs = c;
+        // two-colour kernels from level 0, 1 or 2, or not at all (pair_level
+        // = lc); the colour block size only matters below pair_level
+        int pls[4], npl = 0;
+        for (int p = 0; p < 3 && p < lc; ++p) pls[npl++] = p;
+        pls[npl++] = lc;
+        for (int k = 0; k < npl; ++k)
+            for (int ti = 0; ti < (pls[k] == 0 ? 1 : 3); ++ti) {
+                stk_schedule c{lc, threads[ti], pls[k]};
+                int rc = stk_set_schedule(h, precision, &c);
+                if (rc) { h->prof = prof; return rc; }
+                float ms = 0.f;
+                rc = precision == STK_FP64 ? time_vcycles<double>(h, 3, s, &ms)
+                                           : time_vcycles<float>(h, 3, s, &ms);
+                if (rc) { h->prof = prof; return rc; }
+                if (ms < bms) {
+                    bms = ms;
+                    bs = c;
+                }
             }
-        }
     }
     h->prof = prof;
     int rc = stk_set_schedule(h, precision, &bs);

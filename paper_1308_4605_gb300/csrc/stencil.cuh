@@ -154,15 +154,16 @@ __device__ __forceinline__ T visc_h2_any(int a, const Geom& g, const Coef<T>& C,
 // derivative over h/2, Sec. 3.1; f = 1 inside).  A Gauss-Seidel step is then
 // phi_A <- (rhs + N / h^2) / (alpha + dsum / h^2) with no term in the old
 // phi_A, and the operator is A phi = diag phi_A - N / h^2.
-template <int DIM, int A, typename T, typename TV, bool DIAG>
-__device__ __forceinline__ T visc_offdiag_h2(const Geom& g, const Coef<T>& C, const int q[3],
-                                             const TV* phi, T& dsum) {
+template <int DIM, int A, typename T, bool DIAG, typename PA, typename PB>
+__device__ __forceinline__ T visc_offdiag_acc(const Geom& g, const Coef<T>& C, const int q[3],
+                                              const PA& pa, const PB& pb, T& dsum) {
+    // pa(r): phi_A at the A-face r; pb(B, r): phi_B at the B-face r
     int qp[3] = {q[0], q[1], q[2]};
     int qm[3] = {q[0], q[1], q[2]};
     qp[A] = step(g, A, q[A], 1);
     qm[A] = step(g, A, q[A], -1);
-    const T pp = T(phi[fidx(g, A, qp)]);
-    const T pm = T(phi[fidx(g, A, qm)]);
+    const T pp = pa(qp);
+    const T pm = pa(qm);
     const T mh = ld(C.mu_c + cidx(g, q));
     const T ml = ld(C.mu_c + cidx(g, qm));
     T N = mh * pp;
@@ -184,20 +185,28 @@ __device__ __forceinline__ T visc_offdiag_h2(const Geom& g, const Coef<T>& C, co
         r0[A] = qm[A];
         int r2[3] = {qe[0], qe[1], qe[2]};
         r2[A] = qm[A];
-        const T xlo = T(phi[fidx(g, B, q)]) - T(phi[fidx(g, B, r0)]);
-        const T xhi = T(phi[fidx(g, B, qe)]) - T(phi[fidx(g, B, r2)]);
+        const T xlo = pb(B, q) - pb(B, r0);
+        const T xhi = pb(B, qe) - pb(B, r2);
         T shi = xhi, slo = -xlo;
-        if (!whi) shi += T(phi[fidx(g, A, qe)]);
+        if (!whi) shi += pa(qe);
         if (!wlo) {
             int qb[3] = {q[0], q[1], q[2]};
             qb[B] = step(g, B, q[B], -1);
-            slo += T(phi[fidx(g, A, qb)]);
+            slo += pa(qb);
         }
         N = fma(mhi, shi, N);
         N = fma(mlo, slo, N);
         if (DIAG) dsum += (whi ? T(2) : T(1)) * mhi + (wlo ? T(2) : T(1)) * mlo;
     }
     return N;
+}
+
+template <int DIM, int A, typename T, typename TV, bool DIAG>
+__device__ __forceinline__ T visc_offdiag_h2(const Geom& g, const Coef<T>& C, const int q[3],
+                                             const TV* phi, T& dsum) {
+    return visc_offdiag_acc<DIM, A, T, DIAG>(
+        g, C, q, [&](const int* r) { return T(phi[fidx(g, A, r)]); },
+        [&](int B, const int* r) { return T(phi[fidx(g, B, r)]); }, dsum);
 }
 
 template <int DIM, typename T, typename TV, bool DIAG>
@@ -211,9 +220,10 @@ __device__ __forceinline__ T visc_offdiag_any(int a, const Geom& g, const Coef<T
 // Off-diagonal part of h^2 L_rho at cell q: Nc = sum_a (beta_hi phi[+a] +
 // beta_lo phi[-a]) and bsum = sum_a (beta_hi + beta_lo), so that
 // h^2 (L_rho phi)_q = Nc - bsum phi_q (beta = 0 on wall faces).
-template <int DIM, typename T, typename TV>
-__device__ __forceinline__ T poisson_offdiag_h2(const Geom& g, const Coef<T>& C, const int q[3],
-                                                const TV* phi, T& bsum) {
+template <int DIM, typename T, typename PC>
+__device__ __forceinline__ T poisson_offdiag_acc(const Geom& g, const Coef<T>& C, const int q[3],
+                                                 const PC& pc, T& bsum) {
+    // pc(r): phi at cell r
     T N = T(0);
     bsum = T(0);
 #pragma unroll
@@ -226,11 +236,18 @@ __device__ __forceinline__ T poisson_offdiag_h2(const Geom& g, const Coef<T>& C,
         int cl[3] = {q[0], q[1], q[2]};
         ch[a] = g.per[a] ? wrapm(q[a] + 1, g.n[a]) : min(q[a] + 1, g.n[a] - 1);
         cl[a] = g.per[a] ? wrapm(q[a] - 1, g.n[a]) : max(q[a] - 1, 0);
-        N = fma(bh, T(phi[cidx(g, ch)]), N);
-        N = fma(bl, T(phi[cidx(g, cl)]), N);
+        N = fma(bh, pc(ch), N);
+        N = fma(bl, pc(cl), N);
         bsum += bh + bl;
     }
     return N;
+}
+
+template <int DIM, typename T, typename TV>
+__device__ __forceinline__ T poisson_offdiag_h2(const Geom& g, const Coef<T>& C, const int q[3],
+                                                const TV* phi, T& bsum) {
+    return poisson_offdiag_acc<DIM, T>(g, C, q, [&](const int* r) { return T(phi[cidx(g, r)]); },
+                                       bsum);
 }
 
 // (L_rho phi) at cell q and its diagonal; beta = 0 on wall faces.
@@ -261,6 +278,15 @@ __device__ __forceinline__ T poisson_cell(const Geom& g, const Coef<T>& C, const
 // Gauss-Seidel update phi += D^{-1}(rhs - A phi) of the interior A-face q
 // (App. C, omega = 1).  FP32 forms the diagonal on the fly; FP64 loads the
 // stored inverse diagonal (an FP64 division costs more than the load).
+template <typename T>
+__device__ __forceinline__ T vel_gs_value(const Geom& g, const Coef<T>& C, int f, T N, T dsum,
+                                          const T* rhs) {
+    const T ih2 = gih2<T>(g);
+    const T num = fma(ih2, N, rhs[f]);
+    if constexpr (sizeof(T) == 4) return num / fma(ih2, dsum, ld(C.alpha + f));
+    else return num * ld(C.invd_u + f);
+}
+
 template <int DIM, int A, typename T>
 __device__ __forceinline__ void vel_gs_point(const Geom& g, const Coef<T>& C, const int q[3],
                                              T* phi, const T* rhs) {
@@ -268,10 +294,7 @@ __device__ __forceinline__ void vel_gs_point(const Geom& g, const Coef<T>& C, co
     T dsum;
     const T N = visc_offdiag_h2<DIM, A, T, T, F32>(g, C, q, phi, dsum);
     const int f = fidx(g, A, q);
-    const T ih2 = gih2<T>(g);
-    const T num = fma(ih2, N, rhs[f]);
-    if constexpr (F32) phi[f] = num / fma(ih2, dsum, ld(C.alpha + f));
-    else phi[f] = num * ld(C.invd_u + f);
+    phi[f] = vel_gs_value<T>(g, C, f, N, dsum, rhs);
 }
 
 template <int DIM, typename T>
@@ -382,16 +405,23 @@ __device__ __forceinline__ T vel_prolong_point(const Geom& gc, const int q[3],
     return acc;
 }
 
-template <int DIM, typename T>
-__device__ __forceinline__ void cell_gs_point(const Geom& g, const Coef<T>& C, const int q[3],
-                                              T* phi, const T* rhs) {
+template <int DIM, typename T, typename PC>
+__device__ __forceinline__ T cell_gs_value(const Geom& g, const Coef<T>& C, const int q[3],
+                                           const PC& pc, const T* rhs) {
     T bsum;
-    const T N = poisson_offdiag_h2<DIM, T, T>(g, C, q, phi, bsum);
+    const T N = poisson_offdiag_acc<DIM, T>(g, C, q, pc, bsum);
     const int c = cidx(g, q);
     const T ih2 = gih2<T>(g);
     const T num = fma(-ih2, N, rhs[c]);   // (rhs - off-diagonal part) / diag
-    if constexpr (sizeof(T) == 4) phi[c] = num / (-ih2 * bsum);
-    else phi[c] = num * ld(C.invd_p + c);
+    if constexpr (sizeof(T) == 4) return num / (-ih2 * bsum);
+    else return num * ld(C.invd_p + c);
+}
+
+template <int DIM, typename T>
+__device__ __forceinline__ void cell_gs_point(const Geom& g, const Coef<T>& C, const int q[3],
+                                              T* phi, const T* rhs) {
+    phi[cidx(g, q)] =
+        cell_gs_value<DIM, T>(g, C, q, [&](const int* r) { return T(phi[cidx(g, r)]); }, rhs);
 }
 
 template <int DIM, typename T>

@@ -26,7 +26,7 @@ STK_ERR_ARG, STK_ERR_SIZE, STK_ERR_CUDA, STK_ERR_NOT_CONVERGED = -1, -2, -3, -4
 STK_ERR_NONFINITE, STK_ERR_TIMEOUT, STK_ERR_STATE = -5, -6, -7
 STK_P1, STK_P2, STK_P3, STK_P4, STK_P5 = 1, 2, 3, 4, 5
 STK_FP64, STK_MIXED = 0, 1
-STK_NPROF = 20
+STK_NPROF = 24
 
 
 class StokesError(RuntimeError):
@@ -52,7 +52,11 @@ class stk_solve_info(ctypes.Structure):
 
 
 class stk_schedule(ctypes.Structure):
-    _fields_ = [("coarse_level", ctypes.c_int), ("threads", ctypes.c_int)]
+    _fields_ = [("coarse_level", ctypes.c_int), ("threads", ctypes.c_int),
+                ("pair_level", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class stk_batch_io(ctypes.Structure):
@@ -257,18 +261,18 @@ def stk_solve_batched(handles, params, b_us, b_ps, x_us, x_ps, stream=None):
 def stk_get_schedule(h, precision):
     sc = stk_schedule()
     _check(h, _lib.stk_get_schedule(h, int(precision), ctypes.byref(sc)))
-    return {"coarse_level": sc.coarse_level, "threads": sc.threads}
+    return sc.as_dict()
 
 
-def stk_set_schedule(h, precision, coarse_level, threads):
-    sc = stk_schedule(int(coarse_level), int(threads))
+def stk_set_schedule(h, precision, coarse_level, threads, pair_level):
+    sc = stk_schedule(int(coarse_level), int(threads), int(pair_level))
     return _check(h, _lib.stk_set_schedule(h, int(precision), ctypes.byref(sc)))
 
 
 def stk_autotune(h, precision, stream=None):
     sc = stk_schedule()
     _check(h, _lib.stk_autotune(h, int(precision), ctypes.byref(sc), _stream(stream)))
-    return {"coarse_level": sc.coarse_level, "threads": sc.threads}
+    return sc.as_dict()
 
 
 def stk_profile(h, enable):

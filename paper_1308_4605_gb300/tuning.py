@@ -1,9 +1,9 @@
 """Autotuned multigrid schedules, cached on disk.
 
 stk_autotune (C ABI) times every admissible schedule -- the level from which
-the single-block coarse kernel takes over, and the threads per block of the
-Gauss-Seidel colour kernels -- on the handle's own grid and applies the
-fastest.  `tune` wraps it with a JSON cache keyed by device name, grid,
+the single-block coarse kernel takes over, the level from which smoothing
+runs as two-colour kernels, and the threads per block of the per-colour
+Gauss-Seidel kernels -- on the handle's own grid and applies the fastest.  `tune` wraps it with a JSON cache keyed by device name, grid,
 boundary conditions and precision, so each shape is timed once per machine.
 Cache file: $STK_TUNING_CACHE, else ~/.cache/stokes_gb300/schedules.json.
 """
@@ -25,7 +25,7 @@ def cache_path():
 def _key(solver, precision):
     import torch
     dev = torch.cuda.get_device_name(torch.cuda.current_device())
-    return f"{dev}|{solver.dim}|{'x'.join(map(str, solver.n[:solver.dim]))}|" \
+    return f"s2|{dev}|{solver.dim}|{'x'.join(map(str, solver.n[:solver.dim]))}|" \
            f"{','.join(map(str, solver.bc[:2 * solver.dim]))}|{precision}"
 
 
@@ -45,7 +45,8 @@ def tune(solver, precision, path=None):
     key = _key(solver, precision)
     if key in cache:
         sc = cache[key]
-        S.stk_set_schedule(solver.handle, precision, sc["coarse_level"], sc["threads"])
+        S.stk_set_schedule(solver.handle, precision, sc["coarse_level"], sc["threads"],
+                           sc["pair_level"])
         return sc
     sc = S.stk_autotune(solver.handle, precision)
     cache = _load(path)

@@ -84,8 +84,9 @@ def test_batched_rejects_duplicate_handles(S):
 
 
 def test_schedules_change_timing_not_results(S, tmp_path):
-    """Every multigrid schedule (coarse-kernel level, colour block size) gives
-    bitwise the same solution; the autotuner picks one and caches it."""
+    """Every multigrid schedule (coarse-kernel level, two-colour level, colour
+    block size) gives bitwise the same solution; the autotuner picks one and
+    caches it."""
     from paper_1308_4605_gb300 import tuning
     pr = wl.config_c4_instance(5, 128)
     sv = S.StokesSolver(2, pr.n[:2], pr.bc[:4], pr.h)
@@ -96,8 +97,9 @@ def test_schedules_change_timing_not_results(S, tmp_path):
     nlev = 7                      # 128, 64, ..., 2
     for prec in (0, 1):
         ref = None
-        for lc, th in ((nlev, 256), (0, 256), (2, 128), (3, 512), (4, 64)):
-            S.stk_set_schedule(sv.handle, prec, lc, th)
+        for lc, th, pl in ((nlev, 256, nlev), (0, 256, 0), (2, 128, 0), (3, 512, 1), (4, 64, 4),
+                           (nlev, 128, 0), (5, 256, 2)):
+            S.stk_set_schedule(sv.handle, prec, lc, th, pl)
             xu, xp, info = sv.solve(bu, bp, precision=prec)
             assert info["converged"]
             if ref is None:
@@ -108,6 +110,91 @@ def test_schedules_change_timing_not_results(S, tmp_path):
         path = str(tmp_path / "sched.json")
         sc = tuning.tune(sv, prec, path)
         assert 0 <= sc["coarse_level"] <= nlev and sc["threads"] in (128, 256, 512)
+        assert 0 <= sc["pair_level"] <= sc["coarse_level"]
         assert tuning.tune(sv, prec, path) == sc          # cache hit
         assert S.stk_get_schedule(sv.handle, prec) == sc
+    sv.close()
+
+
+@pytest.mark.parametrize("bc", [(0,) * 6, (1, 1, 2, 1, 0, 0)])
+def test_two_colour_sweeps_equal_per_colour_3d(S, bc):
+    """3D: V-cycles and solves (FP64 and mixed) with the two-colour kernels
+    on every grid level equal, bitwise, those with one launch per colour
+    (periodic, and mixed no-slip / free-slip / periodic boundaries whose
+    face arrays are not multiples of the tile)."""
+    n = (64, 32, 16) if bc[0] == 0 else (32, 16, 16)
+    theta = 1.0 if bc[0] == 0 else 0.0
+    pr = wl.generic(3, n, bc, theta=theta, seed=41, precond=1 if theta else 2)
+    sv = S.StokesSolver(3, pr.n, pr.bc, pr.h)
+    sv.set_coefficients(_t(pr.rho), _t(pr.mu), pr.theta)
+    g = Grid(3, pr.n, pr.h, pr.bc)
+    rng = np.random.default_rng(4)
+    ru, rp = g.unpack(rng.standard_normal(g.size) * g.active)
+    ru = [_t(x) for x in ru]
+    rp = _t(rp - rp.mean())
+    bu = [_t(x) for x in pr.b_u]
+    bp = _t(pr.b_p)
+    sched = {p: S.stk_get_schedule(sv.handle, p) for p in (0, 1)}
+    out = []
+    for paired in (True, False):
+        for p in (0, 1):
+            sc = sched[p]
+            S.stk_set_schedule(sv.handle, p, sc["coarse_level"], sc["threads"],
+                               0 if paired else sc["coarse_level"])
+        xu = [torch.zeros_like(x) for x in ru]
+        xp = torch.zeros_like(rp)
+        S.stk_velocity_vcycle(sv.handle, ru, xu)
+        S.stk_pressure_vcycle(sv.handle, rp, xp)
+        torch.cuda.synchronize()
+        res = [xu, xp]
+        for prec in (0, 1):
+            su, sp, info = sv.solve(bu, bp, precision=prec, precond=pr.precond)
+            assert info["converged"]
+            res += [su, sp]
+        out.append(res)
+    for a, b in zip(out[0], out[1]):
+        if isinstance(a, list):
+            assert all(torch.equal(x, y) for x, y in zip(a, b))
+        else:
+            assert torch.equal(a, b)
+    sv.close()
+
+
+def test_coefficient_updates_keep_graphs_valid(S):
+    """set_coefficients keeps the captured preconditioner graphs unless theta
+    switches between zero and non-zero (they read coefficients and theta
+    from device memory): a solve after new coefficients and a new theta must
+    equal, bitwise, the same solve on a fresh handle."""
+    pr = wl.config_c1(32)
+    pr2 = wl.generic(2, (32, 32), (0,) * 4, theta=0.5, rho_contrast=5.0, mu_contrast=30.0, seed=77)
+    bu = [_t(x) for x in pr.b_u]
+    bp = _t(pr.b_p)
+    sv = S.StokesSolver(2, pr.n[:2], pr.bc[:4], pr.h)
+    for prec in (0, 1):
+        sv.set_coefficients(_t(pr.rho), _t(pr.mu), pr.theta)
+        sv.solve(bu, bp, precision=prec)
+        for rho, mu, theta in ((pr2.rho, pr2.mu, 0.5), (pr.rho, pr.mu, 2.0), (pr2.rho, pr2.mu, 0.5)):
+            sv.set_coefficients(_t(rho), _t(mu), theta)
+            xu, xp, info = sv.solve(bu, bp, precision=prec)
+            fresh = S.StokesSolver(2, pr.n[:2], pr.bc[:4], pr.h)
+            fresh.set_coefficients(_t(rho), _t(mu), theta)
+            fu, fp, finfo = fresh.solve(bu, bp, precision=prec)
+            fresh.close()
+            assert info["converged"] and info["iterations"] == finfo["iterations"]
+            assert all(torch.equal(a, b) for a, b in zip(xu, fu)) and torch.equal(xp, fp)
+    sv.close()
+    # theta switching to zero and back (walls: steady flow is admissible)
+    pw = wl.generic(2, (32, 32), (1,) * 4, theta=1.0, seed=78, precond=2)
+    sv = S.StokesSolver(2, pw.n[:2], pw.bc[:4], pw.h)
+    bu = [_t(x) for x in pw.b_u]
+    bp = _t(pw.b_p)
+    for theta in (1.0, 0.0, 3.0, 0.0):
+        sv.set_coefficients(_t(pw.rho), _t(pw.mu), theta)
+        xu, xp, info = sv.solve(bu, bp, precond=2)
+        fresh = S.StokesSolver(2, pw.n[:2], pw.bc[:4], pw.h)
+        fresh.set_coefficients(_t(pw.rho), _t(pw.mu), theta)
+        fu, fp, _ = fresh.solve(bu, bp, precond=2)
+        fresh.close()
+        assert info["converged"]
+        assert all(torch.equal(a, b) for a, b in zip(xu, fu)) and torch.equal(xp, fp)
     sv.close()
