@@ -78,6 +78,11 @@ typedef struct {
     int    precision;  /* STK_FP64 or STK_MIXED                                     */
     int    nu;         /* smoothing sweeps before and after the coarse correction (2) */
     int    ncoarse;    /* sweeps on the coarsest level (8, App. C)                  */
+    int    vcycles_u;  /* V-cycles per velocity subsolve (1; 1..64): the first from
+                        * zero, each further one on the residual, x += V(r - A x)
+                        * (the number of multigrid cycles of Sec. 4.1.2)           */
+    int    vcycles_p;  /* the same for the pressure subsolve (1; 1..64), residual
+                        * projected onto mean-zero vectors                         */
 } stk_solver_params;
 
 typedef struct {
@@ -92,7 +97,7 @@ typedef struct {
 } stk_solve_info;
 
 /* Default parameters: P1, m = 10, rtol = 1e-10, maxit = 1000, FP64, nu = 2,
- * ncoarse = 8 (Sec. 4.1.1, 4.1.2, 4.2.2, App. C). */
+ * ncoarse = 8, one V-cycle per subsolve (Sec. 4.1.1, 4.1.2, 4.2.2, App. C). */
 void stk_default_params(stk_solver_params* p);
 
 /* Create a grid of dim (2 or 3) dimensions with n[0..dim-1] cells per axis,
@@ -136,6 +141,15 @@ int stk_apply_operator(stk_handle* h, const double* const* x_u, const double* x_
 int stk_apply_preconditioner(stk_handle* h, int which, const double* const* b_u,
                              const double* b_p, double* const* x_u, double* x_p,
                              void* stream);
+
+/* The same with the subsolver settings of params (precond, precision, nu,
+ * ncoarse, vcycles_u, vcycles_p; the Krylov fields are ignored).  With
+ * precision STK_MIXED the preconditioner runs in FP32 on the FP32
+ * coefficient hierarchy (inputs rounded to FP32, outputs widened to FP64),
+ * as inside the flexible solve. */
+int stk_apply_preconditioner_params(stk_handle* h, const stk_solver_params* params,
+                                    const double* const* b_u, const double* b_p,
+                                    double* const* x_u, double* x_p, void* stream);
 
 /* One velocity V-cycle for A x = r (x = A~^{-1} r, zero initial guess, App. C)
  * and one pressure V-cycle for L_rho x = r (x = L~_rho^{-1} r), in FP64. */

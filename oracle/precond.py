@@ -17,6 +17,14 @@ diagonal of cell viscosities), rho^{-1} the diagonal of inverse face densities.
                              started from x*
 With theta = 0 the Poisson solve drops out of S~^{-1} (Sec. 2.2).
 
+Subsolvers with more than one multigrid cycle (Sec. 4.1.2 studies the
+number of V-cycles per application of the preconditioner): the velocity
+subsolve with c_u cycles is x = V(r), then c_u - 1 times x = x + V(r - A x)
+(multigrid as a stationary iteration); the pressure subsolve projects r onto
+mean-zero vectors, phi = V(r), then c_p - 1 times phi = phi + V(res) with
+res = r - L_rho phi projected onto mean-zero vectors.  As c grows both tend
+to the exact subsolves (pinned).
+
 Readings (stated, pinned by the exact-subsolver identities of App. B):
   * the pressure null space (constant p) is handled by removing the mean of
     every right-hand side handed to the Poisson solver and the mean of x_p;
@@ -43,12 +51,14 @@ from .grid import Grid
 
 
 class Preconditioner:
-    def __init__(self, grid: Grid, rho, mu, theta, which=1, exact=False, nu=2, ncoarse=8):
+    def __init__(self, grid: Grid, rho, mu, theta, which=1, exact=False, nu=2, ncoarse=8,
+                 cycles_u=1, cycles_p=1):
         self.grid = grid
         self.theta = float(theta)
         self.which = int(which)
         self.exact = exact
         self.nu, self.ncoarse = nu, ncoarse
+        self.cycles_u, self.cycles_p = int(cycles_u), int(cycles_p)
         self.coef = asm.fine_coefficients(grid, rho, mu, theta)
         self.mu = np.asarray(mu, dtype=np.float64).ravel()
         self.inv_rho_f = np.concatenate([np.asarray(b).ravel() for b in self.coef["beta"]])
@@ -71,13 +81,21 @@ class Preconditioner:
             out = np.zeros_like(r)
             out[self._va] = sla.lu_solve(self._A_lu, r[self._va])
             return out
-        return mg.vcycle_velocity(self.levels, r, 0, self.nu, self.ncoarse)
+        x = mg.vcycle_velocity(self.levels, r, 0, self.nu, self.ncoarse)
+        for _ in range(self.cycles_u - 1):
+            x = x + mg.vcycle_velocity(self.levels, r - self.A @ x, 0, self.nu, self.ncoarse)
+        return x
 
     def poisson_solve(self, r):
         r = r - r.mean()
         if self.exact:
             return self._L_pinv @ r
-        return mg.vcycle_pressure(self.levels, r, 0, self.nu, self.ncoarse)
+        phi = mg.vcycle_pressure(self.levels, r, 0, self.nu, self.ncoarse)
+        for _ in range(self.cycles_p - 1):
+            res = r - self.levels[0].Lrho @ phi
+            res = res - res.mean()
+            phi = phi + mg.vcycle_pressure(self.levels, res, 0, self.nu, self.ncoarse)
+        return phi
 
     def neg_schur_inverse(self, r):
         """-S~^{-1} r = theta L~^{-1} r - 2 mu r."""

@@ -63,6 +63,8 @@ struct PBuf {            // level-0 buffers of the preconditioner in precision T
     T* bc;               // cell: D x* + b_p
     T* tmpu;             // velocity temporary
     T* xs;               // velocity x*
+    T *ru, *du;          // velocity residual and correction of repeated V-cycles
+    T *rp, *dp;          // the same for the pressure
 };
 
 }  // namespace
@@ -83,7 +85,7 @@ struct stk_handle {
     double *bk = nullptr, *xk = nullptr, *tmp = nullptr;
     int lcoarse_d = 0, lcoarse_f = 0;        // first level run by the coarse kernel (FP64, FP32)
     int tpb_d = 256, tpb_f = 256;            // threads per block of the colour kernels
-    int lpair_d = 1, lpair_f = 0;            // first level smoothed by the two-colour kernels
+    int lpair_d = 0, lpair_f = 0;            // first level smoothed by the two-colour kernels
     CLevel<double>* cld = nullptr;           // device copies of the level descriptors
     CLevel<float>* clf = nullptr;
     double* red = nullptr;    // reduction scratch (RED_BLOCKS * 36 doubles)
@@ -98,7 +100,7 @@ struct stk_handle {
         long long kernels = 0;
         std::vector<ProfRec> recs;   // event pairs captured inside (profiling)
     };
-    std::map<std::tuple<int, int, const void*, void*, int, int, int>, GraphEntry> graphs;
+    std::map<std::tuple<int, int, const void*, void*, int, int, int, int>, GraphEntry> graphs;
     bool use_graphs = true;
     bool capturing = false;
     long long cap_kernels = 0;
@@ -296,6 +298,8 @@ template <> PBuf<float>& pbuf_of<float>(stk_handle* h) { return h->pf; }
 struct MGParams {
     int nu = 2;
     int ncoarse = 8;
+    int cu = 1;   // V-cycles per velocity subsolve
+    int cp = 1;   // V-cycles per pressure subsolve
 };
 
 // Floating-point operations of one Gauss-Seidel point update (adds + muls +
@@ -454,12 +458,46 @@ template <typename T>
 void poisson_solve(stk_handle* h, const T* r, T* phi, const MGParams& mp, cudaStream_t s) {
     const Level& L = h->lev[0];
     Work<T> W = work_of<T>(L);
+    PBuf<T>& B = pbuf_of<T>(h);
+    const int nc = L.g.ncell;
     {
-        Scope sc(h, PF_MEAN, 2.0 * sizeof(T) * L.g.ncell, s, 4);
-        launch_sum<T>(L.g.ncell, r, h->red, h->dsc + DS_SUM, s);
-        launch_copy_sub_mean<T>(L.g.ncell, r, W.rhs_p, h->dsc + DS_SUM, s);
+        Scope sc(h, PF_MEAN, 2.0 * sizeof(T) * nc, s, 4);
+        launch_sum<T>(nc, r, h->red, h->dsc + DS_SUM, s);
+        launch_copy_sub_mean<T>(nc, r, W.rhs_p, h->dsc + DS_SUM, s);
     }
     vcycle_cell<T>(h, 0, W.rhs_p, phi, mp, s);
+    // further cycles: phi += V(r - L phi), the residual projected onto
+    // mean-zero vectors like the right-hand side (Sec. 4.1.2)
+    for (int c = 1; c < mp.cp; ++c) {
+        {
+            Scope sc(h, PF_CRES, sizeof(T) * (3.0 * nc + L.g.nvel), s);
+            launch_cell_residual<T>(L.g, coef_of<T>(L), phi, W.rhs_p, B.rp, s);
+        }
+        {
+            Scope sc(h, PF_MEAN, 3.0 * sizeof(T) * nc, s, 4);
+            launch_sum<T>(nc, B.rp, h->red, h->dsc + DS_SUM + 4, s);
+            launch_sub_mean<T>(nc, B.rp, h->dsc + DS_SUM + 4, s);
+        }
+        vcycle_cell<T>(h, 0, B.rp, B.dp, mp, s);
+        { Scope sc(h, PF_ALG, 3.0 * sizeof(T) * nc, s); launch_axpy<T>(nc, T(1), B.dp, phi, s); }
+    }
+}
+
+// Velocity subsolve: mp.cu V-cycles, the first from zero, each further one
+// on the residual: x += V(r - A x) (Sec. 4.1.2).
+template <typename T>
+void velocity_solve(stk_handle* h, const T* r, T* x, const MGParams& mp, cudaStream_t s) {
+    vcycle_vel<T>(h, 0, r, x, mp, s);
+    const Level& L = h->lev[0];
+    PBuf<T>& B = pbuf_of<T>(h);
+    for (int c = 1; c < mp.cu; ++c) {
+        {
+            Scope sc(h, PF_VRES, bytes_vel_residual<T>(L.g), s);
+            launch_vel_residual<T>(L.g, coef_of<T>(L), x, r, B.ru, s);
+        }
+        vcycle_vel<T>(h, 0, B.ru, B.du, mp, s);
+        { Scope sc(h, PF_ALG, 3.0 * sizeof(T) * L.g.nvel, s); launch_axpy<T>(L.g.nvel, T(1), B.du, x, s); }
+    }
 }
 
 template <typename T>
@@ -486,7 +524,7 @@ void apply_precond(stk_handle* h, int which, const T* b, T* x, const MGParams& m
     const double alg_cell = sizeof(T) * 3.0 * g.ncell + sizeof(T) * g.nvel;
     switch (which) {
     case STK_P1: {
-        vcycle_vel<T>(h, 0, bu, B.xs, mp, s);
+        velocity_solve<T>(h, bu, B.xs, mp, s);
         { Scope sc(h, PF_ALG, alg_cell, s); launch_div_plus<T>(g, B.xs, bp, B.bc, s); }
         poisson_solve<T>(h, B.bc, W.phi_p, mp, s);
         {
@@ -497,7 +535,7 @@ void apply_precond(stk_handle* h, int which, const T* b, T* x, const MGParams& m
         break;
     }
     case STK_P2: {
-        vcycle_vel<T>(h, 0, bu, xu, mp, s);
+        velocity_solve<T>(h, bu, xu, mp, s);
         { Scope sc(h, PF_ALG, alg_cell, s); launch_div_plus<T>(g, xu, bp, B.bc, s); }
         if (pois) poisson_solve<T>(h, B.bc, W.phi_p, mp, s);
         { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, h->dsc + DS_THETA, pois ? W.phi_p : nullptr, C.mu_c, B.bc, xp, s); }
@@ -510,17 +548,17 @@ void apply_precond(stk_handle* h, int which, const T* b, T* x, const MGParams& m
             Scope sc(h, PF_ALG, sizeof(T) * (2.0 * g.nvel + g.ncell), s);
             launch_sub_grad<T>(g, (const T*)nullptr, bu, xp, B.tmpu, s);
         }
-        vcycle_vel<T>(h, 0, B.tmpu, xu, mp, s);
+        velocity_solve<T>(h, B.tmpu, xu, mp, s);
         break;
     }
     case STK_P4: {
-        vcycle_vel<T>(h, 0, bu, xu, mp, s);
+        velocity_solve<T>(h, bu, xu, mp, s);
         if (pois) poisson_solve<T>(h, bp, W.phi_p, mp, s);
         { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, h->dsc + DS_THETA, pois ? W.phi_p : nullptr, C.mu_c, bp, xp, s); }
         break;
     }
     default: {  // STK_P5
-        vcycle_vel<T>(h, 0, bu, B.xs, mp, s);
+        velocity_solve<T>(h, bu, B.xs, mp, s);
         { Scope sc(h, PF_ALG, alg_cell, s); launch_div_plus<T>(g, B.xs, bp, B.bc, s); }
         if (pois) poisson_solve<T>(h, B.bc, W.phi_p, mp, s);
         { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, h->dsc + DS_THETA, pois ? W.phi_p : nullptr, C.mu_c, B.bc, xp, s); }
@@ -528,7 +566,7 @@ void apply_precond(stk_handle* h, int which, const T* b, T* x, const MGParams& m
             Scope sc(h, PF_ALG, bytes_vel_residual<T>(g), s);
             launch_vel_correction_rhs<T>(g, C, bu, xp, B.xs, B.tmpu, s);
         }
-        vcycle_vel<T>(h, 0, B.tmpu, xu, mp, s);
+        velocity_solve<T>(h, B.tmpu, xu, mp, s);
         { Scope sc(h, PF_ALG, 3.0 * sizeof(T) * g.nvel, s); launch_axpy<T>(g.nvel, T(1), B.xs, xu, s); }
         break;
     }
@@ -560,7 +598,7 @@ int run_precond(stk_handle* h, int which, const T* b, T* x, const MGParams& mp, 
         return STK_OK;
     }
     auto key = std::make_tuple(which, (int)sizeof(T), (const void*)b, (void*)x, mp.nu, mp.ncoarse,
-                               h->prof ? 1 : 0);
+                               mp.cu * 1000 + mp.cp, h->prof ? 1 : 0);
     auto it = h->graphs.find(key);
     if (it == h->graphs.end()) {
         stk_handle::GraphEntry e;
@@ -590,12 +628,12 @@ int run_precond(stk_handle* h, int which, const T* b, T* x, const MGParams& mp, 
     return STK_OK;
 }
 
-double scalar_vcycles(const stk_handle* h, int which) {
-    double d = h->dim;
-    double p = h->theta != 0.0 ? 1.0 : 0.0;
-    if (which == STK_P1) return d + 1.0;
-    if (which == STK_P5) return 2.0 * d + p;
-    return d + p;
+double scalar_vcycles(const stk_handle* h, int which, const MGParams& mp) {
+    const double u = double(h->dim) * mp.cu;          // d scalar cycles per velocity cycle
+    const double p = h->theta != 0.0 ? mp.cp : 0.0;
+    if (which == STK_P1) return u + mp.cp;
+    if (which == STK_P5) return 2.0 * u + p;
+    return u + p;
 }
 
 int nstokes(const stk_handle* h) { return h->lev[0].g.nvel + h->lev[0].g.ncell; }
@@ -762,6 +800,8 @@ void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm) {
     MGParams mp;
     mp.nu = prm.nu;
     mp.ncoarse = prm.ncoarse;
+    mp.cu = prm.vcycles_u;
+    mp.cp = prm.vcycles_p;
     std::vector<Inst*> act;
     for (auto& it : insts) {
         it.hcol.assign(m + 2, 0.0);
@@ -820,7 +860,7 @@ void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm) {
             for (Inst* it : cyc) {
                 int rc = run_precond<double>(it->h, prm.precond, it->h->tmp, it->h->V[0], mp, it->s);
                 if (rc) { finish(it, rc); continue; }
-                it->info.scalar_vcycles += scalar_vcycles(it->h, prm.precond);
+                it->info.scalar_vcycles += scalar_vcycles(it->h, prm.precond, mp);
                 norm_enqueue(it->h, it->h->V[0], it->s);
             }
             sync_all(cyc);
@@ -872,7 +912,7 @@ void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm) {
                     }
                     if ((rc = run_precond<double>(h, prm.precond, h->tmp, h->V[j + 1], mp, it->s))) { finish(it, rc); continue; }
                 }
-                it->info.scalar_vcycles += scalar_vcycles(h, prm.precond);
+                it->info.scalar_vcycles += scalar_vcycles(h, prm.precond, mp);
                 orth_enqueue(h, j, 0, it->s);
             }
             sync_all(step);
@@ -951,6 +991,8 @@ int validate_params(stk_handle* h, const stk_solver_params& prm) {
     if (prm.maxit < 1) return fail(h, STK_ERR_ARG, "maxit must be >= 1");
     if (prm.precision != STK_FP64 && prm.precision != STK_MIXED) return fail(h, STK_ERR_ARG, "bad precision");
     if (prm.nu < 0 || prm.ncoarse < 1) return fail(h, STK_ERR_ARG, "bad sweep counts");
+    if (prm.vcycles_u < 1 || prm.vcycles_u > 64 || prm.vcycles_p < 1 || prm.vcycles_p > 64)
+        return fail(h, STK_ERR_ARG, "V-cycles per subsolve must be 1..64");
     return STK_OK;
 }
 
@@ -970,6 +1012,8 @@ void stk_default_params(stk_solver_params* p) {
     p->precision = STK_FP64;
     p->nu = 2;
     p->ncoarse = 8;
+    p->vcycles_u = 1;
+    p->vcycles_p = 1;
 }
 
 const char* stk_last_error(const stk_handle* h) {
@@ -1074,10 +1118,18 @@ int stk_create(int dim, const int* n, double hh, const int* bc, stk_handle** out
     CKC(dalloc(h, &h->pd.bc, g0.ncell));
     CKC(dalloc(h, &h->pd.tmpu, g0.nvel));
     CKC(dalloc(h, &h->pd.xs, g0.nvel));
+    CKC(dalloc(h, &h->pd.ru, g0.nvel));
+    CKC(dalloc(h, &h->pd.du, g0.nvel));
+    CKC(dalloc(h, &h->pd.rp, g0.ncell));
+    CKC(dalloc(h, &h->pd.dp, g0.ncell));
     CKC(dalloc(h, &h->pf.in, ns));
     CKC(dalloc(h, &h->pf.bc, g0.ncell));
     CKC(dalloc(h, &h->pf.tmpu, g0.nvel));
     CKC(dalloc(h, &h->pf.xs, g0.nvel));
+    CKC(dalloc(h, &h->pf.ru, g0.nvel));
+    CKC(dalloc(h, &h->pf.du, g0.nvel));
+    CKC(dalloc(h, &h->pf.rp, g0.ncell));
+    CKC(dalloc(h, &h->pf.dp, g0.ncell));
     CKC(dalloc(h, &h->bk, ns));
     CKC(dalloc(h, &h->xk, ns));
     CKC(dalloc(h, &h->tmp, ns));
@@ -1094,6 +1146,10 @@ int stk_create(int dim, const int* n, double hh, const int* bc, stk_handle** out
     {   // level descriptors of the single-block coarse-level kernel
         const int nl = (int)h->lev.size();
         h->lcoarse_d = h->lcoarse_f = nl;
+        // two-colour sweeps by default only in FP32 2D, where their halo
+        // recomputation is small (measured; the autotuner decides per grid)
+        h->lpair_d = nl;
+        h->lpair_f = h->dim == 2 ? 0 : nl;
         while (h->lcoarse_f > 0 && h->lev[h->lcoarse_f - 1].g.ncell <= COARSE_MAX_CELLS_F32) --h->lcoarse_f;
         while (h->lcoarse_d > 0 && h->lev[h->lcoarse_d - 1].g.ncell <= COARSE_MAX_CELLS_F64) --h->lcoarse_d;
         std::vector<CLevel<double>> cd(nl);
@@ -1198,6 +1254,37 @@ int stk_apply_preconditioner(stk_handle* h, int which, const double* const* b_u,
     if ((rc = gather(h, b_u, b_p, h->bk, s))) return rc;
     MGParams mp;
     apply_precond<double>(h, which, h->bk, h->tmp, mp, s);
+    CKL();
+    return scatter(h, h->tmp, x_u, x_p, s);
+}
+
+int stk_apply_preconditioner_params(stk_handle* h, const stk_solver_params* params,
+                                    const double* const* b_u, const double* b_p,
+                                    double* const* x_u, double* x_p, void* stream) {
+    if (!h) return STK_ERR_ARG;
+    if (!params) return fail(h, STK_ERR_ARG, "null params");
+    if (!h->coef_set) return fail(h, STK_ERR_STATE, "coefficients not set");
+    int rc;
+    if ((rc = validate_params(h, *params))) return rc;
+    if ((rc = check_ptrs(h, (const void* const*)b_u, b_p))) return rc;
+    if ((rc = check_ptrs(h, (const void* const*)x_u, x_p))) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(cudaSetDevice(h->device));
+    MGParams mp;
+    mp.nu = params->nu;
+    mp.ncoarse = params->ncoarse;
+    mp.cu = params->vcycles_u;
+    mp.cp = params->vcycles_p;
+    if ((rc = gather(h, b_u, b_p, h->bk, s))) return rc;
+    if (params->precision == STK_MIXED) {
+        if ((rc = ensure_krylov(h, 1))) return rc;
+        const int n = nstokes(h);
+        launch_convert<double, float>(n, h->bk, h->pf.in, s);
+        apply_precond<float>(h, params->precond, h->pf.in, h->Z[0], mp, s);
+        launch_convert<float, double>(n, h->Z[0], h->tmp, s);
+    } else {
+        apply_precond<double>(h, params->precond, h->bk, h->tmp, mp, s);
+    }
     CKL();
     return scatter(h, h->tmp, x_u, x_p, s);
 }

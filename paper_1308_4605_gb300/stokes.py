@@ -38,7 +38,7 @@ class StokesError(RuntimeError):
 class stk_solver_params(ctypes.Structure):
     _fields_ = [("precond", ctypes.c_int), ("restart", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("maxit", ctypes.c_int), ("precision", ctypes.c_int), ("nu", ctypes.c_int),
-                ("ncoarse", ctypes.c_int)]
+                ("ncoarse", ctypes.c_int), ("vcycles_u", ctypes.c_int), ("vcycles_p", ctypes.c_int)]
 
 
 class stk_solve_info(ctypes.Structure):
@@ -83,6 +83,7 @@ def _load():
         "stk_set_coefficients": (I, [P, P, P, D, P]),
         "stk_apply_operator": (I, [P, PP, P, PP, P, P]),
         "stk_apply_preconditioner": (I, [P, I, PP, P, PP, P, P]),
+        "stk_apply_preconditioner_params": (I, [P, ctypes.POINTER(stk_solver_params), PP, P, PP, P, P]),
         "stk_velocity_vcycle": (I, [P, PP, PP, P]),
         "stk_pressure_vcycle": (I, [P, P, P, P]),
         "stk_solve": (I, [P, ctypes.POINTER(stk_solver_params), PP, P, PP, P,
@@ -109,7 +110,7 @@ def _load():
 _lib = _load()
 EXPORTED = ["stk_default_params", "stk_create", "stk_destroy", "stk_last_error", "stk_face_length",
             "stk_cell_length", "stk_set_coefficients", "stk_apply_operator",
-            "stk_apply_preconditioner", "stk_velocity_vcycle", "stk_pressure_vcycle", "stk_solve",
+            "stk_apply_preconditioner", "stk_apply_preconditioner_params", "stk_velocity_vcycle", "stk_pressure_vcycle", "stk_solve",
             "stk_profile", "stk_profile_read", "stk_kernel_launches", "stk_pressure_vcycle_noalloc", "stk_gradient", "stk_solve_batched", "stk_get_schedule", "stk_set_schedule", "stk_autotune"]
 
 
@@ -209,6 +210,13 @@ def stk_apply_preconditioner(h, which, b_u, b_p, x_u, x_p, stream=None):
     fl, nc = _lengths(h, len(b_u))
     return _check(h, _lib.stk_apply_preconditioner(h, int(which), _ptrs(b_u, fl), _ptr(b_p, nc),
                                                    _ptrs(x_u, fl), _ptr(x_p, nc), _stream(stream)))
+
+
+def stk_apply_preconditioner_params(h, params, b_u, b_p, x_u, x_p, stream=None):
+    fl, nc = _lengths(h, len(b_u))
+    return _check(h, _lib.stk_apply_preconditioner_params(
+        h, ctypes.byref(params), _ptrs(b_u, fl), _ptr(b_p, nc), _ptrs(x_u, fl), _ptr(x_p, nc),
+        _stream(stream)))
 
 
 def stk_velocity_vcycle(h, r_u, x_u, stream=None):
@@ -358,9 +366,18 @@ class StokesSolver:
         stk_apply_operator(self.handle, x_u, x_p, y_u, y_p)
         return y_u, y_p
 
-    def apply_preconditioner(self, which, b_u, b_p):
+    def apply_preconditioner(self, which, b_u, b_p, **kw):
+        """x = P_which^{-1} b; keyword arguments (precision, nu, ncoarse,
+        vcycles_u, vcycles_p) select stk_apply_preconditioner_params."""
         x_u, x_p = self.zeros(b_p.device)
-        stk_apply_preconditioner(self.handle, which, b_u, b_p, x_u, x_p)
+        if kw:
+            p = stk_default_params()
+            p.precond = int(which)
+            for k, v in kw.items():
+                setattr(p, k, v)
+            stk_apply_preconditioner_params(self.handle, p, b_u, b_p, x_u, x_p)
+        else:
+            stk_apply_preconditioner(self.handle, which, b_u, b_p, x_u, x_p)
         return x_u, x_p
 
     def solve(self, b_u, b_p, x_u=None, x_p=None, **kw):

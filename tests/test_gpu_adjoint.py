@@ -139,3 +139,56 @@ def test_adjoint_64_finite_differences(S):
             worst = max(worst, abs(fd - an) / abs(fd))
     assert worst <= 1e-6, worst
     solver.close()
+
+
+@pytest.mark.parametrize("dim,n,bc,theta", [
+    (2, (32, 16), (NOSLIP, NOSLIP, FREESLIP, NOSLIP), 0.7),
+    (3, (16, 16, 8), (PERIODIC, PERIODIC, NOSLIP, NOSLIP, FREESLIP, FREESLIP), 1.0),
+])
+def test_adjoint_identity(S, dim, n, bc, theta):
+    """<y, M x> = <M y, x> for the GPU operator (M is its own adjoint, so the
+    adjoint solve is a forward solve), on random x, y with zero wall faces."""
+    pr = wl.generic(dim, n, bc, theta=theta, seed=51)
+    g = Grid(dim, pr.n, pr.h, pr.bc)
+    sv = S.StokesSolver(dim, pr.n[:dim], pr.bc[:2 * dim], pr.h)
+    sv.set_coefficients(_t(pr.rho), _t(pr.mu), theta)
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal(g.size) * g.active
+    y = rng.standard_normal(g.size) * g.active
+    xu, xp = g.unpack(x)
+    yu, yp = g.unpack(y)
+    Mxu, Mxp = sv.apply_operator([_t(a) for a in xu], _t(xp))
+    Myu, Myp = sv.apply_operator([_t(a) for a in yu], _t(yp))
+    Mx = g.pack([a.cpu().numpy() for a in Mxu], Mxp.cpu().numpy())
+    My = g.pack([a.cpu().numpy() for a in Myu], Myp.cpu().numpy())
+    lhs, rhs = float(y @ Mx), float(My @ x)
+    scale = np.linalg.norm(y) * np.linalg.norm(Mx)
+    assert abs(lhs - rhs) <= 1e-13 * scale
+    sv.close()
+
+
+def test_gradient_taylor_remainder(S):
+    """Taylor test of the autograd gradient on the 16^3 no-slip workload:
+    |L(m + eps d) - L(m) - eps <grad L, d>| falls as eps^2 (ratio about 4
+    per halving of eps) while the first-order remainder falls as eps."""
+    pr = wl.config_c5(16)
+    g, solver, u_t, loss = _loss_setup(S, pr, 12)
+    lm = _t(np.log(pr.mu)).requires_grad_(True)
+    rho = _t(pr.rho)
+    L0 = loss(lm, rho)
+    L0.backward()
+    grad = lm.grad.detach()
+    d = _t(wl.smooth_field_3d(pr.n, pr.h, 901, kmax=4))
+    d /= torch.linalg.norm(d)
+    slope = float((grad * d).sum())
+    rem2, rem1 = [], []
+    with torch.no_grad():
+        for eps in (0.04, 0.02, 0.01, 0.005):
+            Le = float(loss(lm + eps * d, rho))
+            rem1.append(abs(Le - float(L0)))
+            rem2.append(abs(Le - float(L0) - eps * slope))
+    r1 = [rem1[i] / rem1[i + 1] for i in range(3)]
+    r2 = [rem2[i] / rem2[i + 1] for i in range(3)]
+    assert all(1.7 <= r <= 2.3 for r in r1), r1
+    assert all(3.4 <= r <= 4.6 for r in r2), r2
+    solver.close()

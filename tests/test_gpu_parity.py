@@ -134,6 +134,52 @@ def test_preconditioners_match_oracle(S, which, dim, n, bc, theta):
     solver.close()
 
 
+@pytest.mark.parametrize("which", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("dim,n,bc,theta", [CASES[3], CASES[7], CASES[8]])
+def test_repeated_cycle_preconditioners_match_oracle(S, which, dim, n, bc, theta):
+    """Two velocity and three pressure V-cycles per subsolve (Sec. 4.1.2):
+    FP64 to 1e-10 of the oracle; the FP32 form (inputs rounded to FP32,
+    FP32 hierarchy) to 1e-4, the accuracy of FP32 multigrid."""
+    pr = _problem(dim, n, bc, theta, seed=5)
+    g = Grid(dim, pr.n, pr.h, pr.bc)
+    P = Preconditioner(g, pr.rho, pr.mu, pr.theta, which, cycles_u=2, cycles_p=3)
+    rng = np.random.default_rng(12)
+    b = rng.standard_normal(g.size) * g.active
+    ref = P(b)
+    solver = _make(S, pr)
+    for precision, tol in ((0, 1e-10), (1, 1e-4)):
+        x_u, x_p = solver.apply_preconditioner(which, *_split(g, b), precision=precision,
+                                               vcycles_u=2, vcycles_p=3)
+        got = _join(g, x_u, x_p)
+        assert np.abs(got - ref).max() <= tol * np.abs(ref).max(), (precision, np.abs(got - ref).max())
+    solver.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_with_repeated_cycles(S, precision):
+    """GMRES with two V-cycles per subsolve on the 32^2 periodic workload:
+    same discrete solution, iteration count within 2 of the oracle's GMRES
+    with the same preconditioner."""
+    pr = wl.config_c1(32)
+    g = Grid(2, pr.n, pr.h, pr.bc)
+    M = asm.stokes_from_fields(g, pr.rho, pr.mu, pr.theta)
+    b = g.pack(pr.b_u, pr.b_p)
+    xd = direct.solve(g, M, b)
+    P = Preconditioner(g, pr.rho, pr.mu, pr.theta, 1, cycles_u=2, cycles_p=2)
+    _, oinfo = krylov.gmres(lambda v: M @ v, P, b, rtol=1e-10, flexible=bool(precision))
+    solver = _make(S, pr)
+    x_u, x_p, info = solver.solve(*_split(g, b), precision=precision, vcycles_u=2, vcycles_p=2)
+    assert info["converged"]
+    assert abs(info["iterations"] - oinfo["iterations"]) <= 2, (info, oinfo)
+    # P1 with 2 + 2 cycles: d * 2 + 2 = 6 scalar V-cycles per application
+    assert info["scalar_vcycles"] % 6 == 0 and info["scalar_vcycles"] >= 6 * info["iterations"]
+    x = _join(g, x_u, x_p)
+    assert np.linalg.norm(b - M @ x) / np.linalg.norm(b) <= 1.0001e-10
+    eu, ep = direct.relative_error(g, x, xd)
+    assert eu <= 1e-8 and ep <= 1e-8
+    solver.close()
+
+
 def _solve_and_check(S, pr, precision, which=None, rtol=1e-10, tol=1e-8):
     g = Grid(pr.dim, pr.n, pr.h, pr.bc)
     M = asm.stokes_from_fields(g, pr.rho, pr.mu, pr.theta)

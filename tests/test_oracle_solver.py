@@ -165,3 +165,56 @@ def test_workload_generators():
     assert f3.shape == (8, 8, 8) and np.isfinite(f3).all()
     sizes = wl.config_c4_sizes()
     assert len(sizes) == 64 and set(sizes) <= {64, 128, 256, 512}
+
+
+@pytest.mark.parametrize("bc,theta", [((NOSLIP, NOSLIP, FREESLIP, NOSLIP), 1.0),
+                                      ((PERIODIC,) * 4, 2.0),
+                                      ((NOSLIP,) * 4, 0.0)])
+@pytest.mark.parametrize("which", [1, 2, 3, 4, 5])
+def test_repeated_cycles_tend_to_exact_subsolvers(bc, theta, which):
+    """Sec. 4.1.2: with many V-cycles per subsolve the preconditioner becomes
+    the exact-subsolver one (App. B), and the subsolve error falls
+    geometrically with the number of cycles (each V-cycle reduces the
+    residual by about ten, Sec. 4.1.1)."""
+    g = Grid(2, (16, 16), 1.0, bc)
+    rng = np.random.default_rng(6)
+    rho = np.exp(0.5 * rng.standard_normal(g.cell_shape()))
+    mu = np.exp(0.5 * rng.standard_normal(g.cell_shape()))
+    b = rng.standard_normal(g.size) * g.active
+    b[g.nvel:] -= b[g.nvel:].mean()
+    ex = Preconditioner(g, rho, mu, theta, which, exact=True)(b)
+    many = Preconditioner(g, rho, mu, theta, which, cycles_u=40, cycles_p=40)(b)
+    assert np.abs(many - ex).max() <= 1e-9 * np.abs(ex).max()
+    # subsolve errors for 1, 2, 3 cycles
+    P = Preconditioner(g, rho, mu, theta, which)
+    Pe = Preconditioner(g, rho, mu, theta, which, exact=True)
+    r_u = b[:g.nvel]
+    r_p = b[g.nvel:]
+    eu = Pe.velocity_solve(r_u)
+    ep = Pe.poisson_solve(r_p)
+    du, dp = [], []
+    for c in (1, 2, 3):
+        P.cycles_u = P.cycles_p = c
+        du.append(np.linalg.norm(P.velocity_solve(r_u) - eu))
+        x = P.poisson_solve(r_p)
+        dp.append(np.linalg.norm((x - x.mean()) - (ep - ep.mean())))
+    for d in (du, dp):
+        assert d[1] <= 0.25 * d[0] and d[2] <= 0.25 * d[1], d
+
+
+def test_repeated_cycles_gmres_converges_to_direct():
+    """GMRES with two V-cycles per subsolve reaches the same discrete
+    solution with fewer iterations than with one."""
+    pr = wl.config_c1(32)
+    g = Grid(2, pr.n, pr.h, pr.bc)
+    M = asm.stokes_from_fields(g, pr.rho, pr.mu, pr.theta)
+    b = g.pack(pr.b_u, pr.b_p)
+    xd = direct.solve(g, M, b)
+    its = []
+    for c in (1, 2):
+        P = Preconditioner(g, pr.rho, pr.mu, pr.theta, 1, cycles_u=c, cycles_p=c)
+        x, info = krylov.gmres(lambda v: M @ v, P, b, rtol=1e-10)
+        assert info["converged"]
+        assert max(direct.relative_error(g, x, xd)) < 1e-8
+        its.append(info["iterations"])
+    assert its[1] <= its[0]
