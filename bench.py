@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3",
-                    choices=["c3", "c2", "c1", "c5", "bubble2d", "bubble3d", "c4", "c5adj", "study"])
+                    choices=["c3", "c2", "c1", "c5", "bubble2d", "bubble3d", "c4", "c5adj", "study", "timeloop"])
     ap.add_argument("--n", type=int, default=0, help="override the grid size")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -712,8 +712,54 @@ def run_study(args):
     return 0
 
 
+def run_timeloop(args):
+    """Backward-Euler time stepping (Sec. 2, Eq. Stokes_eqn) of the 128^3
+    periodic workload (rho contrast 1e2, mu contrast 1e3, dt = 1, i.e.
+    viscous CFL 1), constant forcing, from rest: ms and GMRES iterations per
+    step, warm-started from the previous step and from zero, FP64 and mixed."""
+    import numpy as np
+    import torch
+    from paper_1308_4605_gb300 import stokes as S
+    from paper_1308_4605_gb300 import timeloop, tuning
+    pr, cfg = make_problem("c3", args.n)
+    dev = torch.device("cuda", 0)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    sv = S.StokesSolver(pr.dim, pr.n[:pr.dim], pr.bc[:2 * pr.dim], pr.h)
+    rho, mu = t(pr.rho), t(pr.mu)
+    sv.set_coefficients(rho, mu, pr.theta)
+    for prec in (S.STK_FP64, S.STK_MIXED):
+        tuning.tune(sv, prec)
+    f = [t(x) for x in pr.b_u]
+    bp = t(pr.b_p)
+    u0 = [torch.zeros_like(x) for x in f]
+    nsteps = max(args.steps, 2)
+    res = {}
+    for name, prec in (("fp64", S.STK_FP64), ("mixed", S.STK_MIXED)):
+        for warm in (True, False):
+            timeloop.backward_euler(sv, rho, mu, 1.0, u0, 1, f=f, b_p=bp, warm=warm, precision=prec)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, _, infos = timeloop.backward_euler(sv, rho, mu, 1.0, u0, nsteps, f=f, b_p=bp,
+                                                  warm=warm, precision=prec)
+            e1.record()
+            e1.synchronize()
+            res[f"{name}_{'warm' if warm else 'cold'}"] = {
+                "ms_per_step": e0.elapsed_time(e1) / nsteps,
+                "iterations": [i["iterations"] for i in infos],
+                "true_residual": max(i["true_residual"] for i in infos)}
+    sv.close()
+    print(json.dumps({"metric": METRIC, "workload": "backward-Euler steps of " + cfg["workload"],
+                      "unit": UNIT, "steps": nsteps, "data": "synthetic", "dtype": "f64",
+                      "dt": 1.0, "results": res}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "timeloop":
+        return run_timeloop(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "study":

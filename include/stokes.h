@@ -165,6 +165,18 @@ int stk_solve(stk_handle* h, const stk_solver_params* params, const double* cons
               const double* b_p, double* const* x_u, double* x_p, stk_solve_info* info,
               void* stream);
 
+/* Momentum right-hand side of one backward-Euler time step (Sec. 2, Eq.
+ * Stokes_eqn: rho (u^{n+1} - u^n)/dt + grad p^{n+1} = div tau(u^{n+1}) +
+ * f^{n+1}, div u^{n+1} = g^{n+1}): b_u = (rho_f / dt) u^n + f on every
+ * unknown face and 0 on wall faces, with rho_f / dt = theta rho_f the face
+ * coefficient of the last stk_set_coefficients (dt finite, else
+ * STK_ERR_STATE).  u_n, f, b_u: device face arrays of length
+ * stk_face_length(h, a); f may be NULL (no forcing); b_u may be u_n.  The
+ * step then solves M x = (b_u, -g^{n+1}) with stk_solve, x = u^n a good
+ * initial guess.  Stream-ordered, no synchronisation. */
+int stk_backward_euler_rhs(stk_handle* h, const double* const* u_n, const double* const* f,
+                           double* const* b_u, void* stream);
+
 /* Gradient of a loss L(u) of the velocity with respect to the cell
  * log-viscosity and density, by the adjoint method: given the forward
  * velocity u (solution of M x = b) and the adjoint velocity lambda (solution

@@ -230,6 +230,9 @@ void launch_axpy(int n, T a, const T* x, T* y, cudaStream_t s);
 template <typename TA, typename TB>
 void launch_convert(int n, const TA* a, TB* b, cudaStream_t s);
 // dL/dlog mu and dL/drho (cell arrays) from packed velocities u and lambda
+// b = alpha u + f on the a-faces (f may be null), zero on wall faces
+void launch_inertial_rhs(const Geom& g, int a, const double* alpha, const double* u,
+                         const double* f, double* b, cudaStream_t s);
 void launch_gradient(const Geom& g, const double* mu, double theta, const double* u,
                      const double* lam, double* glogmu, double* grho, cudaStream_t s);
 // out[0] = number of non-finite entries, out[1] = number of entries <= 0

@@ -612,6 +612,18 @@ __global__ void k_axpy(int n, T a, const T* __restrict__ x, T* __restrict__ y) {
     if (t < n) y[t] += a * x[t];
 }
 
+// Right-hand side of a backward-Euler step on the a-faces: b = alpha u + f
+// (alpha = rho_f / dt), zero on wall faces; f may be null.
+__global__ void k_inertial_rhs(Geom g, int a, const double* __restrict__ alpha,
+                               const double* u, const double* f, double* b) {
+    pdl_entry();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.fsize[a]) return;
+    int q[3];
+    decode_face(g, a, t, q);
+    b[t] = wall_face(g, a, q) ? 0.0 : fma(alpha[g.foff[a] + t], u[t], f ? f[t] : 0.0);
+}
+
 __global__ void k_check_fields(int n, const double* __restrict__ rho, const double* __restrict__ mu,
                                double* part) {
     pdl_entry();
@@ -813,6 +825,11 @@ void launch_zero(int n, T* x, cudaStream_t s) {
 template <typename T>
 void launch_axpy(int n, T a, const T* x, T* y, cudaStream_t s) {
     launch_pdl(k_axpy<T>, dim3(nblk(n)), dim3(TPB), s, n, a, x, y);
+}
+
+void launch_inertial_rhs(const Geom& g, int a, const double* alpha, const double* u,
+                         const double* f, double* b, cudaStream_t s) {
+    launch_pdl(k_inertial_rhs, dim3(nblk(g.fsize[a])), dim3(TPB), s, g, a, alpha, u, f, b);
 }
 
 void launch_gradient(const Geom& g, const double* mu, double theta, const double* u,

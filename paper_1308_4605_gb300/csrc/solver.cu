@@ -1289,6 +1289,23 @@ int stk_apply_preconditioner_params(stk_handle* h, const stk_solver_params* para
     return scatter(h, h->tmp, x_u, x_p, s);
 }
 
+int stk_backward_euler_rhs(stk_handle* h, const double* const* u_n, const double* const* f,
+                           double* const* b_u, void* stream) {
+    if (!h) return STK_ERR_ARG;
+    if (!h->coef_set) return fail(h, STK_ERR_STATE, "coefficients not set");
+    if (!u_n || !b_u) return fail(h, STK_ERR_ARG, "null pointer");
+    if (h->theta == 0.0) return fail(h, STK_ERR_STATE, "steady coefficients (dt = inf): no time step");
+    const Geom& g = h->lev[0].g;
+    for (int a = 0; a < g.dim; ++a)
+        if (!u_n[a] || !b_u[a] || (f && !f[a])) return fail(h, STK_ERR_ARG, "null face array %d", a);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(cudaSetDevice(h->device));
+    for (int a = 0; a < g.dim; ++a)
+        launch_inertial_rhs(g, a, h->lev[0].cd.alpha, u_n[a], f ? f[a] : nullptr, b_u[a], s);
+    CKL();
+    return STK_OK;
+}
+
 int stk_velocity_vcycle(stk_handle* h, const double* const* r_u, double* const* x_u,
                         void* stream) {
     if (!h) return STK_ERR_ARG;

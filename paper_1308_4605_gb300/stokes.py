@@ -91,6 +91,7 @@ def _load():
         "stk_profile": (I, [P, I]),
         "stk_kernel_launches": (ctypes.c_longlong, [P]),
         "stk_gradient": (I, [P, PP, PP, P, P, P]),
+        "stk_backward_euler_rhs": (I, [P, PP, PP, PP, P]),
         "stk_get_schedule": (I, [P, I, ctypes.POINTER(stk_schedule)]),
         "stk_set_schedule": (I, [P, I, ctypes.POINTER(stk_schedule)]),
         "stk_autotune": (I, [P, I, ctypes.POINTER(stk_schedule), P]),
@@ -111,7 +112,7 @@ _lib = _load()
 EXPORTED = ["stk_default_params", "stk_create", "stk_destroy", "stk_last_error", "stk_face_length",
             "stk_cell_length", "stk_set_coefficients", "stk_apply_operator",
             "stk_apply_preconditioner", "stk_apply_preconditioner_params", "stk_velocity_vcycle", "stk_pressure_vcycle", "stk_solve",
-            "stk_profile", "stk_profile_read", "stk_kernel_launches", "stk_pressure_vcycle_noalloc", "stk_gradient", "stk_solve_batched", "stk_get_schedule", "stk_set_schedule", "stk_autotune"]
+            "stk_profile", "stk_profile_read", "stk_kernel_launches", "stk_pressure_vcycle_noalloc", "stk_gradient", "stk_backward_euler_rhs", "stk_solve_batched", "stk_get_schedule", "stk_set_schedule", "stk_autotune"]
 
 
 def library():
@@ -217,6 +218,13 @@ def stk_apply_preconditioner_params(h, params, b_u, b_p, x_u, x_p, stream=None):
     return _check(h, _lib.stk_apply_preconditioner_params(
         h, ctypes.byref(params), _ptrs(b_u, fl), _ptr(b_p, nc), _ptrs(x_u, fl), _ptr(x_p, nc),
         _stream(stream)))
+
+
+def stk_backward_euler_rhs(h, u_n, f, b_u, stream=None):
+    fl, _ = _lengths(h, len(u_n))
+    fp = _ptrs(f, fl) if f is not None else None
+    return _check(h, _lib.stk_backward_euler_rhs(h, _ptrs(u_n, fl), fp, _ptrs(b_u, fl),
+                                                 _stream(stream)))
 
 
 def stk_velocity_vcycle(h, r_u, x_u, stream=None):
