@@ -103,15 +103,19 @@ def edge_viscosity(grid: Grid, mu):
     return out
 
 
-def fine_coefficients(grid: Grid, rho, mu, theta):
+def fine_coefficients(grid: Grid, rho, mu, theta, gamma=None):
     """Coefficients of the finest level: alpha_f = theta rho_f, beta_f = 1/rho_f
-    on faces, mu at cells and at edges."""
+    on faces, mu at cells and at edges; with a bulk viscosity gamma (Sec. 2:
+    tau = mu (grad u + grad u^T) + (gamma - 2/3 mu)(div u) I) also
+    lam_c = gamma - 2/3 mu at cells."""
     rho_f = face_density(grid, rho)
     alpha = [theta * r for r in rho_f]
     beta = [np.where(r > 0, 1.0 / np.where(r > 0, r, 1.0), 0.0) for r in rho_f]
-    return {"alpha": alpha, "beta": beta,
-            "mu_c": np.asarray(mu, dtype=np.float64).reshape(grid.cell_shape()).copy(),
-            "mu_e": edge_viscosity(grid, mu)}
+    mu_c = np.asarray(mu, dtype=np.float64).reshape(grid.cell_shape()).copy()
+    out = {"alpha": alpha, "beta": beta, "mu_c": mu_c, "mu_e": edge_viscosity(grid, mu)}
+    if gamma is not None:
+        out["lam_c"] = np.asarray(gamma, dtype=np.float64).reshape(grid.cell_shape()) - 2.0 / 3.0 * mu_c
+    return out
 
 
 # -------------------------------------------------------------------- operators
@@ -240,10 +244,23 @@ def viscous(grid: Grid, mu_c, mu_e, form="stress"):
     return L.tocsr()
 
 
+def bulk_viscous(grid: Grid, lam_c):
+    """The bulk part of the viscous operator, grad (lam div u) = G diag(lam) D:
+    on the a-face between cells c-e_a and c it is
+    (lam_c (D u)_c - lam_{c-e_a} (D u)_{c-e_a}) / h (Sec. 2, bulk-viscosity
+    stress; D u vanishes identically on divergence-free fields)."""
+    return (gradient(grid) @ sp.diags(np.asarray(lam_c, dtype=np.float64).ravel())
+            @ divergence(grid)).tocsr()
+
+
 def velocity_operator(grid: Grid, coef, form="stress"):
-    """A = diag(alpha) - L_mu (Sec. 2)."""
+    """A = diag(alpha) - L_mu (Sec. 2), L_mu including the bulk part when
+    the coefficients carry lam_c."""
     alpha = np.concatenate([np.asarray(x).ravel() for x in coef["alpha"]])
-    return (sp.diags(alpha) - viscous(grid, coef["mu_c"], coef["mu_e"], form)).tocsr()
+    A = sp.diags(alpha) - viscous(grid, coef["mu_c"], coef["mu_e"], form)
+    if coef.get("lam_c") is not None:
+        A = A - bulk_viscous(grid, coef["lam_c"])
+    return A.tocsr()
 
 
 def poisson_operator(grid: Grid, beta):
@@ -261,8 +278,8 @@ def stokes_operator(grid: Grid, coef, form="stress"):
     return sp.bmat([[A, G], [-D, Z]], format="csr")
 
 
-def stokes_from_fields(grid: Grid, rho, mu, theta, form="stress"):
-    return stokes_operator(grid, fine_coefficients(grid, rho, mu, theta), form)
+def stokes_from_fields(grid: Grid, rho, mu, theta, form="stress", gamma=None):
+    return stokes_operator(grid, fine_coefficients(grid, rho, mu, theta, gamma), form)
 
 
 def pressure_nullspace(grid: Grid):

@@ -77,6 +77,12 @@ def coarse_coefficients(gf: Grid, cf, gc: Grid):
         acc += _gather(cf["mu_c"], gf.n, fi)
         cnt += 1
     out["mu_c"] = (acc / cnt).reshape(gc.cell_shape())
+    if cf.get("lam_c") is not None:    # bulk term: cell average, like mu_c
+        acc = np.zeros(idx[0].shape)
+        for t in np.ndindex(*([2] * d)):
+            fi = [2 * idx[c] + (t[c] if c < d else 0) if c < d else idx[c] for c in range(3)]
+            acc += _gather(cf["lam_c"], gf.n, fi)
+        out["lam_c"] = (acc / cnt).reshape(gc.cell_shape())
     for (a, b), arr in cf["mu_e"].items():
         idx = gc.edge_positions(a, b)
         fext = gf.edge_ext(a, b)

@@ -52,15 +52,20 @@ from .grid import Grid
 
 class Preconditioner:
     def __init__(self, grid: Grid, rho, mu, theta, which=1, exact=False, nu=2, ncoarse=8,
-                 cycles_u=1, cycles_p=1):
+                 cycles_u=1, cycles_p=1, gamma=None):
         self.grid = grid
         self.theta = float(theta)
         self.which = int(which)
         self.exact = exact
         self.nu, self.ncoarse = nu, ncoarse
         self.cycles_u, self.cycles_p = int(cycles_u), int(cycles_p)
-        self.coef = asm.fine_coefficients(grid, rho, mu, theta)
+        self.coef = asm.fine_coefficients(grid, rho, mu, theta, gamma)
         self.mu = np.asarray(mu, dtype=np.float64).ravel()
+        # the local-viscosity Schur factor: 2 mu (Eq. Schur_app_varDen_varVis),
+        # gamma + 4/3 mu = 2 mu + lam with bulk viscosity (Eq. Schur_app_bulk)
+        self.kappa = 2.0 * self.mu
+        if gamma is not None:
+            self.kappa = 2.0 * self.mu + self.coef["lam_c"].ravel()
         self.inv_rho_f = np.concatenate([np.asarray(b).ravel() for b in self.coef["beta"]])
         self.D = asm.divergence(grid)
         self.G = asm.gradient(grid)
@@ -98,8 +103,9 @@ class Preconditioner:
         return phi
 
     def neg_schur_inverse(self, r):
-        """-S~^{-1} r = theta L~^{-1} r - 2 mu r."""
-        out = -2.0 * self.mu * r
+        """-S~^{-1} r = theta L~^{-1} r - kappa r, kappa = 2 mu (or
+        gamma + 4/3 mu with bulk viscosity)."""
+        out = -self.kappa * r
         if self.theta != 0.0:
             out = out + self.theta * self.poisson_solve(r)
         return out
@@ -114,7 +120,7 @@ class Preconditioner:
             bc = self.D @ xs + b_p
             phi = self.poisson_solve(bc)
             x_u = xs - self.inv_rho_f * (self.G @ phi)
-            x_p = self.theta * phi - 2.0 * self.mu * bc
+            x_p = self.theta * phi - self.kappa * bc
         elif w == 2:
             x_u = self.velocity_solve(b_u)
             x_p = self.neg_schur_inverse(self.D @ x_u + b_p)
