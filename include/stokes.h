@@ -127,6 +127,18 @@ long long stk_cell_length(const stk_handle* h);
 int stk_set_coefficients(stk_handle* h, const double* rho, const double* mu, double dt,
                          void* stream);
 
+/* Bulk-viscosity stress form (Sec. 2): tau = mu (grad u + grad u^T) +
+ * (gamma - 2/3 mu)(div u) I, for flows with div u = g != 0.  gamma: device
+ * cell array of bulk viscosities >= 0 (copied), or NULL to return to the
+ * stress form without the bulk term.  Call after stk_set_coefficients; the
+ * setting persists through later stk_set_coefficients calls.  The operator,
+ * the smoothers (coarse levels average lam = gamma - 2/3 mu over the fine
+ * cells, like mu) and the Schur approximation -theta L_rho^{-1} +
+ * (gamma + 4/3 mu) (Eq. Schur_app_bulk) all use it; stk_gradient then
+ * returns STK_ERR_STATE.  Errors: STK_ERR_STATE (no coefficients),
+ * STK_ERR_NONFINITE, STK_ERR_ARG (gamma < 0).  Synchronises the stream. */
+int stk_set_bulk_viscosity(stk_handle* h, const double* gamma, void* stream);
+
 /* y = M x  (Eq. Saddle_sys): y_u = theta rho_f x_u - L_mu x_u + G x_p and
  * y_p = -D x_u, with the stress-form viscous operator of Eq. div_stress.
  * x_u[a], y_u[a] are face arrays, x_p, y_p cell arrays; y must not alias x. */

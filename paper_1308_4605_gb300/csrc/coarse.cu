@@ -17,7 +17,7 @@ namespace {
 using namespace st;
 constexpr int CT = 1024;
 
-template <int DIM, typename T>
+template <int DIM, typename T, bool BULK>
 __device__ void c_vel_sweeps(const Geom& g, const Coef<T>& C, int nsweep, T* phi, const T* rhs) {
     for (int it = 0; it < nsweep; ++it)
 #pragma unroll
@@ -27,9 +27,9 @@ __device__ void c_vel_sweeps(const Geom& g, const Coef<T>& C, int nsweep, T* phi
                 for (int t = threadIdx.x; t < nt; t += CT) {
                     int q[3];
                     if (!decode_face_colour(g, a, par, t, q) || wall_face(g, a, q)) continue;
-                    if (a == 0) vel_gs_point<DIM, 0, T>(g, C, q, phi, rhs);
-                    else if (a == 1) vel_gs_point<DIM, 1, T>(g, C, q, phi, rhs);
-                    else vel_gs_point<DIM, DIM == 3 ? 2 : 1, T>(g, C, q, phi, rhs);
+                    if (a == 0) vel_gs_point<DIM, 0, T, BULK>(g, C, q, phi, rhs);
+                    else if (a == 1) vel_gs_point<DIM, 1, T, BULK>(g, C, q, phi, rhs);
+                    else vel_gs_point<DIM, DIM == 3 ? 2 : 1, T, BULK>(g, C, q, phi, rhs);
                 }
                 __syncthreads();
             }
@@ -56,7 +56,7 @@ __device__ __forceinline__ void load_geom(Geom* dst, const Geom* src) {
     for (int i = threadIdx.x; i < (int)(sizeof(Geom) / sizeof(int)); i += CT) d[i] = s[i];
 }
 
-template <int DIM, typename T>
+template <int DIM, typename T, bool BULK>
 __global__ void __launch_bounds__(CT) k_coarse_vel(const CLevel<T>* __restrict__ Ls, int nlev,
                                                    const T* rhs0, T* phi0, int nu, int ncoarse) {
     pdl_entry();
@@ -73,17 +73,17 @@ __global__ void __launch_bounds__(CT) k_coarse_vel(const CLevel<T>* __restrict__
         for (int t = threadIdx.x; t < g.nvel; t += CT) phi[t] = T(0);
         __syncthreads();
         if (l + 1 == nlev) {
-            c_vel_sweeps<DIM, T>(g, C, ncoarse, phi, rhs);
+            c_vel_sweeps<DIM, T, BULK>(g, C, ncoarse, phi, rhs);
             break;
         }
-        c_vel_sweeps<DIM, T>(g, C, nu, phi, rhs);
+        c_vel_sweeps<DIM, T, BULK>(g, C, nu, phi, rhs);
         T* res = Ls[l].res_u;
         for (int t = threadIdx.x; t < g.nvel; t += CT) {
             int a = 0;
             while (a + 1 < DIM && t >= g.foff[a + 1]) ++a;
             int q[3];
             decode_face(g, a, t - g.foff[a], q);
-            res[t] = wall_face(g, a, q) ? T(0) : vel_res_point<DIM, T>(a, g, C, q, phi, rhs);
+            res[t] = wall_face(g, a, q) ? T(0) : vel_res_point<DIM, T, BULK>(a, g, C, q, phi, rhs);
         }
         __syncthreads();
         const Geom& gc = gsh[1];
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(CT) k_coarse_vel(const CLevel<T>* __restrict__
             phi[t] += v;
         }
         __syncthreads();
-        c_vel_sweeps<DIM, T>(g, C, nu, phi, rhs);
+        c_vel_sweeps<DIM, T, BULK>(g, C, nu, phi, rhs);
     }
 }
 
@@ -192,9 +192,9 @@ __global__ void __launch_bounds__(CT) k_coarse_cell(const CLevel<T>* __restrict_
 
 template <typename T>
 void launch_coarse_vcycle_vel(int dim, const CLevel<T>* L, int nlev, const T* rhs, T* phi, int nu,
-                              int ncoarse, cudaStream_t s) {
-    if (dim == 2) launch_pdl(k_coarse_vel<2, T>, dim3(1), dim3(CT), s, L, nlev, rhs, phi, nu, ncoarse);
-    else launch_pdl(k_coarse_vel<3, T>, dim3(1), dim3(CT), s, L, nlev, rhs, phi, nu, ncoarse);
+                              int ncoarse, bool bulk, cudaStream_t s) {
+    if (dim == 2) launch_pdl(bulk ? k_coarse_vel<2, T, true> : k_coarse_vel<2, T, false>, dim3(1), dim3(CT), s, L, nlev, rhs, phi, nu, ncoarse);
+    else launch_pdl(bulk ? k_coarse_vel<3, T, true> : k_coarse_vel<3, T, false>, dim3(1), dim3(CT), s, L, nlev, rhs, phi, nu, ncoarse);
 }
 
 template <typename T>
@@ -205,9 +205,9 @@ void launch_coarse_vcycle_cell(int dim, const CLevel<T>* L, int nlev, const T* r
 }
 
 template void launch_coarse_vcycle_vel<double>(int, const CLevel<double>*, int, const double*,
-                                               double*, int, int, cudaStream_t);
+                                               double*, int, int, bool, cudaStream_t);
 template void launch_coarse_vcycle_vel<float>(int, const CLevel<float>*, int, const float*, float*,
-                                              int, int, cudaStream_t);
+                                              int, int, bool, cudaStream_t);
 template void launch_coarse_vcycle_cell<double>(int, const CLevel<double>*, int, const double*,
                                                 double*, int, int, cudaStream_t);
 template void launch_coarse_vcycle_cell<float>(int, const CLevel<float>*, int, const float*,

@@ -84,6 +84,7 @@ struct Coef {
     T* invd_u;
     T* invd_p;
     T* diag_u;   // the diagonal of A itself (FP64 hierarchy only; null in FP32)
+    T* lam_c;    // bulk term gamma - 2/3 mu at cells; null without bulk viscosity
 };
 
 // Launch with programmatic dependent launch allowed: the kernel may be
@@ -126,6 +127,8 @@ void launch_zero(int n, T* x, cudaStream_t s);
 // coefficients
 void launch_fine_coefficients(const Geom& g, const double* rho, const double* mu, double theta,
                               Coef<double> C, cudaStream_t s);
+// lam = gamma - 2/3 mu on the cells of the finest level
+void launch_bulk_lambda(int n, const double* gamma, const double* mu, double* lam, cudaStream_t s);
 void launch_coarsen_coefficients(const Geom& gf, Coef<double> Cf, const Geom& gc, Coef<double> Cc,
                                  cudaStream_t s);
 void launch_inverse_diagonals(const Geom& g, Coef<double> C, cudaStream_t s);
@@ -185,7 +188,7 @@ constexpr int COARSE_MAX_CELLS_F32 = 4096;
 constexpr int COARSE_MAX_CELLS_F64 = 512;
 template <typename T>
 void launch_coarse_vcycle_vel(int dim, const CLevel<T>* L, int nlev, const T* rhs, T* phi, int nu,
-                              int ncoarse, cudaStream_t s);
+                              int ncoarse, bool bulk, cudaStream_t s);
 template <typename T>
 void launch_coarse_vcycle_cell(int dim, const CLevel<T>* L, int nlev, const T* rhs, T* phi, int nu,
                                int ncoarse, cudaStream_t s);
@@ -198,8 +201,9 @@ void launch_sub_grad(const Geom& g, const T* beta, const T* u, const T* p, T* ou
 template <typename T>  // out = b - G p - A u
 void launch_vel_correction_rhs(const Geom& g, Coef<T> C, const T* b, const T* p, const T* u,
                                T* out, cudaStream_t s);
-template <typename T>  // xp = theta phi - 2 mu bc  (phi may be null)
-void launch_schur_combine(int n, const double* theta, const T* phi, const T* mu, const T* bc, T* xp,
+template <typename T>  // xp = theta phi - (2 mu + lam) bc  (phi, lam may be null)
+void launch_schur_combine(int n, const double* theta, const T* phi, const T* mu, const T* lam,
+                          const T* bc, T* xp,
                           cudaStream_t s);
 
 // reductions with a fixed block count: deterministic results

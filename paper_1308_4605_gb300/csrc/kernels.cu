@@ -187,7 +187,7 @@ __global__ void k_coarsen_edges(Geom gf, Geom gc, int p, int c, const double* __
     }
 }
 
-template <int DIM>
+template <int DIM, bool BULK>
 __global__ void k_inverse_diagonals(Geom g, Coef<double> C, Segs sg) {
     pdl_entry();
     int t;
@@ -212,10 +212,18 @@ __global__ void k_inverse_diagonals(Geom g, Coef<double> C, Segs sg) {
         return;
     }
     double dsum = 0.0;
-    visc_h2_any<DIM, double, double, true>(s, g, C, q, C.alpha, dsum);
+    visc_offdiag_any<DIM, double, double, true, BULK>(s, g, C, q, C.alpha, dsum);   // N unused
     double d = C.alpha[f] + g.ih2 * dsum;
     C.invd_u[f] = d != 0.0 ? 1.0 / d : 0.0;
     if (C.diag_u) C.diag_u[f] = d;
+}
+
+// bulk term of the stress at cells: lam = gamma - 2/3 mu (Sec. 2)
+__global__ void k_bulk_lambda(int n, const double* __restrict__ gamma, const double* __restrict__ mu,
+                              double* __restrict__ lam) {
+    pdl_entry();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) lam[t] = fma(-2.0 / 3.0, mu[t], gamma[t]);
 }
 
 template <typename TA, typename TB>
@@ -228,7 +236,7 @@ __global__ void k_convert(int n, const TA* __restrict__ a, TB* __restrict__ b) {
 // ----------------------------------------------------------------- Stokes matvec
 // y_u = alpha x_u - L_mu x_u + G x_p on unknown faces (0 on wall faces),
 // y_p = -D x_u on cells (Eq. Saddle_sys).
-template <int DIM, typename TV>
+template <int DIM, typename TV, bool BULK>
 __global__ void k_stokes_matvec(Geom g, Coef<double> C, Segs sg, const TV* __restrict__ x,
                                 const double* __restrict__ b, double* __restrict__ y) {
     pdl_entry();
@@ -258,7 +266,7 @@ __global__ void k_stokes_matvec(Geom g, Coef<double> C, Segs sg, const TV* __res
         return;
     }
     double dsum;
-    const double N = visc_offdiag_any<DIM, double, TV, false>(s, g, C, q, x, dsum);
+    const double N = visc_offdiag_any<DIM, double, TV, false, BULK>(s, g, C, q, x, dsum);
     int qm[3] = {q[0], q[1], q[2]};
     qm[s] = step(g, s, q[s], -1);
     double Mx = g.ih * (double(xp[cidx(g, q)]) - double(xp[cidx(g, qm)]));
@@ -270,7 +278,7 @@ __global__ void k_stokes_matvec(Geom g, Coef<double> C, Segs sg, const TV* __res
 // ------------------------------------------------------------------- multigrid
 // One colour of the staggered Gauss-Seidel smoother (App. C): every A-face
 // with (i + j + k) % 2 == parity gets phi += D^{-1} (rhs - A phi).
-template <int DIM, int A, typename T>
+template <int DIM, int A, typename T, bool BULK>
 __global__ void __launch_bounds__(512) k_vel_gs(Geom g, Coef<T> C, int parity, T* __restrict__ phi,
                                                 const T* __restrict__ rhs, int nthreads) {
     pdl_entry();
@@ -278,10 +286,10 @@ __global__ void __launch_bounds__(512) k_vel_gs(Geom g, Coef<T> C, int parity, T
     if (t >= nthreads) return;
     int q[3];
     if (!decode_face_colour(g, A, parity, t, q) || wall_face(g, A, q)) return;
-    vel_gs_point<DIM, A, T>(g, C, q, phi, rhs);
+    vel_gs_point<DIM, A, T, BULK>(g, C, q, phi, rhs);
 }
 
-template <int DIM, typename T>
+template <int DIM, typename T, bool BULK>
 __global__ void __launch_bounds__(TPB) k_vel_residual(Geom g, Coef<T> C, Segs sg,
                                                       const T* __restrict__ phi,
                                                       const T* __restrict__ rhs, T* __restrict__ res) {
@@ -292,7 +300,7 @@ __global__ void __launch_bounds__(TPB) k_vel_residual(Geom g, Coef<T> C, Segs sg
     int q[3];
     decode_face(g, s, t, q);
     const int f = g.foff[s] + t;
-    res[f] = wall_face(g, s, q) ? T(0) : vel_res_point<DIM, T>(s, g, C, q, phi, rhs);
+    res[f] = wall_face(g, s, q) ? T(0) : vel_res_point<DIM, T, BULK>(s, g, C, q, phi, rhs);
 }
 
 template <int DIM, typename T>
@@ -417,7 +425,7 @@ __global__ void k_sub_grad(Geom g, Segs sg, const T* __restrict__ beta, const T*
     out[f] = u[f] - (beta ? beta[f] : T(1)) * grad;
 }
 
-template <int DIM, typename T>
+template <int DIM, typename T, bool BULK>
 __global__ void k_vel_correction_rhs(Geom g, Coef<T> C, Segs sg, const T* __restrict__ b,
                                      const T* __restrict__ p, const T* __restrict__ u,
                                      T* __restrict__ out) {
@@ -435,17 +443,19 @@ __global__ void k_vel_correction_rhs(Geom g, Coef<T> C, Segs sg, const T* __rest
     int qm[3] = {q[0], q[1], q[2]};
     qm[s] = step(g, s, q[s], -1);
     T grad = (p[cidx(g, q)] - p[cidx(g, qm)]) * gih<T>(g);
-    out[f] = vel_res_point<DIM, T>(s, g, C, q, u, b) - grad;
+    out[f] = vel_res_point<DIM, T, BULK>(s, g, C, q, u, b) - grad;
 }
 
 template <typename T>
 __global__ void k_schur_combine(int n, const double* __restrict__ theta, const T* __restrict__ phi,
-                                const T* __restrict__ mu, const T* __restrict__ bc,
-                                T* __restrict__ xp) {
+                                const T* __restrict__ mu, const T* __restrict__ lam,
+                                const T* __restrict__ bc, T* __restrict__ xp) {
     pdl_entry();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
-    T v = -T(2) * mu[t] * bc[t];
+    T k = T(2) * mu[t];          // 2 mu, or gamma + 4/3 mu = 2 mu + lam (Eq. Schur_app_bulk)
+    if (lam) k += lam[t];
+    T v = -k * bc[t];
     if (phi) v += T(*theta) * phi[t];
     xp[t] = v;
 }
@@ -660,6 +670,8 @@ void launch_coarsen_coefficients(const Geom& gf, Coef<double> Cf, const Geom& gc
                                  cudaStream_t s) {
     launch_pdl(k_coarsen_faces, dim3(nblk(gc.nvel)), dim3(TPB), s, gf, gc, Cf.alpha, Cf.beta, Cc.alpha, Cc.beta);
     launch_pdl(k_coarsen_cells, dim3(nblk(gc.ncell)), dim3(TPB), s, gf, gc, Cf.mu_c, Cc.mu_c);
+    if (Cf.lam_c && Cc.lam_c)   // bulk term: cell average, like mu_c
+        launch_pdl(k_coarsen_cells, dim3(nblk(gc.ncell)), dim3(TPB), s, gf, gc, Cf.lam_c, Cc.lam_c);
     for (int a = 0; a < gc.dim; ++a)
         for (int b = a + 1; b < gc.dim; ++b) {
             int p = a + b - 1;
@@ -668,10 +680,15 @@ void launch_coarsen_coefficients(const Geom& gf, Coef<double> Cf, const Geom& gc
         }
 }
 
+void launch_bulk_lambda(int n, const double* gamma, const double* mu, double* lam, cudaStream_t s) {
+    launch_pdl(k_bulk_lambda, dim3(nblk(n)), dim3(TPB), s, n, gamma, mu, lam);
+}
+
 void launch_inverse_diagonals(const Geom& g, Coef<double> C, cudaStream_t s) {
     Segs sg = face_segs(g, true);
-    if (g.dim == 2) launch_pdl(k_inverse_diagonals<2>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg);
-    else launch_pdl(k_inverse_diagonals<3>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg);
+    const bool bk = C.lam_c != nullptr;
+    if (g.dim == 2) launch_pdl(bk ? k_inverse_diagonals<2, true> : k_inverse_diagonals<2, false>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg);
+    else launch_pdl(bk ? k_inverse_diagonals<3, true> : k_inverse_diagonals<3, false>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg);
 }
 
 template <typename TA, typename TB>
@@ -688,20 +705,23 @@ void launch_convert_coefficients(const Geom& g, Coef<double> C, Coef<float> F, c
         if (g.esize[p] > 0 && C.mu_e[p]) launch_convert(g.esize[p], C.mu_e[p], F.mu_e[p], s);
     launch_convert(g.nvel, C.invd_u, F.invd_u, s);
     launch_convert(g.ncell, C.invd_p, F.invd_p, s);
+    if (C.lam_c && F.lam_c) launch_convert(g.ncell, C.lam_c, F.lam_c, s);
 }
 
 template <typename TV>
 void launch_stokes_matvec(const Geom& g, Coef<double> C, const TV* x, double* y, cudaStream_t s) {
     Segs sg = face_segs(g, true);
-    if (g.dim == 2) launch_pdl(k_stokes_matvec<2, TV>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, x, nullptr, y);
-    else launch_pdl(k_stokes_matvec<3, TV>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, x, nullptr, y);
+    const bool bk = C.lam_c != nullptr;
+    if (g.dim == 2) launch_pdl(bk ? k_stokes_matvec<2, TV, true> : k_stokes_matvec<2, TV, false>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, x, nullptr, y);
+    else launch_pdl(bk ? k_stokes_matvec<3, TV, true> : k_stokes_matvec<3, TV, false>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, x, nullptr, y);
 }
 
 void launch_stokes_residual(const Geom& g, Coef<double> C, const double* x, const double* b,
                             double* r, cudaStream_t s) {
     Segs sg = face_segs(g, true);
-    if (g.dim == 2) launch_pdl(k_stokes_matvec<2, double>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, x, b, r);
-    else launch_pdl(k_stokes_matvec<3, double>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, x, b, r);
+    const bool bk = C.lam_c != nullptr;
+    if (g.dim == 2) launch_pdl(bk ? k_stokes_matvec<2, double, true> : k_stokes_matvec<2, double, false>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, x, b, r);
+    else launch_pdl(bk ? k_stokes_matvec<3, double, true> : k_stokes_matvec<3, double, false>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, x, b, r);
 }
 
 template <typename T>
@@ -709,22 +729,26 @@ void launch_vel_gs_colour(const Geom& g, Coef<T> C, int comp, int parity, T* phi
                           cudaStream_t s, int tpb) {
     const int nt = ((g.fe[comp][0] + 1) / 2) * g.fe[comp][1] * g.fe[comp][2];
     const int nb = (nt + tpb - 1) / tpb;
+    const bool bk = C.lam_c != nullptr;
+#define STK_VGS(D, A) (bk ? k_vel_gs<D, A, T, true> : k_vel_gs<D, A, T, false>)
     if (g.dim == 2) {
-        if (comp == 0) launch_pdl(k_vel_gs<2, 0, T>, dim3(nb), dim3(tpb), s, g, C, parity, phi, rhs, nt);
-        else launch_pdl(k_vel_gs<2, 1, T>, dim3(nb), dim3(tpb), s, g, C, parity, phi, rhs, nt);
+        if (comp == 0) launch_pdl(STK_VGS(2, 0), dim3(nb), dim3(tpb), s, g, C, parity, phi, rhs, nt);
+        else launch_pdl(STK_VGS(2, 1), dim3(nb), dim3(tpb), s, g, C, parity, phi, rhs, nt);
     } else {
-        if (comp == 0) launch_pdl(k_vel_gs<3, 0, T>, dim3(nb), dim3(tpb), s, g, C, parity, phi, rhs, nt);
-        else if (comp == 1) launch_pdl(k_vel_gs<3, 1, T>, dim3(nb), dim3(tpb), s, g, C, parity, phi, rhs, nt);
-        else launch_pdl(k_vel_gs<3, 2, T>, dim3(nb), dim3(tpb), s, g, C, parity, phi, rhs, nt);
+        if (comp == 0) launch_pdl(STK_VGS(3, 0), dim3(nb), dim3(tpb), s, g, C, parity, phi, rhs, nt);
+        else if (comp == 1) launch_pdl(STK_VGS(3, 1), dim3(nb), dim3(tpb), s, g, C, parity, phi, rhs, nt);
+        else launch_pdl(STK_VGS(3, 2), dim3(nb), dim3(tpb), s, g, C, parity, phi, rhs, nt);
     }
+#undef STK_VGS
 }
 
 template <typename T>
 void launch_vel_residual(const Geom& g, Coef<T> C, const T* phi, const T* rhs, T* res,
                          cudaStream_t s) {
     Segs sg = face_segs(g, false);
-    if (g.dim == 2) launch_pdl(k_vel_residual<2, T>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, phi, rhs, res);
-    else launch_pdl(k_vel_residual<3, T>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, phi, rhs, res);
+    const bool bk = C.lam_c != nullptr;
+    if (g.dim == 2) launch_pdl(bk ? k_vel_residual<2, T, true> : k_vel_residual<2, T, false>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, phi, rhs, res);
+    else launch_pdl(bk ? k_vel_residual<3, T, true> : k_vel_residual<3, T, false>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, phi, rhs, res);
 }
 
 template <typename T>
@@ -787,15 +811,15 @@ void launch_vel_correction_rhs(const Geom& g, Coef<T> C, const T* b, const T* p,
                                T* out, cudaStream_t s) {
     Segs sg = face_segs(g, false);
     if (g.dim == 2)
-        launch_pdl(k_vel_correction_rhs<2, T>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, b, p, u, out);
+        launch_pdl(C.lam_c ? k_vel_correction_rhs<2, T, true> : k_vel_correction_rhs<2, T, false>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, b, p, u, out);
     else
-        launch_pdl(k_vel_correction_rhs<3, T>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, b, p, u, out);
+        launch_pdl(C.lam_c ? k_vel_correction_rhs<3, T, true> : k_vel_correction_rhs<3, T, false>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, b, p, u, out);
 }
 
 template <typename T>
-void launch_schur_combine(int n, const double* theta, const T* phi, const T* mu, const T* bc, T* xp,
-                          cudaStream_t s) {
-    launch_pdl(k_schur_combine<T>, dim3(nblk(n)), dim3(TPB), s, n, theta, phi, mu, bc, xp);
+void launch_schur_combine(int n, const double* theta, const T* phi, const T* mu, const T* lam,
+                          const T* bc, T* xp, cudaStream_t s) {
+    launch_pdl(k_schur_combine<T>, dim3(nblk(n)), dim3(TPB), s, n, theta, phi, mu, lam, bc, xp);
 }
 
 template <typename T>
@@ -865,7 +889,8 @@ void launch_check_fields(int n, const double* rho, const double* mu, double* scr
                                      cudaStream_t);                                                \
     template void launch_vel_correction_rhs<T>(const Geom&, Coef<T>, const T*, const T*,         \
                                                const T*, T*, cudaStream_t);                        \
-    template void launch_schur_combine<T>(int, const double*, const T*, const T*, const T*, T*,  \
+    template void launch_schur_combine<T>(int, const double*, const T*, const T*, const T*,      \
+                                          const T*, T*,                                            \
                                           cudaStream_t);                                           \
     template void launch_sum<T>(int, const T*, double*, double*, cudaStream_t);                  \
     template void launch_sub_mean<T>(int, T*, double*, cudaStream_t);                            \

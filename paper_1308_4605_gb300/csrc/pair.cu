@@ -43,7 +43,7 @@ __device__ __forceinline__ int slot(int c, int o, int W, int e) {
 
 // Velocity component A.  Tile: 2 TXC faces along x (TXC of each colour),
 // TY along y, TZ along z (3D); one thread per black point.
-template <int DIM, int A, typename T, int TXC, int TY, int TZ>
+template <int DIM, int A, typename T, int TXC, int TY, int TZ, bool BULK>
 __global__ void __launch_bounds__(TXC * TY * TZ)
 k_vel_gs_pair(Geom g, Coef<T> C, const T* src, T* dst, const T* __restrict__ rhs) {
     pdl_entry();
@@ -80,7 +80,7 @@ k_vel_gs_pair(Geom g, Coef<T> C, const T* src, T* dst, const T* __restrict__ rhs
             T v = T(0);
             if (!wall_face(g, A, q)) {
                 T dsum;
-                const T N = visc_offdiag_acc<DIM, A, T, F32>(g, C, q, pa, pb, dsum);
+                const T N = visc_offdiag_acc<DIM, A, T, F32, BULK>(g, C, q, pa, pb, dsum);
                 const int f = fidx(g, A, q);
                 v = vel_gs_value<T>(g, C, f, N, dsum, rhs);
                 const bool inner = lx >= 1 && lx <= 2 * TXC && ux < e0 && ly >= 1 && ly <= TY &&
@@ -109,7 +109,7 @@ k_vel_gs_pair(Geom g, Coef<T> C, const T* src, T* dst, const T* __restrict__ rhs
         return R[sz][sy][sx];
     };
     T dsum;
-    const T N = visc_offdiag_acc<DIM, A, T, F32>(g, C, q, pa, pb, dsum);
+    const T N = visc_offdiag_acc<DIM, A, T, F32, BULK>(g, C, q, pa, pb, dsum);
     const int f = fidx(g, A, q);
     dst[f] = vel_gs_value<T>(g, C, f, N, dsum, rhs);
 }
@@ -186,16 +186,21 @@ template <typename T>
 void launch_vel_gs_pair(const Geom& g, Coef<T> C, int comp, const T* src, T* dst, const T* rhs,
                         cudaStream_t s) {
     const dim3 gr = pair_grid(g.dim, g.fe[comp][0], g.fe[comp][1], g.fe[comp][2]);
+    const bool bk = C.lam_c != nullptr;
+#define STK_P2(A) (bk ? k_vel_gs_pair<2, A, T, P2X, P2Y, 1, true> : k_vel_gs_pair<2, A, T, P2X, P2Y, 1, false>)
+#define STK_P3(A) (bk ? k_vel_gs_pair<3, A, T, P3X, P3Y, P3Z, true> : k_vel_gs_pair<3, A, T, P3X, P3Y, P3Z, false>)
     if (g.dim == 2) {
         const dim3 bl(P2X * P2Y);
-        if (comp == 0) launch_pdl(k_vel_gs_pair<2, 0, T, P2X, P2Y, 1>, gr, bl, s, g, C, src, dst, rhs);
-        else launch_pdl(k_vel_gs_pair<2, 1, T, P2X, P2Y, 1>, gr, bl, s, g, C, src, dst, rhs);
+        if (comp == 0) launch_pdl(STK_P2(0), gr, bl, s, g, C, src, dst, rhs);
+        else launch_pdl(STK_P2(1), gr, bl, s, g, C, src, dst, rhs);
     } else {
         const dim3 bl(P3X * P3Y * P3Z);
-        if (comp == 0) launch_pdl(k_vel_gs_pair<3, 0, T, P3X, P3Y, P3Z>, gr, bl, s, g, C, src, dst, rhs);
-        else if (comp == 1) launch_pdl(k_vel_gs_pair<3, 1, T, P3X, P3Y, P3Z>, gr, bl, s, g, C, src, dst, rhs);
-        else launch_pdl(k_vel_gs_pair<3, 2, T, P3X, P3Y, P3Z>, gr, bl, s, g, C, src, dst, rhs);
+        if (comp == 0) launch_pdl(STK_P3(0), gr, bl, s, g, C, src, dst, rhs);
+        else if (comp == 1) launch_pdl(STK_P3(1), gr, bl, s, g, C, src, dst, rhs);
+        else launch_pdl(STK_P3(2), gr, bl, s, g, C, src, dst, rhs);
     }
+#undef STK_P2
+#undef STK_P3
 }
 
 template <typename T>

@@ -55,6 +55,8 @@ struct Level {
     Coef<float> cf;
     Work<double> wd;
     Work<float> wf;
+    double* lam_d = nullptr;   // storage of the bulk term (allocated on first use)
+    float* lam_f = nullptr;
 };
 
 template <typename T>
@@ -86,6 +88,8 @@ struct stk_handle {
     int lcoarse_d = 0, lcoarse_f = 0;        // first level run by the coarse kernel (FP64, FP32)
     int tpb_d = 256, tpb_f = 256;            // threads per block of the colour kernels
     int lpair_d = 0, lpair_f = 0;            // first level smoothed by the two-colour kernels
+    bool bulk = false;                       // bulk-viscosity stress form on
+    double *gamma = nullptr, *rho0 = nullptr, *mu0 = nullptr;   // level-0 fields
     CLevel<double>* cld = nullptr;           // device copies of the level descriptors
     CLevel<float>* clf = nullptr;
     double* red = nullptr;    // reduction scratch (RED_BLOCKS * 36 doubles)
@@ -390,7 +394,7 @@ void vcycle_vel(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp, 
     if (l >= lcoarse_of<T>(h)) {   // this level and all coarser ones in one launch
         Scope sc(h, PF_COARSE, 0.0, s);
         launch_coarse_vcycle_vel<T>(L.g.dim, clev_of<T>(h) + l, (int)h->lev.size() - l, rhs, phi,
-                                    mp.nu, mp.ncoarse, s);
+                                    mp.nu, mp.ncoarse, h->bulk, s);
         return;
     }
     launch_zero<T>(L.g.nvel, phi, s);
@@ -531,19 +535,19 @@ void apply_precond(stk_handle* h, int which, const T* b, T* x, const MGParams& m
             Scope sc(h, PF_ALG, sizeof(T) * (3.0 * g.nvel + g.ncell), s);
             launch_sub_grad<T>(g, C.beta, B.xs, W.phi_p, xu, s);
         }
-        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, h->dsc + DS_THETA, W.phi_p, C.mu_c, B.bc, xp, s); }
+        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, h->dsc + DS_THETA, W.phi_p, C.mu_c, C.lam_c, B.bc, xp, s); }
         break;
     }
     case STK_P2: {
         velocity_solve<T>(h, bu, xu, mp, s);
         { Scope sc(h, PF_ALG, alg_cell, s); launch_div_plus<T>(g, xu, bp, B.bc, s); }
         if (pois) poisson_solve<T>(h, B.bc, W.phi_p, mp, s);
-        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, h->dsc + DS_THETA, pois ? W.phi_p : nullptr, C.mu_c, B.bc, xp, s); }
+        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, h->dsc + DS_THETA, pois ? W.phi_p : nullptr, C.mu_c, C.lam_c, B.bc, xp, s); }
         break;
     }
     case STK_P3: {
         if (pois) poisson_solve<T>(h, bp, W.phi_p, mp, s);
-        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, h->dsc + DS_THETA, pois ? W.phi_p : nullptr, C.mu_c, bp, xp, s); }
+        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, h->dsc + DS_THETA, pois ? W.phi_p : nullptr, C.mu_c, C.lam_c, bp, xp, s); }
         {
             Scope sc(h, PF_ALG, sizeof(T) * (2.0 * g.nvel + g.ncell), s);
             launch_sub_grad<T>(g, (const T*)nullptr, bu, xp, B.tmpu, s);
@@ -554,14 +558,14 @@ void apply_precond(stk_handle* h, int which, const T* b, T* x, const MGParams& m
     case STK_P4: {
         velocity_solve<T>(h, bu, xu, mp, s);
         if (pois) poisson_solve<T>(h, bp, W.phi_p, mp, s);
-        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, h->dsc + DS_THETA, pois ? W.phi_p : nullptr, C.mu_c, bp, xp, s); }
+        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, h->dsc + DS_THETA, pois ? W.phi_p : nullptr, C.mu_c, C.lam_c, bp, xp, s); }
         break;
     }
     default: {  // STK_P5
         velocity_solve<T>(h, bu, B.xs, mp, s);
         { Scope sc(h, PF_ALG, alg_cell, s); launch_div_plus<T>(g, B.xs, bp, B.bc, s); }
         if (pois) poisson_solve<T>(h, B.bc, W.phi_p, mp, s);
-        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, h->dsc + DS_THETA, pois ? W.phi_p : nullptr, C.mu_c, B.bc, xp, s); }
+        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, h->dsc + DS_THETA, pois ? W.phi_p : nullptr, C.mu_c, C.lam_c, B.bc, xp, s); }
         {
             Scope sc(h, PF_ALG, bytes_vel_residual<T>(g), s);
             launch_vel_correction_rhs<T>(g, C, bu, xp, B.xs, B.tmpu, s);
@@ -998,6 +1002,35 @@ int validate_params(stk_handle* h, const stk_solver_params& prm) {
 
 bool is_pow2(int v) { return v >= 2 && (v & (v - 1)) == 0; }
 
+// level descriptors of the single-block coarse-level kernel (they embed the
+// coefficient pointers, so they are rewritten when the bulk term toggles)
+cudaError_t upload_clevels(stk_handle* h) {
+    const int nl = (int)h->lev.size();
+    std::vector<CLevel<double>> cd(nl);
+    std::vector<CLevel<float>> cf(nl);
+    for (int l = 0; l < nl; ++l) {
+        const Level& L = h->lev[l];
+        cd[l] = CLevel<double>{L.g, L.cd, L.wd.phi_u, L.wd.rhs_u, L.wd.res_u, L.wd.phi_p, L.wd.rhs_p, L.wd.res_p};
+        cf[l] = CLevel<float>{L.g, L.cf, L.wf.phi_u, L.wf.rhs_u, L.wf.res_u, L.wf.phi_p, L.wf.rhs_p, L.wf.res_p};
+    }
+    cudaError_t e = cudaMemcpy(h->cld, cd.data(), sizeof(CLevel<double>) * nl, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(h->clf, cf.data(), sizeof(CLevel<float>) * nl, cudaMemcpyHostToDevice);
+}
+
+// all coefficients from rho, mu (and gamma) on the finest level down
+void build_coefficients(stk_handle* h, const double* rho, const double* mu, cudaStream_t s) {
+    const Geom& g0 = h->lev[0].g;
+    launch_fine_coefficients(g0, rho, mu, h->theta, h->lev[0].cd, s);
+    if (h->bulk) launch_bulk_lambda(g0.ncell, h->gamma, mu, h->lev[0].cd.lam_c, s);
+    for (size_t l = 1; l < h->lev.size(); ++l)
+        launch_coarsen_coefficients(h->lev[l - 1].g, h->lev[l - 1].cd, h->lev[l].g, h->lev[l].cd, s);
+    for (auto& L : h->lev) {
+        launch_inverse_diagonals(L.g, L.cd, s);
+        launch_convert_coefficients(L.g, L.cd, L.cf, s);
+    }
+}
+
 }  // namespace
 
 // ===================================================================== C ABI
@@ -1134,6 +1167,8 @@ int stk_create(int dim, const int* n, double hh, const int* bc, stk_handle** out
     CKC(dalloc(h, &h->xk, ns));
     CKC(dalloc(h, &h->tmp, ns));
     CKC(dalloc(h, &h->red, (size_t)RED_SCRATCH));
+    CKC(dalloc(h, &h->rho0, g0.ncell));
+    CKC(dalloc(h, &h->mu0, g0.ncell));
     CKC(dalloc(h, &h->dsc, NDSC));
     {
         void* p = nullptr;
@@ -1154,15 +1189,9 @@ int stk_create(int dim, const int* n, double hh, const int* bc, stk_handle** out
         while (h->lcoarse_d > 0 && h->lev[h->lcoarse_d - 1].g.ncell <= COARSE_MAX_CELLS_F64) --h->lcoarse_d;
         std::vector<CLevel<double>> cd(nl);
         std::vector<CLevel<float>> cf(nl);
-        for (int l = 0; l < nl; ++l) {
-            const Level& L = h->lev[l];
-            cd[l] = CLevel<double>{L.g, L.cd, L.wd.phi_u, L.wd.rhs_u, L.wd.res_u, L.wd.phi_p, L.wd.rhs_p, L.wd.res_p};
-            cf[l] = CLevel<float>{L.g, L.cf, L.wf.phi_u, L.wf.rhs_u, L.wf.res_u, L.wf.phi_p, L.wf.rhs_p, L.wf.res_p};
-        }
         CKC(dalloc(h, &h->cld, nl));
         CKC(dalloc(h, &h->clf, nl));
-        CKC(cudaMemcpy(h->cld, cd.data(), sizeof(CLevel<double>) * nl, cudaMemcpyHostToDevice));
-        CKC(cudaMemcpy(h->clf, cf.data(), sizeof(CLevel<float>) * nl, cudaMemcpyHostToDevice));
+        CKC(upload_clevels(h));
     }
 #undef CKC
     *out = h;
@@ -1210,16 +1239,53 @@ int stk_set_coefficients(stk_handle* h, const double* rho, const double* mu, dou
     h->theta = theta;
     h->hpin[HP_THETA] = theta;
     CK(cudaMemcpyAsync(h->dsc + DS_THETA, h->hpin + HP_THETA, sizeof(double), cudaMemcpyHostToDevice, s));
-    launch_fine_coefficients(g0, rho, mu, h->theta, h->lev[0].cd, s);
-    for (size_t l = 1; l < h->lev.size(); ++l)
-        launch_coarsen_coefficients(h->lev[l - 1].g, h->lev[l - 1].cd, h->lev[l].g, h->lev[l].cd, s);
-    for (auto& L : h->lev) {
-        launch_inverse_diagonals(L.g, L.cd, s);
-        launch_convert_coefficients(L.g, L.cd, L.cf, s);
-    }
+    // rho and mu are kept so that stk_set_bulk_viscosity can rebuild
+    CK(cudaMemcpyAsync(h->rho0, rho, sizeof(double) * g0.ncell, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(h->mu0, mu, sizeof(double) * g0.ncell, cudaMemcpyDeviceToDevice, s));
+    build_coefficients(h, rho, mu, s);
     CKL();
     CK(cudaStreamSynchronize(s));
     h->coef_set = true;
+    return STK_OK;
+}
+
+int stk_set_bulk_viscosity(stk_handle* h, const double* gamma, void* stream) {
+    if (!h) return STK_ERR_ARG;
+    if (!h->coef_set) return fail(h, STK_ERR_STATE, "coefficients not set");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(cudaSetDevice(h->device));
+    const Geom& g0 = h->lev[0].g;
+    const bool on = gamma != nullptr;
+    if (on) {   // gamma finite and >= 0 (checked beside the stored rho > 0)
+        launch_check_fields(g0.ncell, h->rho0, gamma, h->red, h->dsc + DS_N2, s);
+        CKL();
+        CK(cudaMemcpyAsync(h->hpin, h->dsc + DS_N2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (h->hpin[0] != 0.0) return fail(h, STK_ERR_NONFINITE, "gamma has %g non-finite entries", h->hpin[0]);
+        if (h->hpin[1] != 0.0) return fail(h, STK_ERR_ARG, "gamma < 0 at %g cells", h->hpin[1]);
+        if (!h->gamma) {   // first use: level-0 gamma and the lam hierarchy
+            CK(dalloc(h, &h->gamma, g0.ncell));
+            for (auto& L : h->lev) {
+                CK(dalloc(h, &L.lam_d, L.g.ncell));
+                CK(dalloc(h, &L.lam_f, L.g.ncell));
+            }
+        }
+        CK(cudaMemcpyAsync(h->gamma, gamma, sizeof(double) * g0.ncell, cudaMemcpyDeviceToDevice, s));
+    }
+    if (on != h->bulk) {
+        // the coefficient structs carry the lam pointers only while the bulk
+        // term is on; graphs and level descriptors embed those structs
+        clear_graphs(h);
+        for (auto& L : h->lev) {
+            L.cd.lam_c = on ? L.lam_d : nullptr;
+            L.cf.lam_c = on ? L.lam_f : nullptr;
+        }
+        h->bulk = on;
+        CK(upload_clevels(h));
+    }
+    build_coefficients(h, h->rho0, h->mu0, s);
+    CKL();
+    CK(cudaStreamSynchronize(s));
     return STK_OK;
 }
 
@@ -1556,6 +1622,7 @@ int stk_gradient(stk_handle* h, const double* const* u, const double* const* lam
                  double* dL_dlogmu, double* dL_drho, void* stream) {
     if (!h) return STK_ERR_ARG;
     if (!h->coef_set) return fail(h, STK_ERR_STATE, "coefficients not set");
+    if (h->bulk) return fail(h, STK_ERR_STATE, "the gradient is defined for the stress form without bulk viscosity");
     if (!u || !lambda || !dL_dlogmu || !dL_drho) return fail(h, STK_ERR_ARG, "null pointer");
     for (int a = 0; a < h->dim; ++a)
         if (!u[a] || !lambda[a]) return fail(h, STK_ERR_ARG, "null face array");

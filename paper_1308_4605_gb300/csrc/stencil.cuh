@@ -86,67 +86,8 @@ template <int A> struct Trans<3, A> {
 };
 
 // h^2 (L_mu phi)_A at the interior A-face q (Eq. div_stress with the wall
-// closures of Sec. 3.1), grid scaling factored out, arithmetic in T.  With
-// DIAG, dsum receives h^2 times the viscous part of A's diagonal (a no-slip
-// wall edge counts twice: its derivative is taken over h/2).
-template <int DIM, int A, typename T, typename TV, bool DIAG>
-__device__ __forceinline__ T visc_h2(const Geom& g, const Coef<T>& C, const int q[3],
-                                     const TV* phi, T& dsum) {
-    int qp[3] = {q[0], q[1], q[2]};
-    int qm[3] = {q[0], q[1], q[2]};
-    qp[A] = step(g, A, q[A], 1);
-    qm[A] = step(g, A, q[A], -1);
-    const T pa = T(phi[fidx(g, A, q)]);
-    const T pp = T(phi[fidx(g, A, qp)]);
-    const T pm = T(phi[fidx(g, A, qm)]);
-    const T mh = ld(C.mu_c + cidx(g, q));
-    const T ml = ld(C.mu_c + cidx(g, qm));
-    T L = mh * (pp - pa);
-    L = fma(-ml, pa - pm, L);
-    L = L + L;
-    if (DIAG) dsum = T(2) * (mh + ml);
-#pragma unroll
-    for (int B = 0; B < DIM; ++B) {
-        if (B == A) continue;
-        const int P = A + B - 1;   // edge pair index of {A, B}
-        const bool wlo = !g.per[B] && q[B] == 0;
-        const bool whi = !g.per[B] && q[B] == g.n[B] - 1;
-        int qe[3] = {q[0], q[1], q[2]};
-        qe[B] = step(g, B, q[B], 1);
-        const T mlo = ld(C.mu_e[P] + eidx(g, P, q));
-        const T mhi = ld(C.mu_e[P] + eidx(g, P, qe));
-        T dlo, dhi;
-        if (wlo) {
-            dlo = pa + pa;               // (phi - 0) / (h/2)
-        } else {
-            int qb[3] = {q[0], q[1], q[2]};
-            qb[B] = step(g, B, q[B], -1);
-            dlo = pa - T(phi[fidx(g, A, qb)]);
-        }
-        dhi = whi ? -(pa + pa) : T(phi[fidx(g, A, qe)]) - pa;
-        // d phi_B / dx_A on the two edges: B-faces in A-cells q[A] and q[A]-1
-        int r0[3] = {q[0], q[1], q[2]};
-        r0[A] = qm[A];
-        int r2[3] = {qe[0], qe[1], qe[2]};
-        r2[A] = qm[A];
-        const T xlo = T(phi[fidx(g, B, q)]) - T(phi[fidx(g, B, r0)]);
-        const T xhi = T(phi[fidx(g, B, qe)]) - T(phi[fidx(g, B, r2)]);
-        L = fma(mhi, dhi + xhi, L);
-        L = fma(-mlo, dlo + xlo, L);
-        if (DIAG) dsum += (whi ? T(2) : T(1)) * mhi + (wlo ? T(2) : T(1)) * mlo;
-    }
-    return L;
-}
-
-template <int DIM, typename T, typename TV, bool DIAG>
-__device__ __forceinline__ T visc_h2_any(int a, const Geom& g, const Coef<T>& C, const int q[3],
-                                         const TV* phi, T& dsum) {
-    if (a == 0) return visc_h2<DIM, 0, T, TV, DIAG>(g, C, q, phi, dsum);
-    if (a == 1) return visc_h2<DIM, 1, T, TV, DIAG>(g, C, q, phi, dsum);
-    return visc_h2<DIM, DIM == 3 ? 2 : 1, T, TV, DIAG>(g, C, q, phi, dsum);
-}
-
-// The same operator split into its off-diagonal part: h^2 L_A = N - phi_A dsum,
+// closures of Sec. 3.1), grid scaling factored out, arithmetic in T, split
+// into its off-diagonal part: h^2 L_A = N - phi_A dsum,
 //   N    = 2 (mu_hi phi_A[+a] + mu_lo phi_A[-a])
 //          + sum_B mu_e,hi (phi_A[+b] + dphi_B/dx_A|hi) + mu_e,lo (phi_A[-b] - dphi_B/dx_A|lo)
 //   dsum = 2 (mu_hi + mu_lo) + sum_B (f_hi mu_e,hi + f_lo mu_e,lo),
@@ -154,7 +95,12 @@ __device__ __forceinline__ T visc_h2_any(int a, const Geom& g, const Coef<T>& C,
 // derivative over h/2, Sec. 3.1; f = 1 inside).  A Gauss-Seidel step is then
 // phi_A <- (rhs + N / h^2) / (alpha + dsum / h^2) with no term in the old
 // phi_A, and the operator is A phi = diag phi_A - N / h^2.
-template <int DIM, int A, typename T, bool DIAG, typename PA, typename PB>
+// With bulk viscosity (Sec. 2: + (gamma - 2/3 mu)(div u) I in the stress,
+// lam = gamma - 2/3 mu at cells) the normal stresses of the two cells gain
+// lam times their divergence: N += lam_hi (phi_A[+a] + sum_B dphi_B|hi)
+// + lam_lo (phi_A[-a] - sum_B dphi_B|lo), dphi_B the B-face difference
+// across the cell, and dsum += lam_hi + lam_lo.
+template <int DIM, int A, typename T, bool DIAG, bool BULK, typename PA, typename PB>
 __device__ __forceinline__ T visc_offdiag_acc(const Geom& g, const Coef<T>& C, const int q[3],
                                               const PA& pa, const PB& pb, T& dsum) {
     // pa(r): phi_A at the A-face r; pb(B, r): phi_B at the B-face r
@@ -170,6 +116,15 @@ __device__ __forceinline__ T visc_offdiag_acc(const Geom& g, const Coef<T>& C, c
     N = fma(ml, pm, N);
     N = N + N;
     if (DIAG) dsum = T(2) * (mh + ml);
+    constexpr bool bulk = BULK;   // a compile-time switch: the plain form issues no bulk work
+    T lh = T(0), ll = T(0);
+    if (bulk) {
+        lh = ld(C.lam_c + cidx(g, q));
+        ll = ld(C.lam_c + cidx(g, qm));
+        N = fma(lh, pp, N);
+        N = fma(ll, pm, N);
+        if (DIAG) dsum += lh + ll;
+    }
 #pragma unroll
     for (int B = 0; B < DIM; ++B) {
         if (B == A) continue;
@@ -197,24 +152,28 @@ __device__ __forceinline__ T visc_offdiag_acc(const Geom& g, const Coef<T>& C, c
         N = fma(mhi, shi, N);
         N = fma(mlo, slo, N);
         if (DIAG) dsum += (whi ? T(2) : T(1)) * mhi + (wlo ? T(2) : T(1)) * mlo;
+        if (bulk) {   // B-divergence of the cells q (hi) and q - e_A (lo)
+            N = fma(lh, pb(B, qe) - pb(B, q), N);
+            N = fma(-ll, pb(B, r2) - pb(B, r0), N);
+        }
     }
     return N;
 }
 
-template <int DIM, int A, typename T, typename TV, bool DIAG>
+template <int DIM, int A, typename T, typename TV, bool DIAG, bool BULK = false>
 __device__ __forceinline__ T visc_offdiag_h2(const Geom& g, const Coef<T>& C, const int q[3],
                                              const TV* phi, T& dsum) {
-    return visc_offdiag_acc<DIM, A, T, DIAG>(
+    return visc_offdiag_acc<DIM, A, T, DIAG, BULK>(
         g, C, q, [&](const int* r) { return T(phi[fidx(g, A, r)]); },
         [&](int B, const int* r) { return T(phi[fidx(g, B, r)]); }, dsum);
 }
 
-template <int DIM, typename T, typename TV, bool DIAG>
+template <int DIM, typename T, typename TV, bool DIAG, bool BULK = false>
 __device__ __forceinline__ T visc_offdiag_any(int a, const Geom& g, const Coef<T>& C,
                                               const int q[3], const TV* phi, T& dsum) {
-    if (a == 0) return visc_offdiag_h2<DIM, 0, T, TV, DIAG>(g, C, q, phi, dsum);
-    if (a == 1) return visc_offdiag_h2<DIM, 1, T, TV, DIAG>(g, C, q, phi, dsum);
-    return visc_offdiag_h2<DIM, DIM == 3 ? 2 : 1, T, TV, DIAG>(g, C, q, phi, dsum);
+    if (a == 0) return visc_offdiag_h2<DIM, 0, T, TV, DIAG, BULK>(g, C, q, phi, dsum);
+    if (a == 1) return visc_offdiag_h2<DIM, 1, T, TV, DIAG, BULK>(g, C, q, phi, dsum);
+    return visc_offdiag_h2<DIM, DIM == 3 ? 2 : 1, T, TV, DIAG, BULK>(g, C, q, phi, dsum);
 }
 
 // Off-diagonal part of h^2 L_rho at cell q: Nc = sum_a (beta_hi phi[+a] +
@@ -287,23 +246,23 @@ __device__ __forceinline__ T vel_gs_value(const Geom& g, const Coef<T>& C, int f
     else return num * ld(C.invd_u + f);
 }
 
-template <int DIM, int A, typename T>
+template <int DIM, int A, typename T, bool BULK = false>
 __device__ __forceinline__ void vel_gs_point(const Geom& g, const Coef<T>& C, const int q[3],
                                              T* phi, const T* rhs) {
     constexpr bool F32 = sizeof(T) == 4;
     T dsum;
-    const T N = visc_offdiag_h2<DIM, A, T, T, F32>(g, C, q, phi, dsum);
+    const T N = visc_offdiag_h2<DIM, A, T, T, F32, BULK>(g, C, q, phi, dsum);
     const int f = fidx(g, A, q);
     phi[f] = vel_gs_value<T>(g, C, f, N, dsum, rhs);
 }
 
-template <int DIM, typename T>
+template <int DIM, typename T, bool BULK = false>
 __device__ __forceinline__ T vel_res_point(int a, const Geom& g, const Coef<T>& C, const int q[3],
                                            const T* phi, const T* rhs) {
     constexpr bool F32 = sizeof(T) == 4;
     const int f = fidx(g, a, q);
     T dsum;
-    const T N = visc_offdiag_any<DIM, T, T, F32>(a, g, C, q, phi, dsum);
+    const T N = visc_offdiag_any<DIM, T, T, F32, BULK>(a, g, C, q, phi, dsum);
     const T ih2 = gih2<T>(g);
     const T diag = F32 ? fma(ih2, dsum, ld(C.alpha + f)) : ld(C.diag_u + f);
     return fma(ih2, N, rhs[f]) - diag * phi[f];

@@ -81,6 +81,7 @@ def _load():
         "stk_face_length": (ctypes.c_longlong, [P, I]),
         "stk_cell_length": (ctypes.c_longlong, [P]),
         "stk_set_coefficients": (I, [P, P, P, D, P]),
+        "stk_set_bulk_viscosity": (I, [P, P, P]),
         "stk_apply_operator": (I, [P, PP, P, PP, P, P]),
         "stk_apply_preconditioner": (I, [P, I, PP, P, PP, P, P]),
         "stk_apply_preconditioner_params": (I, [P, ctypes.POINTER(stk_solver_params), PP, P, PP, P, P]),
@@ -110,7 +111,7 @@ def _load():
 
 _lib = _load()
 EXPORTED = ["stk_default_params", "stk_create", "stk_destroy", "stk_last_error", "stk_face_length",
-            "stk_cell_length", "stk_set_coefficients", "stk_apply_operator",
+            "stk_cell_length", "stk_set_coefficients", "stk_set_bulk_viscosity", "stk_apply_operator",
             "stk_apply_preconditioner", "stk_apply_preconditioner_params", "stk_velocity_vcycle", "stk_pressure_vcycle", "stk_solve",
             "stk_profile", "stk_profile_read", "stk_kernel_launches", "stk_pressure_vcycle_noalloc", "stk_gradient", "stk_backward_euler_rhs", "stk_solve_batched", "stk_get_schedule", "stk_set_schedule", "stk_autotune"]
 
@@ -199,6 +200,12 @@ def stk_set_coefficients(h, rho, mu, dt, stream=None):
     nc = stk_cell_length(h)
     return _check(h, _lib.stk_set_coefficients(h, _ptr(rho, nc), _ptr(mu, nc), float(dt),
                                                _stream(stream)))
+
+
+def stk_set_bulk_viscosity(h, gamma, stream=None):
+    nc = int(_lib.stk_cell_length(h))
+    return _check(h, _lib.stk_set_bulk_viscosity(h, _ptr(gamma, nc) if gamma is not None else None,
+                                                 _stream(stream)))
 
 
 def stk_apply_operator(h, x_u, x_p, y_u, y_p, stream=None):
@@ -368,6 +375,10 @@ class StokesSolver:
     def set_coefficients(self, rho, mu, theta):
         dt = math.inf if theta == 0.0 else 1.0 / theta
         stk_set_coefficients(self.handle, rho, mu, dt)
+
+    def set_bulk_viscosity(self, gamma):
+        """gamma: cell array of bulk viscosities, or None to switch off."""
+        stk_set_bulk_viscosity(self.handle, gamma)
 
     def apply_operator(self, x_u, x_p):
         y_u, y_p = self.zeros(x_p.device)
