@@ -177,6 +177,29 @@ int stk_solve(stk_handle* h, const stk_solver_params* params, const double* cons
               const double* b_p, double* const* x_u, double* x_p, stk_solve_info* info,
               void* stream);
 
+/* Inhomogeneous velocity boundary conditions (Sec. 3.2: the viscous
+ * stencils next to a wall use the prescribed values, so the operator is
+ * affine; the Krylov solver works on the homogeneous problem after the
+ * boundary terms are subtracted from the right-hand side):
+ *   b_u -= c_u,  b_p -= c_p,   with M x + c the operator with boundary data,
+ * for the Stokes operator and coefficients set on h (bulk term included).
+ * u_wall: NULL, or dim face arrays whose wall faces (the a-faces at index 0
+ *   and n_a of a non-periodic axis a) hold the prescribed normal velocity;
+ *   other entries are ignored (a NULL entry means zero).
+ * u_tan: NULL, or 18 pointers, u_tan[3 * (2 d + side) + a] for the wall of
+ *   axis d (side 0 low, 1 high) and component a != d: the prescribed
+ *   tangential velocity on that wall at the positions of the a-faces, an
+ *   array with the extents of the a-face array with axis d removed (x
+ *   fastest); NULL means zero.  Only no-slip walls use it (a free-slip wall
+ *   has zero shear stress).
+ * The solution of M x = b' is then the interior field; its wall faces are
+ * the prescribed normal velocities.  With walls all around, the net normal
+ * flux must match the integral of g (the pressure right-hand side must have
+ * zero mean).  Stream-ordered, no synchronisation. */
+int stk_subtract_boundary_terms(stk_handle* h, const double* const* u_wall,
+                                const double* const* u_tan, double* const* b_u, double* b_p,
+                                void* stream);
+
 /* Momentum right-hand side of one backward-Euler time step (Sec. 2, Eq.
  * Stokes_eqn: rho (u^{n+1} - u^n)/dt + grad p^{n+1} = div tau(u^{n+1}) +
  * f^{n+1}, div u^{n+1} = g^{n+1}): b_u = (rho_f / dt) u^n + f on every

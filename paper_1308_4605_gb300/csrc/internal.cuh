@@ -234,6 +234,11 @@ void launch_axpy(int n, T a, const T* x, T* y, cudaStream_t s);
 template <typename TA, typename TB>
 void launch_convert(int n, const TA* a, TB* b, cudaStream_t s);
 // dL/dlog mu and dL/drho (cell arrays) from packed velocities u and lambda
+// inhomogeneous boundary data: wall faces of src into the packed dst; the
+// tangential-velocity terms of a no-slip wall subtracted from c
+void launch_copy_walls(const Geom& g, int a, const double* src, double* dst, cudaStream_t s);
+void launch_wall_tangential(const Geom& g, const double* mu_e, int d, int side, int a,
+                            const double* U, double* c, cudaStream_t s);
 // b = alpha u + f on the a-faces (f may be null), zero on wall faces
 void launch_inertial_rhs(const Geom& g, int a, const double* alpha, const double* u,
                          const double* f, double* b, cudaStream_t s);

@@ -634,6 +634,39 @@ __global__ void k_inertial_rhs(Geom g, int a, const double* __restrict__ alpha,
     b[t] = wall_face(g, a, q) ? 0.0 : fma(alpha[g.foff[a] + t], u[t], f ? f[t] : 0.0);
 }
 
+// Inhomogeneous boundary data: copy the wall faces of the a-component face
+// array src into the packed vector dst (other entries untouched).
+__global__ void k_copy_walls(Geom g, int a, const double* __restrict__ src, double* __restrict__ dst) {
+    pdl_entry();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.fsize[a]) return;
+    int q[3];
+    decode_face(g, a, t, q);
+    if (wall_face(g, a, q)) dst[g.foff[a] + t] = src[t];
+}
+
+// Tangential velocity U of a no-slip wall of axis d (side 0 low, 1 high) for
+// component a != d: the one-sided wall derivative (u_first - U)/(h/2) adds
+// 2 mu_e U / h^2 to L_mu at the first interior a-faces, i.e. c -= 2 mu_e U / h^2
+// in the momentum rows.  U is indexed by the a-face position without axis d.
+__global__ void k_wall_tangential(Geom g, const double* __restrict__ mu_e, int d, int side, int a,
+                                  const double* __restrict__ U, double* c) {
+    pdl_entry();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.fsize[a]) return;
+    int q[3];
+    decode_face(g, a, t, q);
+    if (wall_face(g, a, q) || q[d] != (side ? g.n[d] - 1 : 0)) return;
+    int qe[3] = {q[0], q[1], q[2]};
+    if (side) qe[d] = g.n[d];
+    const int p = a + d - 1;
+    int c0 = -1, c1 = -1;
+    for (int k = 0; k < 3; ++k)
+        if (k != d) { if (c0 < 0) c0 = k; else c1 = k; }
+    const int iu = q[c1] * g.fe[a][c0] + q[c0];
+    c[g.foff[a] + t] -= 2.0 * mu_e[eidx(g, p, qe)] * U[iu] * g.ih2;
+}
+
 __global__ void k_check_fields(int n, const double* __restrict__ rho, const double* __restrict__ mu,
                                double* part) {
     pdl_entry();
@@ -854,6 +887,15 @@ void launch_axpy(int n, T a, const T* x, T* y, cudaStream_t s) {
 void launch_inertial_rhs(const Geom& g, int a, const double* alpha, const double* u,
                          const double* f, double* b, cudaStream_t s) {
     launch_pdl(k_inertial_rhs, dim3(nblk(g.fsize[a])), dim3(TPB), s, g, a, alpha, u, f, b);
+}
+
+void launch_copy_walls(const Geom& g, int a, const double* src, double* dst, cudaStream_t s) {
+    launch_pdl(k_copy_walls, dim3(nblk(g.fsize[a])), dim3(TPB), s, g, a, src, dst);
+}
+
+void launch_wall_tangential(const Geom& g, const double* mu_e, int d, int side, int a,
+                            const double* U, double* c, cudaStream_t s) {
+    launch_pdl(k_wall_tangential, dim3(nblk(g.fsize[a])), dim3(TPB), s, g, mu_e, d, side, a, U, c);
 }
 
 void launch_gradient(const Geom& g, const double* mu, double theta, const double* u,

@@ -1355,6 +1355,43 @@ int stk_apply_preconditioner_params(stk_handle* h, const stk_solver_params* para
     return scatter(h, h->tmp, x_u, x_p, s);
 }
 
+int stk_subtract_boundary_terms(stk_handle* h, const double* const* u_wall,
+                                const double* const* u_tan, double* const* b_u, double* b_p,
+                                void* stream) {
+    if (!h) return STK_ERR_ARG;
+    if (!h->coef_set) return fail(h, STK_ERR_STATE, "coefficients not set");
+    int rc;
+    if ((rc = check_ptrs(h, (const void* const*)b_u, b_p))) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(cudaSetDevice(h->device));
+    const Level& L = h->lev[0];
+    const Geom& g = L.g;
+    const int n = nstokes(h);
+    // M applied to the vector that holds only the normal wall velocities
+    launch_zero<double>(n, h->xk, s);
+    if (u_wall)
+        for (int a = 0; a < g.dim; ++a)
+            if (!g.per[a] && u_wall[a]) launch_copy_walls(g, a, u_wall[a], h->xk, s);
+    launch_stokes_matvec<double>(g, L.cd, h->xk, h->tmp, s);
+    // tangential velocities of no-slip walls
+    if (u_tan)
+        for (int d = 0; d < g.dim; ++d) {
+            if (g.per[d]) continue;
+            for (int side = 0; side < 2; ++side) {
+                if ((side ? g.bchi[d] : g.bclo[d]) != STK_NOSLIP) continue;
+                for (int a = 0; a < g.dim; ++a) {
+                    const double* U = u_tan[3 * (2 * d + side) + a];
+                    if (a == d || !U) continue;
+                    launch_wall_tangential(g, L.cd.mu_e[a + d - 1], d, side, a, U, h->tmp, s);
+                }
+            }
+        }
+    for (int a = 0; a < g.dim; ++a) launch_axpy<double>(g.fsize[a], -1.0, h->tmp + g.foff[a], b_u[a], s);
+    launch_axpy<double>(g.ncell, -1.0, h->tmp + g.nvel, b_p, s);
+    CKL();
+    return STK_OK;
+}
+
 int stk_backward_euler_rhs(stk_handle* h, const double* const* u_n, const double* const* f,
                            double* const* b_u, void* stream) {
     if (!h) return STK_ERR_ARG;

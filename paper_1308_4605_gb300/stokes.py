@@ -93,6 +93,7 @@ def _load():
         "stk_kernel_launches": (ctypes.c_longlong, [P]),
         "stk_gradient": (I, [P, PP, PP, P, P, P]),
         "stk_backward_euler_rhs": (I, [P, PP, PP, PP, P]),
+        "stk_subtract_boundary_terms": (I, [P, PP, ctypes.POINTER(ctypes.c_void_p), PP, P, P]),
         "stk_get_schedule": (I, [P, I, ctypes.POINTER(stk_schedule)]),
         "stk_set_schedule": (I, [P, I, ctypes.POINTER(stk_schedule)]),
         "stk_autotune": (I, [P, I, ctypes.POINTER(stk_schedule), P]),
@@ -113,7 +114,7 @@ _lib = _load()
 EXPORTED = ["stk_default_params", "stk_create", "stk_destroy", "stk_last_error", "stk_face_length",
             "stk_cell_length", "stk_set_coefficients", "stk_set_bulk_viscosity", "stk_apply_operator",
             "stk_apply_preconditioner", "stk_apply_preconditioner_params", "stk_velocity_vcycle", "stk_pressure_vcycle", "stk_solve",
-            "stk_profile", "stk_profile_read", "stk_kernel_launches", "stk_pressure_vcycle_noalloc", "stk_gradient", "stk_backward_euler_rhs", "stk_solve_batched", "stk_get_schedule", "stk_set_schedule", "stk_autotune"]
+            "stk_profile", "stk_profile_read", "stk_kernel_launches", "stk_pressure_vcycle_noalloc", "stk_gradient", "stk_backward_euler_rhs", "stk_subtract_boundary_terms", "stk_solve_batched", "stk_get_schedule", "stk_set_schedule", "stk_autotune"]
 
 
 def library():
@@ -225,6 +226,23 @@ def stk_apply_preconditioner_params(h, params, b_u, b_p, x_u, x_p, stream=None):
     return _check(h, _lib.stk_apply_preconditioner_params(
         h, ctypes.byref(params), _ptrs(b_u, fl), _ptr(b_p, nc), _ptrs(x_u, fl), _ptr(x_p, nc),
         _stream(stream)))
+
+
+def stk_subtract_boundary_terms(h, u_wall, u_tan, b_u, b_p, stream=None):
+    """b -= boundary terms.  u_wall: list of face arrays (wall entries used)
+    or None; u_tan: dict {(d, side, a): array} of tangential wall velocities
+    or None (see stokes.h)."""
+    fl, nc = _lengths(h, len(b_u))
+    uw = _ptrs(u_wall, fl) if u_wall is not None else None
+    ut = None
+    keep = []
+    if u_tan:
+        ut = (ctypes.c_void_p * 18)()
+        for (d, side, a), t in u_tan.items():
+            keep.append(t)
+            ut[3 * (2 * d + side) + a] = _ptr(t).value
+    return _check(h, _lib.stk_subtract_boundary_terms(h, uw, ut, _ptrs(b_u, fl), _ptr(b_p, nc),
+                                                      _stream(stream)))
 
 
 def stk_backward_euler_rhs(h, u_n, f, b_u, stream=None):
@@ -375,6 +393,23 @@ class StokesSolver:
     def set_coefficients(self, rho, mu, theta):
         dt = math.inf if theta == 0.0 else 1.0 / theta
         stk_set_coefficients(self.handle, rho, mu, dt)
+
+    def subtract_boundary_terms(self, b_u, b_p, u_wall=None, u_tan=None):
+        """b -= the boundary terms of inhomogeneous velocity boundary
+        conditions (stk_subtract_boundary_terms); u_tan arrays are checked
+        against the a-face extents without axis d."""
+        if u_tan:
+            for (d, side, a), t in u_tan.items():
+                ext = list(face_shape(self.n, self.bc, a))[::-1]   # (x, y, z)
+                want = 1
+                for c in range(3):
+                    if c != d:
+                        want *= ext[c]
+                if d == a or not (0 <= d < self.dim) or self.bc[2 * d + side] == STK_PERIODIC:
+                    raise ValueError(f"no tangential data for wall {(d, side)} and component {a}")
+                if t.numel() != want:
+                    raise ValueError(f"tangential data {(d, side, a)}: {t.numel()} values, expected {want}")
+        stk_subtract_boundary_terms(self.handle, u_wall, u_tan, b_u, b_p)
 
     def set_bulk_viscosity(self, gamma):
         """gamma: cell array of bulk viscosities, or None to switch off."""
