@@ -295,73 +295,64 @@ __device__ __forceinline__ T vel_restrict_point(const Geom& gf, const int Q[3],
 
 // transverse weights of the face prolongation along axis b for fine cell j:
 // 3/4 on coarse cell J = j/2, 1/4 on the nearer neighbour; a neighbour across
-// a wall is a ghost -phi (no-slip) or +phi (free-slip) folded onto J.
-__device__ __forceinline__ void prolong_transverse(const Geom& gc, int b, int j, int& J, int& nb,
-                                                   float& wo, float& wn) {
+// a wall is a ghost -phi (no-slip) or +phi (free-slip) folded onto J.  With
+// `half` both weights are halved (the normal-direction average of an odd
+// fine face folded in).  The weights are selected constants of type T (no
+// conversions, no multiplies).
+template <typename T>
+__device__ __forceinline__ void prolong_transverse(const Geom& gc, int b, int j, bool half, int& J,
+                                                   int& nb, T& wo, T& wn) {
     J = j >> 1;
     nb = (j & 1) ? J + 1 : J - 1;
-    wo = 0.75f;
-    wn = 0.25f;
+    wo = half ? T(0.375) : T(0.75);
+    wn = half ? T(0.125) : T(0.25);
     if (nb < 0 || nb >= gc.n[b]) {
         if (gc.per[b]) {
             nb = wrapm(nb, gc.n[b]);
         } else {
-            const int code = nb < 0 ? gc.bclo[b] : gc.bchi[b];
-            wo += code == NOSLIP ? -0.25f : 0.25f;
-            wn = 0.f;
+            const bool noslip = (nb < 0 ? gc.bclo[b] : gc.bchi[b]) == NOSLIP;
+            wo = noslip ? (half ? T(0.25) : T(0.5)) : (half ? T(0.5) : T(1));
+            wn = T(0);
             nb = J;
         }
     }
 }
 
-// (P phi_c) at the interior fine A-face q (App. C face prolongation)
+// (P phi_c) at the interior fine A-face q (App. C face prolongation): the
+// coincident coarse faces (even q_A) or the mean of the two enclosing ones
+// (odd q_A), interpolated transversally with the weights above.
 template <int DIM, int A, typename T>
 __device__ __forceinline__ T vel_prolong_point(const Geom& gc, const int q[3],
                                                const T* pc) {
     using TR = Trans<DIM, A>;
-    int ca0 = q[A] >> 1, ca1 = ca0;
-    T wa0 = T(1), wa1 = T(0);
-    if (q[A] & 1) {
-        ca1 = ca0 + 1;
-        if (gc.per[A] && ca1 >= gc.n[A]) ca1 -= gc.n[A];
-        wa0 = wa1 = T(0.5);
-    }
+    const int ca0 = q[A] >> 1;
+    const bool odd = q[A] & 1;
+    int ca1 = ca0 + 1;
+    if (gc.per[A] && ca1 >= gc.n[A]) ca1 -= gc.n[A];
     int J0, N0, J1 = 0, N1 = 0;
-    float wo0, wn0, wo1 = 1.f, wn1 = 0.f;
-    prolong_transverse(gc, TR::b0, q[TR::b0], J0, N0, wo0, wn0);
-    if (TR::n == 2) prolong_transverse(gc, TR::b1, q[TR::b1], J1, N1, wo1, wn1);
-    // separable: along the second transverse axis, then the first, then the normal
-    auto line = [&](int ca) -> T {
+    T wo0, wn0, wo1 = T(1), wn1 = T(0);
+    prolong_transverse<T>(gc, TR::b0, q[TR::b0], odd, J0, N0, wo0, wn0);
+    if (TR::n == 2) prolong_transverse<T>(gc, TR::b1, q[TR::b1], false, J1, N1, wo1, wn1);
+    // coarse value at transverse position (j0, j1): one face (even) or the
+    // sum of the two along A (odd; the 1/2 is in wo0, wn0)
+    auto at = [&](int j0, int j1) -> T {
         int Q[3] = {0, 0, 0};
-        Q[A] = ca;
-        Q[TR::b0] = J0;
-        T t0, t1;
-        if (TR::n == 2) {
-            Q[TR::b1] = J1;
-            t0 = T(wo1) * pc[fidx(gc, A, Q)];
-            if (wn1 != 0.f) {
-                Q[TR::b1] = N1;
-                t0 = fma(T(wn1), pc[fidx(gc, A, Q)], t0);
-            }
-            Q[TR::b0] = N0;
-            Q[TR::b1] = J1;
-            t1 = T(wo1) * pc[fidx(gc, A, Q)];
-            if (wn1 != 0.f) {
-                Q[TR::b1] = N1;
-                t1 = fma(T(wn1), pc[fidx(gc, A, Q)], t1);
-            }
-        } else {
-            t0 = pc[fidx(gc, A, Q)];
-            Q[TR::b0] = N0;
-            t1 = pc[fidx(gc, A, Q)];
+        Q[A] = ca0;
+        Q[TR::b0] = j0;
+        if (TR::n == 2) Q[TR::b1] = j1;
+        T v = pc[fidx(gc, A, Q)];
+        if (odd) {
+            Q[A] = ca1;
+            v += pc[fidx(gc, A, Q)];
         }
-        T v = T(wo0) * t0;
-        if (wn0 != 0.f) v = fma(T(wn0), t1, v);
         return v;
     };
-    T acc = line(ca0);
-    if (wa1 != T(0)) acc = wa0 * acc + wa1 * line(ca1);
-    return acc;
+    if (TR::n == 2) {
+        const T t0 = fma(wn1, at(J0, N1), wo1 * at(J0, J1));
+        const T t1 = fma(wn1, at(N0, N1), wo1 * at(N0, J1));
+        return fma(wn0, t1, wo0 * t0);
+    }
+    return fma(wn0, at(N0, 0), wo0 * at(J0, 0));
 }
 
 template <int DIM, typename T, typename PC>
