@@ -190,13 +190,14 @@ def traffic_per_launch(family, form):
     return None
 
 
-def roofline_of(fams, form, peaks):
+def roofline_of(fams, form, peaks, family=None):
     """Roofline of the dominant kernel family of a solve (largest device
-    time).  FP64 Gauss-Seidel kernels are bound by the FP64 pipe (about 0.19
+    time), or of `family`.  FP64 Gauss-Seidel kernels are bound by the FP64 pipe (about 0.19
     FLOP per byte, at the GB300 balance of 1.25 TFLOP/s over 6.8 TB/s, with
     the pipe 80-89 % busy under ncu): reported as "alu" in TFLOP/s.  The rest
     is reported against HBM bandwidth."""
-    dom = max(fams, key=lambda f: f["ms"])
+    dom = max(fams, key=lambda f: f["ms"]) if family is None else \
+        next(f for f in fams if f["name"] == family)
     secs = dom["ms"] * 1e-3
     per_launch_us = dom["ms"] * 1e3 / dom["launches"]
     traffic = traffic_per_launch(dom["name"], form) if dom["name"].endswith("_l0") else None
@@ -430,6 +431,10 @@ def run_ours(args):
         pass
     roofline = roofline_of(fam64, "fp64", peaks)
     roofline_mixed = roofline_of(fam_mx, "mixed", peaks)
+    # the level-0 FP32 smoother: the mixed form's bandwidth-bound kernel (the
+    # dominant family above is latency-bound work on the small levels)
+    roofline_mixed_l0 = roofline_of(fam_mx, "mixed", peaks, "vel_smooth_colour_l0") \
+        if any(f["name"] == "vel_smooth_colour_l0" for f in fam_mx) else None
 
     def fam_table(fams, total):
         return {f["name"]: {"launches": f["launches"], "ms": round(f["ms"], 4),
@@ -464,6 +469,7 @@ def run_ours(args):
         },
         "roofline": roofline,
         "roofline_mixed": roofline_mixed,
+        "roofline_mixed_l0": roofline_mixed_l0,
         "kernels_fp64": fam_table(fam64, sum(f["ms"] for f in fam64)),
         "kernels_mixed": fam_table(fam_mx, sum(f["ms"] for f in fam_mx)),
         "cpu_baseline": cpu,

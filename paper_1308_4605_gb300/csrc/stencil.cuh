@@ -13,6 +13,10 @@
 // (phi, rhs, residuals) are read with ordinary coherent loads, never through
 // the read-only path: the coarse-level kernel reads them again after a
 // __syncthreads() within the same launch.  Only coefficients use __ldg.
+// Every product that is added to something is written as an explicit fma,
+// so that the compiler's contraction choices cannot differ between the
+// kernels that inline these functions: the per-colour, two-colour and
+// coarse-level kernels then give bitwise the same results.
 #pragma once
 #include "internal.cuh"
 
@@ -151,7 +155,10 @@ __device__ __forceinline__ T visc_offdiag_acc(const Geom& g, const Coef<T>& C, c
         }
         N = fma(mhi, shi, N);
         N = fma(mlo, slo, N);
-        if (DIAG) dsum += (whi ? T(2) : T(1)) * mhi + (wlo ? T(2) : T(1)) * mlo;
+        if (DIAG) {   // explicit fmas: the same rounding in every kernel that inlines this
+            dsum = fma(whi ? T(2) : T(1), mhi, dsum);
+            dsum = fma(wlo ? T(2) : T(1), mlo, dsum);
+        }
         if (bulk) {   // B-divergence of the cells q (hi) and q - e_A (lo)
             N = fma(lh, pb(B, qe) - pb(B, q), N);
             N = fma(-ll, pb(B, r2) - pb(B, r0), N);
@@ -265,7 +272,7 @@ __device__ __forceinline__ T vel_res_point(int a, const Geom& g, const Coef<T>& 
     const T N = visc_offdiag_any<DIM, T, T, F32, BULK>(a, g, C, q, phi, dsum);
     const T ih2 = gih2<T>(g);
     const T diag = F32 ? fma(ih2, dsum, ld(C.alpha + f)) : ld(C.diag_u + f);
-    return fma(ih2, N, rhs[f]) - diag * phi[f];
+    return fma(-diag, phi[f], fma(ih2, N, rhs[f]));
 }
 
 // 6-point (2D) / 12-point (3D) restriction to the interior coarse A-face Q:
@@ -287,7 +294,7 @@ __device__ __forceinline__ T vel_restrict_point(const Geom& gf, const int Q[3],
                 q[A] = step(gf, A, q[A], s);
                 q[TR::b0] += t0;
                 if (TR::n == 2) q[TR::b1] += t1;
-                acc += w * res[fidx(gf, A, q)];
+                acc = fma(w, res[fidx(gf, A, q)], acc);
             }
     }
     return acc;
@@ -380,7 +387,7 @@ __device__ __forceinline__ T cell_res_point(const Geom& g, const Coef<T>& C, con
     T bsum;
     const T N = poisson_offdiag_h2<DIM, T, T>(g, C, q, phi, bsum);
     const int c = cidx(g, q);
-    return rhs[c] - gih2<T>(g) * fma(-bsum, T(phi[c]), N);
+    return fma(-gih2<T>(g), fma(-bsum, T(phi[c]), N), rhs[c]);
 }
 
 template <int DIM, typename T>
