@@ -9,6 +9,13 @@
 // of stencil.cuh in the same stage order (nu pre-sweeps, residual,
 // restriction, recursion, prolongation, nu post-sweeps; ncoarse sweeps on the
 // coarsest level; zero initial guess on every level).
+//
+// When the work vectors of these levels (phi, rhs and residual of each) fit
+// in shared memory, the SMEM variant keeps them there: the kernel is a chain
+// of about a hundred dependent stages, and each stage then waits on shared-
+// memory instead of L2 latency.  Only the level's right-hand side is read
+// from, and its solution written to, global memory; coefficients stay in
+// global memory (read-only, cached).
 #include "stencil.cuh"
 
 namespace stk {
@@ -16,6 +23,19 @@ namespace {
 
 using namespace st;
 constexpr int CT = 1024;
+constexpr int CMAXL = 16;
+
+// shared-memory layout of the SMEM variant: level l's phi at off[l], its rhs
+// at off[l] + n_l and its residual at off[l] + 2 n_l (n_l = faces or cells)
+struct SmemLevels {
+    int off[CMAXL];
+    int n[CMAXL];
+};
+
+template <typename T, bool SMEM>
+struct LevelVecs {
+    T *phi, *rhs, *res;
+};
 
 template <int DIM, typename T, bool BULK>
 __device__ void c_vel_sweeps(const Geom& g, const Coef<T>& C, int nsweep, T* phi, const T* rhs) {
@@ -56,11 +76,31 @@ __device__ __forceinline__ void load_geom(Geom* dst, const Geom* src) {
     for (int i = threadIdx.x; i < (int)(sizeof(Geom) / sizeof(int)); i += CT) d[i] = s[i];
 }
 
-template <int DIM, typename T, bool BULK>
+template <int DIM, typename T, bool BULK, bool SMEM>
 __global__ void __launch_bounds__(CT) k_coarse_vel(const CLevel<T>* __restrict__ Ls, int nlev,
                                                    const T* rhs0, T* phi0, int nu, int ncoarse) {
     pdl_entry();
     __shared__ Geom gsh[2];
+    __shared__ SmemLevels sl;
+    extern __shared__ __align__(16) unsigned char c_smem[];
+    T* sm = reinterpret_cast<T*>(c_smem);
+    if (SMEM) {
+        if (threadIdx.x == 0) {
+            int cur = 0;
+            for (int l = 0; l < nlev; ++l) {
+                sl.off[l] = cur;
+                sl.n[l] = Ls[l].g.nvel;
+                cur += 3 * sl.n[l];
+            }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < sl.n[0]; t += CT) sm[sl.n[0] + t] = rhs0[t];
+    }
+    auto PHI = [&](int l) -> T* { return SMEM ? sm + sl.off[l] : (l == 0 ? phi0 : Ls[l].phi_u); };
+    auto RHS = [&](int l) -> T* {
+        return SMEM ? sm + sl.off[l] + sl.n[l] : (l == 0 ? const_cast<T*>(rhs0) : Ls[l].rhs_u);
+    };
+    auto RES = [&](int l) -> T* { return SMEM ? sm + sl.off[l] + 2 * sl.n[l] : Ls[l].res_u; };
     // down: pre-smoothing, residual, restriction
     for (int l = 0; l < nlev; ++l) {
         load_geom(&gsh[0], &Ls[l].g);
@@ -68,8 +108,8 @@ __global__ void __launch_bounds__(CT) k_coarse_vel(const CLevel<T>* __restrict__
         __syncthreads();
         const Geom& g = gsh[0];
         const Coef<T> C = Ls[l].C;
-        T* phi = l == 0 ? phi0 : Ls[l].phi_u;
-        const T* rhs = l == 0 ? rhs0 : Ls[l].rhs_u;
+        T* phi = PHI(l);
+        const T* rhs = RHS(l);
         for (int t = threadIdx.x; t < g.nvel; t += CT) phi[t] = T(0);
         __syncthreads();
         if (l + 1 == nlev) {
@@ -77,7 +117,7 @@ __global__ void __launch_bounds__(CT) k_coarse_vel(const CLevel<T>* __restrict__
             break;
         }
         c_vel_sweeps<DIM, T, BULK>(g, C, nu, phi, rhs);
-        T* res = Ls[l].res_u;
+        T* res = RES(l);
         for (int t = threadIdx.x; t < g.nvel; t += CT) {
             int a = 0;
             while (a + 1 < DIM && t >= g.foff[a + 1]) ++a;
@@ -87,7 +127,7 @@ __global__ void __launch_bounds__(CT) k_coarse_vel(const CLevel<T>* __restrict__
         }
         __syncthreads();
         const Geom& gc = gsh[1];
-        T* rc = Ls[l + 1].rhs_u;
+        T* rc = RHS(l + 1);
         for (int t = threadIdx.x; t < gc.nvel; t += CT) {
             int a = 0;
             while (a + 1 < DIM && t >= gc.foff[a + 1]) ++a;
@@ -111,9 +151,9 @@ __global__ void __launch_bounds__(CT) k_coarse_vel(const CLevel<T>* __restrict__
         const Geom& g = gsh[0];
         const Geom& gc = gsh[1];
         const Coef<T> C = Ls[l].C;
-        T* phi = l == 0 ? phi0 : Ls[l].phi_u;
-        const T* rhs = l == 0 ? rhs0 : Ls[l].rhs_u;
-        const T* pc = Ls[l + 1].phi_u;
+        T* phi = PHI(l);
+        const T* rhs = RHS(l);
+        const T* pc = PHI(l + 1);
         for (int t = threadIdx.x; t < g.nvel; t += CT) {
             int a = 0;
             while (a + 1 < DIM && t >= g.foff[a + 1]) ++a;
@@ -129,21 +169,45 @@ __global__ void __launch_bounds__(CT) k_coarse_vel(const CLevel<T>* __restrict__
         __syncthreads();
         c_vel_sweeps<DIM, T, BULK>(g, C, nu, phi, rhs);
     }
+    if (SMEM) {   // the solution of the first level back to global memory
+        __syncthreads();
+        for (int t = threadIdx.x; t < sl.n[0]; t += CT) phi0[t] = sm[t];
+    }
 }
 
-template <int DIM, typename T>
+template <int DIM, typename T, bool SMEM>
 __global__ void __launch_bounds__(CT) k_coarse_cell(const CLevel<T>* __restrict__ Ls, int nlev,
                                                     const T* rhs0, T* phi0, int nu, int ncoarse) {
     pdl_entry();
     __shared__ Geom gsh[2];
+    __shared__ SmemLevels sl;
+    extern __shared__ __align__(16) unsigned char c_smem[];
+    T* sm = reinterpret_cast<T*>(c_smem);
+    if (SMEM) {
+        if (threadIdx.x == 0) {
+            int cur = 0;
+            for (int l = 0; l < nlev; ++l) {
+                sl.off[l] = cur;
+                sl.n[l] = Ls[l].g.ncell;
+                cur += 3 * sl.n[l];
+            }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < sl.n[0]; t += CT) sm[sl.n[0] + t] = rhs0[t];
+    }
+    auto PHI = [&](int l) -> T* { return SMEM ? sm + sl.off[l] : (l == 0 ? phi0 : Ls[l].phi_p); };
+    auto RHS = [&](int l) -> T* {
+        return SMEM ? sm + sl.off[l] + sl.n[l] : (l == 0 ? const_cast<T*>(rhs0) : Ls[l].rhs_p);
+    };
+    auto RES = [&](int l) -> T* { return SMEM ? sm + sl.off[l] + 2 * sl.n[l] : Ls[l].res_p; };
     for (int l = 0; l < nlev; ++l) {
         load_geom(&gsh[0], &Ls[l].g);
         if (l + 1 < nlev) load_geom(&gsh[1], &Ls[l + 1].g);
         __syncthreads();
         const Geom& g = gsh[0];
         const Coef<T> C = Ls[l].C;
-        T* phi = l == 0 ? phi0 : Ls[l].phi_p;
-        const T* rhs = l == 0 ? rhs0 : Ls[l].rhs_p;
+        T* phi = PHI(l);
+        const T* rhs = RHS(l);
         for (int t = threadIdx.x; t < g.ncell; t += CT) phi[t] = T(0);
         __syncthreads();
         if (l + 1 == nlev) {
@@ -151,7 +215,7 @@ __global__ void __launch_bounds__(CT) k_coarse_cell(const CLevel<T>* __restrict_
             break;
         }
         c_cell_sweeps<DIM, T>(g, C, nu, phi, rhs);
-        T* res = Ls[l].res_p;
+        T* res = RES(l);
         for (int t = threadIdx.x; t < g.ncell; t += CT) {
             int q[3];
             decode_cell(g, t, q);
@@ -159,7 +223,7 @@ __global__ void __launch_bounds__(CT) k_coarse_cell(const CLevel<T>* __restrict_
         }
         __syncthreads();
         const Geom& gc = gsh[1];
-        T* rc = Ls[l + 1].rhs_p;
+        T* rc = RHS(l + 1);
         for (int t = threadIdx.x; t < gc.ncell; t += CT) {
             int Q[3];
             decode_cell(gc, t, Q);
@@ -174,9 +238,9 @@ __global__ void __launch_bounds__(CT) k_coarse_cell(const CLevel<T>* __restrict_
         const Geom& g = gsh[0];
         const Geom& gc = gsh[1];
         const Coef<T> C = Ls[l].C;
-        T* phi = l == 0 ? phi0 : Ls[l].phi_p;
-        const T* rhs = l == 0 ? rhs0 : Ls[l].rhs_p;
-        const T* pc = Ls[l + 1].phi_p;
+        T* phi = PHI(l);
+        const T* rhs = RHS(l);
+        const T* pc = PHI(l + 1);
         for (int t = threadIdx.x; t < g.ncell; t += CT) {
             int q[3];
             decode_cell(g, t, q);
@@ -186,31 +250,86 @@ __global__ void __launch_bounds__(CT) k_coarse_cell(const CLevel<T>* __restrict_
         __syncthreads();
         c_cell_sweeps<DIM, T>(g, C, nu, phi, rhs);
     }
+    if (SMEM) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < sl.n[0]; t += CT) phi0[t] = sm[t];
+    }
 }
 
 }  // namespace
 
+// dynamic shared memory the SMEM variants may use (set on every kernel by
+// prepare_coarse_kernels; the static Geom copies and layout need ~2 KB more)
+constexpr size_t COARSE_SMEM_MAX = COARSE_SMEM_LIMIT;
+
+template <typename K>
+void set_smem_attr(K kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)COARSE_SMEM_MAX);
+}
+
 template <typename T>
 void launch_coarse_vcycle_vel(int dim, const CLevel<T>* L, int nlev, const T* rhs, T* phi, int nu,
-                              int ncoarse, bool bulk, cudaStream_t s) {
-    if (dim == 2) launch_pdl(bulk ? k_coarse_vel<2, T, true> : k_coarse_vel<2, T, false>, dim3(1), dim3(CT), s, L, nlev, rhs, phi, nu, ncoarse);
-    else launch_pdl(bulk ? k_coarse_vel<3, T, true> : k_coarse_vel<3, T, false>, dim3(1), dim3(CT), s, L, nlev, rhs, phi, nu, ncoarse);
+                              int ncoarse, bool bulk, size_t smem, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1);
+    cfg.blockDim = dim3(CT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const bool sm = smem > 0 && smem <= COARSE_SMEM_MAX;
+    if (!sm) cfg.dynamicSmemBytes = 0;
+#define STK_CV(D, B) (sm ? k_coarse_vel<D, T, B, true> : k_coarse_vel<D, T, B, false>)
+    auto kern = dim == 2 ? (bulk ? STK_CV(2, true) : STK_CV(2, false))
+                         : (bulk ? STK_CV(3, true) : STK_CV(3, false));
+#undef STK_CV
+    cudaLaunchKernelEx(&cfg, kern, L, nlev, rhs, phi, nu, ncoarse);
 }
 
 template <typename T>
 void launch_coarse_vcycle_cell(int dim, const CLevel<T>* L, int nlev, const T* rhs, T* phi, int nu,
-                               int ncoarse, cudaStream_t s) {
-    if (dim == 2) launch_pdl(k_coarse_cell<2, T>, dim3(1), dim3(CT), s, L, nlev, rhs, phi, nu, ncoarse);
-    else launch_pdl(k_coarse_cell<3, T>, dim3(1), dim3(CT), s, L, nlev, rhs, phi, nu, ncoarse);
+                               int ncoarse, size_t smem, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1);
+    cfg.blockDim = dim3(CT);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const bool sm = smem > 0 && smem <= COARSE_SMEM_MAX;
+    cfg.dynamicSmemBytes = sm ? smem : 0;
+    auto kern = dim == 2 ? (sm ? k_coarse_cell<2, T, true> : k_coarse_cell<2, T, false>)
+                         : (sm ? k_coarse_cell<3, T, true> : k_coarse_cell<3, T, false>);
+    cudaLaunchKernelEx(&cfg, kern, L, nlev, rhs, phi, nu, ncoarse);
+}
+
+void prepare_coarse_kernels() {
+    set_smem_attr(k_coarse_vel<2, double, false, true>);
+    set_smem_attr(k_coarse_vel<3, double, false, true>);
+    set_smem_attr(k_coarse_vel<2, double, true, true>);
+    set_smem_attr(k_coarse_vel<3, double, true, true>);
+    set_smem_attr(k_coarse_vel<2, float, false, true>);
+    set_smem_attr(k_coarse_vel<3, float, false, true>);
+    set_smem_attr(k_coarse_vel<2, float, true, true>);
+    set_smem_attr(k_coarse_vel<3, float, true, true>);
+    set_smem_attr(k_coarse_cell<2, double, true>);
+    set_smem_attr(k_coarse_cell<3, double, true>);
+    set_smem_attr(k_coarse_cell<2, float, true>);
+    set_smem_attr(k_coarse_cell<3, float, true>);
 }
 
 template void launch_coarse_vcycle_vel<double>(int, const CLevel<double>*, int, const double*,
-                                               double*, int, int, bool, cudaStream_t);
+                                               double*, int, int, bool, size_t, cudaStream_t);
 template void launch_coarse_vcycle_vel<float>(int, const CLevel<float>*, int, const float*, float*,
-                                              int, int, bool, cudaStream_t);
+                                              int, int, bool, size_t, cudaStream_t);
 template void launch_coarse_vcycle_cell<double>(int, const CLevel<double>*, int, const double*,
-                                                double*, int, int, cudaStream_t);
+                                                double*, int, int, size_t, cudaStream_t);
 template void launch_coarse_vcycle_cell<float>(int, const CLevel<float>*, int, const float*,
-                                               float*, int, int, cudaStream_t);
+                                               float*, int, int, size_t, cudaStream_t);
 
 }  // namespace stk

@@ -188,10 +188,17 @@ constexpr int COARSE_MAX_CELLS_F32 = 4096;
 constexpr int COARSE_MAX_CELLS_F64 = 512;
 template <typename T>
 void launch_coarse_vcycle_vel(int dim, const CLevel<T>* L, int nlev, const T* rhs, T* phi, int nu,
-                              int ncoarse, bool bulk, cudaStream_t s);
+                              int ncoarse, bool bulk, size_t smem, cudaStream_t s);
 template <typename T>
 void launch_coarse_vcycle_cell(int dim, const CLevel<T>* L, int nlev, const T* rhs, T* phi, int nu,
-                               int ncoarse, cudaStream_t s);
+                               int ncoarse, size_t smem, cudaStream_t s);
+// Shared-memory budget of the coarse-level kernels: with smem > 0 (the bytes
+// of phi, rhs and residual of every level handled) and at most this many
+// bytes, the work vectors live in shared memory; 0 keeps them in global
+// memory.  prepare_coarse_kernels() raises the kernels' dynamic shared-memory
+// limit on the current device.
+constexpr size_t COARSE_SMEM_LIMIT = 220 * 1024;
+void prepare_coarse_kernels();
 
 // preconditioner algebra (precision T)
 template <typename T>  // bc = D u + bp
@@ -220,9 +227,9 @@ void launch_copy_sub_mean(int n, const T* in, T* out, double* sum, cudaStream_t 
 // h[i] = <w, V_i> for i <= j and h[j+1] = <w, w>;  V = array of j+1 device pointers
 void launch_multidot(int n, int j, const double* const* V, const double* w, double* scratch,
                      double* h, cudaStream_t s);
-// w -= sum_i h[i] V_i (i <= j), then out[0] = <w, w>
-void launch_update_norm(int n, int j, const double* const* V, const double* h, double* w,
-                        double* scratch, double* out, cudaStream_t s);
+// modified Gram-Schmidt step: w -= h[k] vk, then out[0] = <w, u> (u = null: <w, w>)
+void launch_mgs_step(int n, const double* vk, const double* u, const double* h, int k, double* w,
+                     double* scratch, double* out, cudaStream_t s);
 // x += sum_i y[i] V_i (i < k); V of precision TV
 template <typename TV>
 void launch_combine(int n, int k, const TV* const* V, const double* y, double* x, cudaStream_t s);

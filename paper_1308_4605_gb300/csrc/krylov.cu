@@ -1,6 +1,8 @@
-// Krylov vector kernels of the GMRES core (Sec. 3.2): classical Gram-Schmidt
-// projections (one multi-dot pass), the update w -= sum h_i v_i fused with
-// ||w||^2, the solution update x += sum y_i z_i and scalings.
+// Krylov vector kernels of the GMRES core (Sec. 3.2): modified Gram-Schmidt
+// steps (w -= h_k v_k fused with the next projection <w, v_{k+1}>, or with
+// ||w||^2 after the last one), classical multi-dot / update passes (norms,
+// and the projections of a vector on several others), the solution update
+// x += sum y_i z_i and scalings.
 //
 // These are streaming kernels over packed Stokes vectors of N doubles.  The
 // number of basis vectors is a template parameter (dispatched at run time),
@@ -94,35 +96,33 @@ __global__ void __launch_bounds__(KT) k_mdot(int n, PtrArr V, const double* __re
     block_sums<J + 2>(acc, part);
 }
 
-// w -= sum_{i <= J} h[i] V_i, then ||w||^2
-template <int J>
-__global__ void __launch_bounds__(KT) k_upd(int n, PtrArr V, const double* __restrict__ h,
-                                             double* __restrict__ w, double* __restrict__ part) {
+// One modified Gram-Schmidt step: w -= h[k] v_k, then the block partials
+// of <w, u> (u = v_{k+1}), or of <w, w> when u is null.
+__global__ void __launch_bounds__(KT) k_mgs_step(int n, const double* __restrict__ vk,
+                                                 const double* __restrict__ u,
+                                                 const double* __restrict__ h, int k,
+                                                 double* __restrict__ w, double* __restrict__ part) {
     pdl_entry();
-    double hh[J + 1];
-#pragma unroll
-    for (int i = 0; i <= J; ++i) hh[i] = h[i];
+    const double hk = h[k];
     double s[1] = {0.0};
     const int n2 = n >> 1;
     double2* w2 = reinterpret_cast<double2*>(w);
+    const double2* v2 = reinterpret_cast<const double2*>(vk);
+    const double2* u2 = reinterpret_cast<const double2*>(u);
     for (int t = blockIdx.x * KT + threadIdx.x; t < n2; t += KRY_BLOCKS * KT) {
         double2 a = w2[t];
-#pragma unroll
-        for (int i = 0; i <= J; ++i) {
-            const double2 v = reinterpret_cast<const double2*>(V.p[i])[t];
-            a.x = fma(-hh[i], v.x, a.x);
-            a.y = fma(-hh[i], v.y, a.y);
-        }
+        const double2 v = v2[t];
+        a.x = fma(-hk, v.x, a.x);
+        a.y = fma(-hk, v.y, a.y);
         w2[t] = a;
-        s[0] = fma(a.x, a.x, s[0]);
-        s[0] = fma(a.y, a.y, s[0]);
+        const double2 b = u ? u2[t] : a;
+        s[0] = fma(a.x, b.x, s[0]);
+        s[0] = fma(a.y, b.y, s[0]);
     }
     if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
-        double a = w[n - 1];
-#pragma unroll
-        for (int i = 0; i <= J; ++i) a = fma(-hh[i], static_cast<const double*>(V.p[i])[n - 1], a);
+        double a = fma(-hk, vk[n - 1], w[n - 1]);
         w[n - 1] = a;
-        s[0] = fma(a, a, s[0]);
+        s[0] = fma(a, u ? u[n - 1] : a, s[0]);
     }
     block_sums<1>(s, part);
 }
@@ -192,18 +192,6 @@ void launch_multidot(int n, int j, const double* const* V, const double* w, doub
     launch_pdl(k_final_multi, dim3(j + 2), dim3(KT), s, scratch, h);
 }
 
-void launch_update_norm(int n, int j, const double* const* V, const double* h, double* w,
-                        double* scratch, double* out, cudaStream_t s) {
-    PtrArr pa = pack(reinterpret_cast<const void* const*>(V), j + 1);
-    switch (j) {
-#define X(J) case J: launch_pdl(k_upd<J>, dim3(KRY_BLOCKS), dim3(KT), s, n, pa, h, w, scratch); break;
-    STK_J_CASES(X)
-#undef X
-    default: return;
-    }
-    launch_pdl(k_final_multi, dim3(1), dim3(KT), s, scratch, out);
-}
-
 template <typename TV>
 void launch_combine(int n, int k, const TV* const* V, const double* y, double* x, cudaStream_t s) {
     PtrArr pa = pack(reinterpret_cast<const void* const*>(V), k);
@@ -213,6 +201,12 @@ void launch_combine(int n, int k, const TV* const* V, const double* y, double* x
 #undef X
     default: return;
     }
+}
+
+void launch_mgs_step(int n, const double* vk, const double* u, const double* h, int k, double* w,
+                     double* scratch, double* out, cudaStream_t s) {
+    launch_pdl(k_mgs_step, dim3(KRY_BLOCKS), dim3(KT), s, n, vk, u, h, k, w, scratch);
+    launch_pdl(k_final_multi, dim3(1), dim3(KT), s, scratch, out);
 }
 
 void launch_scale_inv_sqrt(int n, double* x, const double* nrm2, cudaStream_t s) {

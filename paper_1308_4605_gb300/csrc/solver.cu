@@ -299,6 +299,18 @@ template <typename T> PBuf<T>& pbuf_of(stk_handle* h);
 template <> PBuf<double>& pbuf_of<double>(stk_handle* h) { return h->pd; }
 template <> PBuf<float>& pbuf_of<float>(stk_handle* h) { return h->pf; }
 
+// Bytes of phi, rhs and residual of levels l.. (faces or cells) if they fit
+// the coarse kernel's shared-memory budget, else 0 (global-memory variant).
+template <typename T>
+size_t coarse_smem(const stk_handle* h, int l, bool vel) {
+    const int nl = (int)h->lev.size();
+    if (nl - l > 16) return 0;
+    size_t b = 0;
+    for (int k = l; k < nl; ++k)
+        b += 3 * sizeof(T) * (size_t)(vel ? h->lev[k].g.nvel : h->lev[k].g.ncell);
+    return b <= COARSE_SMEM_LIMIT ? b : 0;
+}
+
 struct MGParams {
     int nu = 2;
     int ncoarse = 8;
@@ -394,7 +406,7 @@ void vcycle_vel(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp, 
     if (l >= lcoarse_of<T>(h)) {   // this level and all coarser ones in one launch
         Scope sc(h, PF_COARSE, 0.0, s);
         launch_coarse_vcycle_vel<T>(L.g.dim, clev_of<T>(h) + l, (int)h->lev.size() - l, rhs, phi,
-                                    mp.nu, mp.ncoarse, h->bulk, s);
+                                    mp.nu, mp.ncoarse, h->bulk, coarse_smem<T>(h, l, true), s);
         return;
     }
     launch_zero<T>(L.g.nvel, phi, s);
@@ -429,7 +441,7 @@ void vcycle_cell(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp,
     if (l >= lcoarse_of<T>(h)) {
         Scope sc(h, PF_COARSE, 0.0, s);
         launch_coarse_vcycle_cell<T>(L.g.dim, clev_of<T>(h) + l, (int)h->lev.size() - l, rhs, phi,
-                                     mp.nu, mp.ncoarse, s);
+                                     mp.nu, mp.ncoarse, coarse_smem<T>(h, l, false), s);
         return;
     }
     launch_zero<T>(L.g.ncell, phi, s);
@@ -719,28 +731,31 @@ struct Arnoldi {
 };
 
 // ---------------------------------------------------------------- GMRES core
-// Arnoldi step pieces.  w = V[j+1] (unnormalised) is orthogonalised against
-// V[0..j] by classical Gram-Schmidt: one multi-dot pass (which also gives
-// ||w||^2 before) and one update pass (which gives ||w||^2 after); when the
-// norm falls below 1/sqrt(2) of its start a second pass re-orthogonalises.
-// The projections and norms are staged to pinned host memory.
-constexpr int HP_H = 0, HP_AFTER = 40, HP_NRM = 41, HP_H2 = 64, HP_Y = 128, HP_THETA = 250;
+// Pinned host staging slots: the Arnoldi column, ||w||^2 after the
+// orthogonalisation, ||b|| or ||r||, the least-squares solution, theta.
+constexpr int HP_H = 0, HP_AFTER = 40, HP_NRM = 41, HP_Y = 128, HP_THETA = 250;
 
-void orth_enqueue(stk_handle* h, int j, int pass, cudaStream_t s) {
+// Orthogonalise w = V[j+1] against V[0..j] by modified Gram-Schmidt (the
+// Arnoldi process of Sec. 3.2): h_0 = <w, v_0>; for k = 0..j: w -= h_k v_k
+// fused with h_{k+1} = <w, v_{k+1}> (the last step forms ||w||^2 instead).
+// Every coefficient stays on the device between steps; h_0..h_j and ||w||^2
+// are copied to the host at the end.
+void orth_enqueue(stk_handle* h, int j, cudaStream_t s) {
     const int n = nstokes(h);
     double* w = h->V[j + 1];
-    std::vector<const double*> Vp(h->V.begin(), h->V.begin() + j + 1);
     double* hd = h->dsc + DS_H;
     {
-        Scope sc(h, PF_MDOT, 8.0 * n * (j + 2), s, 2);
-        launch_multidot(n, j, Vp.data(), w, h->red, hd, s);
+        Scope sc(h, PF_MDOT, 16.0 * n, s, 2);
+        const double* v0 = h->V[0];
+        launch_multidot(n, 0, &v0, w, h->red, hd, s);
     }
-    {
-        Scope sc(h, PF_UPD, 8.0 * n * (j + 3), s, 2);
-        launch_update_norm(n, j, Vp.data(), hd, w, h->red, h->dsc + DS_N2, s);
+    for (int k = 0; k <= j; ++k) {
+        const bool last = k == j;
+        Scope sc(h, PF_UPD, 8.0 * n * (last ? 3 : 4), s, 2);
+        launch_mgs_step(n, h->V[k], last ? nullptr : h->V[k + 1], hd, k, w, h->red,
+                        last ? h->dsc + DS_N2 : hd + k + 1, s);
     }
-    cudaMemcpyAsync(h->hpin + (pass ? HP_H2 : HP_H), hd, sizeof(double) * (j + 2),
-                    cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(h->hpin + HP_H, hd, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(h->hpin + HP_AFTER, h->dsc + DS_N2, sizeof(double), cudaMemcpyDeviceToHost, s);
 }
 
@@ -763,7 +778,6 @@ struct Inst {
     std::vector<double> hcol, y;
     Arnoldi ar{1};
     int k = 0;
-    bool reorth = false;
 };
 
 int sync_all(std::vector<Inst*>& v) {
@@ -917,30 +931,18 @@ void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm) {
                     if ((rc = run_precond<double>(h, prm.precond, h->tmp, h->V[j + 1], mp, it->s))) { finish(it, rc); continue; }
                 }
                 it->info.scalar_vcycles += scalar_vcycles(h, prm.precond, mp);
-                orth_enqueue(h, j, 0, it->s);
+                orth_enqueue(h, j, it->s);
             }
             sync_all(step);
-            bool any_reorth = false;
             for (Inst* it : step) {
                 if (it->done) continue;
                 const double* hp = it->h->hpin;
-                for (int i = 0; i <= j; ++i) it->hcol[i] = hp[HP_H + i];
-                const double before = hp[HP_H + j + 1], after = hp[HP_AFTER];
-                if (!(std::isfinite(after) && std::isfinite(before))) {
-                    finish(it, fail(it->h, STK_ERR_NONFINITE, "non-finite value in the Arnoldi process"));
-                    continue;
+                bool finite = std::isfinite(hp[HP_AFTER]);
+                for (int i = 0; i <= j; ++i) {
+                    it->hcol[i] = hp[HP_H + i];
+                    finite = finite && std::isfinite(it->hcol[i]);
                 }
-                it->reorth = after < 0.5 * before;
-                if (it->reorth) {
-                    orth_enqueue(it->h, j, 1, it->s);
-                    any_reorth = true;
-                }
-            }
-            if (any_reorth) {
-                sync_all(step);
-                for (Inst* it : step)
-                    if (!it->done && it->reorth)
-                        for (int i = 0; i <= j; ++i) it->hcol[i] += it->h->hpin[HP_H2 + i];
+                if (!finite) finish(it, fail(it->h, STK_ERR_NONFINITE, "non-finite value in the Arnoldi process"));
             }
             for (Inst* it : step) {
                 if (it->done) continue;
@@ -1192,6 +1194,8 @@ int stk_create(int dim, const int* n, double hh, const int* bc, stk_handle** out
         CKC(dalloc(h, &h->cld, nl));
         CKC(dalloc(h, &h->clf, nl));
         CKC(upload_clevels(h));
+        prepare_coarse_kernels();
+        CKC(cudaGetLastError());
     }
 #undef CKC
     *out = h;
