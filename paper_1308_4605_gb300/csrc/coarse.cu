@@ -123,7 +123,9 @@ __global__ void __launch_bounds__(CT) k_coarse_vel(const CLevel<T>* __restrict__
             while (a + 1 < DIM && t >= g.foff[a + 1]) ++a;
             int q[3];
             decode_face(g, a, t - g.foff[a], q);
-            res[t] = wall_face(g, a, q) ? T(0) : vel_res_point<DIM, T, BULK>(a, g, C, q, phi, rhs);
+            // the black faces of the last component were just solved: zero residual
+            const bool solved = nu > 0 && a == DIM - 1 && ((q[0] + q[1] + q[2]) & 1);
+            res[t] = (wall_face(g, a, q) || solved) ? T(0) : vel_res_point<DIM, T, BULK>(a, g, C, q, phi, rhs);
         }
         __syncthreads();
         const Geom& gc = gsh[1];
@@ -219,7 +221,7 @@ __global__ void __launch_bounds__(CT) k_coarse_cell(const CLevel<T>* __restrict_
         for (int t = threadIdx.x; t < g.ncell; t += CT) {
             int q[3];
             decode_cell(g, t, q);
-            res[t] = cell_res_point<DIM, T>(g, C, q, phi, rhs);
+            res[t] = (nu > 0 && ((q[0] + q[1] + q[2]) & 1)) ? T(0) : cell_res_point<DIM, T>(g, C, q, phi, rhs);
         }
         __syncthreads();
         const Geom& gc = gsh[1];

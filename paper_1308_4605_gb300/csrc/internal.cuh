@@ -79,7 +79,7 @@ template <typename T>
 struct Coef {
     T* alpha;
     T* beta;
-    T* mu_c;
+    T* mu2_c;    // 2 mu at cells: the factor of the normal stresses 2 mu du_a/dx_a
     T* mu_e[3];
     T* invd_u;
     T* invd_p;
@@ -147,7 +147,7 @@ void launch_vel_gs_colour(const Geom& g, Coef<T> C, int comp, int parity, T* phi
                           cudaStream_t s, int tpb = 256);   // tpb <= 512
 template <typename T>
 void launch_vel_residual(const Geom& g, Coef<T> C, const T* phi, const T* rhs, T* res,
-                         cudaStream_t s);
+                         cudaStream_t s, bool after_sweep = false);
 template <typename T>
 void launch_vel_restrict(const Geom& gf, const T* res, const Geom& gc, T* rhs_c, cudaStream_t s);
 template <typename T>
@@ -166,7 +166,7 @@ void launch_cell_gs_colour(const Geom& g, Coef<T> C, int parity, T* phi, const T
                            cudaStream_t s, int tpb = 256);  // tpb <= 512
 template <typename T>
 void launch_cell_residual(const Geom& g, Coef<T> C, const T* phi, const T* rhs, T* res,
-                          cudaStream_t s);
+                          cudaStream_t s, bool after_sweep = false);
 template <typename T>
 void launch_cell_restrict(const Geom& gf, const T* res, const Geom& gc, T* rhs_c, cudaStream_t s);
 template <typename T>
@@ -208,8 +208,8 @@ void launch_sub_grad(const Geom& g, const T* beta, const T* u, const T* p, T* ou
 template <typename T>  // out = b - G p - A u
 void launch_vel_correction_rhs(const Geom& g, Coef<T> C, const T* b, const T* p, const T* u,
                                T* out, cudaStream_t s);
-template <typename T>  // xp = theta phi - (2 mu + lam) bc  (phi, lam may be null)
-void launch_schur_combine(int n, const double* theta, const T* phi, const T* mu, const T* lam,
+template <typename T>  // xp = theta phi - (mu2 + lam) bc, mu2 = 2 mu  (phi, lam may be null)
+void launch_schur_combine(int n, const double* theta, const T* phi, const T* mu2, const T* lam,
                           const T* bc, T* xp,
                           cudaStream_t s);
 

@@ -218,6 +218,13 @@ __global__ void k_inverse_diagonals(Geom g, Coef<double> C, Segs sg) {
     if (C.diag_u) C.diag_u[f] = d;
 }
 
+// 2 mu at cells (the coefficient arrays hold the doubled viscosity)
+__global__ void k_twice(int n, const double* __restrict__ mu, double* __restrict__ mu2) {
+    pdl_entry();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) mu2[t] = 2.0 * mu[t];
+}
+
 // bulk term of the stress at cells: lam = gamma - 2/3 mu (Sec. 2)
 __global__ void k_bulk_lambda(int n, const double* __restrict__ gamma, const double* __restrict__ mu,
                               double* __restrict__ lam) {
@@ -289,10 +296,14 @@ __global__ void __launch_bounds__(512) k_vel_gs(Geom g, Coef<T> C, int parity, T
     vel_gs_point<DIM, A, T, BULK>(g, C, q, phi, rhs);
 }
 
+// Residual rhs - A phi.  zl >= 0: the sweeps just ended with the black
+// faces of component zl, whose equations they solved exactly with every
+// neighbour final, so their residual is zero (up to rounding) and is set so.
 template <int DIM, typename T, bool BULK>
 __global__ void __launch_bounds__(TPB) k_vel_residual(Geom g, Coef<T> C, Segs sg,
                                                       const T* __restrict__ phi,
-                                                      const T* __restrict__ rhs, T* __restrict__ res) {
+                                                      const T* __restrict__ rhs, T* __restrict__ res,
+                                                      int zl) {
     pdl_entry();
     int t;
     const int s = seg_of(sg, blockIdx.x, t);
@@ -300,7 +311,11 @@ __global__ void __launch_bounds__(TPB) k_vel_residual(Geom g, Coef<T> C, Segs sg
     int q[3];
     decode_face(g, s, t, q);
     const int f = g.foff[s] + t;
-    res[f] = wall_face(g, s, q) ? T(0) : vel_res_point<DIM, T, BULK>(s, g, C, q, phi, rhs);
+    if (wall_face(g, s, q) || (s == zl && ((q[0] + q[1] + q[2]) & 1))) {
+        res[f] = T(0);
+        return;
+    }
+    res[f] = vel_res_point<DIM, T, BULK>(s, g, C, q, phi, rhs);
 }
 
 template <int DIM, typename T>
@@ -352,15 +367,18 @@ __global__ void __launch_bounds__(512) k_cell_gs(Geom g, Coef<T> C, int parity, 
     cell_gs_point<DIM, T>(g, C, q, phi, rhs);
 }
 
+// Residual rhs - L_rho phi; zb: the sweeps just ended with the black cells,
+// whose residual is then zero (see k_vel_residual).
 template <int DIM, typename T>
 __global__ void __launch_bounds__(TPB) k_cell_residual(Geom g, Coef<T> C, const T* __restrict__ phi,
-                                                       const T* __restrict__ rhs, T* __restrict__ res) {
+                                                       const T* __restrict__ rhs, T* __restrict__ res,
+                                                       int zb) {
     pdl_entry();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.ncell) return;
     int q[3];
     decode_cell(g, t, q);
-    res[t] = cell_res_point<DIM, T>(g, C, q, phi, rhs);
+    res[t] = (zb && ((q[0] + q[1] + q[2]) & 1)) ? T(0) : cell_res_point<DIM, T>(g, C, q, phi, rhs);
 }
 
 template <int DIM, typename T>
@@ -448,12 +466,12 @@ __global__ void k_vel_correction_rhs(Geom g, Coef<T> C, Segs sg, const T* __rest
 
 template <typename T>
 __global__ void k_schur_combine(int n, const double* __restrict__ theta, const T* __restrict__ phi,
-                                const T* __restrict__ mu, const T* __restrict__ lam,
+                                const T* __restrict__ mu2, const T* __restrict__ lam,
                                 const T* __restrict__ bc, T* __restrict__ xp) {
     pdl_entry();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
-    T k = T(2) * mu[t];          // 2 mu, or gamma + 4/3 mu = 2 mu + lam (Eq. Schur_app_bulk)
+    T k = mu2[t];                // 2 mu, or gamma + 4/3 mu = 2 mu + lam (Eq. Schur_app_bulk)
     if (lam) k += lam[t];
     T v = -k * bc[t];
     if (phi) v += T(*theta) * phi[t];
@@ -691,7 +709,7 @@ inline int nblk(long long n) { return (int)((n + TPB - 1) / TPB); }
 void launch_fine_coefficients(const Geom& g, const double* rho, const double* mu, double theta,
                               Coef<double> C, cudaStream_t s) {
     launch_pdl(k_fine_faces, dim3(nblk(g.nvel)), dim3(TPB), s, g, rho, theta, C.alpha, C.beta);
-    cudaMemcpyAsync(C.mu_c, mu, sizeof(double) * g.ncell, cudaMemcpyDeviceToDevice, s);
+    launch_pdl(k_twice, dim3(nblk(g.ncell)), dim3(TPB), s, g.ncell, mu, C.mu2_c);
     for (int a = 0; a < g.dim; ++a)
         for (int b = a + 1; b < g.dim; ++b) {
             int p = a + b - 1;
@@ -702,8 +720,8 @@ void launch_fine_coefficients(const Geom& g, const double* rho, const double* mu
 void launch_coarsen_coefficients(const Geom& gf, Coef<double> Cf, const Geom& gc, Coef<double> Cc,
                                  cudaStream_t s) {
     launch_pdl(k_coarsen_faces, dim3(nblk(gc.nvel)), dim3(TPB), s, gf, gc, Cf.alpha, Cf.beta, Cc.alpha, Cc.beta);
-    launch_pdl(k_coarsen_cells, dim3(nblk(gc.ncell)), dim3(TPB), s, gf, gc, Cf.mu_c, Cc.mu_c);
-    if (Cf.lam_c && Cc.lam_c)   // bulk term: cell average, like mu_c
+    launch_pdl(k_coarsen_cells, dim3(nblk(gc.ncell)), dim3(TPB), s, gf, gc, Cf.mu2_c, Cc.mu2_c);
+    if (Cf.lam_c && Cc.lam_c)   // bulk term: cell average, like mu
         launch_pdl(k_coarsen_cells, dim3(nblk(gc.ncell)), dim3(TPB), s, gf, gc, Cf.lam_c, Cc.lam_c);
     for (int a = 0; a < gc.dim; ++a)
         for (int b = a + 1; b < gc.dim; ++b) {
@@ -733,7 +751,7 @@ void launch_convert_coefficients(const Geom& g, Coef<double> C, Coef<float> F, c
     // F.diag_u stays null: the FP32 kernels form the diagonal on the fly
     launch_convert(g.nvel, C.alpha, F.alpha, s);
     launch_convert(g.nvel, C.beta, F.beta, s);
-    launch_convert(g.ncell, C.mu_c, F.mu_c, s);
+    launch_convert(g.ncell, C.mu2_c, F.mu2_c, s);
     for (int p = 0; p < 3; ++p)
         if (g.esize[p] > 0 && C.mu_e[p]) launch_convert(g.esize[p], C.mu_e[p], F.mu_e[p], s);
     launch_convert(g.nvel, C.invd_u, F.invd_u, s);
@@ -777,11 +795,12 @@ void launch_vel_gs_colour(const Geom& g, Coef<T> C, int comp, int parity, T* phi
 
 template <typename T>
 void launch_vel_residual(const Geom& g, Coef<T> C, const T* phi, const T* rhs, T* res,
-                         cudaStream_t s) {
+                         cudaStream_t s, bool after_sweep) {
+    const int zl = after_sweep ? g.dim - 1 : -1;
     Segs sg = face_segs(g, false);
     const bool bk = C.lam_c != nullptr;
-    if (g.dim == 2) launch_pdl(bk ? k_vel_residual<2, T, true> : k_vel_residual<2, T, false>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, phi, rhs, res);
-    else launch_pdl(bk ? k_vel_residual<3, T, true> : k_vel_residual<3, T, false>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, phi, rhs, res);
+    if (g.dim == 2) launch_pdl(bk ? k_vel_residual<2, T, true> : k_vel_residual<2, T, false>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, phi, rhs, res, zl);
+    else launch_pdl(bk ? k_vel_residual<3, T, true> : k_vel_residual<3, T, false>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, phi, rhs, res, zl);
 }
 
 template <typename T>
@@ -809,9 +828,10 @@ void launch_cell_gs_colour(const Geom& g, Coef<T> C, int parity, T* phi, const T
 
 template <typename T>
 void launch_cell_residual(const Geom& g, Coef<T> C, const T* phi, const T* rhs, T* res,
-                          cudaStream_t s) {
-    if (g.dim == 2) launch_pdl(k_cell_residual<2, T>, dim3(nblk(g.ncell)), dim3(TPB), s, g, C, phi, rhs, res);
-    else launch_pdl(k_cell_residual<3, T>, dim3(nblk(g.ncell)), dim3(TPB), s, g, C, phi, rhs, res);
+                          cudaStream_t s, bool after_sweep) {
+    const int zb = after_sweep ? 1 : 0;
+    if (g.dim == 2) launch_pdl(k_cell_residual<2, T>, dim3(nblk(g.ncell)), dim3(TPB), s, g, C, phi, rhs, res, zb);
+    else launch_pdl(k_cell_residual<3, T>, dim3(nblk(g.ncell)), dim3(TPB), s, g, C, phi, rhs, res, zb);
 }
 
 template <typename T>
@@ -850,9 +870,9 @@ void launch_vel_correction_rhs(const Geom& g, Coef<T> C, const T* b, const T* p,
 }
 
 template <typename T>
-void launch_schur_combine(int n, const double* theta, const T* phi, const T* mu, const T* lam,
+void launch_schur_combine(int n, const double* theta, const T* phi, const T* mu2, const T* lam,
                           const T* bc, T* xp, cudaStream_t s) {
-    launch_pdl(k_schur_combine<T>, dim3(nblk(n)), dim3(TPB), s, n, theta, phi, mu, lam, bc, xp);
+    launch_pdl(k_schur_combine<T>, dim3(nblk(n)), dim3(TPB), s, n, theta, phi, mu2, lam, bc, xp);
 }
 
 template <typename T>
@@ -915,14 +935,14 @@ void launch_check_fields(int n, const double* rho, const double* mu, double* scr
     template void launch_vel_gs_colour<T>(const Geom&, Coef<T>, int, int, T*, const T*,          \
                                           cudaStream_t, int);                                      \
     template void launch_vel_residual<T>(const Geom&, Coef<T>, const T*, const T*, T*,           \
-                                         cudaStream_t);                                            \
+                                         cudaStream_t, bool);                                      \
     template void launch_vel_restrict<T>(const Geom&, const T*, const Geom&, T*, cudaStream_t);  \
     template void launch_vel_prolong_add<T>(const Geom&, const T*, const Geom&, T*,              \
                                             cudaStream_t);                                         \
     template void launch_cell_gs_colour<T>(const Geom&, Coef<T>, int, T*, const T*,              \
                                            cudaStream_t, int);                                     \
     template void launch_cell_residual<T>(const Geom&, Coef<T>, const T*, const T*, T*,          \
-                                          cudaStream_t);                                           \
+                                          cudaStream_t, bool);                                     \
     template void launch_cell_restrict<T>(const Geom&, const T*, const Geom&, T*, cudaStream_t); \
     template void launch_cell_prolong_add<T>(const Geom&, const T*, const Geom&, T*,             \
                                              cudaStream_t);                                        \

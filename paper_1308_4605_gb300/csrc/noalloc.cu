@@ -156,7 +156,7 @@ void na_vcycle(NaLevel* L, int nlev, int l, const double* rhs, double* phi, cuda
         return;
     }
     sweeps(nu);
-    stk::launch_cell_residual<double>(Lv.g, Lv.C, phi, rhs, Lv.res, s);
+    stk::launch_cell_residual<double>(Lv.g, Lv.C, phi, rhs, Lv.res, s, true);
     stk::launch_cell_restrict<double>(Lv.g, Lv.res, L[l + 1].g, L[l + 1].rhs, s);
     na_vcycle(L, nlev, l + 1, L[l + 1].rhs, L[l + 1].phi, s);
     stk::launch_cell_prolong_add<double>(L[l + 1].g, L[l + 1].phi, Lv.g, phi, s);

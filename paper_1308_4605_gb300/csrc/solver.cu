@@ -263,7 +263,7 @@ double bytes_vel_colour(const Geom& g, int a) {
     for (int b = 0; b < g.dim; ++b)
         if (b != a) e += g.esize[a + b - 1];
     // half of comp a: rhs, alpha, invd read and phi written; phi of all
-    // components, mu_c and the edge viscosities of comp a read
+    // components, mu2_c and the edge viscosities of comp a read
     return sizeof(T) * (2.0 * g.fsize[a] + g.nvel + g.ncell + e);
 }
 template <typename T>
@@ -340,7 +340,7 @@ double bytes_vel_pair(const Geom& g, int a) {
     for (int b = 0; b < g.dim; ++b)
         if (b != a) e += g.esize[a + b - 1];
     // comp a: rhs, alpha (or inverse diagonal) read and phi written; phi of
-    // all components, mu_c and the edge viscosities of comp a read
+    // all components, mu2_c and the edge viscosities of comp a read
     return sizeof(T) * (3.0 * g.fsize[a] + g.nvel + g.ncell + e);
 }
 
@@ -419,7 +419,7 @@ void vcycle_vel(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp, 
     vel_sweeps<T>(h, l, mp.nu, phi, rhs, s);
     {
         Scope sc(h, PF_VRES, bytes_vel_residual<T>(L.g), s);
-        launch_vel_residual<T>(L.g, coef_of<T>(L), phi, rhs, W.res_u, s);
+        launch_vel_residual<T>(L.g, coef_of<T>(L), phi, rhs, W.res_u, s, mp.nu > 0);
     }
     {
         Scope sc(h, PF_VRESTR, sizeof(T) * (L.g.nvel + Lc.g.nvel), s);
@@ -454,7 +454,7 @@ void vcycle_cell(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp,
     cell_sweeps<T>(h, l, mp.nu, phi, rhs, s);
     {
         Scope sc(h, PF_CRES, sizeof(T) * (3.0 * L.g.ncell + L.g.nvel), s);
-        launch_cell_residual<T>(L.g, coef_of<T>(L), phi, rhs, W.res_p, s);
+        launch_cell_residual<T>(L.g, coef_of<T>(L), phi, rhs, W.res_p, s, mp.nu > 0);
     }
     {
         Scope sc(h, PF_CRESTR, sizeof(T) * (L.g.ncell + Lc.g.ncell), s);
@@ -547,19 +547,19 @@ void apply_precond(stk_handle* h, int which, const T* b, T* x, const MGParams& m
             Scope sc(h, PF_ALG, sizeof(T) * (3.0 * g.nvel + g.ncell), s);
             launch_sub_grad<T>(g, C.beta, B.xs, W.phi_p, xu, s);
         }
-        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, h->dsc + DS_THETA, W.phi_p, C.mu_c, C.lam_c, B.bc, xp, s); }
+        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, h->dsc + DS_THETA, W.phi_p, C.mu2_c, C.lam_c, B.bc, xp, s); }
         break;
     }
     case STK_P2: {
         velocity_solve<T>(h, bu, xu, mp, s);
         { Scope sc(h, PF_ALG, alg_cell, s); launch_div_plus<T>(g, xu, bp, B.bc, s); }
         if (pois) poisson_solve<T>(h, B.bc, W.phi_p, mp, s);
-        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, h->dsc + DS_THETA, pois ? W.phi_p : nullptr, C.mu_c, C.lam_c, B.bc, xp, s); }
+        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, h->dsc + DS_THETA, pois ? W.phi_p : nullptr, C.mu2_c, C.lam_c, B.bc, xp, s); }
         break;
     }
     case STK_P3: {
         if (pois) poisson_solve<T>(h, bp, W.phi_p, mp, s);
-        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, h->dsc + DS_THETA, pois ? W.phi_p : nullptr, C.mu_c, C.lam_c, bp, xp, s); }
+        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, h->dsc + DS_THETA, pois ? W.phi_p : nullptr, C.mu2_c, C.lam_c, bp, xp, s); }
         {
             Scope sc(h, PF_ALG, sizeof(T) * (2.0 * g.nvel + g.ncell), s);
             launch_sub_grad<T>(g, (const T*)nullptr, bu, xp, B.tmpu, s);
@@ -570,14 +570,14 @@ void apply_precond(stk_handle* h, int which, const T* b, T* x, const MGParams& m
     case STK_P4: {
         velocity_solve<T>(h, bu, xu, mp, s);
         if (pois) poisson_solve<T>(h, bp, W.phi_p, mp, s);
-        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, h->dsc + DS_THETA, pois ? W.phi_p : nullptr, C.mu_c, C.lam_c, bp, xp, s); }
+        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, h->dsc + DS_THETA, pois ? W.phi_p : nullptr, C.mu2_c, C.lam_c, bp, xp, s); }
         break;
     }
     default: {  // STK_P5
         velocity_solve<T>(h, bu, B.xs, mp, s);
         { Scope sc(h, PF_ALG, alg_cell, s); launch_div_plus<T>(g, B.xs, bp, B.bc, s); }
         if (pois) poisson_solve<T>(h, B.bc, W.phi_p, mp, s);
-        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, h->dsc + DS_THETA, pois ? W.phi_p : nullptr, C.mu_c, C.lam_c, B.bc, xp, s); }
+        { Scope sc(h, PF_ALG, alg_cell, s); launch_schur_combine<T>(g.ncell, h->dsc + DS_THETA, pois ? W.phi_p : nullptr, C.mu2_c, C.lam_c, B.bc, xp, s); }
         {
             Scope sc(h, PF_ALG, bytes_vel_residual<T>(g), s);
             launch_vel_correction_rhs<T>(g, C, bu, xp, B.xs, B.tmpu, s);
@@ -1112,14 +1112,14 @@ int stk_create(int dim, const int* n, double hh, const int* bc, stk_handle** out
         const Geom& g = L.g;
         CKC(dalloc(h, &L.cd.alpha, g.nvel));
         CKC(dalloc(h, &L.cd.beta, g.nvel));
-        CKC(dalloc(h, &L.cd.mu_c, g.ncell));
+        CKC(dalloc(h, &L.cd.mu2_c, g.ncell));
         CKC(dalloc(h, &L.cd.invd_u, g.nvel));
         CKC(dalloc(h, &L.cd.invd_p, g.ncell));
         CKC(dalloc(h, &L.cd.diag_u, g.nvel));
         L.cf.diag_u = nullptr;
         CKC(dalloc(h, &L.cf.alpha, g.nvel));
         CKC(dalloc(h, &L.cf.beta, g.nvel));
-        CKC(dalloc(h, &L.cf.mu_c, g.ncell));
+        CKC(dalloc(h, &L.cf.mu2_c, g.ncell));
         CKC(dalloc(h, &L.cf.invd_u, g.nvel));
         CKC(dalloc(h, &L.cf.invd_p, g.ncell));
         for (int p = 0; p < 3; ++p) {
@@ -1676,7 +1676,7 @@ int stk_gradient(stk_handle* h, const double* const* u, const double* const* lam
     }
     {
         Scope sc(h, PF_ALG, 8.0 * (2.0 * g.nvel + 3.0 * g.ncell), s);
-        launch_gradient(g, h->lev[0].cd.mu_c, h->theta, h->bk, h->tmp, dL_dlogmu, dL_drho, s);
+        launch_gradient(g, h->mu0, h->theta, h->bk, h->tmp, dL_dlogmu, dL_drho, s);
     }
     CKL();
     return STK_OK;

@@ -114,12 +114,13 @@ __device__ __forceinline__ T visc_offdiag_acc(const Geom& g, const Coef<T>& C, c
     qm[A] = step(g, A, q[A], -1);
     const T pp = pa(qp);
     const T pm = pa(qm);
-    const T mh = ld(C.mu_c + cidx(g, q));
-    const T ml = ld(C.mu_c + cidx(g, qm));
+    // normal stresses: 2 mu of the two cells (stored doubled: scaling by two
+    // is exact, so this equals doubling mu pp + mu pm afterwards)
+    const T mh = ld(C.mu2_c + cidx(g, q));
+    const T ml = ld(C.mu2_c + cidx(g, qm));
     T N = mh * pp;
     N = fma(ml, pm, N);
-    N = N + N;
-    if (DIAG) dsum = T(2) * (mh + ml);
+    if (DIAG) dsum = mh + ml;
     constexpr bool bulk = BULK;   // a compile-time switch: the plain form issues no bulk work
     T lh = T(0), ll = T(0);
     if (bulk) {
