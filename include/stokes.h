@@ -254,7 +254,9 @@ int stk_solve_batched(int count, stk_handle* const* hs, const stk_solver_params*
  * red points of a one-point halo around its tile); finer levels launch once
  * per colour with `threads` threads per block (64, 128, 256 or 512).
  * 0 <= pair_level, coarse_level <= number of levels.  The arithmetic does
- * not depend on the schedule.  stk_autotune times one velocity + one
+ * not depend on the schedule, except that with coarse_level = 0 the finest
+ * level's FP64 residual is evaluated point by point instead of through the
+ * stresses of the grid kernels (equal up to rounding).  stk_autotune times one velocity + one
  * pressure V-cycle (as a captured graph) for every admissible schedule,
  * applies the fastest and returns it; stk_set_schedule applies a known one
  * (e.g. cached from an earlier run). */

@@ -135,6 +135,18 @@ void launch_inverse_diagonals(const Geom& g, Coef<double> C, cudaStream_t s);
 void launch_convert_coefficients(const Geom& g, Coef<double> C, Coef<float> Cf, cudaStream_t s);
 
 // y = M x (packed Stokes vectors); input precision TV, output double
+// The FP64 operator and the finest-level FP64 velocity residual evaluated
+// through stresses computed once per cell and edge (stress.cu); W holds the
+// scratch stress arrays of the finest level (cells: dim arrays of ncell;
+// edges: one array of esize[p] per pair p).
+struct StressWork {
+    double* tc[3];
+    double* te[3];
+};
+void launch_stokes_matvec_stress(const Geom& g, Coef<double> C, const StressWork& W, const double* x,
+                                 const double* b, double* y, cudaStream_t s);
+void launch_vel_residual_stress(const Geom& g, Coef<double> C, const StressWork& W, const double* phi,
+                                const double* rhs, double* res, bool after_sweep, cudaStream_t s);
 template <typename TV>
 void launch_stokes_matvec(const Geom& g, Coef<double> C, const TV* x, double* y, cudaStream_t s);
 // r = b - M x

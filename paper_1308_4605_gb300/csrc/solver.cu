@@ -89,6 +89,7 @@ struct stk_handle {
     int tpb_d = 256, tpb_f = 256;            // threads per block of the colour kernels
     int lpair_d = 0, lpair_f = 0;            // first level smoothed by the two-colour kernels
     bool bulk = false;                       // bulk-viscosity stress form on
+    StressWork sw{};                         // stress scratch of the finest level (FP64)
     double *gamma = nullptr, *rho0 = nullptr, *mu0 = nullptr;   // level-0 fields
     CLevel<double>* cld = nullptr;           // device copies of the level descriptors
     CLevel<float>* clf = nullptr;
@@ -274,6 +275,10 @@ template <typename T>
 double bytes_cell_colour(const Geom& g) {    // half: rhs, invd, write; phi, beta all
     return sizeof(T) * (1.5 * g.ncell + g.ncell + g.nvel);
 }
+// kernels of one stress-based operator or residual evaluation: cells, one
+// per edge family, faces
+int stress_kernels(const Geom& g) { return g.dim == 3 ? 5 : 3; }
+
 double bytes_matvec(const Geom& g, int in_size) {
     return in_size * double(g.nvel + g.ncell) + 8.0 * (2.0 * g.nvel + 2.0 * g.ncell + esum(g));
 }
@@ -418,8 +423,14 @@ void vcycle_vel(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp, 
     Work<T> Wc = work_of<T>(Lc);
     vel_sweeps<T>(h, l, mp.nu, phi, rhs, s);
     {
-        Scope sc(h, PF_VRES, bytes_vel_residual<T>(L.g), s);
-        launch_vel_residual<T>(L.g, coef_of<T>(L), phi, rhs, W.res_u, s, mp.nu > 0);
+        const bool st = sizeof(T) == 8 && l == 0;
+        Scope sc(h, PF_VRES, bytes_vel_residual<T>(L.g), s, st ? stress_kernels(L.g) : 1);
+        if (st)   // FP64 finest level: through the stresses
+            launch_vel_residual_stress(L.g, h->lev[0].cd, h->sw, reinterpret_cast<const double*>(phi),
+                                       reinterpret_cast<const double*>(rhs),
+                                       reinterpret_cast<double*>(W.res_u), mp.nu > 0, s);
+        else
+            launch_vel_residual<T>(L.g, coef_of<T>(L), phi, rhs, W.res_u, s, mp.nu > 0);
     }
     {
         Scope sc(h, PF_VRESTR, sizeof(T) * (L.g.nvel + Lc.g.nvel), s);
@@ -849,8 +860,8 @@ void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm) {
         for (Inst* it : act) {
             stk_handle* h = it->h;
             const Geom& g = h->lev[0].g;
-            Scope sc(h, PF_MATVEC, bytes_matvec(g, 8) + 8.0 * nstokes(h), it->s);
-            launch_stokes_residual(g, h->lev[0].cd, h->xk, h->bk, h->tmp, it->s);
+            Scope sc(h, PF_MATVEC, bytes_matvec(g, 8) + 8.0 * nstokes(h), it->s, stress_kernels(g));
+            launch_stokes_matvec_stress(g, h->lev[0].cd, h->sw, h->xk, h->bk, h->tmp, it->s);
             norm_enqueue(h, h->tmp, it->s);
         }
         sync_all(act);
@@ -921,12 +932,12 @@ void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm) {
                         Scope sc(h, PF_CONV, 12.0 * n, it->s);
                         launch_convert<float, double>(n, h->Z[j], h->tmp, it->s);
                     }
-                    Scope sc(h, PF_MATVEC, bytes_matvec(g, 8), it->s);
-                    launch_stokes_matvec<double>(g, h->lev[0].cd, h->tmp, h->V[j + 1], it->s);
+                    Scope sc(h, PF_MATVEC, bytes_matvec(g, 8), it->s, stress_kernels(g));
+                    launch_stokes_matvec_stress(g, h->lev[0].cd, h->sw, h->tmp, nullptr, h->V[j + 1], it->s);
                 } else {
                     {
-                        Scope sc(h, PF_MATVEC, bytes_matvec(g, 8), it->s);
-                        launch_stokes_matvec<double>(g, h->lev[0].cd, h->V[j], h->tmp, it->s);
+                        Scope sc(h, PF_MATVEC, bytes_matvec(g, 8), it->s, stress_kernels(g));
+                        launch_stokes_matvec_stress(g, h->lev[0].cd, h->sw, h->V[j], nullptr, h->tmp, it->s);
                     }
                     if ((rc = run_precond<double>(h, prm.precond, h->tmp, h->V[j + 1], mp, it->s))) { finish(it, rc); continue; }
                 }
@@ -1169,6 +1180,9 @@ int stk_create(int dim, const int* n, double hh, const int* bc, stk_handle** out
     CKC(dalloc(h, &h->xk, ns));
     CKC(dalloc(h, &h->tmp, ns));
     CKC(dalloc(h, &h->red, (size_t)RED_SCRATCH));
+    for (int a = 0; a < g0.dim; ++a) CKC(dalloc(h, &h->sw.tc[a], g0.ncell));
+    for (int p = 0; p < 3; ++p)
+        if (g0.esize[p] > 0) CKC(dalloc(h, &h->sw.te[p], g0.esize[p]));
     CKC(dalloc(h, &h->rho0, g0.ncell));
     CKC(dalloc(h, &h->mu0, g0.ncell));
     CKC(dalloc(h, &h->dsc, NDSC));
@@ -1304,8 +1318,8 @@ int stk_apply_operator(stk_handle* h, const double* const* x_u, const double* x_
     CK(cudaSetDevice(h->device));
     if ((rc = gather(h, x_u, x_p, h->xk, s))) return rc;
     {
-        Scope sc(h, PF_MATVEC, bytes_matvec(h->lev[0].g, 8), s);
-        launch_stokes_matvec<double>(h->lev[0].g, h->lev[0].cd, h->xk, h->tmp, s);
+        Scope sc(h, PF_MATVEC, bytes_matvec(h->lev[0].g, 8), s, stress_kernels(h->lev[0].g));
+        launch_stokes_matvec_stress(h->lev[0].g, h->lev[0].cd, h->sw, h->xk, nullptr, h->tmp, s);
     }
     CKL();
     return scatter(h, h->tmp, y_u, y_p, s);
@@ -1376,7 +1390,8 @@ int stk_subtract_boundary_terms(stk_handle* h, const double* const* u_wall,
     if (u_wall)
         for (int a = 0; a < g.dim; ++a)
             if (!g.per[a] && u_wall[a]) launch_copy_walls(g, a, u_wall[a], h->xk, s);
-    launch_stokes_matvec<double>(g, L.cd, h->xk, h->tmp, s);
+    launch_stokes_matvec_stress(g, L.cd, h->sw, h->xk, nullptr, h->tmp, s);
+    h->nkern += stress_kernels(g);
     // tangential velocities of no-slip walls
     if (u_tan)
         for (int d = 0; d < g.dim; ++d) {

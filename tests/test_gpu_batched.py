@@ -85,8 +85,9 @@ def test_batched_rejects_duplicate_handles(S):
 
 def test_schedules_change_timing_not_results(S, tmp_path):
     """Every multigrid schedule (coarse-kernel level, two-colour level, colour
-    block size) gives bitwise the same solution; the autotuner picks one and
-    caches it."""
+    block size) gives bitwise the same solution (FP64 with the whole V-cycle
+    in the coarse kernel: the same up to rounding); the autotuner picks one
+    and caches it."""
     from paper_1308_4605_gb300 import tuning
     pr = wl.config_c4_instance(5, 128)
     sv = S.StokesSolver(2, pr.n[:2], pr.bc[:4], pr.h)
@@ -104,6 +105,13 @@ def test_schedules_change_timing_not_results(S, tmp_path):
             assert info["converged"]
             if ref is None:
                 ref = (xu, xp, info["iterations"])
+            elif prec == 0 and lc == 0:
+                # the whole V-cycle in the single-block kernel evaluates the
+                # finest FP64 residual point by point instead of through the
+                # stresses: equal up to rounding
+                assert abs(info["iterations"] - ref[2]) <= 1
+                for a, b in zip(list(xu) + [xp], list(ref[0]) + [ref[1]]):
+                    assert float((a - b).abs().max()) <= 1e-9 * float(b.abs().max())
             else:
                 assert info["iterations"] == ref[2]
                 assert all(torch.equal(a, b) for a, b in zip(xu, ref[0])) and torch.equal(xp, ref[1])
