@@ -164,10 +164,10 @@ class ClockSampler:
 # ------------------------------------------------------------------ roofline
 FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (an FMA probe measured 1.20 on this machine)
 # FP64 instructions per FLOP of the level-0 velocity Gauss-Seidel point
-# (19 instructions, 25 FLOP, from ncu's SASS op counters): the FP64 pipe
+# (18 instructions, 24 FLOP, from ncu's SASS op counters): the FP64 pipe
 # issues one instruction (an FMA = 2 FLOP) per slot, so the kernel's share of
-# the pipe's issue rate is achieved FLOP/s x 19/25 / (peak FLOP/s / 2).
-FP64_INSTR_PER_FLOP = 19.0 / 25.0
+# the pipe's issue rate is achieved FLOP/s x 18/24 / (peak FLOP/s / 2).
+FP64_INSTR_PER_FLOP = 18.0 / 24.0
 
 
 def traffic_per_launch(family, form):

@@ -325,13 +325,13 @@ struct MGParams {
 
 // Floating-point operations of one Gauss-Seidel point update (adds + muls +
 // 2 x fmas), counted with ncu (sm__sass_thread_inst_executed_op_*) on the
-// 3D kernels: FP64 velocity 25, FP32 velocity 46 (the FP32 division is a
-// short FMA sequence), FP64 cell 15; the 2D velocity stencil has one
-// transverse axis instead of two (8 fewer FP64 operations).
+// 3D kernels: FP64 velocity 24 (18 instructions), FP32 velocity 44 (the FP32
+// division is a short FMA sequence), FP64 cell 15; the 2D velocity stencil
+// has one transverse axis instead of two (8 fewer operations).
 template <typename T>
 double flops_vel_point(int dim) {
-    if (sizeof(T) == 8) return dim == 3 ? 25.0 : 17.0;
-    return dim == 3 ? 46.0 : 38.0;
+    if (sizeof(T) == 8) return dim == 3 ? 24.0 : 16.0;
+    return dim == 3 ? 44.0 : 36.0;
 }
 double updated_faces(const Geom& g, int a) {   // unknown a-faces of one colour
     double n = double(g.fe[a][0]) * g.fe[a][1] * g.fe[a][2];

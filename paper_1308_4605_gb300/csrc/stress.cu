@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(ST) k_stress_edges(Geom g, Coef<double> Cf, co
     int q[3];
     unflat(t, g.ee[P], q);
     const double m = ld(Cf.mu_e[P] + t);
-    tau[t] = m == 0.0 ? 0.0 : m * (edge_diff<A, B>(g, q, x) + edge_diff<B, A>(g, q, x));
+    tau[t] = m * (edge_diff<A, B>(g, q, x) + edge_diff<B, A>(g, q, x));   // m = 0: zero
 }
 
 // Momentum row of the interior A-face q.  MODE 0: y = alpha u - L u / h^2 + G p
