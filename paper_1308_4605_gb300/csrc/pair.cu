@@ -55,11 +55,12 @@ k_vel_gs_pair(Geom g, Coef<T> C, const T* src, T* dst, const T* __restrict__ rhs
     const int ox = blockIdx.x * 2 * TXC - 1, oy = blockIdx.y * TY - 1;
     const int oz = DIM == 3 ? int(blockIdx.z) * TZ - 1 : 0;
     // components swept before A in this sweep are in dst, the others in src
-    auto pb = [&](int B, const int* r) { return T((B < A ? dst : src)[fidx(g, B, r)]); };
+    auto pb = [&](int B, int i) { return T((B < A ? dst : src)[i]); };
 
     // 1. red points of the haloed tile, from the input values
     {
-        auto pa = [&](const int* r) { return T(src[fidx(g, A, r)]); };
+        auto aidx = [&](const int* r) { return fidx(g, A, r); };
+        auto ga = [&](int i) { return T(src[i]); };
         for (int t = threadIdx.x; t < (TXC + 1) * WY * WZ; t += NT) {
             const int xr = t % (TXC + 1);
             const int rr = t / (TXC + 1);
@@ -80,7 +81,7 @@ k_vel_gs_pair(Geom g, Coef<T> C, const T* src, T* dst, const T* __restrict__ rhs
             T v = T(0);
             if (!wall_face(g, A, q)) {
                 T dsum;
-                const T N = visc_offdiag_acc<DIM, A, T, F32, BULK>(g, C, q, pa, pb, dsum);
+                const T N = visc_offdiag_acc<DIM, A, T, F32, BULK>(g, C, q, aidx, ga, pb, dsum);
                 const int f = fidx(g, A, q);
                 v = vel_gs_value<T>(g, C, f, N, dsum, rhs);
                 const bool inner = lx >= 1 && lx <= 2 * TXC && ux < e0 && ly >= 1 && ly <= TY &&
@@ -102,14 +103,16 @@ k_vel_gs_pair(Geom g, Coef<T> C, const T* src, T* dst, const T* __restrict__ rhs
     if (ux >= e0 || uy >= e1 || (DIM == 3 && uz >= e2)) return;
     const int q[3] = {ux, uy, DIM == 3 ? uz : 0};
     if (wall_face(g, A, q)) return;
-    auto pa = [&](const int* r) {
+    auto aidx = [&](const int* r) {
         const int sx = slot(r[0], ox, WX, e0);
         const int sy = slot(r[1], oy, WY, e1);
         const int sz = DIM == 3 ? slot(r[2], oz, WZ, e2) : 0;
-        return R[sz][sy][sx];
+        return (sz * WY + sy) * WX + sx;
     };
+    const T* Rf = &R[0][0][0];
+    auto ga = [&](int i) { return Rf[i]; };
     T dsum;
-    const T N = visc_offdiag_acc<DIM, A, T, F32, BULK>(g, C, q, pa, pb, dsum);
+    const T N = visc_offdiag_acc<DIM, A, T, F32, BULK>(g, C, q, aidx, ga, pb, dsum);
     const int f = fidx(g, A, q);
     dst[f] = vel_gs_value<T>(g, C, f, N, dsum, rhs);
 }

@@ -104,76 +104,163 @@ template <int A> struct Trans<3, A> {
 // lam times their divergence: N += lam_hi (phi_A[+a] + sum_B dphi_B|hi)
 // + lam_lo (phi_A[-a] - sum_B dphi_B|lo), dphi_B the B-face difference
 // across the cell, and dsum += lam_hi + lam_lo.
-template <int DIM, int A, typename T, bool DIAG, bool BULK, typename PA, typename PB>
-__device__ __forceinline__ T visc_offdiag_acc(const Geom& g, const Coef<T>& C, const int q[3],
-                                              const PA& pa, const PB& pb, T& dsum) {
-    // pa(r): phi_A at the A-face r; pb(B, r): phi_B at the B-face r
+// Where the stencil of the A-face q reads its values: indices of phi_A at
+// q +- e_A and at q +- e_B, of mu at the cells q and q - e_A, of mu_e on the
+// edges q and q + e_B, and of phi_B at the B-faces q, q - e_A, q + e_B and
+// q + e_B - e_A, for the transverse axes B in increasing order (slot j).
+// wlo / whi: q is next to a wall of axis B on the low / high side.
+struct Nbr {
+    int a_p, a_m, c_h, c_l;
+    int e_lo[2], e_hi[2], b_q[2], b_r0[2], b_qe[2], b_r2[2], a_bp[2], a_bm[2];
+    bool wlo[2], whi[2];
+};
+
+// transverse axis of slot j (increasing order)
+__host__ __device__ constexpr int trans_axis(int dim, int a, int j) {
+    return dim == 2 ? 1 - a : (j == 0 ? (a == 0 ? 1 : 0) : (a == 2 ? 1 : 2));
+}
+
+// Index table from linear strides: one base index per array and constant
+// offsets, with a branch-free correction on the faces next to a periodic
+// seam (equal to the coordinate form, whose stepping wraps there).
+template <int DIM, int A>
+__device__ __forceinline__ void nbr_lin(const Geom& g, const int q[3], Nbr& X) {
+    int kp[3], km[3];   // +1 / -1 steps in units of the stride: 1, or 1 - n across a seam
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        kp[d] = (g.per[d] && q[d] == g.n[d] - 1) ? 1 - g.n[d] : 1;
+        km[d] = (g.per[d] && q[d] == 0) ? 1 - g.n[d] : 1;
+    }
+    const int sA[3] = {1, g.fe[A][0], g.fe[A][0] * g.fe[A][1]};
+    const int f = fidx(g, A, q);
+    X.a_p = f + kp[A] * sA[A];
+    X.a_m = f - km[A] * sA[A];
+    const int sc[3] = {1, g.n[0], g.n[0] * g.n[1]};
+    X.c_h = cidx(g, q);
+    X.c_l = X.c_h - km[A] * sc[A];
+#pragma unroll
+    for (int j = 0; j < DIM - 1; ++j) {
+        const int B = trans_axis(DIM, A, j);
+        const int P = A + B - 1;
+        const int se[3] = {1, g.ee[P][0], g.ee[P][0] * g.ee[P][1]};
+        const int e = eidx(g, P, q);
+        X.e_lo[j] = e;
+        X.e_hi[j] = e + kp[B] * se[B];
+        const int sB[3] = {1, g.fe[B][0], g.fe[B][0] * g.fe[B][1]};
+        const int fb = fidx(g, B, q);
+        X.b_q[j] = fb;
+        X.b_r0[j] = fb - km[A] * sB[A];
+        X.b_qe[j] = fb + kp[B] * sB[B];
+        X.b_r2[j] = X.b_qe[j] - km[A] * sB[A];
+        X.a_bp[j] = f + kp[B] * sA[B];
+        X.a_bm[j] = f - km[B] * sA[B];
+        X.wlo[j] = !g.per[B] && q[B] == 0;
+        X.whi[j] = !g.per[B] && q[B] == g.n[B] - 1;
+    }
+}
+
+// Index table from coordinates; aidx(r) gives the index of phi_A at the
+// A-face r (a global index, or a shared-memory slot), B-faces are global.
+template <int DIM, int A, typename AI>
+__device__ __forceinline__ void nbr_coord(const Geom& g, const int q[3], const AI& aidx, Nbr& X) {
     int qp[3] = {q[0], q[1], q[2]};
     int qm[3] = {q[0], q[1], q[2]};
     qp[A] = step(g, A, q[A], 1);
     qm[A] = step(g, A, q[A], -1);
-    const T pp = pa(qp);
-    const T pm = pa(qm);
+    X.a_p = aidx(qp);
+    X.a_m = aidx(qm);
+    X.c_h = cidx(g, q);
+    X.c_l = cidx(g, qm);
+#pragma unroll
+    for (int j = 0; j < DIM - 1; ++j) {
+        const int B = trans_axis(DIM, A, j);
+        const int P = A + B - 1;
+        int qe[3] = {q[0], q[1], q[2]};
+        qe[B] = step(g, B, q[B], 1);
+        X.e_lo[j] = eidx(g, P, q);
+        X.e_hi[j] = eidx(g, P, qe);
+        int r0[3] = {q[0], q[1], q[2]};
+        r0[A] = qm[A];
+        int r2[3] = {qe[0], qe[1], qe[2]};
+        r2[A] = qm[A];
+        X.b_q[j] = fidx(g, B, q);
+        X.b_r0[j] = fidx(g, B, r0);
+        X.b_qe[j] = fidx(g, B, qe);
+        X.b_r2[j] = fidx(g, B, r2);
+        X.wlo[j] = !g.per[B] && q[B] == 0;
+        X.whi[j] = !g.per[B] && q[B] == g.n[B] - 1;
+        X.a_bp[j] = X.whi[j] ? 0 : aidx(qe);
+        int qb[3] = {q[0], q[1], q[2]};
+        qb[B] = step(g, B, q[B], -1);
+        X.a_bm[j] = X.wlo[j] ? 0 : aidx(qb);
+    }
+}
+
+// The arithmetic: ga(i) reads phi_A at index i, gb(B, i) phi_B at index i.
+template <int DIM, int A, typename T, bool DIAG, bool BULK, typename GA, typename GB>
+__device__ __forceinline__ T visc_offdiag_tab(const Coef<T>& C, const Nbr& X, const GA& ga,
+                                              const GB& gb, T& dsum) {
+    const T pp = ga(X.a_p);
+    const T pm = ga(X.a_m);
     // normal stresses: 2 mu of the two cells (stored doubled: scaling by two
     // is exact, so this equals doubling mu pp + mu pm afterwards)
-    const T mh = ld(C.mu2_c + cidx(g, q));
-    const T ml = ld(C.mu2_c + cidx(g, qm));
+    const T mh = ld(C.mu2_c + X.c_h);
+    const T ml = ld(C.mu2_c + X.c_l);
     T N = mh * pp;
     N = fma(ml, pm, N);
     if (DIAG) dsum = mh + ml;
-    constexpr bool bulk = BULK;   // a compile-time switch: the plain form issues no bulk work
     T lh = T(0), ll = T(0);
-    if (bulk) {
-        lh = ld(C.lam_c + cidx(g, q));
-        ll = ld(C.lam_c + cidx(g, qm));
+    if (BULK) {   // a compile-time switch: the plain form issues no bulk work
+        lh = ld(C.lam_c + X.c_h);
+        ll = ld(C.lam_c + X.c_l);
         N = fma(lh, pp, N);
         N = fma(ll, pm, N);
         if (DIAG) dsum += lh + ll;
     }
 #pragma unroll
-    for (int B = 0; B < DIM; ++B) {
-        if (B == A) continue;
+    for (int j = 0; j < DIM - 1; ++j) {
+        const int B = trans_axis(DIM, A, j);
         const int P = A + B - 1;   // edge pair index of {A, B}
-        const bool wlo = !g.per[B] && q[B] == 0;
-        const bool whi = !g.per[B] && q[B] == g.n[B] - 1;
-        int qe[3] = {q[0], q[1], q[2]};
-        qe[B] = step(g, B, q[B], 1);
-        const T mlo = ld(C.mu_e[P] + eidx(g, P, q));
-        const T mhi = ld(C.mu_e[P] + eidx(g, P, qe));
+        const T mlo = ld(C.mu_e[P] + X.e_lo[j]);
+        const T mhi = ld(C.mu_e[P] + X.e_hi[j]);
         // d phi_B / dx_A on the two edges: B-faces in A-cells q[A] and q[A]-1
-        int r0[3] = {q[0], q[1], q[2]};
-        r0[A] = qm[A];
-        int r2[3] = {qe[0], qe[1], qe[2]};
-        r2[A] = qm[A];
-        const T xlo = pb(B, q) - pb(B, r0);
-        const T xhi = pb(B, qe) - pb(B, r2);
+        const T xlo = gb(B, X.b_q[j]) - gb(B, X.b_r0[j]);
+        const T xhi = gb(B, X.b_qe[j]) - gb(B, X.b_r2[j]);
         T shi = xhi, slo = -xlo;
-        if (!whi) shi += pa(qe);
-        if (!wlo) {
-            int qb[3] = {q[0], q[1], q[2]};
-            qb[B] = step(g, B, q[B], -1);
-            slo += pa(qb);
-        }
+        if (!X.whi[j]) shi += ga(X.a_bp[j]);
+        if (!X.wlo[j]) slo += ga(X.a_bm[j]);
         N = fma(mhi, shi, N);
         N = fma(mlo, slo, N);
         if (DIAG) {   // explicit fmas: the same rounding in every kernel that inlines this
-            dsum = fma(whi ? T(2) : T(1), mhi, dsum);
-            dsum = fma(wlo ? T(2) : T(1), mlo, dsum);
+            dsum = fma(X.whi[j] ? T(2) : T(1), mhi, dsum);
+            dsum = fma(X.wlo[j] ? T(2) : T(1), mlo, dsum);
         }
-        if (bulk) {   // B-divergence of the cells q (hi) and q - e_A (lo)
-            N = fma(lh, pb(B, qe) - pb(B, q), N);
-            N = fma(-ll, pb(B, r2) - pb(B, r0), N);
+        if (BULK) {   // B-divergence of the cells q (hi) and q - e_A (lo)
+            N = fma(lh, gb(B, X.b_qe[j]) - gb(B, X.b_q[j]), N);
+            N = fma(-ll, gb(B, X.b_r2[j]) - gb(B, X.b_r0[j]), N);
         }
     }
     return N;
 }
 
+// Coordinate accessors: pa(r) reads phi_A at the A-face r (any storage, e.g.
+// shared memory), pb(B, i) reads phi_B at the global index i.
+template <int DIM, int A, typename T, bool DIAG, bool BULK, typename AI, typename GA, typename PB>
+__device__ __forceinline__ T visc_offdiag_acc(const Geom& g, const Coef<T>& C, const int q[3],
+                                              const AI& aidx, const GA& ga, const PB& pb, T& dsum) {
+    Nbr X;
+    nbr_coord<DIM, A>(g, q, aidx, X);
+    return visc_offdiag_tab<DIM, A, T, DIAG, BULK>(C, X, ga, pb, dsum);
+}
+
+// phi a packed global vector: the strided index table
 template <int DIM, int A, typename T, typename TV, bool DIAG, bool BULK = false>
 __device__ __forceinline__ T visc_offdiag_h2(const Geom& g, const Coef<T>& C, const int q[3],
                                              const TV* phi, T& dsum) {
-    return visc_offdiag_acc<DIM, A, T, DIAG, BULK>(
-        g, C, q, [&](const int* r) { return T(phi[fidx(g, A, r)]); },
-        [&](int B, const int* r) { return T(phi[fidx(g, B, r)]); }, dsum);
+    Nbr X;
+    nbr_lin<DIM, A>(g, q, X);
+    return visc_offdiag_tab<DIM, A, T, DIAG, BULK>(
+        C, X, [&](int i) { return T(phi[i]); }, [&](int, int i) { return T(phi[i]); }, dsum);
 }
 
 template <int DIM, typename T, typename TV, bool DIAG, bool BULK = false>
