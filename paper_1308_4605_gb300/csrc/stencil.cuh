@@ -297,11 +297,33 @@ __device__ __forceinline__ T poisson_offdiag_acc(const Geom& g, const Coef<T>& C
     return N;
 }
 
+// The same sum for phi a packed cell vector (c = cidx(q)), from one base
+// index per array and constant strides; the periodic seam and the clamped
+// wall neighbour (itself, with beta = 0) are branch-free corrections.  Same
+// arithmetic order as poisson_offdiag_acc, so the same rounding.
 template <int DIM, typename T, typename TV>
 __device__ __forceinline__ T poisson_offdiag_h2(const Geom& g, const Coef<T>& C, const int q[3],
-                                                const TV* phi, T& bsum) {
-    return poisson_offdiag_acc<DIM, T>(g, C, q, [&](const int* r) { return T(phi[cidx(g, r)]); },
-                                       bsum);
+                                                int c, const TV* phi, T& bsum) {
+    T N = T(0);
+    bsum = T(0);
+    int sc = 1;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        const int na = g.n[a];
+        const bool top = q[a] == na - 1, bot = q[a] == 0;
+        const int sf = a == 0 ? 1 : (a == 1 ? g.fe[a][0] : g.fe[a][0] * g.fe[a][1]);
+        const int fl = fidx(g, a, q);
+        const int fh = fl + ((g.per[a] && top) ? 1 - na : 1) * sf;
+        const int ch = c + (top ? (g.per[a] ? 1 - na : 0) : 1) * sc;
+        const int cl = c - (bot ? (g.per[a] ? 1 - na : 0) : 1) * sc;
+        const T bh = ld(C.beta + fh);
+        const T bl = ld(C.beta + fl);
+        N = fma(bh, T(phi[ch]), N);
+        N = fma(bl, T(phi[cl]), N);
+        bsum += bh + bl;
+        sc *= na;
+    }
+    return N;
 }
 
 // (L_rho phi) at cell q and its diagonal; beta = 0 on wall faces.
@@ -450,31 +472,38 @@ __device__ __forceinline__ T vel_prolong_point(const Geom& gc, const int q[3],
     return fma(wn0, at(N0, 0), wo0 * at(J0, 0));
 }
 
-template <int DIM, typename T, typename PC>
-__device__ __forceinline__ T cell_gs_value(const Geom& g, const Coef<T>& C, const int q[3],
-                                           const PC& pc, const T* rhs) {
-    T bsum;
-    const T N = poisson_offdiag_acc<DIM, T>(g, C, q, pc, bsum);
-    const int c = cidx(g, q);
+template <typename T>
+__device__ __forceinline__ T cell_gs_update(const Geom& g, const Coef<T>& C, int c, T N, T bsum,
+                                            const T* rhs) {
     const T ih2 = gih2<T>(g);
     const T num = fma(-ih2, N, rhs[c]);   // (rhs - off-diagonal part) / diag
     if constexpr (sizeof(T) == 4) return num / (-ih2 * bsum);
     else return num * ld(C.invd_p + c);
 }
 
+template <int DIM, typename T, typename PC>
+__device__ __forceinline__ T cell_gs_value(const Geom& g, const Coef<T>& C, const int q[3],
+                                           const PC& pc, const T* rhs) {
+    T bsum;
+    const T N = poisson_offdiag_acc<DIM, T>(g, C, q, pc, bsum);
+    return cell_gs_update<T>(g, C, cidx(g, q), N, bsum, rhs);
+}
+
 template <int DIM, typename T>
 __device__ __forceinline__ void cell_gs_point(const Geom& g, const Coef<T>& C, const int q[3],
                                               T* phi, const T* rhs) {
-    phi[cidx(g, q)] =
-        cell_gs_value<DIM, T>(g, C, q, [&](const int* r) { return T(phi[cidx(g, r)]); }, rhs);
+    const int c = cidx(g, q);
+    T bsum;
+    const T N = poisson_offdiag_h2<DIM, T, T>(g, C, q, c, phi, bsum);
+    phi[c] = cell_gs_update<T>(g, C, c, N, bsum, rhs);
 }
 
 template <int DIM, typename T>
 __device__ __forceinline__ T cell_res_point(const Geom& g, const Coef<T>& C, const int q[3],
                                             const T* phi, const T* rhs) {
-    T bsum;
-    const T N = poisson_offdiag_h2<DIM, T, T>(g, C, q, phi, bsum);
     const int c = cidx(g, q);
+    T bsum;
+    const T N = poisson_offdiag_h2<DIM, T, T>(g, C, q, c, phi, bsum);
     return fma(-gih2<T>(g), fma(-bsum, T(phi[c]), N), rhs[c]);
 }
 
