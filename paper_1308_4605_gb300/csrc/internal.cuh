@@ -154,9 +154,12 @@ void launch_stokes_residual(const Geom& g, Coef<double> C, const double* x, cons
                             double* r, cudaStream_t s);
 
 // multigrid (precision T)
+// first: this colour belongs to the first sweep from a zero initial guess
+// (sweeps run red, then black, component by component), so the faces of the
+// colour not yet swept and the later components are known to be zero
 template <typename T>
 void launch_vel_gs_colour(const Geom& g, Coef<T> C, int comp, int parity, T* phi, const T* rhs,
-                          cudaStream_t s, int tpb = 256);   // tpb <= 512
+                          cudaStream_t s, int tpb = 256, bool first = false);   // tpb <= 512
 template <typename T>
 void launch_vel_residual(const Geom& g, Coef<T> C, const T* phi, const T* rhs, T* res,
                          cudaStream_t s, bool after_sweep = false);
@@ -175,7 +178,7 @@ void launch_cell_gs_pair(const Geom& g, Coef<T> C, const T* src, T* dst, const T
                          cudaStream_t s);
 template <typename T>
 void launch_cell_gs_colour(const Geom& g, Coef<T> C, int parity, T* phi, const T* rhs,
-                           cudaStream_t s, int tpb = 256);  // tpb <= 512
+                           cudaStream_t s, int tpb = 256, bool first = false);  // tpb <= 512
 template <typename T>
 void launch_cell_residual(const Geom& g, Coef<T> C, const T* phi, const T* rhs, T* res,
                           cudaStream_t s, bool after_sweep = false);

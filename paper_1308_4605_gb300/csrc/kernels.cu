@@ -285,7 +285,8 @@ __global__ void k_stokes_matvec(Geom g, Coef<double> C, Segs sg, const TV* __res
 // ------------------------------------------------------------------- multigrid
 // One colour of the staggered Gauss-Seidel smoother (App. C): every A-face
 // with (i + j + k) % 2 == parity gets phi += D^{-1} (rhs - A phi).
-template <int DIM, int A, typename T, bool BULK>
+// ZM: components known to be zero (first sweep from a zero initial guess).
+template <int DIM, int A, typename T, bool BULK, int ZM = 0>
 __global__ void __launch_bounds__(512) k_vel_gs(Geom g, Coef<T> C, int parity, T* __restrict__ phi,
                                                 const T* __restrict__ rhs, int nthreads) {
     pdl_entry();
@@ -293,7 +294,7 @@ __global__ void __launch_bounds__(512) k_vel_gs(Geom g, Coef<T> C, int parity, T
     if (t >= nthreads) return;
     int q[3];
     if (!decode_face_colour(g, A, parity, t, q) || wall_face(g, A, q)) return;
-    vel_gs_point<DIM, A, T, BULK>(g, C, q, phi, rhs);
+    vel_gs_point<DIM, A, T, BULK, ZM>(g, C, q, phi, rhs);
 }
 
 // Residual rhs - A phi.  zl >= 0: the sweeps just ended with the black
@@ -356,7 +357,8 @@ __global__ void __launch_bounds__(TPB) k_vel_prolong_add(Geom gc, Geom gf, Segs 
 }
 
 // Red-black Gauss-Seidel colour for L_rho phi = rhs (App. C).
-template <int DIM, typename T>
+// Z: every neighbour is zero (first colour of a sweep from a zero initial guess).
+template <int DIM, typename T, bool Z = false>
 __global__ void __launch_bounds__(512) k_cell_gs(Geom g, Coef<T> C, int parity, T* __restrict__ phi,
                                                  const T* __restrict__ rhs, int nthreads) {
     pdl_entry();
@@ -364,7 +366,7 @@ __global__ void __launch_bounds__(512) k_cell_gs(Geom g, Coef<T> C, int parity, 
     if (t >= nthreads) return;
     int q[3];
     decode_cell_colour(g, parity, t, q);
-    cell_gs_point<DIM, T>(g, C, q, phi, rhs);
+    cell_gs_point<DIM, T, Z>(g, C, q, phi, rhs);
 }
 
 // Residual rhs - L_rho phi; zb: the sweeps just ended with the black cells,
@@ -777,10 +779,28 @@ void launch_stokes_residual(const Geom& g, Coef<double> C, const double* x, cons
 
 template <typename T>
 void launch_vel_gs_colour(const Geom& g, Coef<T> C, int comp, int parity, T* phi, const T* rhs,
-                          cudaStream_t s, int tpb) {
+                          cudaStream_t s, int tpb, bool first) {
     const int nt = ((g.fe[comp][0] + 1) / 2) * g.fe[comp][1] * g.fe[comp][2];
     const int nb = (nt + tpb - 1) / tpb;
     const bool bk = C.lam_c != nullptr;
+    if (first && !bk) {
+        // first sweep from zero, red (parity 0) before black, components in
+        // order: zero are the faces of comp not yet swept and the later components
+        const int zm = (parity == 0 ? 1 << comp : 0) | (((1 << g.dim) - 1) & ~((2 << comp) - 1));
+        void (*k)(Geom, Coef<T>, int, T*, const T*, int) = nullptr;
+        if (g.dim == 2) {
+            if (zm == 3) k = k_vel_gs<2, 0, T, false, 3>;
+            else if (zm == 2) k = comp == 0 ? k_vel_gs<2, 0, T, false, 2> : k_vel_gs<2, 1, T, false, 2>;
+        } else {
+            if (zm == 7) k = k_vel_gs<3, 0, T, false, 7>;
+            else if (zm == 6) k = comp == 0 ? k_vel_gs<3, 0, T, false, 6> : k_vel_gs<3, 1, T, false, 6>;
+            else if (zm == 4) k = comp == 1 ? k_vel_gs<3, 1, T, false, 4> : k_vel_gs<3, 2, T, false, 4>;
+        }
+        if (k) {
+            launch_pdl(k, dim3(nb), dim3(tpb), s, g, C, parity, phi, rhs, nt);
+            return;
+        }
+    }
 #define STK_VGS(D, A) (bk ? k_vel_gs<D, A, T, true> : k_vel_gs<D, A, T, false>)
     if (g.dim == 2) {
         if (comp == 0) launch_pdl(STK_VGS(2, 0), dim3(nb), dim3(tpb), s, g, C, parity, phi, rhs, nt);
@@ -819,11 +839,14 @@ void launch_vel_prolong_add(const Geom& gc, const T* pc, const Geom& gf, T* pf, 
 
 template <typename T>
 void launch_cell_gs_colour(const Geom& g, Coef<T> C, int parity, T* phi, const T* rhs,
-                           cudaStream_t s, int tpb) {
+                           cudaStream_t s, int tpb, bool first) {
     const int nt = (g.n[0] / 2) * g.n[1] * g.n[2];
     const int nb = (nt + tpb - 1) / tpb;
-    if (g.dim == 2) launch_pdl(k_cell_gs<2, T>, dim3(nb), dim3(tpb), s, g, C, parity, phi, rhs, nt);
-    else launch_pdl(k_cell_gs<3, T>, dim3(nb), dim3(tpb), s, g, C, parity, phi, rhs, nt);
+    const bool z = first && parity == 0;   // red first: all its neighbours are black
+    if (g.dim == 2)
+        launch_pdl(z ? k_cell_gs<2, T, true> : k_cell_gs<2, T>, dim3(nb), dim3(tpb), s, g, C, parity, phi, rhs, nt);
+    else
+        launch_pdl(z ? k_cell_gs<3, T, true> : k_cell_gs<3, T>, dim3(nb), dim3(tpb), s, g, C, parity, phi, rhs, nt);
 }
 
 template <typename T>
@@ -933,14 +956,14 @@ void launch_check_fields(int n, const double* rho, const double* mu, double* scr
 // explicit instantiations
 #define STK_INST(T)                                                                                \
     template void launch_vel_gs_colour<T>(const Geom&, Coef<T>, int, int, T*, const T*,          \
-                                          cudaStream_t, int);                                      \
+                                          cudaStream_t, int, bool);                                \
     template void launch_vel_residual<T>(const Geom&, Coef<T>, const T*, const T*, T*,           \
                                          cudaStream_t, bool);                                      \
     template void launch_vel_restrict<T>(const Geom&, const T*, const Geom&, T*, cudaStream_t);  \
     template void launch_vel_prolong_add<T>(const Geom&, const T*, const Geom&, T*,              \
                                             cudaStream_t);                                         \
     template void launch_cell_gs_colour<T>(const Geom&, Coef<T>, int, T*, const T*,              \
-                                           cudaStream_t, int);                                     \
+                                           cudaStream_t, int, bool);                               \
     template void launch_cell_residual<T>(const Geom&, Coef<T>, const T*, const T*, T*,          \
                                           cudaStream_t, bool);                                     \
     template void launch_cell_restrict<T>(const Geom&, const T*, const Geom&, T*, cudaStream_t); \

@@ -35,12 +35,12 @@ const char* kProfNames[STK_NPROF] = {
     "cell_prolong_add", "precond_algebra",   "mean_removal",  "arnoldi_multidot",
     "arnoldi_update",   "krylov_combine",    "convert",       "coarse_levels",
     "vel_smooth_colour_l0", "cell_smooth_colour_l0", "vel_smooth_pair_l0", "vel_smooth_pair",
-    "cell_smooth_pair_l0", "cell_smooth_pair", "unused_22", "unused_23"};
+    "cell_smooth_pair_l0", "cell_smooth_pair", "vel_smooth_first", "cell_smooth_first"};
 
 enum {
     PF_MATVEC = 0, PF_VSMOOTH, PF_VRES, PF_VRESTR, PF_VPROL, PF_CSMOOTH, PF_CRES, PF_CRESTR,
     PF_CPROL, PF_ALG, PF_MEAN, PF_MDOT, PF_UPD, PF_COMB, PF_CONV, PF_COARSE, PF_VSMOOTH0,
-    PF_CSMOOTH0, PF_VPAIR0, PF_VPAIR, PF_CPAIR0, PF_CPAIR
+    PF_CSMOOTH0, PF_VPAIR0, PF_VPAIR, PF_CPAIR0, PF_CPAIR, PF_VFIRST, PF_CFIRST
 };
 
 template <typename T>
@@ -275,6 +275,28 @@ template <typename T>
 double bytes_cell_colour(const Geom& g) {    // half: rhs, invd, write; phi, beta all
     return sizeof(T) * (1.5 * g.ncell + g.ncell + g.nvel);
 }
+// The colours of the first sweep from zero read only what is not known to be
+// zero (k_vel_gs with its zero mask): the half of comp a (rhs, alpha or the
+// inverse diagonal, phi written) always; phi_a unless its other colour is
+// still zero; phi_b of the components already swept; mu2_c and the edge
+// viscosities wherever a term or (FP32) the diagonal needs them.
+template <typename T>
+double bytes_vel_first(const Geom& g, int a, int parity) {
+    const bool f32 = sizeof(T) == 4;
+    const bool za = parity == 0;
+    double w = 2.0 * g.fsize[a] + (za ? 0.0 : g.fsize[a]) + ((za && !f32) ? 0.0 : g.ncell);
+    for (int b = 0; b < g.dim; ++b) {
+        if (b == a) continue;
+        const bool zb = b > a;
+        if (!zb) w += g.fsize[b];
+        if (!(za && zb) || f32) w += g.esize[a + b - 1];
+    }
+    return sizeof(T) * w;
+}
+template <typename T>
+double bytes_cell_first(const Geom& g) {   // red from zero: rhs, invd half, write half (FP32: beta all)
+    return sizeof(T) * (sizeof(T) == 8 ? 1.5 * g.ncell : 1.0 * g.ncell + g.nvel);
+}
 // kernels of one stress-based operator or residual evaluation: cells, one
 // per edge family, faces
 int stress_kernels(const Geom& g) { return g.dim == 3 ? 5 : 3; }
@@ -355,7 +377,8 @@ double bytes_vel_pair(const Geom& g, int a) {
 // in phi); an odd last sweep, and levels below lpair, use one launch per
 // colour in place.
 template <typename T>
-void vel_sweeps(stk_handle* h, int l, int nsweep, T* phi, const T* rhs, cudaStream_t s) {
+void vel_sweeps(stk_handle* h, int l, int nsweep, T* phi, const T* rhs, cudaStream_t s,
+                bool from_zero = false) {
     const Level& L = h->lev[l];
     Coef<T> C = coef_of<T>(L);
     const bool fine = l == 0;
@@ -373,6 +396,14 @@ void vel_sweeps(stk_handle* h, int l, int nsweep, T* phi, const T* rhs, cudaStre
     for (; it < nsweep; ++it)
         for (int a = 0; a < L.g.dim; ++a)
             for (int par = 0; par < 2; ++par) {
+                // the first sweep from zero skips the terms of zero values
+                // (plain form only; with bulk viscosity every sweep is full)
+                const bool first = from_zero && it == 0 && !h->bulk;
+                if (first) {
+                    Scope sc(h, PF_VFIRST, bytes_vel_first<T>(L.g, a, par), s, 1, 0.0);
+                    launch_vel_gs_colour<T>(L.g, C, a, par, phi, rhs, s, tpb_of<T>(h), true);
+                    continue;
+                }
                 Scope sc(h, fine ? PF_VSMOOTH0 : PF_VSMOOTH, bytes_vel_colour<T>(L.g, a), s, 1,
                          fl * updated_faces(L.g, a));
                 launch_vel_gs_colour<T>(L.g, C, a, par, phi, rhs, s, tpb_of<T>(h));
@@ -380,7 +411,8 @@ void vel_sweeps(stk_handle* h, int l, int nsweep, T* phi, const T* rhs, cudaStre
 }
 
 template <typename T>
-void cell_sweeps(stk_handle* h, int l, int nsweep, T* phi, const T* rhs, cudaStream_t s) {
+void cell_sweeps(stk_handle* h, int l, int nsweep, T* phi, const T* rhs, cudaStream_t s,
+                 bool from_zero = false) {
     const Level& L = h->lev[l];
     Coef<T> C = coef_of<T>(L);
     const bool fine = l == 0;
@@ -397,6 +429,11 @@ void cell_sweeps(stk_handle* h, int l, int nsweep, T* phi, const T* rhs, cudaStr
     }
     for (; it < nsweep; ++it)
         for (int par = 0; par < 2; ++par) {
+            if (from_zero && it == 0 && par == 0) {   // red from zero: no neighbour terms
+                Scope sc(h, PF_CFIRST, bytes_cell_first<T>(L.g), s, 1, 0.0);
+                launch_cell_gs_colour<T>(L.g, C, par, phi, rhs, s, tpb_of<T>(h), true);
+                continue;
+            }
             Scope sc(h, fine ? PF_CSMOOTH0 : PF_CSMOOTH, bytes_cell_colour<T>(L.g), s, 1, fl);
             launch_cell_gs_colour<T>(L.g, C, par, phi, rhs, s, tpb_of<T>(h));
         }
@@ -416,12 +453,12 @@ void vcycle_vel(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp, 
     }
     launch_zero<T>(L.g.nvel, phi, s);
     if (l + 1 == (int)h->lev.size()) {
-        vel_sweeps<T>(h, l, mp.ncoarse, phi, rhs, s);
+        vel_sweeps<T>(h, l, mp.ncoarse, phi, rhs, s, true);
         return;
     }
     const Level& Lc = h->lev[l + 1];
     Work<T> Wc = work_of<T>(Lc);
-    vel_sweeps<T>(h, l, mp.nu, phi, rhs, s);
+    vel_sweeps<T>(h, l, mp.nu, phi, rhs, s, true);
     {
         const bool st = sizeof(T) == 8 && l == 0;
         Scope sc(h, PF_VRES, bytes_vel_residual<T>(L.g), s, st ? stress_kernels(L.g) : 1);
@@ -457,12 +494,12 @@ void vcycle_cell(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp,
     }
     launch_zero<T>(L.g.ncell, phi, s);
     if (l + 1 == (int)h->lev.size()) {
-        cell_sweeps<T>(h, l, mp.ncoarse, phi, rhs, s);
+        cell_sweeps<T>(h, l, mp.ncoarse, phi, rhs, s, true);
         return;
     }
     const Level& Lc = h->lev[l + 1];
     Work<T> Wc = work_of<T>(Lc);
-    cell_sweeps<T>(h, l, mp.nu, phi, rhs, s);
+    cell_sweeps<T>(h, l, mp.nu, phi, rhs, s, true);
     {
         Scope sc(h, PF_CRES, sizeof(T) * (3.0 * L.g.ncell + L.g.nvel), s);
         launch_cell_residual<T>(L.g, coef_of<T>(L), phi, rhs, W.res_p, s, mp.nu > 0);

@@ -197,45 +197,69 @@ __device__ __forceinline__ void nbr_coord(const Geom& g, const int q[3], const A
 }
 
 // The arithmetic: ga(i) reads phi_A at index i, gb(B, i) phi_B at index i.
-template <int DIM, int A, typename T, bool DIAG, bool BULK, typename GA, typename GB>
+// ZM: components known to be zero (bit c for phi_c), as in the first sweep
+// from a zero initial guess, where the faces of the colour not yet updated
+// and the components after A are still zero.  Their terms are left out
+// rather than multiplied by zero: the same sum up to the sign of a zero.
+template <int DIM, int A, typename T, bool DIAG, bool BULK, int ZM = 0, typename GA, typename GB>
 __device__ __forceinline__ T visc_offdiag_tab(const Coef<T>& C, const Nbr& X, const GA& ga,
                                               const GB& gb, T& dsum) {
-    const T pp = ga(X.a_p);
-    const T pm = ga(X.a_m);
+    constexpr bool za = (ZM >> A) & 1;
+    T N = T(0);
+    T mh = T(0), ml = T(0), pp = T(0), pm = T(0);
     // normal stresses: 2 mu of the two cells (stored doubled: scaling by two
     // is exact, so this equals doubling mu pp + mu pm afterwards)
-    const T mh = ld(C.mu2_c + X.c_h);
-    const T ml = ld(C.mu2_c + X.c_l);
-    T N = mh * pp;
-    N = fma(ml, pm, N);
+    if (!za || DIAG) {
+        mh = ld(C.mu2_c + X.c_h);
+        ml = ld(C.mu2_c + X.c_l);
+    }
+    if (!za) {
+        pp = ga(X.a_p);
+        pm = ga(X.a_m);
+        N = mh * pp;
+        N = fma(ml, pm, N);
+    }
     if (DIAG) dsum = mh + ml;
     T lh = T(0), ll = T(0);
     if (BULK) {   // a compile-time switch: the plain form issues no bulk work
         lh = ld(C.lam_c + X.c_h);
         ll = ld(C.lam_c + X.c_l);
-        N = fma(lh, pp, N);
-        N = fma(ll, pm, N);
+        if (!za) {
+            N = fma(lh, pp, N);
+            N = fma(ll, pm, N);
+        }
         if (DIAG) dsum += lh + ll;
     }
 #pragma unroll
     for (int j = 0; j < DIM - 1; ++j) {
         const int B = trans_axis(DIM, A, j);
         const int P = A + B - 1;   // edge pair index of {A, B}
+        const bool zb = (ZM >> B) & 1;   // folds to a constant once j is unrolled
+        if (za && zb && !DIAG) continue;
         const T mlo = ld(C.mu_e[P] + X.e_lo[j]);
         const T mhi = ld(C.mu_e[P] + X.e_hi[j]);
-        // d phi_B / dx_A on the two edges: B-faces in A-cells q[A] and q[A]-1
-        const T xlo = gb(B, X.b_q[j]) - gb(B, X.b_r0[j]);
-        const T xhi = gb(B, X.b_qe[j]) - gb(B, X.b_r2[j]);
-        T shi = xhi, slo = -xlo;
-        if (!X.whi[j]) shi += ga(X.a_bp[j]);
-        if (!X.wlo[j]) slo += ga(X.a_bm[j]);
-        N = fma(mhi, shi, N);
-        N = fma(mlo, slo, N);
+        if (!zb) {
+            // d phi_B / dx_A on the two edges: B-faces in A-cells q[A] and q[A]-1
+            const T xlo = gb(B, X.b_q[j]) - gb(B, X.b_r0[j]);
+            const T xhi = gb(B, X.b_qe[j]) - gb(B, X.b_r2[j]);
+            T shi = xhi, slo = -xlo;
+            if (!za) {
+                if (!X.whi[j]) shi += ga(X.a_bp[j]);
+                if (!X.wlo[j]) slo += ga(X.a_bm[j]);
+            }
+            N = fma(mhi, shi, N);
+            N = fma(mlo, slo, N);
+        } else if (!za) {
+            const T shi = X.whi[j] ? T(0) : ga(X.a_bp[j]);
+            const T slo = X.wlo[j] ? T(0) : ga(X.a_bm[j]);
+            N = fma(mhi, shi, N);
+            N = fma(mlo, slo, N);
+        }
         if (DIAG) {   // explicit fmas: the same rounding in every kernel that inlines this
             dsum = fma(X.whi[j] ? T(2) : T(1), mhi, dsum);
             dsum = fma(X.wlo[j] ? T(2) : T(1), mlo, dsum);
         }
-        if (BULK) {   // B-divergence of the cells q (hi) and q - e_A (lo)
+        if (BULK && !zb) {   // B-divergence of the cells q (hi) and q - e_A (lo)
             N = fma(lh, gb(B, X.b_qe[j]) - gb(B, X.b_q[j]), N);
             N = fma(-ll, gb(B, X.b_r2[j]) - gb(B, X.b_r0[j]), N);
         }
@@ -254,12 +278,12 @@ __device__ __forceinline__ T visc_offdiag_acc(const Geom& g, const Coef<T>& C, c
 }
 
 // phi a packed global vector: the strided index table
-template <int DIM, int A, typename T, typename TV, bool DIAG, bool BULK = false>
+template <int DIM, int A, typename T, typename TV, bool DIAG, bool BULK = false, int ZM = 0>
 __device__ __forceinline__ T visc_offdiag_h2(const Geom& g, const Coef<T>& C, const int q[3],
                                              const TV* phi, T& dsum) {
     Nbr X;
     nbr_lin<DIM, A>(g, q, X);
-    return visc_offdiag_tab<DIM, A, T, DIAG, BULK>(
+    return visc_offdiag_tab<DIM, A, T, DIAG, BULK, ZM>(
         C, X, [&](int i) { return T(phi[i]); }, [&](int, int i) { return T(phi[i]); }, dsum);
 }
 
@@ -301,7 +325,9 @@ __device__ __forceinline__ T poisson_offdiag_acc(const Geom& g, const Coef<T>& C
 // index per array and constant strides; the periodic seam and the clamped
 // wall neighbour (itself, with beta = 0) are branch-free corrections.  Same
 // arithmetic order as poisson_offdiag_acc, so the same rounding.
-template <int DIM, typename T, typename TV>
+// Z: every neighbour is known to be zero (the first colour of a sweep from a
+// zero initial guess); N is then zero and only bsum is formed.
+template <int DIM, typename T, typename TV, bool Z = false>
 __device__ __forceinline__ T poisson_offdiag_h2(const Geom& g, const Coef<T>& C, const int q[3],
                                                 int c, const TV* phi, T& bsum) {
     T N = T(0);
@@ -314,12 +340,14 @@ __device__ __forceinline__ T poisson_offdiag_h2(const Geom& g, const Coef<T>& C,
         const int sf = a == 0 ? 1 : (a == 1 ? g.fe[a][0] : g.fe[a][0] * g.fe[a][1]);
         const int fl = fidx(g, a, q);
         const int fh = fl + ((g.per[a] && top) ? 1 - na : 1) * sf;
-        const int ch = c + (top ? (g.per[a] ? 1 - na : 0) : 1) * sc;
-        const int cl = c - (bot ? (g.per[a] ? 1 - na : 0) : 1) * sc;
         const T bh = ld(C.beta + fh);
         const T bl = ld(C.beta + fl);
-        N = fma(bh, T(phi[ch]), N);
-        N = fma(bl, T(phi[cl]), N);
+        if (!Z) {
+            const int ch = c + (top ? (g.per[a] ? 1 - na : 0) : 1) * sc;
+            const int cl = c - (bot ? (g.per[a] ? 1 - na : 0) : 1) * sc;
+            N = fma(bh, T(phi[ch]), N);
+            N = fma(bl, T(phi[cl]), N);
+        }
         bsum += bh + bl;
         sc *= na;
     }
@@ -363,12 +391,12 @@ __device__ __forceinline__ T vel_gs_value(const Geom& g, const Coef<T>& C, int f
     else return num * ld(C.invd_u + f);
 }
 
-template <int DIM, int A, typename T, bool BULK = false>
+template <int DIM, int A, typename T, bool BULK = false, int ZM = 0>
 __device__ __forceinline__ void vel_gs_point(const Geom& g, const Coef<T>& C, const int q[3],
                                              T* phi, const T* rhs) {
     constexpr bool F32 = sizeof(T) == 4;
     T dsum;
-    const T N = visc_offdiag_h2<DIM, A, T, T, F32, BULK>(g, C, q, phi, dsum);
+    const T N = visc_offdiag_h2<DIM, A, T, T, F32, BULK, ZM>(g, C, q, phi, dsum);
     const int f = fidx(g, A, q);
     phi[f] = vel_gs_value<T>(g, C, f, N, dsum, rhs);
 }
@@ -489,12 +517,16 @@ __device__ __forceinline__ T cell_gs_value(const Geom& g, const Coef<T>& C, cons
     return cell_gs_update<T>(g, C, cidx(g, q), N, bsum, rhs);
 }
 
-template <int DIM, typename T>
+template <int DIM, typename T, bool Z = false>
 __device__ __forceinline__ void cell_gs_point(const Geom& g, const Coef<T>& C, const int q[3],
                                               T* phi, const T* rhs) {
     const int c = cidx(g, q);
+    if (Z && sizeof(T) == 8) {   // FP64: the inverse diagonal is stored; no beta needed
+        phi[c] = cell_gs_update<T>(g, C, c, T(0), T(0), rhs);
+        return;
+    }
     T bsum;
-    const T N = poisson_offdiag_h2<DIM, T, T>(g, C, q, c, phi, bsum);
+    const T N = poisson_offdiag_h2<DIM, T, T, Z>(g, C, q, c, phi, bsum);
     phi[c] = cell_gs_update<T>(g, C, c, N, bsum, rhs);
 }
 
