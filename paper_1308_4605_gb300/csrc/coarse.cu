@@ -69,6 +69,17 @@ __device__ void c_cell_sweeps(const Geom& g, const Coef<T>& C, int nsweep, T* ph
         }
 }
 
+// phi = S rhs with S stored column-major (st[i * n + j] = S_ji): each thread
+// forms whole rows, summing over i in increasing order
+template <typename T>
+__device__ void smat_apply(const T* __restrict__ st, int n, const T* rhs, T* phi) {
+    for (int j = threadIdx.x; j < n; j += CT) {
+        T acc = T(0);
+        for (int i = 0; i < n; ++i) acc = fma(st[(size_t)i * n + j], rhs[i], acc);
+        phi[j] = acc;
+    }
+}
+
 __device__ __forceinline__ void load_geom(Geom* dst, const Geom* src) {
     // cooperative copy of a level's geometry into shared memory
     const int* s = reinterpret_cast<const int*>(src);
@@ -113,7 +124,8 @@ __global__ void __launch_bounds__(CT) k_coarse_vel(const CLevel<T>* __restrict__
         for (int t = threadIdx.x; t < g.nvel; t += CT) phi[t] = T(0);
         __syncthreads();
         if (l + 1 == nlev) {
-            c_vel_sweeps<DIM, T, BULK>(g, C, ncoarse, phi, rhs);
+            if (Ls[l].smat_u && Ls[l].smat_nc == ncoarse) smat_apply<T>(Ls[l].smat_u, g.nvel, rhs, phi);
+            else c_vel_sweeps<DIM, T, BULK>(g, C, ncoarse, phi, rhs);
             break;
         }
         c_vel_sweeps<DIM, T, BULK>(g, C, nu, phi, rhs);
@@ -213,7 +225,8 @@ __global__ void __launch_bounds__(CT) k_coarse_cell(const CLevel<T>* __restrict_
         for (int t = threadIdx.x; t < g.ncell; t += CT) phi[t] = T(0);
         __syncthreads();
         if (l + 1 == nlev) {
-            c_cell_sweeps<DIM, T>(g, C, ncoarse, phi, rhs);
+            if (Ls[l].smat_p && Ls[l].smat_nc == ncoarse) smat_apply<T>(Ls[l].smat_p, g.ncell, rhs, phi);
+            else c_cell_sweeps<DIM, T>(g, C, ncoarse, phi, rhs);
             break;
         }
         c_cell_sweeps<DIM, T>(g, C, nu, phi, rhs);
@@ -258,7 +271,74 @@ __global__ void __launch_bounds__(CT) k_coarse_cell(const CLevel<T>* __restrict_
     }
 }
 
+// Column i of the coarse-solve matrix: the ncoarse sweeps applied to e_i.
+template <int DIM, typename T, bool BULK>
+__global__ void __launch_bounds__(CT) k_smat_vel(Geom g, Coef<T> C, int ncoarse, T* __restrict__ st) {
+    pdl_entry();
+    __shared__ T phi[SMAT_MAX], rhs[SMAT_MAX];
+    const int i = blockIdx.x, n = g.nvel;
+    for (int t = threadIdx.x; t < n; t += CT) {
+        phi[t] = T(0);
+        rhs[t] = t == i ? T(1) : T(0);
+    }
+    __syncthreads();
+    c_vel_sweeps<DIM, T, BULK>(g, C, ncoarse, phi, rhs);
+    for (int t = threadIdx.x; t < n; t += CT) st[(size_t)i * n + t] = phi[t];
+}
+
+template <int DIM, typename T>
+__global__ void __launch_bounds__(CT) k_smat_cell(Geom g, Coef<T> C, int ncoarse, T* __restrict__ st) {
+    pdl_entry();
+    __shared__ T phi[SMAT_MAX], rhs[SMAT_MAX];
+    const int i = blockIdx.x, n = g.ncell;
+    for (int t = threadIdx.x; t < n; t += CT) {
+        phi[t] = T(0);
+        rhs[t] = t == i ? T(1) : T(0);
+    }
+    __syncthreads();
+    c_cell_sweeps<DIM, T>(g, C, ncoarse, phi, rhs);
+    for (int t = threadIdx.x; t < n; t += CT) st[(size_t)i * n + t] = phi[t];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(CT) k_smat_apply(int n, const T* __restrict__ st, const T* __restrict__ rhs,
+                                                   T* __restrict__ phi) {
+    pdl_entry();
+    smat_apply<T>(st, n, rhs, phi);
+}
+
 }  // namespace
+
+template <typename T>
+void launch_coarsest_matrix_vel(const Geom& g, Coef<T> C, int ncoarse, T* st, cudaStream_t s) {
+    if (g.nvel > SMAT_MAX || g.nvel < 1) return;
+    const bool bk = C.lam_c != nullptr;
+    if (g.dim == 2)
+        launch_pdl(bk ? k_smat_vel<2, T, true> : k_smat_vel<2, T, false>, dim3(g.nvel), dim3(CT), s, g, C,
+                   ncoarse, st);
+    else
+        launch_pdl(bk ? k_smat_vel<3, T, true> : k_smat_vel<3, T, false>, dim3(g.nvel), dim3(CT), s, g, C,
+                   ncoarse, st);
+}
+
+template <typename T>
+void launch_coarsest_matrix_cell(const Geom& g, Coef<T> C, int ncoarse, T* st, cudaStream_t s) {
+    if (g.ncell > SMAT_MAX || g.ncell < 1) return;
+    if (g.dim == 2) launch_pdl(k_smat_cell<2, T>, dim3(g.ncell), dim3(CT), s, g, C, ncoarse, st);
+    else launch_pdl(k_smat_cell<3, T>, dim3(g.ncell), dim3(CT), s, g, C, ncoarse, st);
+}
+
+template <typename T>
+void launch_coarsest_apply(int n, const T* st, const T* rhs, T* phi, cudaStream_t s) {
+    launch_pdl(k_smat_apply<T>, dim3(1), dim3(CT), s, n, st, rhs, phi);
+}
+
+template void launch_coarsest_matrix_vel<double>(const Geom&, Coef<double>, int, double*, cudaStream_t);
+template void launch_coarsest_matrix_vel<float>(const Geom&, Coef<float>, int, float*, cudaStream_t);
+template void launch_coarsest_matrix_cell<double>(const Geom&, Coef<double>, int, double*, cudaStream_t);
+template void launch_coarsest_matrix_cell<float>(const Geom&, Coef<float>, int, float*, cudaStream_t);
+template void launch_coarsest_apply<double>(int, const double*, const double*, double*, cudaStream_t);
+template void launch_coarsest_apply<float>(int, const float*, const float*, float*, cudaStream_t);
 
 // dynamic shared memory the SMEM variants may use (set on every kernel by
 // prepare_coarse_kernels; the static Geom copies and layout need ~2 KB more)

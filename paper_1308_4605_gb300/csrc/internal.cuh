@@ -94,9 +94,15 @@ struct Coef {
 // has completed and its memory is visible.  Inside a captured graph the
 // same holds through programmatic edges.  Semantics are those of ordinary
 // stream order; only launch latency is hidden.
+// launches issued by this host thread through launch_pdl: entry points that
+// launch outside the profiled scopes (coefficient setup) add the difference
+// to their handle's kernel count
+inline thread_local long long tl_launches = 0;
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t s,
                               Args... args) {
+    ++tl_launches;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
@@ -195,6 +201,11 @@ struct CLevel {
     Geom g;
     Coef<T> C;
     T *phi_u, *rhs_u, *res_u, *phi_p, *rhs_p, *res_p;
+    // coarsest level only: the matrices of its coarse solve (see
+    // launch_coarsest_matrix) and the sweep count they hold (0: none)
+    const T* smat_u = nullptr;
+    const T* smat_p = nullptr;
+    int smat_nc = 0;
 };
 // levels this small run in the coarse kernel: one SM's FP32 rate makes 4096
 // cells (16^3, 64^2) worth it; its FP64 rate (1/152 of about 1.2 TFLOP/s)
@@ -214,6 +225,24 @@ void launch_coarse_vcycle_cell(int dim, const CLevel<T>* L, int nlev, const T* r
 // limit on the current device.
 constexpr size_t COARSE_SMEM_LIMIT = 220 * 1024;
 void prepare_coarse_kernels();
+
+// The coarse solve of App. C, ncoarse Gauss-Seidel sweeps on the coarsest
+// level from a zero initial guess, is a fixed linear map phi = S rhs of that
+// level's n unknowns (n = faces, or cells).  For n <= SMAT_MAX it is formed
+// once per coefficient set, column i from the same sweeps applied to the
+// unit vector e_i (stored column-major: st[i * n + j] = S_ji), and then
+// applied as a matrix: one short parallel stage instead of 6 ncoarse
+// (velocity) or 2 ncoarse (pressure) dependent ones.  The two agree up to
+// rounding.
+constexpr int SMAT_MAX = 1024;
+template <typename T>
+void launch_coarsest_matrix_vel(const Geom& g, Coef<T> C, int ncoarse, T* st, cudaStream_t s);
+template <typename T>
+void launch_coarsest_matrix_cell(const Geom& g, Coef<T> C, int ncoarse, T* st, cudaStream_t s);
+// phi = S rhs (one block; the same sums, in the same order, as inside the
+// coarse-level kernel)
+template <typename T>
+void launch_coarsest_apply(int n, const T* st, const T* rhs, T* phi, cudaStream_t s);
 
 // preconditioner algebra (precision T)
 template <typename T>  // bc = D u + bp

@@ -57,7 +57,23 @@ struct Level {
     Work<float> wf;
     double* lam_d = nullptr;   // storage of the bulk term (allocated on first use)
     float* lam_f = nullptr;
+    // coarsest level only: the coarse-solve matrices (launch_coarsest_matrix),
+    // allocated when the level has at most SMAT_MAX faces (cells)
+    double* smat_ud = nullptr;
+    double* smat_pd = nullptr;
+    float* smat_uf = nullptr;
+    float* smat_pf = nullptr;
 };
+
+// the sweep count the coarse-solve matrices are formed for: the default
+// ncoarse (App. C); other counts sweep
+constexpr int SMAT_SWEEPS = 8;
+template <typename T> const T* smat_u_of(const Level& L);
+template <> const double* smat_u_of<double>(const Level& L) { return L.smat_ud; }
+template <> const float* smat_u_of<float>(const Level& L) { return L.smat_uf; }
+template <typename T> const T* smat_p_of(const Level& L);
+template <> const double* smat_p_of<double>(const Level& L) { return L.smat_pd; }
+template <> const float* smat_p_of<float>(const Level& L) { return L.smat_pf; }
 
 template <typename T>
 struct PBuf {            // level-0 buffers of the preconditioner in precision T
@@ -451,6 +467,11 @@ void vcycle_vel(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp, 
                                     mp.nu, mp.ncoarse, h->bulk, coarse_smem<T>(h, l, true), s);
         return;
     }
+    if (l + 1 == (int)h->lev.size() && smat_u_of<T>(L) && mp.ncoarse == SMAT_SWEEPS) {
+        Scope sc(h, PF_COARSE, 0.0, s);
+        launch_coarsest_apply<T>(L.g.nvel, smat_u_of<T>(L), rhs, phi, s);
+        return;
+    }
     launch_zero<T>(L.g.nvel, phi, s);
     if (l + 1 == (int)h->lev.size()) {
         vel_sweeps<T>(h, l, mp.ncoarse, phi, rhs, s, true);
@@ -490,6 +511,11 @@ void vcycle_cell(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp,
         Scope sc(h, PF_COARSE, 0.0, s);
         launch_coarse_vcycle_cell<T>(L.g.dim, clev_of<T>(h) + l, (int)h->lev.size() - l, rhs, phi,
                                      mp.nu, mp.ncoarse, coarse_smem<T>(h, l, false), s);
+        return;
+    }
+    if (l + 1 == (int)h->lev.size() && smat_p_of<T>(L) && mp.ncoarse == SMAT_SWEEPS) {
+        Scope sc(h, PF_COARSE, 0.0, s);
+        launch_coarsest_apply<T>(L.g.ncell, smat_p_of<T>(L), rhs, phi, s);
         return;
     }
     launch_zero<T>(L.g.ncell, phi, s);
@@ -1062,6 +1088,11 @@ cudaError_t upload_clevels(stk_handle* h) {
         const Level& L = h->lev[l];
         cd[l] = CLevel<double>{L.g, L.cd, L.wd.phi_u, L.wd.rhs_u, L.wd.res_u, L.wd.phi_p, L.wd.rhs_p, L.wd.res_p};
         cf[l] = CLevel<float>{L.g, L.cf, L.wf.phi_u, L.wf.rhs_u, L.wf.res_u, L.wf.phi_p, L.wf.rhs_p, L.wf.res_p};
+        cd[l].smat_u = L.smat_ud;
+        cd[l].smat_p = L.smat_pd;
+        cf[l].smat_u = L.smat_uf;
+        cf[l].smat_p = L.smat_pf;
+        cd[l].smat_nc = cf[l].smat_nc = (L.smat_ud || L.smat_pd) ? SMAT_SWEEPS : 0;
     }
     cudaError_t e = cudaMemcpy(h->cld, cd.data(), sizeof(CLevel<double>) * nl, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
@@ -1078,6 +1109,15 @@ void build_coefficients(stk_handle* h, const double* rho, const double* mu, cuda
     for (auto& L : h->lev) {
         launch_inverse_diagonals(L.g, L.cd, s);
         launch_convert_coefficients(L.g, L.cd, L.cf, s);
+    }
+    Level& Lc = h->lev.back();   // the coarse-solve matrices of both hierarchies
+    if (Lc.smat_ud) {
+        launch_coarsest_matrix_vel<double>(Lc.g, Lc.cd, SMAT_SWEEPS, Lc.smat_ud, s);
+        launch_coarsest_matrix_vel<float>(Lc.g, Lc.cf, SMAT_SWEEPS, Lc.smat_uf, s);
+    }
+    if (Lc.smat_pd) {
+        launch_coarsest_matrix_cell<double>(Lc.g, Lc.cd, SMAT_SWEEPS, Lc.smat_pd, s);
+        launch_coarsest_matrix_cell<float>(Lc.g, Lc.cf, SMAT_SWEEPS, Lc.smat_pf, s);
     }
 }
 
@@ -1195,6 +1235,18 @@ int stk_create(int dim, const int* n, double hh, const int* bc, stk_handle** out
         CKC(dalloc(h, &L.wf.alt_u, g.nvel));
         CKC(dalloc(h, &L.wf.alt_p, g.ncell));
     }
+    {
+        Level& Lc = h->lev.back();
+        const size_t nu = (size_t)Lc.g.nvel, np = (size_t)Lc.g.ncell;
+        if (nu <= (size_t)SMAT_MAX) {
+            CKC(dalloc(h, &Lc.smat_ud, nu * nu));
+            CKC(dalloc(h, &Lc.smat_uf, nu * nu));
+        }
+        if (np <= (size_t)SMAT_MAX) {
+            CKC(dalloc(h, &Lc.smat_pd, np * np));
+            CKC(dalloc(h, &Lc.smat_pf, np * np));
+        }
+    }
     const Geom& g0 = h->lev[0].g;
     const int ns = g0.nvel + g0.ncell;
     CKC(dalloc(h, &h->pd.in, ns));
@@ -1274,6 +1326,7 @@ int stk_set_coefficients(stk_handle* h, const double* rho, const double* mu, dou
     if (!(dt > 0.0)) return fail(h, STK_ERR_ARG, "dt must be > 0 (+INFINITY for steady flow)");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     CK(cudaSetDevice(h->device));
+    const long long k0 = tl_launches;
     const Geom& g0 = h->lev[0].g;
     launch_check_fields(g0.ncell, rho, mu, h->red, h->dsc + DS_N2, s);
     CKL();
@@ -1299,6 +1352,7 @@ int stk_set_coefficients(stk_handle* h, const double* rho, const double* mu, dou
     CK(cudaMemcpyAsync(h->mu0, mu, sizeof(double) * g0.ncell, cudaMemcpyDeviceToDevice, s));
     build_coefficients(h, rho, mu, s);
     CKL();
+    h->nkern += tl_launches - k0;
     CK(cudaStreamSynchronize(s));
     h->coef_set = true;
     return STK_OK;
@@ -1309,6 +1363,7 @@ int stk_set_bulk_viscosity(stk_handle* h, const double* gamma, void* stream) {
     if (!h->coef_set) return fail(h, STK_ERR_STATE, "coefficients not set");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     CK(cudaSetDevice(h->device));
+    const long long k0 = tl_launches;
     const Geom& g0 = h->lev[0].g;
     const bool on = gamma != nullptr;
     if (on) {   // gamma finite and >= 0 (checked beside the stored rho > 0)
@@ -1340,6 +1395,7 @@ int stk_set_bulk_viscosity(stk_handle* h, const double* gamma, void* stream) {
     }
     build_coefficients(h, h->rho0, h->mu0, s);
     CKL();
+    h->nkern += tl_launches - k0;
     CK(cudaStreamSynchronize(s));
     return STK_OK;
 }

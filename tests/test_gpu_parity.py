@@ -155,6 +155,27 @@ def test_repeated_cycle_preconditioners_match_oracle(S, which, dim, n, bc, theta
     solver.close()
 
 
+@pytest.mark.parametrize("ncoarse", [8, 3])
+@pytest.mark.parametrize("dim,n,bc,theta", [CASES[1], CASES[4], CASES[7], CASES[8]])
+def test_coarse_solve_sweep_counts_match_oracle(S, ncoarse, dim, n, bc, theta):
+    """The coarsest-level solve (App. C) with the default 8 sweeps, which the
+    library applies as the precomputed matrix of those sweeps, and with
+    another count, which it sweeps, both match the oracle's sweeps: FP64 to
+    1e-10, FP32 to 1e-4."""
+    pr = _problem(dim, n, bc, theta, seed=6)
+    g = Grid(dim, pr.n, pr.h, pr.bc)
+    P = Preconditioner(g, pr.rho, pr.mu, pr.theta, 1, ncoarse=ncoarse)
+    rng = np.random.default_rng(13)
+    b = rng.standard_normal(g.size) * g.active
+    ref = P(b)
+    solver = _make(S, pr)
+    for precision, tol in ((0, 1e-10), (1, 1e-4)):
+        x_u, x_p = solver.apply_preconditioner(1, *_split(g, b), precision=precision, ncoarse=ncoarse)
+        got = _join(g, x_u, x_p)
+        assert np.abs(got - ref).max() <= tol * np.abs(ref).max(), (precision, np.abs(got - ref).max())
+    solver.close()
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_solve_with_repeated_cycles(S, precision):
     """GMRES with two V-cycles per subsolve on the 32^2 periodic workload:
