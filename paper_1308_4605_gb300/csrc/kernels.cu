@@ -750,7 +750,7 @@ void launch_convert(int n, const TA* a, TB* b, cudaStream_t s) {
 }
 
 void launch_convert_coefficients(const Geom& g, Coef<double> C, Coef<float> F, cudaStream_t s) {
-    // F.diag_u stays null: the FP32 kernels form the diagonal on the fly
+    // F.diag_u stays null: the FP32 residual forms the diagonal on the fly
     launch_convert(g.nvel, C.alpha, F.alpha, s);
     launch_convert(g.nvel, C.beta, F.beta, s);
     launch_convert(g.ncell, C.mu2_c, F.mu2_c, s);

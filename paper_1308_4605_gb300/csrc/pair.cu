@@ -47,7 +47,6 @@ template <int DIM, int A, typename T, int TXC, int TY, int TZ, bool BULK>
 __global__ void __launch_bounds__(TXC * TY * TZ)
 k_vel_gs_pair(Geom g, Coef<T> C, const T* src, T* dst, const T* __restrict__ rhs) {
     pdl_entry();
-    constexpr bool F32 = sizeof(T) == 4;
     constexpr int NT = TXC * TY * TZ;
     constexpr int WX = 2 * TXC + 2, WY = TY + 2, WZ = DIM == 3 ? TZ + 2 : 1;
     __shared__ T R[WZ][WY][WX];
@@ -81,9 +80,9 @@ k_vel_gs_pair(Geom g, Coef<T> C, const T* src, T* dst, const T* __restrict__ rhs
             T v = T(0);
             if (!wall_face(g, A, q)) {
                 T dsum;
-                const T N = visc_offdiag_acc<DIM, A, T, F32, BULK>(g, C, q, aidx, ga, pb, dsum);
+                const T N = visc_offdiag_acc<DIM, A, T, false, BULK>(g, C, q, aidx, ga, pb, dsum);
                 const int f = fidx(g, A, q);
-                v = vel_gs_value<T>(g, C, f, N, dsum, rhs);
+                v = vel_gs_value<T>(g, C, f, N, rhs);
                 const bool inner = lx >= 1 && lx <= 2 * TXC && ux < e0 && ly >= 1 && ly <= TY &&
                                    uy < e1 && (DIM == 2 || (lz >= 1 && lz <= TZ && uz < e2));
                 if (inner) dst[f] = v;
@@ -112,9 +111,9 @@ k_vel_gs_pair(Geom g, Coef<T> C, const T* src, T* dst, const T* __restrict__ rhs
     const T* Rf = &R[0][0][0];
     auto ga = [&](int i) { return Rf[i]; };
     T dsum;
-    const T N = visc_offdiag_acc<DIM, A, T, F32, BULK>(g, C, q, aidx, ga, pb, dsum);
+    const T N = visc_offdiag_acc<DIM, A, T, false, BULK>(g, C, q, aidx, ga, pb, dsum);
     const int f = fidx(g, A, q);
-    dst[f] = vel_gs_value<T>(g, C, f, N, dsum, rhs);
+    dst[f] = vel_gs_value<T>(g, C, f, N, rhs);
 }
 
 // Cells.  Tile: 2 TXC cells along x, TY along y, TZ along z (3D).

@@ -279,9 +279,9 @@ double bytes_vel_colour(const Geom& g, int a) {
     double e = 0;
     for (int b = 0; b < g.dim; ++b)
         if (b != a) e += g.esize[a + b - 1];
-    // half of comp a: rhs, alpha, invd read and phi written; phi of all
+    // half of comp a: rhs and invd read and phi written; phi of all
     // components, mu2_c and the edge viscosities of comp a read
-    return sizeof(T) * (2.0 * g.fsize[a] + g.nvel + g.ncell + e);
+    return sizeof(T) * (1.5 * g.fsize[a] + g.nvel + g.ncell + e);
 }
 template <typename T>
 double bytes_vel_residual(const Geom& g) {   // phi, rhs, alpha read; res written
@@ -292,26 +292,25 @@ double bytes_cell_colour(const Geom& g) {    // half: rhs, invd, write; phi, bet
     return sizeof(T) * (1.5 * g.ncell + g.ncell + g.nvel);
 }
 // The colours of the first sweep from zero read only what is not known to be
-// zero (k_vel_gs with its zero mask): the half of comp a (rhs, alpha or the
-// inverse diagonal, phi written) always; phi_a unless its other colour is
-// still zero; phi_b of the components already swept; mu2_c and the edge
-// viscosities wherever a term or (FP32) the diagonal needs them.
+// zero (k_vel_gs with its zero mask): the half of comp a (rhs and the
+// inverse diagonal read, phi written) always; phi_a unless its other colour
+// is still zero; phi_b of the components already swept; mu2_c and the edge
+// viscosities wherever a term needs them.
 template <typename T>
 double bytes_vel_first(const Geom& g, int a, int parity) {
-    const bool f32 = sizeof(T) == 4;
     const bool za = parity == 0;
-    double w = 2.0 * g.fsize[a] + (za ? 0.0 : g.fsize[a]) + ((za && !f32) ? 0.0 : g.ncell);
+    double w = 1.5 * g.fsize[a] + (za ? 0.0 : g.fsize[a] + g.ncell);
     for (int b = 0; b < g.dim; ++b) {
         if (b == a) continue;
         const bool zb = b > a;
         if (!zb) w += g.fsize[b];
-        if (!(za && zb) || f32) w += g.esize[a + b - 1];
+        if (!(za && zb)) w += g.esize[a + b - 1];
     }
     return sizeof(T) * w;
 }
 template <typename T>
-double bytes_cell_first(const Geom& g) {   // red from zero: rhs, invd half, write half (FP32: beta all)
-    return sizeof(T) * (sizeof(T) == 8 ? 1.5 * g.ncell : 1.0 * g.ncell + g.nvel);
+double bytes_cell_first(const Geom& g) {   // red from zero: rhs, invd half, write half
+    return sizeof(T) * 1.5 * g.ncell;
 }
 // kernels of one stress-based operator or residual evaluation: cells, one
 // per edge family, faces
@@ -382,7 +381,7 @@ double bytes_vel_pair(const Geom& g, int a) {
     double e = 0;
     for (int b = 0; b < g.dim; ++b)
         if (b != a) e += g.esize[a + b - 1];
-    // comp a: rhs, alpha (or inverse diagonal) read and phi written; phi of
+    // comp a: rhs and the inverse diagonal read and phi written; phi of
     // all components, mu2_c and the edge viscosities of comp a read
     return sizeof(T) * (3.0 * g.fsize[a] + g.nvel + g.ncell + e);
 }

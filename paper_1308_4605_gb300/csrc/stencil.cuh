@@ -325,9 +325,7 @@ __device__ __forceinline__ T poisson_offdiag_acc(const Geom& g, const Coef<T>& C
 // index per array and constant strides; the periodic seam and the clamped
 // wall neighbour (itself, with beta = 0) are branch-free corrections.  Same
 // arithmetic order as poisson_offdiag_acc, so the same rounding.
-// Z: every neighbour is known to be zero (the first colour of a sweep from a
-// zero initial guess); N is then zero and only bsum is formed.
-template <int DIM, typename T, typename TV, bool Z = false>
+template <int DIM, typename T, typename TV>
 __device__ __forceinline__ T poisson_offdiag_h2(const Geom& g, const Coef<T>& C, const int q[3],
                                                 int c, const TV* phi, T& bsum) {
     T N = T(0);
@@ -340,14 +338,12 @@ __device__ __forceinline__ T poisson_offdiag_h2(const Geom& g, const Coef<T>& C,
         const int sf = a == 0 ? 1 : (a == 1 ? g.fe[a][0] : g.fe[a][0] * g.fe[a][1]);
         const int fl = fidx(g, a, q);
         const int fh = fl + ((g.per[a] && top) ? 1 - na : 1) * sf;
+        const int ch = c + (top ? (g.per[a] ? 1 - na : 0) : 1) * sc;
+        const int cl = c - (bot ? (g.per[a] ? 1 - na : 0) : 1) * sc;
         const T bh = ld(C.beta + fh);
         const T bl = ld(C.beta + fl);
-        if (!Z) {
-            const int ch = c + (top ? (g.per[a] ? 1 - na : 0) : 1) * sc;
-            const int cl = c - (bot ? (g.per[a] ? 1 - na : 0) : 1) * sc;
-            N = fma(bh, T(phi[ch]), N);
-            N = fma(bl, T(phi[cl]), N);
-        }
+        N = fma(bh, T(phi[ch]), N);
+        N = fma(bl, T(phi[cl]), N);
         bsum += bh + bl;
         sc *= na;
     }
@@ -380,25 +376,22 @@ __device__ __forceinline__ T poisson_cell(const Geom& g, const Coef<T>& C, const
 
 // ---------------------------------------------------------- per-point updates
 // Gauss-Seidel update phi += D^{-1}(rhs - A phi) of the interior A-face q
-// (App. C, omega = 1).  FP32 forms the diagonal on the fly; FP64 loads the
-// stored inverse diagonal (an FP64 division costs more than the load).
+// (App. C, omega = 1) with the stored inverse diagonal of the level's
+// precision (FP32: the FP64 inverse rounded): a load in place of forming
+// the diagonal and dividing.
 template <typename T>
-__device__ __forceinline__ T vel_gs_value(const Geom& g, const Coef<T>& C, int f, T N, T dsum,
-                                          const T* rhs) {
-    const T ih2 = gih2<T>(g);
-    const T num = fma(ih2, N, rhs[f]);
-    if constexpr (sizeof(T) == 4) return num / fma(ih2, dsum, ld(C.alpha + f));
-    else return num * ld(C.invd_u + f);
+__device__ __forceinline__ T vel_gs_value(const Geom& g, const Coef<T>& C, int f, T N, const T* rhs) {
+    const T num = fma(gih2<T>(g), N, rhs[f]);
+    return num * ld(C.invd_u + f);
 }
 
 template <int DIM, int A, typename T, bool BULK = false, int ZM = 0>
 __device__ __forceinline__ void vel_gs_point(const Geom& g, const Coef<T>& C, const int q[3],
                                              T* phi, const T* rhs) {
-    constexpr bool F32 = sizeof(T) == 4;
     T dsum;
-    const T N = visc_offdiag_h2<DIM, A, T, T, F32, BULK, ZM>(g, C, q, phi, dsum);
+    const T N = visc_offdiag_h2<DIM, A, T, T, false, BULK, ZM>(g, C, q, phi, dsum);
     const int f = fidx(g, A, q);
-    phi[f] = vel_gs_value<T>(g, C, f, N, dsum, rhs);
+    phi[f] = vel_gs_value<T>(g, C, f, N, rhs);
 }
 
 template <int DIM, typename T, bool BULK = false>
@@ -501,12 +494,10 @@ __device__ __forceinline__ T vel_prolong_point(const Geom& gc, const int q[3],
 }
 
 template <typename T>
-__device__ __forceinline__ T cell_gs_update(const Geom& g, const Coef<T>& C, int c, T N, T bsum,
+__device__ __forceinline__ T cell_gs_update(const Geom& g, const Coef<T>& C, int c, T N,
                                             const T* rhs) {
-    const T ih2 = gih2<T>(g);
-    const T num = fma(-ih2, N, rhs[c]);   // (rhs - off-diagonal part) / diag
-    if constexpr (sizeof(T) == 4) return num / (-ih2 * bsum);
-    else return num * ld(C.invd_p + c);
+    const T num = fma(-gih2<T>(g), N, rhs[c]);   // (rhs - off-diagonal part) / diag
+    return num * ld(C.invd_p + c);
 }
 
 template <int DIM, typename T, typename PC>
@@ -514,20 +505,20 @@ __device__ __forceinline__ T cell_gs_value(const Geom& g, const Coef<T>& C, cons
                                            const PC& pc, const T* rhs) {
     T bsum;
     const T N = poisson_offdiag_acc<DIM, T>(g, C, q, pc, bsum);
-    return cell_gs_update<T>(g, C, cidx(g, q), N, bsum, rhs);
+    return cell_gs_update<T>(g, C, cidx(g, q), N, rhs);
 }
 
 template <int DIM, typename T, bool Z = false>
 __device__ __forceinline__ void cell_gs_point(const Geom& g, const Coef<T>& C, const int q[3],
                                               T* phi, const T* rhs) {
     const int c = cidx(g, q);
-    if (Z && sizeof(T) == 8) {   // FP64: the inverse diagonal is stored; no beta needed
-        phi[c] = cell_gs_update<T>(g, C, c, T(0), T(0), rhs);
+    if (Z) {   // every neighbour zero: no beta needed either
+        phi[c] = cell_gs_update<T>(g, C, c, T(0), rhs);
         return;
     }
     T bsum;
-    const T N = poisson_offdiag_h2<DIM, T, T, Z>(g, C, q, c, phi, bsum);
-    phi[c] = cell_gs_update<T>(g, C, c, N, bsum, rhs);
+    const T N = poisson_offdiag_h2<DIM, T, T>(g, C, q, c, phi, bsum);
+    phi[c] = cell_gs_update<T>(g, C, c, N, rhs);
 }
 
 template <int DIM, typename T>
