@@ -6,10 +6,11 @@
 // The per-face stencil (stencil.cuh) recomputes each edge stress for every
 // face that touches the edge (four of them) and each normal stress for both
 // faces of a cell.  On GB300 the FP64 operator is bound by the FP64 pipe, so
-// computing each stress once (21 FP64 operations per cell, then 9 per face)
-// instead of about 20 per face is worth the extra stores and loads of the
-// stress arrays.  Stresses are kept scaled by h (differences, not
-// derivatives); the momentum rows then carry 1/h^2.
+// computing each stress once (a few FP64 operations per cell and edge, then
+// 6 to 7 per face) instead of about 20 per face is worth the extra stores
+// and loads of the stress arrays.  Shear stresses are kept scaled by h
+// (differences, not derivatives) and the momentum rows carry their 1/h^2;
+// for the operator the cell values already include 1/h^2 and the pressure.
 //
 // Conventions as in stencil.cuh: wall faces hold the prescribed normal
 // velocity (zero for the homogeneous problem); a no-slip wall's tangential
@@ -35,8 +36,12 @@ __device__ __forceinline__ void unflat(int t, const int e[3], int q[3]) {
 
 // Normal stresses tau_aa = 2 mu (u_a[c + e_a] - u_a[c]) (+ lam div u with bulk
 // viscosity) and, when ycell is given, the continuity rows ycell_c = -(D u)_c
-// (or bcell_c + (D u)_c).
-template <int DIM, bool BULK>
+// (or bcell_c + (D u)_c).  PRES (the operator): the cell values are the full
+// normal components of the stress divided by h, tau_aa / h^2 - p / h, so that
+// a momentum row takes the pressure gradient and the 1/h^2 scaling of the
+// normal stresses with them (two operations per cell instead of three per
+// face).
+template <int DIM, bool BULK, bool PRES>
 __global__ void __launch_bounds__(ST) k_stress_cells(Geom g, Coef<double> C, const double* __restrict__ x,
                                                      const double* __restrict__ bcell,
                                                      double* __restrict__ ycell,
@@ -57,11 +62,20 @@ __global__ void __launch_bounds__(ST) k_stress_cells(Geom g, Coef<double> C, con
     const double d1 = dif(std::integral_constant<int, 1>{});
     const double d2 = DIM == 3 ? dif(std::integral_constant<int, 2>{}) : 0.0;
     const double div = DIM == 3 ? d0 + d1 + d2 : d0 + d1;
-    const double m2 = ld(C.mu2_c + t);
-    const double lam = BULK ? ld(C.lam_c + t) : 0.0;
-    tau0[t] = BULK ? fma(lam, div, m2 * d0) : m2 * d0;
-    tau1[t] = BULK ? fma(lam, div, m2 * d1) : m2 * d1;
-    if (DIM == 3) tau2[t] = BULK ? fma(lam, div, m2 * d2) : m2 * d2;
+    if (PRES) {
+        const double m2 = ld(C.mu2_c + t) * g.ih2;
+        double base = -g.ih * x[g.nvel + t];
+        if (BULK) base = fma(ld(C.lam_c + t) * g.ih2, div, base);
+        tau0[t] = fma(m2, d0, base);
+        tau1[t] = fma(m2, d1, base);
+        if (DIM == 3) tau2[t] = fma(m2, d2, base);
+    } else {
+        const double m2 = ld(C.mu2_c + t);
+        const double lam = BULK ? ld(C.lam_c + t) : 0.0;
+        tau0[t] = BULK ? fma(lam, div, m2 * d0) : m2 * d0;
+        tau1[t] = BULK ? fma(lam, div, m2 * d1) : m2 * d1;
+        if (DIM == 3) tau2[t] = BULK ? fma(lam, div, m2 * d2) : m2 * d2;
+    }
     if (ycell) ycell[t] = bcell ? fma(g.ih, div, bcell[t]) : -g.ih * div;
 }
 
@@ -99,15 +113,20 @@ __global__ void __launch_bounds__(ST) k_stress_edges(Geom g, Coef<double> Cf, co
     tau[t] = m * (edge_diff<A, B>(g, q, x) + edge_diff<B, A>(g, q, x));   // m = 0: zero
 }
 
-// Momentum row of the interior A-face q.  MODE 0: y = alpha u - L u / h^2 + G p
-// (or b - that); MODE 1: r = rhs - alpha u + L u / h^2.
+// Momentum row of the interior A-face q.  MODE 0 (cell values from PRES):
+// y = alpha u - (div of the stress, pressure included) (or b - that);
+// MODE 1: r = rhs - alpha u + L u / h^2.
 template <int DIM, int A, int MODE>
 __device__ __forceinline__ double face_row(const Geom& g, const Coef<double>& C, const int q[3], int f,
                                            const double* x, const double* tca, const double* te0,
                                            const double* te1, const double* te2, const double* bb) {
     int qm[3] = {q[0], q[1], q[2]};
     qm[A] = step(g, A, q[A], -1);
-    double L = tca[cidx(g, q)] - tca[cidx(g, qm)];
+    const double tn = tca[cidx(g, q)] - tca[cidx(g, qm)];
+    // MODE 0: L holds the shear part alone (differences across the face's
+    // edges); MODE 1: normal and shear parts
+    double L = tn;
+    bool first = true;
 #pragma unroll
     for (int Bx = 0; Bx < DIM; ++Bx) {
         if (Bx == A) continue;
@@ -115,13 +134,14 @@ __device__ __forceinline__ double face_row(const Geom& g, const Coef<double>& C,
         const double* te = p == 0 ? te0 : (p == 1 ? te1 : te2);
         int qe[3] = {q[0], q[1], q[2]};
         qe[Bx] = g.per[Bx] ? wrapm(q[Bx] + 1, g.n[Bx]) : q[Bx] + 1;
-        L += te[eidx(g, p, qe)] - te[eidx(g, p, q)];
+        const double de = te[eidx(g, p, qe)] - te[eidx(g, p, q)];
+        L = (MODE == 0 && first) ? de : L + de;
+        first = false;
     }
     const double u = x[f];
     if (MODE == 0) {
-        double Mx = g.ih * (x[g.nvel + cidx(g, q)] - x[g.nvel + cidx(g, qm)]);
-        Mx = fma(-g.ih2, L, Mx);
-        Mx = fma(ld(C.alpha + f), u, Mx);
+        const double Lf = fma(g.ih2, L, tn);   // the stress divergence, -grad p included
+        const double Mx = fma(ld(C.alpha + f), u, -Lf);
         return bb ? bb[f] - Mx : Mx;
     }
     return fma(g.ih2, L, fma(-ld(C.alpha + f), u, bb[f]));
@@ -158,15 +178,16 @@ __global__ void __launch_bounds__(ST) k_stress_faces(Geom g, Coef<double> C, int
 
 inline int nb(long long n) { return (int)((n + ST - 1) / ST); }
 
+template <bool PRES>
 void stress_pass(const Geom& g, Coef<double> C, const StressWork& W, const double* x,
                  const double* bcell, double* ycell, cudaStream_t s) {
     const bool bulk = C.lam_c != nullptr;
     if (g.dim == 2)
-        launch_pdl(bulk ? k_stress_cells<2, true> : k_stress_cells<2, false>, dim3(nb(g.ncell)), dim3(ST), s,
-                   g, C, x, bcell, ycell, W.tc[0], W.tc[1], W.tc[2]);
+        launch_pdl(bulk ? k_stress_cells<2, true, PRES> : k_stress_cells<2, false, PRES>, dim3(nb(g.ncell)),
+                   dim3(ST), s, g, C, x, bcell, ycell, W.tc[0], W.tc[1], W.tc[2]);
     else
-        launch_pdl(bulk ? k_stress_cells<3, true> : k_stress_cells<3, false>, dim3(nb(g.ncell)), dim3(ST), s,
-                   g, C, x, bcell, ycell, W.tc[0], W.tc[1], W.tc[2]);
+        launch_pdl(bulk ? k_stress_cells<3, true, PRES> : k_stress_cells<3, false, PRES>, dim3(nb(g.ncell)),
+                   dim3(ST), s, g, C, x, bcell, ycell, W.tc[0], W.tc[1], W.tc[2]);
     launch_pdl(k_stress_edges<0>, dim3(nb(g.esize[0])), dim3(ST), s, g, C, x, W.te[0]);
     if (g.dim == 3) {
         launch_pdl(k_stress_edges<1>, dim3(nb(g.esize[1])), dim3(ST), s, g, C, x, W.te[1]);
@@ -193,13 +214,13 @@ void face_pass(const Geom& g, Coef<double> C, const StressWork& W, const double*
 
 void launch_stokes_matvec_stress(const Geom& g, Coef<double> C, const StressWork& W, const double* x,
                                  const double* b, double* y, cudaStream_t s) {
-    stress_pass(g, C, W, x, b ? b + g.nvel : nullptr, y + g.nvel, s);
+    stress_pass<true>(g, C, W, x, b ? b + g.nvel : nullptr, y + g.nvel, s);
     face_pass<0>(g, C, W, x, b, y, -1, s);
 }
 
 void launch_vel_residual_stress(const Geom& g, Coef<double> C, const StressWork& W, const double* phi,
                                 const double* rhs, double* res, bool after_sweep, cudaStream_t s) {
-    stress_pass(g, C, W, phi, nullptr, nullptr, s);
+    stress_pass<false>(g, C, W, phi, nullptr, nullptr, s);
     face_pass<1>(g, C, W, phi, rhs, res, after_sweep ? g.dim - 1 : -1, s);
 }
 
