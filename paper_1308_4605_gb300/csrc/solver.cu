@@ -362,13 +362,12 @@ struct MGParams {
 
 // Floating-point operations of one Gauss-Seidel point update (adds + muls +
 // 2 x fmas), counted with ncu (sm__sass_thread_inst_executed_op_*) on the
-// 3D kernels: FP64 velocity 24 (18 instructions), FP32 velocity 44 (the FP32
-// division is a short FMA sequence), FP64 cell 15; the 2D velocity stencil
-// has one transverse axis instead of two (8 fewer operations).
+// 3D kernels: velocity 24 (FP64: 18 instructions), cell 15, in both
+// precisions (both multiply by the stored inverse diagonal); the 2D velocity
+// stencil has one transverse axis instead of two (8 fewer operations).
 template <typename T>
 double flops_vel_point(int dim) {
-    if (sizeof(T) == 8) return dim == 3 ? 24.0 : 16.0;
-    return dim == 3 ? 44.0 : 36.0;
+    return dim == 3 ? 24.0 : 16.0;
 }
 double updated_faces(const Geom& g, int a) {   // unknown a-faces of one colour
     double n = double(g.fe[a][0]) * g.fe[a][1] * g.fe[a][2];
@@ -431,7 +430,7 @@ void cell_sweeps(stk_handle* h, int l, int nsweep, T* phi, const T* rhs, cudaStr
     const Level& L = h->lev[l];
     Coef<T> C = coef_of<T>(L);
     const bool fine = l == 0;
-    const double fl = (sizeof(T) == 8 ? 15.0 : 40.0) * 0.5 * L.g.ncell;
+    const double fl = 15.0 * 0.5 * L.g.ncell;
     int it = 0;
     if (l >= lpair_of<T>(h)) {
         T* buf[2] = {phi, work_of<T>(L).alt_p};
