@@ -170,10 +170,16 @@ FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (an FMA probe measured 1.20 
 FP64_INSTR_PER_FLOP = 18.0 / 24.0
 
 
-def traffic_per_launch(family, form):
+TRAFFIC_WORKLOAD = "3d_unsteady_periodic_128^3"   # the workload the ncu summary covers
+
+
+def traffic_per_launch(family, form, workload):
     """DRAM bytes per launch of `family` from the committed ncu summary, or
-    None when the kernel sources changed since the counters were taken."""
+    None when the kernel sources changed since the counters were taken or
+    the workload is not the one the counters were taken on."""
     import hashlib
+    if workload != TRAFFIC_WORKLOAD:
+        return None
     h = hashlib.sha256()
     for f in ("stencil.cuh", "kernels.cu", "pair.cu"):
         with open(os.path.join(ROOT, "paper_1308_4605_gb300", "csrc", f), "rb") as fh:
@@ -190,7 +196,7 @@ def traffic_per_launch(family, form):
     return None
 
 
-def roofline_of(fams, form, peaks, family=None):
+def roofline_of(fams, form, peaks, family=None, workload=TRAFFIC_WORKLOAD):
     """Roofline of the dominant kernel family of a solve (largest device
     time), or of `family`.  FP64 Gauss-Seidel kernels are bound by the FP64 pipe (about 0.19
     FLOP per byte, at the GB300 balance of 1.25 TFLOP/s over 6.8 TB/s, with
@@ -200,7 +206,7 @@ def roofline_of(fams, form, peaks, family=None):
         next(f for f in fams if f["name"] == family)
     secs = dom["ms"] * 1e-3
     per_launch_us = dom["ms"] * 1e3 / dom["launches"]
-    traffic = traffic_per_launch(dom["name"], form) if dom["name"].endswith("_l0") else None
+    traffic = traffic_per_launch(dom["name"], form, workload) if dom["name"].endswith("_l0") else None
     hbm = peaks.get("hbm_gbs")
     if form == "fp64" and dom["flops"] > 0:
         achieved = dom["flops"] / secs / 1e12
@@ -434,11 +440,12 @@ def run_ours(args):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    roofline = roofline_of(fam64, "fp64", peaks)
-    roofline_mixed = roofline_of(fam_mx, "mixed", peaks)
+    wl_name = cfg["workload"]
+    roofline = roofline_of(fam64, "fp64", peaks, workload=wl_name)
+    roofline_mixed = roofline_of(fam_mx, "mixed", peaks, workload=wl_name)
     # the level-0 FP32 smoother: the mixed form's bandwidth-bound kernel (the
     # dominant family above is latency-bound work on the small levels)
-    roofline_mixed_l0 = roofline_of(fam_mx, "mixed", peaks, "vel_smooth_colour_l0") \
+    roofline_mixed_l0 = roofline_of(fam_mx, "mixed", peaks, "vel_smooth_colour_l0", wl_name) \
         if any(f["name"] == "vel_smooth_colour_l0" for f in fam_mx) else None
 
     def fam_table(fams, total):

@@ -1,0 +1,31 @@
+"""bench.py's roofline bookkeeping on CPU: the DRAM traffic figures of the
+committed ncu summary apply only to the workload they were taken on and
+only while the smoother sources hash to the recorded value."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_traffic_only_for_its_workload():
+    for form in ("fp64", "mixed"):
+        t = bench.traffic_per_launch("vel_smooth_colour_l0", form, bench.TRAFFIC_WORKLOAD)
+        assert t is None or t > 0
+        assert bench.traffic_per_launch("vel_smooth_colour_l0", form, "bubble_2d_r100_steady_512^2") is None
+    assert bench.traffic_per_launch("no_such_family", "fp64", bench.TRAFFIC_WORKLOAD) is None
+
+
+def test_roofline_alu_and_hbm_fractions():
+    fams = [{"name": "vel_smooth_colour_l0", "launches": 10, "ms": 0.4, "bytes": 10 * 134217728.0,
+             "flops": 10 * 25165824.0},
+            {"name": "vel_residual", "launches": 2, "ms": 0.1, "bytes": 2e8, "flops": 0.0}]
+    peaks = {"hbm_gbs": 6790.3}
+    r = bench.roofline_of(fams, "fp64", peaks, workload="other")
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s" and r["traffic"] is None
+    assert abs(r["achieved"] - 10 * 25165824.0 / 0.4e-3 / 1e12) < 1e-12
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-15
+    m = bench.roofline_of(fams, "mixed", peaks, "vel_smooth_colour_l0", "other")
+    assert m["bound"] == "hbm" and m["peak"] == 6790.3
+    assert abs(m["achieved"] - 10 * 134217728.0 / 0.4e-3 / 1e9) < 1e-9
