@@ -362,12 +362,13 @@ struct MGParams {
 
 // Floating-point operations of one Gauss-Seidel point update (adds + muls +
 // 2 x fmas), counted with ncu (sm__sass_thread_inst_executed_op_*) on the
-// 3D kernels: velocity 24 (FP64: 18 instructions), cell 15, in both
+// 3D kernels: velocity FP64 22 (16 instructions), FP32 24, cell 15 in both
 // precisions (both multiply by the stored inverse diagonal); the 2D velocity
 // stencil has one transverse axis instead of two (8 fewer operations).
 template <typename T>
 double flops_vel_point(int dim) {
-    return dim == 3 ? 24.0 : 16.0;
+    const double f3 = sizeof(T) == 8 ? 22.0 : 24.0;
+    return dim == 3 ? f3 : f3 - 8.0;
 }
 double updated_faces(const Geom& g, int a) {   // unknown a-faces of one colour
     double n = double(g.fe[a][0]) * g.fe[a][1] * g.fe[a][2];
