@@ -189,3 +189,21 @@ def test_level_count():
     assert mg.n_levels(Grid(3, (128, 128, 128))) == 7
     assert mg.n_levels(Grid(2, (32, 32))) == 5
     assert mg.n_levels(Grid(2, (16, 4))) == 2
+
+
+@pytest.mark.parametrize("dim,n,bc", BCS)
+def test_coarse_solve_sweeps_are_a_fixed_matrix(dim, n, bc):
+    """The coarse solve (8 Gauss-Seidel sweeps from zero on the coarsest
+    level, App. C) is linear in its right-hand side: the matrix whose
+    columns are the sweeps applied to unit vectors reproduces the sweeps of
+    any right-hand side (the library applies the coarse solve this way)."""
+    g = Grid(dim, n, 1.0, bc)
+    lev = mg.build_hierarchy(g, _coef(g, 8))[-1]
+    gc = lev.grid
+    rng = np.random.default_rng(9)
+    for nun, sweep in ((gc.nvel, mg.gs_velocity), (gc.ncell, mg.gs_pressure)):
+        S = np.column_stack([sweep(lev, np.zeros(nun), e, 8) for e in np.eye(nun)])
+        r = rng.standard_normal(nun)
+        direct = sweep(lev, np.zeros(nun), r, 8)
+        assert np.abs(S @ r - direct).max() <= 1e-13 * max(1.0, np.abs(direct).max())
+        assert np.abs(direct).max() > 0.0
