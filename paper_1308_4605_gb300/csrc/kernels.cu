@@ -22,6 +22,7 @@ namespace {
 using namespace st;
 
 constexpr int TPB = 256;
+constexpr int SUBG = 4;   // faces per thread of k_sub_grad
 
 // plain decode (coefficient set-up only)
 __device__ __forceinline__ void decode(int t, const int e[3], int q[3]) {
@@ -37,12 +38,13 @@ struct Segs {
     int nseg;
 };
 
-inline Segs face_segs(const Geom& g, bool with_cells) {
+// per: faces handled by one thread
+inline Segs face_segs(const Geom& g, bool with_cells, int per = 1) {
     Segs s{};
     int b = 0;
     for (int a = 0; a < g.dim; ++a) {
         s.start[a] = b;
-        b += (g.fsize[a] + TPB - 1) / TPB;
+        b += (g.fsize[a] + TPB * per - 1) / (TPB * per);
     }
     s.nseg = g.dim;
     if (with_cells) {
@@ -240,6 +242,42 @@ __global__ void k_convert(int n, const TA* __restrict__ a, TB* __restrict__ b) {
     if (t < n) b[t] = TB(a[t]);
 }
 
+// 16-byte loads and stores of four consecutive elements (both arrays 16-byte
+// aligned): a streaming copy with one element per thread is latency-bound
+// well below HBM bandwidth; four per thread, in wide accesses, keep more
+// bytes in flight.
+__device__ __forceinline__ void ld4(const float* p, float v[4]) {
+    const float4 x = *reinterpret_cast<const float4*>(p);
+    v[0] = x.x, v[1] = x.y, v[2] = x.z, v[3] = x.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double v[4]) {
+    const double2 x = reinterpret_cast<const double2*>(p)[0];
+    const double2 y = reinterpret_cast<const double2*>(p)[1];
+    v[0] = x.x, v[1] = x.y, v[2] = y.x, v[3] = y.y;
+}
+__device__ __forceinline__ void st4(float* p, const float v[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double v[4]) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+template <typename TA, typename TB>
+__global__ void k_convert4(int n, const TA* __restrict__ a, TB* __restrict__ b) {
+    pdl_entry();
+    const long long i = 4LL * (blockIdx.x * (long long)blockDim.x + threadIdx.x);
+    if (i + 3 < n) {
+        TA v[4];
+        TB w[4];
+        ld4(a + i, v);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) w[k] = TB(v[k]);
+        st4(b + i, w);
+    } else {
+        for (long long k = i; k < n; ++k) b[k] = TB(a[k]);
+    }
+}
+
 // ----------------------------------------------------------------- Stokes matvec
 // y_u = alpha x_u - L_mu x_u + G x_p on unknown faces (0 on wall faces),
 // y_p = -D x_u on cells (Eq. Saddle_sys).
@@ -429,20 +467,30 @@ template <int DIM, typename T>
 __global__ void k_sub_grad(Geom g, Segs sg, const T* __restrict__ beta, const T* __restrict__ u,
                            const T* __restrict__ p, T* __restrict__ out) {
     pdl_entry();
+    // SUBG consecutive faces of one component per thread, all loads before
+    // the stores (more bytes in flight than one face per thread)
     int t;
-    int a = seg_of(sg, blockIdx.x, t);
-    if (t >= g.fsize[a]) return;
-    int q[3];
-    decode_face(g, a, t, q);
-    int f = g.foff[a] + t;
-    if (wall_face(g, a, q)) {
-        out[f] = T(0);
-        return;
+    const int a = seg_of(sg, blockIdx.x, t);
+    T v[SUBG];
+    int f[SUBG];
+#pragma unroll
+    for (int k = 0; k < SUBG; ++k) {
+        const int tk = t * SUBG + k;
+        f[k] = -1;
+        v[k] = T(0);
+        if (tk >= g.fsize[a]) continue;
+        int q[3];
+        decode_face(g, a, tk, q);
+        f[k] = g.foff[a] + tk;
+        if (wall_face(g, a, q)) continue;
+        int qm[3] = {q[0], q[1], q[2]};
+        qm[a] = step(g, a, q[a], -1);
+        const T grad = (p[cidx(g, q)] - p[cidx(g, qm)]) * gih<T>(g);
+        v[k] = u[f[k]] - (beta ? beta[f[k]] : T(1)) * grad;
     }
-    int qm[3] = {q[0], q[1], q[2]};
-    qm[a] = step(g, a, q[a], -1);
-    T grad = (p[cidx(g, q)] - p[cidx(g, qm)]) * gih<T>(g);
-    out[f] = u[f] - (beta ? beta[f] : T(1)) * grad;
+#pragma unroll
+    for (int k = 0; k < SUBG; ++k)
+        if (f[k] >= 0) out[f[k]] = v[k];
 }
 
 template <int DIM, typename T, bool BULK>
@@ -746,7 +794,10 @@ void launch_inverse_diagonals(const Geom& g, Coef<double> C, cudaStream_t s) {
 
 template <typename TA, typename TB>
 void launch_convert(int n, const TA* a, TB* b, cudaStream_t s) {
-    if (n > 0) launch_pdl(k_convert<TA, TB>, dim3(nblk(n)), dim3(TPB), s, n, a, b);
+    if (n <= 0) return;
+    const bool wide = ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15) == 0;
+    if (wide) launch_pdl(k_convert4<TA, TB>, dim3(nblk((n + 3) / 4)), dim3(TPB), s, n, a, b);
+    else launch_pdl(k_convert<TA, TB>, dim3(nblk(n)), dim3(TPB), s, n, a, b);
 }
 
 void launch_convert_coefficients(const Geom& g, Coef<double> C, Coef<float> F, cudaStream_t s) {
@@ -877,7 +928,7 @@ void launch_div_plus(const Geom& g, const T* u, const T* bp, T* bc, cudaStream_t
 
 template <typename T>
 void launch_sub_grad(const Geom& g, const T* beta, const T* u, const T* p, T* out, cudaStream_t s) {
-    Segs sg = face_segs(g, false);
+    Segs sg = face_segs(g, false, SUBG);
     if (g.dim == 2) launch_pdl(k_sub_grad<2, T>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, sg, beta, u, p, out);
     else launch_pdl(k_sub_grad<3, T>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, sg, beta, u, p, out);
 }
