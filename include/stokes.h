@@ -77,7 +77,11 @@ typedef struct {
     int    maxit;      /* maximum number of Arnoldi steps                           */
     int    precision;  /* STK_FP64 or STK_MIXED                                     */
     int    nu;         /* smoothing sweeps before and after the coarse correction (2) */
-    int    ncoarse;    /* sweeps on the coarsest level (8, App. C)                  */
+    int    ncoarse;    /* sweeps on the coarsest level (8, App. C).  The 8 sweeps
+                        * from zero are a fixed linear map; with at most 1024
+                        * coarsest unknowns it is formed at stk_set_coefficients
+                        * and applied as a matrix (the same map up to rounding);
+                        * other counts sweep                                      */
     int    vcycles_u;  /* V-cycles per velocity subsolve (1; 1..64): the first from
                         * zero, each further one on the residual, x += V(r - A x)
                         * (the number of multigrid cycles of Sec. 4.1.2)           */
