@@ -140,8 +140,8 @@ void launch_coarsen_coefficients(const Geom& gf, Coef<double> Cf, const Geom& gc
 void launch_inverse_diagonals(const Geom& g, Coef<double> C, cudaStream_t s);
 void launch_convert_coefficients(const Geom& g, Coef<double> C, Coef<float> Cf, cudaStream_t s);
 
-// y = M x (packed Stokes vectors); input precision TV, output double
-// The FP64 operator and the finest-level FP64 velocity residual evaluated
+// y = M x (packed Stokes vectors, FP64; y = b - M x when b is given) and the
+// finest-level FP64 velocity residual, evaluated
 // through stresses computed once per cell and edge (stress.cu); W holds the
 // scratch stress arrays of the finest level (cells: dim arrays of ncell;
 // edges: one array of esize[p] per pair p).
@@ -153,11 +153,6 @@ void launch_stokes_matvec_stress(const Geom& g, Coef<double> C, const StressWork
                                  const double* b, double* y, cudaStream_t s);
 void launch_vel_residual_stress(const Geom& g, Coef<double> C, const StressWork& W, const double* phi,
                                 const double* rhs, double* res, bool after_sweep, cudaStream_t s);
-template <typename TV>
-void launch_stokes_matvec(const Geom& g, Coef<double> C, const TV* x, double* y, cudaStream_t s);
-// r = b - M x
-void launch_stokes_residual(const Geom& g, Coef<double> C, const double* x, const double* b,
-                            double* r, cudaStream_t s);
 
 // multigrid (precision T)
 // first: this colour belongs to the first sweep from a zero initial guess

@@ -278,48 +278,6 @@ __global__ void k_convert4(int n, const TA* __restrict__ a, TB* __restrict__ b) 
     }
 }
 
-// ----------------------------------------------------------------- Stokes matvec
-// y_u = alpha x_u - L_mu x_u + G x_p on unknown faces (0 on wall faces),
-// y_p = -D x_u on cells (Eq. Saddle_sys).
-template <int DIM, typename TV, bool BULK>
-__global__ void k_stokes_matvec(Geom g, Coef<double> C, Segs sg, const TV* __restrict__ x,
-                                const double* __restrict__ b, double* __restrict__ y) {
-    pdl_entry();
-    int t;
-    int s = seg_of(sg, blockIdx.x, t);
-    int q[3];
-    const TV* xp = x + g.nvel;
-    if (s == DIM) {
-        if (t >= g.ncell) return;
-        decode_cell(g, t, q);
-        double div = 0.0;
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) {
-            int qh[3] = {q[0], q[1], q[2]};
-            qh[a] = step(g, a, q[a], 1);
-            div += (double(x[fidx(g, a, qh)]) - double(x[fidx(g, a, q)])) * g.ih;
-        }
-        int c = g.nvel + t;
-        y[c] = b ? b[c] + div : -div;
-        return;
-    }
-    if (t >= g.fsize[s]) return;
-    decode_face(g, s, t, q);
-    int f = g.foff[s] + t;
-    if (wall_face(g, s, q)) {
-        y[f] = 0.0;
-        return;
-    }
-    double dsum;
-    const double N = visc_offdiag_any<DIM, double, TV, false, BULK>(s, g, C, q, x, dsum);
-    int qm[3] = {q[0], q[1], q[2]};
-    qm[s] = step(g, s, q[s], -1);
-    double Mx = g.ih * (double(xp[cidx(g, q)]) - double(xp[cidx(g, qm)]));
-    Mx = fma(-g.ih2, N, Mx);
-    Mx = fma(ld(C.diag_u + f), double(x[f]), Mx);
-    y[f] = b ? b[f] - Mx : Mx;
-}
-
 // ------------------------------------------------------------------- multigrid
 // One colour of the staggered Gauss-Seidel smoother (App. C): every A-face
 // with (i + j + k) % 2 == parity gets phi += D^{-1} (rhs - A phi).
@@ -812,22 +770,6 @@ void launch_convert_coefficients(const Geom& g, Coef<double> C, Coef<float> F, c
     if (C.lam_c && F.lam_c) launch_convert(g.ncell, C.lam_c, F.lam_c, s);
 }
 
-template <typename TV>
-void launch_stokes_matvec(const Geom& g, Coef<double> C, const TV* x, double* y, cudaStream_t s) {
-    Segs sg = face_segs(g, true);
-    const bool bk = C.lam_c != nullptr;
-    if (g.dim == 2) launch_pdl(bk ? k_stokes_matvec<2, TV, true> : k_stokes_matvec<2, TV, false>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, x, nullptr, y);
-    else launch_pdl(bk ? k_stokes_matvec<3, TV, true> : k_stokes_matvec<3, TV, false>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, x, nullptr, y);
-}
-
-void launch_stokes_residual(const Geom& g, Coef<double> C, const double* x, const double* b,
-                            double* r, cudaStream_t s) {
-    Segs sg = face_segs(g, true);
-    const bool bk = C.lam_c != nullptr;
-    if (g.dim == 2) launch_pdl(bk ? k_stokes_matvec<2, double, true> : k_stokes_matvec<2, double, false>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, x, b, r);
-    else launch_pdl(bk ? k_stokes_matvec<3, double, true> : k_stokes_matvec<3, double, false>, dim3(sg.start[sg.nseg]), dim3(TPB), s, g, C, sg, x, b, r);
-}
-
 template <typename T>
 void launch_vel_gs_colour(const Geom& g, Coef<T> C, int comp, int parity, T* phi, const T* rhs,
                           cudaStream_t s, int tpb, bool first) {
@@ -1031,8 +973,6 @@ void launch_check_fields(int n, const double* rho, const double* mu, double* scr
     template void launch_sum<T>(int, const T*, double*, double*, cudaStream_t);                  \
     template void launch_sub_mean<T>(int, T*, double*, cudaStream_t);                            \
     template void launch_copy_sub_mean<T>(int, const T*, T*, double*, cudaStream_t);             \
-    template void launch_stokes_matvec<T>(const Geom&, Coef<double>, const T*, double*,          \
-                                          cudaStream_t);                                           \
     template void launch_axpy<T>(int, T, const T*, T*, cudaStream_t);                            \
     template void launch_zero<T>(int, T*, cudaStream_t);
 STK_INST(double)
