@@ -259,6 +259,9 @@ constexpr int KRY_BLOCKS = 1216;  // 8 x 152 SMs: grid of the Krylov kernels (kr
 constexpr int RED_SCRATCH = KRY_BLOCKS * 36;   // doubles of reduction scratch
 template <typename T>  // out[0] = sum x  (scratch >= RED_BLOCKS doubles)
 void launch_sum(int n, const T* x, double* scratch, double* out, cudaStream_t s);
+// out[0] = sum x for an FP32 vector, x 16-byte aligned (krylov.cu; scratch >=
+// KRY_BLOCKS doubles): wide loads, sums of four in FP32 widened once
+void launch_sum_f32x4(int n, const float* x, double* scratch, double* out, cudaStream_t s);
 template <typename T>  // x -= (*sum) / n    (sum[1] receives the mean)
 void launch_sub_mean(int n, T* x, double* sum, cudaStream_t s);
 template <typename T>  // out = in - (*sum)/n  (sum[1] receives the mean)

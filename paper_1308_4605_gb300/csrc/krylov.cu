@@ -173,7 +173,31 @@ PtrArr pack(const void* const* V, int k) {
     return pa;
 }
 
+// Partial sums of an FP32 vector (n % 4 == 0 handled by block 0's tail,
+// x 16-byte aligned): four elements per 16-byte load, summed in FP32 in a
+// fixed order and widened to FP64 once per four.  The widening runs on
+// GB300's FP64 pipe, so one per element made this pass FP64-bound; the
+// FP32 sum of four adds a relative rounding of about 2^-23 to each term,
+// below the FP32 data's own.
+__global__ void __launch_bounds__(KT) k_sum_f32x4(int n, const float* __restrict__ x, double* part) {
+    pdl_entry();
+    const int n4 = n >> 2;
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    double acc[1] = {0.0};
+    for (int i = blockIdx.x * KT + threadIdx.x; i < n4; i += KRY_BLOCKS * KT) {
+        const float4 v = x4[i];
+        acc[0] += double((v.x + v.y) + (v.z + v.w));
+    }
+    if (blockIdx.x == 0 && threadIdx.x < (n & 3)) acc[0] += double(x[4 * n4 + threadIdx.x]);
+    block_sums<1>(acc, part);
+}
+
 }  // namespace
+
+void launch_sum_f32x4(int n, const float* x, double* scratch, double* out, cudaStream_t s) {
+    launch_pdl(k_sum_f32x4, dim3(KRY_BLOCKS), dim3(KT), s, n, x, scratch);
+    launch_pdl(k_final_multi, dim3(1), dim3(KT), s, scratch, out);
+}
 
 #define STK_J_CASES(X) \
     X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) \

@@ -541,6 +541,19 @@ void vcycle_cell(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp,
     cell_sweeps<T>(h, l, mp.nu, phi, rhs, s);
 }
 
+// out[0] = sum x of a cell vector: FP32 vectors with 16-byte alignment
+// take the wide-load reduction, the rest the plain one
+template <typename T>
+void cell_sum(stk_handle* h, int n, const T* x, double* out, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
+            launch_sum_f32x4(n, reinterpret_cast<const float*>(x), h->red, out, s);
+            return;
+        }
+    }
+    launch_sum<T>(n, x, h->red, out, s);
+}
+
 // phi = L~_rho^{-1} (r - mean r): the Poisson right-hand side is projected
 // onto mean-zero vectors (the constant null space of L_rho, Sec. 3.2).
 template <typename T>
@@ -551,7 +564,7 @@ void poisson_solve(stk_handle* h, const T* r, T* phi, const MGParams& mp, cudaSt
     const int nc = L.g.ncell;
     {
         Scope sc(h, PF_MEAN, 2.0 * sizeof(T) * nc, s, 4);
-        launch_sum<T>(nc, r, h->red, h->dsc + DS_SUM, s);
+        cell_sum<T>(h, nc, r, h->dsc + DS_SUM, s);
         launch_copy_sub_mean<T>(nc, r, W.rhs_p, h->dsc + DS_SUM, s);
     }
     vcycle_cell<T>(h, 0, W.rhs_p, phi, mp, s);
@@ -564,7 +577,7 @@ void poisson_solve(stk_handle* h, const T* r, T* phi, const MGParams& mp, cudaSt
         }
         {
             Scope sc(h, PF_MEAN, 3.0 * sizeof(T) * nc, s, 4);
-            launch_sum<T>(nc, B.rp, h->red, h->dsc + DS_SUM + 4, s);
+            cell_sum<T>(h, nc, B.rp, h->dsc + DS_SUM + 4, s);
             launch_sub_mean<T>(nc, B.rp, h->dsc + DS_SUM + 4, s);
         }
         vcycle_cell<T>(h, 0, B.rp, B.dp, mp, s);
@@ -593,7 +606,7 @@ template <typename T>
 void remove_mean(stk_handle* h, T* x, cudaStream_t s) {
     const Level& L = h->lev[0];
     Scope sc(h, PF_MEAN, 3.0 * sizeof(T) * L.g.ncell, s, 4);
-    launch_sum<T>(L.g.ncell, x, h->red, h->dsc + DS_SUM + 2, s);
+    cell_sum<T>(h, L.g.ncell, x, h->dsc + DS_SUM + 2, s);
     launch_sub_mean<T>(L.g.ncell, x, h->dsc + DS_SUM + 2, s);
 }
 
