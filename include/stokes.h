@@ -283,7 +283,10 @@ int stk_autotune(stk_handle* h, int precision, stk_schedule* best, void* stream)
  * has families of its own.  Returns -1 when k is out of range. */
 #define STK_NPROF 24
 int stk_profile(stk_handle* h, int enable);
-/* Number of CUDA kernels this handle has launched since it was created. */
+/* Number of CUDA kernels this handle has launched since it was created:
+ * coefficient setup (stk_set_coefficients, stk_set_bulk_viscosity), solves,
+ * preconditioner and operator applications (graph replays count the kernels
+ * they contain). */
 long long stk_kernel_launches(const stk_handle* h);
 int stk_profile_read(stk_handle* h, int k, const char** name, long long* launches,
                      double* ms, double* bytes, double* flops);
