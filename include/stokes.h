@@ -229,6 +229,14 @@ int stk_backward_euler_rhs(stk_handle* h, const double* const* u_n, const double
 int stk_gradient(stk_handle* h, const double* const* u, const double* const* lambda,
                  double* dL_dlogmu, double* dL_drho, void* stream);
 
+/* y_p = x_p - mean(x_p): projection of a cell array onto mean-zero vectors,
+ * the complement of the constant-pressure null space of M (Sec. 3.2: the
+ * pressure is determined up to a constant with periodic, no-slip and
+ * free-slip boundaries, so a pressure right-hand side must have zero mean,
+ * e.g. the pressure part of an adjoint right-hand side).  x_p, y_p: device
+ * cell arrays; y_p may be x_p.  Stream-ordered, no synchronisation. */
+int stk_remove_mean(stk_handle* h, const double* x_p, double* y_p, void* stream);
+
 /* Batched solve: count independent systems, each on its own handle (any
  * grid size, boundary conditions and coefficients), solved together with
  * the same parameters.  The GMRES iterations of all instances advance in
@@ -296,24 +304,32 @@ int stk_profile_read(stk_handle* h, int k, const char** name, long long* launche
  * stk_pressure_vcycle.)  Callers whose device memory is wholly owned by another
  * allocator, or whose loop cannot afford the implicit synchronisation of
  * cudaMalloc, cannot create an stk_handle; this call needs none.  It computes
- * x_p = L~_rho^{-1} r_p, one V-cycle with zero initial guess for
- * D (1/rho_f) G x = r (App. C), exactly as stk_pressure_vcycle does on a handle
- * whose coefficients were set from the same rho, for the grid (dim, n, h, bc)
- * described as in stk_create.  rho, r_p (inputs) and x_p (output) are
- * caller-owned device cell arrays.
+ * x_p = L~_rho^{-1} r_p: one multigrid V-cycle with zero initial guess for the
+ * density-weighted Poisson equation div (1/rho_f) grad x = r (two red-black
+ * Gauss-Seidel sweeps before and after each coarse correction, eight on the
+ * coarsest grid), the same V-cycle as stk_pressure_vcycle on a handle whose
+ * coefficients were set from the same rho, equal to it up to rounding, for the
+ * grid (dim, n, h, bc) described as in stk_create.  rho, r_p (inputs) and x_p
+ * (output) are caller-owned device cell arrays.
  * Workspace: a file-scope device array of 2,097,152 doubles (16 MiB) that every
- * GPU loading this library holds until the process exits; grids needing more
+ * GPU using this call holds until the process exits; grids needing more
  * (about 6 doubles per cell: 2D up to 512^2, 3D up to 64^3 fit) are rejected
  * with STK_ERR_SIZE before any device work.  No cudaMalloc, cudaFree or other
- * allocating call is made.  The first call on each device looks up the
- * array's device address (with that device current), so make that first call
- * before any stream capture.  All calls on a device share that device's one
- * array and leave their workspace in it; each call writes every value it
- * later reads, so a call does not depend on what an earlier call left.  Calls
- * whose work overlaps on the same GPU (issued on different streams, or from
- * different host threads, without ordering between them) race on the array:
- * serialise them.  Returns STK_OK, STK_ERR_ARG, STK_ERR_SIZE or STK_ERR_CUDA
- * (no message is recorded for stk_last_error). */
+ * allocating call is made by the call itself, but with CUDA's lazy module
+ * loading (the default) the array and the code of the kernels it uses are
+ * placed in device memory during the first call on each device: make that
+ * first call (a warm-up on a small grid) before the caller's allocator
+ * reserves the device memory, and before any stream capture (it also looks
+ * up the array's device address, with that device current).  Later calls
+ * leave the device's free memory unchanged.  All calls on a device share that
+ * device's one array and leave their workspace in it; each call writes every
+ * value it later reads, so a call does not depend on what an earlier call
+ * left.  Calls whose work overlaps on the same GPU (issued on different
+ * streams, or from different host threads, without ordering between them)
+ * race on the array: serialise them.  Returns STK_OK, STK_ERR_ARG,
+ * STK_ERR_SIZE or STK_ERR_CUDA (also when a CUDA error from earlier work is
+ * already pending; it is left pending); no message is recorded for
+ * stk_last_error. */
 int stk_pressure_vcycle_noalloc(int dim, const int* n, double h, const int* bc,
                                 const double* rho, const double* r_p, double* x_p,
                                 void* stream);

@@ -39,9 +39,11 @@ class _StokesSolve(torch.autograd.Function):
         solver.set_coefficients(rho.contiguous(), mu.contiguous(), ctx.theta)
         g_u = [g.contiguous() if g is not None else torch.zeros_like(x_u[a])
                for a, g in enumerate(grads[:dim])]
-        g_p = grads[dim]
-        g_p = torch.zeros(solver.cell_shape(), dtype=torch.float64, device=log_mu.device) \
-            if g_p is None else (g_p - g_p.mean()).contiguous()
+        g_p = torch.zeros(solver.cell_shape(), dtype=torch.float64, device=log_mu.device)
+        if grads[dim] is not None:
+            # the pressure part of the adjoint right-hand side, projected onto
+            # mean-zero vectors (the pressure null space) by the library
+            S.stk_remove_mean(solver.handle, grads[dim].contiguous(), g_p)
         lam_u, lam_p, info = solver.solve(g_u, g_p, **ctx.opts)
         if not info["converged"]:
             raise S.StokesError(S.STK_ERR_NOT_CONVERGED, f"adjoint solve: {info}")

@@ -12,9 +12,20 @@
 // file-scope device array of fixed size.  Every GPU that loads this library
 // holds that array until the process exits.
 //
-// The arithmetic is that of stk_pressure_vcycle on a handle whose coefficients
-// were set with the same rho: the same kernels (kernels.cu) on the same
-// hierarchy, built here with the same formulas.
+// It runs the same V-cycle as stk_pressure_vcycle on a handle whose
+// coefficients were set with the same rho, equal to it up to rounding: the
+// smoothing, residual and transfer kernels are those of kernels.cu, while the
+// coefficient setup (k_na_fine_beta, k_na_coarse_beta, k_na_invdiag) is a
+// local copy of the same formulas that sums the diagonal in its own order, and
+// the coarsest level is swept 8 times (the handle applies those sweeps as a
+// precomputed matrix).  A change to the face coefficients or their coarsening
+// in kernels.cu must be mirrored here.
+//
+// With CUDA's lazy module loading (the default since CUDA 12.2) the scratch
+// array and the code of the kernels used here are placed in device memory
+// when the first call on a device runs, not when the library is loaded: a
+// caller whose allocator is about to reserve the device memory makes one
+// warm-up call first.
 #include "internal.cuh"
 #include "../../include/stokes.h"
 
@@ -171,6 +182,10 @@ extern "C" int stk_pressure_vcycle_noalloc(int dim, const int* n, double h, cons
                                            const double* rho, const double* r_p, double* x_p,
                                            void* stream) {
     if (dim != 2 && dim != 3) return STK_ERR_ARG;
+    // an error left pending by the caller's earlier work is reported as
+    // STK_ERR_CUDA and left in place (peeked, not cleared), so that the
+    // final check below sees only this call's launches
+    if (cudaPeekAtLastError() != cudaSuccess) return STK_ERR_CUDA;
     if (!n || !bc || !rho || !r_p || !x_p) return STK_ERR_ARG;
     if (!(h > 0.0) || !std::isfinite(h)) return STK_ERR_ARG;
     int nn[3] = {1, 1, 1}, bb[6] = {0, 0, 0, 0, 0, 0};
@@ -195,14 +210,17 @@ extern "C" int stk_pressure_vcycle_noalloc(int dim, const int* n, double h, cons
             if (nlev == kMaxLevels) return STK_ERR_SIZE;
             Geom g = na_geom(dim, cur, hl, bb);
             L[nlev].g = g;
-            // beta, invd, res, and phi, rhs below the finest level; every
-            // array starts on a 256-byte boundary (as carved below)
+            // beta, invd, res above the coarsest level, and phi, rhs below
+            // the finest level; every array starts on a 256-byte boundary
+            // (as carved below)
             auto rounded = [](long long c) { return (c + 31) & ~31LL; };
-            words += rounded(g.nvel) + 2 * rounded(g.ncell) + (nlev > 0 ? 2 * rounded(g.ncell) : 0);
-            ++nlev;
             int mn = cur[0];
             for (int a = 1; a < dim; ++a) mn = cur[a] < mn ? cur[a] : mn;
-            if (mn <= 2) break;
+            const bool coarsest = mn <= 2;
+            words += rounded(g.nvel) + rounded(g.ncell) + (coarsest ? 0 : rounded(g.ncell)) +
+                     (nlev > 0 ? 2 * rounded(g.ncell) : 0);
+            ++nlev;
+            if (coarsest) break;
             for (int a = 0; a < dim; ++a) cur[a] /= 2;
             hl *= 2.0;
         }
@@ -236,7 +254,7 @@ extern "C" int stk_pressure_vcycle_noalloc(int dim, const int* n, double h, cons
             L[l].C = stk::Coef<double>{};
             L[l].C.beta = take(g.nvel);
             L[l].C.invd_p = take(g.ncell);
-            L[l].res = take(g.ncell);
+            L[l].res = l + 1 < nlev ? take(g.ncell) : nullptr;   // coarsest: sweeps only
             L[l].phi = l > 0 ? take(g.ncell) : nullptr;
             L[l].rhs = l > 0 ? take(g.ncell) : nullptr;
         }

@@ -1802,6 +1802,21 @@ int stk_gradient(stk_handle* h, const double* const* u, const double* const* lam
     return STK_OK;
 }
 
+int stk_remove_mean(stk_handle* h, const double* x_p, double* y_p, void* stream) {
+    if (!h) return STK_ERR_ARG;
+    if (!x_p || !y_p) return fail(h, STK_ERR_ARG, "null pointer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(cudaSetDevice(h->device));
+    const int nc = h->lev[0].g.ncell;
+    {
+        Scope sc(h, PF_MEAN, 2.0 * sizeof(double) * nc, s, 4);
+        cell_sum<double>(h, nc, x_p, h->dsc + DS_SUM + 6, s);
+        launch_copy_sub_mean<double>(nc, x_p, y_p, h->dsc + DS_SUM + 6, s);
+    }
+    CKL();
+    return STK_OK;
+}
+
 int stk_profile_read(stk_handle* h, int k, const char** name, long long* launches, double* ms,
                      double* bytes, double* flops) {
     if (!h || k < 0 || k >= STK_NPROF) return -1;

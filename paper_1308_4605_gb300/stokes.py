@@ -99,6 +99,7 @@ def _load():
         "stk_autotune": (I, [P, I, ctypes.POINTER(stk_schedule), P]),
         "stk_solve_batched": (I, [I, ctypes.POINTER(P), ctypes.POINTER(stk_solver_params),
                                   ctypes.POINTER(stk_batch_io), ctypes.POINTER(stk_solve_info), P]),
+        "stk_remove_mean": (I, [P, P, P, P]),
         "stk_pressure_vcycle_noalloc": (I, [I, ctypes.POINTER(I), D, ctypes.POINTER(I), P, P, P, P]),
         "stk_profile_read": (I, [P, I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong),
                                  ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D)]),
@@ -114,7 +115,7 @@ _lib = _load()
 EXPORTED = ["stk_default_params", "stk_create", "stk_destroy", "stk_last_error", "stk_face_length",
             "stk_cell_length", "stk_set_coefficients", "stk_set_bulk_viscosity", "stk_apply_operator",
             "stk_apply_preconditioner", "stk_apply_preconditioner_params", "stk_velocity_vcycle", "stk_pressure_vcycle", "stk_solve",
-            "stk_profile", "stk_profile_read", "stk_kernel_launches", "stk_pressure_vcycle_noalloc", "stk_gradient", "stk_backward_euler_rhs", "stk_subtract_boundary_terms", "stk_solve_batched", "stk_get_schedule", "stk_set_schedule", "stk_autotune"]
+            "stk_profile", "stk_profile_read", "stk_kernel_launches", "stk_pressure_vcycle_noalloc", "stk_remove_mean", "stk_gradient", "stk_backward_euler_rhs", "stk_subtract_boundary_terms", "stk_solve_batched", "stk_get_schedule", "stk_set_schedule", "stk_autotune"]
 
 
 def library():
@@ -336,6 +337,11 @@ def stk_gradient(h, u, lam, dlogmu, drho, stream=None):
     fl, nc = _lengths(h, len(u))
     return _check(h, _lib.stk_gradient(h, _ptrs(u, fl), _ptrs(lam, fl), _ptr(dlogmu, nc), _ptr(drho, nc),
                                        _stream(stream)))
+
+
+def stk_remove_mean(h, x_p, y_p, stream=None):
+    nc = stk_cell_length(h)
+    return _check(h, _lib.stk_remove_mean(h, _ptr(x_p, nc), _ptr(y_p, nc), _stream(stream)))
 
 
 def stk_kernel_launches(h):

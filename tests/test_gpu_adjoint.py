@@ -192,3 +192,22 @@ def test_gradient_taylor_remainder(S):
     assert all(1.7 <= r <= 2.3 for r in r1), r1
     assert all(3.4 <= r <= 4.6 for r in r2), r2
     solver.close()
+
+
+@pytest.mark.parametrize("n,inplace", [((16, 8), False), ((64, 64), True), ((32, 16, 8), False)])
+def test_remove_mean(S, n, inplace):
+    """stk_remove_mean: y = x - mean(x) on a cell array (the projection the
+    adjoint applies to the pressure part of its right-hand side)."""
+    dim = len(n)
+    solver = S.StokesSolver(dim, n, (PERIODIC,) * (2 * dim), 1.0)
+    one = torch.ones(solver.cell_shape(), dtype=torch.float64, device=DEV)
+    solver.set_coefficients(one, one, 1.0)
+    x = np.random.default_rng(3).standard_normal(solver.cell_shape()) + 2.5
+    xt = _t(x)
+    y = xt if inplace else torch.empty_like(xt)
+    S.stk_remove_mean(solver.handle, xt, y)
+    ref = x - x.mean()
+    got = y.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+    assert abs(got.mean()) <= 1e-14 * np.abs(got).max() * 10
+    solver.close()

@@ -65,6 +65,27 @@ def test_no_alloc_matches_handle_on_two_calls_in_a_row(S):
     assert np.abs(again - refs[1]).max() <= 1e-12 * np.abs(refs[1]).max()
 
 
+def test_no_alloc_leaves_free_memory_unchanged(S):
+    """After a warm-up call (which, under lazy module loading, places the
+    workspace array and the kernels' code on the device), a call allocates
+    nothing: the device's free memory is the same before and after it."""
+    dev = torch.device("cuda", 0)
+    pr, r = _case(3, (32, 32, 32), (NOSLIP,) * 6, 3)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    rho, rr = t(pr.rho), t(r)
+    x = torch.zeros(pr.rho.shape, dtype=torch.float64, device=dev)
+    call = lambda: S.stk_pressure_vcycle_noalloc(pr.dim, pr.n[:3], pr.h, pr.bc[:6], rho, rr, x)
+    call()                                        # warm-up
+    torch.cuda.synchronize()
+    first = x.clone()
+    free0, _ = torch.cuda.mem_get_info(dev)
+    call()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(dev)
+    assert free1 == free0, (free0, free1)
+    assert torch.equal(x, first)
+
+
 def test_no_alloc_rejects_oversized_grids(S):
     """A 128^3 grid needs about 12.6M doubles of workspace, more than the
     2,097,152 of the array: rejected before any device work."""
