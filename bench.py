@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--n", type=int, default=0, help="override the grid size")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-others", action="store_true",
+                    help="skip the other configurations measured after the headline")
     ap.add_argument("--quick", action="store_true",
                     help="profiling runs: only the timed solves of --form, no baseline/e2e/profile passes")
     ap.add_argument("--form", default="both", choices=["both", "fp64", "mixed"])
@@ -226,81 +228,87 @@ def roofline_of(fams, form, peaks, family=None, workload=TRAFFIC_WORKLOAD):
 
 
 # --------------------------------------------------------------- oracle arm
-def oracle_time_to_solution(pr, gpu_iterations=None, budget_s=20.0):
-    """Time the FP64 CPU oracle on a bounded sample of the workload.
-
-    The sample is the same generator at the largest size whose setup and a
-    few GMRES(10) iterations fit the budget (64^3 for the 128^3 workload,
-    full size for small 2D workloads); the time to solution is
-    setup + iterations * time per iteration, scaled by the ratio of unknowns
-    to the full size.  Returns (ms, description, cores)."""
-    import numpy as np
+def oracle_solve_time(pr):
+    """Time the FP64 CPU oracle solving the workload `pr` as it stands:
+    sparse assembly of M, the preconditioner's multigrid hierarchy (setup),
+    then GMRES(10) from x = 0 to ||b - M x|| <= 1e-10 ||b|| with its own
+    iteration count.  Nothing is extrapolated: the value is the wall time of
+    that one solve.  scipy.sparse and numpy run single-threaded here.
+    Returns (ms, description, threads used)."""
     from oracle import assemble as asm
     from oracle import krylov
     from oracle.grid import Grid
     from oracle.precond import Preconditioner
-    from paper_1308_4605_gb300 import workloads as wl
-
-    full_unknowns = (pr.dim + 1) * int(np.prod(pr.n))
-    n_full = pr.n[0]
-    n = n_full
-    while n > 8 and (pr.dim + 1) * n ** pr.dim > (2_200_000 if pr.dim == 3 else 1_100_000):
-        n //= 2
-    if pr.name.startswith("3d_unsteady_periodic"):
-        spr = wl.config_c3(n)
-    elif pr.name.startswith("3d_steady_noslip"):
-        spr = wl.config_c5(n)
-    elif pr.name.startswith("2d_steady_noslip_inclusions"):
-        spr = wl.config_c2(n)
-    elif pr.name.startswith("2d_unsteady_periodic"):
-        spr = wl.config_c1(n)
-    else:
-        spr = pr if n == n_full else wl.bubble(pr.dim, n)
-    g = Grid(spr.dim, spr.n, spr.h, spr.bc)
+    g = Grid(pr.dim, pr.n, pr.h, pr.bc)
     t0 = time.perf_counter()
-    M = asm.stokes_from_fields(g, spr.rho, spr.mu, spr.theta)
-    P = Preconditioner(g, spr.rho, spr.mu, spr.theta, spr.precond)
+    M = asm.stokes_from_fields(g, pr.rho, pr.mu, pr.theta)
+    P = Preconditioner(g, pr.rho, pr.mu, pr.theta, pr.precond)
     t_setup = time.perf_counter() - t0
-    b = g.pack(spr.b_u, spr.b_p)
-    t0 = time.perf_counter()
-    if gpu_iterations:   # a few iterations; the count to solution is the GPU's
-        k = 3
-        _, info = krylov.gmres(lambda v: M @ v, P, b, rtol=1e-30, maxit=k)
-        iters, whose = gpu_iterations, "the GPU's count"
-    else:                # the oracle's own solve of the sample to 1e-10
-        _, info = krylov.gmres(lambda v: M @ v, P, b, rtol=1e-10, maxit=300)
-        k = iters = info["iterations"]
-        whose = "the oracle's count on the sample"
-    t_iter = (time.perf_counter() - t0) / max(info["iterations"], 1)
-    scale = full_unknowns / ((spr.dim + 1) * int(np.prod(spr.n)))
-    ms = (t_setup + iters * t_iter) * scale * 1e3
-    desc = (f"oracle (scipy.sparse, FP64) setup + {k} GMRES(10) iterations of the same generator at "
-            f"{'x'.join(map(str, spr.n[:spr.dim]))} ({t_setup:.1f} s setup, {t_iter:.2f} s/iteration), "
-            f"time to solution = setup + {iters} iterations ({whose}), scaled x{scale:.0f} to "
-            f"{'x'.join(map(str, pr.n[:pr.dim]))} unknowns")
+    b = g.pack(pr.b_u, pr.b_p)
+    b[~g.active] = 0.0
+    t1 = time.perf_counter()
+    _, info = krylov.gmres(lambda v: M @ v, P, b, rtol=1e-10, maxit=600)
+    t_solve = time.perf_counter() - t1
+    ms = (t_setup + t_solve) * 1e3
+    desc = (f"oracle (scipy.sparse, FP64, one thread) on the full "
+            f"{'x'.join(map(str, pr.n[:pr.dim]))} workload: setup {t_setup:.1f} s + "
+            f"{info['iterations']} GMRES(10) iterations {t_solve:.1f} s to a true residual of "
+            f"{info['true_residual'][-1]:.1e} (its own count, measured, not scaled); "
+            f"host has {os.cpu_count()} cores")
     return ms, desc, 1
 
 
+def reference_sample(pr):
+    """The bounded sample a reference-arm step solves: the same generator at
+    half the grid size per axis in 3D (64^3 for the 128^3 workload), the
+    workload itself in 2D."""
+    from paper_1308_4605_gb300 import workloads as wl
+    if pr.dim == 2:
+        return pr
+    n = max(pr.n[0] // 2, 8)
+    if pr.name.startswith("3d_unsteady_periodic"):
+        return wl.config_c3(n)
+    if pr.name.startswith("3d_steady_noslip"):
+        return wl.config_c5(n)
+    return wl.bubble(3, n)
+
+
 def run_reference(args):
+    """The FP64 CPU oracle as the reference arm: each step is one complete
+    oracle solve (setup and GMRES to 1e-10 with its own iteration count) of a
+    bounded sample of the workload, timed as it runs; the value is that
+    measured time, so steps x value is the timed region."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     pr, cfg = make_problem(args.workload, args.n)
+    spr = reference_sample(pr)
     times = []
     desc = ""
+    t_all = time.perf_counter()
     for i in range(args.warmup + args.steps):
-        ms, desc, cores = oracle_time_to_solution(pr)
+        if i == args.warmup:
+            t_all = time.perf_counter()
+        ms, desc, cores = oracle_solve_time(spr)
         if i >= args.warmup:
             times.append(ms)
+    wall = time.perf_counter() - t_all
     v = statistics.mean(times)
+    size = "x".join(map(str, spr.n[:spr.dim]))
     cfg = dict(cfg, l2="oracle on host cores")
+    if spr is not pr:
+        cfg = dict(cfg, workload=spr.name, sample_of=cfg["workload"])
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
             "impl": "reference",
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
-            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"each step: {desc}" + ("" if spr is pr else
+                                       f" (a bounded sample of the {cfg['sample_of']} workload: the "
+                                       f"same generator at {size})")},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s_timed_steps": wall}
     print(json.dumps(line))
     return 0
 
@@ -457,10 +465,14 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            cms, desc, cores = oracle_time_to_solution(pr, infos64[0]["iterations"])
+            cms, desc, cores = oracle_solve_time(pr)
             cpu = {"value": cms, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
         except Exception as e:  # the baseline is informative only
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+
+    others = None
+    if rank == 0 and world == 1 and args.workload == "c3" and not args.no_others:
+        others = other_configs(min(args.steps, 5), min(args.warmup, 2), peaks)
 
     line = {
         "metric": METRIC, "value": ms64, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -489,6 +501,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clocks,
         "wall_s_fp64_steps": wall64,
+        "other_configs": others,
     }
     if rank == 0:
         print(json.dumps(line))
@@ -497,10 +510,12 @@ def run_ours(args):
     return 0
 
 
-def run_batched(args):
+def measure_batched(steps, warmup, e2e=True):
     """64 independent 2D periodic unsteady instances of {64..512}^2 (sizes
     drawn by seed), mu contrast 1e3, P1: one after another with the FP64
-    solver, then all together with stk_solve_batched (FP64 and mixed)."""
+    solver, then all together with stk_solve_batched (FP64 and mixed); with
+    e2e, the mixed batched solve from pinned host buffers (inputs copied in,
+    solutions copied out, inside the timed region)."""
     import numpy as np
     import torch
     from paper_1308_4605_gb300 import stokes as S
@@ -509,7 +524,7 @@ def run_batched(args):
     dev = torch.device("cuda", 0)
     sizes = wl.config_c4_sizes()
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-    solvers, bus, bps, xus, xps = [], [], [], [], []
+    solvers, bus, bps, xus, xps, prs = [], [], [], [], [], []
     for i, n in enumerate(sizes):
         pr = wl.config_c4_instance(i, n)
         sv = S.StokesSolver(2, pr.n[:2], pr.bc[:4], pr.h)
@@ -517,6 +532,7 @@ def run_batched(args):
         tuning.tune(sv, S.STK_FP64)
         tuning.tune(sv, S.STK_MIXED)
         solvers.append(sv)
+        prs.append(pr)
         bus.append([t(x) for x in pr.b_u])
         bps.append(t(pr.b_p))
         xu, xp = sv.zeros(dev)
@@ -562,7 +578,7 @@ def run_batched(args):
             times.append(e0.elapsed_time(e1))
         return statistics.mean(times), infos
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         sequential(S.STK_FP64)
         batched(S.STK_FP64)
         batched(S.STK_MIXED)
@@ -571,36 +587,180 @@ def run_batched(args):
                            ("batched_fp64", batched, S.STK_FP64),
                            ("batched_mixed", batched, S.STK_MIXED),
                            ("sequential_mixed", sequential, S.STK_MIXED)):
-        ms, infos = timed(fn, prec, args.steps)
+        ms, infos = timed(fn, prec, steps)
         res[name] = {"ms": ms, "iterations_total": int(sum(i["iterations"] for i in infos)),
                      "max_true_residual": max(i["true_residual"] for i in infos),
                      "all_converged": all(i["converged"] for i in infos)}
-    cells = int(sum(n * n for n in sizes))
+    out = {"forms": res, "sizes_histogram": {str(n): sizes.count(n) for n in sorted(set(sizes))},
+           "cells": int(sum(n * n for n in sizes)),
+           "speedup_batched_mixed_vs_sequential_fp64": res["sequential_fp64"]["ms"] / res["batched_mixed"]["ms"]}
+    if e2e:
+        h_in = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in list(pr.b_u) + [pr.b_p]]
+                for pr in prs]
+        h_out = [[torch.empty(v.shape, dtype=torch.float64).pin_memory() for v in xu + [xp]]
+                 for xu, xp in zip(xus, xps)]
+        h2d = sum(v.numel() * 8 for hs in h_in for v in hs)
+        d2h = sum(v.numel() * 8 for hs in h_out for v in hs)
+        et = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for k in range(len(solvers)):
+                for d, hh in zip(bus[k] + [bps[k]], h_in[k]):
+                    d.copy_(hh, non_blocking=True)
+            batched(S.STK_MIXED)
+            for k in range(len(solvers)):
+                for hh, d in zip(h_out[k], xus[k] + [xps[k]]):
+                    hh.copy_(d, non_blocking=True)
+            e1.record()
+            e1.synchronize()
+            et.append(e0.elapsed_time(e1))
+        out["e2e"] = {"value": statistics.mean(et), "unit": UNIT, "form": "batched_mixed",
+                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    for sv in solvers:
+        sv.close()
+    return out
+
+
+def measure_config(pr, steps, warmup, peaks, maxit=3000, e2e=True, cpu=False, precond=None,
+                   history=False):
+    """Time-to-1e-10 of one workload on cuda:0 in both forms (set the
+    coefficients, solve from x = 0), with the dominant kernel family's
+    roofline from one profiled FP64 solve, the FP64 solve from pinned host
+    buffers (e2e) and, with cpu, the oracle's full solve of the same
+    workload.  A solve that stops at maxit is reported with its residual."""
+    import numpy as np
+    import torch
+    from paper_1308_4605_gb300 import stokes as S
+    from paper_1308_4605_gb300 import tuning
+    dev = torch.device("cuda", 0)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    rho, mu = t(pr.rho), t(pr.mu)
+    b_u = [t(x) for x in pr.b_u]
+    b_p = t(pr.b_p)
+    sv = S.StokesSolver(pr.dim, pr.n[:pr.dim], pr.bc[:2 * pr.dim], pr.h)
+    x_u, x_p = sv.zeros(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    pc = precond or pr.precond
+
+    def step(precision):
+        sv.set_coefficients(rho, mu, pr.theta)
+        for v in x_u:
+            v.zero_()
+        x_p.zero_()
+        p = S.stk_default_params()
+        p.precond, p.rtol, p.maxit, p.precision = pc, 1e-10, maxit, precision
+        return S.stk_solve(sv.handle, p, b_u, b_p, x_u, x_p)
+
+    sv.set_coefficients(rho, mu, pr.theta)
+    out = {"precond": f"P{pc}"}
+    for name, prec in (("fp64", S.STK_FP64), ("mixed", S.STK_MIXED)):
+        tuning.tune(sv, prec)
+        for _ in range(warmup):
+            step(prec)
+        times = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            info = step(prec)
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        rec = {"ms": statistics.mean(times), "iterations": info["iterations"],
+               "converged": bool(info["converged"]), "true_residual": info["true_residual"]}
+        if history:
+            h = S.stk_solve_history(sv.handle, 0)
+            stride = max(1, len(h) // 20)
+            rec["true_residual_at_restarts"] = {str(i): h[i] for i in range(0, len(h), stride)}
+            rec["true_residual_at_restarts"][str(len(h) - 1)] = h[-1]
+        out[name] = rec
+    S.stk_profile(sv.handle, 1)
+    flush.fill_(1.0)
+    step(S.STK_FP64)
+    fams = [f for f in (S.stk_profile_read(sv.handle, k) for k in range(S.STK_NPROF)) if f["launches"] > 0]
+    S.stk_profile(sv.handle, 0)
+    out["roofline"] = roofline_of(fams, "fp64", peaks, workload=pr.name)
+    if e2e:
+        h_in = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in
+                [pr.rho, pr.mu] + list(pr.b_u) + [pr.b_p]]
+        h_out = [torch.empty(v.shape, dtype=torch.float64).pin_memory() for v in x_u + [x_p]]
+        et = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for d, hh in zip([rho, mu] + b_u + [b_p], h_in):
+                d.copy_(hh, non_blocking=True)
+            step(S.STK_FP64)
+            for hh, d in zip(h_out, x_u + [x_p]):
+                hh.copy_(d, non_blocking=True)
+            e1.record()
+            e1.synchronize()
+            et.append(e0.elapsed_time(e1))
+        out["e2e"] = {"value": statistics.mean(et), "unit": UNIT,
+                      "h2d_bytes_per_step": sum(v.numel() * 8 for v in h_in),
+                      "d2h_bytes_per_step": sum(v.numel() * 8 for v in h_out)}
+    sv.close()
+    if cpu:
+        cms, desc, cores = oracle_solve_time(pr)
+        out["cpu_baseline"] = {"value": cms, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+    return out
+
+
+def other_configs(steps, warmup, peaks):
+    """The remaining benchmark configurations, measured after the headline:
+    2D 32^2 periodic unsteady (P1), the 2D 512^2 sharp-inclusion workload
+    (P2 and P1, and the tanh-smoothed variant; these stall, so they run to a
+    bounded iteration count and report their residual histories), the
+    64-instance batched workload and the 256^3 steady forward + adjoint."""
+    from paper_1308_4605_gb300 import workloads as wl
+    out = {}
+    out["2d_unsteady_periodic_32^2"] = measure_config(wl.config_c1(32), steps, warmup, peaks, cpu=True)
+    c2 = wl.config_c2(512)
+    out["2d_steady_noslip_20_inclusions_mu1e4_512^2"] = {
+        "P2": measure_config(c2, 1, 0, peaks, maxit=500, e2e=False, history=True),
+        "P1": measure_config(c2, 1, 0, peaks, maxit=500, e2e=False, precond=1, history=True),
+        "P2_tanh_smoothed_eps_h": measure_config(wl.config_c2(512, smooth=True), 1, 0, peaks, maxit=500,
+                                                 e2e=False, history=True),
+        "note": "the App. C velocity V-cycle diverges on the sharp mu = 1e4 disks and GMRES(10) stalls; "
+                "bounded at 500 iterations"}
+    out["batched_64_periodic_2d_instances"] = measure_batched(steps, warmup)
+    out["adjoint_3d_steady_noslip_256^3"] = measure_adjoint(256, max(1, steps // 4), 1)
+    return out
+
+
+def run_batched(args):
+    r = measure_batched(args.steps, args.warmup)
+    res = r["forms"]
     line = {"metric": METRIC, "value": res["batched_mixed"]["ms"], "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["batched_mixed"]["ms"],
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
             "data": "synthetic",
-            "config": {"workload": f"batched_64_periodic_2d_instances_{cells}_cells",
-                       "sizes_histogram": {str(n): sizes.count(n) for n in sorted(set(sizes))},
+            "config": {"workload": f"batched_64_periodic_2d_instances_{r['cells']}_cells",
+                       "sizes_histogram": r["sizes_histogram"],
                        "mu_contrast": 1e3, "precond": "P1", "l2": "flushed between steps"},
-            "forms": res,
-            "speedup_batched_mixed_vs_sequential_fp64": res["sequential_fp64"]["ms"] / res["batched_mixed"]["ms"]}
+            "forms": res, "e2e": r.get("e2e"),
+            "speedup_batched_mixed_vs_sequential_fp64": r["speedup_batched_mixed_vs_sequential_fp64"]}
     print(json.dumps(line))
-    for sv in solvers:
-        sv.close()
     return 0
 
 
-def run_adjoint(args):
+def measure_adjoint(n, steps, warmup):
     """Forward + adjoint (gradient w.r.t. log mu) of the 3D steady no-slip
-    workload at n^3 (default 256), loss 1/2||u - u_t||^2, FP64 and mixed."""
+    workload at n^3, loss 1/2||u - u_t||^2, FP64 and mixed."""
     import numpy as np
     import torch
     from paper_1308_4605_gb300 import adjoint
     from paper_1308_4605_gb300 import stokes as S
+    from paper_1308_4605_gb300 import tuning
     from paper_1308_4605_gb300 import workloads as wl
     dev = torch.device("cuda", 0)
-    n = args.n or 256
     pr = wl.config_c5(n)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     solver = S.StokesSolver(3, pr.n, pr.bc, pr.h)
@@ -610,6 +770,9 @@ def run_adjoint(args):
     ut = [t(rng.standard_normal(x.shape)) for x in pr.b_u]
     rho = t(pr.rho)
     lm0 = t(np.log(pr.mu))
+    solver.set_coefficients(rho, t(pr.mu), 0.0)
+    for prec in (S.STK_FP64, S.STK_MIXED):
+        tuning.tune(solver, prec)
     res = {}
     for name, precision in (("fp64", S.STK_FP64), ("mixed", S.STK_MIXED)):
         def step():
@@ -619,11 +782,11 @@ def run_adjoint(args):
             L = 0.5 * sum(((o - q) ** 2).sum() for o, q in zip(out[:3], ut))
             L.backward()
             return lm.grad
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             step()
         torch.cuda.synchronize()
         times = []
-        for _ in range(args.steps):
+        for _ in range(steps):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -633,6 +796,13 @@ def run_adjoint(args):
             times.append(e0.elapsed_time(e1))
         res[name] = {"ms_forward_plus_adjoint": statistics.mean(times),
                      "grad_norm": float(torch.linalg.norm(gr))}
+    solver.close()
+    return res
+
+
+def run_adjoint(args):
+    n = args.n or 256
+    res = measure_adjoint(n, args.steps, args.warmup)
     line = {"metric": METRIC, "value": res["mixed"]["ms_forward_plus_adjoint"], "unit": UNIT,
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": res["mixed"]["ms_forward_plus_adjoint"], "higher_is_better": False,
@@ -640,7 +810,6 @@ def run_adjoint(args):
             "config": {"workload": f"adjoint_3d_steady_noslip_{n}^3", "mu_contrast": 1e2, "precond": "P2"},
             "forms": res}
     print(json.dumps(line))
-    solver.close()
     return 0
 
 

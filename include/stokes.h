@@ -229,6 +229,16 @@ int stk_backward_euler_rhs(stk_handle* h, const double* const* u_n, const double
 int stk_gradient(stk_handle* h, const double* const* u, const double* const* lambda,
                  double* dL_dlogmu, double* dL_drho, void* stream);
 
+/* Residual history of the last stk_solve / stk_solve_batched on h (Sec. 3.2
+ * distinguishes the true residual r = b - M x from the preconditioned one):
+ * kind 0: the true relative residual ||b - M x|| / ||b|| at the start of every
+ * GMRES cycle and at the end (at most 256 kept); kind 1: the Arnoldi residual
+ * estimate divided by ||b|| after every Arnoldi step (the preconditioned
+ * residual of the left form, the true residual of the flexible form; at
+ * most 2048 kept).  Copies min(cap, count) values to the host array out (out
+ * may be NULL) and returns the count, or STK_ERR_ARG. */
+int stk_solve_history(const stk_handle* h, int kind, double* out, int cap);
+
 /* y_p = x_p - mean(x_p): projection of a cell array onto mean-zero vectors,
  * the complement of the constant-pressure null space of M (Sec. 3.2: the
  * pressure is determined up to a constant with periodic, no-slip and

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libstokes_gb300.so")
-SOURCES = ["kernels.cu", "pair.cu", "stress.cu", "krylov.cu", "coarse.cu", "solver.cu", "noalloc.cu"]
+SOURCES = ["kernels.cu", "pair.cu", "stress.cu", "krylov.cu", "gmres.cu", "coarse.cu", "solver.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,218 @@
+// Device-resident control of restarted GMRES (Sec. 3.2) and of its flexible
+// variant (Sec. 4): the Hessenberg least-squares problem, its Givens
+// rotations, the residual estimate, the stopping decisions and the
+// back-substitution live in one GmState record in device memory, updated by
+// single-thread kernels between the vector kernels of each Arnoldi step.
+//
+// Every decision is written to st->cond[] and, inside a CUDA graph, also to
+// the conditional node that gates the next phase (cudaGraphSetConditional),
+// so one GMRES cycle of m Arnoldi steps runs as one graph launch with no
+// host round trip; the host reads the record once per cycle.  Without a
+// graph (profiling) the host reads st->cond[] after each phase instead.  The
+// arithmetic is the textbook one (Saad): column j of the Hessenberg matrix is
+// rotated by the j earlier rotations, a new rotation zeroes h_{j+1,j}, the
+// right-hand side g = beta e_1 is rotated alongside, |g_{j+1}| is the
+// residual estimate, and y solves the k x k triangular system R y = g.
+#include "internal.cuh"
+
+#include <cmath>
+
+namespace stk {
+namespace {
+
+__device__ __forceinline__ void set_cond(GmState* st, int slot, unsigned v,
+                                         cudaGraphConditionalHandle hc, int use) {
+    st->cond[slot] = v;
+    if (use) cudaGraphSetConditional(hc, v);
+}
+
+__device__ __forceinline__ bool finite(double v) { return isfinite(v); }
+
+__device__ __forceinline__ void fail_nonfinite(GmState* st, int why) {
+    if (st->state == GM_RUNNING) {
+        st->state = GM_NONFINITE;
+        st->why = why;
+    }
+}
+
+// solve start: ||b|| from its square
+__global__ void k_gm_begin(GmState* st, const double* __restrict__ bn2, double rtol, int maxit,
+                           int m, int flex) {
+    pdl_entry();
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    st->bnorm = sqrt(*bn2);
+    st->rtol = rtol;
+    st->maxit = maxit;
+    st->m = m;
+    st->flex = flex;
+    st->iterations = 0;
+    st->restarts = 0;
+    st->k = 0;
+    st->nhist = 0;
+    st->nest = 0;
+    st->why = 0;
+    st->rnorm = st->beta = st->target = st->est = 0.0;
+    st->state = finite(st->bnorm) ? GM_RUNNING : GM_NONFINITE;
+    if (!finite(st->bnorm)) st->why = GM_WHY_RHS;
+    for (int i = 0; i < GM_NCOND; ++i) st->cond[i] = 0;
+}
+
+// cycle start, after r = b - M x and ||r||^2: record the true residual, stop
+// on convergence, maxit or a non-finite residual; otherwise open the cycle
+__global__ void k_gm_check(GmState* st, const double* __restrict__ rn2,
+                           cudaGraphConditionalHandle hpre, int use) {
+    pdl_entry();
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    st->k = 0;
+    unsigned go = 0;
+    if (st->state == GM_RUNNING) {
+        const double rn = sqrt(*rn2);
+        st->rnorm = rn;
+        if (!finite(rn)) {
+            fail_nonfinite(st, GM_WHY_RESIDUAL);
+        } else {
+            if (st->nhist < GM_NHIST) st->hist[st->nhist] = rn / st->bnorm;
+            ++st->nhist;
+            if (rn <= st->rtol * st->bnorm) st->state = GM_CONVERGED;
+            else if (st->iterations >= st->maxit) st->state = GM_MAXIT;
+            else go = 1;
+        }
+    }
+    set_cond(st, GM_COND_PRE, go, hpre, use);
+}
+
+// after the cycle's first basis vector r0 (left: P^{-1} r, flexible: r) and,
+// for the left form, ||r0||^2: beta, the cycle's target and 1 / beta
+__global__ void k_gm_start(GmState* st, const double* __restrict__ vn2,
+                           cudaGraphConditionalHandle h0, int use0,
+                           cudaGraphConditionalHandle hfin, int usefin) {
+    pdl_entry();
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned go = 0;
+    if (st->state == GM_RUNNING) {
+        const double beta = st->flex ? st->rnorm : sqrt(*vn2);
+        st->beta = beta;
+        if (!finite(beta)) {
+            fail_nonfinite(st, GM_WHY_PRECOND);
+        } else if (beta == 0.0) {
+            // the preconditioned residual vanished while the true one did not
+            st->state = GM_MAXIT;
+        } else {
+            // flexible: the Arnoldi residual is the true residual; left: the
+            // preconditioned residual must fall by the factor the true
+            // residual still needs
+            st->target = st->flex ? st->rtol * st->bnorm : beta * (st->rtol * st->bnorm / st->rnorm);
+            st->g[0] = beta;
+            for (int i = 1; i <= st->m; ++i) st->g[i] = 0.0;
+            st->inv_scale = 1.0 / beta;
+            ++st->restarts;
+            go = 1;
+        }
+    }
+    set_cond(st, GM_COND_STEP0, go, h0, use0);
+    set_cond(st, GM_COND_FIN, go, hfin, usefin);
+}
+
+// Arnoldi step j done: h[0..j] = projections, *n2 = ||w||^2 after them.
+// Rotate the new column, form the next rotation, update g and the estimate,
+// and decide whether step j + 1 runs.
+__global__ void k_gm_step(GmState* st, int j, const double* __restrict__ hcol,
+                          const double* __restrict__ n2, cudaGraphConditionalHandle hn, int use) {
+    pdl_entry();
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (st->state != GM_RUNNING) {
+        if (j + 1 < st->m) set_cond(st, GM_COND_STEP0 + j + 1, 0u, hn, use);
+        return;
+    }
+    const int m = st->m;
+    double* H = st->H + j * (GM_MMAX + 1);   // column j, rows 0..j+1
+    bool ok = finite(*n2);
+    for (int i = 0; i <= j; ++i) {
+        H[i] = hcol[i];
+        ok = ok && finite(H[i]);
+    }
+    const double hnext = sqrt(*n2);
+    H[j + 1] = hnext;
+    ++st->iterations;
+    st->k = j + 1;
+    if (!ok) {
+        fail_nonfinite(st, GM_WHY_ARNOLDI);
+        st->k = 0;
+        if (j + 1 < m) set_cond(st, GM_COND_STEP0 + j + 1, 0u, hn, use);
+        return;
+    }
+    for (int i = 0; i < j; ++i) {
+        const double t = st->cs[i] * H[i] + st->sn[i] * H[i + 1];
+        H[i + 1] = -st->sn[i] * H[i] + st->cs[i] * H[i + 1];
+        H[i] = t;
+    }
+    const double a = H[j], b = H[j + 1];
+    const double r = hypot(a, b);
+    st->cs[j] = r == 0.0 ? 1.0 : a / r;
+    st->sn[j] = r == 0.0 ? 0.0 : b / r;
+    H[j] = st->cs[j] * a + st->sn[j] * b;
+    H[j + 1] = 0.0;
+    st->g[j + 1] = -st->sn[j] * st->g[j];
+    st->g[j] = st->cs[j] * st->g[j];
+    const double est = fabs(st->g[j + 1]);
+    st->est = est;
+    if (st->nest < GM_NEST) st->est_hist[st->nest] = est / st->bnorm;
+    ++st->nest;
+    st->inv_scale = hnext > 0.0 ? 1.0 / hnext : 1.0;
+    const bool more = est > st->target && hnext > 0.0 && st->iterations < st->maxit;
+    if (j + 1 < m) set_cond(st, GM_COND_STEP0 + j + 1, more ? 1u : 0u, hn, use);
+}
+
+// cycle end: y = R^{-1} g over the k steps taken (k = 0 after a failure:
+// no update)
+__global__ void k_gm_finish(GmState* st) {
+    pdl_entry();
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int k = st->k;
+    bool ok = true;
+    for (int i = k - 1; i >= 0; --i) {
+        double s = st->g[i];
+        for (int c = i + 1; c < k; ++c) s -= st->H[c * (GM_MMAX + 1) + i] * st->y[c];
+        st->y[i] = s / st->H[i * (GM_MMAX + 1) + i];
+        ok = ok && finite(st->y[i]);
+    }
+    if (!ok) {
+        fail_nonfinite(st, GM_WHY_UPDATE);
+        st->k = 0;
+    }
+}
+
+// x *= *s
+__global__ void __launch_bounds__(256) k_scal_dev(int n, double* __restrict__ x,
+                                                  const double* __restrict__ s) {
+    pdl_entry();
+    const double a = *s;
+    for (int t = blockIdx.x * 256 + threadIdx.x; t < n; t += KRY_BLOCKS * 256) x[t] *= a;
+}
+
+}  // namespace
+
+void launch_gm_begin(GmState* st, const double* bn2, double rtol, int maxit, int m, int flex,
+                     cudaStream_t s) {
+    launch_pdl(k_gm_begin, dim3(1), dim3(32), s, st, bn2, rtol, maxit, m, flex);
+}
+void launch_gm_check(GmState* st, const double* rn2, cudaGraphConditionalHandle hpre, int use,
+                     cudaStream_t s) {
+    launch_pdl(k_gm_check, dim3(1), dim3(32), s, st, rn2, hpre, use);
+}
+void launch_gm_start(GmState* st, const double* vn2, cudaGraphConditionalHandle h0, int use0,
+                     cudaGraphConditionalHandle hfin, int usefin, cudaStream_t s) {
+    launch_pdl(k_gm_start, dim3(1), dim3(32), s, st, vn2, h0, use0, hfin, usefin);
+}
+void launch_gm_step(GmState* st, int j, const double* hcol, const double* n2,
+                    cudaGraphConditionalHandle hn, int use, cudaStream_t s) {
+    launch_pdl(k_gm_step, dim3(1), dim3(32), s, st, j, hcol, n2, hn, use);
+}
+void launch_gm_finish(GmState* st, cudaStream_t s) {
+    launch_pdl(k_gm_finish, dim3(1), dim3(32), s, st);
+}
+void launch_scale_dev(int n, double* x, const double* a, cudaStream_t s) {
+    launch_pdl(k_scal_dev, dim3(KRY_BLOCKS), dim3(256), s, n, x, a);
+}
+
+}  // namespace stk

@@ -252,6 +252,44 @@ void launch_schur_combine(int n, const double* theta, const T* phi, const T* mu2
                           const T* bc, T* xp,
                           cudaStream_t s);
 
+// Device-resident state of restarted GMRES (gmres.cu): the rotated
+// Hessenberg matrix, the Givens rotations, the rotated right-hand side g, the
+// least-squares solution y, the residuals and the stopping decisions of the
+// current cycle.  cond[] holds the decisions that gate the next phase: the
+// preconditioned start of a cycle (GM_COND_PRE), its final update
+// (GM_COND_FIN) and Arnoldi step j (GM_COND_STEP0 + j).
+constexpr int GM_MMAX = 32;
+constexpr int GM_NHIST = 256;    // true relative residuals at cycle starts kept
+constexpr int GM_NEST = 2048;    // Arnoldi residual estimates kept
+constexpr int GM_COND_PRE = 0, GM_COND_FIN = 1, GM_COND_STEP0 = 2;
+constexpr int GM_NCOND = GM_COND_STEP0 + GM_MMAX;
+enum { GM_RUNNING = 0, GM_CONVERGED = 1, GM_MAXIT = 2, GM_NONFINITE = 3 };
+enum { GM_WHY_RHS = 1, GM_WHY_RESIDUAL, GM_WHY_PRECOND, GM_WHY_ARNOLDI, GM_WHY_UPDATE };
+struct GmState {
+    // header: read by the host after every cycle
+    int state, why, k, iterations, restarts, maxit, m, flex, nhist, nest;
+    double bnorm, rnorm, beta, target, est, rtol, inv_scale;
+    unsigned cond[GM_NCOND];
+    // column j of H at H[j * (GM_MMAX + 1)], rows 0..j+1
+    double H[(GM_MMAX + 1) * GM_MMAX];
+    double cs[GM_MMAX], sn[GM_MMAX], g[GM_MMAX + 1], y[GM_MMAX];
+    double hist[GM_NHIST];       // ||b - M x|| / ||b|| at each cycle start
+    double est_hist[GM_NEST];    // |g_{j+1}| / ||b|| after each Arnoldi step
+};
+// solve start (*bn2 = ||b||^2), cycle start (*rn2 = ||b - M x||^2), first
+// basis vector (*vn2 = ||P^{-1} r||^2 for the left form), Arnoldi step j
+// (hcol[0..j] the projections, *n2 = ||w||^2 after them), cycle end.  With
+// use != 0 the decision is also written to the graph's conditional handle.
+void launch_gm_begin(GmState* st, const double* bn2, double rtol, int maxit, int m, int flex,
+                     cudaStream_t s);
+void launch_gm_check(GmState* st, const double* rn2, cudaGraphConditionalHandle hpre, int use,
+                     cudaStream_t s);
+void launch_gm_start(GmState* st, const double* vn2, cudaGraphConditionalHandle h0, int use0,
+                     cudaGraphConditionalHandle hfin, int usefin, cudaStream_t s);
+void launch_gm_step(GmState* st, int j, const double* hcol, const double* n2,
+                    cudaGraphConditionalHandle hn, int use, cudaStream_t s);
+void launch_gm_finish(GmState* st, cudaStream_t s);
+
 // reductions with a fixed block count: deterministic results
 constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
 constexpr int RED_THREADS = 256;
@@ -275,6 +313,13 @@ void launch_mgs_step(int n, const double* vk, const double* u, const double* h, 
 // x += sum_i y[i] V_i (i < k); V of precision TV
 template <typename TV>
 void launch_combine(int n, int k, const TV* const* V, const double* y, double* x, cudaStream_t s);
+// x += sum_i y[i] V_i for i < *k (k read on the device, 0 <= *k <= m <= 32;
+// the vectors beyond *k are not read)
+template <typename TV>
+void launch_combine_dev(int n, int m, const TV* const* V, const double* y, const int* k, double* x,
+                        cudaStream_t s);
+// x *= *a (a device scalar)
+void launch_scale_dev(int n, double* x, const double* a, cudaStream_t s);
 // x *= 1 / sqrt(*nrm2)
 void launch_scale_inv_sqrt(int n, double* x, const double* nrm2, cudaStream_t s);
 void launch_scale(int n, double* x, double a, cudaStream_t s);

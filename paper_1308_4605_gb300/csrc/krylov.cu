@@ -160,6 +160,41 @@ __global__ void __launch_bounds__(KT) k_comb(int n, PtrArr V, const double* __re
     }
 }
 
+// x += sum_{i < *k} y[i] V_i with *k <= K read on the device (the branch is
+// uniform: the vectors beyond *k are not loaded)
+template <int K, typename TV>
+__global__ void __launch_bounds__(KT) k_comb_dev(int n, PtrArr V, const double* __restrict__ y,
+                                                  const int* __restrict__ kp, double* __restrict__ x) {
+    pdl_entry();
+    using V2 = typename Vec2<TV>::type;
+    const int k = *kp;
+    if (k <= 0) return;
+    double yy[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) yy[i] = i < k ? y[i] : 0.0;
+    const int n2 = n >> 1;
+    double2* x2 = reinterpret_cast<double2*>(x);
+    for (int t = blockIdx.x * KT + threadIdx.x; t < n2; t += KRY_BLOCKS * KT) {
+        double2 a = x2[t];
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            if (i < k) {
+                const V2 v = reinterpret_cast<const V2*>(V.p[i])[t];
+                a.x = fma(yy[i], double(v.x), a.x);
+                a.y = fma(yy[i], double(v.y), a.y);
+            }
+        }
+        x2[t] = a;
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        double a = x[n - 1];
+#pragma unroll
+        for (int i = 0; i < K; ++i)
+            if (i < k) a = fma(yy[i], double(static_cast<const TV*>(V.p[i])[n - 1]), a);
+        x[n - 1] = a;
+    }
+}
+
 __global__ void __launch_bounds__(KT) k_scal(int n, double* __restrict__ x, double a,
                                              const double* __restrict__ nrm2) {
     pdl_entry();
@@ -227,6 +262,18 @@ void launch_combine(int n, int k, const TV* const* V, const double* y, double* x
     }
 }
 
+template <typename TV>
+void launch_combine_dev(int n, int m, const TV* const* V, const double* y, const int* k, double* x,
+                        cudaStream_t s) {
+    PtrArr pa = pack(reinterpret_cast<const void* const*>(V), m);
+    switch (m - 1) {
+#define X(J) case J: launch_pdl(k_comb_dev<J + 1, TV>, dim3(KRY_BLOCKS), dim3(KT), s, n, pa, y, k, x); break;
+    STK_J_CASES(X)
+#undef X
+    default: return;
+    }
+}
+
 void launch_mgs_step(int n, const double* vk, const double* u, const double* h, int k, double* w,
                      double* scratch, double* out, cudaStream_t s) {
     launch_pdl(k_mgs_step, dim3(KRY_BLOCKS), dim3(KT), s, n, vk, u, h, k, w, scratch);
@@ -245,5 +292,9 @@ template void launch_combine<double>(int, int, const double* const*, const doubl
                                      cudaStream_t);
 template void launch_combine<float>(int, int, const float* const*, const double*, double*,
                                     cudaStream_t);
+template void launch_combine_dev<double>(int, int, const double* const*, const double*, const int*,
+                                         double*, cudaStream_t);
+template void launch_combine_dev<float>(int, int, const float* const*, const double*, const int*,
+                                        double*, cudaStream_t);
 
 }  // namespace stk

@@ -7,8 +7,10 @@
 #include "internal.cuh"
 #include "../../include/stokes.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -129,6 +131,17 @@ struct stk_handle {
     cudaStream_t cap = nullptr;    // private stream used for capture only
     cudaStream_t run = nullptr;    // this handle's stream inside a batched solve
     cudaEvent_t join = nullptr;    // marks the end of its work in a batched solve
+    // graphs of one GMRES cycle (conditional nodes gate its phases), keyed by
+    // (precond, flexible, m, nu, ncoarse, cycles); kernels per phase
+    struct CycleGraph {
+        cudaGraphExec_t exec = nullptr;
+        long long k_chk = 0, k_pre = 0, k_fin = 0;
+        std::vector<long long> k_step;
+    };
+    std::map<std::tuple<int, int, int, int, int, int>, CycleGraph> cgraphs;
+    GmState* gst = nullptr;        // device state of the GMRES least-squares problem
+    GmState* gst_host = nullptr;   // pinned copy
+    std::vector<double> hist_true, hist_est;   // residual histories of the last solve
     std::vector<ProfRec> recs;
     std::vector<cudaEvent_t> evpool;
     size_t evnext = 0;
@@ -143,8 +156,8 @@ constexpr int NDSC = 128;     // device scalar slots
 constexpr int DS_SUM = 0;     // mean removal sums
 constexpr int DS_H = 8;       // Arnoldi column h[0..m+1]
 constexpr int DS_N2 = 48;     // norms
-constexpr int DS_Y = 64;      // least-squares solution y
 constexpr int DS_THETA = 100; // theta = 1/dt (read by the preconditioner graphs)
+constexpr int HP_THETA = 250; // pinned host staging slot of theta
 
 int fail(stk_handle* h, int code, const char* fmt, ...) {
     char buf[512];
@@ -677,7 +690,7 @@ void apply_precond(stk_handle* h, int which, const T* b, T* x, const MGParams& m
 }
 
 void clear_graphs(stk_handle* h) {
-    if (h->graphs.empty()) return;
+    if (h->graphs.empty() && h->cgraphs.empty()) return;
     cudaDeviceSynchronize();   // no launch of these graphs may still be in flight
     for (auto& kv : h->graphs) {
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
@@ -687,6 +700,10 @@ void clear_graphs(stk_handle* h) {
         }
     }
     h->graphs.clear();
+    // the GMRES cycle graphs contain preconditioner applications
+    for (auto& kv : h->cgraphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    h->cgraphs.clear();
 }
 
 // x = P^{-1} b through a CUDA graph captured on first use (one graph per
@@ -783,49 +800,19 @@ int ensure_krylov(stk_handle* h, int m) {
     return STK_OK;
 }
 
-// Givens rotation helpers on the host: H is (m+1) x m column-major in hc
-struct Arnoldi {
-    int m;
-    std::vector<double> H, cs, sn, g;
-    explicit Arnoldi(int m_) : m(m_), H((m_ + 1) * m_, 0.0), cs(m_), sn(m_), g(m_ + 1, 0.0) {}
-    double& at(int i, int j) { return H[j * (m + 1) + i]; }
-    // column j holds h[0..j+1]; returns |g[j+1]|
-    double add_column(int j, const double* col) {
-        for (int i = 0; i <= j + 1; ++i) at(i, j) = col[i];
-        for (int i = 0; i < j; ++i) {
-            double t = cs[i] * at(i, j) + sn[i] * at(i + 1, j);
-            at(i + 1, j) = -sn[i] * at(i, j) + cs[i] * at(i + 1, j);
-            at(i, j) = t;
-        }
-        double a = at(j, j), b = at(j + 1, j);
-        double r = std::hypot(a, b);
-        cs[j] = r == 0.0 ? 1.0 : a / r;
-        sn[j] = r == 0.0 ? 0.0 : b / r;
-        at(j, j) = cs[j] * a + sn[j] * b;
-        at(j + 1, j) = 0.0;
-        g[j + 1] = -sn[j] * g[j];
-        g[j] = cs[j] * g[j];
-        return std::fabs(g[j + 1]);
-    }
-    void solve(int k, double* y) {
-        for (int i = k - 1; i >= 0; --i) {
-            double s = g[i];
-            for (int c = i + 1; c < k; ++c) s -= at(i, c) * y[c];
-            y[i] = s / at(i, i);
-        }
-    }
-};
-
 // ---------------------------------------------------------------- GMRES core
-// Pinned host staging slots: the Arnoldi column, ||w||^2 after the
-// orthogonalisation, ||b|| or ||r||, the least-squares solution, theta.
-constexpr int HP_H = 0, HP_AFTER = 40, HP_NRM = 41, HP_Y = 128, HP_THETA = 250;
+// The Arnoldi process of Sec. 3.2 with its least-squares problem kept on the
+// device (gmres.cu): one GMRES cycle is enqueued as phases -- the true
+// residual and the stopping test, the first basis vector, Arnoldi steps
+// 0..m-1, the update of x -- each gated by a decision a kernel of the
+// previous phase wrote.  Inside a CUDA graph the gates are conditional
+// nodes, so a whole cycle is one graph launch and the host reads the state
+// once per cycle; without graphs (profiling) the host reads each decision.
 
-// Orthogonalise w = V[j+1] against V[0..j] by modified Gram-Schmidt (the
-// Arnoldi process of Sec. 3.2): h_0 = <w, v_0>; for k = 0..j: w -= h_k v_k
-// fused with h_{k+1} = <w, v_{k+1}> (the last step forms ||w||^2 instead).
-// Every coefficient stays on the device between steps; h_0..h_j and ||w||^2
-// are copied to the host at the end.
+// Orthogonalise w = V[j+1] against V[0..j] by modified Gram-Schmidt:
+// h_0 = <w, v_0>; for k = 0..j: w -= h_k v_k fused with h_{k+1} = <w, v_{k+1}>
+// (the last step forms ||w||^2 in DS_N2 instead).  The coefficients stay in
+// device memory (DS_H) for the Givens kernel.
 void orth_enqueue(stk_handle* h, int j, cudaStream_t s) {
     const int n = nstokes(h);
     double* w = h->V[j + 1];
@@ -841,15 +828,161 @@ void orth_enqueue(stk_handle* h, int j, cudaStream_t s) {
         launch_mgs_step(n, h->V[k], last ? nullptr : h->V[k + 1], hd, k, w, h->red,
                         last ? h->dsc + DS_N2 : hd + k + 1, s);
     }
-    cudaMemcpyAsync(h->hpin + HP_H, hd, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(h->hpin + HP_AFTER, h->dsc + DS_N2, sizeof(double), cudaMemcpyDeviceToHost, s);
 }
 
-void norm_enqueue(stk_handle* h, const double* x, cudaStream_t s) {
+// out[0] = ||x||^2 (device)
+void norm_enqueue(stk_handle* h, const double* x, double* out, cudaStream_t s) {
     const int n = nstokes(h);
     Scope sc(h, PF_MDOT, 8.0 * n, s, 2);
-    launch_multidot(n, -1, nullptr, x, h->red, h->dsc + DS_N2 + 1, s);
-    cudaMemcpyAsync(h->hpin + HP_NRM, h->dsc + DS_N2 + 1, sizeof(double), cudaMemcpyDeviceToHost, s);
+    launch_multidot(n, -1, nullptr, x, h->red, out, s);
+}
+
+struct CycleCtx {
+    stk_handle* h;
+    int which, m;
+    bool flex;
+    MGParams mp;
+};
+
+// phase 1: r = b - M x, ||r||^2, stopping test (gate of phase 2)
+void enq_check(const CycleCtx& c, cudaStream_t s, cudaGraphConditionalHandle hpre, int use) {
+    stk_handle* h = c.h;
+    const Geom& g = h->lev[0].g;
+    {
+        Scope sc(h, PF_MATVEC, bytes_matvec(g, 8) + 8.0 * nstokes(h), s, stress_kernels(g));
+        launch_stokes_matvec_stress(g, h->lev[0].cd, h->sw, h->xk, h->bk, h->tmp, s);
+    }
+    norm_enqueue(h, h->tmp, h->dsc + DS_N2 + 1, s);
+    { Scope sc(h, PF_ALG, 0.0, s); launch_gm_check(h->gst, h->dsc + DS_N2 + 1, hpre, use, s); }
+}
+
+// phase 2: v_0 = P^{-1} r (left) or r (flexible), beta, target (gates of the
+// first Arnoldi step and of the update)
+int enq_pre(const CycleCtx& c, cudaStream_t s, cudaGraphConditionalHandle h0,
+            cudaGraphConditionalHandle hfin, int use) {
+    stk_handle* h = c.h;
+    if (c.flex) {
+        CK(cudaMemcpyAsync(h->V[0], h->tmp, sizeof(double) * nstokes(h), cudaMemcpyDeviceToDevice, s));
+    } else {
+        apply_precond<double>(h, c.which, h->tmp, h->V[0], c.mp, s);
+        norm_enqueue(h, h->V[0], h->dsc + DS_N2 + 2, s);
+    }
+    { Scope sc(h, PF_ALG, 0.0, s); launch_gm_start(h->gst, h->dsc + DS_N2 + 2, h0, use, hfin, use, s); }
+    return STK_OK;
+}
+
+// phase 3 + j: Arnoldi step j (gate of step j + 1)
+void enq_step(const CycleCtx& c, int j, cudaStream_t s, cudaGraphConditionalHandle hn, int use) {
+    stk_handle* h = c.h;
+    const Geom& g = h->lev[0].g;
+    const int n = nstokes(h);
+    {   // v_j /= beta (j = 0) or h_{j,j-1}
+        Scope sc(h, PF_COMB, 16.0 * n, s);
+        launch_scale_dev(n, h->V[j], &h->gst->inv_scale, s);
+    }
+    if (c.flex) {
+        {
+            Scope sc(h, PF_CONV, 12.0 * n, s);
+            launch_convert<double, float>(n, h->V[j], h->pf.in, s);
+        }
+        apply_precond<float>(h, c.which, h->pf.in, h->Z[j], c.mp, s);
+        {   // the FP64 matvec of the FP32 direction z_j (converted once)
+            Scope sc(h, PF_CONV, 12.0 * n, s);
+            launch_convert<float, double>(n, h->Z[j], h->tmp, s);
+        }
+        Scope sc(h, PF_MATVEC, bytes_matvec(g, 8), s, stress_kernels(g));
+        launch_stokes_matvec_stress(g, h->lev[0].cd, h->sw, h->tmp, nullptr, h->V[j + 1], s);
+    } else {
+        {
+            Scope sc(h, PF_MATVEC, bytes_matvec(g, 8), s, stress_kernels(g));
+            launch_stokes_matvec_stress(g, h->lev[0].cd, h->sw, h->V[j], nullptr, h->tmp, s);
+        }
+        apply_precond<double>(h, c.which, h->tmp, h->V[j + 1], c.mp, s);
+    }
+    orth_enqueue(h, j, s);
+    Scope sc(h, PF_ALG, 0.0, s);
+    launch_gm_step(h->gst, j, h->dsc + DS_H, h->dsc + DS_N2, hn, use, s);
+}
+
+// last phase: y = R^{-1} g, x += V y (left) or Z y (flexible)
+void enq_fin(const CycleCtx& c, cudaStream_t s) {
+    stk_handle* h = c.h;
+    const int n = nstokes(h);
+    { Scope sc(h, PF_ALG, 0.0, s); launch_gm_finish(h->gst, s); }
+    Scope sc(h, PF_COMB, (c.flex ? 4.0 : 8.0) * n * c.m + 16.0 * n, s);
+    if (c.flex) {
+        std::vector<const float*> Zp(h->Z.begin(), h->Z.begin() + c.m);
+        launch_combine_dev<float>(n, c.m, Zp.data(), h->gst->y, &h->gst->k, h->xk, s);
+    } else {
+        std::vector<const double*> Vp(h->V.begin(), h->V.begin() + c.m);
+        launch_combine_dev<double>(n, c.m, Vp.data(), h->gst->y, &h->gst->k, h->xk, s);
+    }
+}
+
+// Build the graph of one GMRES cycle: a chain of conditional (if) nodes,
+// each holding one phase captured from the enqueue functions above; the
+// first node's condition is 1 at every launch, the others are set by the
+// kernels of the phase before them.
+int build_cycle_graph(const CycleCtx& c, stk_handle::CycleGraph& out) {
+    stk_handle* h = c.h;
+    cudaGraph_t G = nullptr;
+    CK(cudaGraphCreate(&G, 0));
+    const int m = c.m;
+    std::vector<cudaGraphConditionalHandle> hs(m + 3);   // check, pre, fin, step 0..m-1
+    int rc = STK_OK;
+    for (int i = 0; i < m + 3 && rc == STK_OK; ++i) {
+        cudaError_t e = cudaGraphConditionalHandleCreate(&hs[i], G, i == 0 ? 1u : 0u,
+                                                         cudaGraphCondAssignDefault);
+        if (e != cudaSuccess) rc = fail(h, STK_ERR_CUDA, "conditional handle: %s", cudaGetErrorString(e));
+    }
+    const cudaGraphConditionalHandle hchk = hs[0], hpre = hs[1], hfin = hs[2];
+    auto hstep = [&](int j) { return hs[3 + j]; };
+    cudaGraphNode_t prev = nullptr;
+    // add an if-node after prev whose body is captured from fn(stream)
+    auto add_if = [&](cudaGraphConditionalHandle hc, auto&& fn, long long& kernels) -> int {
+        if (rc) return rc;
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = hc;
+        np.conditional.type = cudaGraphCondTypeIf;
+        np.conditional.size = 1;
+        cudaGraphNode_t node = nullptr;
+        cudaError_t e = cudaGraphAddNode(&node, G, prev ? &prev : nullptr, nullptr, prev ? 1 : 0, &np);
+        if (e != cudaSuccess) return rc = fail(h, STK_ERR_CUDA, "conditional node: %s", cudaGetErrorString(e));
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(h->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return rc = fail(h, STK_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
+        h->capturing = true;
+        h->cap_kernels = 0;
+        int frc = fn(h->cap);
+        h->capturing = false;
+        cudaGraph_t got = nullptr;
+        e = cudaStreamEndCapture(h->cap, &got);
+        if (frc) return rc = frc;
+        if (e != cudaSuccess) return rc = fail(h, STK_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
+        kernels = h->cap_kernels;
+        prev = node;
+        return STK_OK;
+    };
+    out.k_step.assign(m, 0);
+    add_if(hchk, [&](cudaStream_t s) { enq_check(c, s, hpre, 1); return STK_OK; }, out.k_chk);
+    add_if(hpre, [&](cudaStream_t s) { return enq_pre(c, s, hstep(0), hfin, 1); }, out.k_pre);
+    for (int j = 0; j < m; ++j)
+        add_if(hstep(j), [&](cudaStream_t s) {
+            enq_step(c, j, s, j + 1 < m ? hstep(j + 1) : 0, j + 1 < m ? 1 : 0);
+            return STK_OK;
+        }, out.k_step[j]);
+    add_if(hfin, [&](cudaStream_t s) { enq_fin(c, s); return STK_OK; }, out.k_fin);
+    if (rc == STK_OK) {
+        cudaError_t e = cudaGraphInstantiate(&out.exec, G, 0);
+        if (e != cudaSuccess) {
+            out.exec = nullptr;
+            rc = fail(h, STK_ERR_CUDA, "cycle graph instantiate: %s", cudaGetErrorString(e));
+        }
+    }
+    cudaGraphDestroy(G);
+    cudaGetLastError();
+    return rc;
 }
 
 // One GMRES instance advanced in lockstep with others (Sec. 3.2, Sec. 4).
@@ -858,13 +991,12 @@ struct Inst {
     cudaStream_t s = nullptr;
     stk_solve_info info{};
     int rc = STK_OK;
-    bool done = false;      // solve finished (converged, maxit or error)
-    bool in_cycle = false;  // Arnoldi cycle still running
-    double bnorm = 0, rnorm = 0, beta = 0, target = 0;
-    std::vector<double> hcol, y;
-    Arnoldi ar{1};
-    int k = 0;
+    bool done = false;              // solve finished (converged, maxit or error)
+    stk_handle::CycleGraph* cg = nullptr;
+    int it_before = 0;              // iterations before the current cycle
 };
+
+constexpr size_t GM_HEADER = offsetof(GmState, H);   // bytes the host reads per cycle
 
 int sync_all(std::vector<Inst*>& v) {
     int rc = STK_OK;
@@ -888,7 +1020,41 @@ int sync_all(std::vector<Inst*>& v) {
 void finish(Inst* it, int rc) {
     if (it->rc == STK_OK) it->rc = rc;
     it->done = true;
-    it->in_cycle = false;
+}
+
+void read_header(Inst* it) {
+    cudaMemcpyAsync(it->h->gst_host, it->h->gst, GM_HEADER, cudaMemcpyDeviceToHost, it->s);
+}
+
+// Fold the device state read after a cycle into the info record; finish the
+// instance when the device stopped it.
+void absorb_cycle(Inst* it, const stk_solver_params& prm, const MGParams& mp) {
+    stk_handle* h = it->h;
+    const GmState& st = *h->gst_host;
+    const int steps = st.iterations - it->it_before;
+    const double sv = scalar_vcycles(h, prm.precond, mp);
+    it->info.scalar_vcycles += sv * steps + ((prm.precision != STK_MIXED && st.cond[GM_COND_PRE]) ? sv : 0.0);
+    it->info.iterations = st.iterations;
+    it->info.restarts = st.restarts;
+    it->info.true_residual = st.rnorm / st.bnorm;
+    it->info.est_residual = st.est / st.bnorm;
+    if (it->cg) {   // kernels the graph ran: the gates the device opened
+        const auto& cg = *it->cg;
+        h->nkern += cg.k_chk + (st.cond[GM_COND_PRE] ? cg.k_pre : 0) + (st.cond[GM_COND_FIN] ? cg.k_fin : 0);
+        for (int j = 0; j < steps && j < (int)cg.k_step.size(); ++j) h->nkern += cg.k_step[j];
+    }
+    it->it_before = st.iterations;
+    switch (st.state) {
+    case GM_RUNNING: break;
+    case GM_CONVERGED: it->info.converged = 1; finish(it, STK_OK); break;
+    case GM_MAXIT: finish(it, STK_ERR_NOT_CONVERGED); break;
+    default: {
+        static const char* why[] = {"", "non-finite right-hand side", "non-finite residual",
+                                    "non-finite preconditioned residual",
+                                    "non-finite value in the Arnoldi process", "non-finite GMRES update"};
+        finish(it, fail(h, STK_ERR_NONFINITE, "%s", why[st.why >= 1 && st.why <= 5 ? st.why : 0]));
+    }
+    }
 }
 
 // Restarted GMRES for every instance: left-preconditioned with an FP64
@@ -896,8 +1062,9 @@ void finish(Inst* it, int rc) {
 // Stopping rule: ||b - M x|| <= rtol ||b||, checked at the start of every
 // cycle; inside a cycle the Arnoldi estimate must fall to rtol ||b||
 // (flexible) or to its start value times rtol ||b|| / ||b - M x|| (left).
-// Every phase enqueues the work of all active instances on their streams and
-// then synchronises once for all of them.
+// With graphs each cycle of every active instance is one graph launch on its
+// stream and the host synchronises once per cycle for the whole batch;
+// without graphs (profiling) once per phase.
 void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm) {
     const int m = prm.restart;
     const bool flex = prm.precision == STK_MIXED;
@@ -908,172 +1075,113 @@ void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm) {
     mp.cp = prm.vcycles_p;
     std::vector<Inst*> act;
     for (auto& it : insts) {
-        it.hcol.assign(m + 2, 0.0);
-        it.y.assign(m, 0.0);
+        if (it.done) continue;
         int rc = ensure_krylov(it.h, m);
         if (rc) { finish(&it, rc); continue; }
-        norm_enqueue(it.h, it.h->bk, it.s);
+        norm_enqueue(it.h, it.h->bk, it.h->dsc + DS_N2 + 3, it.s);
+        launch_gm_begin(it.h->gst, it.h->dsc + DS_N2 + 3, prm.rtol, prm.maxit, m, flex ? 1 : 0, it.s);
+        ++it.h->nkern;
+        read_header(&it);
         act.push_back(&it);
     }
     sync_all(act);
     for (Inst* it : act) {
         if (it->done) continue;
-        it->bnorm = std::sqrt(it->h->hpin[HP_NRM]);
-        if (!std::isfinite(it->bnorm)) finish(it, fail(it->h, STK_ERR_NONFINITE, "non-finite right-hand side"));
-        else if (it->bnorm == 0.0) {
+        const GmState& st = *it->h->gst_host;
+        if (st.state == GM_NONFINITE) finish(it, fail(it->h, STK_ERR_NONFINITE, "non-finite right-hand side"));
+        else if (st.bnorm == 0.0) {
             cudaMemsetAsync(it->h->xk, 0, sizeof(double) * nstokes(it->h), it->s);
             it->info.converged = 1;
             finish(it, STK_OK);
         }
     }
+    // graphs of the cycle (built on first use per handle and configuration)
+    for (Inst* it : act) {
+        if (it->done) continue;
+        stk_handle* h = it->h;
+        it->cg = nullptr;
+        if (!h->use_graphs || h->prof) continue;
+        auto key = std::make_tuple(prm.precond, flex ? 1 : 0, m, mp.nu, mp.ncoarse, mp.cu * 1000 + mp.cp);
+        auto f = h->cgraphs.find(key);
+        if (f == h->cgraphs.end()) {
+            stk_handle::CycleGraph cg;
+            CycleCtx c{h, prm.precond, m, flex, mp};
+            if (build_cycle_graph(c, cg) != STK_OK) {
+                h->use_graphs = false;   // fall back to host-gated phases
+                continue;
+            }
+            f = h->cgraphs.emplace(key, std::move(cg)).first;
+        }
+        it->cg = &f->second;
+    }
     while (true) {
-        // cycle start: true residual
         act.clear();
         for (auto& it : insts)
             if (!it.done) act.push_back(&it);
         if (act.empty()) break;
+        std::vector<Inst*> eager;
         for (Inst* it : act) {
-            stk_handle* h = it->h;
-            const Geom& g = h->lev[0].g;
-            Scope sc(h, PF_MATVEC, bytes_matvec(g, 8) + 8.0 * nstokes(h), it->s, stress_kernels(g));
-            launch_stokes_matvec_stress(g, h->lev[0].cd, h->sw, h->xk, h->bk, h->tmp, it->s);
-            norm_enqueue(h, h->tmp, it->s);
+            if (it->cg) {
+                cudaError_t e = cudaGraphLaunch(it->cg->exec, it->s);
+                if (e != cudaSuccess) { finish(it, fail(it->h, STK_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e))); continue; }
+                read_header(it);
+            } else {
+                eager.push_back(it);
+            }
+        }
+        if (!eager.empty()) {   // the same phases, gated by the host
+            for (Inst* it : eager) {
+                CycleCtx c{it->h, prm.precond, m, flex, mp};
+                enq_check(c, it->s, 0, 0);
+                read_header(it);
+            }
+            sync_all(eager);
+            std::vector<Inst*> run;
+            for (Inst* it : eager)
+                if (!it->done && it->h->gst_host->cond[GM_COND_PRE]) run.push_back(it);
+            for (Inst* it : run) {
+                CycleCtx c{it->h, prm.precond, m, flex, mp};
+                int rc = enq_pre(c, it->s, 0, 0, 0);
+                if (rc) { finish(it, rc); continue; }
+                read_header(it);
+            }
+            sync_all(run);
+            for (int j = 0; j < m; ++j) {
+                std::vector<Inst*> step;
+                for (Inst* it : run)
+                    if (!it->done && it->h->gst_host->cond[GM_COND_STEP0 + j]) step.push_back(it);
+                if (step.empty()) break;
+                for (Inst* it : step) {
+                    CycleCtx c{it->h, prm.precond, m, flex, mp};
+                    enq_step(c, j, it->s, 0, 0);
+                    read_header(it);
+                }
+                sync_all(step);
+            }
+            for (Inst* it : run) {
+                if (it->done || !it->h->gst_host->cond[GM_COND_FIN]) continue;
+                CycleCtx c{it->h, prm.precond, m, flex, mp};
+                enq_fin(c, it->s);
+                read_header(it);
+            }
         }
         sync_all(act);
-        std::vector<Inst*> cyc;
-        for (Inst* it : act) {
-            if (it->done) continue;
-            it->rnorm = std::sqrt(it->h->hpin[HP_NRM]);
-            if (!std::isfinite(it->rnorm)) { finish(it, fail(it->h, STK_ERR_NONFINITE, "non-finite residual")); continue; }
-            it->info.true_residual = it->rnorm / it->bnorm;
-            if (it->info.true_residual <= prm.rtol) { it->info.converged = 1; finish(it, STK_OK); continue; }
-            if (it->info.iterations >= prm.maxit) { finish(it, STK_ERR_NOT_CONVERGED); continue; }
-            cyc.push_back(it);
-        }
-        if (cyc.empty()) continue;
-        const double sv_dummy = 0.0;
-        (void)sv_dummy;
-        if (flex) {
-            for (Inst* it : cyc) {
-                cudaMemcpyAsync(it->h->V[0], it->h->tmp, sizeof(double) * nstokes(it->h),
-                                cudaMemcpyDeviceToDevice, it->s);
-                it->beta = it->rnorm;
-                it->target = prm.rtol * it->bnorm;
-            }
-        } else {
-            for (Inst* it : cyc) {
-                int rc = run_precond<double>(it->h, prm.precond, it->h->tmp, it->h->V[0], mp, it->s);
-                if (rc) { finish(it, rc); continue; }
-                it->info.scalar_vcycles += scalar_vcycles(it->h, prm.precond, mp);
-                norm_enqueue(it->h, it->h->V[0], it->s);
-            }
-            sync_all(cyc);
-            for (Inst* it : cyc) {
-                if (it->done) continue;
-                it->beta = std::sqrt(it->h->hpin[HP_NRM]);
-                if (!std::isfinite(it->beta)) { finish(it, fail(it->h, STK_ERR_NONFINITE, "non-finite preconditioned residual")); continue; }
-                it->target = it->beta * (prm.rtol * it->bnorm / it->rnorm);
-            }
-        }
-        std::vector<Inst*> run;
-        for (Inst* it : cyc) {
-            if (it->done) continue;
-            if (it->beta == 0.0) { finish(it, it->info.converged ? STK_OK : STK_ERR_NOT_CONVERGED); continue; }
-            Scope sc(it->h, PF_COMB, 16.0 * nstokes(it->h), it->s);
-            launch_scale(nstokes(it->h), it->h->V[0], 1.0 / it->beta, it->s);
-            it->ar = Arnoldi(m);
-            it->ar.g[0] = it->beta;
-            it->k = 0;
-            it->in_cycle = true;
-            run.push_back(it);
-        }
-        for (int j = 0; j < m; ++j) {
-            std::vector<Inst*> step;
-            for (Inst* it : run)
-                if (it->in_cycle && !it->done && it->info.iterations < prm.maxit) step.push_back(it);
-            if (step.empty()) break;
-            for (Inst* it : step) {
-                stk_handle* h = it->h;
-                const Geom& g = h->lev[0].g;
-                const int n = nstokes(h);
-                int rc;
-                if (flex) {
-                    {
-                        Scope sc(h, PF_CONV, 12.0 * n, it->s);
-                        launch_convert<double, float>(n, h->V[j], h->pf.in, it->s);
-                    }
-                    if ((rc = run_precond<float>(h, prm.precond, h->pf.in, h->Z[j], mp, it->s))) { finish(it, rc); continue; }
-                    {   // the FP64 matvec of the FP32 direction z_j (converted once)
-                        Scope sc(h, PF_CONV, 12.0 * n, it->s);
-                        launch_convert<float, double>(n, h->Z[j], h->tmp, it->s);
-                    }
-                    Scope sc(h, PF_MATVEC, bytes_matvec(g, 8), it->s, stress_kernels(g));
-                    launch_stokes_matvec_stress(g, h->lev[0].cd, h->sw, h->tmp, nullptr, h->V[j + 1], it->s);
-                } else {
-                    {
-                        Scope sc(h, PF_MATVEC, bytes_matvec(g, 8), it->s, stress_kernels(g));
-                        launch_stokes_matvec_stress(g, h->lev[0].cd, h->sw, h->V[j], nullptr, h->tmp, it->s);
-                    }
-                    if ((rc = run_precond<double>(h, prm.precond, h->tmp, h->V[j + 1], mp, it->s))) { finish(it, rc); continue; }
-                }
-                it->info.scalar_vcycles += scalar_vcycles(h, prm.precond, mp);
-                orth_enqueue(h, j, it->s);
-            }
-            sync_all(step);
-            for (Inst* it : step) {
-                if (it->done) continue;
-                const double* hp = it->h->hpin;
-                bool finite = std::isfinite(hp[HP_AFTER]);
-                for (int i = 0; i <= j; ++i) {
-                    it->hcol[i] = hp[HP_H + i];
-                    finite = finite && std::isfinite(it->hcol[i]);
-                }
-                if (!finite) finish(it, fail(it->h, STK_ERR_NONFINITE, "non-finite value in the Arnoldi process"));
-            }
-            for (Inst* it : step) {
-                if (it->done) continue;
-                stk_handle* h = it->h;
-                const int n = nstokes(h);
-                it->hcol[j + 1] = std::sqrt(h->hpin[HP_AFTER]);
-                if (it->hcol[j + 1] > 0.0) {
-                    Scope sc(h, PF_COMB, 16.0 * n, it->s);
-                    launch_scale(n, h->V[j + 1], 1.0 / it->hcol[j + 1], it->s);
-                }
-                ++it->info.iterations;
-                it->k = j + 1;
-                const double est = it->ar.add_column(j, it->hcol.data());
-                it->info.est_residual = est / it->bnorm;
-                if (est <= it->target || it->hcol[j + 1] == 0.0) it->in_cycle = false;
-            }
-        }
-        // x += V y (left) or Z y (flexible)
-        for (Inst* it : run) {
-            if (it->done) continue;
-            stk_handle* h = it->h;
-            const int n = nstokes(h);
-            const int k = it->k;
-            it->in_cycle = false;
-            ++it->info.restarts;
-            if (k == 0) continue;
-            it->ar.solve(k, it->y.data());
-            bool ok = true;
-            for (int i = 0; i < k; ++i) ok = ok && std::isfinite(it->y[i]);
-            if (!ok) { finish(it, fail(h, STK_ERR_NONFINITE, "non-finite GMRES update")); continue; }
-            std::memcpy(h->hpin + HP_Y, it->y.data(), sizeof(double) * k);
-            cudaMemcpyAsync(h->dsc + DS_Y, h->hpin + HP_Y, sizeof(double) * k, cudaMemcpyHostToDevice, it->s);
-            Scope sc(h, PF_COMB, (flex ? 4.0 : 8.0) * n * k + 16.0 * n, it->s);
-            if (flex) {
-                std::vector<const float*> Zp(h->Z.begin(), h->Z.begin() + k);
-                launch_combine<float>(n, k, Zp.data(), h->dsc + DS_Y, h->xk, it->s);
-            } else {
-                std::vector<const double*> Vp(h->V.begin(), h->V.begin() + k);
-                launch_combine<double>(n, k, Vp.data(), h->dsc + DS_Y, h->xk, it->s);
-            }
-        }
+        for (Inst* it : act)
+            if (!it->done) absorb_cycle(it, prm, mp);
     }
     std::vector<Inst*> all;
     for (auto& it : insts) all.push_back(&it);
+    // residual histories of the solve
+    for (Inst* it : all) {
+        stk_handle* h = it->h;
+        cudaMemcpyAsync(h->gst_host, h->gst, sizeof(GmState), cudaMemcpyDeviceToHost, it->s);
+    }
     sync_all(all);
+    for (Inst* it : all) {
+        const GmState& st = *it->h->gst_host;
+        it->h->hist_true.assign(st.hist, st.hist + std::min(st.nhist, GM_NHIST));
+        it->h->hist_est.assign(st.est_hist, st.est_hist + std::min(st.nest, GM_NEST));
+    }
 }
 
 int validate_params(stk_handle* h, const stk_solver_params& prm) {
@@ -1291,6 +1399,12 @@ int stk_create(int dim, const int* n, double hh, const int* bc, stk_handle** out
         void* p = nullptr;
         CKC(cudaMallocHost(&p, sizeof(double) * 256));
         h->hpin = static_cast<double*>(p);
+        double* q = nullptr;
+        CKC(dalloc(h, &q, (sizeof(GmState) + 7) / 8));
+        h->gst = reinterpret_cast<GmState*>(q);
+        CKC(cudaMallocHost(&p, sizeof(GmState)));
+        h->gst_host = static_cast<GmState*>(p);
+        std::memset(h->gst_host, 0, sizeof(GmState));
     }
     CKC(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
     CKC(cudaStreamCreateWithFlags(&h->run, cudaStreamNonBlocking));
@@ -1326,6 +1440,7 @@ int stk_destroy(stk_handle* h) {
     if (h->join) cudaEventDestroy(h->join);
     for (void* p : h->allocs) cudaFree(p);
     if (h->hpin) cudaFreeHost(h->hpin);
+    if (h->gst_host) cudaFreeHost(h->gst_host);
     for (auto e : h->evpool) cudaEventDestroy(e);
     delete h;
     return STK_OK;
@@ -1800,6 +1915,14 @@ int stk_gradient(stk_handle* h, const double* const* u, const double* const* lam
     }
     CKL();
     return STK_OK;
+}
+
+int stk_solve_history(const stk_handle* h, int kind, double* out, int cap) {
+    if (!h || (kind != 0 && kind != 1) || cap < 0) return STK_ERR_ARG;
+    const std::vector<double>& v = kind == 0 ? h->hist_true : h->hist_est;
+    if (out)
+        for (int i = 0; i < cap && i < (int)v.size(); ++i) out[i] = v[i];
+    return (int)v.size();
 }
 
 int stk_remove_mean(stk_handle* h, const double* x_p, double* y_p, void* stream) {

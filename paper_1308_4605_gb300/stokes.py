@@ -100,6 +100,7 @@ def _load():
         "stk_solve_batched": (I, [I, ctypes.POINTER(P), ctypes.POINTER(stk_solver_params),
                                   ctypes.POINTER(stk_batch_io), ctypes.POINTER(stk_solve_info), P]),
         "stk_remove_mean": (I, [P, P, P, P]),
+        "stk_solve_history": (I, [P, I, ctypes.POINTER(D), I]),
         "stk_pressure_vcycle_noalloc": (I, [I, ctypes.POINTER(I), D, ctypes.POINTER(I), P, P, P, P]),
         "stk_profile_read": (I, [P, I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong),
                                  ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D)]),
@@ -115,7 +116,7 @@ _lib = _load()
 EXPORTED = ["stk_default_params", "stk_create", "stk_destroy", "stk_last_error", "stk_face_length",
             "stk_cell_length", "stk_set_coefficients", "stk_set_bulk_viscosity", "stk_apply_operator",
             "stk_apply_preconditioner", "stk_apply_preconditioner_params", "stk_velocity_vcycle", "stk_pressure_vcycle", "stk_solve",
-            "stk_profile", "stk_profile_read", "stk_kernel_launches", "stk_pressure_vcycle_noalloc", "stk_remove_mean", "stk_gradient", "stk_backward_euler_rhs", "stk_subtract_boundary_terms", "stk_solve_batched", "stk_get_schedule", "stk_set_schedule", "stk_autotune"]
+            "stk_profile", "stk_profile_read", "stk_kernel_launches", "stk_pressure_vcycle_noalloc", "stk_remove_mean", "stk_solve_history", "stk_gradient", "stk_backward_euler_rhs", "stk_subtract_boundary_terms", "stk_solve_batched", "stk_get_schedule", "stk_set_schedule", "stk_autotune"]
 
 
 def library():
@@ -342,6 +343,17 @@ def stk_gradient(h, u, lam, dlogmu, drho, stream=None):
 def stk_remove_mean(h, x_p, y_p, stream=None):
     nc = stk_cell_length(h)
     return _check(h, _lib.stk_remove_mean(h, _ptr(x_p, nc), _ptr(y_p, nc), _stream(stream)))
+
+
+def stk_solve_history(h, kind):
+    """Residual history of the last solve on h: kind 0 the true relative
+    residual at every cycle start, kind 1 the Arnoldi estimates (stokes.h)."""
+    n = int(_lib.stk_solve_history(h, int(kind), None, 0))
+    if n < 0:
+        raise StokesError(n, "stk_solve_history failed")
+    buf = (ctypes.c_double * max(n, 1))()
+    got = int(_lib.stk_solve_history(h, int(kind), buf, n))
+    return [buf[i] for i in range(min(n, got))]
 
 
 def stk_kernel_launches(h):

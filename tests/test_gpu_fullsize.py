@@ -108,7 +108,7 @@ def _solve(S, pr, precision):
 def test_full_size_solves_match_oracle(S, oracle, cfg):
     pr = wl.config_c3(128) if cfg == "c3" else wl.config_c5(128)
     sols = [_solve(S, pr, precision) for precision in (0, 1)]
-    ref = oracle[cfg].get()
+    ref = oracle[cfg].get(timeout=1800)
     for x_u, x_p in sols:
         g, x = _pack(pr, x_u, x_p)
         _compare(g, pr, x, ref)
@@ -137,7 +137,7 @@ def test_full_batched_workload_matches_oracle(S, oracle):
         assert info["converged"] and info["true_residual"] <= 1e-10, (i, info)
     for i, pr in enumerate(prs):
         g, x = _pack(pr, xus[i], xps[i])
-        _compare(g, pr, x, oracle["c4"][i].get())
+        _compare(g, pr, x, oracle["c4"][i].get(timeout=1800))
 
 
 @pytest.mark.parametrize("precision", [0, 1])
