@@ -57,6 +57,14 @@ __global__ void k_gm_begin(GmState* st, const double* __restrict__ bn2, double r
     for (int i = 0; i < GM_NCOND; ++i) st->cond[i] = 0;
 }
 
+// graph cycles: the stopping test runs only while the solve is running (a
+// finished instance of a batch graph costs this one kernel per cycle)
+__global__ void k_gm_gate(GmState* st, cudaGraphConditionalHandle hchk) {
+    pdl_entry();
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    set_cond(st, GM_COND_CHK, st->state == GM_RUNNING ? 1u : 0u, hchk, 1);
+}
+
 // cycle start, after r = b - M x and ||r||^2: record the true residual, stop
 // on convergence, maxit or a non-finite residual; otherwise open the cycle
 __global__ void k_gm_check(GmState* st, const double* __restrict__ rn2,
@@ -64,6 +72,9 @@ __global__ void k_gm_check(GmState* st, const double* __restrict__ rn2,
     pdl_entry();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     st->k = 0;
+    st->cond[GM_COND_CHK] = 1;
+    st->cond[GM_COND_FIN] = 0;
+    for (int j = 0; j < GM_MMAX; ++j) st->cond[GM_COND_STEP0 + j] = 0;
     unsigned go = 0;
     if (st->state == GM_RUNNING) {
         const double rn = sqrt(*rn2);
@@ -199,6 +210,9 @@ void launch_gm_begin(GmState* st, const double* bn2, double rtol, int maxit, int
 void launch_gm_check(GmState* st, const double* rn2, cudaGraphConditionalHandle hpre, int use,
                      cudaStream_t s) {
     launch_pdl(k_gm_check, dim3(1), dim3(32), s, st, rn2, hpre, use);
+}
+void launch_gm_gate(GmState* st, cudaGraphConditionalHandle hchk, cudaStream_t s) {
+    launch_pdl(k_gm_gate, dim3(1), dim3(32), s, st, hchk);
 }
 void launch_gm_start(GmState* st, const double* vn2, cudaGraphConditionalHandle h0, int use0,
                      cudaGraphConditionalHandle hfin, int usefin, cudaStream_t s) {

@@ -256,12 +256,13 @@ void launch_schur_combine(int n, const double* theta, const T* phi, const T* mu2
 // Hessenberg matrix, the Givens rotations, the rotated right-hand side g, the
 // least-squares solution y, the residuals and the stopping decisions of the
 // current cycle.  cond[] holds the decisions that gate the next phase: the
-// preconditioned start of a cycle (GM_COND_PRE), its final update
-// (GM_COND_FIN) and Arnoldi step j (GM_COND_STEP0 + j).
+// stopping test of a cycle (GM_COND_CHK, open while the solve runs), its
+// preconditioned start (GM_COND_PRE), its final update (GM_COND_FIN) and
+// Arnoldi step j (GM_COND_STEP0 + j).
 constexpr int GM_MMAX = 32;
 constexpr int GM_NHIST = 256;    // true relative residuals at cycle starts kept
 constexpr int GM_NEST = 2048;    // Arnoldi residual estimates kept
-constexpr int GM_COND_PRE = 0, GM_COND_FIN = 1, GM_COND_STEP0 = 2;
+constexpr int GM_COND_PRE = 0, GM_COND_FIN = 1, GM_COND_CHK = 2, GM_COND_STEP0 = 3;
 constexpr int GM_NCOND = GM_COND_STEP0 + GM_MMAX;
 enum { GM_RUNNING = 0, GM_CONVERGED = 1, GM_MAXIT = 2, GM_NONFINITE = 3 };
 enum { GM_WHY_RHS = 1, GM_WHY_RESIDUAL, GM_WHY_PRECOND, GM_WHY_ARNOLDI, GM_WHY_UPDATE };
@@ -284,6 +285,8 @@ void launch_gm_begin(GmState* st, const double* bn2, double rtol, int maxit, int
                      cudaStream_t s);
 void launch_gm_check(GmState* st, const double* rn2, cudaGraphConditionalHandle hpre, int use,
                      cudaStream_t s);
+// graph only: open the cycle's stopping test while the solve is running
+void launch_gm_gate(GmState* st, cudaGraphConditionalHandle hchk, cudaStream_t s);
 void launch_gm_start(GmState* st, const double* vn2, cudaGraphConditionalHandle h0, int use0,
                      cudaGraphConditionalHandle hfin, int usefin, cudaStream_t s);
 void launch_gm_step(GmState* st, int j, const double* hcol, const double* n2,

@@ -8,6 +8,7 @@
 #include "../../include/stokes.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstddef>
@@ -135,10 +136,21 @@ struct stk_handle {
     // (precond, flexible, m, nu, ncoarse, cycles); kernels per phase
     struct CycleGraph {
         cudaGraphExec_t exec = nullptr;
-        long long k_chk = 0, k_pre = 0, k_fin = 0;
+        long long k_gate = 0, k_chk = 0, k_pre = 0, k_fin = 0;
         std::vector<long long> k_step;
     };
     std::map<std::tuple<int, int, int, int, int, int>, CycleGraph> cgraphs;
+    // one graph holding the cycles of a whole batch led by this handle
+    // (stk_solve_batched): the members' (uid, generation) pairs and the
+    // parameter key it was built for, and each member's kernels per phase
+    struct BatchGraph {
+        cudaGraphExec_t exec = nullptr;
+        std::vector<long long> sig;
+        std::vector<CycleGraph> members;
+    };
+    BatchGraph batch;
+    long long uid = 0;             // unique per handle in this process
+    long long gen = 0;             // bumped whenever the graphs are cleared
     GmState* gst = nullptr;        // device state of the GMRES least-squares problem
     GmState* gst_host = nullptr;   // pinned copy
     std::vector<double> hist_true, hist_est;   // residual histories of the last solve
@@ -690,8 +702,11 @@ void apply_precond(stk_handle* h, int which, const T* b, T* x, const MGParams& m
 }
 
 void clear_graphs(stk_handle* h) {
-    if (h->graphs.empty() && h->cgraphs.empty()) return;
+    ++h->gen;   // batch graphs that contain this handle's cycles become stale
+    if (h->graphs.empty() && h->cgraphs.empty() && !h->batch.exec) return;
     cudaDeviceSynchronize();   // no launch of these graphs may still be in flight
+    if (h->batch.exec) cudaGraphExecDestroy(h->batch.exec);
+    h->batch = stk_handle::BatchGraph{};
     for (auto& kv : h->graphs) {
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
         for (auto& r : kv.second.recs) {
@@ -919,24 +934,23 @@ void enq_fin(const CycleCtx& c, cudaStream_t s) {
     }
 }
 
-// Build the graph of one GMRES cycle: a chain of conditional (if) nodes,
-// each holding one phase captured from the enqueue functions above; the
-// first node's condition is 1 at every launch, the others are set by the
-// kernels of the phase before them.
-int build_cycle_graph(const CycleCtx& c, stk_handle::CycleGraph& out) {
+// Append the chain of one instance's GMRES cycle to the graph G: conditional
+// (if) nodes, each holding one phase captured from the enqueue functions
+// above.  The first node's condition is 1 at every launch; its gate kernel
+// opens the stopping test only while the instance is still running, and each
+// later condition is set by the kernels of the phase before it.
+int build_chain(cudaGraph_t G, const CycleCtx& c, stk_handle::CycleGraph& out) {
     stk_handle* h = c.h;
-    cudaGraph_t G = nullptr;
-    CK(cudaGraphCreate(&G, 0));
     const int m = c.m;
-    std::vector<cudaGraphConditionalHandle> hs(m + 3);   // check, pre, fin, step 0..m-1
+    std::vector<cudaGraphConditionalHandle> hs(m + 4);   // gate, check, pre, fin, step 0..m-1
     int rc = STK_OK;
-    for (int i = 0; i < m + 3 && rc == STK_OK; ++i) {
+    for (int i = 0; i < m + 4 && rc == STK_OK; ++i) {
         cudaError_t e = cudaGraphConditionalHandleCreate(&hs[i], G, i == 0 ? 1u : 0u,
                                                          cudaGraphCondAssignDefault);
         if (e != cudaSuccess) rc = fail(h, STK_ERR_CUDA, "conditional handle: %s", cudaGetErrorString(e));
     }
-    const cudaGraphConditionalHandle hchk = hs[0], hpre = hs[1], hfin = hs[2];
-    auto hstep = [&](int j) { return hs[3 + j]; };
+    const cudaGraphConditionalHandle hgate = hs[0], hchk = hs[1], hpre = hs[2], hfin = hs[3];
+    auto hstep = [&](int j) { return hs[4 + j]; };
     cudaGraphNode_t prev = nullptr;
     // add an if-node after prev whose body is captured from fn(stream)
     auto add_if = [&](cudaGraphConditionalHandle hc, auto&& fn, long long& kernels) -> int {
@@ -965,6 +979,11 @@ int build_cycle_graph(const CycleCtx& c, stk_handle::CycleGraph& out) {
         return STK_OK;
     };
     out.k_step.assign(m, 0);
+    add_if(hgate, [&](cudaStream_t s) {
+        Scope sc(h, PF_ALG, 0.0, s);
+        launch_gm_gate(h->gst, hchk, s);
+        return STK_OK;
+    }, out.k_gate);
     add_if(hchk, [&](cudaStream_t s) { enq_check(c, s, hpre, 1); return STK_OK; }, out.k_chk);
     add_if(hpre, [&](cudaStream_t s) { return enq_pre(c, s, hstep(0), hfin, 1); }, out.k_pre);
     for (int j = 0; j < m; ++j)
@@ -973,13 +992,41 @@ int build_cycle_graph(const CycleCtx& c, stk_handle::CycleGraph& out) {
             return STK_OK;
         }, out.k_step[j]);
     add_if(hfin, [&](cudaStream_t s) { enq_fin(c, s); return STK_OK; }, out.k_fin);
-    if (rc == STK_OK) {
-        cudaError_t e = cudaGraphInstantiate(&out.exec, G, 0);
-        if (e != cudaSuccess) {
-            out.exec = nullptr;
-            rc = fail(h, STK_ERR_CUDA, "cycle graph instantiate: %s", cudaGetErrorString(e));
-        }
+    return rc;
+}
+
+int instantiate(stk_handle* h, cudaGraph_t G, cudaGraphExec_t* exec) {
+    cudaError_t e = cudaGraphInstantiate(exec, G, 0);
+    if (e != cudaSuccess) {
+        *exec = nullptr;
+        cudaGetLastError();
+        return fail(h, STK_ERR_CUDA, "cycle graph instantiate: %s", cudaGetErrorString(e));
     }
+    return STK_OK;
+}
+
+// The graph of one GMRES cycle of one instance.
+int build_cycle_graph(const CycleCtx& c, stk_handle::CycleGraph& out) {
+    stk_handle* h = c.h;
+    cudaGraph_t G = nullptr;
+    CK(cudaGraphCreate(&G, 0));
+    int rc = build_chain(G, c, out);
+    if (rc == STK_OK) rc = instantiate(h, G, &out.exec);
+    cudaGraphDestroy(G);
+    cudaGetLastError();
+    return rc;
+}
+
+// The graph of one GMRES cycle of every instance of a batch: independent
+// chains in one graph, so the whole batch advances by one graph launch.
+int build_batch_graph(const std::vector<CycleCtx>& cs, stk_handle::BatchGraph& out) {
+    stk_handle* h = cs[0].h;
+    cudaGraph_t G = nullptr;
+    CK(cudaGraphCreate(&G, 0));
+    out.members.assign(cs.size(), stk_handle::CycleGraph{});
+    int rc = STK_OK;
+    for (size_t i = 0; i < cs.size() && rc == STK_OK; ++i) rc = build_chain(G, cs[i], out.members[i]);
+    if (rc == STK_OK) rc = instantiate(h, G, &out.exec);
     cudaGraphDestroy(G);
     cudaGetLastError();
     return rc;
@@ -1040,7 +1087,8 @@ void absorb_cycle(Inst* it, const stk_solver_params& prm, const MGParams& mp) {
     it->info.est_residual = st.est / st.bnorm;
     if (it->cg) {   // kernels the graph ran: the gates the device opened
         const auto& cg = *it->cg;
-        h->nkern += cg.k_chk + (st.cond[GM_COND_PRE] ? cg.k_pre : 0) + (st.cond[GM_COND_FIN] ? cg.k_fin : 0);
+        h->nkern += cg.k_gate + (st.cond[GM_COND_CHK] ? cg.k_chk : 0) +
+                    (st.cond[GM_COND_PRE] ? cg.k_pre : 0) + (st.cond[GM_COND_FIN] ? cg.k_fin : 0);
         for (int j = 0; j < steps && j < (int)cg.k_step.size(); ++j) h->nkern += cg.k_step[j];
     }
     it->it_before = st.iterations;
@@ -1065,7 +1113,7 @@ void absorb_cycle(Inst* it, const stk_solver_params& prm, const MGParams& mp) {
 // With graphs each cycle of every active instance is one graph launch on its
 // stream and the host synchronises once per cycle for the whole batch;
 // without graphs (profiling) once per phase.
-void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm) {
+void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm, bool batch_graph) {
     const int m = prm.restart;
     const bool flex = prm.precision == STK_MIXED;
     MGParams mp;
@@ -1095,9 +1143,35 @@ void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm) {
             finish(it, STK_OK);
         }
     }
+    // one graph for the cycles of the whole batch (built on first use for
+    // this batch composition and configuration, kept by the first handle)
+    stk_handle::BatchGraph* bg = nullptr;
+    if (batch_graph) {
+        stk_handle* h0 = insts[0].h;
+        std::vector<long long> sig = {prm.precond, flex ? 1 : 0, m, mp.nu, mp.ncoarse, mp.cu * 1000 + mp.cp};
+        for (auto& it : insts) {
+            sig.push_back(it.h->uid);
+            sig.push_back(it.h->gen);
+        }
+        if (!h0->batch.exec || h0->batch.sig != sig) {
+            if (h0->batch.exec) {
+                cudaDeviceSynchronize();
+                cudaGraphExecDestroy(h0->batch.exec);
+            }
+            h0->batch = stk_handle::BatchGraph{};
+            std::vector<CycleCtx> cs;
+            for (auto& it : insts) cs.push_back(CycleCtx{it.h, prm.precond, m, flex, mp});
+            if (build_batch_graph(cs, h0->batch) == STK_OK) h0->batch.sig = sig;
+            else h0->batch = stk_handle::BatchGraph{};
+        }
+        if (h0->batch.exec) {
+            bg = &h0->batch;
+            for (size_t i = 0; i < insts.size(); ++i) insts[i].cg = &bg->members[i];
+        }
+    }
     // graphs of the cycle (built on first use per handle and configuration)
     for (Inst* it : act) {
-        if (it->done) continue;
+        if (it->done || bg) continue;
         stk_handle* h = it->h;
         it->cg = nullptr;
         if (!h->use_graphs || h->prof) continue;
@@ -1120,7 +1194,16 @@ void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm) {
             if (!it.done) act.push_back(&it);
         if (act.empty()) break;
         std::vector<Inst*> eager;
+        if (bg) {   // the whole batch: one launch (finished instances stop at their gate)
+            cudaError_t e = cudaGraphLaunch(bg->exec, act[0]->s);
+            if (e != cudaSuccess) {
+                const int rc = fail(act[0]->h, STK_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e));
+                for (Inst* it : act) finish(it, rc);
+            }
+            for (Inst* it : act) read_header(it);
+        }
         for (Inst* it : act) {
+            if (bg) break;
             if (it->cg) {
                 cudaError_t e = cudaGraphLaunch(it->cg->exec, it->s);
                 if (e != cudaSuccess) { finish(it, fail(it->h, STK_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e))); continue; }
@@ -1293,6 +1376,8 @@ int stk_create(int dim, const int* n, double hh, const int* bc, stk_handle** out
     for (int a = 0; a < dim; ++a) total *= nn[a];
     if (total * (dim + 1) > (1LL << 30)) return fail(nullptr, STK_ERR_SIZE, "grid too large");
     h = new stk_handle();
+    static std::atomic<long long> next_uid{0};
+    h->uid = ++next_uid;
     cudaGetDevice(&h->device);
     h->dim = dim;
     int cur[3] = {nn[0], nn[1], nn[2]};
@@ -1723,16 +1808,21 @@ int stk_solve_batched(int count, stk_handle* const* hs, const stk_solver_params*
         CK(cudaEventCreate(&e1));
         CK(cudaEventRecord(e0, us));
     }
+    // several instances with graphs: one graph for the whole batch, launched
+    // on the caller's stream; otherwise each instance on its own stream
+    bool batch_graph = count > 1;
+    for (int i = 0; i < count; ++i) batch_graph = batch_graph && hs[i]->use_graphs && !hs[i]->prof;
+    const bool fork = count > 1 && !batch_graph;
     for (int i = 0; i < count; ++i) {
         Inst& it = insts[i];
         it.h = hs[i];
-        it.s = count == 1 ? us : hs[i]->run;
-        if (count > 1) cudaStreamWaitEvent(it.s, e0, 0);
+        it.s = fork ? hs[i]->run : us;
+        if (fork) cudaStreamWaitEvent(it.s, e0, 0);
         int rc = gather(it.h, io[i].b_u, io[i].b_p, it.h->bk, it.s);
         if (!rc) rc = gather(it.h, io[i].x_u, io[i].x_p, it.h->xk, it.s);
         if (rc) finish(&it, rc);
     }
-    gmres_lockstep(insts, prm);
+    gmres_lockstep(insts, prm, batch_graph);
     int worst = STK_OK;
     for (int i = 0; i < count; ++i) {
         Inst& it = insts[i];
@@ -1740,7 +1830,7 @@ int stk_solve_batched(int count, stk_handle* const* hs, const stk_solver_params*
             int rc2 = scatter(it.h, it.h->xk, io[i].x_u, io[i].x_p, it.s);
             if (rc2) it.rc = rc2;
         }
-        if (count > 1) {
+        if (fork) {
             cudaEventRecord(it.h->join, it.s);
             cudaStreamWaitEvent(us, it.h->join, 0);
         }

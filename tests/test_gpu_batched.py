@@ -124,13 +124,14 @@ def test_schedules_change_timing_not_results(S, tmp_path):
     sv.close()
 
 
-@pytest.mark.parametrize("bc", [(0,) * 6, (1, 1, 2, 1, 0, 0)])
-def test_two_colour_sweeps_equal_per_colour_3d(S, bc):
+@pytest.mark.parametrize("n,bc", [((64, 32, 16), (0,) * 6), ((32, 16, 16), (1, 1, 2, 1, 0, 0)),
+                                  ((16, 32, 64), (1, 1, 0, 0, 2, 1)), ((128, 16, 32), (0,) * 6)])
+def test_two_colour_sweeps_equal_per_colour_3d(S, n, bc):
     """3D: V-cycles and solves (FP64 and mixed) with the two-colour kernels
-    on every grid level equal, bitwise, those with one launch per colour
-    (periodic, and mixed no-slip / free-slip / periodic boundaries whose
-    face arrays are not multiples of the tile)."""
-    n = (64, 32, 16) if bc[0] == 0 else (32, 16, 16)
+    (columns marching along z) on every grid level equal, bitwise, those with
+    one launch per colour (periodic, and mixed no-slip / free-slip / periodic
+    boundaries whose face arrays are not multiples of the column; several
+    columns along x and several z ranges per column)."""
     theta = 1.0 if bc[0] == 0 else 0.0
     pr = wl.generic(3, n, bc, theta=theta, seed=41, precond=1 if theta else 2)
     sv = S.StokesSolver(3, pr.n, pr.bc, pr.h)
