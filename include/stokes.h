@@ -309,6 +309,21 @@ long long stk_kernel_launches(const stk_handle* h);
 int stk_profile_read(stk_handle* h, int k, const char** name, long long* launches,
                      double* ms, double* bytes, double* flops);
 
+/* Bounds-checked builds (compiled with -DSTK_BOUNDS_CHECK: `python -m
+ * paper_1308_4605_gb300.build --bounds-check` writes libstokes_gb300_check.so
+ * beside the release library): every array index the stencil, transfer and
+ * coarse-level kernels form is checked against the length of its array; an
+ * index out of range is counted and the access goes to element 0 instead, so
+ * nothing traps or faults.  stk_bounds_violations returns the number counted
+ * since the library was loaded or last reset (reset != 0 clears it), with the
+ * kind of the first (1 face, 2 cell, 3 edge, 4 shared memory) and its value
+ * (either pointer may be NULL); it synchronises the device.  Release builds
+ * return -1.  stk_bounds_selftest launches a kernel that checks the index 7
+ * against the length 7 without accessing memory (one count of kind 2);
+ * release builds return STK_ERR_STATE. */
+long long stk_bounds_violations(long long* first_kind, long long* first_index, int reset);
+int stk_bounds_selftest(void* stream);
+
 /* Pressure V-cycle for callers that cannot allocate device memory.
  * (No counterpart in the paper: this is a deployment variant of
  * stk_pressure_vcycle.)  Callers whose device memory is wholly owned by another

@@ -414,4 +414,6 @@ template void launch_coarse_vcycle_cell<double>(int, const CLevel<double>*, int,
 template void launch_coarse_vcycle_cell<float>(int, const CLevel<float>*, int, const float*,
                                                float*, int, int, size_t, cudaStream_t);
 
+STK_OOB_READER(coarse)
+
 }  // namespace stk

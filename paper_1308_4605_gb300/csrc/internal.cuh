@@ -124,6 +124,54 @@ __device__ __forceinline__ void pdl_entry() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+// Bounds-checked builds (nvcc -DSTK_BOUNDS_CHECK, `build.py --bounds-check`):
+// the stencil index helpers check every index against the length of the
+// array it addresses.  An index out of range is counted, the first one is
+// recorded with its kind (1 face, 2 cell, 3 edge, 4 shared memory), and the
+// access goes to element 0 instead, so it stays in bounds and the kernel
+// runs to its end: no trap and no fault.  Each translation unit keeps its
+// own record (module-local device variable) and exports a reader through
+// STK_OOB_READER(name).  Release builds compile the checks away.
+#ifdef STK_BOUNDS_CHECK
+namespace {
+__device__ unsigned long long g_oob[3];   // count, first kind, first index
+}
+__device__ __forceinline__ int chk_index(int i, int n, int kind) {
+    if (i >= 0 && i < n) return i;
+    if (atomicAdd(&g_oob[0], 1ull) == 0ull) {
+        g_oob[1] = (unsigned long long)kind;
+        g_oob[2] = (unsigned long long)(long long)i;
+    }
+    return 0;
+}
+#define STK_IDX(i, n, kind) ::stk::chk_index((i), (n), (kind))
+// long long oob_<name>(long long first[2], int reset): this module's count
+#define STK_OOB_READER(name)                                                          \
+    long long oob_##name(long long first[2], int reset) {                             \
+        unsigned long long v[3] = {0, 0, 0};                                          \
+        if (cudaMemcpyFromSymbol(v, g_oob, sizeof v) != cudaSuccess) return -1;       \
+        if (first && v[0]) {                                                          \
+            first[0] = (long long)v[1];                                               \
+            first[1] = (long long)v[2];                                               \
+        }                                                                             \
+        if (reset) {                                                                  \
+            const unsigned long long z[3] = {0, 0, 0};                                \
+            cudaMemcpyToSymbol(g_oob, z, sizeof z);                                   \
+        }                                                                             \
+        return (long long)v[0];                                                       \
+    }
+long long oob_kernels(long long first[2], int reset);
+long long oob_pair(long long first[2], int reset);
+long long oob_stress(long long first[2], int reset);
+long long oob_coarse(long long first[2], int reset);
+// a kernel that checks index n against length n (out of range by one)
+// without any memory access: exercises the record in bounds-checked builds
+void launch_oob_selftest(int n, cudaStream_t s);
+#else
+#define STK_IDX(i, n, kind) (i)
+#define STK_OOB_READER(name)
+#endif
+
 // zero n elements (a kernel, so that it takes part in the launch chain)
 template <typename T>
 void launch_zero(int n, T* x, cudaStream_t s);

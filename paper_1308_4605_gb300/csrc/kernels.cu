@@ -981,4 +981,15 @@ STK_INST(float)
 template void launch_convert<double, float>(int, const double*, float*, cudaStream_t);
 template void launch_convert<float, double>(int, const float*, double*, cudaStream_t);
 
+#ifdef STK_BOUNDS_CHECK
+namespace {
+// index n against length n: recorded as out of range; no memory is accessed
+__global__ void k_oob_selftest(int n) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) (void)STK_IDX(n, n, 2);
+}
+}  // namespace
+void launch_oob_selftest(int n, cudaStream_t s) { k_oob_selftest<<<1, 32, 0, s>>>(n); }
+#endif
+STK_OOB_READER(kernels)
+
 }  // namespace stk

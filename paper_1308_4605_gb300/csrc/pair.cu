@@ -106,7 +106,7 @@ k_vel_gs_pair(Geom g, Coef<T> C, const T* src, T* dst, const T* __restrict__ rhs
         const int sx = slot(r[0], ox, WX, e0);
         const int sy = slot(r[1], oy, WY, e1);
         const int sz = DIM == 3 ? slot(r[2], oz, WZ, e2) : 0;
-        return (sz * WY + sy) * WX + sx;
+        return STK_IDX((sz * WY + sy) * WX + sx, WZ * WY * WX, 4);
     };
     const T* Rf = &R[0][0][0];
     auto ga = [&](int i) { return Rf[i]; };
@@ -168,7 +168,7 @@ k_cell_gs_pair(Geom g, Coef<T> C, const T* src, T* dst, const T* __restrict__ rh
         const int sx = slot(r[0], ox, WX, e0);
         const int sy = slot(r[1], oy, WY, e1);
         const int sz = DIM == 3 ? slot(r[2], oz, WZ, e2) : 0;
-        return R[sz][sy][sx];
+        return (&R[0][0][0])[STK_IDX((sz * WY + sy) * WX + sx, WZ * WY * WX, 4)];
     };
     dst[cidx(g, q)] = cell_gs_value<DIM, T>(g, C, q, pc, rhs);
 }
@@ -256,7 +256,7 @@ k_vel_gs_zpair(Geom g, Coef<T> C, const T* src, T* dst, const T* __restrict__ rh
         auto aidx = [&](const int* r) {
             const int sx = slot(r[0], ox, WX, e0);
             const int sy = slot(r[1], oy, WY, e1);
-            return (ring_slot(g, r[2], kb, e2) * WY + sy) * WX + sx;
+            return STK_IDX((ring_slot(g, r[2], kb, e2) * WY + sy) * WX + sx, 3 * WY * WX, 4);
         };
         auto ga = [&](int i) { return Rf[i]; };
         T dsum;
@@ -324,7 +324,7 @@ k_cell_gs_zpair(Geom g, Coef<T> C, const T* src, T* dst, const T* __restrict__ r
         auto pc = [&](const int* r) {
             const int sx = slot(r[0], ox, WX, e0);
             const int sy = slot(r[1], oy, WY, e1);
-            return R[ring_slot(g, r[2], kb, e2)][sy][sx];
+            return (&R[0][0][0])[STK_IDX((ring_slot(g, r[2], kb, e2) * WY + sy) * WX + sx, 3 * WY * WX, 4)];
         };
         dst[cidx(g, q)] = cell_gs_value<3, T>(g, C, q, pc, rhs);
     };
@@ -387,5 +387,7 @@ template void launch_cell_gs_pair<double>(const Geom&, Coef<double>, const doubl
                                           const double*, cudaStream_t);
 template void launch_cell_gs_pair<float>(const Geom&, Coef<float>, const float*, float*,
                                          const float*, cudaStream_t);
+
+STK_OOB_READER(pair)
 
 }  // namespace stk

@@ -7,8 +7,9 @@
 #include "internal.cuh"
 #include "../../include/stokes.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
-#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstddef>
@@ -24,6 +25,15 @@ using namespace stk;
 namespace {
 
 thread_local std::string g_create_error;
+
+// NVTX range over a host-side phase (visible to Nsight tools; a no-op
+// without an attached tool)
+struct Nvtx {
+    explicit Nvtx(const char* name) { nvtxRangePushA(name); }
+    ~Nvtx() { nvtxRangePop(); }
+    Nvtx(const Nvtx&) = delete;
+    Nvtx& operator=(const Nvtx&) = delete;
+};
 
 struct ProfRec {
     int cat;
@@ -140,17 +150,7 @@ struct stk_handle {
         std::vector<long long> k_step;
     };
     std::map<std::tuple<int, int, int, int, int, int>, CycleGraph> cgraphs;
-    // one graph holding the cycles of a whole batch led by this handle
-    // (stk_solve_batched): the members' (uid, generation) pairs and the
-    // parameter key it was built for, and each member's kernels per phase
-    struct BatchGraph {
-        cudaGraphExec_t exec = nullptr;
-        std::vector<long long> sig;
-        std::vector<CycleGraph> members;
-    };
-    BatchGraph batch;
-    long long uid = 0;             // unique per handle in this process
-    long long gen = 0;             // bumped whenever the graphs are cleared
+
     GmState* gst = nullptr;        // device state of the GMRES least-squares problem
     GmState* gst_host = nullptr;   // pinned copy
     std::vector<double> hist_true, hist_est;   // residual histories of the last solve
@@ -702,11 +702,8 @@ void apply_precond(stk_handle* h, int which, const T* b, T* x, const MGParams& m
 }
 
 void clear_graphs(stk_handle* h) {
-    ++h->gen;   // batch graphs that contain this handle's cycles become stale
-    if (h->graphs.empty() && h->cgraphs.empty() && !h->batch.exec) return;
+    if (h->graphs.empty() && h->cgraphs.empty()) return;
     cudaDeviceSynchronize();   // no launch of these graphs may still be in flight
-    if (h->batch.exec) cudaGraphExecDestroy(h->batch.exec);
-    h->batch = stk_handle::BatchGraph{};
     for (auto& kv : h->graphs) {
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
         for (auto& r : kv.second.recs) {
@@ -859,6 +856,17 @@ struct CycleCtx {
     MGParams mp;
 };
 
+// x = P^{-1} b inside a GMRES phase: captured kernel by kernel into a cycle
+// graph, otherwise as the preconditioner's own graph (run_precond)
+template <typename T>
+int precond_enqueue(stk_handle* h, int which, const T* b, T* x, const MGParams& mp, cudaStream_t s) {
+    if (h->capturing) {
+        apply_precond<T>(h, which, b, x, mp, s);
+        return STK_OK;
+    }
+    return run_precond<T>(h, which, b, x, mp, s);
+}
+
 // phase 1: r = b - M x, ||r||^2, stopping test (gate of phase 2)
 void enq_check(const CycleCtx& c, cudaStream_t s, cudaGraphConditionalHandle hpre, int use) {
     stk_handle* h = c.h;
@@ -879,7 +887,8 @@ int enq_pre(const CycleCtx& c, cudaStream_t s, cudaGraphConditionalHandle h0,
     if (c.flex) {
         CK(cudaMemcpyAsync(h->V[0], h->tmp, sizeof(double) * nstokes(h), cudaMemcpyDeviceToDevice, s));
     } else {
-        apply_precond<double>(h, c.which, h->tmp, h->V[0], c.mp, s);
+        int rc = precond_enqueue<double>(h, c.which, h->tmp, h->V[0], c.mp, s);
+        if (rc) return rc;
         norm_enqueue(h, h->V[0], h->dsc + DS_N2 + 2, s);
     }
     { Scope sc(h, PF_ALG, 0.0, s); launch_gm_start(h->gst, h->dsc + DS_N2 + 2, h0, use, hfin, use, s); }
@@ -887,7 +896,7 @@ int enq_pre(const CycleCtx& c, cudaStream_t s, cudaGraphConditionalHandle h0,
 }
 
 // phase 3 + j: Arnoldi step j (gate of step j + 1)
-void enq_step(const CycleCtx& c, int j, cudaStream_t s, cudaGraphConditionalHandle hn, int use) {
+int enq_step(const CycleCtx& c, int j, cudaStream_t s, cudaGraphConditionalHandle hn, int use) {
     stk_handle* h = c.h;
     const Geom& g = h->lev[0].g;
     const int n = nstokes(h);
@@ -900,7 +909,8 @@ void enq_step(const CycleCtx& c, int j, cudaStream_t s, cudaGraphConditionalHand
             Scope sc(h, PF_CONV, 12.0 * n, s);
             launch_convert<double, float>(n, h->V[j], h->pf.in, s);
         }
-        apply_precond<float>(h, c.which, h->pf.in, h->Z[j], c.mp, s);
+        int rc = precond_enqueue<float>(h, c.which, h->pf.in, h->Z[j], c.mp, s);
+        if (rc) return rc;
         {   // the FP64 matvec of the FP32 direction z_j (converted once)
             Scope sc(h, PF_CONV, 12.0 * n, s);
             launch_convert<float, double>(n, h->Z[j], h->tmp, s);
@@ -912,11 +922,13 @@ void enq_step(const CycleCtx& c, int j, cudaStream_t s, cudaGraphConditionalHand
             Scope sc(h, PF_MATVEC, bytes_matvec(g, 8), s, stress_kernels(g));
             launch_stokes_matvec_stress(g, h->lev[0].cd, h->sw, h->V[j], nullptr, h->tmp, s);
         }
-        apply_precond<double>(h, c.which, h->tmp, h->V[j + 1], c.mp, s);
+        int rc = precond_enqueue<double>(h, c.which, h->tmp, h->V[j + 1], c.mp, s);
+        if (rc) return rc;
     }
     orth_enqueue(h, j, s);
     Scope sc(h, PF_ALG, 0.0, s);
     launch_gm_step(h->gst, j, h->dsc + DS_H, h->dsc + DS_N2, hn, use, s);
+    return STK_OK;
 }
 
 // last phase: y = R^{-1} g, x += V y (left) or Z y (flexible)
@@ -988,8 +1000,7 @@ int build_chain(cudaGraph_t G, const CycleCtx& c, stk_handle::CycleGraph& out) {
     add_if(hpre, [&](cudaStream_t s) { return enq_pre(c, s, hstep(0), hfin, 1); }, out.k_pre);
     for (int j = 0; j < m; ++j)
         add_if(hstep(j), [&](cudaStream_t s) {
-            enq_step(c, j, s, j + 1 < m ? hstep(j + 1) : 0, j + 1 < m ? 1 : 0);
-            return STK_OK;
+            return enq_step(c, j, s, j + 1 < m ? hstep(j + 1) : 0, j + 1 < m ? 1 : 0);
         }, out.k_step[j]);
     add_if(hfin, [&](cudaStream_t s) { enq_fin(c, s); return STK_OK; }, out.k_fin);
     return rc;
@@ -1011,21 +1022,6 @@ int build_cycle_graph(const CycleCtx& c, stk_handle::CycleGraph& out) {
     cudaGraph_t G = nullptr;
     CK(cudaGraphCreate(&G, 0));
     int rc = build_chain(G, c, out);
-    if (rc == STK_OK) rc = instantiate(h, G, &out.exec);
-    cudaGraphDestroy(G);
-    cudaGetLastError();
-    return rc;
-}
-
-// The graph of one GMRES cycle of every instance of a batch: independent
-// chains in one graph, so the whole batch advances by one graph launch.
-int build_batch_graph(const std::vector<CycleCtx>& cs, stk_handle::BatchGraph& out) {
-    stk_handle* h = cs[0].h;
-    cudaGraph_t G = nullptr;
-    CK(cudaGraphCreate(&G, 0));
-    out.members.assign(cs.size(), stk_handle::CycleGraph{});
-    int rc = STK_OK;
-    for (size_t i = 0; i < cs.size() && rc == STK_OK; ++i) rc = build_chain(G, cs[i], out.members[i]);
     if (rc == STK_OK) rc = instantiate(h, G, &out.exec);
     cudaGraphDestroy(G);
     cudaGetLastError();
@@ -1110,10 +1106,11 @@ void absorb_cycle(Inst* it, const stk_solver_params& prm, const MGParams& mp) {
 // Stopping rule: ||b - M x|| <= rtol ||b||, checked at the start of every
 // cycle; inside a cycle the Arnoldi estimate must fall to rtol ||b||
 // (flexible) or to its start value times rtol ||b|| / ||b - M x|| (left).
-// With graphs each cycle of every active instance is one graph launch on its
-// stream and the host synchronises once per cycle for the whole batch;
-// without graphs (profiling) once per phase.
-void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm, bool batch_graph) {
+// With cycle_graphs (a single solve, graphs on, profiling off) each cycle is
+// one graph launch and the host synchronises once per cycle; otherwise the
+// host gates the phases of all instances together, one synchronisation per
+// phase for the whole batch, each preconditioner application one graph.
+void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm, bool cycle_graphs) {
     const int m = prm.restart;
     const bool flex = prm.precision == STK_MIXED;
     MGParams mp;
@@ -1143,35 +1140,9 @@ void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm, bool
             finish(it, STK_OK);
         }
     }
-    // one graph for the cycles of the whole batch (built on first use for
-    // this batch composition and configuration, kept by the first handle)
-    stk_handle::BatchGraph* bg = nullptr;
-    if (batch_graph) {
-        stk_handle* h0 = insts[0].h;
-        std::vector<long long> sig = {prm.precond, flex ? 1 : 0, m, mp.nu, mp.ncoarse, mp.cu * 1000 + mp.cp};
-        for (auto& it : insts) {
-            sig.push_back(it.h->uid);
-            sig.push_back(it.h->gen);
-        }
-        if (!h0->batch.exec || h0->batch.sig != sig) {
-            if (h0->batch.exec) {
-                cudaDeviceSynchronize();
-                cudaGraphExecDestroy(h0->batch.exec);
-            }
-            h0->batch = stk_handle::BatchGraph{};
-            std::vector<CycleCtx> cs;
-            for (auto& it : insts) cs.push_back(CycleCtx{it.h, prm.precond, m, flex, mp});
-            if (build_batch_graph(cs, h0->batch) == STK_OK) h0->batch.sig = sig;
-            else h0->batch = stk_handle::BatchGraph{};
-        }
-        if (h0->batch.exec) {
-            bg = &h0->batch;
-            for (size_t i = 0; i < insts.size(); ++i) insts[i].cg = &bg->members[i];
-        }
-    }
     // graphs of the cycle (built on first use per handle and configuration)
     for (Inst* it : act) {
-        if (it->done || bg) continue;
+        if (it->done || !cycle_graphs) continue;
         stk_handle* h = it->h;
         it->cg = nullptr;
         if (!h->use_graphs || h->prof) continue;
@@ -1193,17 +1164,9 @@ void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm, bool
         for (auto& it : insts)
             if (!it.done) act.push_back(&it);
         if (act.empty()) break;
+        Nvtx range("gmres cycle");
         std::vector<Inst*> eager;
-        if (bg) {   // the whole batch: one launch (finished instances stop at their gate)
-            cudaError_t e = cudaGraphLaunch(bg->exec, act[0]->s);
-            if (e != cudaSuccess) {
-                const int rc = fail(act[0]->h, STK_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e));
-                for (Inst* it : act) finish(it, rc);
-            }
-            for (Inst* it : act) read_header(it);
-        }
         for (Inst* it : act) {
-            if (bg) break;
             if (it->cg) {
                 cudaError_t e = cudaGraphLaunch(it->cg->exec, it->s);
                 if (e != cudaSuccess) { finish(it, fail(it->h, STK_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e))); continue; }
@@ -1236,7 +1199,8 @@ void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm, bool
                 if (step.empty()) break;
                 for (Inst* it : step) {
                     CycleCtx c{it->h, prm.precond, m, flex, mp};
-                    enq_step(c, j, it->s, 0, 0);
+                    int rc = enq_step(c, j, it->s, 0, 0);
+                    if (rc) { finish(it, rc); continue; }
                     read_header(it);
                 }
                 sync_all(step);
@@ -1376,8 +1340,6 @@ int stk_create(int dim, const int* n, double hh, const int* bc, stk_handle** out
     for (int a = 0; a < dim; ++a) total *= nn[a];
     if (total * (dim + 1) > (1LL << 30)) return fail(nullptr, STK_ERR_SIZE, "grid too large");
     h = new stk_handle();
-    static std::atomic<long long> next_uid{0};
-    h->uid = ++next_uid;
     cudaGetDevice(&h->device);
     h->dim = dim;
     int cur[3] = {nn[0], nn[1], nn[2]};
@@ -1534,6 +1496,7 @@ int stk_destroy(stk_handle* h) {
 int stk_set_coefficients(stk_handle* h, const double* rho, const double* mu, double dt,
                          void* stream) {
     if (!h) return STK_ERR_ARG;
+    Nvtx range("stk_set_coefficients");
     if (!rho || !mu) return fail(h, STK_ERR_ARG, "null rho or mu");
     if (!(dt > 0.0)) return fail(h, STK_ERR_ARG, "dt must be > 0 (+INFINITY for steady flow)");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1777,6 +1740,7 @@ int stk_solve(stk_handle* h, const stk_solver_params* params, const double* cons
 int stk_solve_batched(int count, stk_handle* const* hs, const stk_solver_params* params,
                       const stk_batch_io* io, stk_solve_info* infos, void* stream) {
     if (count < 1 || !hs || !io) return STK_ERR_ARG;
+    Nvtx range(count == 1 ? "stk_solve" : "stk_solve_batched");
     stk_solver_params prm;
     stk_default_params(&prm);
     if (params) prm = *params;
@@ -1808,11 +1772,11 @@ int stk_solve_batched(int count, stk_handle* const* hs, const stk_solver_params*
         CK(cudaEventCreate(&e1));
         CK(cudaEventRecord(e0, us));
     }
-    // several instances with graphs: one graph for the whole batch, launched
-    // on the caller's stream; otherwise each instance on its own stream
-    bool batch_graph = count > 1;
-    for (int i = 0; i < count; ++i) batch_graph = batch_graph && hs[i]->use_graphs && !hs[i]->prof;
-    const bool fork = count > 1 && !batch_graph;
+    // one solve: the caller's stream, each GMRES cycle one graph launch;
+    // several: each instance on its handle's own stream, the cycles' phases
+    // gated by the host for the whole batch at once (measured faster for the
+    // batched workload than one cycle graph per instance)
+    const bool fork = count > 1;
     for (int i = 0; i < count; ++i) {
         Inst& it = insts[i];
         it.h = hs[i];
@@ -1822,7 +1786,7 @@ int stk_solve_batched(int count, stk_handle* const* hs, const stk_solver_params*
         if (!rc) rc = gather(it.h, io[i].x_u, io[i].x_p, it.h->xk, it.s);
         if (rc) finish(&it, rc);
     }
-    gmres_lockstep(insts, prm, batch_graph);
+    gmres_lockstep(insts, prm, count == 1);
     int worst = STK_OK;
     for (int i = 0; i < count; ++i) {
         Inst& it = insts[i];
@@ -1926,6 +1890,7 @@ extern "C" {
 
 int stk_autotune(stk_handle* h, int precision, stk_schedule* best, void* stream) {
     if (!h) return STK_ERR_ARG;
+    Nvtx range("stk_autotune");
     if (!h->coef_set) return fail(h, STK_ERR_STATE, "coefficients not set");
     if (precision != STK_FP64 && precision != STK_MIXED) return fail(h, STK_ERR_ARG, "bad precision");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -2005,6 +1970,42 @@ int stk_gradient(stk_handle* h, const double* const* u, const double* const* lam
     }
     CKL();
     return STK_OK;
+}
+
+long long stk_bounds_violations(long long* first_kind, long long* first_index, int reset) {
+#ifdef STK_BOUNDS_CHECK
+    if (cudaDeviceSynchronize() != cudaSuccess) return -1;
+    long long (*readers[])(long long*, int) = {oob_kernels, oob_pair, oob_stress, oob_coarse};
+    long long total = 0;
+    bool have = false;
+    for (auto rd : readers) {
+        long long first[2] = {0, 0};
+        const long long c = rd(first, reset);
+        if (c < 0) return -1;
+        if (c > 0 && !have) {
+            have = true;
+            if (first_kind) *first_kind = first[0];
+            if (first_index) *first_index = first[1];
+        }
+        total += c;
+    }
+    return total;
+#else
+    (void)first_kind;
+    (void)first_index;
+    (void)reset;
+    return -1;
+#endif
+}
+
+int stk_bounds_selftest(void* stream) {
+#ifdef STK_BOUNDS_CHECK
+    launch_oob_selftest(7, static_cast<cudaStream_t>(stream));
+    return cudaGetLastError() == cudaSuccess ? STK_OK : STK_ERR_CUDA;
+#else
+    (void)stream;
+    return STK_ERR_STATE;
+#endif
 }
 
 int stk_solve_history(const stk_handle* h, int kind, double* out, int cap) {

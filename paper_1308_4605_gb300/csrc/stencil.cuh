@@ -27,13 +27,13 @@ __host__ __device__ __forceinline__ int wrapm(int i, int n) {
     return i < 0 ? i + n : (i >= n ? i - n : i);
 }
 __device__ __forceinline__ int fidx(const Geom& g, int a, const int q[3]) {
-    return g.foff[a] + (q[2] * g.fe[a][1] + q[1]) * g.fe[a][0] + q[0];
+    return STK_IDX(g.foff[a] + (q[2] * g.fe[a][1] + q[1]) * g.fe[a][0] + q[0], g.nvel, 1);
 }
 __device__ __forceinline__ int cidx(const Geom& g, const int q[3]) {
-    return (q[2] * g.n[1] + q[1]) * g.n[0] + q[0];
+    return STK_IDX((q[2] * g.n[1] + q[1]) * g.n[0] + q[0], g.ncell, 2);
 }
 __device__ __forceinline__ int eidx(const Geom& g, int p, const int q[3]) {
-    return (q[2] * g.ee[p][1] + q[1]) * g.ee[p][0] + q[0];
+    return STK_IDX((q[2] * g.ee[p][1] + q[1]) * g.ee[p][0] + q[0], g.esize[p], 3);
 }
 // t -> (i, j, k) over the face array of component a
 __device__ __forceinline__ void decode_face(const Geom& g, int a, int t, int q[3]) {
@@ -156,7 +156,23 @@ __device__ __forceinline__ void nbr_lin(const Geom& g, const int q[3], Nbr& X) {
         X.a_bm[j] = f - km[B] * sA[B];
         X.wlo[j] = !g.per[B] && q[B] == 0;
         X.whi[j] = !g.per[B] && q[B] == g.n[B] - 1;
+#ifdef STK_BOUNDS_CHECK
+        X.e_lo[j] = STK_IDX(X.e_lo[j], g.esize[P], 3);
+        X.e_hi[j] = STK_IDX(X.e_hi[j], g.esize[P], 3);
+        X.b_q[j] = STK_IDX(X.b_q[j], g.nvel, 1);
+        X.b_r0[j] = STK_IDX(X.b_r0[j], g.nvel, 1);
+        X.b_qe[j] = STK_IDX(X.b_qe[j], g.nvel, 1);
+        X.b_r2[j] = STK_IDX(X.b_r2[j], g.nvel, 1);
+        if (!X.whi[j]) X.a_bp[j] = STK_IDX(X.a_bp[j], g.nvel, 1);
+        if (!X.wlo[j]) X.a_bm[j] = STK_IDX(X.a_bm[j], g.nvel, 1);
+#endif
     }
+#ifdef STK_BOUNDS_CHECK
+    X.a_p = STK_IDX(X.a_p, g.nvel, 1);
+    X.a_m = STK_IDX(X.a_m, g.nvel, 1);
+    X.c_h = STK_IDX(X.c_h, g.ncell, 2);
+    X.c_l = STK_IDX(X.c_l, g.ncell, 2);
+#endif
 }
 
 // Index table from coordinates; aidx(r) gives the index of phi_A at the
@@ -348,9 +364,9 @@ __device__ __forceinline__ T poisson_offdiag_h2(const Geom& g, const Coef<T>& C,
         const bool top = q[a] == na - 1, bot = q[a] == 0;
         const int sf = a == 0 ? 1 : (a == 1 ? g.fe[a][0] : g.fe[a][0] * g.fe[a][1]);
         const int fl = fidx(g, a, q);
-        const int fh = fl + ((g.per[a] && top) ? 1 - na : 1) * sf;
-        const int ch = c + (top ? (g.per[a] ? 1 - na : 0) : 1) * sc;
-        const int cl = c - (bot ? (g.per[a] ? 1 - na : 0) : 1) * sc;
+        const int fh = STK_IDX(fl + ((g.per[a] && top) ? 1 - na : 1) * sf, g.nvel, 1);
+        const int ch = STK_IDX(c + (top ? (g.per[a] ? 1 - na : 0) : 1) * sc, g.ncell, 2);
+        const int cl = STK_IDX(c - (bot ? (g.per[a] ? 1 - na : 0) : 1) * sc, g.ncell, 2);
         const T bh = ld(C.beta + fh);
         const T bl = ld(C.beta + fl);
         N = fma(bh, T(phi[ch]), N);

@@ -224,4 +224,6 @@ void launch_vel_residual_stress(const Geom& g, Coef<double> C, const StressWork&
     face_pass<1>(g, C, W, phi, rhs, res, after_sweep ? g.dim - 1 : -1, s);
 }
 
+STK_OOB_READER(stress)
+
 }  // namespace stk

@@ -18,7 +18,9 @@ import math
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libstokes_gb300.so")
+# STK_LIBRARY selects another build of the library (e.g. the bounds-checked
+# libstokes_gb300_check.so); the default is the release build beside this file
+LIB_PATH = os.environ.get("STK_LIBRARY") or os.path.join(HERE, "libstokes_gb300.so")
 
 STK_PERIODIC, STK_NOSLIP, STK_FREESLIP = 0, 1, 2
 STK_OK = 0
@@ -100,6 +102,9 @@ def _load():
         "stk_solve_batched": (I, [I, ctypes.POINTER(P), ctypes.POINTER(stk_solver_params),
                                   ctypes.POINTER(stk_batch_io), ctypes.POINTER(stk_solve_info), P]),
         "stk_remove_mean": (I, [P, P, P, P]),
+        "stk_bounds_violations": (ctypes.c_longlong, [ctypes.POINTER(ctypes.c_longlong),
+                                                      ctypes.POINTER(ctypes.c_longlong), I]),
+        "stk_bounds_selftest": (I, [P]),
         "stk_solve_history": (I, [P, I, ctypes.POINTER(D), I]),
         "stk_pressure_vcycle_noalloc": (I, [I, ctypes.POINTER(I), D, ctypes.POINTER(I), P, P, P, P]),
         "stk_profile_read": (I, [P, I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong),
@@ -116,7 +121,7 @@ _lib = _load()
 EXPORTED = ["stk_default_params", "stk_create", "stk_destroy", "stk_last_error", "stk_face_length",
             "stk_cell_length", "stk_set_coefficients", "stk_set_bulk_viscosity", "stk_apply_operator",
             "stk_apply_preconditioner", "stk_apply_preconditioner_params", "stk_velocity_vcycle", "stk_pressure_vcycle", "stk_solve",
-            "stk_profile", "stk_profile_read", "stk_kernel_launches", "stk_pressure_vcycle_noalloc", "stk_remove_mean", "stk_solve_history", "stk_gradient", "stk_backward_euler_rhs", "stk_subtract_boundary_terms", "stk_solve_batched", "stk_get_schedule", "stk_set_schedule", "stk_autotune"]
+            "stk_profile", "stk_profile_read", "stk_kernel_launches", "stk_pressure_vcycle_noalloc", "stk_remove_mean", "stk_solve_history", "stk_bounds_violations", "stk_bounds_selftest", "stk_gradient", "stk_backward_euler_rhs", "stk_subtract_boundary_terms", "stk_solve_batched", "stk_get_schedule", "stk_set_schedule", "stk_autotune"]
 
 
 def library():
@@ -354,6 +359,18 @@ def stk_solve_history(h, kind):
     buf = (ctypes.c_double * max(n, 1))()
     got = int(_lib.stk_solve_history(h, int(kind), buf, n))
     return [buf[i] for i in range(min(n, got))]
+
+
+def stk_bounds_violations(reset=False):
+    """(count, first kind, first index) of out-of-range indices met by a
+    bounds-checked build; count -1 for a release build."""
+    k, i = ctypes.c_longlong(0), ctypes.c_longlong(0)
+    n = int(_lib.stk_bounds_violations(ctypes.byref(k), ctypes.byref(i), int(bool(reset))))
+    return n, k.value, i.value
+
+
+def stk_bounds_selftest(stream=None):
+    return _check(None, _lib.stk_bounds_selftest(_stream(stream)))
 
 
 def stk_kernel_launches(h):
