@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--quick", action="store_true",
                     help="profiling runs: only the timed solves of --form, no baseline/e2e/profile passes")
     ap.add_argument("--form", default="both", choices=["both", "fp64", "mixed"])
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="quick mode: launch every kernel from the host (for profilers)")
+    ap.add_argument("--schedule", default="",
+                    help="quick mode: coarse_level,threads,pair_level instead of the tuned schedule")
     ap.add_argument("--big", action="store_true",
                     help="study: add the 512^3 steady bubble to the size series (about 140 GB)")
     return ap.parse_args()
@@ -369,11 +373,17 @@ def run_ours(args):
         from paper_1308_4605_gb300 import tuning
         solver.set_coefficients(rho, mu, pr.theta)
         tuning.tune(solver, form)   # cached: a repeated command launches no tuning kernels
+        if args.schedule:
+            S.stk_set_schedule(solver.handle, form, *[int(v) for v in args.schedule.split(",")])
+        if args.no_graphs:
+            S.stk_set_graphs(solver.handle, 0)
         for _ in range(args.warmup):
             step(form)
         times, infos = timed(form, args.steps)
         if rank == 0:
-            print(json.dumps({"quick": True, "form": args.form, "ms": times, "iterations": infos[0]["iterations"],
+            print(json.dumps({"quick": True, "form": args.form, "graphs": not args.no_graphs,
+                              "schedule": S.stk_get_schedule(solver.handle, form),
+                              "ms": times, "iterations": infos[0]["iterations"],
                               "true_residual": infos[0]["true_residual"], "config": cfg}))
         solver.close()
         return 0

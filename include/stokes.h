@@ -229,6 +229,14 @@ int stk_backward_euler_rhs(stk_handle* h, const double* const* u_n, const double
 int stk_gradient(stk_handle* h, const double* const* u, const double* const* lambda,
                  double* dL_dlogmu, double* dL_drho, void* stream);
 
+/* CUDA graphs on (enable = 1, the default) or off (0) for h.  With graphs on,
+ * every preconditioner application outside a solve is one graph launch and a
+ * single stk_solve runs each GMRES cycle as one graph whose phases are gated
+ * on the device; with graphs off every kernel is launched from the host and
+ * the host gates the phases (for tools that do not follow kernels inside
+ * graphs, and for debugging).  The results are bitwise the same. */
+int stk_set_graphs(stk_handle* h, int enable);
+
 /* Residual history of the last stk_solve / stk_solve_batched on h (Sec. 3.2
  * distinguishes the true residual r = b - M x from the preconditioned one):
  * kind 0: the true relative residual ||b - M x|| / ||b|| at the start of every

@@ -2008,6 +2008,13 @@ int stk_bounds_selftest(void* stream) {
 #endif
 }
 
+int stk_set_graphs(stk_handle* h, int enable) {
+    if (!h) return STK_ERR_ARG;
+    clear_graphs(h);
+    h->use_graphs = enable != 0;
+    return STK_OK;
+}
+
 int stk_solve_history(const stk_handle* h, int kind, double* out, int cap) {
     if (!h || (kind != 0 && kind != 1) || cap < 0) return STK_ERR_ARG;
     const std::vector<double>& v = kind == 0 ? h->hist_true : h->hist_est;

@@ -102,6 +102,7 @@ def _load():
         "stk_solve_batched": (I, [I, ctypes.POINTER(P), ctypes.POINTER(stk_solver_params),
                                   ctypes.POINTER(stk_batch_io), ctypes.POINTER(stk_solve_info), P]),
         "stk_remove_mean": (I, [P, P, P, P]),
+        "stk_set_graphs": (I, [P, I]),
         "stk_bounds_violations": (ctypes.c_longlong, [ctypes.POINTER(ctypes.c_longlong),
                                                       ctypes.POINTER(ctypes.c_longlong), I]),
         "stk_bounds_selftest": (I, [P]),
@@ -121,7 +122,7 @@ _lib = _load()
 EXPORTED = ["stk_default_params", "stk_create", "stk_destroy", "stk_last_error", "stk_face_length",
             "stk_cell_length", "stk_set_coefficients", "stk_set_bulk_viscosity", "stk_apply_operator",
             "stk_apply_preconditioner", "stk_apply_preconditioner_params", "stk_velocity_vcycle", "stk_pressure_vcycle", "stk_solve",
-            "stk_profile", "stk_profile_read", "stk_kernel_launches", "stk_pressure_vcycle_noalloc", "stk_remove_mean", "stk_solve_history", "stk_bounds_violations", "stk_bounds_selftest", "stk_gradient", "stk_backward_euler_rhs", "stk_subtract_boundary_terms", "stk_solve_batched", "stk_get_schedule", "stk_set_schedule", "stk_autotune"]
+            "stk_profile", "stk_profile_read", "stk_kernel_launches", "stk_pressure_vcycle_noalloc", "stk_remove_mean", "stk_set_graphs", "stk_solve_history", "stk_bounds_violations", "stk_bounds_selftest", "stk_gradient", "stk_backward_euler_rhs", "stk_subtract_boundary_terms", "stk_solve_batched", "stk_get_schedule", "stk_set_schedule", "stk_autotune"]
 
 
 def library():
@@ -371,6 +372,10 @@ def stk_bounds_violations(reset=False):
 
 def stk_bounds_selftest(stream=None):
     return _check(None, _lib.stk_bounds_selftest(_stream(stream)))
+
+
+def stk_set_graphs(h, enable):
+    return _check(h, _lib.stk_set_graphs(h, int(bool(enable))))
 
 
 def stk_kernel_launches(h):

@@ -35,8 +35,9 @@ def test_bounds_checked_build_meets_no_out_of_range_index():
     assert out["selftest"] == [1, 2, 7]            # counted: kind 2 (cell), index 7
     assert out["violations"][0] == 0, out["violations"]
     for rec in out["cases"]:
-        for key, (its, res) in rec.items():
+        for key, val in rec.items():
             if key.startswith("p"):
+                its, res = val
                 assert res <= 1e-10, (rec["n"], rec["bc"], key, its, res)
 
 

@@ -43,12 +43,15 @@ def test_graph_gated_cycles_equal_host_gated(S, k, precision):
     sv.set_coefficients(_t(pr.rho), _t(pr.mu), pr.theta)
     bu, bp = [_t(x) for x in pr.b_u], _t(pr.b_p)
     out = []
-    for prof in (0, 1, 0):
+    # graph-gated, host-gated (profiling), graph-gated again, graphs off
+    for prof, graphs in ((0, 1), (1, 1), (0, 1), (0, 0)):
         S.stk_profile(sv.handle, prof)
+        S.stk_set_graphs(sv.handle, graphs)
         xu, xp, info = sv.solve(bu, bp, precond=pr.precond, precision=precision, restart=7)
         assert info["converged"], info
         out.append(([a.cpu().numpy() for a in xu], xp.cpu().numpy(), info))
     S.stk_profile(sv.handle, 0)
+    S.stk_set_graphs(sv.handle, 1)
     sv.close()
     for xu, xp, info in out[1:]:
         assert info["iterations"] == out[0][2]["iterations"]
