@@ -229,6 +229,17 @@ int stk_backward_euler_rhs(stk_handle* h, const double* const* u_n, const double
 int stk_gradient(stk_handle* h, const double* const* u, const double* const* lambda,
                  double* dL_dlogmu, double* dL_drho, void* stream);
 
+/* Bound of every device-side wait of h's kernels (the grid barriers of the
+ * persistent multi-block V-cycle), in clock64() cycles of the SM clock
+ * (default 2e9, about one second).  A wait that runs out writes
+ * STK_ERR_TIMEOUT to h's device status word and the launch ends at its next
+ * barriers without faulting or hanging; stk_solve then returns
+ * STK_ERR_TIMEOUT (its result is not a solution).  stk_wait_status returns
+ * STK_OK or STK_ERR_TIMEOUT for the work issued so far (synchronises the
+ * device; reset != 0 clears the word; stk_solve clears it when it starts). */
+int stk_set_wait_budget(stk_handle* h, long long cycles);
+int stk_wait_status(stk_handle* h, int reset);
+
 /* CUDA graphs on (enable = 1, the default) or off (0) for h.  With graphs on,
  * every preconditioner application outside a solve is one graph launch and a
  * single stk_solve runs each GMRES cycle as one graph whose phases are gated
@@ -236,6 +247,9 @@ int stk_gradient(stk_handle* h, const double* const* u, const double* const* lam
  * the host gates the phases (for tools that do not follow kernels inside
  * graphs, and for debugging).  The results are bitwise the same. */
 int stk_set_graphs(stk_handle* h, int enable);
+/* 1 while h uses graphs, 0 once they are off (stk_set_graphs, or a graph the
+ * library could not build, after which it launches from the host). */
+int stk_graphs_in_use(const stk_handle* h);
 
 /* Residual history of the last stk_solve / stk_solve_batched on h (Sec. 3.2
  * distinguishes the true residual r = b - M x from the preconditioned one):
@@ -283,7 +297,13 @@ int stk_solve_batched(int count, stk_handle* const* hs, const stk_solver_params*
  * per sweep and component doing both colours (each block recomputes the
  * red points of a one-point halo around its tile); finer levels launch once
  * per colour with `threads` threads per block (64, 128, 256 or 512).
- * 0 <= pair_level, coarse_level <= number of levels.  The arithmetic does
+ * Levels grid_level and coarser, down to coarse_level, run as one persistent
+ * multi-block launch (cooperative, all blocks resident, grid-wide barriers
+ * between the stages instead of kernel boundaries; the levels from
+ * coarse_level on are then done by one of its blocks); grid_level >=
+ * coarse_level switches it off.  Each barrier wait is bounded (see
+ * stk_set_wait_budget).
+ * 0 <= pair_level, coarse_level, grid_level <= number of levels.  The arithmetic does
  * not depend on the schedule, except that with coarse_level = 0 the finest
  * level's FP64 residual is evaluated point by point instead of through the
  * stresses of the grid kernels (equal up to rounding).  stk_autotune times one velocity + one
@@ -294,6 +314,7 @@ typedef struct {
     int coarse_level;
     int threads;
     int pair_level;
+    int grid_level;
 } stk_schedule;
 int stk_get_schedule(const stk_handle* h, int precision, stk_schedule* out);
 int stk_set_schedule(stk_handle* h, int precision, const stk_schedule* sc);

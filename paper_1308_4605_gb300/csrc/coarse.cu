@@ -17,6 +17,7 @@
 // from, and its solution written to, global memory; coefficients stay in
 // global memory (read-only, cached).
 #include "stencil.cuh"
+#include "../../include/stokes.h"
 
 namespace stk {
 namespace {
@@ -32,48 +33,107 @@ struct SmemLevels {
     int n[CMAXL];
 };
 
-template <typename T, bool SMEM>
-struct LevelVecs {
-    T *phi, *rhs, *res;
+// Barrier policies.  BlockSync: one block of CT threads, __syncthreads()
+// between stages (the single-block kernel).  GridSync: every block of a
+// cooperative launch, a grid-wide barrier between stages (the persistent
+// multi-block kernel); each wait is bounded by a clock64() budget, after
+// which the barrier writes STK_ERR_TIMEOUT to *status and every block
+// returns at its next barrier, so a stalled launch ends instead of hanging.
+struct BlockSync {
+    __device__ __forceinline__ int tid() const { return threadIdx.x; }
+    __device__ __forceinline__ int nth() const { return CT; }
+    __device__ __forceinline__ bool sync() const {
+        __syncthreads();
+        return true;
+    }
 };
 
-template <int DIM, typename T, bool BULK>
-__device__ void c_vel_sweeps(const Geom& g, const Coef<T>& C, int nsweep, T* phi, const T* rhs) {
+struct GridSync {
+    unsigned* bar;        // [0] arrivals, [1] generation (zeroed before the launch)
+    long long budget;     // clock64() cycles one wait may last
+    int* status;          // 0, or STK_ERR_TIMEOUT once a wait ran out
+    __device__ __forceinline__ int tid() const { return blockIdx.x * CT + threadIdx.x; }
+    __device__ __forceinline__ int nth() const { return gridDim.x * CT; }
+    // Sense-counting grid barrier: the block's writes are ordered before its
+    // arrival (bar.sync, then a device-scope fence by thread 0), the last
+    // block to arrive resets the count and advances the generation, the
+    // others wait for the generation to change; the fence after the wait
+    // orders the reads that follow.  false: a wait ran out (here or in
+    // another block); the caller returns.
+    __device__ bool sync() const {
+        __shared__ int ok;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            volatile unsigned* gen = bar + 1;
+            volatile int* st = status;
+            const unsigned g0 = *gen;
+            __threadfence();
+            int res = 1;
+            if (atomicAdd(bar, 1u) + 1u == gridDim.x) {
+                bar[0] = 0u;
+                __threadfence();
+                atomicAdd(bar + 1, 1u);
+            } else {
+                const long long t0 = clock64();
+                while (*gen == g0) {
+                    if (*st != 0 || clock64() - t0 > budget) {
+                        atomicCAS(status, 0, STK_ERR_TIMEOUT);
+                        res = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __threadfence();
+            if (*st != 0) res = 0;
+            ok = res;
+        }
+        __syncthreads();
+        return ok != 0;
+    }
+};
+
+template <int DIM, typename T, bool BULK, typename SY>
+__device__ bool c_vel_sweeps(const SY& S, const Geom& g, const Coef<T>& C, int nsweep, T* phi,
+                             const T* rhs) {
     for (int it = 0; it < nsweep; ++it)
 #pragma unroll
         for (int a = 0; a < DIM; ++a)
             for (int par = 0; par < 2; ++par) {
                 const int nt = ((g.fe[a][0] + 1) >> 1) * g.fe[a][1] * g.fe[a][2];
-                for (int t = threadIdx.x; t < nt; t += CT) {
+                for (int t = S.tid(); t < nt; t += S.nth()) {
                     int q[3];
                     if (!decode_face_colour(g, a, par, t, q) || wall_face(g, a, q)) continue;
                     if (a == 0) vel_gs_point<DIM, 0, T, BULK>(g, C, q, phi, rhs);
                     else if (a == 1) vel_gs_point<DIM, 1, T, BULK>(g, C, q, phi, rhs);
                     else vel_gs_point<DIM, DIM == 3 ? 2 : 1, T, BULK>(g, C, q, phi, rhs);
                 }
-                __syncthreads();
+                if (!S.sync()) return false;
             }
+    return true;
 }
 
-template <int DIM, typename T>
-__device__ void c_cell_sweeps(const Geom& g, const Coef<T>& C, int nsweep, T* phi, const T* rhs) {
+template <int DIM, typename T, typename SY>
+__device__ bool c_cell_sweeps(const SY& S, const Geom& g, const Coef<T>& C, int nsweep, T* phi,
+                              const T* rhs) {
     const int nt = (g.n[0] >> 1) * g.n[1] * g.n[2];
     for (int it = 0; it < nsweep; ++it)
         for (int par = 0; par < 2; ++par) {
-            for (int t = threadIdx.x; t < nt; t += CT) {
+            for (int t = S.tid(); t < nt; t += S.nth()) {
                 int q[3];
                 decode_cell_colour(g, par, t, q);
                 cell_gs_point<DIM, T>(g, C, q, phi, rhs);
             }
-            __syncthreads();
+            if (!S.sync()) return false;
         }
+    return true;
 }
 
 // phi = S rhs with S stored column-major (st[i * n + j] = S_ji): each thread
 // forms whole rows, summing over i in increasing order
-template <typename T>
-__device__ void smat_apply(const T* __restrict__ st, int n, const T* rhs, T* phi) {
-    for (int j = threadIdx.x; j < n; j += CT) {
+template <typename T, typename SY>
+__device__ void smat_apply(const SY& S, const T* __restrict__ st, int n, const T* rhs, T* phi) {
+    for (int j = S.tid(); j < n; j += S.nth()) {
         T acc = T(0);
         for (int i = 0; i < n; ++i) acc = fma(st[(size_t)i * n + j], rhs[i], acc);
         phi[j] = acc;
@@ -87,6 +147,189 @@ __device__ __forceinline__ void load_geom(Geom* dst, const Geom* src) {
     for (int i = threadIdx.x; i < (int)(sizeof(Geom) / sizeof(int)); i += CT) d[i] = s[i];
 }
 
+// Work vectors of level l: shared memory (SMEM) or the level's own arrays,
+// level 0's right-hand side and solution being the caller's.
+template <typename T, bool SMEM, bool VEL>
+struct Vecs {
+    const CLevel<T>* Ls;
+    T* sm;
+    const SmemLevels* sl;
+    const T* rhs0;
+    T* phi0;
+    __device__ T* phi(int l) const {
+        return SMEM ? sm + sl->off[l] : (l == 0 ? phi0 : (VEL ? Ls[l].phi_u : Ls[l].phi_p));
+    }
+    __device__ T* rhs(int l) const {
+        return SMEM ? sm + sl->off[l] + sl->n[l]
+                    : (l == 0 ? const_cast<T*>(rhs0) : (VEL ? Ls[l].rhs_u : Ls[l].rhs_p));
+    }
+    __device__ T* res(int l) const {
+        return SMEM ? sm + sl->off[l] + 2 * sl->n[l] : (VEL ? Ls[l].res_u : Ls[l].res_p);
+    }
+};
+
+// One velocity V-cycle (zero guess) over levels 0..nlev-1 of Ls.  Levels
+// below lblock run with the barrier policy S; from level lblock on (lblock
+// < nlev), block 0 alone runs the rest as a single-block V-cycle while the
+// other blocks wait at the next barrier.  false: a barrier ran out.
+template <int DIM, typename T, bool BULK, bool SMEM, typename SY>
+__device__ bool vcycle_vel_body(const SY& S, Geom* gsh, const CLevel<T>* __restrict__ Ls, int nlev,
+                                int lblock, const Vecs<T, SMEM, true> V, int nu, int ncoarse) {
+    const int ltop = lblock < nlev ? lblock : nlev;
+    // down: pre-smoothing, residual, restriction
+    for (int l = 0; l < ltop; ++l) {
+        load_geom(&gsh[0], &Ls[l].g);
+        if (l + 1 < nlev) load_geom(&gsh[1], &Ls[l + 1].g);
+        __syncthreads();
+        const Geom& g = gsh[0];
+        const Coef<T> C = Ls[l].C;
+        T* phi = V.phi(l);
+        const T* rhs = V.rhs(l);
+        for (int t = S.tid(); t < g.nvel; t += S.nth()) phi[t] = T(0);
+        if (!S.sync()) return false;
+        if (l + 1 == nlev) {   // coarsest level: the coarse solve, then up
+            if (Ls[l].smat_u && Ls[l].smat_nc == ncoarse) smat_apply<T>(S, Ls[l].smat_u, g.nvel, rhs, phi);
+            else if (!c_vel_sweeps<DIM, T, BULK>(S, g, C, ncoarse, phi, rhs)) return false;
+            if (!S.sync()) return false;
+            break;
+        }
+        if (!c_vel_sweeps<DIM, T, BULK>(S, g, C, nu, phi, rhs)) return false;
+        T* res = V.res(l);
+        for (int t = S.tid(); t < g.nvel; t += S.nth()) {
+            int a = 0;
+            while (a + 1 < DIM && t >= g.foff[a + 1]) ++a;
+            int q[3];
+            decode_face(g, a, t - g.foff[a], q);
+            // the black faces of the last component were just solved: zero residual
+            const bool solved = nu > 0 && a == DIM - 1 && ((q[0] + q[1] + q[2]) & 1);
+            res[t] = (wall_face(g, a, q) || solved) ? T(0) : vel_res_point<DIM, T, BULK>(a, g, C, q, phi, rhs);
+        }
+        if (!S.sync()) return false;
+        const Geom& gc = gsh[1];
+        T* rc = V.rhs(l + 1);
+        for (int t = S.tid(); t < gc.nvel; t += S.nth()) {
+            int a = 0;
+            while (a + 1 < DIM && t >= gc.foff[a + 1]) ++a;
+            int Q[3];
+            decode_face(gc, a, t - gc.foff[a], Q);
+            T v = T(0);
+            if (!wall_face(gc, a, Q)) {
+                if (a == 0) v = vel_restrict_point<DIM, 0, T>(g, Q, res);
+                else if (a == 1) v = vel_restrict_point<DIM, 1, T>(g, Q, res);
+                else v = vel_restrict_point<DIM, DIM == 3 ? 2 : 1, T>(g, Q, res);
+            }
+            rc[t] = v;
+        }
+        if (!S.sync()) return false;
+    }
+    if (ltop < nlev) {   // the coarse levels, one block
+        if (blockIdx.x == 0) {
+            const Vecs<T, false, true> Vb{Ls + ltop, nullptr, nullptr, V.rhs(ltop), V.phi(ltop)};
+            vcycle_vel_body<DIM, T, BULK, false>(BlockSync{}, gsh, Ls + ltop, nlev - ltop, nlev - ltop, Vb,
+                                                 nu, ncoarse);
+        }
+        if (!S.sync()) return false;
+    }
+    // up: prolongation and correction, post-smoothing
+    for (int l = ltop - 1; l >= 0; --l) {
+        if (l + 1 >= nlev) continue;
+        load_geom(&gsh[0], &Ls[l].g);
+        load_geom(&gsh[1], &Ls[l + 1].g);
+        __syncthreads();
+        const Geom& g = gsh[0];
+        const Geom& gc = gsh[1];
+        const Coef<T> C = Ls[l].C;
+        T* phi = V.phi(l);
+        const T* rhs = V.rhs(l);
+        const T* pc = V.phi(l + 1);
+        for (int t = S.tid(); t < g.nvel; t += S.nth()) {
+            int a = 0;
+            while (a + 1 < DIM && t >= g.foff[a + 1]) ++a;
+            int q[3];
+            decode_face(g, a, t - g.foff[a], q);
+            if (wall_face(g, a, q)) continue;
+            T v;
+            if (a == 0) v = vel_prolong_point<DIM, 0, T>(gc, q, pc);
+            else if (a == 1) v = vel_prolong_point<DIM, 1, T>(gc, q, pc);
+            else v = vel_prolong_point<DIM, DIM == 3 ? 2 : 1, T>(gc, q, pc);
+            phi[t] += v;
+        }
+        if (!S.sync()) return false;
+        if (!c_vel_sweeps<DIM, T, BULK>(S, g, C, nu, phi, rhs)) return false;
+    }
+    return true;
+}
+
+template <int DIM, typename T, bool SMEM, typename SY>
+__device__ bool vcycle_cell_body(const SY& S, Geom* gsh, const CLevel<T>* __restrict__ Ls, int nlev,
+                                 int lblock, const Vecs<T, SMEM, false> V, int nu, int ncoarse) {
+    const int ltop = lblock < nlev ? lblock : nlev;
+    for (int l = 0; l < ltop; ++l) {
+        load_geom(&gsh[0], &Ls[l].g);
+        if (l + 1 < nlev) load_geom(&gsh[1], &Ls[l + 1].g);
+        __syncthreads();
+        const Geom& g = gsh[0];
+        const Coef<T> C = Ls[l].C;
+        T* phi = V.phi(l);
+        const T* rhs = V.rhs(l);
+        for (int t = S.tid(); t < g.ncell; t += S.nth()) phi[t] = T(0);
+        if (!S.sync()) return false;
+        if (l + 1 == nlev) {
+            if (Ls[l].smat_p && Ls[l].smat_nc == ncoarse) smat_apply<T>(S, Ls[l].smat_p, g.ncell, rhs, phi);
+            else if (!c_cell_sweeps<DIM, T>(S, g, C, ncoarse, phi, rhs)) return false;
+            if (!S.sync()) return false;
+            break;
+        }
+        if (!c_cell_sweeps<DIM, T>(S, g, C, nu, phi, rhs)) return false;
+        T* res = V.res(l);
+        for (int t = S.tid(); t < g.ncell; t += S.nth()) {
+            int q[3];
+            decode_cell(g, t, q);
+            res[t] = (nu > 0 && ((q[0] + q[1] + q[2]) & 1)) ? T(0) : cell_res_point<DIM, T>(g, C, q, phi, rhs);
+        }
+        if (!S.sync()) return false;
+        const Geom& gc = gsh[1];
+        T* rc = V.rhs(l + 1);
+        for (int t = S.tid(); t < gc.ncell; t += S.nth()) {
+            int Q[3];
+            decode_cell(gc, t, Q);
+            rc[t] = cell_restrict_point<DIM, T>(g, Q, res);
+        }
+        if (!S.sync()) return false;
+    }
+    if (ltop < nlev) {
+        if (blockIdx.x == 0) {
+            const Vecs<T, false, false> Vb{Ls + ltop, nullptr, nullptr, V.rhs(ltop), V.phi(ltop)};
+            vcycle_cell_body<DIM, T, false>(BlockSync{}, gsh, Ls + ltop, nlev - ltop, nlev - ltop, Vb, nu,
+                                            ncoarse);
+        }
+        if (!S.sync()) return false;
+    }
+    for (int l = ltop - 1; l >= 0; --l) {
+        if (l + 1 >= nlev) continue;
+        load_geom(&gsh[0], &Ls[l].g);
+        load_geom(&gsh[1], &Ls[l + 1].g);
+        __syncthreads();
+        const Geom& g = gsh[0];
+        const Geom& gc = gsh[1];
+        const Coef<T> C = Ls[l].C;
+        T* phi = V.phi(l);
+        const T* rhs = V.rhs(l);
+        const T* pc = V.phi(l + 1);
+        for (int t = S.tid(); t < g.ncell; t += S.nth()) {
+            int q[3];
+            decode_cell(g, t, q);
+            int Q[3] = {q[0] >> 1, q[1] >> 1, DIM == 3 ? q[2] >> 1 : 0};
+            phi[t] += pc[cidx(gc, Q)];
+        }
+        if (!S.sync()) return false;
+        if (!c_cell_sweeps<DIM, T>(S, g, C, nu, phi, rhs)) return false;
+    }
+    return true;
+}
+
+// single block: every level from Ls[0] down, work vectors in shared memory
+// when they fit (SMEM), else in global memory
 template <int DIM, typename T, bool BULK, bool SMEM>
 __global__ void __launch_bounds__(CT) k_coarse_vel(const CLevel<T>* __restrict__ Ls, int nlev,
                                                    const T* rhs0, T* phi0, int nu, int ncoarse) {
@@ -107,82 +350,8 @@ __global__ void __launch_bounds__(CT) k_coarse_vel(const CLevel<T>* __restrict__
         __syncthreads();
         for (int t = threadIdx.x; t < sl.n[0]; t += CT) sm[sl.n[0] + t] = rhs0[t];
     }
-    auto PHI = [&](int l) -> T* { return SMEM ? sm + sl.off[l] : (l == 0 ? phi0 : Ls[l].phi_u); };
-    auto RHS = [&](int l) -> T* {
-        return SMEM ? sm + sl.off[l] + sl.n[l] : (l == 0 ? const_cast<T*>(rhs0) : Ls[l].rhs_u);
-    };
-    auto RES = [&](int l) -> T* { return SMEM ? sm + sl.off[l] + 2 * sl.n[l] : Ls[l].res_u; };
-    // down: pre-smoothing, residual, restriction
-    for (int l = 0; l < nlev; ++l) {
-        load_geom(&gsh[0], &Ls[l].g);
-        if (l + 1 < nlev) load_geom(&gsh[1], &Ls[l + 1].g);
-        __syncthreads();
-        const Geom& g = gsh[0];
-        const Coef<T> C = Ls[l].C;
-        T* phi = PHI(l);
-        const T* rhs = RHS(l);
-        for (int t = threadIdx.x; t < g.nvel; t += CT) phi[t] = T(0);
-        __syncthreads();
-        if (l + 1 == nlev) {
-            if (Ls[l].smat_u && Ls[l].smat_nc == ncoarse) smat_apply<T>(Ls[l].smat_u, g.nvel, rhs, phi);
-            else c_vel_sweeps<DIM, T, BULK>(g, C, ncoarse, phi, rhs);
-            break;
-        }
-        c_vel_sweeps<DIM, T, BULK>(g, C, nu, phi, rhs);
-        T* res = RES(l);
-        for (int t = threadIdx.x; t < g.nvel; t += CT) {
-            int a = 0;
-            while (a + 1 < DIM && t >= g.foff[a + 1]) ++a;
-            int q[3];
-            decode_face(g, a, t - g.foff[a], q);
-            // the black faces of the last component were just solved: zero residual
-            const bool solved = nu > 0 && a == DIM - 1 && ((q[0] + q[1] + q[2]) & 1);
-            res[t] = (wall_face(g, a, q) || solved) ? T(0) : vel_res_point<DIM, T, BULK>(a, g, C, q, phi, rhs);
-        }
-        __syncthreads();
-        const Geom& gc = gsh[1];
-        T* rc = RHS(l + 1);
-        for (int t = threadIdx.x; t < gc.nvel; t += CT) {
-            int a = 0;
-            while (a + 1 < DIM && t >= gc.foff[a + 1]) ++a;
-            int Q[3];
-            decode_face(gc, a, t - gc.foff[a], Q);
-            T v = T(0);
-            if (!wall_face(gc, a, Q)) {
-                if (a == 0) v = vel_restrict_point<DIM, 0, T>(g, Q, res);
-                else if (a == 1) v = vel_restrict_point<DIM, 1, T>(g, Q, res);
-                else v = vel_restrict_point<DIM, DIM == 3 ? 2 : 1, T>(g, Q, res);
-            }
-            rc[t] = v;
-        }
-        __syncthreads();
-    }
-    // up: prolongation and correction, post-smoothing
-    for (int l = nlev - 2; l >= 0; --l) {
-        load_geom(&gsh[0], &Ls[l].g);
-        load_geom(&gsh[1], &Ls[l + 1].g);
-        __syncthreads();
-        const Geom& g = gsh[0];
-        const Geom& gc = gsh[1];
-        const Coef<T> C = Ls[l].C;
-        T* phi = PHI(l);
-        const T* rhs = RHS(l);
-        const T* pc = PHI(l + 1);
-        for (int t = threadIdx.x; t < g.nvel; t += CT) {
-            int a = 0;
-            while (a + 1 < DIM && t >= g.foff[a + 1]) ++a;
-            int q[3];
-            decode_face(g, a, t - g.foff[a], q);
-            if (wall_face(g, a, q)) continue;
-            T v;
-            if (a == 0) v = vel_prolong_point<DIM, 0, T>(gc, q, pc);
-            else if (a == 1) v = vel_prolong_point<DIM, 1, T>(gc, q, pc);
-            else v = vel_prolong_point<DIM, DIM == 3 ? 2 : 1, T>(gc, q, pc);
-            phi[t] += v;
-        }
-        __syncthreads();
-        c_vel_sweeps<DIM, T, BULK>(g, C, nu, phi, rhs);
-    }
+    const Vecs<T, SMEM, true> V{Ls, sm, &sl, rhs0, phi0};
+    vcycle_vel_body<DIM, T, BULK, SMEM>(BlockSync{}, gsh, Ls, nlev, nlev, V, nu, ncoarse);
     if (SMEM) {   // the solution of the first level back to global memory
         __syncthreads();
         for (int t = threadIdx.x; t < sl.n[0]; t += CT) phi0[t] = sm[t];
@@ -209,66 +378,35 @@ __global__ void __launch_bounds__(CT) k_coarse_cell(const CLevel<T>* __restrict_
         __syncthreads();
         for (int t = threadIdx.x; t < sl.n[0]; t += CT) sm[sl.n[0] + t] = rhs0[t];
     }
-    auto PHI = [&](int l) -> T* { return SMEM ? sm + sl.off[l] : (l == 0 ? phi0 : Ls[l].phi_p); };
-    auto RHS = [&](int l) -> T* {
-        return SMEM ? sm + sl.off[l] + sl.n[l] : (l == 0 ? const_cast<T*>(rhs0) : Ls[l].rhs_p);
-    };
-    auto RES = [&](int l) -> T* { return SMEM ? sm + sl.off[l] + 2 * sl.n[l] : Ls[l].res_p; };
-    for (int l = 0; l < nlev; ++l) {
-        load_geom(&gsh[0], &Ls[l].g);
-        if (l + 1 < nlev) load_geom(&gsh[1], &Ls[l + 1].g);
-        __syncthreads();
-        const Geom& g = gsh[0];
-        const Coef<T> C = Ls[l].C;
-        T* phi = PHI(l);
-        const T* rhs = RHS(l);
-        for (int t = threadIdx.x; t < g.ncell; t += CT) phi[t] = T(0);
-        __syncthreads();
-        if (l + 1 == nlev) {
-            if (Ls[l].smat_p && Ls[l].smat_nc == ncoarse) smat_apply<T>(Ls[l].smat_p, g.ncell, rhs, phi);
-            else c_cell_sweeps<DIM, T>(g, C, ncoarse, phi, rhs);
-            break;
-        }
-        c_cell_sweeps<DIM, T>(g, C, nu, phi, rhs);
-        T* res = RES(l);
-        for (int t = threadIdx.x; t < g.ncell; t += CT) {
-            int q[3];
-            decode_cell(g, t, q);
-            res[t] = (nu > 0 && ((q[0] + q[1] + q[2]) & 1)) ? T(0) : cell_res_point<DIM, T>(g, C, q, phi, rhs);
-        }
-        __syncthreads();
-        const Geom& gc = gsh[1];
-        T* rc = RHS(l + 1);
-        for (int t = threadIdx.x; t < gc.ncell; t += CT) {
-            int Q[3];
-            decode_cell(gc, t, Q);
-            rc[t] = cell_restrict_point<DIM, T>(g, Q, res);
-        }
-        __syncthreads();
-    }
-    for (int l = nlev - 2; l >= 0; --l) {
-        load_geom(&gsh[0], &Ls[l].g);
-        load_geom(&gsh[1], &Ls[l + 1].g);
-        __syncthreads();
-        const Geom& g = gsh[0];
-        const Geom& gc = gsh[1];
-        const Coef<T> C = Ls[l].C;
-        T* phi = PHI(l);
-        const T* rhs = RHS(l);
-        const T* pc = PHI(l + 1);
-        for (int t = threadIdx.x; t < g.ncell; t += CT) {
-            int q[3];
-            decode_cell(g, t, q);
-            int Q[3] = {q[0] >> 1, q[1] >> 1, DIM == 3 ? q[2] >> 1 : 0};
-            phi[t] += pc[cidx(gc, Q)];
-        }
-        __syncthreads();
-        c_cell_sweeps<DIM, T>(g, C, nu, phi, rhs);
-    }
+    const Vecs<T, SMEM, false> V{Ls, sm, &sl, rhs0, phi0};
+    vcycle_cell_body<DIM, T, SMEM>(BlockSync{}, gsh, Ls, nlev, nlev, V, nu, ncoarse);
     if (SMEM) {
         __syncthreads();
         for (int t = threadIdx.x; t < sl.n[0]; t += CT) phi0[t] = sm[t];
     }
+}
+
+// Persistent multi-block V-cycle (cooperative launch, every block resident):
+// levels 0..lblock-1 of Ls as grid-wide stages separated by bounded grid
+// barriers, the levels from lblock on by block 0 alone.  It replaces one
+// kernel launch per colour and transfer on the middle levels, where a launch
+// costs more than the stage's work.
+template <int DIM, typename T, bool BULK>
+__global__ void __launch_bounds__(CT) k_grid_vel(const CLevel<T>* __restrict__ Ls, int nlev, int lblock,
+                                                 const T* rhs0, T* phi0, int nu, int ncoarse,
+                                                 GridSync S) {
+    __shared__ Geom gsh[2];
+    const Vecs<T, false, true> V{Ls, nullptr, nullptr, rhs0, phi0};
+    vcycle_vel_body<DIM, T, BULK, false>(S, gsh, Ls, nlev, lblock, V, nu, ncoarse);
+}
+
+template <int DIM, typename T>
+__global__ void __launch_bounds__(CT) k_grid_cell(const CLevel<T>* __restrict__ Ls, int nlev, int lblock,
+                                                  const T* rhs0, T* phi0, int nu, int ncoarse,
+                                                  GridSync S) {
+    __shared__ Geom gsh[2];
+    const Vecs<T, false, false> V{Ls, nullptr, nullptr, rhs0, phi0};
+    vcycle_cell_body<DIM, T, false>(S, gsh, Ls, nlev, lblock, V, nu, ncoarse);
 }
 
 // Column i of the coarse-solve matrix: the ncoarse sweeps applied to e_i.
@@ -282,7 +420,7 @@ __global__ void __launch_bounds__(CT) k_smat_vel(Geom g, Coef<T> C, int ncoarse,
         rhs[t] = t == i ? T(1) : T(0);
     }
     __syncthreads();
-    c_vel_sweeps<DIM, T, BULK>(g, C, ncoarse, phi, rhs);
+    c_vel_sweeps<DIM, T, BULK>(BlockSync{}, g, C, ncoarse, phi, rhs);
     for (int t = threadIdx.x; t < n; t += CT) st[(size_t)i * n + t] = phi[t];
 }
 
@@ -296,7 +434,7 @@ __global__ void __launch_bounds__(CT) k_smat_cell(Geom g, Coef<T> C, int ncoarse
         rhs[t] = t == i ? T(1) : T(0);
     }
     __syncthreads();
-    c_cell_sweeps<DIM, T>(g, C, ncoarse, phi, rhs);
+    c_cell_sweeps<DIM, T>(BlockSync{}, g, C, ncoarse, phi, rhs);
     for (int t = threadIdx.x; t < n; t += CT) st[(size_t)i * n + t] = phi[t];
 }
 
@@ -304,7 +442,7 @@ template <typename T>
 __global__ void __launch_bounds__(CT) k_smat_apply(int n, const T* __restrict__ st, const T* __restrict__ rhs,
                                                    T* __restrict__ phi) {
     pdl_entry();
-    smat_apply<T>(st, n, rhs, phi);
+    smat_apply<T>(BlockSync{}, st, n, rhs, phi);
 }
 
 }  // namespace
@@ -389,6 +527,71 @@ void launch_coarse_vcycle_cell(int dim, const CLevel<T>* L, int nlev, const T* r
                          : (sm ? k_coarse_cell<3, T, true> : k_coarse_cell<3, T, false>);
     cudaLaunchKernelEx(&cfg, kern, L, nlev, rhs, phi, nu, ncoarse);
 }
+
+template <typename T>
+int grid_vcycle_blocks(const Geom& g, bool vel) {
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms < 1) sms = 1;
+    // one point of one colour per thread on the first level, one block per SM at most
+    const int pts = vel ? (g.nvel / (2 * g.dim) + 1) : (g.ncell / 2 + 1);
+    int nb = (pts + CT - 1) / CT;
+    return nb < 1 ? 1 : (nb > sms ? sms : nb);
+}
+
+template <typename K, typename... Args>
+cudaError_t launch_cooperative(K kern, int nb, cudaStream_t s, unsigned* bar, Args... args) {
+    cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CT, 0);
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nb);
+    cfg.blockDim = dim3(CT);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+template <typename T>
+cudaError_t launch_grid_vcycle_vel(int dim, const Geom& g0, const CLevel<T>* L, int nlev, int lblock,
+                                   const T* rhs, T* phi, int nu, int ncoarse, bool bulk, unsigned* bar,
+                                   long long budget, int* status, cudaStream_t s) {
+    const GridSync S{bar, budget, status};
+    const int nb = grid_vcycle_blocks<T>(g0, true);
+    auto kern = dim == 2 ? (bulk ? k_grid_vel<2, T, true> : k_grid_vel<2, T, false>)
+                         : (bulk ? k_grid_vel<3, T, true> : k_grid_vel<3, T, false>);
+    return launch_cooperative(kern, nb, s, bar, L, nlev, lblock, rhs, phi, nu, ncoarse, S);
+}
+
+template <typename T>
+cudaError_t launch_grid_vcycle_cell(int dim, const Geom& g0, const CLevel<T>* L, int nlev, int lblock,
+                                    const T* rhs, T* phi, int nu, int ncoarse, unsigned* bar,
+                                    long long budget, int* status, cudaStream_t s) {
+    const GridSync S{bar, budget, status};
+    const int nb = grid_vcycle_blocks<T>(g0, false);
+    auto kern = dim == 2 ? k_grid_cell<2, T> : k_grid_cell<3, T>;
+    return launch_cooperative(kern, nb, s, bar, L, nlev, lblock, rhs, phi, nu, ncoarse, S);
+}
+
+template cudaError_t launch_grid_vcycle_vel<double>(int, const Geom&, const CLevel<double>*, int, int,
+                                                    const double*, double*, int, int, bool, unsigned*,
+                                                    long long, int*, cudaStream_t);
+template cudaError_t launch_grid_vcycle_vel<float>(int, const Geom&, const CLevel<float>*, int, int,
+                                                   const float*, float*, int, int, bool, unsigned*,
+                                                   long long, int*, cudaStream_t);
+template cudaError_t launch_grid_vcycle_cell<double>(int, const Geom&, const CLevel<double>*, int, int,
+                                                     const double*, double*, int, int, unsigned*,
+                                                     long long, int*, cudaStream_t);
+template cudaError_t launch_grid_vcycle_cell<float>(int, const Geom&, const CLevel<float>*, int, int,
+                                                    const float*, float*, int, int, unsigned*,
+                                                    long long, int*, cudaStream_t);
 
 void prepare_coarse_kernels() {
     set_smem_attr(k_coarse_vel<2, double, false, true>);

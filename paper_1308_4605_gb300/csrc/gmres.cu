@@ -28,6 +28,14 @@ __device__ __forceinline__ void set_cond(GmState* st, int slot, unsigned v,
 
 __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 
+// a bounded device wait (a grid barrier of the persistent V-cycle) ran out:
+// the iteration stops
+__device__ __forceinline__ bool timed_out(GmState* st) {
+    if (st->wait_status == 0) return false;
+    if (st->state == GM_RUNNING) st->state = GM_TIMEOUT;
+    return true;
+}
+
 __device__ __forceinline__ void fail_nonfinite(GmState* st, int why) {
     if (st->state == GM_RUNNING) {
         st->state = GM_NONFINITE;
@@ -52,6 +60,7 @@ __global__ void k_gm_begin(GmState* st, const double* __restrict__ bn2, double r
     st->nest = 0;
     st->why = 0;
     st->rnorm = st->beta = st->target = st->est = 0.0;
+    st->wait_status = 0;
     st->state = finite(st->bnorm) ? GM_RUNNING : GM_NONFINITE;
     if (!finite(st->bnorm)) st->why = GM_WHY_RHS;
     for (int i = 0; i < GM_NCOND; ++i) st->cond[i] = 0;
@@ -76,6 +85,7 @@ __global__ void k_gm_check(GmState* st, const double* __restrict__ rn2,
     st->cond[GM_COND_FIN] = 0;
     for (int j = 0; j < GM_MMAX; ++j) st->cond[GM_COND_STEP0 + j] = 0;
     unsigned go = 0;
+    timed_out(st);
     if (st->state == GM_RUNNING) {
         const double rn = sqrt(*rn2);
         st->rnorm = rn;
@@ -100,6 +110,7 @@ __global__ void k_gm_start(GmState* st, const double* __restrict__ vn2,
     pdl_entry();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     unsigned go = 0;
+    timed_out(st);
     if (st->state == GM_RUNNING) {
         const double beta = st->flex ? st->rnorm : sqrt(*vn2);
         st->beta = beta;
@@ -131,6 +142,7 @@ __global__ void k_gm_step(GmState* st, int j, const double* __restrict__ hcol,
                           const double* __restrict__ n2, cudaGraphConditionalHandle hn, int use) {
     pdl_entry();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (timed_out(st)) st->k = 0;   // no update from a cycle whose preconditioner failed
     if (st->state != GM_RUNNING) {
         if (j + 1 < st->m) set_cond(st, GM_COND_STEP0 + j + 1, 0u, hn, use);
         return;

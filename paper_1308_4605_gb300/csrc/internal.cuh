@@ -261,6 +261,22 @@ void launch_coarse_vcycle_vel(int dim, const CLevel<T>* L, int nlev, const T* rh
 template <typename T>
 void launch_coarse_vcycle_cell(int dim, const CLevel<T>* L, int nlev, const T* rhs, T* phi, int nu,
                                int ncoarse, size_t smem, cudaStream_t s);
+// The same V-cycle from the level L[0] down as one persistent cooperative
+// launch (coarse.cu): levels 0..lblock-1 as grid-wide stages separated by
+// grid barriers (every block resident: one block of 1024 threads per SM at
+// most, as many as the first level has points of one colour per 1024
+// threads), levels lblock.. by one block.  Each barrier wait is bounded by
+// budget clock64() cycles; when one runs out, STK_ERR_TIMEOUT is written to
+// *status and the launch ends at its next barriers.  bar: two unsigned words
+// of device memory (zeroed before the launch, on s).  g0: L[0]'s geometry.
+template <typename T>
+cudaError_t launch_grid_vcycle_vel(int dim, const Geom& g0, const CLevel<T>* L, int nlev, int lblock,
+                                   const T* rhs, T* phi, int nu, int ncoarse, bool bulk, unsigned* bar,
+                                   long long budget, int* status, cudaStream_t s);
+template <typename T>
+cudaError_t launch_grid_vcycle_cell(int dim, const Geom& g0, const CLevel<T>* L, int nlev, int lblock,
+                                    const T* rhs, T* phi, int nu, int ncoarse, unsigned* bar,
+                                    long long budget, int* status, cudaStream_t s);
 // Shared-memory budget of the coarse-level kernels: with smem > 0 (the bytes
 // of phi, rhs and residual of every level handled) and at most this many
 // bytes, the work vectors live in shared memory; 0 keeps them in global
@@ -312,11 +328,12 @@ constexpr int GM_NHIST = 256;    // true relative residuals at cycle starts kept
 constexpr int GM_NEST = 2048;    // Arnoldi residual estimates kept
 constexpr int GM_COND_PRE = 0, GM_COND_FIN = 1, GM_COND_CHK = 2, GM_COND_STEP0 = 3;
 constexpr int GM_NCOND = GM_COND_STEP0 + GM_MMAX;
-enum { GM_RUNNING = 0, GM_CONVERGED = 1, GM_MAXIT = 2, GM_NONFINITE = 3 };
+enum { GM_RUNNING = 0, GM_CONVERGED = 1, GM_MAXIT = 2, GM_NONFINITE = 3, GM_TIMEOUT = 4 };
 enum { GM_WHY_RHS = 1, GM_WHY_RESIDUAL, GM_WHY_PRECOND, GM_WHY_ARNOLDI, GM_WHY_UPDATE };
 struct GmState {
     // header: read by the host after every cycle
     int state, why, k, iterations, restarts, maxit, m, flex, nhist, nest;
+    int wait_status;   // STK_ERR_TIMEOUT once a bounded device wait ran out, else 0
     double bnorm, rnorm, beta, target, est, rtol, inv_scale;
     unsigned cond[GM_NCOND];
     // column j of H at H[j * (GM_MMAX + 1)], rows 0..j+1

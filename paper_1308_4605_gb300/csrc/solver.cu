@@ -117,6 +117,9 @@ struct stk_handle {
     int lcoarse_d = 0, lcoarse_f = 0;        // first level run by the coarse kernel (FP64, FP32)
     int tpb_d = 256, tpb_f = 256;            // threads per block of the colour kernels
     int lpair_d = 0, lpair_f = 0;            // first level smoothed by the two-colour kernels
+    int lgrid_d = 0, lgrid_f = 0;            // first level run by the persistent multi-block kernel
+    unsigned* gbar = nullptr;                // its grid barrier (two words)
+    long long wait_budget = 2000000000LL;    // clock64() cycles a device wait may last
     bool bulk = false;                       // bulk-viscosity stress form on
     StressWork sw{};                         // stress scratch of the finest level (FP64)
     double *gamma = nullptr, *rho0 = nullptr, *mu0 = nullptr;   // level-0 fields
@@ -356,6 +359,7 @@ template <typename T> int lcoarse_of(const stk_handle* h) {
     return sizeof(T) == 8 ? h->lcoarse_d : h->lcoarse_f;
 }
 template <typename T> int tpb_of(const stk_handle* h) { return sizeof(T) == 8 ? h->tpb_d : h->tpb_f; }
+template <typename T> int lgrid_of(const stk_handle* h) { return sizeof(T) == 8 ? h->lgrid_d : h->lgrid_f; }
 template <typename T> int lpair_of(const stk_handle* h) {
     return sizeof(T) == 8 ? h->lpair_d : h->lpair_f;
 }
@@ -491,6 +495,13 @@ void vcycle_vel(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp, 
                                     mp.nu, mp.ncoarse, h->bulk, coarse_smem<T>(h, l, true), s);
         return;
     }
+    if (l >= lgrid_of<T>(h)) {     // this level down as one persistent multi-block launch
+        Scope sc(h, PF_COARSE, 0.0, s);
+        launch_grid_vcycle_vel<T>(L.g.dim, L.g, clev_of<T>(h) + l, (int)h->lev.size() - l,
+                                  lcoarse_of<T>(h) - l, rhs, phi, mp.nu, mp.ncoarse, h->bulk, h->gbar,
+                                  h->wait_budget, &h->gst->wait_status, s);
+        return;
+    }
     if (l + 1 == (int)h->lev.size() && smat_u_of<T>(L) && mp.ncoarse == SMAT_SWEEPS) {
         Scope sc(h, PF_COARSE, 0.0, s);
         launch_coarsest_apply<T>(L.g.nvel, smat_u_of<T>(L), rhs, phi, s);
@@ -535,6 +546,13 @@ void vcycle_cell(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp,
         Scope sc(h, PF_COARSE, 0.0, s);
         launch_coarse_vcycle_cell<T>(L.g.dim, clev_of<T>(h) + l, (int)h->lev.size() - l, rhs, phi,
                                      mp.nu, mp.ncoarse, coarse_smem<T>(h, l, false), s);
+        return;
+    }
+    if (l >= lgrid_of<T>(h)) {
+        Scope sc(h, PF_COARSE, 0.0, s);
+        launch_grid_vcycle_cell<T>(L.g.dim, L.g, clev_of<T>(h) + l, (int)h->lev.size() - l,
+                                   lcoarse_of<T>(h) - l, rhs, phi, mp.nu, mp.ncoarse, h->gbar,
+                                   h->wait_budget, &h->gst->wait_status, s);
         return;
     }
     if (l + 1 == (int)h->lev.size() && smat_p_of<T>(L) && mp.ncoarse == SMAT_SWEEPS) {
@@ -1092,6 +1110,9 @@ void absorb_cycle(Inst* it, const stk_solver_params& prm, const MGParams& mp) {
     case GM_RUNNING: break;
     case GM_CONVERGED: it->info.converged = 1; finish(it, STK_OK); break;
     case GM_MAXIT: finish(it, STK_ERR_NOT_CONVERGED); break;
+    case GM_TIMEOUT:
+        finish(it, fail(h, STK_ERR_TIMEOUT, "a bounded device wait (grid barrier) ran out"));
+        break;
     default: {
         static const char* why[] = {"", "non-finite right-hand side", "non-finite residual",
                                     "non-finite preconditioned residual",
@@ -1449,6 +1470,7 @@ int stk_create(int dim, const int* n, double hh, const int* bc, stk_handle** out
         double* q = nullptr;
         CKC(dalloc(h, &q, (sizeof(GmState) + 7) / 8));
         h->gst = reinterpret_cast<GmState*>(q);
+        CKC(dalloc(h, &h->gbar, 2));
         CKC(cudaMallocHost(&p, sizeof(GmState)));
         h->gst_host = static_cast<GmState*>(p);
         std::memset(h->gst_host, 0, sizeof(GmState));
@@ -1459,6 +1481,7 @@ int stk_create(int dim, const int* n, double hh, const int* bc, stk_handle** out
     {   // level descriptors of the single-block coarse-level kernel
         const int nl = (int)h->lev.size();
         h->lcoarse_d = h->lcoarse_f = nl;
+        h->lgrid_d = h->lgrid_f = nl;
         // two-colour sweeps by default only in FP32 2D, where their halo
         // recomputation is small (measured; the autotuner decides per grid)
         h->lpair_d = nl;
@@ -1822,6 +1845,7 @@ int stk_get_schedule(const stk_handle* h, int precision, stk_schedule* out) {
     out->coarse_level = precision == STK_FP64 ? h->lcoarse_d : h->lcoarse_f;
     out->threads = precision == STK_FP64 ? h->tpb_d : h->tpb_f;
     out->pair_level = precision == STK_FP64 ? h->lpair_d : h->lpair_f;
+    out->grid_level = precision == STK_FP64 ? h->lgrid_d : h->lgrid_f;
     return STK_OK;
 }
 
@@ -1835,15 +1859,19 @@ int stk_set_schedule(stk_handle* h, int precision, const stk_schedule* sc) {
         return fail(h, STK_ERR_ARG, "threads must be 64, 128, 256 or 512");
     if (sc->pair_level < 0 || sc->pair_level > (int)h->lev.size())
         return fail(h, STK_ERR_ARG, "pair_level must be in 0..%d", (int)h->lev.size());
+    if (sc->grid_level < 0 || sc->grid_level > (int)h->lev.size())
+        return fail(h, STK_ERR_ARG, "grid_level must be in 0..%d", (int)h->lev.size());
     clear_graphs(h);
     if (precision == STK_FP64) {
         h->lcoarse_d = sc->coarse_level;
         h->tpb_d = sc->threads;
         h->lpair_d = sc->pair_level;
+        h->lgrid_d = sc->grid_level;
     } else {
         h->lcoarse_f = sc->coarse_level;
         h->tpb_f = sc->threads;
         h->lpair_f = sc->pair_level;
+        h->lgrid_f = sc->grid_level;
     }
     return STK_OK;
 }
@@ -1911,15 +1939,26 @@ int stk_autotune(stk_handle* h, int precision, stk_schedule* best, void* stream)
         int pls[4], npl = 0;
         for (int p = 0; p < 3 && p < lc; ++p) pls[npl++] = p;
         pls[npl++] = lc;
+        // the persistent multi-block kernel from one or two levels above
+        // the single-block one (grid_level), or not at all (= lc)
+        int gls[3], ngl = 0;
+        gls[ngl++] = lc;
+        for (int d = 1; d <= 2 && lc - d >= 0; ++d)
+            if (h->lev[lc - d].g.ncell <= 262144) gls[ngl++] = lc - d;
         for (int k = 0; k < npl; ++k)
+            for (int gi = 0; gi < ngl; ++gi)
             for (int ti = 0; ti < (pls[k] == 0 ? 1 : 3); ++ti) {
-                stk_schedule c{lc, threads[ti], pls[k]};
+                if (gls[gi] < lc && pls[k] > gls[gi] && pls[k] < lc) continue;
+                stk_schedule c{lc, threads[ti], pls[k], gls[gi]};
                 int rc = stk_set_schedule(h, precision, &c);
                 if (rc) { h->prof = prof; return rc; }
                 float ms = 0.f;
                 rc = precision == STK_FP64 ? time_vcycles<double>(h, 3, s, &ms)
                                            : time_vcycles<float>(h, 3, s, &ms);
-                if (rc) { h->prof = prof; return rc; }
+                if (rc) {   // a schedule that cannot be captured or launched is skipped
+                    cudaGetLastError();
+                    continue;
+                }
                 if (ms < bms) {
                     bms = ms;
                     bs = c;
@@ -2013,6 +2052,25 @@ int stk_set_graphs(stk_handle* h, int enable) {
     clear_graphs(h);
     h->use_graphs = enable != 0;
     return STK_OK;
+}
+
+int stk_graphs_in_use(const stk_handle* h) { return h ? (h->use_graphs ? 1 : 0) : STK_ERR_ARG; }
+
+int stk_set_wait_budget(stk_handle* h, long long cycles) {
+    if (!h) return STK_ERR_ARG;
+    if (cycles < 0) return fail(h, STK_ERR_ARG, "the wait budget must be >= 0");
+    h->wait_budget = cycles;
+    return STK_OK;
+}
+
+int stk_wait_status(stk_handle* h, int reset) {
+    if (!h) return STK_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    CK(cudaDeviceSynchronize());
+    int v = 0;
+    CK(cudaMemcpy(&v, &h->gst->wait_status, sizeof v, cudaMemcpyDeviceToHost));
+    if (reset) CK(cudaMemset(&h->gst->wait_status, 0, sizeof v));
+    return v == 0 ? STK_OK : STK_ERR_TIMEOUT;
 }
 
 int stk_solve_history(const stk_handle* h, int kind, double* out, int cap) {

@@ -55,7 +55,7 @@ class stk_solve_info(ctypes.Structure):
 
 class stk_schedule(ctypes.Structure):
     _fields_ = [("coarse_level", ctypes.c_int), ("threads", ctypes.c_int),
-                ("pair_level", ctypes.c_int)]
+                ("pair_level", ctypes.c_int), ("grid_level", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -103,6 +103,9 @@ def _load():
                                   ctypes.POINTER(stk_batch_io), ctypes.POINTER(stk_solve_info), P]),
         "stk_remove_mean": (I, [P, P, P, P]),
         "stk_set_graphs": (I, [P, I]),
+        "stk_graphs_in_use": (I, [P]),
+        "stk_set_wait_budget": (I, [P, ctypes.c_longlong]),
+        "stk_wait_status": (I, [P, I]),
         "stk_bounds_violations": (ctypes.c_longlong, [ctypes.POINTER(ctypes.c_longlong),
                                                       ctypes.POINTER(ctypes.c_longlong), I]),
         "stk_bounds_selftest": (I, [P]),
@@ -122,7 +125,7 @@ _lib = _load()
 EXPORTED = ["stk_default_params", "stk_create", "stk_destroy", "stk_last_error", "stk_face_length",
             "stk_cell_length", "stk_set_coefficients", "stk_set_bulk_viscosity", "stk_apply_operator",
             "stk_apply_preconditioner", "stk_apply_preconditioner_params", "stk_velocity_vcycle", "stk_pressure_vcycle", "stk_solve",
-            "stk_profile", "stk_profile_read", "stk_kernel_launches", "stk_pressure_vcycle_noalloc", "stk_remove_mean", "stk_set_graphs", "stk_solve_history", "stk_bounds_violations", "stk_bounds_selftest", "stk_gradient", "stk_backward_euler_rhs", "stk_subtract_boundary_terms", "stk_solve_batched", "stk_get_schedule", "stk_set_schedule", "stk_autotune"]
+            "stk_profile", "stk_profile_read", "stk_kernel_launches", "stk_pressure_vcycle_noalloc", "stk_remove_mean", "stk_set_graphs", "stk_graphs_in_use", "stk_set_wait_budget", "stk_wait_status", "stk_solve_history", "stk_bounds_violations", "stk_bounds_selftest", "stk_gradient", "stk_backward_euler_rhs", "stk_subtract_boundary_terms", "stk_solve_batched", "stk_get_schedule", "stk_set_schedule", "stk_autotune"]
 
 
 def library():
@@ -313,8 +316,10 @@ def stk_get_schedule(h, precision):
     return sc.as_dict()
 
 
-def stk_set_schedule(h, precision, coarse_level, threads, pair_level):
-    sc = stk_schedule(int(coarse_level), int(threads), int(pair_level))
+def stk_set_schedule(h, precision, coarse_level, threads, pair_level, grid_level=None):
+    """grid_level None: no persistent multi-block levels (= coarse_level)."""
+    gl = coarse_level if grid_level is None else grid_level
+    sc = stk_schedule(int(coarse_level), int(threads), int(pair_level), int(gl))
     return _check(h, _lib.stk_set_schedule(h, int(precision), ctypes.byref(sc)))
 
 
@@ -376,6 +381,19 @@ def stk_bounds_selftest(stream=None):
 
 def stk_set_graphs(h, enable):
     return _check(h, _lib.stk_set_graphs(h, int(bool(enable))))
+
+
+def stk_graphs_in_use(h):
+    return int(_lib.stk_graphs_in_use(h))
+
+
+def stk_set_wait_budget(h, cycles):
+    return _check(h, _lib.stk_set_wait_budget(h, int(cycles)))
+
+
+def stk_wait_status(h, reset=False):
+    """STK_OK, or STK_ERR_TIMEOUT when a bounded device wait ran out."""
+    return int(_lib.stk_wait_status(h, int(bool(reset))))
 
 
 def stk_kernel_launches(h):

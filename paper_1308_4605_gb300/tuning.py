@@ -25,7 +25,7 @@ def cache_path():
 def _key(solver, precision):
     import torch
     dev = torch.cuda.get_device_name(torch.cuda.current_device())
-    return f"s2|{dev}|{solver.dim}|{'x'.join(map(str, solver.n[:solver.dim]))}|" \
+    return f"s3|{dev}|{solver.dim}|{'x'.join(map(str, solver.n[:solver.dim]))}|" \
            f"{','.join(map(str, solver.bc[:2 * solver.dim]))}|{precision}"
 
 
@@ -46,7 +46,7 @@ def tune(solver, precision, path=None):
     if key in cache:
         sc = cache[key]
         S.stk_set_schedule(solver.handle, precision, sc["coarse_level"], sc["threads"],
-                           sc["pair_level"])
+                           sc["pair_level"], sc.get("grid_level"))
         return sc
     sc = S.stk_autotune(solver.handle, precision)
     cache = _load(path)
