@@ -50,7 +50,7 @@ struct BlockSync {
 
 struct GridSync {
     unsigned* bar;        // [0] arrivals, [1] generation (zeroed before the launch)
-    long long budget;     // clock64() cycles one wait may last
+    long long budget;     // clock64() cycles one wait may last (read from device memory at launch)
     int* status;          // 0, or STK_ERR_TIMEOUT once a wait ran out
     __device__ __forceinline__ int tid() const { return blockIdx.x * CT + threadIdx.x; }
     __device__ __forceinline__ int nth() const { return gridDim.x * CT; }
@@ -394,8 +394,9 @@ __global__ void __launch_bounds__(CT) k_coarse_cell(const CLevel<T>* __restrict_
 template <int DIM, typename T, bool BULK>
 __global__ void __launch_bounds__(CT) k_grid_vel(const CLevel<T>* __restrict__ Ls, int nlev, int lblock,
                                                  const T* rhs0, T* phi0, int nu, int ncoarse,
-                                                 GridSync S) {
+                                                 unsigned* bar, const long long* budget, int* status) {
     __shared__ Geom gsh[2];
+    const GridSync S{bar, *budget, status};
     const Vecs<T, false, true> V{Ls, nullptr, nullptr, rhs0, phi0};
     vcycle_vel_body<DIM, T, BULK, false>(S, gsh, Ls, nlev, lblock, V, nu, ncoarse);
 }
@@ -403,8 +404,9 @@ __global__ void __launch_bounds__(CT) k_grid_vel(const CLevel<T>* __restrict__ L
 template <int DIM, typename T>
 __global__ void __launch_bounds__(CT) k_grid_cell(const CLevel<T>* __restrict__ Ls, int nlev, int lblock,
                                                   const T* rhs0, T* phi0, int nu, int ncoarse,
-                                                  GridSync S) {
+                                                  unsigned* bar, const long long* budget, int* status) {
     __shared__ Geom gsh[2];
+    const GridSync S{bar, *budget, status};
     const Vecs<T, false, false> V{Ls, nullptr, nullptr, rhs0, phi0};
     vcycle_cell_body<DIM, T, false>(S, gsh, Ls, nlev, lblock, V, nu, ncoarse);
 }
@@ -562,36 +564,36 @@ cudaError_t launch_cooperative(K kern, int nb, cudaStream_t s, unsigned* bar, Ar
 template <typename T>
 cudaError_t launch_grid_vcycle_vel(int dim, const Geom& g0, const CLevel<T>* L, int nlev, int lblock,
                                    const T* rhs, T* phi, int nu, int ncoarse, bool bulk, unsigned* bar,
-                                   long long budget, int* status, cudaStream_t s) {
-    const GridSync S{bar, budget, status};
+                                   const long long* budget, int* status, cudaStream_t s) {
     const int nb = grid_vcycle_blocks<T>(g0, true);
     auto kern = dim == 2 ? (bulk ? k_grid_vel<2, T, true> : k_grid_vel<2, T, false>)
                          : (bulk ? k_grid_vel<3, T, true> : k_grid_vel<3, T, false>);
-    return launch_cooperative(kern, nb, s, bar, L, nlev, lblock, rhs, phi, nu, ncoarse, S);
+    return launch_cooperative(kern, nb, s, bar, L, nlev, lblock, rhs, phi, nu, ncoarse, bar, budget,
+                              status);
 }
 
 template <typename T>
 cudaError_t launch_grid_vcycle_cell(int dim, const Geom& g0, const CLevel<T>* L, int nlev, int lblock,
                                     const T* rhs, T* phi, int nu, int ncoarse, unsigned* bar,
-                                    long long budget, int* status, cudaStream_t s) {
-    const GridSync S{bar, budget, status};
+                                    const long long* budget, int* status, cudaStream_t s) {
     const int nb = grid_vcycle_blocks<T>(g0, false);
     auto kern = dim == 2 ? k_grid_cell<2, T> : k_grid_cell<3, T>;
-    return launch_cooperative(kern, nb, s, bar, L, nlev, lblock, rhs, phi, nu, ncoarse, S);
+    return launch_cooperative(kern, nb, s, bar, L, nlev, lblock, rhs, phi, nu, ncoarse, bar, budget,
+                              status);
 }
 
 template cudaError_t launch_grid_vcycle_vel<double>(int, const Geom&, const CLevel<double>*, int, int,
                                                     const double*, double*, int, int, bool, unsigned*,
-                                                    long long, int*, cudaStream_t);
+                                                    const long long*, int*, cudaStream_t);
 template cudaError_t launch_grid_vcycle_vel<float>(int, const Geom&, const CLevel<float>*, int, int,
                                                    const float*, float*, int, int, bool, unsigned*,
-                                                   long long, int*, cudaStream_t);
+                                                   const long long*, int*, cudaStream_t);
 template cudaError_t launch_grid_vcycle_cell<double>(int, const Geom&, const CLevel<double>*, int, int,
                                                      const double*, double*, int, int, unsigned*,
-                                                     long long, int*, cudaStream_t);
+                                                     const long long*, int*, cudaStream_t);
 template cudaError_t launch_grid_vcycle_cell<float>(int, const Geom&, const CLevel<float>*, int, int,
                                                     const float*, float*, int, int, unsigned*,
-                                                    long long, int*, cudaStream_t);
+                                                    const long long*, int*, cudaStream_t);
 
 void prepare_coarse_kernels() {
     set_smem_attr(k_coarse_vel<2, double, false, true>);

@@ -266,17 +266,18 @@ void launch_coarse_vcycle_cell(int dim, const CLevel<T>* L, int nlev, const T* r
 // grid barriers (every block resident: one block of 1024 threads per SM at
 // most, as many as the first level has points of one colour per 1024
 // threads), levels lblock.. by one block.  Each barrier wait is bounded by
-// budget clock64() cycles; when one runs out, STK_ERR_TIMEOUT is written to
+// *budget clock64() cycles (a device scalar, read at launch, so captured
+// graphs follow changes); when one runs out, STK_ERR_TIMEOUT is written to
 // *status and the launch ends at its next barriers.  bar: two unsigned words
 // of device memory (zeroed before the launch, on s).  g0: L[0]'s geometry.
 template <typename T>
 cudaError_t launch_grid_vcycle_vel(int dim, const Geom& g0, const CLevel<T>* L, int nlev, int lblock,
                                    const T* rhs, T* phi, int nu, int ncoarse, bool bulk, unsigned* bar,
-                                   long long budget, int* status, cudaStream_t s);
+                                   const long long* budget, int* status, cudaStream_t s);
 template <typename T>
 cudaError_t launch_grid_vcycle_cell(int dim, const Geom& g0, const CLevel<T>* L, int nlev, int lblock,
                                     const T* rhs, T* phi, int nu, int ncoarse, unsigned* bar,
-                                    long long budget, int* status, cudaStream_t s);
+                                    const long long* budget, int* status, cudaStream_t s);
 // Shared-memory budget of the coarse-level kernels: with smem > 0 (the bytes
 // of phi, rhs and residual of every level handled) and at most this many
 // bytes, the work vectors live in shared memory; 0 keeps them in global

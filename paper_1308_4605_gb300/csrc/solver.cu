@@ -118,8 +118,8 @@ struct stk_handle {
     int tpb_d = 256, tpb_f = 256;            // threads per block of the colour kernels
     int lpair_d = 0, lpair_f = 0;            // first level smoothed by the two-colour kernels
     int lgrid_d = 0, lgrid_f = 0;            // first level run by the persistent multi-block kernel
-    unsigned* gbar = nullptr;                // its grid barrier (two words)
-    long long wait_budget = 2000000000LL;    // clock64() cycles a device wait may last
+    unsigned* gbar = nullptr;                // its grid barrier (two words), then the wait
+                                             // budget in clock64() cycles (a long long)
     bool bulk = false;                       // bulk-viscosity stress form on
     StressWork sw{};                         // stress scratch of the finest level (FP64)
     double *gamma = nullptr, *rho0 = nullptr, *mu0 = nullptr;   // level-0 fields
@@ -499,7 +499,7 @@ void vcycle_vel(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp, 
         Scope sc(h, PF_COARSE, 0.0, s);
         launch_grid_vcycle_vel<T>(L.g.dim, L.g, clev_of<T>(h) + l, (int)h->lev.size() - l,
                                   lcoarse_of<T>(h) - l, rhs, phi, mp.nu, mp.ncoarse, h->bulk, h->gbar,
-                                  h->wait_budget, &h->gst->wait_status, s);
+                                  reinterpret_cast<const long long*>(h->gbar + 2), &h->gst->wait_status, s);
         return;
     }
     if (l + 1 == (int)h->lev.size() && smat_u_of<T>(L) && mp.ncoarse == SMAT_SWEEPS) {
@@ -552,7 +552,7 @@ void vcycle_cell(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp,
         Scope sc(h, PF_COARSE, 0.0, s);
         launch_grid_vcycle_cell<T>(L.g.dim, L.g, clev_of<T>(h) + l, (int)h->lev.size() - l,
                                    lcoarse_of<T>(h) - l, rhs, phi, mp.nu, mp.ncoarse, h->gbar,
-                                   h->wait_budget, &h->gst->wait_status, s);
+                                   reinterpret_cast<const long long*>(h->gbar + 2), &h->gst->wait_status, s);
         return;
     }
     if (l + 1 == (int)h->lev.size() && smat_p_of<T>(L) && mp.ncoarse == SMAT_SWEEPS) {
@@ -1470,7 +1470,9 @@ int stk_create(int dim, const int* n, double hh, const int* bc, stk_handle** out
         double* q = nullptr;
         CKC(dalloc(h, &q, (sizeof(GmState) + 7) / 8));
         h->gst = reinterpret_cast<GmState*>(q);
-        CKC(dalloc(h, &h->gbar, 2));
+        CKC(dalloc(h, &h->gbar, 4));
+        const long long budget = 2000000000LL;   // about one second at 2 GHz
+        CKC(cudaMemcpy(h->gbar + 2, &budget, sizeof budget, cudaMemcpyHostToDevice));
         CKC(cudaMallocHost(&p, sizeof(GmState)));
         h->gst_host = static_cast<GmState*>(p);
         std::memset(h->gst_host, 0, sizeof(GmState));
@@ -2059,7 +2061,8 @@ int stk_graphs_in_use(const stk_handle* h) { return h ? (h->use_graphs ? 1 : 0) 
 int stk_set_wait_budget(stk_handle* h, long long cycles) {
     if (!h) return STK_ERR_ARG;
     if (cycles < 0) return fail(h, STK_ERR_ARG, "the wait budget must be >= 0");
-    h->wait_budget = cycles;
+    CK(cudaSetDevice(h->device));
+    CK(cudaMemcpy(h->gbar + 2, &cycles, sizeof cycles, cudaMemcpyHostToDevice));
     return STK_OK;
 }
 
