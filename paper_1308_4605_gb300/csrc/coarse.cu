@@ -536,9 +536,10 @@ int grid_vcycle_blocks(const Geom& g, bool vel) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms < 1) sms = 1;
-    // one point of one colour per thread on the first level, one block per SM at most
+    // about 128 points of one colour per block on the first level (FP64 work
+    // is bound by the per-SM FP64 rate, so spread it), one block per SM at most
     const int pts = vel ? (g.nvel / (2 * g.dim) + 1) : (g.ncell / 2 + 1);
-    int nb = (pts + CT - 1) / CT;
+    int nb = (pts + (sizeof(T) == 8 ? 127 : 511)) / (sizeof(T) == 8 ? 128 : 512);
     return nb < 1 ? 1 : (nb > sms ? sms : nb);
 }
 
