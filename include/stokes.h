@@ -229,6 +229,14 @@ int stk_backward_euler_rhs(stk_handle* h, const double* const* u_n, const double
 int stk_gradient(stk_handle* h, const double* const* u, const double* const* lambda,
                  double* dL_dlogmu, double* dL_drho, void* stream);
 
+/* y = x widened from FP32 to FP64 (n elements, device arrays, no handle),
+ * with the exact conversion the flexible solve applies to its FP32
+ * preconditioner outputs: integer instructions build the binary64 encoding
+ * (GB300's FP64 pipe, which the conversion instruction would occupy, stays
+ * free); bitwise equal to the conversion instruction for every input.
+ * Stream-ordered.  Returns STK_OK, STK_ERR_ARG or STK_ERR_CUDA. */
+int stk_widen(const float* x, double* y, long long n, void* stream);
+
 /* Bound of every device-side wait of h's kernels (the grid barriers of the
  * persistent multi-block V-cycle), in clock64() cycles of the SM clock
  * (default 2e9, about one second).  A wait that runs out writes

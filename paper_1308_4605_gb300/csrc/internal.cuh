@@ -172,6 +172,27 @@ void launch_oob_selftest(int n, cudaStream_t s);
 #define STK_OOB_READER(name)
 #endif
 
+// FP32 -> FP64, exact, with integer instructions (IEEE 754 binary32 ->
+// binary64: same sign, exponent rebiased by 1023 - 127 = 896, fraction
+// shifted left by 29).  The conversion instruction runs on GB300's FP64
+// pipe, which streaming kernels that widen every element would otherwise
+// saturate; zeros are built here too, and only subnormal, infinite and NaN
+// inputs (exponent field 0 with a non-zero fraction, or 255) take the
+// conversion instruction.
+__device__ __forceinline__ double widen(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    if (e == 0u || e == 0xffu) {
+        if ((u & 0x7fffffffu) == 0u) return __longlong_as_double((long long)sign);
+        return double(f);
+    }
+    const unsigned long long bits = sign | ((unsigned long long)(e + 896u) << 52) |
+                                    ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
 // zero n elements (a kernel, so that it takes part in the launch chain)
 template <typename T>
 void launch_zero(int n, T* x, cudaStream_t s);

@@ -235,11 +235,19 @@ __global__ void k_bulk_lambda(int n, const double* __restrict__ gamma, const dou
     if (t < n) lam[t] = fma(-2.0 / 3.0, mu[t], gamma[t]);
 }
 
+// b = a converted: FP32 -> FP64 by widen() (integer instructions, exact),
+// FP64 -> FP32 by the rounding conversion
+template <typename TB, typename TA>
+__device__ __forceinline__ TB conv(TA v) {
+    if constexpr (sizeof(TB) == 8 && sizeof(TA) == 4) return widen(v);
+    else return TB(v);
+}
+
 template <typename TA, typename TB>
 __global__ void k_convert(int n, const TA* __restrict__ a, TB* __restrict__ b) {
     pdl_entry();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n) b[t] = TB(a[t]);
+    if (t < n) b[t] = conv<TB>(a[t]);
 }
 
 // 16-byte loads and stores of four consecutive elements (both arrays 16-byte
@@ -271,10 +279,10 @@ __global__ void k_convert4(int n, const TA* __restrict__ a, TB* __restrict__ b) 
         TB w[4];
         ld4(a + i, v);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) w[k] = TB(v[k]);
+        for (int k = 0; k < 4; ++k) w[k] = conv<TB>(v[k]);
         st4(b + i, w);
     } else {
-        for (long long k = i; k < n; ++k) b[k] = TB(a[k]);
+        for (long long k = i; k < n; ++k) b[k] = conv<TB>(a[k]);
     }
 }
 

@@ -147,15 +147,15 @@ __global__ void __launch_bounds__(KT) k_comb(int n, PtrArr V, const double* __re
 #pragma unroll
         for (int i = 0; i < K; ++i) {
             const V2 v = reinterpret_cast<const V2*>(V.p[i])[t];
-            a.x = fma(yy[i], double(v.x), a.x);
-            a.y = fma(yy[i], double(v.y), a.y);
+            a.x = fma(yy[i], widen(v.x), a.x);
+            a.y = fma(yy[i], widen(v.y), a.y);
         }
         x2[t] = a;
     }
     if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
         double a = x[n - 1];
 #pragma unroll
-        for (int i = 0; i < K; ++i) a = fma(yy[i], double(static_cast<const TV*>(V.p[i])[n - 1]), a);
+        for (int i = 0; i < K; ++i) a = fma(yy[i], widen(static_cast<const TV*>(V.p[i])[n - 1]), a);
         x[n - 1] = a;
     }
 }
@@ -180,8 +180,8 @@ __global__ void __launch_bounds__(KT) k_comb_dev(int n, PtrArr V, const double* 
         for (int i = 0; i < K; ++i) {
             if (i < k) {
                 const V2 v = reinterpret_cast<const V2*>(V.p[i])[t];
-                a.x = fma(yy[i], double(v.x), a.x);
-                a.y = fma(yy[i], double(v.y), a.y);
+                a.x = fma(yy[i], widen(v.x), a.x);
+                a.y = fma(yy[i], widen(v.y), a.y);
             }
         }
         x2[t] = a;
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(KT) k_comb_dev(int n, PtrArr V, const double* 
         double a = x[n - 1];
 #pragma unroll
         for (int i = 0; i < K; ++i)
-            if (i < k) a = fma(yy[i], double(static_cast<const TV*>(V.p[i])[n - 1]), a);
+            if (i < k) a = fma(yy[i], widen(static_cast<const TV*>(V.p[i])[n - 1]), a);
         x[n - 1] = a;
     }
 }

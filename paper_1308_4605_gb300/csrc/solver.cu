@@ -2056,6 +2056,13 @@ int stk_set_graphs(stk_handle* h, int enable) {
     return STK_OK;
 }
 
+int stk_widen(const float* x, double* y, long long n, void* stream) {
+    if (!x || !y || n < 0 || n > 0x7fffffffLL) return STK_ERR_ARG;
+    if (n == 0) return STK_OK;
+    launch_convert<float, double>((int)n, x, y, static_cast<cudaStream_t>(stream));
+    return cudaGetLastError() == cudaSuccess ? STK_OK : STK_ERR_CUDA;
+}
+
 int stk_graphs_in_use(const stk_handle* h) { return h ? (h->use_graphs ? 1 : 0) : STK_ERR_ARG; }
 
 int stk_set_wait_budget(stk_handle* h, long long cycles) {

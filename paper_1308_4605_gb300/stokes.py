@@ -104,6 +104,7 @@ def _load():
         "stk_remove_mean": (I, [P, P, P, P]),
         "stk_set_graphs": (I, [P, I]),
         "stk_graphs_in_use": (I, [P]),
+        "stk_widen": (I, [P, P, ctypes.c_longlong, P]),
         "stk_set_wait_budget": (I, [P, ctypes.c_longlong]),
         "stk_wait_status": (I, [P, I]),
         "stk_bounds_violations": (ctypes.c_longlong, [ctypes.POINTER(ctypes.c_longlong),
@@ -125,7 +126,7 @@ _lib = _load()
 EXPORTED = ["stk_default_params", "stk_create", "stk_destroy", "stk_last_error", "stk_face_length",
             "stk_cell_length", "stk_set_coefficients", "stk_set_bulk_viscosity", "stk_apply_operator",
             "stk_apply_preconditioner", "stk_apply_preconditioner_params", "stk_velocity_vcycle", "stk_pressure_vcycle", "stk_solve",
-            "stk_profile", "stk_profile_read", "stk_kernel_launches", "stk_pressure_vcycle_noalloc", "stk_remove_mean", "stk_set_graphs", "stk_graphs_in_use", "stk_set_wait_budget", "stk_wait_status", "stk_solve_history", "stk_bounds_violations", "stk_bounds_selftest", "stk_gradient", "stk_backward_euler_rhs", "stk_subtract_boundary_terms", "stk_solve_batched", "stk_get_schedule", "stk_set_schedule", "stk_autotune"]
+            "stk_profile", "stk_profile_read", "stk_kernel_launches", "stk_pressure_vcycle_noalloc", "stk_remove_mean", "stk_set_graphs", "stk_graphs_in_use", "stk_widen", "stk_set_wait_budget", "stk_wait_status", "stk_solve_history", "stk_bounds_violations", "stk_bounds_selftest", "stk_gradient", "stk_backward_euler_rhs", "stk_subtract_boundary_terms", "stk_solve_batched", "stk_get_schedule", "stk_set_schedule", "stk_autotune"]
 
 
 def library():
@@ -381,6 +382,16 @@ def stk_bounds_selftest(stream=None):
 
 def stk_set_graphs(h, enable):
     return _check(h, _lib.stk_set_graphs(h, int(bool(enable))))
+
+
+def stk_widen(x, y, stream=None):
+    """y (float64) = x (float32), the library's exact widening."""
+    import torch
+    n = x.numel()
+    rc = _lib.stk_widen(_ptr(x, n, dtype=torch.float32), _ptr(y, n), n, _stream(stream))
+    if rc != STK_OK:
+        raise StokesError(rc, "stk_widen failed")
+    return rc
 
 
 def stk_graphs_in_use(h):

@@ -97,3 +97,24 @@ def test_zero_rhs_and_maxit(S):
     assert not info["converged"] and info["iterations"] == 3
     assert info["status"] == S.STK_ERR_NOT_CONVERGED
     sv.close()
+
+
+def test_widening_is_bitwise_the_conversion_instruction(S):
+    """stk_widen (integer construction of the binary64 encoding, used for the
+    FP32 preconditioner outputs of the flexible solve) equals the hardware
+    conversion bit for bit: random bit patterns plus zeros, subnormals, the
+    extreme normals, infinities and NaN."""
+    rng = np.random.default_rng(12)
+    bits = rng.integers(0, 2 ** 32, size=1 << 20, dtype=np.uint64).astype(np.uint32)
+    special = np.array([0x00000000, 0x80000000, 0x00000001, 0x807fffff, 0x00800000, 0x7f7fffff,
+                        0xff7fffff, 0x7f800000, 0xff800000, 0x7fc00000, 0x3f800000, 0xbf800001],
+                       dtype=np.uint32)
+    bits = np.concatenate([bits, special])
+    x = torch.from_numpy(bits.view(np.float32).copy()).to(DEV)
+    y = torch.empty(x.numel(), dtype=torch.float64, device=DEV)
+    S.stk_widen(x, y)
+    ref = x.double()
+    yb, rb = y.cpu().numpy().view(np.uint64), ref.cpu().numpy().view(np.uint64)
+    nan = np.isnan(ref.cpu().numpy())
+    assert np.array_equal(yb[~nan], rb[~nan])
+    assert np.isnan(y.cpu().numpy()[nan]).all()
