@@ -153,6 +153,9 @@ struct stk_handle {
         std::vector<long long> k_step;
     };
     std::map<std::tuple<int, int, int, int, int, int>, CycleGraph> cgraphs;
+    // graphs of single phases of a cycle (host-gated batches), keyed by
+    // (phase, precond, flexible, m, nu, ncoarse, cycles); kernels each
+    std::map<std::tuple<int, int, int, int, int, int, int>, std::pair<cudaGraphExec_t, long long>> pgraphs;
 
     GmState* gst = nullptr;        // device state of the GMRES least-squares problem
     GmState* gst_host = nullptr;   // pinned copy
@@ -720,7 +723,7 @@ void apply_precond(stk_handle* h, int which, const T* b, T* x, const MGParams& m
 }
 
 void clear_graphs(stk_handle* h) {
-    if (h->graphs.empty() && h->cgraphs.empty()) return;
+    if (h->graphs.empty() && h->cgraphs.empty() && h->pgraphs.empty()) return;
     cudaDeviceSynchronize();   // no launch of these graphs may still be in flight
     for (auto& kv : h->graphs) {
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
@@ -730,10 +733,13 @@ void clear_graphs(stk_handle* h) {
         }
     }
     h->graphs.clear();
-    // the GMRES cycle graphs contain preconditioner applications
+    // the GMRES cycle and phase graphs contain preconditioner applications
     for (auto& kv : h->cgraphs)
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     h->cgraphs.clear();
+    for (auto& kv : h->pgraphs)
+        if (kv.second.first) cudaGraphExecDestroy(kv.second.first);
+    h->pgraphs.clear();
 }
 
 // x = P^{-1} b through a CUDA graph captured on first use (one graph per
@@ -1046,6 +1052,53 @@ int build_cycle_graph(const CycleCtx& c, stk_handle::CycleGraph& out) {
     return rc;
 }
 
+// One phase of a host-gated cycle: 0 the stopping test, 1 the first basis
+// vector, 2 + j Arnoldi step j, m + 2 the update of x.
+int enq_phase(const CycleCtx& c, int ph, cudaStream_t s) {
+    if (ph == 0) {
+        enq_check(c, s, 0, 0);
+        return STK_OK;
+    }
+    if (ph == 1) return enq_pre(c, s, 0, 0, 0);
+    if (ph < c.m + 2) return enq_step(c, ph - 2, s, 0, 0);
+    enq_fin(c, s);
+    return STK_OK;
+}
+
+// Run phase ph on stream s: one launch of a graph of that phase (captured on
+// first use), or kernel by kernel when graphs are off or profiling is on.
+int run_phase(const CycleCtx& c, int ph, cudaStream_t s) {
+    stk_handle* h = c.h;
+    if (!h->use_graphs || h->prof) {
+        int rc = enq_phase(c, ph, s);
+        if (rc) return rc;
+        CKL();
+        return STK_OK;
+    }
+    auto key = std::make_tuple(ph, c.which, c.flex ? 1 : 0, c.m, c.mp.nu, c.mp.ncoarse,
+                               c.mp.cu * 1000 + c.mp.cp);
+    auto f = h->pgraphs.find(key);
+    if (f == h->pgraphs.end()) {
+        CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+        h->capturing = true;
+        h->cap_kernels = 0;
+        int rc = enq_phase(c, ph, h->cap);
+        h->capturing = false;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+        if (rc) return rc;
+        if (e != cudaSuccess) return fail(h, STK_ERR_CUDA, "phase capture: %s", cudaGetErrorString(e));
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(h, STK_ERR_CUDA, "phase graph instantiate: %s", cudaGetErrorString(e));
+        f = h->pgraphs.emplace(key, std::make_pair(ex, h->cap_kernels)).first;
+    }
+    CK(cudaGraphLaunch(f->second.first, s));
+    h->nkern += f->second.second;
+    return STK_OK;
+}
+
 // One GMRES instance advanced in lockstep with others (Sec. 3.2, Sec. 4).
 struct Inst {
     stk_handle* h = nullptr;
@@ -1199,7 +1252,8 @@ void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm, bool
         if (!eager.empty()) {   // the same phases, gated by the host
             for (Inst* it : eager) {
                 CycleCtx c{it->h, prm.precond, m, flex, mp};
-                enq_check(c, it->s, 0, 0);
+                int rc = run_phase(c, 0, it->s);
+                if (rc) { finish(it, rc); continue; }
                 read_header(it);
             }
             sync_all(eager);
@@ -1208,7 +1262,7 @@ void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm, bool
                 if (!it->done && it->h->gst_host->cond[GM_COND_PRE]) run.push_back(it);
             for (Inst* it : run) {
                 CycleCtx c{it->h, prm.precond, m, flex, mp};
-                int rc = enq_pre(c, it->s, 0, 0, 0);
+                int rc = run_phase(c, 1, it->s);
                 if (rc) { finish(it, rc); continue; }
                 read_header(it);
             }
@@ -1220,7 +1274,7 @@ void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm, bool
                 if (step.empty()) break;
                 for (Inst* it : step) {
                     CycleCtx c{it->h, prm.precond, m, flex, mp};
-                    int rc = enq_step(c, j, it->s, 0, 0);
+                    int rc = run_phase(c, 2 + j, it->s);
                     if (rc) { finish(it, rc); continue; }
                     read_header(it);
                 }
@@ -1229,7 +1283,8 @@ void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm, bool
             for (Inst* it : run) {
                 if (it->done || !it->h->gst_host->cond[GM_COND_FIN]) continue;
                 CycleCtx c{it->h, prm.precond, m, flex, mp};
-                enq_fin(c, it->s);
+                int rc = run_phase(c, m + 2, it->s);
+                if (rc) { finish(it, rc); continue; }
                 read_header(it);
             }
         }
