@@ -10,12 +10,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
-#include <atomic>
 #include <cmath>
-#include <condition_variable>
-#include <functional>
-#include <mutex>
-#include <thread>
 #include <cstdarg>
 #include <cstddef>
 #include <cstdio>
@@ -1104,77 +1099,6 @@ int run_phase(const CycleCtx& c, int ph, cudaStream_t s) {
     return STK_OK;
 }
 
-// A small pool of host threads that issue the launches of a large batch in
-// parallel (each issue is a graph launch and a copy of the instance's state
-// on its own stream; one host thread issuing them all in turn was the
-// batched solve's bottleneck).  run(n, f) calls f(0..n-1) on the pool and
-// the calling thread and returns when all calls have returned.
-class IssuePool {
-  public:
-    explicit IssuePool(int nthreads) {
-        for (int i = 0; i < nthreads; ++i) thr_.emplace_back([this] { work(); });
-    }
-    ~IssuePool() {
-        {
-            std::lock_guard<std::mutex> lk(mu_);
-            stop_ = true;
-        }
-        cv_work_.notify_all();
-        for (auto& t : thr_) t.join();
-    }
-    void run(int n, const std::function<void(int)>& f) {
-        {
-            std::lock_guard<std::mutex> lk(mu_);
-            job_ = &f;
-            n_ = n;
-            next_.store(0);
-            busy_ = (int)thr_.size();
-            ++gen_;
-        }
-        cv_work_.notify_all();
-        for (int i; (i = next_.fetch_add(1)) < n;) f(i);
-        std::unique_lock<std::mutex> lk(mu_);
-        cv_done_.wait(lk, [this] { return busy_ == 0; });
-        job_ = nullptr;
-    }
-
-  private:
-    void work() {
-        long long seen = 0;
-        for (;;) {
-            const std::function<void(int)>* f;
-            int n;
-            {
-                std::unique_lock<std::mutex> lk(mu_);
-                cv_work_.wait(lk, [&] { return stop_ || gen_ != seen; });
-                if (stop_) return;
-                seen = gen_;
-                f = job_;
-                n = n_;
-            }
-            for (int i; (i = next_.fetch_add(1)) < n;) (*f)(i);
-            std::lock_guard<std::mutex> lk(mu_);
-            if (--busy_ == 0) cv_done_.notify_all();
-        }
-    }
-    std::vector<std::thread> thr_;
-    std::mutex mu_;
-    std::condition_variable cv_work_, cv_done_;
-    const std::function<void(int)>* job_ = nullptr;
-    std::atomic<int> next_{0};
-    int n_ = 0, busy_ = 0;
-    long long gen_ = 0;
-    bool stop_ = false;
-};
-
-IssuePool& issue_pool() {
-    static IssuePool pool([] {
-        const unsigned hw = std::thread::hardware_concurrency();
-        return hw >= 8 ? 7 : (hw >= 2 ? (int)hw - 1 : 1);
-    }());
-    return pool;
-}
-
 // One GMRES instance advanced in lockstep with others (Sec. 3.2, Sec. 4).
 struct Inst {
     stk_handle* h = nullptr;
@@ -1326,44 +1250,43 @@ void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm, bool
             }
         }
         if (!eager.empty()) {   // the same phases, gated by the host
-            // issue phase ph of every instance in v (several host threads
-            // for a large batch: each issue is a graph launch and a copy)
-            auto issue = [&](std::vector<Inst*>& v, int ph) {
-                auto one = [&](int i) {
-                    Inst* it = v[i];
-                    if (it->done) return;
-                    cudaSetDevice(it->h->device);
-                    CycleCtx c{it->h, prm.precond, m, flex, mp};
-                    const int rc = run_phase(c, ph, it->s);
-                    if (rc) {
-                        finish(it, rc);
-                        return;
-                    }
-                    read_header(it);
-                };
-                if (v.size() >= 16) issue_pool().run((int)v.size(), one);
-                else
-                    for (int i = 0; i < (int)v.size(); ++i) one(i);
-            };
-            issue(eager, 0);
+            for (Inst* it : eager) {
+                CycleCtx c{it->h, prm.precond, m, flex, mp};
+                int rc = run_phase(c, 0, it->s);
+                if (rc) { finish(it, rc); continue; }
+                read_header(it);
+            }
             sync_all(eager);
             std::vector<Inst*> run;
             for (Inst* it : eager)
                 if (!it->done && it->h->gst_host->cond[GM_COND_PRE]) run.push_back(it);
-            issue(run, 1);
+            for (Inst* it : run) {
+                CycleCtx c{it->h, prm.precond, m, flex, mp};
+                int rc = run_phase(c, 1, it->s);
+                if (rc) { finish(it, rc); continue; }
+                read_header(it);
+            }
             sync_all(run);
             for (int j = 0; j < m; ++j) {
                 std::vector<Inst*> step;
                 for (Inst* it : run)
                     if (!it->done && it->h->gst_host->cond[GM_COND_STEP0 + j]) step.push_back(it);
                 if (step.empty()) break;
-                issue(step, 2 + j);
+                for (Inst* it : step) {
+                    CycleCtx c{it->h, prm.precond, m, flex, mp};
+                    int rc = run_phase(c, 2 + j, it->s);
+                    if (rc) { finish(it, rc); continue; }
+                    read_header(it);
+                }
                 sync_all(step);
             }
-            std::vector<Inst*> fin;
-            for (Inst* it : run)
-                if (!it->done && it->h->gst_host->cond[GM_COND_FIN]) fin.push_back(it);
-            issue(fin, m + 2);
+            for (Inst* it : run) {
+                if (it->done || !it->h->gst_host->cond[GM_COND_FIN]) continue;
+                CycleCtx c{it->h, prm.precond, m, flex, mp};
+                int rc = run_phase(c, m + 2, it->s);
+                if (rc) { finish(it, rc); continue; }
+                read_header(it);
+            }
         }
         sync_all(act);
         for (Inst* it : act)
