@@ -110,6 +110,40 @@ void stk_default_params(stk_solver_params* p);
  * axis (App. C).  Uses the current CUDA device.  *out is NULL on failure. */
 int stk_create(int dim, const int* n, double h, const int* bc, stk_handle** out);
 
+/* Stacked batch: `count` independent 2D systems on the same grid (n, h, bc
+ * as in stk_create, dim must be 2), each with its own coefficients and
+ * right-hand side, stored as instances along a third array axis: every face
+ * and cell array of the handle holds the count instances one after another
+ * (instance i of the a-face array at i * stk_face_length(h, a) / count, of
+ * a cell array at i * stk_cell_length(h) / count).  No stencil couples two
+ * instances, so each is the 2D system of Sec. 3.1 on its own: every kernel
+ * of a V-cycle, of the operator and of the preconditioner runs once over
+ * all instances, the reductions and the GMRES least-squares problems
+ * (Sec. 3.2) per instance, and an instance's results equal those of a
+ * handle made by stk_create for it alone (bitwise for the operator,
+ * V-cycles and preconditioners when the coarsest level sweeps, i.e.
+ * ncoarse != 8; the single handle applies a precomputed coarse-solve matrix
+ * for ncoarse = 8).  stk_solve on the handle solves every instance, one
+ * CUDA graph launch per GMRES cycle for all of them; an instance that has
+ * converged sits out the rest of the solve and its solution is final.  The
+ * solve's info summarises the instances (iterations, restarts, residuals
+ * and V-cycles: the largest; converged: all of them); stk_stack_info gives
+ * each.  x receives every instance's final iterate also when the solve
+ * returns STK_ERR_NONFINITE or STK_ERR_TIMEOUT for one of them (the others
+ * are unaffected).  1 <= count <= STK_MAX_STACK.  Not available on a stacked handle:
+ * stk_set_bulk_viscosity, stk_subtract_boundary_terms, stk_gradient and the
+ * persistent multi-block V-cycle (schedule grid_level). */
+#define STK_MAX_STACK 1024
+int stk_create_stacked(int dim, const int* n, double h, const int* bc, int count, stk_handle** out);
+/* Instances of a stacked handle (1 for a handle from stk_create). */
+int stk_stack_count(const stk_handle* h);
+/* The last solve's record of one instance (0 <= instance < count):
+ * converged, iterations, restarts, residuals, V-cycles and status of that
+ * instance, solve_ms of the whole solve.  STK_ERR_STATE before any solve. */
+int stk_stack_info(const stk_handle* h, int instance, stk_solve_info* info);
+/* stk_solve_history for one instance. */
+int stk_stack_history(const stk_handle* h, int instance, int kind, double* out, int cap);
+
 /* Free the handle and every device allocation it owns. */
 int stk_destroy(stk_handle* h);
 
@@ -266,7 +300,8 @@ int stk_graphs_in_use(const stk_handle* h);
  * estimate divided by ||b|| after every Arnoldi step (the preconditioned
  * residual of the left form, the true residual of the flexible form; at
  * most 2048 kept).  Copies min(cap, count) values to the host array out (out
- * may be NULL) and returns the count, or STK_ERR_ARG. */
+ * may be NULL) and returns the count, or STK_ERR_ARG.  A stacked handle:
+ * instance 0 (stk_stack_history gives the others). */
 int stk_solve_history(const stk_handle* h, int kind, double* out, int cap);
 
 /* y_p = x_p - mean(x_p): projection of a cell array onto mean-zero vectors,
@@ -280,7 +315,8 @@ int stk_remove_mean(stk_handle* h, const double* x_p, double* y_p, void* stream)
 /* Batched solve: count independent systems, each on its own handle (any
  * grid size, boundary conditions and coefficients), solved together with
  * the same parameters.  The GMRES iterations of all instances advance in
- * lockstep (one host synchronisation per Arnoldi step for the whole batch)
+ * lockstep (one host synchronisation per GMRES phase -- stopping test,
+ * first basis vector, each Arnoldi step, update -- for the whole batch)
  * and each instance's kernels and preconditioner graphs run on its handle's
  * own stream, forked from and joined back into `stream`, so the instances
  * share the GPU.  io[i] holds instance i's right-hand side and its initial

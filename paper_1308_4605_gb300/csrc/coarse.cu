@@ -39,9 +39,19 @@ struct SmemLevels {
 // multi-block kernel); each wait is bounded by a clock64() budget, after
 // which the barrier writes STK_ERR_TIMEOUT to *status and every block
 // returns at its next barrier, so a stalled launch ends instead of hanging.
+// first() / end(): the points [first, end) of an array of `total` points
+// that this thread visits (stride nth()).  A stacked batch (nsl instances
+// along the slowest axis of every array) is run by one block per instance,
+// each on its own contiguous share; otherwise the block takes every point.
 struct BlockSync {
     __device__ __forceinline__ int tid() const { return threadIdx.x; }
     __device__ __forceinline__ int nth() const { return CT; }
+    __device__ __forceinline__ int first(int total, int nsl) const {
+        return nsl > 1 ? int(blockIdx.x) * (total / nsl) + int(threadIdx.x) : int(threadIdx.x);
+    }
+    __device__ __forceinline__ int end(int total, int nsl) const {
+        return nsl > 1 ? (int(blockIdx.x) + 1) * (total / nsl) : total;
+    }
     __device__ __forceinline__ bool sync() const {
         __syncthreads();
         return true;
@@ -54,6 +64,9 @@ struct GridSync {
     int* status;          // 0, or STK_ERR_TIMEOUT once a wait ran out
     __device__ __forceinline__ int tid() const { return blockIdx.x * CT + threadIdx.x; }
     __device__ __forceinline__ int nth() const { return gridDim.x * CT; }
+    // never used on a stacked batch: every block shares every point
+    __device__ __forceinline__ int first(int, int) const { return tid(); }
+    __device__ __forceinline__ int end(int total, int) const { return total; }
     // Sense-counting grid barrier: the block's writes are ordered before its
     // arrival (bar.sync, then a device-scope fence by thread 0), the last
     // block to arrive resets the count and advances the generation, the
@@ -101,7 +114,8 @@ __device__ bool c_vel_sweeps(const SY& S, const Geom& g, const Coef<T>& C, int n
         for (int a = 0; a < DIM; ++a)
             for (int par = 0; par < 2; ++par) {
                 const int nt = ((g.fe[a][0] + 1) >> 1) * g.fe[a][1] * g.fe[a][2];
-                for (int t = S.tid(); t < nt; t += S.nth()) {
+                const int te = S.end(nt, g.nsl);
+                for (int t = S.first(nt, g.nsl); t < te; t += S.nth()) {
                     int q[3];
                     if (!decode_face_colour(g, a, par, t, q) || wall_face(g, a, q)) continue;
                     if (a == 0) vel_gs_point<DIM, 0, T, BULK>(g, C, q, phi, rhs);
@@ -117,9 +131,10 @@ template <int DIM, typename T, typename SY>
 __device__ bool c_cell_sweeps(const SY& S, const Geom& g, const Coef<T>& C, int nsweep, T* phi,
                               const T* rhs) {
     const int nt = (g.n[0] >> 1) * g.n[1] * g.n[2];
+    const int te = S.end(nt, g.nsl);
     for (int it = 0; it < nsweep; ++it)
         for (int par = 0; par < 2; ++par) {
-            for (int t = S.tid(); t < nt; t += S.nth()) {
+            for (int t = S.first(nt, g.nsl); t < te; t += S.nth()) {
                 int q[3];
                 decode_cell_colour(g, par, t, q);
                 cell_gs_point<DIM, T>(g, C, q, phi, rhs);
@@ -185,7 +200,9 @@ __device__ bool vcycle_vel_body(const SY& S, Geom* gsh, const CLevel<T>* __restr
         const Coef<T> C = Ls[l].C;
         T* phi = V.phi(l);
         const T* rhs = V.rhs(l);
-        for (int t = S.tid(); t < g.nvel; t += S.nth()) phi[t] = T(0);
+        for (int a = 0; a < DIM; ++a)
+            for (int t = S.first(g.fsize[a], g.nsl); t < S.end(g.fsize[a], g.nsl); t += S.nth())
+                phi[g.foff[a] + t] = T(0);
         if (!S.sync()) return false;
         if (l + 1 == nlev) {   // coarsest level: the coarse solve, then up
             if (Ls[l].smat_u && Ls[l].smat_nc == ncoarse) smat_apply<T>(S, Ls[l].smat_u, g.nvel, rhs, phi);
@@ -195,31 +212,31 @@ __device__ bool vcycle_vel_body(const SY& S, Geom* gsh, const CLevel<T>* __restr
         }
         if (!c_vel_sweeps<DIM, T, BULK>(S, g, C, nu, phi, rhs)) return false;
         T* res = V.res(l);
-        for (int t = S.tid(); t < g.nvel; t += S.nth()) {
-            int a = 0;
-            while (a + 1 < DIM && t >= g.foff[a + 1]) ++a;
-            int q[3];
-            decode_face(g, a, t - g.foff[a], q);
-            // the black faces of the last component were just solved: zero residual
-            const bool solved = nu > 0 && a == DIM - 1 && ((q[0] + q[1] + q[2]) & 1);
-            res[t] = (wall_face(g, a, q) || solved) ? T(0) : vel_res_point<DIM, T, BULK>(a, g, C, q, phi, rhs);
-        }
+        for (int a = 0; a < DIM; ++a)
+            for (int t = S.first(g.fsize[a], g.nsl); t < S.end(g.fsize[a], g.nsl); t += S.nth()) {
+                int q[3];
+                decode_face(g, a, t, q);
+                // the black faces of the last component were just solved: zero residual
+                const bool solved = nu > 0 && a == DIM - 1 && (csum<DIM>(q) & 1);
+                res[g.foff[a] + t] = (wall_face(g, a, q) || solved)
+                                         ? T(0)
+                                         : vel_res_point<DIM, T, BULK>(a, g, C, q, phi, rhs);
+            }
         if (!S.sync()) return false;
         const Geom& gc = gsh[1];
         T* rc = V.rhs(l + 1);
-        for (int t = S.tid(); t < gc.nvel; t += S.nth()) {
-            int a = 0;
-            while (a + 1 < DIM && t >= gc.foff[a + 1]) ++a;
-            int Q[3];
-            decode_face(gc, a, t - gc.foff[a], Q);
-            T v = T(0);
-            if (!wall_face(gc, a, Q)) {
-                if (a == 0) v = vel_restrict_point<DIM, 0, T>(g, Q, res);
-                else if (a == 1) v = vel_restrict_point<DIM, 1, T>(g, Q, res);
-                else v = vel_restrict_point<DIM, DIM == 3 ? 2 : 1, T>(g, Q, res);
+        for (int a = 0; a < DIM; ++a)
+            for (int t = S.first(gc.fsize[a], gc.nsl); t < S.end(gc.fsize[a], gc.nsl); t += S.nth()) {
+                int Q[3];
+                decode_face(gc, a, t, Q);
+                T v = T(0);
+                if (!wall_face(gc, a, Q)) {
+                    if (a == 0) v = vel_restrict_point<DIM, 0, T>(g, Q, res);
+                    else if (a == 1) v = vel_restrict_point<DIM, 1, T>(g, Q, res);
+                    else v = vel_restrict_point<DIM, DIM == 3 ? 2 : 1, T>(g, Q, res);
+                }
+                rc[gc.foff[a] + t] = v;
             }
-            rc[t] = v;
-        }
         if (!S.sync()) return false;
     }
     if (ltop < nlev) {   // the coarse levels, one block
@@ -242,18 +259,17 @@ __device__ bool vcycle_vel_body(const SY& S, Geom* gsh, const CLevel<T>* __restr
         T* phi = V.phi(l);
         const T* rhs = V.rhs(l);
         const T* pc = V.phi(l + 1);
-        for (int t = S.tid(); t < g.nvel; t += S.nth()) {
-            int a = 0;
-            while (a + 1 < DIM && t >= g.foff[a + 1]) ++a;
-            int q[3];
-            decode_face(g, a, t - g.foff[a], q);
-            if (wall_face(g, a, q)) continue;
-            T v;
-            if (a == 0) v = vel_prolong_point<DIM, 0, T>(gc, q, pc);
-            else if (a == 1) v = vel_prolong_point<DIM, 1, T>(gc, q, pc);
-            else v = vel_prolong_point<DIM, DIM == 3 ? 2 : 1, T>(gc, q, pc);
-            phi[t] += v;
-        }
+        for (int a = 0; a < DIM; ++a)
+            for (int t = S.first(g.fsize[a], g.nsl); t < S.end(g.fsize[a], g.nsl); t += S.nth()) {
+                int q[3];
+                decode_face(g, a, t, q);
+                if (wall_face(g, a, q)) continue;
+                T v;
+                if (a == 0) v = vel_prolong_point<DIM, 0, T>(gc, q, pc);
+                else if (a == 1) v = vel_prolong_point<DIM, 1, T>(gc, q, pc);
+                else v = vel_prolong_point<DIM, DIM == 3 ? 2 : 1, T>(gc, q, pc);
+                phi[g.foff[a] + t] += v;
+            }
         if (!S.sync()) return false;
         if (!c_vel_sweeps<DIM, T, BULK>(S, g, C, nu, phi, rhs)) return false;
     }
@@ -272,7 +288,7 @@ __device__ bool vcycle_cell_body(const SY& S, Geom* gsh, const CLevel<T>* __rest
         const Coef<T> C = Ls[l].C;
         T* phi = V.phi(l);
         const T* rhs = V.rhs(l);
-        for (int t = S.tid(); t < g.ncell; t += S.nth()) phi[t] = T(0);
+        for (int t = S.first(g.ncell, g.nsl); t < S.end(g.ncell, g.nsl); t += S.nth()) phi[t] = T(0);
         if (!S.sync()) return false;
         if (l + 1 == nlev) {
             if (Ls[l].smat_p && Ls[l].smat_nc == ncoarse) smat_apply<T>(S, Ls[l].smat_p, g.ncell, rhs, phi);
@@ -282,15 +298,15 @@ __device__ bool vcycle_cell_body(const SY& S, Geom* gsh, const CLevel<T>* __rest
         }
         if (!c_cell_sweeps<DIM, T>(S, g, C, nu, phi, rhs)) return false;
         T* res = V.res(l);
-        for (int t = S.tid(); t < g.ncell; t += S.nth()) {
+        for (int t = S.first(g.ncell, g.nsl); t < S.end(g.ncell, g.nsl); t += S.nth()) {
             int q[3];
             decode_cell(g, t, q);
-            res[t] = (nu > 0 && ((q[0] + q[1] + q[2]) & 1)) ? T(0) : cell_res_point<DIM, T>(g, C, q, phi, rhs);
+            res[t] = (nu > 0 && (csum<DIM>(q) & 1)) ? T(0) : cell_res_point<DIM, T>(g, C, q, phi, rhs);
         }
         if (!S.sync()) return false;
         const Geom& gc = gsh[1];
         T* rc = V.rhs(l + 1);
-        for (int t = S.tid(); t < gc.ncell; t += S.nth()) {
+        for (int t = S.first(gc.ncell, gc.nsl); t < S.end(gc.ncell, gc.nsl); t += S.nth()) {
             int Q[3];
             decode_cell(gc, t, Q);
             rc[t] = cell_restrict_point<DIM, T>(g, Q, res);
@@ -316,10 +332,10 @@ __device__ bool vcycle_cell_body(const SY& S, Geom* gsh, const CLevel<T>* __rest
         T* phi = V.phi(l);
         const T* rhs = V.rhs(l);
         const T* pc = V.phi(l + 1);
-        for (int t = S.tid(); t < g.ncell; t += S.nth()) {
+        for (int t = S.first(g.ncell, g.nsl); t < S.end(g.ncell, g.nsl); t += S.nth()) {
             int q[3];
             decode_cell(g, t, q);
-            int Q[3] = {q[0] >> 1, q[1] >> 1, DIM == 3 ? q[2] >> 1 : 0};
+            int Q[3] = {q[0] >> 1, q[1] >> 1, DIM == 3 ? q[2] >> 1 : q[2]};
             phi[t] += pc[cidx(gc, Q)];
         }
         if (!S.sync()) return false;
@@ -490,10 +506,10 @@ void set_smem_attr(K kern) {
 }
 
 template <typename T>
-void launch_coarse_vcycle_vel(int dim, const CLevel<T>* L, int nlev, const T* rhs, T* phi, int nu,
-                              int ncoarse, bool bulk, size_t smem, cudaStream_t s) {
+void launch_coarse_vcycle_vel(int dim, int nsl, const CLevel<T>* L, int nlev, const T* rhs, T* phi,
+                              int nu, int ncoarse, bool bulk, size_t smem, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(1);
+    cfg.gridDim = dim3(nsl > 1 ? nsl : 1);   // a stacked batch: one block per instance
     cfg.blockDim = dim3(CT);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
@@ -502,7 +518,7 @@ void launch_coarse_vcycle_vel(int dim, const CLevel<T>* L, int nlev, const T* rh
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const bool sm = smem > 0 && smem <= COARSE_SMEM_MAX;
+    const bool sm = nsl <= 1 && smem > 0 && smem <= COARSE_SMEM_MAX;
     if (!sm) cfg.dynamicSmemBytes = 0;
 #define STK_CV(D, B) (sm ? k_coarse_vel<D, T, B, true> : k_coarse_vel<D, T, B, false>)
     auto kern = dim == 2 ? (bulk ? STK_CV(2, true) : STK_CV(2, false))
@@ -512,10 +528,10 @@ void launch_coarse_vcycle_vel(int dim, const CLevel<T>* L, int nlev, const T* rh
 }
 
 template <typename T>
-void launch_coarse_vcycle_cell(int dim, const CLevel<T>* L, int nlev, const T* rhs, T* phi, int nu,
-                               int ncoarse, size_t smem, cudaStream_t s) {
+void launch_coarse_vcycle_cell(int dim, int nsl, const CLevel<T>* L, int nlev, const T* rhs, T* phi,
+                               int nu, int ncoarse, size_t smem, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(1);
+    cfg.gridDim = dim3(nsl > 1 ? nsl : 1);
     cfg.blockDim = dim3(CT);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -523,7 +539,7 @@ void launch_coarse_vcycle_cell(int dim, const CLevel<T>* L, int nlev, const T* r
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const bool sm = smem > 0 && smem <= COARSE_SMEM_MAX;
+    const bool sm = nsl <= 1 && smem > 0 && smem <= COARSE_SMEM_MAX;
     cfg.dynamicSmemBytes = sm ? smem : 0;
     auto kern = dim == 2 ? (sm ? k_coarse_cell<2, T, true> : k_coarse_cell<2, T, false>)
                          : (sm ? k_coarse_cell<3, T, true> : k_coarse_cell<3, T, false>);
@@ -611,13 +627,13 @@ void prepare_coarse_kernels() {
     set_smem_attr(k_coarse_cell<3, float, true>);
 }
 
-template void launch_coarse_vcycle_vel<double>(int, const CLevel<double>*, int, const double*,
+template void launch_coarse_vcycle_vel<double>(int, int, const CLevel<double>*, int, const double*,
                                                double*, int, int, bool, size_t, cudaStream_t);
-template void launch_coarse_vcycle_vel<float>(int, const CLevel<float>*, int, const float*, float*,
+template void launch_coarse_vcycle_vel<float>(int, int, const CLevel<float>*, int, const float*, float*,
                                               int, int, bool, size_t, cudaStream_t);
-template void launch_coarse_vcycle_cell<double>(int, const CLevel<double>*, int, const double*,
+template void launch_coarse_vcycle_cell<double>(int, int, const CLevel<double>*, int, const double*,
                                                 double*, int, int, size_t, cudaStream_t);
-template void launch_coarse_vcycle_cell<float>(int, const CLevel<float>*, int, const float*,
+template void launch_coarse_vcycle_cell<float>(int, int, const CLevel<float>*, int, const float*,
                                                float*, int, int, size_t, cudaStream_t);
 
 STK_OOB_READER(coarse)

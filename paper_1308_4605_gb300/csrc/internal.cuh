@@ -38,7 +38,10 @@ __host__ __device__ __forceinline__ int fdiv(int n, const FDiv& f) {
 
 struct Geom {
     int dim;
-    int n[3];        // cells per axis (n[2] = 1 in 2D)
+    int n[3];        // cells per axis (n[2] = 1 in 2D, or the instance count
+                     // of a stacked 2D batch: instances along the third
+                     // array axis, never coupled by a stencil)
+    int nsl;         // instances stacked along the third axis (1 otherwise)
     int per[3];      // 1 if the axis is periodic
     int bclo[3];     // boundary code of the low side of each axis
     int bchi[3];
@@ -54,6 +57,16 @@ struct Geom {
     // fast divisors: face extents fe[a][0], fe[a][1]; the colour row length
     // (fe[a][0]+1)/2; cell extents n[0], n[1]; the cell colour row n[0]/2
     FDiv fd_e0[3], fd_e1[3], fd_h0[3], fd_n0, fd_n1, fd_nh0;
+};
+
+// A packed Stokes vector of a stacked 2D batch: segment k (x faces, y faces,
+// cells) holds the instances' values one after another, len[k] values each,
+// starting at off[k]; nl = len[0] + len[1] + len[2] values per instance.
+// Every length is even (power-of-two grids).
+struct SliceMap {
+    int len[3];
+    int off[3];
+    int nl;
 };
 
 // fill the derived fields of g (call after n, per, fe are set)
@@ -276,12 +289,14 @@ struct CLevel {
 // only 512 (8^3, 16x32)
 constexpr int COARSE_MAX_CELLS_F32 = 4096;
 constexpr int COARSE_MAX_CELLS_F64 = 512;
+// nsl > 1: a stacked batch, one block per instance (these thresholds then
+// apply to the cells of one instance)
 template <typename T>
-void launch_coarse_vcycle_vel(int dim, const CLevel<T>* L, int nlev, const T* rhs, T* phi, int nu,
-                              int ncoarse, bool bulk, size_t smem, cudaStream_t s);
+void launch_coarse_vcycle_vel(int dim, int nsl, const CLevel<T>* L, int nlev, const T* rhs, T* phi,
+                              int nu, int ncoarse, bool bulk, size_t smem, cudaStream_t s);
 template <typename T>
-void launch_coarse_vcycle_cell(int dim, const CLevel<T>* L, int nlev, const T* rhs, T* phi, int nu,
-                               int ncoarse, size_t smem, cudaStream_t s);
+void launch_coarse_vcycle_cell(int dim, int nsl, const CLevel<T>* L, int nlev, const T* rhs, T* phi,
+                               int nu, int ncoarse, size_t smem, cudaStream_t s);
 // The same V-cycle from the level L[0] down as one persistent cooperative
 // launch (coarse.cu): levels 0..lblock-1 as grid-wide stages separated by
 // grid barriers (every block resident: one block of 1024 threads per SM at
@@ -366,19 +381,23 @@ struct GmState {
 };
 // solve start (*bn2 = ||b||^2), cycle start (*rn2 = ||b - M x||^2), first
 // basis vector (*vn2 = ||P^{-1} r||^2 for the left form), Arnoldi step j
-// (hcol[0..j] the projections, *n2 = ||w||^2 after them), cycle end.  With
-// use != 0 the decision is also written to the graph's conditional handle.
-void launch_gm_begin(GmState* st, const double* bn2, double rtol, int maxit, int m, int flex,
+// (hcol[0..j] the projections, *n2 = ||w||^2 after them), cycle end.  st
+// holds nsl records (a stacked batch: one per instance), instance y's
+// scalars at y * dstride; gc[GM_NCOND] receives the OR of the instances'
+// decisions.  With use != 0 that OR is also written to the graph's
+// conditional handle.
+void launch_gm_begin(GmState* st, int nsl, unsigned* gc, const double* bn2, int dstride, double rtol,
+                     int maxit, int m, int flex, cudaStream_t s);
+void launch_gm_check(GmState* st, int nsl, unsigned* gc, const double* rn2, int dstride,
+                     cudaGraphConditionalHandle hpre, int use, cudaStream_t s);
+// graph only: open the cycle's stopping test while an instance is running
+void launch_gm_gate(GmState* st, int nsl, unsigned* gc, cudaGraphConditionalHandle hchk, cudaStream_t s);
+void launch_gm_start(GmState* st, int nsl, unsigned* gc, const double* vn2, int dstride,
+                     cudaGraphConditionalHandle h0, int use0, cudaGraphConditionalHandle hfin, int usefin,
                      cudaStream_t s);
-void launch_gm_check(GmState* st, const double* rn2, cudaGraphConditionalHandle hpre, int use,
-                     cudaStream_t s);
-// graph only: open the cycle's stopping test while the solve is running
-void launch_gm_gate(GmState* st, cudaGraphConditionalHandle hchk, cudaStream_t s);
-void launch_gm_start(GmState* st, const double* vn2, cudaGraphConditionalHandle h0, int use0,
-                     cudaGraphConditionalHandle hfin, int usefin, cudaStream_t s);
-void launch_gm_step(GmState* st, int j, const double* hcol, const double* n2,
-                    cudaGraphConditionalHandle hn, int use, cudaStream_t s);
-void launch_gm_finish(GmState* st, cudaStream_t s);
+void launch_gm_step(GmState* st, int nsl, unsigned* gc, int j, const double* hcol, const double* n2,
+                    int dstride, cudaGraphConditionalHandle hn, int use, cudaStream_t s);
+void launch_gm_finish(GmState* st, int nsl, cudaStream_t s);
 
 // reductions with a fixed block count: deterministic results
 constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
@@ -394,6 +413,16 @@ template <typename T>  // x -= (*sum) / n    (sum[1] receives the mean)
 void launch_sub_mean(int n, T* x, double* sum, cudaStream_t s);
 template <typename T>  // out = in - (*sum)/n  (sum[1] receives the mean)
 void launch_copy_sub_mean(int n, const T* in, T* out, double* sum, cudaStream_t s);
+// Stacked batches: nsl instances of n values one after another.
+// out[y * ostride] = sum of instance y, bitwise the value launch_sum gives
+// for that instance alone (scratch >= nsl * RED_BLOCKS doubles)
+template <typename T>
+void launch_sum_sl(int n, int nsl, const T* x, double* scratch, double* out, int ostride,
+                   cudaStream_t s);
+// out = in - sum[y * stride] / n per instance y (sum[y * stride + 1]
+// receives the mean; in == out allowed)
+template <typename T>
+void launch_sub_mean_sl(int n, int nsl, const T* in, T* out, double* sum, int stride, cudaStream_t s);
 // h[i] = <w, V_i> for i <= j and h[j+1] = <w, w>;  V = array of j+1 device pointers
 void launch_multidot(int n, int j, const double* const* V, const double* w, double* scratch,
                      double* h, cudaStream_t s);
@@ -410,6 +439,23 @@ void launch_combine_dev(int n, int m, const TV* const* V, const double* y, const
                         cudaStream_t s);
 // x *= *a (a device scalar)
 void launch_scale_dev(int n, double* x, const double* a, cudaStream_t s);
+// Stacked batches (krylov.cu): the calls above on every instance of the
+// batch (nsl instances, map m), instance y's results at stride hstride /
+// ostride (y * stride + k), bitwise the ones it gets alone.
+void launch_multidot_sl(const SliceMap& m, int nsl, int j, const double* const* V, const double* w,
+                        double* scratch, double* h, int hstride, cudaStream_t s);
+void launch_mgs_step_sl(const SliceMap& m, int nsl, const double* vk, const double* u, const double* h,
+                        int hstride, int k, double* w, double* scratch, double* out, int ostride,
+                        cudaStream_t s);
+// x += sum_i st[y].y[i] V_i (i < st[y].k) for every instance y
+template <typename TV>
+void launch_combine_dev_sl(const SliceMap& m, int nsl, int mmax, const TV* const* V, const GmState* st,
+                           double* x, cudaStream_t s);
+// x *= st[y].inv_scale where Arnoldi step j of instance y is open, else 0
+void launch_scale_dev_sl(const SliceMap& m, int nsl, double* x, const GmState* st, int j, cudaStream_t s);
+// out[y * ostride] = sum of instance y of an FP32 vector of nsl x n values
+void launch_sum_f32x4_sl(int n, int nsl, const float* x, double* scratch, double* out, int ostride,
+                         cudaStream_t s);
 // x *= 1 / sqrt(*nrm2)
 void launch_scale_inv_sqrt(int n, double* x, const double* nrm2, cudaStream_t s);
 void launch_scale(int n, double* x, double a, cudaStream_t s);

@@ -140,7 +140,7 @@ __global__ void k_coarsen_faces(Geom gf, Geom gc, const double* __restrict__ af,
     for (int b = 0; b < gc.dim; ++b)
         if (b != a) tb[nt++] = b;
     for (int m = 0; m < (1 << nt); ++m) {
-        int q[3] = {2 * Q[0], 2 * Q[1], gc.dim == 3 ? 2 * Q[2] : 0};
+        int q[3] = {2 * Q[0], 2 * Q[1], gc.dim == 3 ? 2 * Q[2] : Q[2]};
         for (int k = 0; k < nt; ++k) q[tb[k]] += (m >> k) & 1;
         int f = fidx(gf, a, q);
         sa += af[f];
@@ -162,7 +162,7 @@ __global__ void k_coarsen_cells(Geom gf, Geom gc, const double* __restrict__ mf,
     for (int dz = 0; dz < nz; ++dz)
         for (int dy = 0; dy < 2; ++dy)
             for (int dx = 0; dx < 2; ++dx) {
-                int q[3] = {2 * Q[0] + dx, 2 * Q[1] + dy, (gc.dim == 3 ? 2 * Q[2] : 0) + dz};
+                int q[3] = {2 * Q[0] + dx, 2 * Q[1] + dy, (gc.dim == 3 ? 2 * Q[2] : Q[2]) + dz};
                 s += mf[cidx(gf, q)];
             }
     mc[t] = s / (gc.dim == 3 ? 8.0 : 4.0);
@@ -178,7 +178,7 @@ __global__ void k_coarsen_edges(Geom gf, Geom gc, int p, int c, const double* __
     int Q[3];
     decode(t, gc.ee[p], Q);
     if (gc.dim == 2) {
-        int q[3] = {2 * Q[0], 2 * Q[1], 0};
+        int q[3] = {2 * Q[0], 2 * Q[1], Q[2]};
         ec[t] = ef[eidx(gf, p, q)];
     } else {
         int q[3] = {2 * Q[0], 2 * Q[1], 2 * Q[2]};
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(TPB) k_vel_residual(Geom g, Coef<T> C, Segs sg
     int q[3];
     decode_face(g, s, t, q);
     const int f = g.foff[s] + t;
-    if (wall_face(g, s, q) || (s == zl && ((q[0] + q[1] + q[2]) & 1))) {
+    if (wall_face(g, s, q) || (s == zl && (csum<DIM>(q) & 1))) {
         res[f] = T(0);
         return;
     }
@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(TPB) k_cell_residual(Geom g, Coef<T> C, const 
     if (t >= g.ncell) return;
     int q[3];
     decode_cell(g, t, q);
-    res[t] = (zb && ((q[0] + q[1] + q[2]) & 1)) ? T(0) : cell_res_point<DIM, T>(g, C, q, phi, rhs);
+    res[t] = (zb && (csum<DIM>(q) & 1)) ? T(0) : cell_res_point<DIM, T>(g, C, q, phi, rhs);
 }
 
 template <int DIM, typename T>
@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(TPB) k_cell_prolong_add(Geom gc, Geom gf, cons
     if (t >= gf.ncell) return;
     int q[3];
     decode_cell(gf, t, q);
-    int Q[3] = {q[0] >> 1, q[1] >> 1, DIM == 3 ? q[2] >> 1 : 0};
+    int Q[3] = {q[0] >> 1, q[1] >> 1, DIM == 3 ? q[2] >> 1 : q[2]};
     pf[t] += pc[cidx(gc, Q)];
 }
 
@@ -641,6 +641,51 @@ __global__ void k_copy_sub_mean(int n, const T* __restrict__ in, T* out,
     const T m = T(sum[1]);
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) out[t] = in[t] - m;
+}
+
+// ----------------------------------------------------------- stacked batches
+// nsl instances of n values each, one after another (a cell vector of a
+// stacked batch).  The sum of each instance uses the partition and the
+// order of k_sum_partials / k_final above, so it is bitwise the sum the
+// instance gets alone; only the blocks that hold values are launched (the
+// others' partials are exact zeros).  Grid (nbu, nsl), blockIdx.y the instance.
+template <typename T>
+__global__ void k_sum_partials_sl(int n, const T* __restrict__ x, double* part, int nbu) {
+    pdl_entry();
+    __shared__ double sh[32];
+    const T* xs = x + (size_t)blockIdx.y * n;
+    double s = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += RED_BLOCKS * blockDim.x)
+        s += double(xs[i]);
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.y * nbu + blockIdx.x] = s;
+}
+
+// out[y * ostride] = the sum of instance y's nbu partials (one block each)
+__global__ void k_final_sl(int nbu, const double* __restrict__ part, double* out, int ostride) {
+    pdl_entry();
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nbu; b += blockDim.x) s += part[blockIdx.x * nbu + b];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) out[(size_t)blockIdx.x * ostride] = s;
+}
+
+// sum[y * stride + 1] = sum[y * stride] / n for every instance y
+__global__ void k_mean_sl(int n, int nsl, double* sum, int stride) {
+    pdl_entry();
+    const int y = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y < nsl) sum[(size_t)y * stride + 1] = sum[(size_t)y * stride] / n;
+}
+
+// out = in - mean of the instance (in place when in == out); grid (.., nsl)
+template <typename T>
+__global__ void k_sub_mean_sl(int n, const T* in, T* out, const double* __restrict__ sum, int stride) {
+    pdl_entry();
+    const T m = T(sum[(size_t)blockIdx.y * stride + 1]);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t i = (size_t)blockIdx.y * n + t;
+    if (t < n) out[i] = in[i] - m;
 }
 
 template <typename T>
@@ -918,6 +963,21 @@ void launch_copy_sub_mean(int n, const T* in, T* out, double* sum, cudaStream_t 
 }
 
 template <typename T>
+void launch_sum_sl(int n, int nsl, const T* x, double* scratch, double* out, int ostride,
+                   cudaStream_t s) {
+    int nbu = (n + RED_THREADS - 1) / RED_THREADS;
+    nbu = nbu < 1 ? 1 : (nbu > RED_BLOCKS ? RED_BLOCKS : nbu);
+    launch_pdl(k_sum_partials_sl<T>, dim3(nbu, nsl), dim3(RED_THREADS), s, n, x, scratch, nbu);
+    launch_pdl(k_final_sl, dim3(nsl), dim3(RED_THREADS), s, nbu, scratch, out, ostride);
+}
+
+template <typename T>
+void launch_sub_mean_sl(int n, int nsl, const T* in, T* out, double* sum, int stride, cudaStream_t s) {
+    launch_pdl(k_mean_sl, dim3((nsl + 31) / 32), dim3(32), s, n, nsl, sum, stride);
+    launch_pdl(k_sub_mean_sl<T>, dim3(nblk(n), nsl), dim3(TPB), s, n, in, out, sum, stride);
+}
+
+template <typename T>
 void launch_zero(int n, T* x, cudaStream_t s) {
     const int nb = nblk(n) < 1216 ? nblk(n) : 1216;
     launch_pdl(k_zero<T>, dim3(nb > 0 ? nb : 1), dim3(TPB), s, n, x);
@@ -979,6 +1039,8 @@ void launch_check_fields(int n, const double* rho, const double* mu, double* scr
                                           const T*, T*,                                            \
                                           cudaStream_t);                                           \
     template void launch_sum<T>(int, const T*, double*, double*, cudaStream_t);                  \
+    template void launch_sum_sl<T>(int, int, const T*, double*, double*, int, cudaStream_t);     \
+    template void launch_sub_mean_sl<T>(int, int, const T*, T*, double*, int, cudaStream_t);     \
     template void launch_sub_mean<T>(int, T*, double*, cudaStream_t);                            \
     template void launch_copy_sub_mean<T>(int, const T*, T*, double*, cudaStream_t);             \
     template void launch_axpy<T>(int, T, const T*, T*, cudaStream_t);                            \

@@ -29,9 +29,9 @@ __device__ __forceinline__ double wsum(double v) {
 }
 
 // Reduce NV per-thread values over the block; value i of block b goes to
-// part[i * KRY_BLOCKS + b].
+// part[i * stride + b].
 template <int NV>
-__device__ __forceinline__ void block_sums(const double (&v)[NV], double* part) {
+__device__ __forceinline__ void block_sums(const double (&v)[NV], double* part, int stride = KRY_BLOCKS) {
     __shared__ double sh[NV][KT / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -44,7 +44,7 @@ __device__ __forceinline__ void block_sums(const double (&v)[NV], double* part) 
         double s = 0.0;
 #pragma unroll
         for (int k = 0; k < KT / 32; ++k) s += sh[threadIdx.x][k];
-        part[threadIdx.x * KRY_BLOCKS + blockIdx.x] = s;
+        part[threadIdx.x * stride + blockIdx.x] = s;
     }
 }
 
@@ -202,6 +202,167 @@ __global__ void __launch_bounds__(KT) k_scal(int n, double* __restrict__ x, doub
     for (int t = blockIdx.x * KT + threadIdx.x; t < n; t += KRY_BLOCKS * KT) x[t] *= s;
 }
 
+// ------------------------------------------------------------ stacked batches
+// The kernels above on every instance of a stacked batch at once (grid
+// (nbu, nsl), blockIdx.y the instance).  Instance y's values are visited in
+// the order of its own packed vector (sl_pair), with the partition over
+// threads and the summation order of the single-instance kernels, so its
+// projections, norms and updates are bitwise the ones it gets alone.  Only
+// the blocks that hold values are launched (nbu); the others' partials
+// would be exact zeros.
+
+// global pair index of pair t (values 2t, 2t + 1) of instance y
+__device__ __forceinline__ int sl_pair(const SliceMap& m, int y, int t) {
+    int i = 2 * t;
+    if (i < m.len[0]) return (m.off[0] + y * m.len[0] + i) >> 1;
+    i -= m.len[0];
+    if (i < m.len[1]) return (m.off[1] + y * m.len[1] + i) >> 1;
+    i -= m.len[1];
+    return (m.off[2] + y * m.len[2] + i) >> 1;
+}
+
+// out[y * ostride + k] = sum of the nbu partials part[(y * nv + k) * nbu + b]
+__global__ void __launch_bounds__(KT) k_final_multi_sl(const double* __restrict__ part, double* out,
+                                                        int nbu, int nv, int ostride) {
+    pdl_entry();
+    __shared__ double sh[KT / 32];
+    const int k = blockIdx.x, y = blockIdx.y;
+    const double* p = part + ((size_t)y * nv + k) * nbu;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nbu; b += KT) s += p[b];
+    s = wsum(s);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = 0.0;
+#pragma unroll
+        for (int i = 0; i < KT / 32; ++i) r += sh[i];
+        out[(size_t)y * ostride + k] = r;
+    }
+}
+
+template <int J>
+__global__ void __launch_bounds__(KT) k_mdot_sl(SliceMap m, PtrArr V, const double* __restrict__ w,
+                                                 double* __restrict__ part, int nbu) {
+    pdl_entry();
+    const int y = blockIdx.y;
+    double acc[J + 2];
+#pragma unroll
+    for (int i = 0; i < J + 2; ++i) acc[i] = 0.0;
+    const int n2 = m.nl >> 1;
+    const double2* w2 = reinterpret_cast<const double2*>(w);
+    for (int t = blockIdx.x * KT + threadIdx.x; t < n2; t += KRY_BLOCKS * KT) {
+        const int p = sl_pair(m, y, t);
+        const double2 a = w2[p];
+#pragma unroll
+        for (int i = 0; i <= J; ++i) {
+            const double2 v = reinterpret_cast<const double2*>(V.p[i])[p];
+            acc[i] = fma(a.x, v.x, acc[i]);
+            acc[i] = fma(a.y, v.y, acc[i]);
+        }
+        acc[J + 1] = fma(a.x, a.x, acc[J + 1]);
+        acc[J + 1] = fma(a.y, a.y, acc[J + 1]);
+    }
+    block_sums<J + 2>(acc, part + (size_t)y * (J + 2) * nbu, nbu);
+}
+
+__global__ void __launch_bounds__(KT) k_mgs_step_sl(SliceMap m, const double* __restrict__ vk,
+                                                    const double* __restrict__ u,
+                                                    const double* __restrict__ h, int hstride, int k,
+                                                    double* __restrict__ w, double* __restrict__ part,
+                                                    int nbu) {
+    pdl_entry();
+    const int y = blockIdx.y;
+    const double hk = h[(size_t)y * hstride + k];
+    double s[1] = {0.0};
+    const int n2 = m.nl >> 1;
+    double2* w2 = reinterpret_cast<double2*>(w);
+    const double2* v2 = reinterpret_cast<const double2*>(vk);
+    const double2* u2 = reinterpret_cast<const double2*>(u);
+    for (int t = blockIdx.x * KT + threadIdx.x; t < n2; t += KRY_BLOCKS * KT) {
+        const int p = sl_pair(m, y, t);
+        double2 a = w2[p];
+        const double2 v = v2[p];
+        a.x = fma(-hk, v.x, a.x);
+        a.y = fma(-hk, v.y, a.y);
+        w2[p] = a;
+        const double2 b = u ? u2[p] : a;
+        s[0] = fma(a.x, b.x, s[0]);
+        s[0] = fma(a.y, b.y, s[0]);
+    }
+    block_sums<1>(s, part + (size_t)y * nbu, nbu);
+}
+
+// x += sum_{i < k_y} y_y[i] V_i with k_y, y_y from instance y's GMRES state
+template <int K, typename TV>
+__global__ void __launch_bounds__(KT) k_comb_dev_sl(SliceMap m, PtrArr V, const GmState* __restrict__ st,
+                                                     double* __restrict__ x) {
+    pdl_entry();
+    using V2 = typename Vec2<TV>::type;
+    const GmState& S = st[blockIdx.y];
+    const int k = S.k;
+    if (k <= 0) return;
+    double yy[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) yy[i] = i < k ? S.y[i] : 0.0;
+    const int n2 = m.nl >> 1;
+    double2* x2 = reinterpret_cast<double2*>(x);
+    for (int t = blockIdx.x * KT + threadIdx.x; t < n2; t += gridDim.x * KT) {
+        const int p = sl_pair(m, blockIdx.y, t);
+        double2 a = x2[p];
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            if (i < k) {
+                const V2 v = reinterpret_cast<const V2*>(V.p[i])[p];
+                a.x = fma(yy[i], widen(v.x), a.x);
+                a.y = fma(yy[i], widen(v.y), a.y);
+            }
+        }
+        x2[p] = a;
+    }
+}
+
+// Arnoldi step j's basis vector: x *= inv_scale of instance y where step j
+// is open; zero where it is not (an instance that has stopped carries zeros
+// through the rest of the cycle, so its vectors stay finite).
+__global__ void __launch_bounds__(KT) k_scal_dev_sl(SliceMap m, double* __restrict__ x,
+                                                    const GmState* __restrict__ st, int j) {
+    pdl_entry();
+    const GmState& S = st[blockIdx.y];
+    const bool open = S.cond[GM_COND_STEP0 + j] != 0;
+    const double a = S.inv_scale;
+    const int n2 = m.nl >> 1;
+    double2* x2 = reinterpret_cast<double2*>(x);
+    for (int t = blockIdx.x * KT + threadIdx.x; t < n2; t += gridDim.x * KT) {
+        const int p = sl_pair(m, blockIdx.y, t);
+        double2 v = x2[p];
+        v.x = open ? v.x * a : 0.0;
+        v.y = open ? v.y * a : 0.0;
+        x2[p] = v;
+    }
+}
+
+// per-instance k_sum_f32x4 (instances of n values one after another)
+__global__ void __launch_bounds__(KT) k_sum_f32x4_sl(int n, const float* __restrict__ x, double* part,
+                                                     int nbu) {
+    pdl_entry();
+    const float* xs = x + (size_t)blockIdx.y * n;
+    const int n4 = n >> 2;
+    const float4* x4 = reinterpret_cast<const float4*>(xs);
+    double acc[1] = {0.0};
+    for (int i = blockIdx.x * KT + threadIdx.x; i < n4; i += KRY_BLOCKS * KT) {
+        const float4 v = x4[i];
+        acc[0] += double((v.x + v.y) + (v.z + v.w));
+    }
+    if (blockIdx.x == 0 && threadIdx.x < (n & 3)) acc[0] += double(xs[4 * n4 + threadIdx.x]);
+    block_sums<1>(acc, part + (size_t)blockIdx.y * nbu, nbu);
+}
+
+int used_blocks(int items) {
+    const int b = (items + KT - 1) / KT;
+    return b < 1 ? 1 : (b > KRY_BLOCKS ? KRY_BLOCKS : b);
+}
+
 PtrArr pack(const void* const* V, int k) {
     PtrArr pa{};
     for (int i = 0; i < k; ++i) pa.p[i] = V[i];
@@ -280,6 +441,53 @@ void launch_mgs_step(int n, const double* vk, const double* u, const double* h, 
     launch_pdl(k_final_multi, dim3(1), dim3(KT), s, scratch, out);
 }
 
+void launch_sum_f32x4_sl(int n, int nsl, const float* x, double* scratch, double* out, int ostride,
+                         cudaStream_t s) {
+    const int nbu = used_blocks(n >> 2);
+    launch_pdl(k_sum_f32x4_sl, dim3(nbu, nsl), dim3(KT), s, n, x, scratch, nbu);
+    launch_pdl(k_final_multi_sl, dim3(1, nsl), dim3(KT), s, scratch, out, nbu, 1, ostride);
+}
+
+void launch_multidot_sl(const SliceMap& m, int nsl, int j, const double* const* V, const double* w,
+                        double* scratch, double* h, int hstride, cudaStream_t s) {
+    PtrArr pa = pack(reinterpret_cast<const void* const*>(V), j + 1);
+    const int nbu = used_blocks(m.nl >> 1);
+    const dim3 gr(nbu, nsl);
+    switch (j) {
+    case -1: launch_pdl(k_mdot_sl<-1>, gr, dim3(KT), s, m, pa, w, scratch, nbu); break;
+#define X(J) case J: launch_pdl(k_mdot_sl<J>, gr, dim3(KT), s, m, pa, w, scratch, nbu); break;
+    STK_J_CASES(X)
+#undef X
+    default: return;
+    }
+    launch_pdl(k_final_multi_sl, dim3(j + 2, nsl), dim3(KT), s, scratch, h, nbu, j + 2, hstride);
+}
+
+void launch_mgs_step_sl(const SliceMap& m, int nsl, const double* vk, const double* u, const double* h,
+                        int hstride, int k, double* w, double* scratch, double* out, int ostride,
+                        cudaStream_t s) {
+    const int nbu = used_blocks(m.nl >> 1);
+    launch_pdl(k_mgs_step_sl, dim3(nbu, nsl), dim3(KT), s, m, vk, u, h, hstride, k, w, scratch, nbu);
+    launch_pdl(k_final_multi_sl, dim3(1, nsl), dim3(KT), s, scratch, out, nbu, 1, ostride);
+}
+
+template <typename TV>
+void launch_combine_dev_sl(const SliceMap& m, int nsl, int mmax, const TV* const* V, const GmState* st,
+                           double* x, cudaStream_t s) {
+    PtrArr pa = pack(reinterpret_cast<const void* const*>(V), mmax);
+    const dim3 gr(used_blocks(m.nl >> 1), nsl);
+    switch (mmax - 1) {
+#define X(J) case J: launch_pdl(k_comb_dev_sl<J + 1, TV>, gr, dim3(KT), s, m, pa, st, x); break;
+    STK_J_CASES(X)
+#undef X
+    default: return;
+    }
+}
+
+void launch_scale_dev_sl(const SliceMap& m, int nsl, double* x, const GmState* st, int j, cudaStream_t s) {
+    launch_pdl(k_scal_dev_sl, dim3(used_blocks(m.nl >> 1), nsl), dim3(KT), s, m, x, st, j);
+}
+
 void launch_scale_inv_sqrt(int n, double* x, const double* nrm2, cudaStream_t s) {
     launch_pdl(k_scal, dim3(KRY_BLOCKS), dim3(KT), s, n, x, 0.0, nrm2);
 }
@@ -296,5 +504,9 @@ template void launch_combine_dev<double>(int, int, const double* const*, const d
                                          double*, cudaStream_t);
 template void launch_combine_dev<float>(int, int, const float* const*, const double*, const int*,
                                         double*, cudaStream_t);
+template void launch_combine_dev_sl<double>(const SliceMap&, int, int, const double* const*,
+                                            const GmState*, double*, cudaStream_t);
+template void launch_combine_dev_sl<float>(const SliceMap&, int, int, const float* const*,
+                                           const GmState*, double*, cudaStream_t);
 
 }  // namespace stk

@@ -123,6 +123,7 @@ __global__ void k_na_invdiag(Geom g, const double* __restrict__ beta, double* in
 Geom na_geom(int dim, const int n[3], double hh, const int bc[6]) {
     Geom g{};
     g.dim = dim;
+    g.nsl = 1;
     for (int a = 0; a < 3; ++a) {
         g.n[a] = a < dim ? n[a] : 1;
         g.per[a] = a < dim ? (bc[2 * a] == STK_PERIODIC) : 1;

@@ -53,6 +53,7 @@ k_vel_gs_pair(Geom g, Coef<T> C, const T* src, T* dst, const T* __restrict__ rhs
     const int e0 = g.fe[A][0], e1 = g.fe[A][1], e2 = g.fe[A][2];
     const int ox = blockIdx.x * 2 * TXC - 1, oy = blockIdx.y * TY - 1;
     const int oz = DIM == 3 ? int(blockIdx.z) * TZ - 1 : 0;
+    const int sl = DIM == 3 ? 0 : int(blockIdx.z);   // 2D: the instance of a stacked batch
     // components swept before A in this sweep are in dst, the others in src
     auto pb = [&](int B, int i) { return T((B < A ? dst : src)[i]); };
 
@@ -72,7 +73,7 @@ k_vel_gs_pair(Geom g, Coef<T> C, const T* src, T* dst, const T* __restrict__ rhs
             int q[3];
             q[0] = halo_coord(g, 0, ux, e0);
             q[1] = halo_coord(g, 1, uy, e1);
-            q[2] = DIM == 3 ? halo_coord(g, 2, uz, e2) : 0;
+            q[2] = DIM == 3 ? halo_coord(g, 2, uz, e2) : sl;
             if (q[0] < 0 || q[1] < 0 || q[2] < 0) {
                 R[lz][ly][lx] = T(0);
                 continue;
@@ -100,7 +101,7 @@ k_vel_gs_pair(Geom g, Coef<T> C, const T* src, T* dst, const T* __restrict__ rhs
     const int lx = 1 + 2 * xb + ((ox + uy + uz) & 1);   // ox + lx + uy + uz odd
     const int ux = ox + lx;
     if (ux >= e0 || uy >= e1 || (DIM == 3 && uz >= e2)) return;
-    const int q[3] = {ux, uy, DIM == 3 ? uz : 0};
+    const int q[3] = {ux, uy, DIM == 3 ? uz : sl};
     if (wall_face(g, A, q)) return;
     auto aidx = [&](const int* r) {
         const int sx = slot(r[0], ox, WX, e0);
@@ -127,6 +128,7 @@ k_cell_gs_pair(Geom g, Coef<T> C, const T* src, T* dst, const T* __restrict__ rh
     const int e0 = g.n[0], e1 = g.n[1], e2 = g.n[2];
     const int ox = blockIdx.x * 2 * TXC - 1, oy = blockIdx.y * TY - 1;
     const int oz = DIM == 3 ? int(blockIdx.z) * TZ - 1 : 0;
+    const int sl = DIM == 3 ? 0 : int(blockIdx.z);   // 2D: the instance of a stacked batch
     {
         auto pc = [&](const int* r) { return T(src[cidx(g, r)]); };
         for (int t = threadIdx.x; t < (TXC + 1) * WY * WZ; t += NT) {
@@ -143,7 +145,7 @@ k_cell_gs_pair(Geom g, Coef<T> C, const T* src, T* dst, const T* __restrict__ rh
             int q[3];
             q[0] = halo_coord(g, 0, ux, e0);
             q[1] = halo_coord(g, 1, uy, e1);
-            q[2] = DIM == 3 ? halo_coord(g, 2, uz, e2) : 0;
+            q[2] = DIM == 3 ? halo_coord(g, 2, uz, e2) : sl;
             if (q[0] < 0 || q[1] < 0 || q[2] < 0) {
                 R[lz][ly][lx] = T(0);
                 continue;
@@ -163,7 +165,7 @@ k_cell_gs_pair(Geom g, Coef<T> C, const T* src, T* dst, const T* __restrict__ rh
     const int lx = 1 + 2 * xb + ((ox + uy + uz) & 1);
     const int ux = ox + lx;
     if (ux >= e0 || uy >= e1 || (DIM == 3 && uz >= e2)) return;
-    const int q[3] = {ux, uy, DIM == 3 ? uz : 0};
+    const int q[3] = {ux, uy, DIM == 3 ? uz : sl};
     auto pc = [&](const int* r) {
         const int sx = slot(r[0], ox, WX, e0);
         const int sy = slot(r[1], oy, WY, e1);
@@ -338,13 +340,13 @@ k_cell_gs_zpair(Geom g, Coef<T> C, const T* src, T* dst, const T* __restrict__ r
     }
 }
 
-// tile shapes: 2D 32 x 16 (256 threads); 3D z-march columns of 64 x 8
-// faces (256 threads) through 16 planes
+// tile shapes: 2D 32 x 16 (256 threads; grid z = the instances of a stacked
+// batch); 3D z-march columns of 64 x 8 faces (256 threads) through 16 planes
 constexpr int P2X = 16, P2Y = 16;
 constexpr int Z3X = 32, Z3Y = 8, Z3K = 16;
 
 inline dim3 pair_grid(int dim, int e0, int e1, int e2) {
-    if (dim == 2) return dim3((e0 + 2 * P2X - 1) / (2 * P2X), (e1 + P2Y - 1) / P2Y, 1);
+    if (dim == 2) return dim3((e0 + 2 * P2X - 1) / (2 * P2X), (e1 + P2Y - 1) / P2Y, e2);
     return dim3((e0 + 2 * Z3X - 1) / (2 * Z3X), (e1 + Z3Y - 1) / Z3Y, (e2 + Z3K - 1) / Z3K);
 }
 

@@ -103,6 +103,10 @@ struct PBuf {            // level-0 buffers of the preconditioner in precision T
 struct stk_handle {
     int device = 0;
     int dim = 0;
+    // a stacked batch (2D): nsl instances of one grid along the third array
+    // axis of every array; smap locates an instance in a packed vector
+    int nsl = 1;
+    SliceMap smap{};
     std::vector<Level> lev;
     double theta = 0.0;
     bool coef_set = false;
@@ -157,9 +161,13 @@ struct stk_handle {
     // (phase, precond, flexible, m, nu, ncoarse, cycles); kernels each
     std::map<std::tuple<int, int, int, int, int, int, int>, std::pair<cudaGraphExec_t, long long>> pgraphs;
 
-    GmState* gst = nullptr;        // device state of the GMRES least-squares problem
+    GmState* gst = nullptr;        // device state of the GMRES least-squares problem (one per instance)
     GmState* gst_host = nullptr;   // pinned copy
-    std::vector<double> hist_true, hist_est;   // residual histories of the last solve
+    unsigned* gcond = nullptr;     // the OR of the instances' decisions (device)
+    unsigned* gcond_host = nullptr;
+    std::vector<stk_solve_info> sinfo;          // per instance, last solve
+    std::vector<int> sit_before;                // iterations before the current cycle
+    std::vector<std::vector<double>> hist_true, hist_est;   // residual histories of the last solve
     std::vector<ProfRec> recs;
     std::vector<cudaEvent_t> evpool;
     size_t evnext = 0;
@@ -212,11 +220,14 @@ cudaError_t dalloc(stk_handle* h, T** p, size_t n) {
     return cudaMemset(q, 0, sizeof(T) * (n ? n : 1));
 }
 
-Geom make_geom(int dim, const int n[3], double hh, const int bc[6]) {
+// nsl > 1 (2D only): nsl instances of the grid stacked along the third
+// array axis (a stacked batch)
+Geom make_geom(int dim, const int n[3], double hh, const int bc[6], int nsl = 1) {
     Geom g{};
     g.dim = dim;
+    g.nsl = dim == 2 ? nsl : 1;
     for (int a = 0; a < 3; ++a) {
-        g.n[a] = a < dim ? n[a] : 1;
+        g.n[a] = a < dim ? n[a] : (a == 2 ? g.nsl : 1);
         g.per[a] = a < dim ? (bc[2 * a] == STK_PERIODIC) : 1;
         g.bclo[a] = a < dim ? bc[2 * a] : STK_PERIODIC;
         g.bchi[a] = a < dim ? bc[2 * a + 1] : STK_PERIODIC;
@@ -494,8 +505,8 @@ void vcycle_vel(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp, 
     Work<T> W = work_of<T>(L);
     if (l >= lcoarse_of<T>(h)) {   // this level and all coarser ones in one launch
         Scope sc(h, PF_COARSE, 0.0, s);
-        launch_coarse_vcycle_vel<T>(L.g.dim, clev_of<T>(h) + l, (int)h->lev.size() - l, rhs, phi,
-                                    mp.nu, mp.ncoarse, h->bulk, coarse_smem<T>(h, l, true), s);
+        launch_coarse_vcycle_vel<T>(L.g.dim, L.g.nsl, clev_of<T>(h) + l, (int)h->lev.size() - l, rhs,
+                                    phi, mp.nu, mp.ncoarse, h->bulk, coarse_smem<T>(h, l, true), s);
         return;
     }
     if (l >= lgrid_of<T>(h)) {     // this level down as one persistent multi-block launch
@@ -547,8 +558,8 @@ void vcycle_cell(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp,
     Work<T> W = work_of<T>(L);
     if (l >= lcoarse_of<T>(h)) {
         Scope sc(h, PF_COARSE, 0.0, s);
-        launch_coarse_vcycle_cell<T>(L.g.dim, clev_of<T>(h) + l, (int)h->lev.size() - l, rhs, phi,
-                                     mp.nu, mp.ncoarse, coarse_smem<T>(h, l, false), s);
+        launch_coarse_vcycle_cell<T>(L.g.dim, L.g.nsl, clev_of<T>(h) + l, (int)h->lev.size() - l, rhs,
+                                     phi, mp.nu, mp.ncoarse, coarse_smem<T>(h, l, false), s);
         return;
     }
     if (l >= lgrid_of<T>(h)) {
@@ -588,16 +599,28 @@ void vcycle_cell(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp,
 }
 
 // out[0] = sum x of a cell vector: FP32 vectors with 16-byte alignment
-// take the wide-load reduction, the rest the plain one
+// take the wide-load reduction, the rest the plain one.  A stacked batch:
+// the sum of each instance, instance y's at out[y * NDSC].
 template <typename T>
 void cell_sum(stk_handle* h, int n, const T* x, double* out, cudaStream_t s) {
+    const int nsl = h->nsl;
     if constexpr (sizeof(T) == 4) {
         if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
-            launch_sum_f32x4(n, reinterpret_cast<const float*>(x), h->red, out, s);
+            if (nsl > 1) launch_sum_f32x4_sl(n / nsl, nsl, reinterpret_cast<const float*>(x), h->red, out, NDSC, s);
+            else launch_sum_f32x4(n, reinterpret_cast<const float*>(x), h->red, out, s);
             return;
         }
     }
-    launch_sum<T>(n, x, h->red, out, s);
+    if (nsl > 1) launch_sum_sl<T>(n / nsl, nsl, x, h->red, out, NDSC, s);
+    else launch_sum<T>(n, x, h->red, out, s);
+}
+
+// out = in - mean(in) (per instance of a stacked batch; sum from cell_sum)
+template <typename T>
+void sub_mean(stk_handle* h, int n, const T* in, T* out, double* sum, cudaStream_t s) {
+    if (h->nsl > 1) launch_sub_mean_sl<T>(n / h->nsl, h->nsl, in, out, sum, NDSC, s);
+    else if (in == out) launch_sub_mean<T>(n, out, sum, s);
+    else launch_copy_sub_mean<T>(n, in, out, sum, s);
 }
 
 // phi = L~_rho^{-1} (r - mean r): the Poisson right-hand side is projected
@@ -611,7 +634,7 @@ void poisson_solve(stk_handle* h, const T* r, T* phi, const MGParams& mp, cudaSt
     {
         Scope sc(h, PF_MEAN, 2.0 * sizeof(T) * nc, s, 4);
         cell_sum<T>(h, nc, r, h->dsc + DS_SUM, s);
-        launch_copy_sub_mean<T>(nc, r, W.rhs_p, h->dsc + DS_SUM, s);
+        sub_mean<T>(h, nc, r, W.rhs_p, h->dsc + DS_SUM, s);
     }
     vcycle_cell<T>(h, 0, W.rhs_p, phi, mp, s);
     // further cycles: phi += V(r - L phi), the residual projected onto
@@ -624,7 +647,7 @@ void poisson_solve(stk_handle* h, const T* r, T* phi, const MGParams& mp, cudaSt
         {
             Scope sc(h, PF_MEAN, 3.0 * sizeof(T) * nc, s, 4);
             cell_sum<T>(h, nc, B.rp, h->dsc + DS_SUM + 4, s);
-            launch_sub_mean<T>(nc, B.rp, h->dsc + DS_SUM + 4, s);
+            sub_mean<T>(h, nc, B.rp, B.rp, h->dsc + DS_SUM + 4, s);
         }
         vcycle_cell<T>(h, 0, B.rp, B.dp, mp, s);
         { Scope sc(h, PF_ALG, 3.0 * sizeof(T) * nc, s); launch_axpy<T>(nc, T(1), B.dp, phi, s); }
@@ -653,7 +676,7 @@ void remove_mean(stk_handle* h, T* x, cudaStream_t s) {
     const Level& L = h->lev[0];
     Scope sc(h, PF_MEAN, 3.0 * sizeof(T) * L.g.ncell, s, 4);
     cell_sum<T>(h, L.g.ncell, x, h->dsc + DS_SUM + 2, s);
-    launch_sub_mean<T>(L.g.ncell, x, h->dsc + DS_SUM + 2, s);
+    sub_mean<T>(h, L.g.ncell, x, x, h->dsc + DS_SUM + 2, s);
 }
 
 // x = P^{-1} b, Sec. 2.1-2.4; b, x packed Stokes vectors of precision T.
@@ -849,28 +872,37 @@ int ensure_krylov(stk_handle* h, int m) {
 // h_0 = <w, v_0>; for k = 0..j: w -= h_k v_k fused with h_{k+1} = <w, v_{k+1}>
 // (the last step forms ||w||^2 in DS_N2 instead).  The coefficients stay in
 // device memory (DS_H) for the Givens kernel.
+// A stacked batch runs the same steps per instance (instance y's scalars
+// at y * NDSC), bitwise as each instance alone.
 void orth_enqueue(stk_handle* h, int j, cudaStream_t s) {
     const int n = nstokes(h);
+    const bool sl = h->nsl > 1;
     double* w = h->V[j + 1];
     double* hd = h->dsc + DS_H;
     {
         Scope sc(h, PF_MDOT, 16.0 * n, s, 2);
         const double* v0 = h->V[0];
-        launch_multidot(n, 0, &v0, w, h->red, hd, s);
+        if (sl) launch_multidot_sl(h->smap, h->nsl, 0, &v0, w, h->red, hd, NDSC, s);
+        else launch_multidot(n, 0, &v0, w, h->red, hd, s);
     }
     for (int k = 0; k <= j; ++k) {
         const bool last = k == j;
         Scope sc(h, PF_UPD, 8.0 * n * (last ? 3 : 4), s, 2);
-        launch_mgs_step(n, h->V[k], last ? nullptr : h->V[k + 1], hd, k, w, h->red,
-                        last ? h->dsc + DS_N2 : hd + k + 1, s);
+        double* out = last ? h->dsc + DS_N2 : hd + k + 1;
+        if (sl)
+            launch_mgs_step_sl(h->smap, h->nsl, h->V[k], last ? nullptr : h->V[k + 1], hd, NDSC, k, w,
+                               h->red, out, NDSC, s);
+        else
+            launch_mgs_step(n, h->V[k], last ? nullptr : h->V[k + 1], hd, k, w, h->red, out, s);
     }
 }
 
-// out[0] = ||x||^2 (device)
+// out[0] = ||x||^2 (device; per instance of a stacked batch at stride NDSC)
 void norm_enqueue(stk_handle* h, const double* x, double* out, cudaStream_t s) {
     const int n = nstokes(h);
     Scope sc(h, PF_MDOT, 8.0 * n, s, 2);
-    launch_multidot(n, -1, nullptr, x, h->red, out, s);
+    if (h->nsl > 1) launch_multidot_sl(h->smap, h->nsl, -1, nullptr, x, h->red, out, NDSC, s);
+    else launch_multidot(n, -1, nullptr, x, h->red, out, s);
 }
 
 struct CycleCtx {
@@ -900,7 +932,10 @@ void enq_check(const CycleCtx& c, cudaStream_t s, cudaGraphConditionalHandle hpr
         launch_stokes_matvec_stress(g, h->lev[0].cd, h->sw, h->xk, h->bk, h->tmp, s);
     }
     norm_enqueue(h, h->tmp, h->dsc + DS_N2 + 1, s);
-    { Scope sc(h, PF_ALG, 0.0, s); launch_gm_check(h->gst, h->dsc + DS_N2 + 1, hpre, use, s); }
+    {
+        Scope sc(h, PF_ALG, 0.0, s);
+        launch_gm_check(h->gst, h->nsl, h->gcond, h->dsc + DS_N2 + 1, NDSC, hpre, use, s);
+    }
 }
 
 // phase 2: v_0 = P^{-1} r (left) or r (flexible), beta, target (gates of the
@@ -915,7 +950,10 @@ int enq_pre(const CycleCtx& c, cudaStream_t s, cudaGraphConditionalHandle h0,
         if (rc) return rc;
         norm_enqueue(h, h->V[0], h->dsc + DS_N2 + 2, s);
     }
-    { Scope sc(h, PF_ALG, 0.0, s); launch_gm_start(h->gst, h->dsc + DS_N2 + 2, h0, use, hfin, use, s); }
+    {
+        Scope sc(h, PF_ALG, 0.0, s);
+        launch_gm_start(h->gst, h->nsl, h->gcond, h->dsc + DS_N2 + 2, NDSC, h0, use, hfin, use, s);
+    }
     return STK_OK;
 }
 
@@ -926,7 +964,8 @@ int enq_step(const CycleCtx& c, int j, cudaStream_t s, cudaGraphConditionalHandl
     const int n = nstokes(h);
     {   // v_j /= beta (j = 0) or h_{j,j-1}
         Scope sc(h, PF_COMB, 16.0 * n, s);
-        launch_scale_dev(n, h->V[j], &h->gst->inv_scale, s);
+        if (h->nsl > 1) launch_scale_dev_sl(h->smap, h->nsl, h->V[j], h->gst, j, s);
+        else launch_scale_dev(n, h->V[j], &h->gst->inv_scale, s);
     }
     if (c.flex) {
         {
@@ -951,7 +990,7 @@ int enq_step(const CycleCtx& c, int j, cudaStream_t s, cudaGraphConditionalHandl
     }
     orth_enqueue(h, j, s);
     Scope sc(h, PF_ALG, 0.0, s);
-    launch_gm_step(h->gst, j, h->dsc + DS_H, h->dsc + DS_N2, hn, use, s);
+    launch_gm_step(h->gst, h->nsl, h->gcond, j, h->dsc + DS_H, h->dsc + DS_N2, NDSC, hn, use, s);
     return STK_OK;
 }
 
@@ -959,14 +998,17 @@ int enq_step(const CycleCtx& c, int j, cudaStream_t s, cudaGraphConditionalHandl
 void enq_fin(const CycleCtx& c, cudaStream_t s) {
     stk_handle* h = c.h;
     const int n = nstokes(h);
-    { Scope sc(h, PF_ALG, 0.0, s); launch_gm_finish(h->gst, s); }
+    { Scope sc(h, PF_ALG, 0.0, s); launch_gm_finish(h->gst, h->nsl, s); }
     Scope sc(h, PF_COMB, (c.flex ? 4.0 : 8.0) * n * c.m + 16.0 * n, s);
+    const bool sl = h->nsl > 1;
     if (c.flex) {
         std::vector<const float*> Zp(h->Z.begin(), h->Z.begin() + c.m);
-        launch_combine_dev<float>(n, c.m, Zp.data(), h->gst->y, &h->gst->k, h->xk, s);
+        if (sl) launch_combine_dev_sl<float>(h->smap, h->nsl, c.m, Zp.data(), h->gst, h->xk, s);
+        else launch_combine_dev<float>(n, c.m, Zp.data(), h->gst->y, &h->gst->k, h->xk, s);
     } else {
         std::vector<const double*> Vp(h->V.begin(), h->V.begin() + c.m);
-        launch_combine_dev<double>(n, c.m, Vp.data(), h->gst->y, &h->gst->k, h->xk, s);
+        if (sl) launch_combine_dev_sl<double>(h->smap, h->nsl, c.m, Vp.data(), h->gst, h->xk, s);
+        else launch_combine_dev<double>(n, c.m, Vp.data(), h->gst->y, &h->gst->k, h->xk, s);
     }
 }
 
@@ -1017,7 +1059,7 @@ int build_chain(cudaGraph_t G, const CycleCtx& c, stk_handle::CycleGraph& out) {
     out.k_step.assign(m, 0);
     add_if(hgate, [&](cudaStream_t s) {
         Scope sc(h, PF_ALG, 0.0, s);
-        launch_gm_gate(h->gst, hchk, s);
+        launch_gm_gate(h->gst, h->nsl, h->gcond, hchk, s);
         return STK_OK;
     }, out.k_gate);
     add_if(hchk, [&](cudaStream_t s) { enq_check(c, s, hpre, 1); return STK_OK; }, out.k_chk);
@@ -1100,6 +1142,9 @@ int run_phase(const CycleCtx& c, int ph, cudaStream_t s) {
 }
 
 // One GMRES instance advanced in lockstep with others (Sec. 3.2, Sec. 4).
+// A stacked batch is one instance here: its records advance together, each
+// on its own (the device kernels skip an instance's record where its phase
+// is not open).
 struct Inst {
     stk_handle* h = nullptr;
     cudaStream_t s = nullptr;
@@ -1107,7 +1152,6 @@ struct Inst {
     int rc = STK_OK;
     bool done = false;              // solve finished (converged, maxit or error)
     stk_handle::CycleGraph* cg = nullptr;
-    int it_before = 0;              // iterations before the current cycle
 };
 
 constexpr size_t GM_HEADER = offsetof(GmState, H);   // bytes the host reads per cycle
@@ -1136,43 +1180,96 @@ void finish(Inst* it, int rc) {
     it->done = true;
 }
 
+// the group decisions and every instance's record header
 void read_header(Inst* it) {
-    cudaMemcpyAsync(it->h->gst_host, it->h->gst, GM_HEADER, cudaMemcpyDeviceToHost, it->s);
+    stk_handle* h = it->h;
+    cudaMemcpyAsync(h->gcond_host, h->gcond, sizeof(unsigned) * GM_NCOND, cudaMemcpyDeviceToHost, it->s);
+    if (h->nsl == 1)
+        cudaMemcpyAsync(h->gst_host, h->gst, GM_HEADER, cudaMemcpyDeviceToHost, it->s);
+    else
+        cudaMemcpy2DAsync(h->gst_host, sizeof(GmState), h->gst, sizeof(GmState), GM_HEADER, h->nsl,
+                          cudaMemcpyDeviceToHost, it->s);
 }
 
-// Fold the device state read after a cycle into the info record; finish the
-// instance when the device stopped it.
+// Summarise the instances' records into the info record; finish the solve
+// once no instance is running (the first failing instance, in order, gives
+// the error).
+void settle(Inst* it) {
+    stk_handle* h = it->h;
+    bool running = false, all_conv = true;
+    stk_solve_info& a = it->info;
+    a.iterations = a.restarts = 0;
+    a.true_residual = a.est_residual = a.scalar_vcycles = 0.0;
+    int bad = -1, bad_state = GM_CONVERGED;
+    for (int y = 0; y < h->nsl; ++y) {
+        const GmState& st = h->gst_host[y];
+        const stk_solve_info& f = h->sinfo[y];
+        running = running || st.state == GM_RUNNING;
+        all_conv = all_conv && st.state == GM_CONVERGED;
+        a.iterations = std::max(a.iterations, f.iterations);
+        a.restarts = std::max(a.restarts, f.restarts);
+        a.true_residual = std::max(a.true_residual, f.true_residual);
+        a.est_residual = std::max(a.est_residual, f.est_residual);
+        a.scalar_vcycles = std::max(a.scalar_vcycles, f.scalar_vcycles);
+        if (bad < 0 && st.state != GM_RUNNING && st.state != GM_CONVERGED && st.state != GM_MAXIT) {
+            bad = y;
+            bad_state = st.state;
+        }
+    }
+    if (running) return;
+    a.converged = all_conv ? 1 : 0;
+    if (all_conv) { finish(it, STK_OK); return; }
+    char who[32] = "";
+    if (h->nsl > 1) snprintf(who, sizeof who, "instance %d: ", bad < 0 ? 0 : bad);
+    if (bad < 0) { finish(it, STK_ERR_NOT_CONVERGED); return; }
+    if (bad_state == GM_TIMEOUT) {
+        finish(it, fail(h, STK_ERR_TIMEOUT, "%sa bounded device wait (grid barrier) ran out", who));
+        return;
+    }
+    static const char* why[] = {"", "non-finite right-hand side", "non-finite residual",
+                                "non-finite preconditioned residual",
+                                "non-finite value in the Arnoldi process", "non-finite GMRES update"};
+    const int w = h->gst_host[bad].why;
+    finish(it, fail(h, STK_ERR_NONFINITE, "%s%s", who, why[w >= 1 && w <= 5 ? w : 0]));
+}
+
+// Fold the records read after a cycle into the per-instance info records.
 void absorb_cycle(Inst* it, const stk_solver_params& prm, const MGParams& mp) {
     stk_handle* h = it->h;
-    const GmState& st = *h->gst_host;
-    const int steps = st.iterations - it->it_before;
+    const unsigned* gc = h->gcond_host;
     const double sv = scalar_vcycles(h, prm.precond, mp);
-    it->info.scalar_vcycles += sv * steps + ((prm.precision != STK_MIXED && st.cond[GM_COND_PRE]) ? sv : 0.0);
-    it->info.iterations = st.iterations;
-    it->info.restarts = st.restarts;
-    it->info.true_residual = st.rnorm / st.bnorm;
-    it->info.est_residual = st.est / st.bnorm;
+    int steps_max = 0;
+    for (int y = 0; y < h->nsl; ++y) {
+        const GmState& st = h->gst_host[y];
+        stk_solve_info& f = h->sinfo[y];
+        const int steps = st.iterations - h->sit_before[y];
+        steps_max = std::max(steps_max, steps);
+        f.scalar_vcycles += sv * steps + ((prm.precision != STK_MIXED && st.cond[GM_COND_PRE]) ? sv : 0.0);
+        f.iterations = st.iterations;
+        f.restarts = st.restarts;
+        f.true_residual = st.bnorm > 0.0 ? st.rnorm / st.bnorm : 0.0;
+        f.est_residual = st.bnorm > 0.0 ? st.est / st.bnorm : 0.0;
+        f.converged = st.state == GM_CONVERGED ? 1 : 0;
+        h->sit_before[y] = st.iterations;
+    }
     if (it->cg) {   // kernels the graph ran: the gates the device opened
         const auto& cg = *it->cg;
-        h->nkern += cg.k_gate + (st.cond[GM_COND_CHK] ? cg.k_chk : 0) +
-                    (st.cond[GM_COND_PRE] ? cg.k_pre : 0) + (st.cond[GM_COND_FIN] ? cg.k_fin : 0);
-        for (int j = 0; j < steps && j < (int)cg.k_step.size(); ++j) h->nkern += cg.k_step[j];
+        h->nkern += cg.k_gate + (gc[GM_COND_CHK] ? cg.k_chk : 0) + (gc[GM_COND_PRE] ? cg.k_pre : 0) +
+                    (gc[GM_COND_FIN] ? cg.k_fin : 0);
+        for (int j = 0; j < steps_max && j < (int)cg.k_step.size(); ++j) h->nkern += cg.k_step[j];
     }
-    it->it_before = st.iterations;
-    switch (st.state) {
-    case GM_RUNNING: break;
-    case GM_CONVERGED: it->info.converged = 1; finish(it, STK_OK); break;
-    case GM_MAXIT: finish(it, STK_ERR_NOT_CONVERGED); break;
-    case GM_TIMEOUT:
-        finish(it, fail(h, STK_ERR_TIMEOUT, "a bounded device wait (grid barrier) ran out"));
-        break;
-    default: {
-        static const char* why[] = {"", "non-finite right-hand side", "non-finite residual",
-                                    "non-finite preconditioned residual",
-                                    "non-finite value in the Arnoldi process", "non-finite GMRES update"};
-        finish(it, fail(h, STK_ERR_NONFINITE, "%s", why[st.why >= 1 && st.why <= 5 ? st.why : 0]));
+    settle(it);
+}
+
+// zero the part of the packed vector x that belongs to instance y
+void zero_instance(stk_handle* h, double* x, int y, cudaStream_t s) {
+    if (h->nsl == 1) {
+        cudaMemsetAsync(x, 0, sizeof(double) * nstokes(h), s);
+        return;
     }
-    }
+    const SliceMap& m = h->smap;
+    for (int k = 0; k < 3; ++k)
+        cudaMemsetAsync(x + m.off[k] + (size_t)y * m.len[k], 0, sizeof(double) * m.len[k], s);
 }
 
 // Restarted GMRES for every instance: left-preconditioned with an FP64
@@ -1183,7 +1280,7 @@ void absorb_cycle(Inst* it, const stk_solver_params& prm, const MGParams& mp) {
 // With cycle_graphs (a single solve, graphs on, profiling off) each cycle is
 // one graph launch and the host synchronises once per cycle; otherwise the
 // host gates the phases of all instances together, one synchronisation per
-// phase for the whole batch, each preconditioner application one graph.
+// phase for the whole batch, each phase one graph launch.
 void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm, bool cycle_graphs) {
     const int m = prm.restart;
     const bool flex = prm.precision == STK_MIXED;
@@ -1197,22 +1294,28 @@ void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm, bool
         if (it.done) continue;
         int rc = ensure_krylov(it.h, m);
         if (rc) { finish(&it, rc); continue; }
-        norm_enqueue(it.h, it.h->bk, it.h->dsc + DS_N2 + 3, it.s);
-        launch_gm_begin(it.h->gst, it.h->dsc + DS_N2 + 3, prm.rtol, prm.maxit, m, flex ? 1 : 0, it.s);
-        ++it.h->nkern;
+        stk_handle* h = it.h;
+        h->sinfo.assign(h->nsl, stk_solve_info{});
+        h->sit_before.assign(h->nsl, 0);
+        norm_enqueue(h, h->bk, h->dsc + DS_N2 + 3, it.s);
+        launch_gm_begin(h->gst, h->nsl, h->gcond, h->dsc + DS_N2 + 3, NDSC, prm.rtol, prm.maxit, m,
+                        flex ? 1 : 0, it.s);
+        ++h->nkern;
         read_header(&it);
         act.push_back(&it);
     }
     sync_all(act);
     for (Inst* it : act) {
         if (it->done) continue;
-        const GmState& st = *it->h->gst_host;
-        if (st.state == GM_NONFINITE) finish(it, fail(it->h, STK_ERR_NONFINITE, "non-finite right-hand side"));
-        else if (st.bnorm == 0.0) {
-            cudaMemsetAsync(it->h->xk, 0, sizeof(double) * nstokes(it->h), it->s);
-            it->info.converged = 1;
-            finish(it, STK_OK);
+        stk_handle* h = it->h;
+        for (int y = 0; y < h->nsl; ++y) {
+            const GmState& st = h->gst_host[y];
+            if (st.state == GM_CONVERGED) {   // zero right-hand side: x = 0
+                zero_instance(h, h->xk, y, it->s);
+                h->sinfo[y].converged = 1;
+            }
         }
+        settle(it);
     }
     // graphs of the cycle (built on first use per handle and configuration)
     for (Inst* it : act) {
@@ -1233,6 +1336,7 @@ void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm, bool
         }
         it->cg = &f->second;
     }
+    auto open_ = [](Inst* it, int slot) { return it->h->gcond_host[slot] != 0; };
     while (true) {
         act.clear();
         for (auto& it : insts)
@@ -1259,7 +1363,7 @@ void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm, bool
             sync_all(eager);
             std::vector<Inst*> run;
             for (Inst* it : eager)
-                if (!it->done && it->h->gst_host->cond[GM_COND_PRE]) run.push_back(it);
+                if (!it->done && open_(it, GM_COND_PRE)) run.push_back(it);
             for (Inst* it : run) {
                 CycleCtx c{it->h, prm.precond, m, flex, mp};
                 int rc = run_phase(c, 1, it->s);
@@ -1270,7 +1374,7 @@ void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm, bool
             for (int j = 0; j < m; ++j) {
                 std::vector<Inst*> step;
                 for (Inst* it : run)
-                    if (!it->done && it->h->gst_host->cond[GM_COND_STEP0 + j]) step.push_back(it);
+                    if (!it->done && open_(it, GM_COND_STEP0 + j)) step.push_back(it);
                 if (step.empty()) break;
                 for (Inst* it : step) {
                     CycleCtx c{it->h, prm.precond, m, flex, mp};
@@ -1281,7 +1385,7 @@ void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm, bool
                 sync_all(step);
             }
             for (Inst* it : run) {
-                if (it->done || !it->h->gst_host->cond[GM_COND_FIN]) continue;
+                if (it->done || !open_(it, GM_COND_FIN)) continue;
                 CycleCtx c{it->h, prm.precond, m, flex, mp};
                 int rc = run_phase(c, m + 2, it->s);
                 if (rc) { finish(it, rc); continue; }
@@ -1297,13 +1401,18 @@ void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm, bool
     // residual histories of the solve
     for (Inst* it : all) {
         stk_handle* h = it->h;
-        cudaMemcpyAsync(h->gst_host, h->gst, sizeof(GmState), cudaMemcpyDeviceToHost, it->s);
+        cudaMemcpyAsync(h->gst_host, h->gst, sizeof(GmState) * h->nsl, cudaMemcpyDeviceToHost, it->s);
     }
     sync_all(all);
     for (Inst* it : all) {
-        const GmState& st = *it->h->gst_host;
-        it->h->hist_true.assign(st.hist, st.hist + std::min(st.nhist, GM_NHIST));
-        it->h->hist_est.assign(st.est_hist, st.est_hist + std::min(st.nest, GM_NEST));
+        stk_handle* h = it->h;
+        h->hist_true.assign(h->nsl, {});
+        h->hist_est.assign(h->nsl, {});
+        for (int y = 0; y < h->nsl; ++y) {
+            const GmState& st = h->gst_host[y];
+            h->hist_true[y].assign(st.hist, st.hist + std::min(st.nhist, GM_NHIST));
+            h->hist_est[y].assign(st.est_hist, st.est_hist + std::min(st.nest, GM_NEST));
+        }
     }
 }
 
@@ -1364,6 +1473,8 @@ void build_coefficients(stk_handle* h, const double* rho, const double* mu, cuda
     }
 }
 
+int create_handle(int dim, const int* n, double hh, const int* bc, int nsl, stk_handle** out);
+
 }  // namespace
 
 // ===================================================================== C ABI
@@ -1394,6 +1505,22 @@ long long stk_face_length(const stk_handle* h, int a) {
 long long stk_cell_length(const stk_handle* h) { return h ? h->lev[0].g.ncell : -1; }
 
 int stk_create(int dim, const int* n, double hh, const int* bc, stk_handle** out) {
+    return create_handle(dim, n, hh, bc, 1, out);
+}
+
+int stk_create_stacked(int dim, const int* n, double hh, const int* bc, int count, stk_handle** out) {
+    if (out) *out = nullptr;
+    if (dim != 2) return fail(nullptr, STK_ERR_ARG, "stacked batches are 2D");
+    if (count < 1 || count > STK_MAX_STACK)
+        return fail(nullptr, STK_ERR_ARG, "count must be 1..%d", STK_MAX_STACK);
+    return create_handle(dim, n, hh, bc, count, out);
+}
+
+}  // extern "C"
+
+namespace {
+
+int create_handle(int dim, const int* n, double hh, const int* bc, int nsl, stk_handle** out) {
     stk_handle* h = nullptr;
     if (!out) return fail(nullptr, STK_ERR_ARG, "out is null");
     *out = nullptr;
@@ -1412,17 +1539,18 @@ int stk_create(int dim, const int* n, double hh, const int* bc, stk_handle** out
         if ((bb[2 * a] == STK_PERIODIC) != (bb[2 * a + 1] == STK_PERIODIC))
             return fail(nullptr, STK_ERR_ARG, "axis %d: periodic must be set on both sides", a);
     }
-    long long total = 1;
+    long long total = nsl;
     for (int a = 0; a < dim; ++a) total *= nn[a];
     if (total * (dim + 1) > (1LL << 30)) return fail(nullptr, STK_ERR_SIZE, "grid too large");
     h = new stk_handle();
     cudaGetDevice(&h->device);
     h->dim = dim;
+    h->nsl = nsl;
     int cur[3] = {nn[0], nn[1], nn[2]};
     double hl = hh;
     while (true) {
         Level L{};
-        L.g = make_geom(dim, cur, hl, bb);
+        L.g = make_geom(dim, cur, hl, bb, nsl);
         h->lev.push_back(L);
         int mn = cur[0];
         for (int a = 1; a < dim; ++a) mn = cur[a] < mn ? cur[a] : mn;
@@ -1478,7 +1606,7 @@ int stk_create(int dim, const int* n, double hh, const int* bc, stk_handle** out
         CKC(dalloc(h, &L.wf.alt_u, g.nvel));
         CKC(dalloc(h, &L.wf.alt_p, g.ncell));
     }
-    {
+    if (nsl == 1) {   // (a stacked batch sweeps on its coarsest level)
         Level& Lc = h->lev.back();
         const size_t nu = (size_t)Lc.g.nvel, np = (size_t)Lc.g.ncell;
         if (nu <= (size_t)SMAT_MAX) {
@@ -1492,6 +1620,13 @@ int stk_create(int dim, const int* n, double hh, const int* bc, stk_handle** out
     }
     const Geom& g0 = h->lev[0].g;
     const int ns = g0.nvel + g0.ncell;
+    h->smap.len[0] = g0.fsize[0] / nsl;
+    h->smap.len[1] = g0.fsize[1] / nsl;
+    h->smap.len[2] = g0.ncell / nsl;
+    h->smap.off[0] = 0;
+    h->smap.off[1] = g0.foff[1];
+    h->smap.off[2] = g0.nvel;
+    h->smap.nl = h->smap.len[0] + h->smap.len[1] + h->smap.len[2];
     CKC(dalloc(h, &h->pd.in, ns));
     CKC(dalloc(h, &h->pd.bc, g0.ncell));
     CKC(dalloc(h, &h->pd.tmpu, g0.nvel));
@@ -1511,26 +1646,31 @@ int stk_create(int dim, const int* n, double hh, const int* bc, stk_handle** out
     CKC(dalloc(h, &h->bk, ns));
     CKC(dalloc(h, &h->xk, ns));
     CKC(dalloc(h, &h->tmp, ns));
-    CKC(dalloc(h, &h->red, (size_t)RED_SCRATCH));
+    CKC(dalloc(h, &h->red, (size_t)RED_SCRATCH * nsl));
     for (int a = 0; a < g0.dim; ++a) CKC(dalloc(h, &h->sw.tc[a], g0.ncell));
     for (int p = 0; p < 3; ++p)
         if (g0.esize[p] > 0) CKC(dalloc(h, &h->sw.te[p], g0.esize[p]));
     CKC(dalloc(h, &h->rho0, g0.ncell));
     CKC(dalloc(h, &h->mu0, g0.ncell));
-    CKC(dalloc(h, &h->dsc, NDSC));
+    CKC(dalloc(h, &h->dsc, (size_t)NDSC * nsl));
     {
         void* p = nullptr;
         CKC(cudaMallocHost(&p, sizeof(double) * 256));
         h->hpin = static_cast<double*>(p);
+        static_assert(sizeof(GmState) % 8 == 0, "GmState records are packed as doubles");
         double* q = nullptr;
-        CKC(dalloc(h, &q, (sizeof(GmState) + 7) / 8));
+        CKC(dalloc(h, &q, sizeof(GmState) / 8 * nsl));
         h->gst = reinterpret_cast<GmState*>(q);
+        CKC(dalloc(h, &h->gcond, GM_NCOND));
         CKC(dalloc(h, &h->gbar, 4));
         const long long budget = 2000000000LL;   // about one second at 2 GHz
         CKC(cudaMemcpy(h->gbar + 2, &budget, sizeof budget, cudaMemcpyHostToDevice));
-        CKC(cudaMallocHost(&p, sizeof(GmState)));
+        CKC(cudaMallocHost(&p, sizeof(GmState) * nsl));
         h->gst_host = static_cast<GmState*>(p);
-        std::memset(h->gst_host, 0, sizeof(GmState));
+        std::memset(h->gst_host, 0, sizeof(GmState) * nsl);
+        CKC(cudaMallocHost(&p, sizeof(unsigned) * GM_NCOND));
+        h->gcond_host = static_cast<unsigned*>(p);
+        std::memset(h->gcond_host, 0, sizeof(unsigned) * GM_NCOND);
     }
     CKC(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
     CKC(cudaStreamCreateWithFlags(&h->run, cudaStreamNonBlocking));
@@ -1543,8 +1683,9 @@ int stk_create(int dim, const int* n, double hh, const int* bc, stk_handle** out
         // recomputation is small (measured; the autotuner decides per grid)
         h->lpair_d = nl;
         h->lpair_f = h->dim == 2 ? 0 : nl;
-        while (h->lcoarse_f > 0 && h->lev[h->lcoarse_f - 1].g.ncell <= COARSE_MAX_CELLS_F32) --h->lcoarse_f;
-        while (h->lcoarse_d > 0 && h->lev[h->lcoarse_d - 1].g.ncell <= COARSE_MAX_CELLS_F64) --h->lcoarse_d;
+        // (a stacked batch: the cells of one instance, each has its own block)
+        while (h->lcoarse_f > 0 && h->lev[h->lcoarse_f - 1].g.ncell / nsl <= COARSE_MAX_CELLS_F32) --h->lcoarse_f;
+        while (h->lcoarse_d > 0 && h->lev[h->lcoarse_d - 1].g.ncell / nsl <= COARSE_MAX_CELLS_F64) --h->lcoarse_d;
         std::vector<CLevel<double>> cd(nl);
         std::vector<CLevel<float>> cf(nl);
         CKC(dalloc(h, &h->cld, nl));
@@ -1558,6 +1699,10 @@ int stk_create(int dim, const int* n, double hh, const int* bc, stk_handle** out
     return STK_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
 int stk_destroy(stk_handle* h) {
     if (!h) return STK_OK;
     cudaDeviceSynchronize();
@@ -1568,6 +1713,7 @@ int stk_destroy(stk_handle* h) {
     for (void* p : h->allocs) cudaFree(p);
     if (h->hpin) cudaFreeHost(h->hpin);
     if (h->gst_host) cudaFreeHost(h->gst_host);
+    if (h->gcond_host) cudaFreeHost(h->gcond_host);
     for (auto e : h->evpool) cudaEventDestroy(e);
     delete h;
     return STK_OK;
@@ -1615,6 +1761,7 @@ int stk_set_coefficients(stk_handle* h, const double* rho, const double* mu, dou
 
 int stk_set_bulk_viscosity(stk_handle* h, const double* gamma, void* stream) {
     if (!h) return STK_ERR_ARG;
+    if (h->nsl > 1) return fail(h, STK_ERR_ARG, "not available on a stacked batch");
     if (!h->coef_set) return fail(h, STK_ERR_STATE, "coefficients not set");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     CK(cudaSetDevice(h->device));
@@ -1725,6 +1872,7 @@ int stk_subtract_boundary_terms(stk_handle* h, const double* const* u_wall,
                                 const double* const* u_tan, double* const* b_u, double* b_p,
                                 void* stream) {
     if (!h) return STK_ERR_ARG;
+    if (h->nsl > 1) return fail(h, STK_ERR_ARG, "not available on a stacked batch");
     if (!h->coef_set) return fail(h, STK_ERR_STATE, "coefficients not set");
     int rc;
     if ((rc = check_ptrs(h, (const void* const*)b_u, b_p))) return rc;
@@ -1870,7 +2018,10 @@ int stk_solve_batched(int count, stk_handle* const* hs, const stk_solver_params*
     int worst = STK_OK;
     for (int i = 0; i < count; ++i) {
         Inst& it = insts[i];
-        if (it.rc == STK_OK || it.rc == STK_ERR_NOT_CONVERGED) {
+        // a stacked batch hands back every instance's iterate (stk_stack_info
+        // says which converged), also when one of them failed
+        const bool partial = it.h->nsl > 1 && (it.rc == STK_ERR_NONFINITE || it.rc == STK_ERR_TIMEOUT);
+        if (it.rc == STK_OK || it.rc == STK_ERR_NOT_CONVERGED || partial) {
             int rc2 = scatter(it.h, it.h->xk, io[i].x_u, io[i].x_p, it.s);
             if (rc2) it.rc = rc2;
         }
@@ -1892,6 +2043,18 @@ int stk_solve_batched(int count, stk_handle* const* hs, const stk_solver_params*
     for (int i = 0; i < count; ++i) {
         insts[i].info.solve_ms = ms;
         insts[i].info.status = insts[i].rc;
+        stk_handle* h = insts[i].h;
+        for (int y = 0; y < (int)h->sinfo.size(); ++y) {
+            stk_solve_info& f = h->sinfo[y];
+            f.solve_ms = ms;
+            switch (h->gst_host[y].state) {
+            case GM_CONVERGED: f.status = STK_OK; break;
+            case GM_MAXIT: f.status = STK_ERR_NOT_CONVERGED; break;
+            case GM_NONFINITE: f.status = STK_ERR_NONFINITE; break;
+            case GM_TIMEOUT: f.status = STK_ERR_TIMEOUT; break;
+            default: f.status = insts[i].rc == STK_OK ? STK_ERR_STATE : insts[i].rc;
+            }
+        }
         if (infos) infos[i] = insts[i].info;
     }
     return worst;
@@ -1918,6 +2081,8 @@ int stk_set_schedule(stk_handle* h, int precision, const stk_schedule* sc) {
         return fail(h, STK_ERR_ARG, "pair_level must be in 0..%d", (int)h->lev.size());
     if (sc->grid_level < 0 || sc->grid_level > (int)h->lev.size())
         return fail(h, STK_ERR_ARG, "grid_level must be in 0..%d", (int)h->lev.size());
+    if (h->nsl > 1 && sc->grid_level < sc->coarse_level)
+        return fail(h, STK_ERR_ARG, "a stacked batch has no persistent multi-block V-cycle (grid_level >= coarse_level)");
     clear_graphs(h);
     if (precision == STK_FP64) {
         h->lcoarse_d = sc->coarse_level;
@@ -1990,7 +2155,7 @@ int stk_autotune(stk_handle* h, int precision, stk_schedule* best, void* stream)
     const int threads[3] = {128, 256, 512};
     for (int lc = 0; lc <= nl; ++lc) {
         // the single-block kernel only pays on small levels
-        if (lc < nl && h->lev[lc].g.ncell > 65536) continue;
+        if (lc < nl && h->lev[lc].g.ncell / h->nsl > 65536) continue;
         // two-colour kernels from level 0, 1 or 2, or not at all (pair_level
         // = lc); the colour block size only matters below pair_level
         int pls[4], npl = 0;
@@ -2000,7 +2165,7 @@ int stk_autotune(stk_handle* h, int precision, stk_schedule* best, void* stream)
         // the single-block one (grid_level), or not at all (= lc)
         int gls[3], ngl = 0;
         gls[ngl++] = lc;
-        for (int d = 1; d <= 2 && lc - d >= 0; ++d)
+        for (int d = 1; d <= 2 && lc - d >= 0 && h->nsl == 1; ++d)
             if (h->lev[lc - d].g.ncell <= 262144) gls[ngl++] = lc - d;
         for (int k = 0; k < npl; ++k)
             for (int gi = 0; gi < ngl; ++gi)
@@ -2048,6 +2213,7 @@ long long stk_kernel_launches(const stk_handle* h) { return h ? h->nkern : -1; }
 int stk_gradient(stk_handle* h, const double* const* u, const double* const* lambda,
                  double* dL_dlogmu, double* dL_drho, void* stream) {
     if (!h) return STK_ERR_ARG;
+    if (h->nsl > 1) return fail(h, STK_ERR_ARG, "not available on a stacked batch");
     if (!h->coef_set) return fail(h, STK_ERR_STATE, "coefficients not set");
     if (h->bulk) return fail(h, STK_ERR_STATE, "the gradient is defined for the stress form without bulk viscosity");
     if (!u || !lambda || !dL_dlogmu || !dL_drho) return fail(h, STK_ERR_ARG, "null pointer");
@@ -2139,12 +2305,27 @@ int stk_wait_status(stk_handle* h, int reset) {
 }
 
 int stk_solve_history(const stk_handle* h, int kind, double* out, int cap) {
-    if (!h || (kind != 0 && kind != 1) || cap < 0) return STK_ERR_ARG;
-    const std::vector<double>& v = kind == 0 ? h->hist_true : h->hist_est;
+    return stk_stack_history(h, 0, kind, out, cap);
+}
+
+int stk_stack_history(const stk_handle* h, int instance, int kind, double* out, int cap) {
+    if (!h || (kind != 0 && kind != 1) || cap < 0 || instance < 0 || instance >= h->nsl) return STK_ERR_ARG;
+    const auto& all = kind == 0 ? h->hist_true : h->hist_est;
+    if (instance >= (int)all.size()) return 0;
+    const std::vector<double>& v = all[instance];
     if (out)
         for (int i = 0; i < cap && i < (int)v.size(); ++i) out[i] = v[i];
     return (int)v.size();
 }
+
+int stk_stack_info(const stk_handle* h, int instance, stk_solve_info* info) {
+    if (!h || !info || instance < 0 || instance >= h->nsl) return STK_ERR_ARG;
+    if (instance >= (int)h->sinfo.size()) return STK_ERR_STATE;
+    *info = h->sinfo[instance];
+    return STK_OK;
+}
+
+int stk_stack_count(const stk_handle* h) { return h ? h->nsl : STK_ERR_ARG; }
 
 int stk_remove_mean(stk_handle* h, const double* x_p, double* y_p, void* stream) {
     if (!h) return STK_ERR_ARG;
@@ -2155,7 +2336,7 @@ int stk_remove_mean(stk_handle* h, const double* x_p, double* y_p, void* stream)
     {
         Scope sc(h, PF_MEAN, 2.0 * sizeof(double) * nc, s, 4);
         cell_sum<double>(h, nc, x_p, h->dsc + DS_SUM + 6, s);
-        launch_copy_sub_mean<double>(nc, x_p, y_p, h->dsc + DS_SUM + 6, s);
+        sub_mean<double>(h, nc, x_p, y_p, h->dsc + DS_SUM + 6, s);
     }
     CKL();
     return STK_OK;

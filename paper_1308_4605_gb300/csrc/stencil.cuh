@@ -48,14 +48,24 @@ __device__ __forceinline__ void decode_cell(const Geom& g, int t, int q[3]) {
     q[2] = fdiv(r, g.fd_n1);
     q[1] = r - q[2] * g.n[1];
 }
-// t-th face of component a with (i + j + k) % 2 == parity; false past the end
+// The colour index i + j (+ k in 3D).  In 2D the third index numbers the
+// instances of a stacked batch and takes no part in the colouring, so each
+// instance is swept exactly as it would be alone.
+__device__ __forceinline__ int csum(const Geom& g, const int q[3]) {
+    return q[0] + q[1] + (g.dim == 3 ? q[2] : 0);
+}
+template <int DIM>
+__device__ __forceinline__ int csum(const int q[3]) {
+    return q[0] + q[1] + (DIM == 3 ? q[2] : 0);
+}
+// t-th face of component a with csum % 2 == parity; false past the end
 __device__ __forceinline__ bool decode_face_colour(const Geom& g, int a, int parity, int t, int q[3]) {
     const int half = (g.fe[a][0] + 1) >> 1;
     const int r = fdiv(t, g.fd_h0[a]);
     const int xh = t - r * half;
     q[2] = fdiv(r, g.fd_e1[a]);
     q[1] = r - q[2] * g.fe[a][1];
-    q[0] = 2 * xh + ((q[1] + q[2] + parity) & 1);
+    q[0] = 2 * xh + ((q[1] + (g.dim == 3 ? q[2] : 0) + parity) & 1);
     return q[0] < g.fe[a][0];
 }
 __device__ __forceinline__ void decode_cell_colour(const Geom& g, int parity, int t, int q[3]) {
@@ -64,7 +74,7 @@ __device__ __forceinline__ void decode_cell_colour(const Geom& g, int parity, in
     const int xh = t - r * half;
     q[2] = fdiv(r, g.fd_n1);
     q[1] = r - q[2] * g.n[1];
-    q[0] = 2 * xh + ((q[1] + q[2] + parity) & 1);
+    q[0] = 2 * xh + ((q[1] + (g.dim == 3 ? q[2] : 0) + parity) & 1);
 }
 __device__ __forceinline__ bool wall_face(const Geom& g, int a, const int q[3]) {
     return !g.per[a] && (q[a] == 0 || q[a] == g.n[a]);
@@ -448,7 +458,7 @@ __device__ __forceinline__ T vel_restrict_point(const Geom& gf, const int Q[3],
         for (int t0 = 0; t0 < 2; ++t0)
 #pragma unroll
             for (int t1 = 0; t1 < (TR::n == 2 ? 2 : 1); ++t1) {
-                int q[3] = {2 * Q[0], 2 * Q[1], DIM == 3 ? 2 * Q[2] : 0};
+                int q[3] = {2 * Q[0], 2 * Q[1], DIM == 3 ? 2 * Q[2] : Q[2]};
                 q[A] = step(gf, A, q[A], s);
                 q[TR::b0] += t0;
                 if (TR::n == 2) q[TR::b1] += t1;
@@ -501,7 +511,7 @@ __device__ __forceinline__ T vel_prolong_point(const Geom& gc, const int q[3],
     // coarse value at transverse position (j0, j1): one face (even) or the
     // sum of the two along A (odd; the 1/2 is in wo0, wn0)
     auto at = [&](int j0, int j1) -> T {
-        int Q[3] = {0, 0, 0};
+        int Q[3] = {0, 0, DIM == 3 ? 0 : q[2]};
         Q[A] = ca0;
         Q[TR::b0] = j0;
         if (TR::n == 2) Q[TR::b1] = j1;
@@ -567,7 +577,7 @@ __device__ __forceinline__ T cell_restrict_point(const Geom& gf, const int Q[3],
         for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
             for (int dx = 0; dx < 2; ++dx) {
-                int q[3] = {2 * Q[0] + dx, 2 * Q[1] + dy, (DIM == 3 ? 2 * Q[2] : 0) + dz};
+                int q[3] = {2 * Q[0] + dx, 2 * Q[1] + dy, (DIM == 3 ? 2 * Q[2] : Q[2]) + dz};
                 s += res[cidx(gf, q)];
             }
     return s * (DIM == 3 ? T(0.125) : T(0.25));

@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(ST) k_stress_faces(Geom g, Coef<double> C, int
     int q[3];
     decode_face(g, a, t, q);
     const int f = g.foff[a] + t;
-    if (wall_face(g, a, q) || (MODE == 1 && a == zl && ((q[0] + q[1] + q[2]) & 1))) {
+    if (wall_face(g, a, q) || (MODE == 1 && a == zl && (csum<DIM>(q) & 1))) {
         y[f] = 0.0;
         return;
     }

@@ -78,6 +78,10 @@ def _load():
     sig = {
         "stk_default_params": (None, [ctypes.POINTER(stk_solver_params)]),
         "stk_create": (I, [I, ctypes.POINTER(I), D, ctypes.POINTER(I), ctypes.POINTER(P)]),
+        "stk_create_stacked": (I, [I, ctypes.POINTER(I), D, ctypes.POINTER(I), I, ctypes.POINTER(P)]),
+        "stk_stack_count": (I, [P]),
+        "stk_stack_info": (I, [P, I, ctypes.POINTER(stk_solve_info)]),
+        "stk_stack_history": (I, [P, I, I, ctypes.POINTER(D), I]),
         "stk_destroy": (I, [P]),
         "stk_last_error": (ctypes.c_char_p, [P]),
         "stk_face_length": (ctypes.c_longlong, [P, I]),
@@ -123,7 +127,8 @@ def _load():
 
 
 _lib = _load()
-EXPORTED = ["stk_default_params", "stk_create", "stk_destroy", "stk_last_error", "stk_face_length",
+EXPORTED = ["stk_default_params", "stk_create", "stk_create_stacked", "stk_stack_count", "stk_stack_info",
+            "stk_stack_history", "stk_destroy", "stk_last_error", "stk_face_length",
             "stk_cell_length", "stk_set_coefficients", "stk_set_bulk_viscosity", "stk_apply_operator",
             "stk_apply_preconditioner", "stk_apply_preconditioner_params", "stk_velocity_vcycle", "stk_pressure_vcycle", "stk_solve",
             "stk_profile", "stk_profile_read", "stk_kernel_launches", "stk_pressure_vcycle_noalloc", "stk_remove_mean", "stk_set_graphs", "stk_graphs_in_use", "stk_widen", "stk_set_wait_budget", "stk_wait_status", "stk_solve_history", "stk_bounds_violations", "stk_bounds_selftest", "stk_gradient", "stk_backward_euler_rhs", "stk_subtract_boundary_terms", "stk_solve_batched", "stk_get_schedule", "stk_set_schedule", "stk_autotune"]
@@ -186,6 +191,33 @@ def stk_create(dim, n, h, bc):
     out = ctypes.c_void_p()
     _check(None, _lib.stk_create(int(dim), nn, float(h), bb, ctypes.byref(out)))
     return out
+
+
+def stk_create_stacked(dim, n, h, bc, count):
+    nn = (ctypes.c_int * 3)(*(list(n) + [1] * (3 - len(n))))
+    bb = (ctypes.c_int * 6)(*(list(bc) + [0] * (6 - len(bc))))
+    out = ctypes.c_void_p()
+    _check(None, _lib.stk_create_stacked(int(dim), nn, float(h), bb, int(count), ctypes.byref(out)))
+    return out
+
+
+def stk_stack_count(h):
+    return int(_lib.stk_stack_count(h))
+
+
+def stk_stack_info(h, instance):
+    info = stk_solve_info()
+    _check(h, _lib.stk_stack_info(h, int(instance), ctypes.byref(info)))
+    return info.as_dict()
+
+
+def stk_stack_history(h, instance, kind):
+    n = int(_lib.stk_stack_history(h, int(instance), int(kind), None, 0))
+    if n < 0:
+        raise StokesError(n, "stk_stack_history failed")
+    buf = (ctypes.c_double * max(n, 1))()
+    got = int(_lib.stk_stack_history(h, int(instance), int(kind), buf, n))
+    return [buf[i] for i in range(min(n, got))]
 
 
 def stk_destroy(h):
@@ -427,14 +459,26 @@ def stk_profile_read(h, k):
 
 # ------------------------------------------------------------ convenience
 class StokesSolver:
-    """Owns one stk_handle; methods take/return torch CUDA tensors."""
+    """Owns one stk_handle; methods take/return torch CUDA tensors.
 
-    def __init__(self, dim, n, bc, h=1.0):
+    count: a stacked batch of `count` 2D instances of the grid
+    (stk_create_stacked); every array then has the instances along its
+    leading axis (face_shape / cell_shape give (count, ny, nx)-shaped arrays)."""
+
+    def __init__(self, dim, n, bc, h=1.0, count=None):
         self.dim = int(dim)
-        self.n = tuple(list(n) + [1] * (3 - len(n)))
+        self.count = int(count) if count is not None else 1
+        self.n = tuple(list(n[:self.dim]) + [1] * (3 - self.dim))
+        if count is not None:
+            if self.dim != 2:
+                raise ValueError("stacked batches are 2D")
+            self.n = (self.n[0], self.n[1], self.count)
         self.bc = tuple(list(bc) + [0] * (6 - len(bc)))
         self.h = float(h)
-        self.handle = stk_create(dim, n, h, bc)
+        if count is not None:
+            self.handle = stk_create_stacked(dim, n[:2], h, bc, self.count)
+        else:
+            self.handle = stk_create(dim, n, h, bc)
 
     def close(self):
         if self.handle is not None and self.handle.value:
@@ -511,3 +555,7 @@ class StokesSolver:
             x_u, x_p = self.zeros(b_p.device)
         info = stk_solve(self.handle, p, b_u, b_p, x_u, x_p)
         return x_u, x_p, info
+
+    def instance_info(self, i):
+        """The last solve's record of instance i of a stacked batch."""
+        return stk_stack_info(self.handle, i)

@@ -25,8 +25,10 @@ def cache_path():
 def _key(solver, precision):
     import torch
     dev = torch.cuda.get_device_name(torch.cuda.current_device())
+    stack = getattr(solver, "count", 1)
     return f"s3|{dev}|{solver.dim}|{'x'.join(map(str, solver.n[:solver.dim]))}|" \
-           f"{','.join(map(str, solver.bc[:2 * solver.dim]))}|{precision}"
+           f"{','.join(map(str, solver.bc[:2 * solver.dim]))}|{precision}" + \
+           (f"|stack{stack}" if stack > 1 else "")
 
 
 def _load(path):

@@ -2,7 +2,8 @@
 started by tests/test_gpu_bounds.py): the operator, both V-cycles, P1..P5 and
 FP64 / mixed solves on small and odd-shaped grids, every boundary mix, with
 the two-colour kernels and the single-block coarse kernel on every level,
-then prints the number of out-of-range indices the kernels met (JSON)."""
+and the same on stacked 2D batches, then prints the number of out-of-range
+indices the kernels met (JSON)."""
 import json
 import os
 import sys
@@ -23,6 +24,9 @@ CASES = [
     (3, (8, 8, 4), (W, W, P, P, F, F)), (3, (16, 32, 8), (F, W, P, P, W, W)),
     (3, (32, 16, 64), (P, P, W, F, W, W)),
 ]
+
+STACKED = [((4, 4), (P, P, P, P)), ((2, 8), (W, W, P, P)), ((16, 4), (W, F, F, W)),
+           ((64, 32), (F, W, W, F))]
 
 
 def main():
@@ -52,6 +56,34 @@ def main():
                 for which in (1, 2, 3, 4, 5):
                     sv.apply_preconditioner(which, bu, bp, precision=prec)
                 xu, xp, info = sv.solve(bu, bp, precond=pr.precond, precision=prec, maxit=400)
+                rec[f"p{prec}_lc{lc}_pl{pl}"] = [info["iterations"], info["true_residual"]]
+        torch.cuda.synchronize()
+        sv.close()
+        out["cases"].append(rec)
+    # stacked 2D batches (three instances of each grid along a third axis)
+    for n, bc in STACKED:
+        prs = [wl.generic(2, n, bc, theta=1.0, rho_contrast=10.0, mu_contrast=30.0 + 20 * i, seed=5 + i)
+               for i in range(3)]
+        pr = prs[0]
+        sv = S.StokesSolver(2, pr.n[:2], pr.bc[:4], pr.h, count=3)
+        stack = lambda arrs, shape: t(np.stack(arrs)).reshape(shape)
+        sv.set_coefficients(stack([q.rho for q in prs], sv.cell_shape()),
+                            stack([q.mu for q in prs], sv.cell_shape()), pr.theta)
+        bu = [stack([q.b_u[a] for q in prs], sv.face_shape(a)) for a in range(2)]
+        bp = stack([q.b_p for q in prs], sv.cell_shape())
+        nlev = 1
+        m = min(pr.n[:2])
+        while m > 2:
+            m //= 2
+            nlev += 1
+        rec = {"dim": 2, "n": n, "bc": bc, "stacked": 3}
+        for prec in (0, 1):
+            for lc, pl in ((nlev, nlev), (nlev, 0), (0, 0)):
+                S.stk_set_schedule(sv.handle, prec, lc, 128, pl)
+                sv.apply_operator(bu, bp)
+                for which in (1, 2, 3, 4, 5):
+                    sv.apply_preconditioner(which, bu, bp, precision=prec)
+                xu, xp, info = sv.solve(bu, bp, precond=1, precision=prec, maxit=400)
                 rec[f"p{prec}_lc{lc}_pl{pl}"] = [info["iterations"], info["true_residual"]]
         torch.cuda.synchronize()
         sv.close()
