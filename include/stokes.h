@@ -314,9 +314,12 @@ int stk_remove_mean(stk_handle* h, const double* x_p, double* y_p, void* stream)
 
 /* Batched solve: count independent systems, each on its own handle (any
  * grid size, boundary conditions and coefficients), solved together with
- * the same parameters.  The GMRES iterations of all instances advance in
- * lockstep (one host synchronisation per GMRES phase -- stopping test,
- * first basis vector, each Arnoldi step, update -- for the whole batch)
+ * the same parameters.  A batch of at most 8 handles (e.g. one stacked
+ * handle per grid size) runs each handle's GMRES cycles as graph launches,
+ * every handle at its own pace (the host waits once per cycle and handle);
+ * larger batches advance in lockstep (one host synchronisation per GMRES
+ * phase -- stopping test, first basis vector, each Arnoldi step, update --
+ * for the whole batch)
  * and each instance's kernels and preconditioner graphs run on its handle's
  * own stream, forked from and joined back into `stream`, so the instances
  * share the GPU.  io[i] holds instance i's right-hand side and its initial

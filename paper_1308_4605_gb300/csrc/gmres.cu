@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(256) k_scal_dev(int n, double* __restrict__ x,
                                                   const double* __restrict__ s) {
     pdl_entry();
     const double a = *s;
-    for (int t = blockIdx.x * 256 + threadIdx.x; t < n; t += KRY_BLOCKS * 256) x[t] *= a;
+    for (int t = blockIdx.x * 256 + threadIdx.x; t < n; t += gridDim.x * 256) x[t] *= a;
 }
 
 // one block with a thread per instance (whole warps)
@@ -285,7 +285,8 @@ void launch_gm_finish(GmState* st, int nsl, cudaStream_t s) {
     launch_pdl(k_gm_finish, dim3(1), ctl_block(nsl), s, st, nsl);
 }
 void launch_scale_dev(int n, double* x, const double* a, cudaStream_t s) {
-    launch_pdl(k_scal_dev, dim3(KRY_BLOCKS), dim3(256), s, n, x, a);
+    const int nb = (n + 256 * 8 - 1) / (256 * 8);   // about eight values per thread
+    launch_pdl(k_scal_dev, dim3(nb < 1 ? 1 : (nb > KRY_BLOCKS ? KRY_BLOCKS : nb)), dim3(256), s, n, x, a);
 }
 
 }  // namespace stk

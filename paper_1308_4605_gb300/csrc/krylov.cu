@@ -6,9 +6,10 @@
 //
 // These are streaming kernels over packed Stokes vectors of N doubles.  The
 // number of basis vectors is a template parameter (dispatched at run time),
-// loads are 16-byte, the grid is a fixed KRY_BLOCKS blocks (8 per SM) and
-// every reduction sums its block partials in a fixed order, so results are
-// bitwise reproducible.  On GB300 the FP64 FMA rate (about 1.2 TFLOP/s) caps a
+// loads are 16-byte, the grid is a function of the vector length alone
+// (about four pairs of values per thread, at most KRY_BLOCKS blocks = 8 per
+// SM; kry_blocks) and every reduction sums its block partials in a fixed
+// order, so results are bitwise reproducible.  On GB300 the FP64 FMA rate (about 1.2 TFLOP/s) caps a
 // pass at about one FMA per 8 bytes read.
 #include "internal.cuh"
 
@@ -31,7 +32,7 @@ __device__ __forceinline__ double wsum(double v) {
 // Reduce NV per-thread values over the block; value i of block b goes to
 // part[i * stride + b].
 template <int NV>
-__device__ __forceinline__ void block_sums(const double (&v)[NV], double* part, int stride = KRY_BLOCKS) {
+__device__ __forceinline__ void block_sums(const double (&v)[NV], double* part, int stride) {
     __shared__ double sh[NV][KT / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -48,13 +49,14 @@ __device__ __forceinline__ void block_sums(const double (&v)[NV], double* part, 
     }
 }
 
-// out[k] = sum_b part[k * KRY_BLOCKS + b], one block per k, fixed order.
-__global__ void __launch_bounds__(KT) k_final_multi(const double* __restrict__ part, double* out) {
+// out[k] = sum_b part[k * nb + b] over the nb block partials, one block per
+// k, fixed order.
+__global__ void __launch_bounds__(KT) k_final_multi(const double* __restrict__ part, double* out, int nb) {
     pdl_entry();
     __shared__ double sh[KT / 32];
     const int k = blockIdx.x;
     double s = 0.0;
-    for (int b = threadIdx.x; b < KRY_BLOCKS; b += KT) s += part[k * KRY_BLOCKS + b];
+    for (int b = threadIdx.x; b < nb; b += KT) s += part[k * nb + b];
     s = wsum(s);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
     __syncthreads();
@@ -76,7 +78,7 @@ __global__ void __launch_bounds__(KT) k_mdot(int n, PtrArr V, const double* __re
     for (int i = 0; i < J + 2; ++i) acc[i] = 0.0;
     const int n2 = n >> 1;
     const double2* w2 = reinterpret_cast<const double2*>(w);
-    for (int t = blockIdx.x * KT + threadIdx.x; t < n2; t += KRY_BLOCKS * KT) {
+    for (int t = blockIdx.x * KT + threadIdx.x; t < n2; t += gridDim.x * KT) {
         const double2 a = w2[t];
 #pragma unroll
         for (int i = 0; i <= J; ++i) {
@@ -93,7 +95,7 @@ __global__ void __launch_bounds__(KT) k_mdot(int n, PtrArr V, const double* __re
         for (int i = 0; i <= J; ++i) acc[i] = fma(a, static_cast<const double*>(V.p[i])[n - 1], acc[i]);
         acc[J + 1] = fma(a, a, acc[J + 1]);
     }
-    block_sums<J + 2>(acc, part);
+    block_sums<J + 2>(acc, part, gridDim.x);
 }
 
 // One modified Gram-Schmidt step: w -= h[k] v_k, then the block partials
@@ -109,7 +111,7 @@ __global__ void __launch_bounds__(KT) k_mgs_step(int n, const double* __restrict
     double2* w2 = reinterpret_cast<double2*>(w);
     const double2* v2 = reinterpret_cast<const double2*>(vk);
     const double2* u2 = reinterpret_cast<const double2*>(u);
-    for (int t = blockIdx.x * KT + threadIdx.x; t < n2; t += KRY_BLOCKS * KT) {
+    for (int t = blockIdx.x * KT + threadIdx.x; t < n2; t += gridDim.x * KT) {
         double2 a = w2[t];
         const double2 v = v2[t];
         a.x = fma(-hk, v.x, a.x);
@@ -124,7 +126,7 @@ __global__ void __launch_bounds__(KT) k_mgs_step(int n, const double* __restrict
         w[n - 1] = a;
         s[0] = fma(a, u ? u[n - 1] : a, s[0]);
     }
-    block_sums<1>(s, part);
+    block_sums<1>(s, part, gridDim.x);
 }
 
 template <typename TV> struct Vec2;
@@ -142,7 +144,7 @@ __global__ void __launch_bounds__(KT) k_comb(int n, PtrArr V, const double* __re
     for (int i = 0; i < K; ++i) yy[i] = y[i];
     const int n2 = n >> 1;
     double2* x2 = reinterpret_cast<double2*>(x);
-    for (int t = blockIdx.x * KT + threadIdx.x; t < n2; t += KRY_BLOCKS * KT) {
+    for (int t = blockIdx.x * KT + threadIdx.x; t < n2; t += gridDim.x * KT) {
         double2 a = x2[t];
 #pragma unroll
         for (int i = 0; i < K; ++i) {
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(KT) k_comb_dev(int n, PtrArr V, const double* 
     for (int i = 0; i < K; ++i) yy[i] = i < k ? y[i] : 0.0;
     const int n2 = n >> 1;
     double2* x2 = reinterpret_cast<double2*>(x);
-    for (int t = blockIdx.x * KT + threadIdx.x; t < n2; t += KRY_BLOCKS * KT) {
+    for (int t = blockIdx.x * KT + threadIdx.x; t < n2; t += gridDim.x * KT) {
         double2 a = x2[t];
 #pragma unroll
         for (int i = 0; i < K; ++i) {
@@ -199,7 +201,7 @@ __global__ void __launch_bounds__(KT) k_scal(int n, double* __restrict__ x, doub
                                              const double* __restrict__ nrm2) {
     pdl_entry();
     const double s = nrm2 ? 1.0 / sqrt(*nrm2) : a;
-    for (int t = blockIdx.x * KT + threadIdx.x; t < n; t += KRY_BLOCKS * KT) x[t] *= s;
+    for (int t = blockIdx.x * KT + threadIdx.x; t < n; t += gridDim.x * KT) x[t] *= s;
 }
 
 // ------------------------------------------------------------ stacked batches
@@ -251,7 +253,7 @@ __global__ void __launch_bounds__(KT) k_mdot_sl(SliceMap m, PtrArr V, const doub
     for (int i = 0; i < J + 2; ++i) acc[i] = 0.0;
     const int n2 = m.nl >> 1;
     const double2* w2 = reinterpret_cast<const double2*>(w);
-    for (int t = blockIdx.x * KT + threadIdx.x; t < n2; t += KRY_BLOCKS * KT) {
+    for (int t = blockIdx.x * KT + threadIdx.x; t < n2; t += gridDim.x * KT) {
         const int p = sl_pair(m, y, t);
         const double2 a = w2[p];
 #pragma unroll
@@ -279,7 +281,7 @@ __global__ void __launch_bounds__(KT) k_mgs_step_sl(SliceMap m, const double* __
     double2* w2 = reinterpret_cast<double2*>(w);
     const double2* v2 = reinterpret_cast<const double2*>(vk);
     const double2* u2 = reinterpret_cast<const double2*>(u);
-    for (int t = blockIdx.x * KT + threadIdx.x; t < n2; t += KRY_BLOCKS * KT) {
+    for (int t = blockIdx.x * KT + threadIdx.x; t < n2; t += gridDim.x * KT) {
         const int p = sl_pair(m, y, t);
         double2 a = w2[p];
         const double2 v = v2[p];
@@ -350,7 +352,7 @@ __global__ void __launch_bounds__(KT) k_sum_f32x4_sl(int n, const float* __restr
     const int n4 = n >> 2;
     const float4* x4 = reinterpret_cast<const float4*>(xs);
     double acc[1] = {0.0};
-    for (int i = blockIdx.x * KT + threadIdx.x; i < n4; i += KRY_BLOCKS * KT) {
+    for (int i = blockIdx.x * KT + threadIdx.x; i < n4; i += gridDim.x * KT) {
         const float4 v = x4[i];
         acc[0] += double((v.x + v.y) + (v.z + v.w));
     }
@@ -358,8 +360,14 @@ __global__ void __launch_bounds__(KT) k_sum_f32x4_sl(int n, const float* __restr
     block_sums<1>(acc, part + (size_t)blockIdx.y * nbu, nbu);
 }
 
-int used_blocks(int items) {
-    const int b = (items + KT - 1) / KT;
+// Blocks of a pass over `items` loads (pairs of doubles, or float4): about
+// four per thread, at most KRY_BLOCKS.  A function of one instance's vector
+// length alone, so a stacked batch partitions each instance exactly as a
+// single handle does.  (A fixed KRY_BLOCKS grid left most threads of a
+// small vector with one load or none and made per-block overhead the cost.)
+int kry_blocks(int items) {
+    constexpr int PER_THREAD = 4;
+    const int b = (items + KT * PER_THREAD - 1) / (KT * PER_THREAD);
     return b < 1 ? 1 : (b > KRY_BLOCKS ? KRY_BLOCKS : b);
 }
 
@@ -380,19 +388,20 @@ __global__ void __launch_bounds__(KT) k_sum_f32x4(int n, const float* __restrict
     const int n4 = n >> 2;
     const float4* x4 = reinterpret_cast<const float4*>(x);
     double acc[1] = {0.0};
-    for (int i = blockIdx.x * KT + threadIdx.x; i < n4; i += KRY_BLOCKS * KT) {
+    for (int i = blockIdx.x * KT + threadIdx.x; i < n4; i += gridDim.x * KT) {
         const float4 v = x4[i];
         acc[0] += double((v.x + v.y) + (v.z + v.w));
     }
     if (blockIdx.x == 0 && threadIdx.x < (n & 3)) acc[0] += double(x[4 * n4 + threadIdx.x]);
-    block_sums<1>(acc, part);
+    block_sums<1>(acc, part, gridDim.x);
 }
 
 }  // namespace
 
 void launch_sum_f32x4(int n, const float* x, double* scratch, double* out, cudaStream_t s) {
-    launch_pdl(k_sum_f32x4, dim3(KRY_BLOCKS), dim3(KT), s, n, x, scratch);
-    launch_pdl(k_final_multi, dim3(1), dim3(KT), s, scratch, out);
+    const int nb = kry_blocks(n >> 2);
+    launch_pdl(k_sum_f32x4, dim3(nb), dim3(KT), s, n, x, scratch);
+    launch_pdl(k_final_multi, dim3(1), dim3(KT), s, scratch, out, nb);
 }
 
 #define STK_J_CASES(X) \
@@ -402,21 +411,22 @@ void launch_sum_f32x4(int n, const float* x, double* scratch, double* out, cudaS
 void launch_multidot(int n, int j, const double* const* V, const double* w, double* scratch,
                      double* h, cudaStream_t s) {
     PtrArr pa = pack(reinterpret_cast<const void* const*>(V), j + 1);
+    const int nb = kry_blocks(n >> 1);
     switch (j) {
-    case -1: launch_pdl(k_mdot<-1>, dim3(KRY_BLOCKS), dim3(KT), s, n, pa, w, scratch); break;
-#define X(J) case J: launch_pdl(k_mdot<J>, dim3(KRY_BLOCKS), dim3(KT), s, n, pa, w, scratch); break;
+    case -1: launch_pdl(k_mdot<-1>, dim3(nb), dim3(KT), s, n, pa, w, scratch); break;
+#define X(J) case J: launch_pdl(k_mdot<J>, dim3(nb), dim3(KT), s, n, pa, w, scratch); break;
     STK_J_CASES(X)
 #undef X
     default: return;
     }
-    launch_pdl(k_final_multi, dim3(j + 2), dim3(KT), s, scratch, h);
+    launch_pdl(k_final_multi, dim3(j + 2), dim3(KT), s, scratch, h, nb);
 }
 
 template <typename TV>
 void launch_combine(int n, int k, const TV* const* V, const double* y, double* x, cudaStream_t s) {
     PtrArr pa = pack(reinterpret_cast<const void* const*>(V), k);
     switch (k - 1) {
-#define X(J) case J: launch_pdl(k_comb<J + 1, TV>, dim3(KRY_BLOCKS), dim3(KT), s, n, pa, y, x); break;
+#define X(J) case J: launch_pdl(k_comb<J + 1, TV>, dim3(kry_blocks(n >> 1)), dim3(KT), s, n, pa, y, x); break;
     STK_J_CASES(X)
 #undef X
     default: return;
@@ -428,7 +438,7 @@ void launch_combine_dev(int n, int m, const TV* const* V, const double* y, const
                         cudaStream_t s) {
     PtrArr pa = pack(reinterpret_cast<const void* const*>(V), m);
     switch (m - 1) {
-#define X(J) case J: launch_pdl(k_comb_dev<J + 1, TV>, dim3(KRY_BLOCKS), dim3(KT), s, n, pa, y, k, x); break;
+#define X(J) case J: launch_pdl(k_comb_dev<J + 1, TV>, dim3(kry_blocks(n >> 1)), dim3(KT), s, n, pa, y, k, x); break;
     STK_J_CASES(X)
 #undef X
     default: return;
@@ -437,13 +447,14 @@ void launch_combine_dev(int n, int m, const TV* const* V, const double* y, const
 
 void launch_mgs_step(int n, const double* vk, const double* u, const double* h, int k, double* w,
                      double* scratch, double* out, cudaStream_t s) {
-    launch_pdl(k_mgs_step, dim3(KRY_BLOCKS), dim3(KT), s, n, vk, u, h, k, w, scratch);
-    launch_pdl(k_final_multi, dim3(1), dim3(KT), s, scratch, out);
+    const int nb = kry_blocks(n >> 1);
+    launch_pdl(k_mgs_step, dim3(nb), dim3(KT), s, n, vk, u, h, k, w, scratch);
+    launch_pdl(k_final_multi, dim3(1), dim3(KT), s, scratch, out, nb);
 }
 
 void launch_sum_f32x4_sl(int n, int nsl, const float* x, double* scratch, double* out, int ostride,
                          cudaStream_t s) {
-    const int nbu = used_blocks(n >> 2);
+    const int nbu = kry_blocks(n >> 2);
     launch_pdl(k_sum_f32x4_sl, dim3(nbu, nsl), dim3(KT), s, n, x, scratch, nbu);
     launch_pdl(k_final_multi_sl, dim3(1, nsl), dim3(KT), s, scratch, out, nbu, 1, ostride);
 }
@@ -451,7 +462,7 @@ void launch_sum_f32x4_sl(int n, int nsl, const float* x, double* scratch, double
 void launch_multidot_sl(const SliceMap& m, int nsl, int j, const double* const* V, const double* w,
                         double* scratch, double* h, int hstride, cudaStream_t s) {
     PtrArr pa = pack(reinterpret_cast<const void* const*>(V), j + 1);
-    const int nbu = used_blocks(m.nl >> 1);
+    const int nbu = kry_blocks(m.nl >> 1);
     const dim3 gr(nbu, nsl);
     switch (j) {
     case -1: launch_pdl(k_mdot_sl<-1>, gr, dim3(KT), s, m, pa, w, scratch, nbu); break;
@@ -466,7 +477,7 @@ void launch_multidot_sl(const SliceMap& m, int nsl, int j, const double* const* 
 void launch_mgs_step_sl(const SliceMap& m, int nsl, const double* vk, const double* u, const double* h,
                         int hstride, int k, double* w, double* scratch, double* out, int ostride,
                         cudaStream_t s) {
-    const int nbu = used_blocks(m.nl >> 1);
+    const int nbu = kry_blocks(m.nl >> 1);
     launch_pdl(k_mgs_step_sl, dim3(nbu, nsl), dim3(KT), s, m, vk, u, h, hstride, k, w, scratch, nbu);
     launch_pdl(k_final_multi_sl, dim3(1, nsl), dim3(KT), s, scratch, out, nbu, 1, ostride);
 }
@@ -475,7 +486,7 @@ template <typename TV>
 void launch_combine_dev_sl(const SliceMap& m, int nsl, int mmax, const TV* const* V, const GmState* st,
                            double* x, cudaStream_t s) {
     PtrArr pa = pack(reinterpret_cast<const void* const*>(V), mmax);
-    const dim3 gr(used_blocks(m.nl >> 1), nsl);
+    const dim3 gr(kry_blocks(m.nl >> 1), nsl);
     switch (mmax - 1) {
 #define X(J) case J: launch_pdl(k_comb_dev_sl<J + 1, TV>, gr, dim3(KT), s, m, pa, st, x); break;
     STK_J_CASES(X)
@@ -485,15 +496,15 @@ void launch_combine_dev_sl(const SliceMap& m, int nsl, int mmax, const TV* const
 }
 
 void launch_scale_dev_sl(const SliceMap& m, int nsl, double* x, const GmState* st, int j, cudaStream_t s) {
-    launch_pdl(k_scal_dev_sl, dim3(used_blocks(m.nl >> 1), nsl), dim3(KT), s, m, x, st, j);
+    launch_pdl(k_scal_dev_sl, dim3(kry_blocks(m.nl >> 1), nsl), dim3(KT), s, m, x, st, j);
 }
 
 void launch_scale_inv_sqrt(int n, double* x, const double* nrm2, cudaStream_t s) {
-    launch_pdl(k_scal, dim3(KRY_BLOCKS), dim3(KT), s, n, x, 0.0, nrm2);
+    launch_pdl(k_scal, dim3(kry_blocks((n + 1) >> 1)), dim3(KT), s, n, x, 0.0, nrm2);
 }
 
 void launch_scale(int n, double* x, double a, cudaStream_t s) {
-    launch_pdl(k_scal, dim3(KRY_BLOCKS), dim3(KT), s, n, x, a, nullptr);
+    launch_pdl(k_scal, dim3(kry_blocks((n + 1) >> 1)), dim3(KT), s, n, x, a, nullptr);
 }
 
 template void launch_combine<double>(int, int, const double* const*, const double*, double*,

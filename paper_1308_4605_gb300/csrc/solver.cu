@@ -17,6 +17,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -149,6 +150,7 @@ struct stk_handle {
     cudaStream_t cap = nullptr;    // private stream used for capture only
     cudaStream_t run = nullptr;    // this handle's stream inside a batched solve
     cudaEvent_t join = nullptr;    // marks the end of its work in a batched solve
+    cudaEvent_t cyc = nullptr;     // marks the end of a GMRES cycle (header read included)
     // graphs of one GMRES cycle (conditional nodes gate its phases), keyed by
     // (precond, flexible, m, nu, ncoarse, cycles); kernels per phase
     struct CycleGraph {
@@ -178,6 +180,8 @@ struct stk_handle {
 namespace {
 
 constexpr int NDSC = 128;     // device scalar slots
+// batches of at most this many handles run one cycle graph per handle
+constexpr int BATCH_CYCLE_GRAPHS = 8;
 // slots of h->dsc
 constexpr int DS_SUM = 0;     // mean removal sums
 constexpr int DS_H = 8;       // Arnoldi column h[0..m+1]
@@ -1277,8 +1281,9 @@ void zero_instance(stk_handle* h, double* x, int y, cudaStream_t s) {
 // Stopping rule: ||b - M x|| <= rtol ||b||, checked at the start of every
 // cycle; inside a cycle the Arnoldi estimate must fall to rtol ||b||
 // (flexible) or to its start value times rtol ||b|| / ||b - M x|| (left).
-// With cycle_graphs (a single solve, graphs on, profiling off) each cycle is
-// one graph launch and the host synchronises once per cycle; otherwise the
+// With cycle_graphs (a single solve or a small batch, graphs on, profiling
+// off) each cycle of each instance is one graph launch and the host waits
+// once per cycle and instance, each instance at its own pace; otherwise the
 // host gates the phases of all instances together, one synchronisation per
 // phase for the whole batch, each phase one graph launch.
 void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm, bool cycle_graphs) {
@@ -1337,7 +1342,57 @@ void gmres_lockstep(std::vector<Inst>& insts, const stk_solver_params& prm, bool
         it->cg = &f->second;
     }
     auto open_ = [](Inst* it, int slot) { return it->h->gcond_host[slot] != 0; };
-    while (true) {
+    bool all_graphs = cycle_graphs;
+    for (auto& it : insts)
+        if (!it.done && !it.cg) all_graphs = false;
+    if (all_graphs) {
+        // Every instance advances on its own: a cycle graph launch, the read
+        // of its records and an event; the host polls the events and starts
+        // an instance's next cycle as soon as its last one has ended, so a
+        // small instance never waits for a large one.
+        auto launch = [](Inst* it) {
+            cudaError_t e = cudaGraphLaunch(it->cg->exec, it->s);
+            if (e != cudaSuccess) {
+                finish(it, fail(it->h, STK_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e)));
+                return;
+            }
+            read_header(it);
+            cudaEventRecord(it->h->cyc, it->s);
+        };
+        std::vector<Inst*> pending;
+        for (auto& it : insts)
+            if (!it.done) {
+                launch(&it);
+                if (!it.done) pending.push_back(&it);
+            }
+        Nvtx range("gmres cycles");
+        while (!pending.empty()) {
+            bool moved = false;
+            for (size_t i = 0; i < pending.size();) {
+                Inst* it = pending[i];
+                const cudaError_t q = cudaEventQuery(it->h->cyc);
+                if (q == cudaErrorNotReady) {
+                    ++i;
+                    continue;
+                }
+                moved = true;
+                if (q != cudaSuccess) {
+                    finish(it, fail(it->h, STK_ERR_CUDA, "cycle: %s", cudaGetErrorString(q)));
+                } else {
+                    absorb_cycle(it, prm, mp);
+                    if (!it->done) launch(it);
+                }
+                if (it->done) {
+                    pending[i] = pending.back();
+                    pending.pop_back();
+                } else {
+                    ++i;
+                }
+            }
+            if (!moved) std::this_thread::yield();
+        }
+    }
+    while (!all_graphs) {
         act.clear();
         for (auto& it : insts)
             if (!it.done) act.push_back(&it);
@@ -1675,6 +1730,7 @@ int create_handle(int dim, const int* n, double hh, const int* bc, int nsl, stk_
     CKC(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
     CKC(cudaStreamCreateWithFlags(&h->run, cudaStreamNonBlocking));
     CKC(cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming));
+    CKC(cudaEventCreateWithFlags(&h->cyc, cudaEventDisableTiming));
     {   // level descriptors of the single-block coarse-level kernel
         const int nl = (int)h->lev.size();
         h->lcoarse_d = h->lcoarse_f = nl;
@@ -1710,6 +1766,7 @@ int stk_destroy(stk_handle* h) {
     if (h->cap) cudaStreamDestroy(h->cap);
     if (h->run) cudaStreamDestroy(h->run);
     if (h->join) cudaEventDestroy(h->join);
+    if (h->cyc) cudaEventDestroy(h->cyc);
     for (void* p : h->allocs) cudaFree(p);
     if (h->hpin) cudaFreeHost(h->hpin);
     if (h->gst_host) cudaFreeHost(h->gst_host);
@@ -2000,10 +2057,13 @@ int stk_solve_batched(int count, stk_handle* const* hs, const stk_solver_params*
         CK(cudaEventCreate(&e1));
         CK(cudaEventRecord(e0, us));
     }
-    // one solve: the caller's stream, each GMRES cycle one graph launch;
-    // several: each instance on its handle's own stream, the cycles' phases
-    // gated by the host for the whole batch at once (measured faster for the
-    // batched workload than one cycle graph per instance)
+    // one solve: the caller's stream, each GMRES cycle one graph launch.
+    // Several: each instance on its handle's own stream.  Up to
+    // BATCH_CYCLE_GRAPHS instances (e.g. one stacked handle per grid size)
+    // each run their cycles as graph launches independently of the others;
+    // larger batches gate the cycles' phases by the host for the whole batch
+    // at once (measured faster for 64 single-instance handles than 64
+    // independent cycle graphs)
     const bool fork = count > 1;
     for (int i = 0; i < count; ++i) {
         Inst& it = insts[i];
@@ -2014,7 +2074,7 @@ int stk_solve_batched(int count, stk_handle* const* hs, const stk_solver_params*
         if (!rc) rc = gather(it.h, io[i].x_u, io[i].x_p, it.h->xk, it.s);
         if (rc) finish(&it, rc);
     }
-    gmres_lockstep(insts, prm, count == 1);
+    gmres_lockstep(insts, prm, count <= BATCH_CYCLE_GRAPHS);
     int worst = STK_OK;
     for (int i = 0; i < count; ++i) {
         Inst& it = insts[i];
