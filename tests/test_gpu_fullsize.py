@@ -11,7 +11,9 @@ point-by-point oracle stencils (oracle/pointwise.py), must be below
 1e-10 ||b||:
   * 3D 128^3 periodic unsteady (P1), FP64 and mixed;
   * every instance of the 64-instance batched workload (2D {64..512}^2
-    periodic, P1, mixed), solved in one stk_solve_batched call;
+    periodic, P1, mixed), solved in one stk_solve_batched call, once with one
+    handle per instance and once as the benchmark's stacked batches (one
+    stacked handle per grid size, FP64 and mixed);
   * the steady no-slip adjoint workload's forward solve (P2) at 128^3, FP64
     and mixed (the oracle's sparse matrices at 256^3 outgrow the host; the
     256^3 solves are checked by the full residual alone).
@@ -138,6 +140,45 @@ def test_full_batched_workload_matches_oracle(S, oracle):
     for i, pr in enumerate(prs):
         g, x = _pack(pr, xus[i], xps[i])
         _compare(g, pr, x, oracle["c4"][i].get(timeout=1800))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_batched_workload_stacked_matches_oracle(S, oracle, precision):
+    """The same 64 instances as four stacked handles (16 x 64^2, 23 x 128^2,
+    11 x 256^2, 14 x 512^2) solved in one stk_solve_batched call, the form
+    the benchmark times."""
+    from paper_1308_4605_gb300 import tuning
+    sizes = wl.config_c4_sizes()
+    prs = [wl.config_c4_instance(i, n) for i, n in enumerate(sizes)]
+    groups = []
+    for n in sorted(set(sizes)):
+        idx = [i for i, s in enumerate(sizes) if s == n]
+        p0 = prs[idx[0]]
+        sv = S.StokesSolver(2, p0.n[:2], p0.bc[:4], p0.h, count=len(idx))
+        stk = lambda arrs, shape: _t(np.stack(arrs)).reshape(shape)
+        sv.set_coefficients(stk([prs[i].rho for i in idx], sv.cell_shape()),
+                            stk([prs[i].mu for i in idx], sv.cell_shape()), p0.theta)
+        tuning.tune(sv, precision)
+        bu = [stk([prs[i].b_u[a] for i in idx], sv.face_shape(a)) for a in range(2)]
+        bp = stk([prs[i].b_p for i in idx], sv.cell_shape())
+        xu, xp = sv.zeros()
+        groups.append((idx, sv, bu, bp, xu, xp))
+    p = S.stk_default_params()
+    p.precision = precision
+    p.maxit = 3000
+    S.stk_solve_batched([gr[1].handle for gr in groups], p, [gr[2] for gr in groups],
+                        [gr[3] for gr in groups], [gr[4] for gr in groups], [gr[5] for gr in groups])
+    recs = {}
+    for idx, sv, _, _, _, _ in groups:
+        for k, i in enumerate(idx):
+            recs[i] = sv.instance_info(k)
+        sv.close()
+    for i in range(len(sizes)):
+        assert recs[i]["converged"] and recs[i]["true_residual"] <= 1e-10, (i, recs[i])
+    for idx, _, _, _, xu, xp in groups:
+        for k, i in enumerate(idx):
+            g, x = _pack(prs[i], [v[k] for v in xu], xp[k])
+            _compare(g, prs[i], x, oracle["c4"][i].get(timeout=1800))
 
 
 @pytest.mark.parametrize("precision", [0, 1])
