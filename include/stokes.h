@@ -349,8 +349,12 @@ int stk_solve_batched(int count, stk_handle* const* hs, const stk_solver_params*
  * between the stages instead of kernel boundaries; the levels from
  * coarse_level on are then done by one of its blocks); grid_level >=
  * coarse_level switches it off.  Each barrier wait is bounded (see
- * stk_set_wait_budget).
- * 0 <= pair_level, coarse_level, grid_level <= number of levels.  The arithmetic does
+ * stk_set_wait_budget).  Levels cluster_level and coarser, down to
+ * coarse_level, run as one thread-block cluster (up to 16 blocks of 1024
+ * threads on one GPC, hardware cluster barriers between the stages; it takes
+ * precedence over grid_level); cluster_level >= coarse_level switches it off.
+ * Stacked handles use neither.
+ * 0 <= pair_level, coarse_level, grid_level, cluster_level <= number of levels.  The arithmetic does
  * not depend on the schedule, except that with coarse_level = 0 the finest
  * level's FP64 residual is evaluated point by point instead of through the
  * stresses of the grid kernels (equal up to rounding).  stk_autotune times one velocity + one
@@ -362,6 +366,7 @@ typedef struct {
     int threads;
     int pair_level;
     int grid_level;
+    int cluster_level;
 } stk_schedule;
 int stk_get_schedule(const stk_handle* h, int precision, stk_schedule* out);
 int stk_set_schedule(stk_handle* h, int precision, const stk_schedule* sc);

@@ -19,6 +19,8 @@
 #include "stencil.cuh"
 #include "../../include/stokes.h"
 
+#include <algorithm>
+
 namespace stk {
 namespace {
 
@@ -103,6 +105,26 @@ struct GridSync {
         }
         __syncthreads();
         return ok != 0;
+    }
+};
+
+// ClusterSync: the CTAs of one thread-block cluster (the whole grid is one
+// cluster of at most 16 CTAs, resident together on one GPC) with the
+// hardware cluster barrier between stages.  The stages exchange data through
+// global memory written on other SMs: each thread fences at device scope
+// before it arrives, and the barrier's acquire orders the loads after it.
+// Every CTA passes the same barriers and waits on nothing outside its own
+// launch.
+struct ClusterSync {
+    __device__ __forceinline__ int tid() const { return blockIdx.x * CT + threadIdx.x; }
+    __device__ __forceinline__ int nth() const { return gridDim.x * CT; }
+    __device__ __forceinline__ int first(int, int) const { return tid(); }
+    __device__ __forceinline__ int end(int total, int) const { return total; }
+    __device__ __forceinline__ bool sync() const {
+        __threadfence();
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                     "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+        return true;
     }
 };
 
@@ -402,6 +424,68 @@ __global__ void __launch_bounds__(CT) k_coarse_cell(const CLevel<T>* __restrict_
     }
 }
 
+// Stacked batches: block s runs instance s.  Lall holds, per instance, the
+// descriptors of the levels handled here (stride lstride between instances):
+// the geometry of one instance and its coefficients (face arrays copied
+// instance by instance, cell and edge arrays in place), so the shared-memory
+// variant runs unchanged on the instance's own vectors.  Only the right-hand
+// side and the solution of the first level are moved between the stacked
+// layout (each face component holds the instances one after another) and
+// shared memory.
+template <typename T>
+__device__ __forceinline__ int stk_index(const Geom& gl, bool vel, int s, int nsl, int i) {
+    if (!vel) return s * gl.ncell + i;
+    int a = 0;
+    while (a + 1 < gl.dim && i >= gl.foff[a + 1]) ++a;
+    return nsl * gl.foff[a] + s * gl.fsize[a] + (i - gl.foff[a]);
+}
+
+template <int DIM, typename T, bool BULK, bool VEL>
+__global__ void __launch_bounds__(CT) k_coarse_stk(const CLevel<T>* __restrict__ Lall, int lstride, int nlev,
+                                                   const T* rhs0, T* phi0, int nu, int ncoarse) {
+    pdl_entry();
+    __shared__ Geom gsh[2];
+    __shared__ SmemLevels sl;
+    extern __shared__ __align__(16) unsigned char c_smem[];
+    T* sm = reinterpret_cast<T*>(c_smem);
+    const int s = blockIdx.x, nsl = gridDim.x;
+    const CLevel<T>* Ls = Lall + (size_t)s * lstride;
+    if (threadIdx.x == 0) {
+        int cur = 0;
+        for (int l = 0; l < nlev; ++l) {
+            sl.off[l] = cur;
+            sl.n[l] = VEL ? Ls[l].g.nvel : Ls[l].g.ncell;
+            cur += 3 * sl.n[l];
+        }
+    }
+    load_geom(&gsh[0], &Ls[0].g);
+    __syncthreads();
+    const int n0 = sl.n[0];
+    for (int t = threadIdx.x; t < n0; t += CT) sm[n0 + t] = rhs0[stk_index<T>(gsh[0], VEL, s, nsl, t)];
+    __syncthreads();
+    if (VEL) {
+        const Vecs<T, true, true> V{Ls, sm, &sl, rhs0, phi0};
+        vcycle_vel_body<DIM, T, BULK, true>(BlockSync{}, gsh, Ls, nlev, nlev, V, nu, ncoarse);
+    } else {
+        const Vecs<T, true, false> V{Ls, sm, &sl, rhs0, phi0};
+        vcycle_cell_body<DIM, T, true>(BlockSync{}, gsh, Ls, nlev, nlev, V, nu, ncoarse);
+    }
+    __syncthreads();
+    load_geom(&gsh[0], &Ls[0].g);
+    __syncthreads();
+    for (int t = threadIdx.x; t < n0; t += CT) phi0[stk_index<T>(gsh[0], VEL, s, nsl, t)] = sm[t];
+}
+
+// instance-by-instance copy of a stacked face array (coarse-level
+// coefficients of a stacked batch): dst[s * nvel + i] = src[stk_index(i)]
+template <typename T>
+__global__ void k_faces_by_instance(Geom gl, int nsl, const T* __restrict__ src, T* __restrict__ dst) {
+    pdl_entry();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.y;
+    if (t < gl.nvel) dst[(size_t)s * gl.nvel + t] = src[stk_index<T>(gl, true, s, nsl, t)];
+}
+
 // Persistent multi-block V-cycle (cooperative launch, every block resident):
 // levels 0..lblock-1 of Ls as grid-wide stages separated by bounded grid
 // barriers, the levels from lblock on by block 0 alone.  It replaces one
@@ -425,6 +509,29 @@ __global__ void __launch_bounds__(CT) k_grid_cell(const CLevel<T>* __restrict__ 
     const GridSync S{bar, *budget, status};
     const Vecs<T, false, false> V{Ls, nullptr, nullptr, rhs0, phi0};
     vcycle_cell_body<DIM, T, false>(S, gsh, Ls, nlev, lblock, V, nu, ncoarse);
+}
+
+// The same V-cycle as one thread-block cluster: levels 0..lblock-1 of Ls as
+// stages separated by cluster barriers (a hardware barrier, much cheaper
+// than a grid-wide one or a kernel boundary), the levels from lblock on by
+// block 0 alone.  Meant for the middle levels, whose launches cost more than
+// their work.
+template <int DIM, typename T, bool BULK>
+__global__ void __launch_bounds__(CT) k_cluster_vel(const CLevel<T>* __restrict__ Ls, int nlev, int lblock,
+                                                    const T* rhs0, T* phi0, int nu, int ncoarse) {
+    pdl_entry();
+    __shared__ Geom gsh[2];
+    const Vecs<T, false, true> V{Ls, nullptr, nullptr, rhs0, phi0};
+    vcycle_vel_body<DIM, T, BULK, false>(ClusterSync{}, gsh, Ls, nlev, lblock, V, nu, ncoarse);
+}
+
+template <int DIM, typename T>
+__global__ void __launch_bounds__(CT) k_cluster_cell(const CLevel<T>* __restrict__ Ls, int nlev, int lblock,
+                                                     const T* rhs0, T* phi0, int nu, int ncoarse) {
+    pdl_entry();
+    __shared__ Geom gsh[2];
+    const Vecs<T, false, false> V{Ls, nullptr, nullptr, rhs0, phi0};
+    vcycle_cell_body<DIM, T, false>(ClusterSync{}, gsh, Ls, nlev, lblock, V, nu, ncoarse);
 }
 
 // Column i of the coarse-solve matrix: the ncoarse sweeps applied to e_i.
@@ -599,6 +706,115 @@ cudaError_t launch_grid_vcycle_cell(int dim, const Geom& g0, const CLevel<T>* L,
                               status);
 }
 
+template <typename T>
+void launch_coarse_stacked(bool vel, int dim, int nsl, const CLevel<T>* Lall, int lstride, int nlev,
+                           const T* rhs, T* phi, int nu, int ncoarse, bool bulk, size_t smem,
+                           cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nsl);
+    cfg.blockDim = dim3(CT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    ++tl_launches;
+    if (dim != 2) return;   // stacked batches are 2D
+    void (*kern)(const CLevel<T>*, int, int, const T*, T*, int, int) = nullptr;
+    if (vel) kern = bulk ? k_coarse_stk<2, T, true, true> : k_coarse_stk<2, T, false, true>;
+    else kern = k_coarse_stk<2, T, false, false>;
+    cudaLaunchKernelEx(&cfg, kern, Lall, lstride, nlev, rhs, phi, nu, ncoarse);
+}
+
+template <typename T>
+void launch_faces_by_instance(const Geom& gl, int nsl, const T* src, T* dst, cudaStream_t s) {
+    launch_pdl(k_faces_by_instance<T>, dim3((gl.nvel + 255) / 256, nsl), dim3(256), s, gl, nsl, src, dst);
+}
+
+template void launch_coarse_stacked<double>(bool, int, int, const CLevel<double>*, int, int, const double*,
+                                            double*, int, int, bool, size_t, cudaStream_t);
+template void launch_coarse_stacked<float>(bool, int, int, const CLevel<float>*, int, int, const float*,
+                                           float*, int, int, bool, size_t, cudaStream_t);
+template void launch_faces_by_instance<double>(const Geom&, int, const double*, double*, cudaStream_t);
+template void launch_faces_by_instance<float>(const Geom&, int, const float*, float*, cudaStream_t);
+
+// the largest cluster the device runs (16 when non-portable sizes are
+// allowed and fit one GPC, else 8); set by prepare_coarse_kernels
+static int g_cluster_max = 8;
+
+template <typename K>
+int max_cluster(K kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    for (int c = 16; c >= 2; c /= 2) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(c);
+        cfg.blockDim = dim3(CT);
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = c;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n >= 1) return c;
+        cudaGetLastError();
+    }
+    return 1;
+}
+
+template <typename K, typename... Args>
+cudaError_t launch_cluster(K kern, int nb, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nb);
+    cfg.blockDim = dim3(CT);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = nb;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+template <typename T>
+int cluster_vcycle_blocks(const Geom& g0, bool vel) {
+    const int nb = grid_vcycle_blocks<T>(g0, vel);
+    return nb < g_cluster_max ? nb : g_cluster_max;
+}
+
+template <typename T>
+cudaError_t launch_cluster_vcycle_vel(int dim, const Geom& g0, const CLevel<T>* L, int nlev, int lblock,
+                                      const T* rhs, T* phi, int nu, int ncoarse, bool bulk, cudaStream_t s) {
+    const int nb = cluster_vcycle_blocks<T>(g0, true);
+    auto kern = dim == 2 ? (bulk ? k_cluster_vel<2, T, true> : k_cluster_vel<2, T, false>)
+                         : (bulk ? k_cluster_vel<3, T, true> : k_cluster_vel<3, T, false>);
+    ++tl_launches;
+    return launch_cluster(kern, nb, s, L, nlev, lblock, rhs, phi, nu, ncoarse);
+}
+
+template <typename T>
+cudaError_t launch_cluster_vcycle_cell(int dim, const Geom& g0, const CLevel<T>* L, int nlev, int lblock,
+                                       const T* rhs, T* phi, int nu, int ncoarse, cudaStream_t s) {
+    const int nb = cluster_vcycle_blocks<T>(g0, false);
+    auto kern = dim == 2 ? k_cluster_cell<2, T> : k_cluster_cell<3, T>;
+    ++tl_launches;
+    return launch_cluster(kern, nb, s, L, nlev, lblock, rhs, phi, nu, ncoarse);
+}
+
+template cudaError_t launch_cluster_vcycle_vel<double>(int, const Geom&, const CLevel<double>*, int, int,
+                                                       const double*, double*, int, int, bool, cudaStream_t);
+template cudaError_t launch_cluster_vcycle_vel<float>(int, const Geom&, const CLevel<float>*, int, int,
+                                                      const float*, float*, int, int, bool, cudaStream_t);
+template cudaError_t launch_cluster_vcycle_cell<double>(int, const Geom&, const CLevel<double>*, int, int,
+                                                        const double*, double*, int, int, cudaStream_t);
+template cudaError_t launch_cluster_vcycle_cell<float>(int, const Geom&, const CLevel<float>*, int, int,
+                                                       const float*, float*, int, int, cudaStream_t);
+
 template cudaError_t launch_grid_vcycle_vel<double>(int, const Geom&, const CLevel<double>*, int, int,
                                                     const double*, double*, int, int, bool, unsigned*,
                                                     const long long*, int*, cudaStream_t);
@@ -613,6 +829,27 @@ template cudaError_t launch_grid_vcycle_cell<float>(int, const Geom&, const CLev
                                                     const long long*, int*, cudaStream_t);
 
 void prepare_coarse_kernels() {
+    static bool clusters_done = false;
+    if (!clusters_done) {   // every cluster kernel uses 1024 threads and the same static memory
+        clusters_done = true;
+        int c = max_cluster(k_cluster_vel<3, double, false>);
+        const auto all = {k_cluster_vel<2, double, false>, k_cluster_vel<2, double, true>,
+                          k_cluster_vel<3, double, false>, k_cluster_vel<3, double, true>};
+        for (auto k : all) cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        const auto allf = {k_cluster_vel<2, float, false>, k_cluster_vel<2, float, true>,
+                           k_cluster_vel<3, float, false>, k_cluster_vel<3, float, true>};
+        for (auto k : allf) cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        const auto allc = {k_cluster_cell<2, double>, k_cluster_cell<3, double>};
+        for (auto k : allc) cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        const auto allcf = {k_cluster_cell<2, float>, k_cluster_cell<3, float>};
+        for (auto k : allcf) cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        for (auto k : allf) c = std::min(c, max_cluster(k));
+        for (auto k : all) c = std::min(c, max_cluster(k));
+        for (auto k : allc) c = std::min(c, max_cluster(k));
+        for (auto k : allcf) c = std::min(c, max_cluster(k));
+        g_cluster_max = c;
+        cudaGetLastError();
+    }
     set_smem_attr(k_coarse_vel<2, double, false, true>);
     set_smem_attr(k_coarse_vel<3, double, false, true>);
     set_smem_attr(k_coarse_vel<2, double, true, true>);
@@ -621,6 +858,12 @@ void prepare_coarse_kernels() {
     set_smem_attr(k_coarse_vel<3, float, false, true>);
     set_smem_attr(k_coarse_vel<2, float, true, true>);
     set_smem_attr(k_coarse_vel<3, float, true, true>);
+    set_smem_attr(k_coarse_stk<2, double, false, true>);
+    set_smem_attr(k_coarse_stk<2, double, true, true>);
+    set_smem_attr(k_coarse_stk<2, double, false, false>);
+    set_smem_attr(k_coarse_stk<2, float, false, true>);
+    set_smem_attr(k_coarse_stk<2, float, true, true>);
+    set_smem_attr(k_coarse_stk<2, float, false, false>);
     set_smem_attr(k_coarse_cell<2, double, true>);
     set_smem_attr(k_coarse_cell<3, double, true>);
     set_smem_attr(k_coarse_cell<2, float, true>);

@@ -314,6 +314,26 @@ template <typename T>
 cudaError_t launch_grid_vcycle_cell(int dim, const Geom& g0, const CLevel<T>* L, int nlev, int lblock,
                                     const T* rhs, T* phi, int nu, int ncoarse, unsigned* bar,
                                     const long long* budget, int* status, cudaStream_t s);
+// Stacked batches, shared-memory variant: block s runs instance s through
+// the descriptors Lall[s * lstride + l] (one instance's geometry and
+// coefficients); rhs, phi in the stacked layout (coarse.cu)
+template <typename T>
+void launch_coarse_stacked(bool vel, int dim, int nsl, const CLevel<T>* Lall, int lstride, int nlev,
+                           const T* rhs, T* phi, int nu, int ncoarse, bool bulk, size_t smem,
+                           cudaStream_t s);
+// dst[s * gl.nvel + i] = the i-th face value of instance s of the stacked
+// face array src (gl: the geometry of one instance)
+template <typename T>
+void launch_faces_by_instance(const Geom& gl, int nsl, const T* src, T* dst, cudaStream_t s);
+// The same as one thread-block cluster (up to 16 CTAs of 1024 threads on one
+// GPC, as many as the level's size calls for): hardware cluster barriers
+// between the stages (coarse.cu).  Not for stacked batches.
+template <typename T>
+cudaError_t launch_cluster_vcycle_vel(int dim, const Geom& g0, const CLevel<T>* L, int nlev, int lblock,
+                                      const T* rhs, T* phi, int nu, int ncoarse, bool bulk, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cluster_vcycle_cell(int dim, const Geom& g0, const CLevel<T>* L, int nlev, int lblock,
+                                       const T* rhs, T* phi, int nu, int ncoarse, cudaStream_t s);
 // Shared-memory budget of the coarse-level kernels: with smem > 0 (the bytes
 // of phi, rhs and residual of every level handled) and at most this many
 // bytes, the work vectors live in shared memory; 0 keeps them in global

@@ -77,6 +77,15 @@ struct Level {
     double* smat_pd = nullptr;
     float* smat_uf = nullptr;
     float* smat_pf = nullptr;
+    // stacked batches, levels from lstk on: the geometry of one instance, its
+    // face coefficients copied instance by instance (cell and edge arrays
+    // already hold the instances one after another) and, on the coarsest
+    // level, one coarse-solve matrix per instance
+    Geom gi{};
+    Coef<double> cdi{};
+    Coef<float> cfi{};
+    double *smat_udi = nullptr, *smat_pdi = nullptr;
+    float *smat_ufi = nullptr, *smat_pfi = nullptr;
 };
 
 // the sweep count the coarse-solve matrices are formed for: the default
@@ -123,6 +132,7 @@ struct stk_handle {
     int tpb_d = 256, tpb_f = 256;            // threads per block of the colour kernels
     int lpair_d = 0, lpair_f = 0;            // first level smoothed by the two-colour kernels
     int lgrid_d = 0, lgrid_f = 0;            // first level run by the persistent multi-block kernel
+    int lcluster_d = 0, lcluster_f = 0;      // first level run by the thread-block-cluster kernel
     unsigned* gbar = nullptr;                // its grid barrier (two words), then the wait
                                              // budget in clock64() cycles (a long long)
     bool bulk = false;                       // bulk-viscosity stress form on
@@ -130,6 +140,11 @@ struct stk_handle {
     double *gamma = nullptr, *rho0 = nullptr, *mu0 = nullptr;   // level-0 fields
     CLevel<double>* cld = nullptr;           // device copies of the level descriptors
     CLevel<float>* clf = nullptr;
+    // stacked batches: descriptors of one instance's levels lstk.. for the
+    // shared-memory coarse-level kernel, instance s at s * (levels - lstk)
+    int lstk = 0;
+    CLevel<double>* clsd = nullptr;
+    CLevel<float>* clsf = nullptr;
     double* red = nullptr;    // reduction scratch (RED_BLOCKS * 36 doubles)
     double* dsc = nullptr;    // device scalars
     double* hpin = nullptr;   // pinned host staging
@@ -378,9 +393,15 @@ template <typename T> int lcoarse_of(const stk_handle* h) {
 }
 template <typename T> int tpb_of(const stk_handle* h) { return sizeof(T) == 8 ? h->tpb_d : h->tpb_f; }
 template <typename T> int lgrid_of(const stk_handle* h) { return sizeof(T) == 8 ? h->lgrid_d : h->lgrid_f; }
+template <typename T> int lcluster_of(const stk_handle* h) {
+    return sizeof(T) == 8 ? h->lcluster_d : h->lcluster_f;
+}
 template <typename T> int lpair_of(const stk_handle* h) {
     return sizeof(T) == 8 ? h->lpair_d : h->lpair_f;
 }
+template <typename T> const CLevel<T>* clstk_of(const stk_handle* h);
+template <> const CLevel<double>* clstk_of<double>(const stk_handle* h) { return h->clsd; }
+template <> const CLevel<float>* clstk_of<float>(const stk_handle* h) { return h->clsf; }
 template <typename T> const CLevel<T>* clev_of(const stk_handle* h);
 template <> const CLevel<double>* clev_of<double>(const stk_handle* h) { return h->cld; }
 template <> const CLevel<float>* clev_of<float>(const stk_handle* h) { return h->clf; }
@@ -397,6 +418,19 @@ size_t coarse_smem(const stk_handle* h, int l, bool vel) {
     size_t b = 0;
     for (int k = l; k < nl; ++k)
         b += 3 * sizeof(T) * (size_t)(vel ? h->lev[k].g.nvel : h->lev[k].g.ncell);
+    return b <= COARSE_SMEM_LIMIT ? b : 0;
+}
+
+// The same for one instance of a stacked batch (the shared-memory kernel
+// runs each instance in its own block); 0 when the levels have no
+// instance copies or do not fit.
+template <typename T>
+size_t coarse_smem_stk(const stk_handle* h, int l, bool vel) {
+    const int nl = (int)h->lev.size();
+    if (h->nsl == 1 || l < h->lstk || nl - l > 16) return 0;
+    size_t b = 0;
+    for (int k = l; k < nl; ++k)
+        b += 3 * sizeof(T) * (size_t)(vel ? h->lev[k].gi.nvel : h->lev[k].gi.ncell);
     return b <= COARSE_SMEM_LIMIT ? b : 0;
 }
 
@@ -509,8 +543,21 @@ void vcycle_vel(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp, 
     Work<T> W = work_of<T>(L);
     if (l >= lcoarse_of<T>(h)) {   // this level and all coarser ones in one launch
         Scope sc(h, PF_COARSE, 0.0, s);
+        const size_t smi = coarse_smem_stk<T>(h, l, true);
+        if (smi > 0) {
+            const int nl = (int)h->lev.size();
+            launch_coarse_stacked<T>(true, L.g.dim, h->nsl, clstk_of<T>(h) + (l - h->lstk), nl - h->lstk,
+                                     nl - l, rhs, phi, mp.nu, mp.ncoarse, h->bulk, smi, s);
+            return;
+        }
         launch_coarse_vcycle_vel<T>(L.g.dim, L.g.nsl, clev_of<T>(h) + l, (int)h->lev.size() - l, rhs,
                                     phi, mp.nu, mp.ncoarse, h->bulk, coarse_smem<T>(h, l, true), s);
+        return;
+    }
+    if (l >= lcluster_of<T>(h)) {  // this level down as one thread-block cluster
+        Scope sc(h, PF_COARSE, 0.0, s);
+        launch_cluster_vcycle_vel<T>(L.g.dim, L.g, clev_of<T>(h) + l, (int)h->lev.size() - l,
+                                     lcoarse_of<T>(h) - l, rhs, phi, mp.nu, mp.ncoarse, h->bulk, s);
         return;
     }
     if (l >= lgrid_of<T>(h)) {     // this level down as one persistent multi-block launch
@@ -562,8 +609,21 @@ void vcycle_cell(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp,
     Work<T> W = work_of<T>(L);
     if (l >= lcoarse_of<T>(h)) {
         Scope sc(h, PF_COARSE, 0.0, s);
+        const size_t smi = coarse_smem_stk<T>(h, l, false);
+        if (smi > 0) {
+            const int nl = (int)h->lev.size();
+            launch_coarse_stacked<T>(false, L.g.dim, h->nsl, clstk_of<T>(h) + (l - h->lstk), nl - h->lstk,
+                                     nl - l, rhs, phi, mp.nu, mp.ncoarse, false, smi, s);
+            return;
+        }
         launch_coarse_vcycle_cell<T>(L.g.dim, L.g.nsl, clev_of<T>(h) + l, (int)h->lev.size() - l, rhs,
                                      phi, mp.nu, mp.ncoarse, coarse_smem<T>(h, l, false), s);
+        return;
+    }
+    if (l >= lcluster_of<T>(h)) {
+        Scope sc(h, PF_COARSE, 0.0, s);
+        launch_cluster_vcycle_cell<T>(L.g.dim, L.g, clev_of<T>(h) + l, (int)h->lev.size() - l,
+                                      lcoarse_of<T>(h) - l, rhs, phi, mp.nu, mp.ncoarse, s);
         return;
     }
     if (l >= lgrid_of<T>(h)) {
@@ -1503,7 +1563,45 @@ cudaError_t upload_clevels(stk_handle* h) {
     }
     cudaError_t e = cudaMemcpy(h->cld, cd.data(), sizeof(CLevel<double>) * nl, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
-    return cudaMemcpy(h->clf, cf.data(), sizeof(CLevel<float>) * nl, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(h->clf, cf.data(), sizeof(CLevel<float>) * nl, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess || !h->clsd) return e;
+    // stacked batches: one instance's levels lstk.., instance by instance
+    const int ls = nl - h->lstk;
+    std::vector<CLevel<double>> sd((size_t)h->nsl * ls);
+    std::vector<CLevel<float>> sf((size_t)h->nsl * ls);
+    for (int y = 0; y < h->nsl; ++y)
+        for (int l = h->lstk; l < nl; ++l) {
+            const Level& L = h->lev[l];
+            const Geom& gi = L.gi;
+            auto inst = [&](auto C) {   // instance y's coefficient pointers
+                const size_t f = (size_t)y * gi.nvel, c = (size_t)y * gi.ncell, e0 = (size_t)y * gi.esize[0];
+                C.alpha += f;
+                C.beta += f;
+                C.invd_u += f;
+                if (C.diag_u) C.diag_u += f;
+                C.mu2_c += c;
+                C.invd_p += c;
+                C.mu_e[0] += e0;
+                return C;
+            };
+            CLevel<double>& a = sd[(size_t)y * ls + (l - h->lstk)];
+            CLevel<float>& b = sf[(size_t)y * ls + (l - h->lstk)];
+            a = CLevel<double>{gi, inst(L.cdi), nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+            b = CLevel<float>{gi, inst(L.cfi), nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+            const size_t nu2 = (size_t)gi.nvel * gi.nvel, np2 = (size_t)gi.ncell * gi.ncell;
+            if (L.smat_udi) {
+                a.smat_u = L.smat_udi + y * nu2;
+                b.smat_u = L.smat_ufi + y * nu2;
+            }
+            if (L.smat_pdi) {
+                a.smat_p = L.smat_pdi + y * np2;
+                b.smat_p = L.smat_pfi + y * np2;
+            }
+            a.smat_nc = b.smat_nc = (L.smat_udi || L.smat_pdi) ? SMAT_SWEEPS : 0;
+        }
+    e = cudaMemcpy(h->clsd, sd.data(), sizeof(CLevel<double>) * sd.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(h->clsf, sf.data(), sizeof(CLevel<float>) * sf.size(), cudaMemcpyHostToDevice);
 }
 
 // all coefficients from rho, mu (and gamma) on the finest level down
@@ -1516,6 +1614,39 @@ void build_coefficients(stk_handle* h, const double* rho, const double* mu, cuda
     for (auto& L : h->lev) {
         launch_inverse_diagonals(L.g, L.cd, s);
         launch_convert_coefficients(L.g, L.cd, L.cf, s);
+    }
+    // stacked batches: the coarse levels' face coefficients instance by
+    // instance, and each instance's coarse-solve matrices
+    for (int l = h->lstk; h->clsd && l < (int)h->lev.size(); ++l) {
+        Level& L = h->lev[l];
+        launch_faces_by_instance<double>(L.gi, h->nsl, L.cd.alpha, L.cdi.alpha, s);
+        launch_faces_by_instance<double>(L.gi, h->nsl, L.cd.beta, L.cdi.beta, s);
+        launch_faces_by_instance<double>(L.gi, h->nsl, L.cd.invd_u, L.cdi.invd_u, s);
+        launch_faces_by_instance<double>(L.gi, h->nsl, L.cd.diag_u, L.cdi.diag_u, s);
+        launch_faces_by_instance<float>(L.gi, h->nsl, L.cf.alpha, L.cfi.alpha, s);
+        launch_faces_by_instance<float>(L.gi, h->nsl, L.cf.beta, L.cfi.beta, s);
+        launch_faces_by_instance<float>(L.gi, h->nsl, L.cf.invd_u, L.cfi.invd_u, s);
+        if (L.smat_udi || L.smat_pdi) {
+            const Geom& gi = L.gi;
+            const size_t nu2 = (size_t)gi.nvel * gi.nvel, np2 = (size_t)gi.ncell * gi.ncell;
+            for (int y = 0; y < h->nsl; ++y) {
+                Coef<double> cd = L.cdi;
+                Coef<float> cf = L.cfi;
+                const size_t f = (size_t)y * gi.nvel, c = (size_t)y * gi.ncell, e0 = (size_t)y * gi.esize[0];
+                cd.alpha += f; cd.beta += f; cd.invd_u += f; cd.diag_u += f;
+                cd.mu2_c += c; cd.invd_p += c; cd.mu_e[0] += e0;
+                cf.alpha += f; cf.beta += f; cf.invd_u += f;
+                cf.mu2_c += c; cf.invd_p += c; cf.mu_e[0] += e0;
+                if (L.smat_udi) {
+                    launch_coarsest_matrix_vel<double>(gi, cd, SMAT_SWEEPS, L.smat_udi + y * nu2, s);
+                    launch_coarsest_matrix_vel<float>(gi, cf, SMAT_SWEEPS, L.smat_ufi + y * nu2, s);
+                }
+                if (L.smat_pdi) {
+                    launch_coarsest_matrix_cell<double>(gi, cd, SMAT_SWEEPS, L.smat_pdi + y * np2, s);
+                    launch_coarsest_matrix_cell<float>(gi, cf, SMAT_SWEEPS, L.smat_pfi + y * np2, s);
+                }
+            }
+        }
     }
     Level& Lc = h->lev.back();   // the coarse-solve matrices of both hierarchies
     if (Lc.smat_ud) {
@@ -1673,6 +1804,45 @@ int create_handle(int dim, const int* n, double hh, const int* bc, int nsl, stk_
             CKC(dalloc(h, &Lc.smat_pf, np * np));
         }
     }
+    // stacked batches: instance copies of the levels that the coarse-level
+    // kernel may take (at most 65536 cells per instance, as stk_autotune)
+    h->lstk = (int)h->lev.size();
+    if (nsl > 1) {
+        while (h->lstk > 0 && h->lev[h->lstk - 1].g.ncell / nsl <= 65536) --h->lstk;
+        for (int l = h->lstk; l < (int)h->lev.size(); ++l) {
+            Level& L = h->lev[l];
+            const Geom& g = L.g;
+            const int nn1[3] = {g.n[0], g.n[1], 1};
+            const int bb1[6] = {g.bclo[0], g.bchi[0], g.bclo[1], g.bchi[1], 0, 0};
+            L.gi = make_geom(dim, nn1, g.h, bb1, 1);
+            const size_t nf = (size_t)L.gi.nvel * nsl;
+            L.cdi = L.cd;
+            L.cfi = L.cf;
+            CKC(dalloc(h, &L.cdi.alpha, nf));
+            CKC(dalloc(h, &L.cdi.beta, nf));
+            CKC(dalloc(h, &L.cdi.invd_u, nf));
+            CKC(dalloc(h, &L.cdi.diag_u, nf));
+            CKC(dalloc(h, &L.cfi.alpha, nf));
+            CKC(dalloc(h, &L.cfi.beta, nf));
+            CKC(dalloc(h, &L.cfi.invd_u, nf));
+            if (l + 1 == (int)h->lev.size()) {
+                const size_t nu = (size_t)L.gi.nvel, np = (size_t)L.gi.ncell;
+                if (nu <= (size_t)SMAT_MAX) {
+                    CKC(dalloc(h, &L.smat_udi, nu * nu * nsl));
+                    CKC(dalloc(h, &L.smat_ufi, nu * nu * nsl));
+                }
+                if (np <= (size_t)SMAT_MAX) {
+                    CKC(dalloc(h, &L.smat_pdi, np * np * nsl));
+                    CKC(dalloc(h, &L.smat_pfi, np * np * nsl));
+                }
+            }
+        }
+        if (h->lstk < (int)h->lev.size()) {
+            const size_t nd = (size_t)nsl * (h->lev.size() - h->lstk);
+            CKC(dalloc(h, &h->clsd, nd));
+            CKC(dalloc(h, &h->clsf, nd));
+        }
+    }
     const Geom& g0 = h->lev[0].g;
     const int ns = g0.nvel + g0.ncell;
     h->smap.len[0] = g0.fsize[0] / nsl;
@@ -1735,6 +1905,7 @@ int create_handle(int dim, const int* n, double hh, const int* bc, int nsl, stk_
         const int nl = (int)h->lev.size();
         h->lcoarse_d = h->lcoarse_f = nl;
         h->lgrid_d = h->lgrid_f = nl;
+        h->lcluster_d = h->lcluster_f = nl;
         // two-colour sweeps by default only in FP32 2D, where their halo
         // recomputation is small (measured; the autotuner decides per grid)
         h->lpair_d = nl;
@@ -2126,6 +2297,7 @@ int stk_get_schedule(const stk_handle* h, int precision, stk_schedule* out) {
     out->threads = precision == STK_FP64 ? h->tpb_d : h->tpb_f;
     out->pair_level = precision == STK_FP64 ? h->lpair_d : h->lpair_f;
     out->grid_level = precision == STK_FP64 ? h->lgrid_d : h->lgrid_f;
+    out->cluster_level = precision == STK_FP64 ? h->lcluster_d : h->lcluster_f;
     return STK_OK;
 }
 
@@ -2143,17 +2315,23 @@ int stk_set_schedule(stk_handle* h, int precision, const stk_schedule* sc) {
         return fail(h, STK_ERR_ARG, "grid_level must be in 0..%d", (int)h->lev.size());
     if (h->nsl > 1 && sc->grid_level < sc->coarse_level)
         return fail(h, STK_ERR_ARG, "a stacked batch has no persistent multi-block V-cycle (grid_level >= coarse_level)");
+    if (sc->cluster_level < 0 || sc->cluster_level > (int)h->lev.size())
+        return fail(h, STK_ERR_ARG, "cluster_level must be in 0..%d", (int)h->lev.size());
+    if (h->nsl > 1 && sc->cluster_level < sc->coarse_level)
+        return fail(h, STK_ERR_ARG, "a stacked batch has no cluster V-cycle (cluster_level >= coarse_level)");
     clear_graphs(h);
     if (precision == STK_FP64) {
         h->lcoarse_d = sc->coarse_level;
         h->tpb_d = sc->threads;
         h->lpair_d = sc->pair_level;
         h->lgrid_d = sc->grid_level;
+        h->lcluster_d = sc->cluster_level;
     } else {
         h->lcoarse_f = sc->coarse_level;
         h->tpb_f = sc->threads;
         h->lpair_f = sc->pair_level;
         h->lgrid_f = sc->grid_level;
+        h->lcluster_f = sc->cluster_level;
     }
     return STK_OK;
 }
@@ -2221,17 +2399,25 @@ int stk_autotune(stk_handle* h, int precision, stk_schedule* best, void* stream)
         int pls[4], npl = 0;
         for (int p = 0; p < 3 && p < lc; ++p) pls[npl++] = p;
         pls[npl++] = lc;
-        // the persistent multi-block kernel from one or two levels above
-        // the single-block one (grid_level), or not at all (= lc)
-        int gls[3], ngl = 0;
-        gls[ngl++] = lc;
+        // the persistent multi-block kernel (grid_level) or the cluster
+        // kernel (cluster_level) from one or two levels above the
+        // single-block one, or neither (= lc)
+        int gls[5], cls[5], ngl = 0;
+        gls[ngl] = lc;
+        cls[ngl++] = lc;
         for (int d = 1; d <= 2 && lc - d >= 0 && h->nsl == 1; ++d)
-            if (h->lev[lc - d].g.ncell <= 262144) gls[ngl++] = lc - d;
+            if (h->lev[lc - d].g.ncell <= 262144) {
+                gls[ngl] = lc - d;
+                cls[ngl++] = lc;
+                gls[ngl] = lc;
+                cls[ngl++] = lc - d;
+            }
         for (int k = 0; k < npl; ++k)
             for (int gi = 0; gi < ngl; ++gi)
             for (int ti = 0; ti < (pls[k] == 0 ? 1 : 3); ++ti) {
-                if (gls[gi] < lc && pls[k] > gls[gi] && pls[k] < lc) continue;
-                stk_schedule c{lc, threads[ti], pls[k], gls[gi]};
+                const int top = std::min(gls[gi], cls[gi]);   // first level run as one launch
+                if (top < lc && pls[k] > top && pls[k] < lc) continue;
+                stk_schedule c{lc, threads[ti], pls[k], gls[gi], cls[gi]};
                 int rc = stk_set_schedule(h, precision, &c);
                 if (rc) { h->prof = prof; return rc; }
                 float ms = 0.f;

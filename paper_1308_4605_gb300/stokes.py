@@ -55,7 +55,8 @@ class stk_solve_info(ctypes.Structure):
 
 class stk_schedule(ctypes.Structure):
     _fields_ = [("coarse_level", ctypes.c_int), ("threads", ctypes.c_int),
-                ("pair_level", ctypes.c_int), ("grid_level", ctypes.c_int)]
+                ("pair_level", ctypes.c_int), ("grid_level", ctypes.c_int),
+                ("cluster_level", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -349,10 +350,13 @@ def stk_get_schedule(h, precision):
     return sc.as_dict()
 
 
-def stk_set_schedule(h, precision, coarse_level, threads, pair_level, grid_level=None):
-    """grid_level None: no persistent multi-block levels (= coarse_level)."""
+def stk_set_schedule(h, precision, coarse_level, threads, pair_level, grid_level=None,
+                     cluster_level=None):
+    """grid_level / cluster_level None: no persistent multi-block / cluster
+    levels (= coarse_level)."""
     gl = coarse_level if grid_level is None else grid_level
-    sc = stk_schedule(int(coarse_level), int(threads), int(pair_level), int(gl))
+    cl = coarse_level if cluster_level is None else cluster_level
+    sc = stk_schedule(int(coarse_level), int(threads), int(pair_level), int(gl), int(cl))
     return _check(h, _lib.stk_set_schedule(h, int(precision), ctypes.byref(sc)))
 
 

@@ -26,7 +26,7 @@ def _key(solver, precision):
     import torch
     dev = torch.cuda.get_device_name(torch.cuda.current_device())
     stack = getattr(solver, "count", 1)
-    return f"s3|{dev}|{solver.dim}|{'x'.join(map(str, solver.n[:solver.dim]))}|" \
+    return f"s4|{dev}|{solver.dim}|{'x'.join(map(str, solver.n[:solver.dim]))}|" \
            f"{','.join(map(str, solver.bc[:2 * solver.dim]))}|{precision}" + \
            (f"|stack{stack}" if stack > 1 else "")
 
@@ -48,7 +48,7 @@ def tune(solver, precision, path=None):
     if key in cache:
         sc = cache[key]
         S.stk_set_schedule(solver.handle, precision, sc["coarse_level"], sc["threads"],
-                           sc["pair_level"], sc.get("grid_level"))
+                           sc["pair_level"], sc.get("grid_level"), sc.get("cluster_level"))
         return sc
     sc = S.stk_autotune(solver.handle, precision)
     cache = _load(path)

@@ -50,13 +50,14 @@ def main():
             nlev += 1
         rec = {"dim": dim, "n": n, "bc": bc}
         for prec in (0, 1):
-            for lc, pl in ((nlev, nlev), (nlev, 0), (0, 0)):
-                S.stk_set_schedule(sv.handle, prec, lc, 128, pl)
+            # last: every level in the thread-block-cluster kernel
+            for lc, pl, cl in ((nlev, nlev, None), (nlev, 0, None), (0, 0, None), (nlev, nlev, 0)):
+                S.stk_set_schedule(sv.handle, prec, lc, 128, pl, None, cl)
                 y_u, y_p = sv.apply_operator(bu, bp)
                 for which in (1, 2, 3, 4, 5):
                     sv.apply_preconditioner(which, bu, bp, precision=prec)
                 xu, xp, info = sv.solve(bu, bp, precond=pr.precond, precision=prec, maxit=400)
-                rec[f"p{prec}_lc{lc}_pl{pl}"] = [info["iterations"], info["true_residual"]]
+                rec[f"p{prec}_lc{lc}_pl{pl}_cl{cl}"] = [info["iterations"], info["true_residual"]]
         torch.cuda.synchronize()
         sv.close()
         out["cases"].append(rec)

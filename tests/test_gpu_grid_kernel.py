@@ -1,6 +1,8 @@
-"""The persistent multi-block V-cycle (schedule field grid_level): the
-middle levels run as one cooperative launch with grid-wide barriers between
-stages instead of one kernel per colour and transfer.  Its stages are the
+"""The persistent multi-block V-cycle (schedule field grid_level) and the
+thread-block-cluster V-cycle (cluster_level): the middle levels run as one
+cooperative launch with grid-wide barriers, or as one cluster with hardware
+cluster barriers, between stages instead of one kernel per colour and
+transfer.  Its stages are the
 same per-point functions in the same order, so V-cycles and solves equal,
 bitwise, those of the per-level kernels; inside a solve it is part of the
 cycle graph.  Every barrier wait is bounded: with a budget of zero cycles the
@@ -59,9 +61,11 @@ def test_grid_kernel_equals_per_level_kernels(S, dim, n, bc):
     out = {}
     for prec in (0, 1):
         # per-level kernels down to level 3, block kernel below; then the
-        # grid kernel from level 1 or 2 down to the block kernel
-        for lc, gl in ((3, 3), (3, 1), (3, 2), (nl, 1)):
-            S.stk_set_schedule(sv.handle, prec, lc, 256, lc, gl)
+        # grid kernel (gl) or the cluster kernel (cl) from level 1 or 2 down
+        # to the block kernel
+        for lc, gl, cl in ((3, 3, 3), (3, 1, 3), (3, 2, 3), (nl, 1, nl), (3, 3, 1), (3, 3, 2),
+                           (nl, nl, 1)):
+            S.stk_set_schedule(sv.handle, prec, lc, 256, lc, gl, cl)
             res = []
             if prec == 0:
                 xu = [torch.zeros_like(x) for x in ru]
@@ -73,10 +77,10 @@ def test_grid_kernel_equals_per_level_kernels(S, dim, n, bc):
             assert info["converged"], info
             assert S.stk_graphs_in_use(sv.handle) == 1
             res += list(su) + [sp, info["iterations"]]
-            out[(prec, lc, gl)] = res
+            out[(prec, lc, gl, cl)] = res
     sv.close()
     for prec in (0, 1):
-        ref = out[(prec, 3, 3)]
+        ref = out[(prec, 3, 3, 3)]
         for key, res in out.items():
             if key[0] != prec:
                 continue

@@ -27,14 +27,14 @@ def fakes(monkeypatch):
     def autotune(h, precision):
         calls["autotune"].append(precision)
         return {"coarse_level": 4, "threads": 256 if precision else 128, "pair_level": 4,
-                "grid_level": 3}
+                "grid_level": 3, "cluster_level": 2}
 
-    def set_schedule(h, precision, lc, th, pl, gl=None):
-        calls["set"].append((precision, lc, th, pl, gl))
+    def set_schedule(h, precision, lc, th, pl, gl=None, cl=None):
+        calls["set"].append((precision, lc, th, pl, gl, cl))
 
     monkeypatch.setattr(tuning.S, "stk_autotune", autotune)
     monkeypatch.setattr(tuning.S, "stk_set_schedule", set_schedule)
-    monkeypatch.setattr(tuning, "_key", lambda sv, p: f"s3|fake-gpu|{sv.dim}|"
+    monkeypatch.setattr(tuning, "_key", lambda sv, p: f"s4|fake-gpu|{sv.dim}|"
                         f"{'x'.join(map(str, sv.n[:sv.dim]))}|{','.join(map(str, sv.bc))}|{p}")
     return calls
 
@@ -48,7 +48,7 @@ def test_first_call_tunes_then_cache_hits(tmp_path, fakes):
     assert list(cache.values()) == [a]
     b = tuning.tune(sv, 1, path)
     assert b == a and fakes["autotune"] == [1]
-    assert fakes["set"] == [(1, 4, 256, 4, 3)]
+    assert fakes["set"] == [(1, 4, 256, 4, 3, 2)]
     tuning.tune(sv, 0, path)                       # another precision is another entry
     assert fakes["autotune"] == [1, 0] and len(json.load(open(path))) == 2
     tuning.tune(_Solver(3, (64, 64, 64), (0,) * 6), 0, path)   # another grid too
