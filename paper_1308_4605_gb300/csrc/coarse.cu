@@ -111,17 +111,16 @@ struct GridSync {
 // ClusterSync: the CTAs of one thread-block cluster (the whole grid is one
 // cluster of at most 16 CTAs, resident together on one GPC) with the
 // hardware cluster barrier between stages.  The stages exchange data through
-// global memory written on other SMs: each thread fences at device scope
-// before it arrives, and the barrier's acquire orders the loads after it.
-// Every CTA passes the same barriers and waits on nothing outside its own
-// launch.
+// global memory written on other SMs of the cluster: the arrive has release
+// and the wait acquire semantics at cluster scope, which order every
+// thread's writes before the barrier with the reads after it.  Every CTA
+// passes the same barriers and waits on nothing outside its own launch.
 struct ClusterSync {
     __device__ __forceinline__ int tid() const { return blockIdx.x * CT + threadIdx.x; }
     __device__ __forceinline__ int nth() const { return gridDim.x * CT; }
     __device__ __forceinline__ int first(int, int) const { return tid(); }
     __device__ __forceinline__ int end(int total, int) const { return total; }
     __device__ __forceinline__ bool sync() const {
-        __threadfence();
         asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
                      "barrier.cluster.wait.acquire.aligned;" ::: "memory");
         return true;
