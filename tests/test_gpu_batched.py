@@ -169,6 +169,27 @@ def test_two_colour_sweeps_equal_per_colour_3d(S, n, bc):
     sv.close()
 
 
+def test_two_colour_sweeps_equal_per_colour_3d_bulk(S):
+    """The same with the bulk-viscosity stress form (mixed solve, two-colour
+    kernels from the finest level)."""
+    pr = wl.generic(3, (32, 32, 16), (1, 1, 0, 0, 2, 2), theta=1.0, seed=43, precond=1)
+    sv = S.StokesSolver(3, pr.n, pr.bc, pr.h)
+    sv.set_coefficients(_t(pr.rho), _t(pr.mu), pr.theta)
+    gam = torch.full(sv.cell_shape(), 0.7, dtype=torch.float64, device=DEV)
+    sv.set_bulk_viscosity(gam)
+    bu = [_t(x) for x in pr.b_u]
+    bp = _t(pr.b_p)
+    out = []
+    for paired in (True, False):
+        sc = S.stk_get_schedule(sv.handle, 1)
+        S.stk_set_schedule(sv.handle, 1, sc["coarse_level"], sc["threads"], 0 if paired else sc["coarse_level"])
+        su, sp, info = sv.solve(bu, bp, precision=1, precond=1)
+        assert info["converged"]
+        out.append([*su, sp])
+    assert all(torch.equal(a, b) for a, b in zip(out[0], out[1]))
+    sv.close()
+
+
 def test_coefficient_updates_keep_graphs_valid(S):
     """set_coefficients keeps the captured preconditioner graphs unless theta
     switches between zero and non-zero (they read coefficients and theta
