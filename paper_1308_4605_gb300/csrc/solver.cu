@@ -572,7 +572,14 @@ void vcycle_vel(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp, 
         launch_coarsest_apply<T>(L.g.nvel, smat_u_of<T>(L), rhs, phi, s);
         return;
     }
-    launch_zero<T>(L.g.nvel, phi, s);
+    // Below the finest level phi is a work array of this level whose wall
+    // faces nothing ever writes (they stay the zeros it was allocated with),
+    // and a first sweep from zero by colour kernels reads no unknown before
+    // writing it: the zero fill is needed only at the finest level (the
+    // caller's array), for two-colour sweeps (they read every value), with
+    // bulk viscosity (full first sweep) or without sweeps.
+    const int nsw = l + 1 == (int)h->lev.size() ? mp.ncoarse : mp.nu;
+    if (l == 0 || l >= lpair_of<T>(h) || h->bulk || nsw < 1) launch_zero<T>(L.g.nvel, phi, s);
     if (l + 1 == (int)h->lev.size()) {
         vel_sweeps<T>(h, l, mp.ncoarse, phi, rhs, s, true);
         return;
@@ -638,7 +645,9 @@ void vcycle_cell(stk_handle* h, int l, const T* rhs, T* phi, const MGParams& mp,
         launch_coarsest_apply<T>(L.g.ncell, smat_p_of<T>(L), rhs, phi, s);
         return;
     }
-    launch_zero<T>(L.g.ncell, phi, s);
+    // as for the velocity: the red cells from zero read no neighbour
+    const int nsw = l + 1 == (int)h->lev.size() ? mp.ncoarse : mp.nu;
+    if (l == 0 || l >= lpair_of<T>(h) || nsw < 1) launch_zero<T>(L.g.ncell, phi, s);
     if (l + 1 == (int)h->lev.size()) {
         cell_sweeps<T>(h, l, mp.ncoarse, phi, rhs, s, true);
         return;
