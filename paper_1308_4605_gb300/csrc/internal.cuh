@@ -424,31 +424,34 @@ constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
 constexpr int RED_THREADS = 256;
 constexpr int KRY_BLOCKS = 1216;  // 8 x 152 SMs: grid of the Krylov kernels (krylov.cu)
 constexpr int RED_SCRATCH = KRY_BLOCKS * 36;   // doubles of reduction scratch
-template <typename T>  // out[0] = sum x  (scratch >= RED_BLOCKS doubles)
-void launch_sum(int n, const T* x, double* scratch, double* out, cudaStream_t s);
-// out[0] = sum x for an FP32 vector, x 16-byte aligned (krylov.cu; scratch >=
+// Reductions finish in the last block of their own launch: cnt is a count
+// in device memory, zero between reductions, one per stream that reduces
+// (per instance for the stacked forms).
+template <typename T>  // out[0] = sum x, out[1] = out[0] / n  (scratch >= RED_BLOCKS doubles)
+void launch_sum(int n, const T* x, double* scratch, double* out, unsigned* cnt, cudaStream_t s);
+// the same for an FP32 vector, x 16-byte aligned (krylov.cu; scratch >=
 // KRY_BLOCKS doubles): wide loads, sums of four in FP32 widened once
-void launch_sum_f32x4(int n, const float* x, double* scratch, double* out, cudaStream_t s);
-template <typename T>  // x -= (*sum) / n    (sum[1] receives the mean)
-void launch_sub_mean(int n, T* x, double* sum, cudaStream_t s);
-template <typename T>  // out = in - (*sum)/n  (sum[1] receives the mean)
-void launch_copy_sub_mean(int n, const T* in, T* out, double* sum, cudaStream_t s);
+void launch_sum_f32x4(int n, const float* x, double* scratch, double* out, unsigned* cnt, cudaStream_t s);
+template <typename T>  // x -= sum[1] (the mean left by launch_sum)
+void launch_sub_mean(int n, T* x, const double* sum, cudaStream_t s);
+template <typename T>  // out = in - sum[1]
+void launch_copy_sub_mean(int n, const T* in, T* out, const double* sum, cudaStream_t s);
 // Stacked batches: nsl instances of n values one after another.
-// out[y * ostride] = sum of instance y, bitwise the value launch_sum gives
-// for that instance alone (scratch >= nsl * RED_BLOCKS doubles)
+// out[y * ostride] = sum of instance y, out[y * ostride + 1] its mean,
+// bitwise the values launch_sum gives for that instance alone (scratch >=
+// nsl * RED_BLOCKS doubles; cnt: nsl counts)
 template <typename T>
-void launch_sum_sl(int n, int nsl, const T* x, double* scratch, double* out, int ostride,
+void launch_sum_sl(int n, int nsl, const T* x, double* scratch, double* out, int ostride, unsigned* cnt,
                    cudaStream_t s);
-// out = in - sum[y * stride] / n per instance y (sum[y * stride + 1]
-// receives the mean; in == out allowed)
+// out = in - sum[y * stride + 1] per instance y (in == out allowed)
 template <typename T>
-void launch_sub_mean_sl(int n, int nsl, const T* in, T* out, double* sum, int stride, cudaStream_t s);
+void launch_sub_mean_sl(int n, int nsl, const T* in, T* out, const double* sum, int stride, cudaStream_t s);
 // h[i] = <w, V_i> for i <= j and h[j+1] = <w, w>;  V = array of j+1 device pointers
 void launch_multidot(int n, int j, const double* const* V, const double* w, double* scratch,
-                     double* h, cudaStream_t s);
+                     double* h, unsigned* cnt, cudaStream_t s);
 // modified Gram-Schmidt step: w -= h[k] vk, then out[0] = <w, u> (u = null: <w, w>)
 void launch_mgs_step(int n, const double* vk, const double* u, const double* h, int k, double* w,
-                     double* scratch, double* out, cudaStream_t s);
+                     double* scratch, double* out, unsigned* cnt, cudaStream_t s);
 // x += sum_i y[i] V_i (i < k); V of precision TV
 template <typename TV>
 void launch_combine(int n, int k, const TV* const* V, const double* y, double* x, cudaStream_t s);
@@ -463,19 +466,20 @@ void launch_scale_dev(int n, double* x, const double* a, cudaStream_t s);
 // batch (nsl instances, map m), instance y's results at stride hstride /
 // ostride (y * stride + k), bitwise the ones it gets alone.
 void launch_multidot_sl(const SliceMap& m, int nsl, int j, const double* const* V, const double* w,
-                        double* scratch, double* h, int hstride, cudaStream_t s);
+                        double* scratch, double* h, int hstride, unsigned* cnt, cudaStream_t s);
 void launch_mgs_step_sl(const SliceMap& m, int nsl, const double* vk, const double* u, const double* h,
                         int hstride, int k, double* w, double* scratch, double* out, int ostride,
-                        cudaStream_t s);
+                        unsigned* cnt, cudaStream_t s);
 // x += sum_i st[y].y[i] V_i (i < st[y].k) for every instance y
 template <typename TV>
 void launch_combine_dev_sl(const SliceMap& m, int nsl, int mmax, const TV* const* V, const GmState* st,
                            double* x, cudaStream_t s);
 // x *= st[y].inv_scale where Arnoldi step j of instance y is open, else 0
 void launch_scale_dev_sl(const SliceMap& m, int nsl, double* x, const GmState* st, int j, cudaStream_t s);
-// out[y * ostride] = sum of instance y of an FP32 vector of nsl x n values
+// out[y * ostride] = sum of instance y of an FP32 vector of nsl x n values,
+// out[y * ostride + 1] its mean
 void launch_sum_f32x4_sl(int n, int nsl, const float* x, double* scratch, double* out, int ostride,
-                         cudaStream_t s);
+                         unsigned* cnt, cudaStream_t s);
 // x *= 1 / sqrt(*nrm2)
 void launch_scale_inv_sqrt(int n, double* x, const double* nrm2, cudaStream_t s);
 void launch_scale(int n, double* x, double a, cudaStream_t s);

@@ -597,8 +597,33 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return r;   // valid in thread 0
 }
 
+// The final sum of a cell-vector reduction and the mean, done by the block
+// that finishes last (no launch of their own): out[0] = sum of the nb =
+// gridDim.x block partials (thread t adds b = t, t + blockDim.x, ..., then
+// block_sum), out[1] = out[0] / n; the count *cnt is reset for the next
+// reduction on the stream (kernels on a stream never overlap: each waits at
+// pdl_entry() for its predecessor to complete).
+__device__ __forceinline__ void finish_sum(const double* part, int n, double* out, unsigned* cnt) {
+    __shared__ unsigned s_last;
+    __shared__ double sh[32];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(cnt, 1u) == gridDim.x - 1u ? 1u : 0u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double s = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += __ldcg(part + b);
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) {
+        out[0] = s;
+        out[1] = s / n;
+        *cnt = 0u;
+    }
+}
+
 template <typename T>
-__global__ void k_sum_partials(int n, const T* __restrict__ x, double* part) {
+__global__ void k_sum_partials(int n, const T* __restrict__ x, double* part, double* out, unsigned* cnt) {
     pdl_entry();
     __shared__ double sh[32];
     double s = 0.0;
@@ -606,6 +631,7 @@ __global__ void k_sum_partials(int n, const T* __restrict__ x, double* part) {
         s += double(x[i]);
     s = block_sum(s, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
+    finish_sum(part, n, out, cnt);
 }
 
 // out[k] = sum over RED_BLOCKS partials part[k * RED_BLOCKS + b], fixed order.
@@ -620,11 +646,6 @@ __global__ void k_final(int nk, const double* __restrict__ part, double* out) {
     }
 }
 
-// sum[1] = sum[0] / n, computed once (one FP64 division, not one per thread)
-__global__ void k_mean(int n, double* sum) {
-    pdl_entry();
-    if (threadIdx.x == 0 && blockIdx.x == 0) sum[1] = sum[0] / n;
-}
 
 template <typename T>
 __global__ void k_sub_mean(int n, T* x, const double* __restrict__ sum) {
@@ -646,36 +667,22 @@ __global__ void k_copy_sub_mean(int n, const T* __restrict__ in, T* out,
 // ----------------------------------------------------------- stacked batches
 // nsl instances of n values each, one after another (a cell vector of a
 // stacked batch).  The sum of each instance uses the partition and the
-// order of k_sum_partials / k_final above, so it is bitwise the sum the
-// instance gets alone; only the blocks that hold values are launched (the
-// others' partials are exact zeros).  Grid (nbu, nsl), blockIdx.y the instance.
+// order of k_sum_partials above (grid (nb, nsl), blockIdx.y the instance,
+// one count per instance), so it is bitwise the sum the instance gets alone:
+// out[y * ostride] the sum, out[y * ostride + 1] the mean.
 template <typename T>
-__global__ void k_sum_partials_sl(int n, const T* __restrict__ x, double* part, int nbu) {
+__global__ void k_sum_partials_sl(int n, const T* __restrict__ x, double* part, double* out, int ostride,
+                                  unsigned* cnt) {
     pdl_entry();
     __shared__ double sh[32];
     const T* xs = x + (size_t)blockIdx.y * n;
     double s = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += RED_BLOCKS * blockDim.x)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         s += double(xs[i]);
     s = block_sum(s, sh);
-    if (threadIdx.x == 0) part[blockIdx.y * nbu + blockIdx.x] = s;
-}
-
-// out[y * ostride] = the sum of instance y's nbu partials (one block each)
-__global__ void k_final_sl(int nbu, const double* __restrict__ part, double* out, int ostride) {
-    pdl_entry();
-    __shared__ double sh[32];
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nbu; b += blockDim.x) s += part[blockIdx.x * nbu + b];
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) out[(size_t)blockIdx.x * ostride] = s;
-}
-
-// sum[y * stride + 1] = sum[y * stride] / n for every instance y
-__global__ void k_mean_sl(int n, int nsl, double* sum, int stride) {
-    pdl_entry();
-    const int y = blockIdx.x * blockDim.x + threadIdx.x;
-    if (y < nsl) sum[(size_t)y * stride + 1] = sum[(size_t)y * stride] / n;
+    double* p = part + (size_t)blockIdx.y * gridDim.x;
+    if (threadIdx.x == 0) p[blockIdx.x] = s;
+    finish_sum(p, n, out + (size_t)blockIdx.y * ostride, cnt + blockIdx.y);
 }
 
 // out = in - mean of the instance (in place when in == out); grid (.., nsl)
@@ -944,36 +951,36 @@ void launch_schur_combine(int n, const double* theta, const T* phi, const T* mu2
     launch_pdl(k_schur_combine<T>, dim3(nblk(n)), dim3(TPB), s, n, theta, phi, mu2, lam, bc, xp);
 }
 
-template <typename T>
-void launch_sum(int n, const T* x, double* scratch, double* out, cudaStream_t s) {
-    launch_pdl(k_sum_partials<T>, dim3(RED_BLOCKS), dim3(RED_THREADS), s, n, x, scratch);
-    launch_pdl(k_final, dim3(1), dim3(RED_THREADS), s, 1, scratch, out);
+// blocks of a cell-vector sum: one value per thread at least, at most RED_BLOCKS
+inline int sum_blocks(int n) {
+    const int b = (n + RED_THREADS - 1) / RED_THREADS;
+    return b < 1 ? 1 : (b > RED_BLOCKS ? RED_BLOCKS : b);
 }
 
 template <typename T>
-void launch_sub_mean(int n, T* x, double* sum, cudaStream_t s) {
-    launch_pdl(k_mean, dim3(1), dim3(32), s, n, sum);
+void launch_sum(int n, const T* x, double* scratch, double* out, unsigned* cnt, cudaStream_t s) {
+    launch_pdl(k_sum_partials<T>, dim3(sum_blocks(n)), dim3(RED_THREADS), s, n, x, scratch, out, cnt);
+}
+
+template <typename T>
+void launch_sub_mean(int n, T* x, const double* sum, cudaStream_t s) {
     launch_pdl(k_sub_mean<T>, dim3(nblk(n)), dim3(TPB), s, n, x, sum);
 }
 
 template <typename T>
-void launch_copy_sub_mean(int n, const T* in, T* out, double* sum, cudaStream_t s) {
-    launch_pdl(k_mean, dim3(1), dim3(32), s, n, sum);
+void launch_copy_sub_mean(int n, const T* in, T* out, const double* sum, cudaStream_t s) {
     launch_pdl(k_copy_sub_mean<T>, dim3(nblk(n)), dim3(TPB), s, n, in, out, sum);
 }
 
 template <typename T>
-void launch_sum_sl(int n, int nsl, const T* x, double* scratch, double* out, int ostride,
+void launch_sum_sl(int n, int nsl, const T* x, double* scratch, double* out, int ostride, unsigned* cnt,
                    cudaStream_t s) {
-    int nbu = (n + RED_THREADS - 1) / RED_THREADS;
-    nbu = nbu < 1 ? 1 : (nbu > RED_BLOCKS ? RED_BLOCKS : nbu);
-    launch_pdl(k_sum_partials_sl<T>, dim3(nbu, nsl), dim3(RED_THREADS), s, n, x, scratch, nbu);
-    launch_pdl(k_final_sl, dim3(nsl), dim3(RED_THREADS), s, nbu, scratch, out, ostride);
+    launch_pdl(k_sum_partials_sl<T>, dim3(sum_blocks(n), nsl), dim3(RED_THREADS), s, n, x, scratch, out,
+               ostride, cnt);
 }
 
 template <typename T>
-void launch_sub_mean_sl(int n, int nsl, const T* in, T* out, double* sum, int stride, cudaStream_t s) {
-    launch_pdl(k_mean_sl, dim3((nsl + 31) / 32), dim3(32), s, n, nsl, sum, stride);
+void launch_sub_mean_sl(int n, int nsl, const T* in, T* out, const double* sum, int stride, cudaStream_t s) {
     launch_pdl(k_sub_mean_sl<T>, dim3(nblk(n), nsl), dim3(TPB), s, n, in, out, sum, stride);
 }
 
@@ -1038,11 +1045,12 @@ void launch_check_fields(int n, const double* rho, const double* mu, double* scr
     template void launch_schur_combine<T>(int, const double*, const T*, const T*, const T*,      \
                                           const T*, T*,                                            \
                                           cudaStream_t);                                           \
-    template void launch_sum<T>(int, const T*, double*, double*, cudaStream_t);                  \
-    template void launch_sum_sl<T>(int, int, const T*, double*, double*, int, cudaStream_t);     \
-    template void launch_sub_mean_sl<T>(int, int, const T*, T*, double*, int, cudaStream_t);     \
-    template void launch_sub_mean<T>(int, T*, double*, cudaStream_t);                            \
-    template void launch_copy_sub_mean<T>(int, const T*, T*, double*, cudaStream_t);             \
+    template void launch_sum<T>(int, const T*, double*, double*, unsigned*, cudaStream_t);       \
+    template void launch_sum_sl<T>(int, int, const T*, double*, double*, int, unsigned*,         \
+                                   cudaStream_t);                                                  \
+    template void launch_sub_mean_sl<T>(int, int, const T*, T*, const double*, int, cudaStream_t); \
+    template void launch_sub_mean<T>(int, T*, const double*, cudaStream_t);                      \
+    template void launch_copy_sub_mean<T>(int, const T*, T*, const double*, cudaStream_t);       \
     template void launch_axpy<T>(int, T, const T*, T*, cudaStream_t);                            \
     template void launch_zero<T>(int, T*, cudaStream_t);
 STK_INST(double)

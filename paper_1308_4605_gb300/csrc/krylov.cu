@@ -49,29 +49,48 @@ __device__ __forceinline__ void block_sums(const double (&v)[NV], double* part, 
     }
 }
 
-// out[k] = sum_b part[k * nb + b] over the nb block partials, one block per
-// k, fixed order.
-__global__ void __launch_bounds__(KT) k_final_multi(const double* __restrict__ part, double* out, int nb) {
-    pdl_entry();
+// The final sums of a reduction, done by the block that finishes last
+// instead of by a launch of their own.  Every block has written its NV
+// partials at part[k * nb + b] (nb = gridDim.x blocks; a stacked batch
+// counts per instance, blockIdx.y).  The block whose arrival completes the
+// count *cnt forms out[k] = sum_b part[k * nb + b] for each k in a fixed
+// order (thread t adds b = t, t + KT, ..., then a shuffle tree per warp and
+// the warps' sums in order) and resets the count for the next reduction on
+// the stream (kernels on a stream never overlap: each waits at pdl_entry()
+// for its predecessor to complete).  Returns true in that block, whose
+// thread 0 wrote every out[k].
+template <int NV>
+__device__ __forceinline__ bool finish_last(const double* part, int nb, double* out, unsigned* cnt) {
+    __shared__ unsigned s_last;
     __shared__ double sh[KT / 32];
-    const int k = blockIdx.x;
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nb; b += KT) s += part[k * nb + b];
-    s = wsum(s);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double r = 0.0;
+    if (threadIdx.x == 0) s_last = atomicAdd(cnt, 1u) == gridDim.x - 1u ? 1u : 0u;
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    for (int k = 0; k < NV; ++k) {
+        double s = 0.0;
+        for (int b = threadIdx.x; b < nb; b += KT) s += __ldcg(part + (size_t)k * nb + b);
+        s = wsum(s);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double r = 0.0;
 #pragma unroll
-        for (int i = 0; i < KT / 32; ++i) r += sh[i];
-        out[k] = r;
+            for (int i = 0; i < KT / 32; ++i) r += sh[i];
+            out[k] = r;
+        }
+        __syncthreads();
     }
+    if (threadIdx.x == 0) *cnt = 0u;
+    return true;
 }
 
 // h[i] = <w, V_i> (i <= J) and h[J+1] = <w, w>
 template <int J>
 __global__ void __launch_bounds__(KT) k_mdot(int n, PtrArr V, const double* __restrict__ w,
-                                              double* __restrict__ part) {
+                                              double* __restrict__ part, double* out, unsigned* cnt) {
     pdl_entry();
     double acc[J + 2];
 #pragma unroll
@@ -96,6 +115,7 @@ __global__ void __launch_bounds__(KT) k_mdot(int n, PtrArr V, const double* __re
         acc[J + 1] = fma(a, a, acc[J + 1]);
     }
     block_sums<J + 2>(acc, part, gridDim.x);
+    finish_last<J + 2>(part, gridDim.x, out, cnt);
 }
 
 // One modified Gram-Schmidt step: w -= h[k] v_k, then the block partials
@@ -103,7 +123,8 @@ __global__ void __launch_bounds__(KT) k_mdot(int n, PtrArr V, const double* __re
 __global__ void __launch_bounds__(KT) k_mgs_step(int n, const double* __restrict__ vk,
                                                  const double* __restrict__ u,
                                                  const double* __restrict__ h, int k,
-                                                 double* __restrict__ w, double* __restrict__ part) {
+                                                 double* __restrict__ w, double* __restrict__ part,
+                                                 double* out, unsigned* cnt) {
     pdl_entry();
     const double hk = h[k];
     double s[1] = {0.0};
@@ -127,6 +148,7 @@ __global__ void __launch_bounds__(KT) k_mgs_step(int n, const double* __restrict
         s[0] = fma(a, u ? u[n - 1] : a, s[0]);
     }
     block_sums<1>(s, part, gridDim.x);
+    finish_last<1>(part, gridDim.x, out, cnt);
 }
 
 template <typename TV> struct Vec2;
@@ -208,10 +230,10 @@ __global__ void __launch_bounds__(KT) k_scal(int n, double* __restrict__ x, doub
 // The kernels above on every instance of a stacked batch at once (grid
 // (nbu, nsl), blockIdx.y the instance).  Instance y's values are visited in
 // the order of its own packed vector (sl_pair), with the partition over
-// threads and the summation order of the single-instance kernels, so its
-// projections, norms and updates are bitwise the ones it gets alone.  Only
-// the blocks that hold values are launched (nbu); the others' partials
-// would be exact zeros.
+// threads and the summation order of the single-instance kernels (the same
+// grid per instance, kry_blocks, and the final sums per instance in its last
+// block), so its projections, norms and updates are bitwise the ones it gets
+// alone.
 
 // global pair index of pair t (values 2t, 2t + 1) of instance y
 __device__ __forceinline__ int sl_pair(const SliceMap& m, int y, int t) {
@@ -223,29 +245,11 @@ __device__ __forceinline__ int sl_pair(const SliceMap& m, int y, int t) {
     return (m.off[2] + y * m.len[2] + i) >> 1;
 }
 
-// out[y * ostride + k] = sum of the nbu partials part[(y * nv + k) * nbu + b]
-__global__ void __launch_bounds__(KT) k_final_multi_sl(const double* __restrict__ part, double* out,
-                                                        int nbu, int nv, int ostride) {
-    pdl_entry();
-    __shared__ double sh[KT / 32];
-    const int k = blockIdx.x, y = blockIdx.y;
-    const double* p = part + ((size_t)y * nv + k) * nbu;
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nbu; b += KT) s += p[b];
-    s = wsum(s);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double r = 0.0;
-#pragma unroll
-        for (int i = 0; i < KT / 32; ++i) r += sh[i];
-        out[(size_t)y * ostride + k] = r;
-    }
-}
-
 template <int J>
 __global__ void __launch_bounds__(KT) k_mdot_sl(SliceMap m, PtrArr V, const double* __restrict__ w,
-                                                 double* __restrict__ part, int nbu) {
+                                                 double* __restrict__ part, double* out, int ostride,
+                                                 unsigned* cnt) {
+    const int nbu = gridDim.x;
     pdl_entry();
     const int y = blockIdx.y;
     double acc[J + 2];
@@ -266,14 +270,16 @@ __global__ void __launch_bounds__(KT) k_mdot_sl(SliceMap m, PtrArr V, const doub
         acc[J + 1] = fma(a.y, a.y, acc[J + 1]);
     }
     block_sums<J + 2>(acc, part + (size_t)y * (J + 2) * nbu, nbu);
+    finish_last<J + 2>(part + (size_t)y * (J + 2) * nbu, nbu, out + (size_t)y * ostride, cnt + y);
 }
 
 __global__ void __launch_bounds__(KT) k_mgs_step_sl(SliceMap m, const double* __restrict__ vk,
                                                     const double* __restrict__ u,
                                                     const double* __restrict__ h, int hstride, int k,
                                                     double* __restrict__ w, double* __restrict__ part,
-                                                    int nbu) {
+                                                    double* out, int ostride, unsigned* cnt) {
     pdl_entry();
+    const int nbu = gridDim.x;
     const int y = blockIdx.y;
     const double hk = h[(size_t)y * hstride + k];
     double s[1] = {0.0};
@@ -293,6 +299,7 @@ __global__ void __launch_bounds__(KT) k_mgs_step_sl(SliceMap m, const double* __
         s[0] = fma(a.y, b.y, s[0]);
     }
     block_sums<1>(s, part + (size_t)y * nbu, nbu);
+    finish_last<1>(part + (size_t)y * nbu, nbu, out + (size_t)y * ostride, cnt + y);
 }
 
 // x += sum_{i < k_y} y_y[i] V_i with k_y, y_y from instance y's GMRES state
@@ -344,10 +351,12 @@ __global__ void __launch_bounds__(KT) k_scal_dev_sl(SliceMap m, double* __restri
     }
 }
 
-// per-instance k_sum_f32x4 (instances of n values one after another)
+// per-instance k_sum_f32x4 (instances of n values one after another):
+// out[y * ostride] = the sum of instance y, out[y * ostride + 1] its mean
 __global__ void __launch_bounds__(KT) k_sum_f32x4_sl(int n, const float* __restrict__ x, double* part,
-                                                     int nbu) {
+                                                     double* out, int ostride, unsigned* cnt) {
     pdl_entry();
+    const int nbu = gridDim.x;
     const float* xs = x + (size_t)blockIdx.y * n;
     const int n4 = n >> 2;
     const float4* x4 = reinterpret_cast<const float4*>(xs);
@@ -358,6 +367,9 @@ __global__ void __launch_bounds__(KT) k_sum_f32x4_sl(int n, const float* __restr
     }
     if (blockIdx.x == 0 && threadIdx.x < (n & 3)) acc[0] += double(xs[4 * n4 + threadIdx.x]);
     block_sums<1>(acc, part + (size_t)blockIdx.y * nbu, nbu);
+    double* o = out + (size_t)blockIdx.y * ostride;
+    if (finish_last<1>(part + (size_t)blockIdx.y * nbu, nbu, o, cnt + blockIdx.y) && threadIdx.x == 0)
+        o[1] = o[0] / n;
 }
 
 // Blocks of a pass over `items` loads (pairs of doubles, or float4): about
@@ -383,7 +395,8 @@ PtrArr pack(const void* const* V, int k) {
 // GB300's FP64 pipe, so one per element made this pass FP64-bound; the
 // FP32 sum of four adds a relative rounding of about 2^-23 to each term,
 // below the FP32 data's own.
-__global__ void __launch_bounds__(KT) k_sum_f32x4(int n, const float* __restrict__ x, double* part) {
+__global__ void __launch_bounds__(KT) k_sum_f32x4(int n, const float* __restrict__ x, double* part,
+                                                   double* out, unsigned* cnt) {
     pdl_entry();
     const int n4 = n >> 2;
     const float4* x4 = reinterpret_cast<const float4*>(x);
@@ -394,14 +407,13 @@ __global__ void __launch_bounds__(KT) k_sum_f32x4(int n, const float* __restrict
     }
     if (blockIdx.x == 0 && threadIdx.x < (n & 3)) acc[0] += double(x[4 * n4 + threadIdx.x]);
     block_sums<1>(acc, part, gridDim.x);
+    if (finish_last<1>(part, gridDim.x, out, cnt) && threadIdx.x == 0) out[1] = out[0] / n;
 }
 
 }  // namespace
 
-void launch_sum_f32x4(int n, const float* x, double* scratch, double* out, cudaStream_t s) {
-    const int nb = kry_blocks(n >> 2);
-    launch_pdl(k_sum_f32x4, dim3(nb), dim3(KT), s, n, x, scratch);
-    launch_pdl(k_final_multi, dim3(1), dim3(KT), s, scratch, out, nb);
+void launch_sum_f32x4(int n, const float* x, double* scratch, double* out, unsigned* cnt, cudaStream_t s) {
+    launch_pdl(k_sum_f32x4, dim3(kry_blocks(n >> 2)), dim3(KT), s, n, x, scratch, out, cnt);
 }
 
 #define STK_J_CASES(X) \
@@ -409,17 +421,16 @@ void launch_sum_f32x4(int n, const float* x, double* scratch, double* out, cudaS
     X(16) X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29) X(30) X(31)
 
 void launch_multidot(int n, int j, const double* const* V, const double* w, double* scratch,
-                     double* h, cudaStream_t s) {
+                     double* h, unsigned* cnt, cudaStream_t s) {
     PtrArr pa = pack(reinterpret_cast<const void* const*>(V), j + 1);
     const int nb = kry_blocks(n >> 1);
     switch (j) {
-    case -1: launch_pdl(k_mdot<-1>, dim3(nb), dim3(KT), s, n, pa, w, scratch); break;
-#define X(J) case J: launch_pdl(k_mdot<J>, dim3(nb), dim3(KT), s, n, pa, w, scratch); break;
+    case -1: launch_pdl(k_mdot<-1>, dim3(nb), dim3(KT), s, n, pa, w, scratch, h, cnt); break;
+#define X(J) case J: launch_pdl(k_mdot<J>, dim3(nb), dim3(KT), s, n, pa, w, scratch, h, cnt); break;
     STK_J_CASES(X)
 #undef X
     default: return;
     }
-    launch_pdl(k_final_multi, dim3(j + 2), dim3(KT), s, scratch, h, nb);
 }
 
 template <typename TV>
@@ -446,40 +457,33 @@ void launch_combine_dev(int n, int m, const TV* const* V, const double* y, const
 }
 
 void launch_mgs_step(int n, const double* vk, const double* u, const double* h, int k, double* w,
-                     double* scratch, double* out, cudaStream_t s) {
-    const int nb = kry_blocks(n >> 1);
-    launch_pdl(k_mgs_step, dim3(nb), dim3(KT), s, n, vk, u, h, k, w, scratch);
-    launch_pdl(k_final_multi, dim3(1), dim3(KT), s, scratch, out, nb);
+                     double* scratch, double* out, unsigned* cnt, cudaStream_t s) {
+    launch_pdl(k_mgs_step, dim3(kry_blocks(n >> 1)), dim3(KT), s, n, vk, u, h, k, w, scratch, out, cnt);
 }
 
 void launch_sum_f32x4_sl(int n, int nsl, const float* x, double* scratch, double* out, int ostride,
-                         cudaStream_t s) {
-    const int nbu = kry_blocks(n >> 2);
-    launch_pdl(k_sum_f32x4_sl, dim3(nbu, nsl), dim3(KT), s, n, x, scratch, nbu);
-    launch_pdl(k_final_multi_sl, dim3(1, nsl), dim3(KT), s, scratch, out, nbu, 1, ostride);
+                         unsigned* cnt, cudaStream_t s) {
+    launch_pdl(k_sum_f32x4_sl, dim3(kry_blocks(n >> 2), nsl), dim3(KT), s, n, x, scratch, out, ostride, cnt);
 }
 
 void launch_multidot_sl(const SliceMap& m, int nsl, int j, const double* const* V, const double* w,
-                        double* scratch, double* h, int hstride, cudaStream_t s) {
+                        double* scratch, double* h, int hstride, unsigned* cnt, cudaStream_t s) {
     PtrArr pa = pack(reinterpret_cast<const void* const*>(V), j + 1);
-    const int nbu = kry_blocks(m.nl >> 1);
-    const dim3 gr(nbu, nsl);
+    const dim3 gr(kry_blocks(m.nl >> 1), nsl);
     switch (j) {
-    case -1: launch_pdl(k_mdot_sl<-1>, gr, dim3(KT), s, m, pa, w, scratch, nbu); break;
-#define X(J) case J: launch_pdl(k_mdot_sl<J>, gr, dim3(KT), s, m, pa, w, scratch, nbu); break;
+    case -1: launch_pdl(k_mdot_sl<-1>, gr, dim3(KT), s, m, pa, w, scratch, h, hstride, cnt); break;
+#define X(J) case J: launch_pdl(k_mdot_sl<J>, gr, dim3(KT), s, m, pa, w, scratch, h, hstride, cnt); break;
     STK_J_CASES(X)
 #undef X
     default: return;
     }
-    launch_pdl(k_final_multi_sl, dim3(j + 2, nsl), dim3(KT), s, scratch, h, nbu, j + 2, hstride);
 }
 
 void launch_mgs_step_sl(const SliceMap& m, int nsl, const double* vk, const double* u, const double* h,
                         int hstride, int k, double* w, double* scratch, double* out, int ostride,
-                        cudaStream_t s) {
-    const int nbu = kry_blocks(m.nl >> 1);
-    launch_pdl(k_mgs_step_sl, dim3(nbu, nsl), dim3(KT), s, m, vk, u, h, hstride, k, w, scratch, nbu);
-    launch_pdl(k_final_multi_sl, dim3(1, nsl), dim3(KT), s, scratch, out, nbu, 1, ostride);
+                        unsigned* cnt, cudaStream_t s) {
+    launch_pdl(k_mgs_step_sl, dim3(kry_blocks(m.nl >> 1), nsl), dim3(KT), s, m, vk, u, h, hstride, k, w,
+               scratch, out, ostride, cnt);
 }
 
 template <typename TV>

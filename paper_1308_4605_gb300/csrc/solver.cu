@@ -146,6 +146,7 @@ struct stk_handle {
     CLevel<double>* clsd = nullptr;
     CLevel<float>* clsf = nullptr;
     double* red = nullptr;    // reduction scratch (RED_BLOCKS * 36 doubles)
+    unsigned* rcnt = nullptr; // counts of the reductions' last blocks (one per instance)
     double* dsc = nullptr;    // device scalars
     double* hpin = nullptr;   // pinned host staging
     bool prof = false;
@@ -679,13 +680,14 @@ void cell_sum(stk_handle* h, int n, const T* x, double* out, cudaStream_t s) {
     const int nsl = h->nsl;
     if constexpr (sizeof(T) == 4) {
         if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
-            if (nsl > 1) launch_sum_f32x4_sl(n / nsl, nsl, reinterpret_cast<const float*>(x), h->red, out, NDSC, s);
-            else launch_sum_f32x4(n, reinterpret_cast<const float*>(x), h->red, out, s);
+            if (nsl > 1)
+                launch_sum_f32x4_sl(n / nsl, nsl, reinterpret_cast<const float*>(x), h->red, out, NDSC, h->rcnt, s);
+            else launch_sum_f32x4(n, reinterpret_cast<const float*>(x), h->red, out, h->rcnt, s);
             return;
         }
     }
-    if (nsl > 1) launch_sum_sl<T>(n / nsl, nsl, x, h->red, out, NDSC, s);
-    else launch_sum<T>(n, x, h->red, out, s);
+    if (nsl > 1) launch_sum_sl<T>(n / nsl, nsl, x, h->red, out, NDSC, h->rcnt, s);
+    else launch_sum<T>(n, x, h->red, out, h->rcnt, s);
 }
 
 // out = in - mean(in) (per instance of a stacked batch; sum from cell_sum)
@@ -705,7 +707,7 @@ void poisson_solve(stk_handle* h, const T* r, T* phi, const MGParams& mp, cudaSt
     PBuf<T>& B = pbuf_of<T>(h);
     const int nc = L.g.ncell;
     {
-        Scope sc(h, PF_MEAN, 2.0 * sizeof(T) * nc, s, 4);
+        Scope sc(h, PF_MEAN, 2.0 * sizeof(T) * nc, s, 2);
         cell_sum<T>(h, nc, r, h->dsc + DS_SUM, s);
         sub_mean<T>(h, nc, r, W.rhs_p, h->dsc + DS_SUM, s);
     }
@@ -718,7 +720,7 @@ void poisson_solve(stk_handle* h, const T* r, T* phi, const MGParams& mp, cudaSt
             launch_cell_residual<T>(L.g, coef_of<T>(L), phi, W.rhs_p, B.rp, s);
         }
         {
-            Scope sc(h, PF_MEAN, 3.0 * sizeof(T) * nc, s, 4);
+            Scope sc(h, PF_MEAN, 3.0 * sizeof(T) * nc, s, 2);
             cell_sum<T>(h, nc, B.rp, h->dsc + DS_SUM + 4, s);
             sub_mean<T>(h, nc, B.rp, B.rp, h->dsc + DS_SUM + 4, s);
         }
@@ -747,7 +749,7 @@ void velocity_solve(stk_handle* h, const T* r, T* x, const MGParams& mp, cudaStr
 template <typename T>
 void remove_mean(stk_handle* h, T* x, cudaStream_t s) {
     const Level& L = h->lev[0];
-    Scope sc(h, PF_MEAN, 3.0 * sizeof(T) * L.g.ncell, s, 4);
+    Scope sc(h, PF_MEAN, 3.0 * sizeof(T) * L.g.ncell, s, 2);
     cell_sum<T>(h, L.g.ncell, x, h->dsc + DS_SUM + 2, s);
     sub_mean<T>(h, L.g.ncell, x, x, h->dsc + DS_SUM + 2, s);
 }
@@ -953,29 +955,29 @@ void orth_enqueue(stk_handle* h, int j, cudaStream_t s) {
     double* w = h->V[j + 1];
     double* hd = h->dsc + DS_H;
     {
-        Scope sc(h, PF_MDOT, 16.0 * n, s, 2);
+        Scope sc(h, PF_MDOT, 16.0 * n, s, 1);
         const double* v0 = h->V[0];
-        if (sl) launch_multidot_sl(h->smap, h->nsl, 0, &v0, w, h->red, hd, NDSC, s);
-        else launch_multidot(n, 0, &v0, w, h->red, hd, s);
+        if (sl) launch_multidot_sl(h->smap, h->nsl, 0, &v0, w, h->red, hd, NDSC, h->rcnt, s);
+        else launch_multidot(n, 0, &v0, w, h->red, hd, h->rcnt, s);
     }
     for (int k = 0; k <= j; ++k) {
         const bool last = k == j;
-        Scope sc(h, PF_UPD, 8.0 * n * (last ? 3 : 4), s, 2);
+        Scope sc(h, PF_UPD, 8.0 * n * (last ? 3 : 4), s, 1);
         double* out = last ? h->dsc + DS_N2 : hd + k + 1;
         if (sl)
             launch_mgs_step_sl(h->smap, h->nsl, h->V[k], last ? nullptr : h->V[k + 1], hd, NDSC, k, w,
-                               h->red, out, NDSC, s);
+                               h->red, out, NDSC, h->rcnt, s);
         else
-            launch_mgs_step(n, h->V[k], last ? nullptr : h->V[k + 1], hd, k, w, h->red, out, s);
+            launch_mgs_step(n, h->V[k], last ? nullptr : h->V[k + 1], hd, k, w, h->red, out, h->rcnt, s);
     }
 }
 
 // out[0] = ||x||^2 (device; per instance of a stacked batch at stride NDSC)
 void norm_enqueue(stk_handle* h, const double* x, double* out, cudaStream_t s) {
     const int n = nstokes(h);
-    Scope sc(h, PF_MDOT, 8.0 * n, s, 2);
-    if (h->nsl > 1) launch_multidot_sl(h->smap, h->nsl, -1, nullptr, x, h->red, out, NDSC, s);
-    else launch_multidot(n, -1, nullptr, x, h->red, out, s);
+    Scope sc(h, PF_MDOT, 8.0 * n, s, 1);
+    if (h->nsl > 1) launch_multidot_sl(h->smap, h->nsl, -1, nullptr, x, h->red, out, NDSC, h->rcnt, s);
+    else launch_multidot(n, -1, nullptr, x, h->red, out, h->rcnt, s);
 }
 
 struct CycleCtx {
@@ -1881,6 +1883,7 @@ int create_handle(int dim, const int* n, double hh, const int* bc, int nsl, stk_
     CKC(dalloc(h, &h->xk, ns));
     CKC(dalloc(h, &h->tmp, ns));
     CKC(dalloc(h, &h->red, (size_t)RED_SCRATCH * nsl));
+    CKC(dalloc(h, &h->rcnt, (size_t)nsl));
     for (int a = 0; a < g0.dim; ++a) CKC(dalloc(h, &h->sw.tc[a], g0.ncell));
     for (int p = 0; p < 3; ++p)
         if (g0.esize[p] > 0) CKC(dalloc(h, &h->sw.te[p], g0.esize[p]));
@@ -2589,7 +2592,7 @@ int stk_remove_mean(stk_handle* h, const double* x_p, double* y_p, void* stream)
     CK(cudaSetDevice(h->device));
     const int nc = h->lev[0].g.ncell;
     {
-        Scope sc(h, PF_MEAN, 2.0 * sizeof(double) * nc, s, 4);
+        Scope sc(h, PF_MEAN, 2.0 * sizeof(double) * nc, s, 2);
         cell_sum<double>(h, nc, x_p, h->dsc + DS_SUM + 6, s);
         sub_mean<double>(h, nc, x_p, y_p, h->dsc + DS_SUM + 6, s);
     }
