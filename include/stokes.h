@@ -358,7 +358,8 @@ int stk_solve_batched(int count, stk_handle* const* hs, const stk_solver_params*
  * not depend on the schedule, except that with coarse_level = 0 the finest
  * level's FP64 residual is evaluated point by point instead of through the
  * stresses of the grid kernels (equal up to rounding).  stk_autotune times one velocity + one
- * pressure V-cycle (as a captured graph) for every admissible schedule,
+ * pressure V-cycle (as a captured graph) for every admissible schedule
+ * (grid_level excepted: measured slower than cluster_level everywhere),
  * applies the fastest and returns it; stk_set_schedule applies a known one
  * (e.g. cached from an earlier run). */
 typedef struct {

@@ -2418,16 +2418,16 @@ int stk_autotune(stk_handle* h, int precision, stk_schedule* best, void* stream)
         int pls[4], npl = 0;
         for (int p = 0; p < 3 && p < lc; ++p) pls[npl++] = p;
         pls[npl++] = lc;
-        // the persistent multi-block kernel (grid_level) or the cluster
-        // kernel (cluster_level) from one or two levels above the
-        // single-block one, or neither (= lc)
+        // the cluster kernel (cluster_level) from one or two levels above
+        // the single-block one, or not (= lc).  The persistent multi-block
+        // kernel (grid_level) is not tried: it was slower than the cluster
+        // kernel on every grid measured (it stays available to
+        // stk_set_schedule).
         int gls[5], cls[5], ngl = 0;
         gls[ngl] = lc;
         cls[ngl++] = lc;
         for (int d = 1; d <= 2 && lc - d >= 0 && h->nsl == 1; ++d)
             if (h->lev[lc - d].g.ncell <= 262144) {
-                gls[ngl] = lc - d;
-                cls[ngl++] = lc;
                 gls[ngl] = lc;
                 cls[ngl++] = lc - d;
             }
