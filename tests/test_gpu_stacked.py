@@ -284,3 +284,35 @@ def test_stacked_rejects(S):
     with pytest.raises(S.StokesError):
         S.stk_set_schedule(st.handle, 0, 2, 256, 2, 0)
     _close(st, singles)
+
+
+def test_stacked_batch_helper_mixed_sizes(S):
+    """paper_1308_4605_gb300.batch.StackedBatch: problems of three grids
+    (periodic 32^2 and 64^2, walled 32x16) in one call; each instance equals,
+    bitwise, the solve on its own handle (ncoarse = 6), and the oracle's exact
+    solution to 1e-8."""
+    from paper_1308_4605_gb300.batch import StackedBatch, problem_dict
+    prs = (_instances((32, 32), (PERIODIC,) * 4, 3, seed=61)
+           + _instances((64, 64), (PERIODIC,) * 4, 2, seed=71)
+           + _instances((32, 16), (NOSLIP,) * 4, 2, seed=81))
+    prs = [prs[i] for i in (0, 3, 5, 1, 6, 4, 2)]          # interleaved sizes
+    sb = StackedBatch([problem_dict(p) for p in prs])
+    assert len(sb.groups) == 3
+    bus = [[_t(x) for x in p.b_u] for p in prs]
+    bps = [_t(p.b_p) for p in prs]
+    xu, xp, infos = sb.solve(bus, bps, precond=1, ncoarse=6)
+    torch.cuda.synchronize()
+    for i, p in enumerate(prs):
+        assert infos[i]["converged"], (i, infos[i])
+        sv = S.StokesSolver(2, p.n[:2], p.bc[:4], p.h)
+        sv.set_coefficients(_t(p.rho), _t(p.mu), p.theta)
+        zu, zp, inf1 = sv.solve(bus[i], bps[i], precond=1, ncoarse=6)
+        sv.close()
+        assert inf1["iterations"] == infos[i]["iterations"]
+        assert _eqv(zu, xu[i]) and _eq(zp, xp[i])
+        g = Grid(2, p.n, p.h, p.bc)
+        M = asm.stokes_from_fields(g, p.rho, p.mu, p.theta)
+        b = g.pack(p.b_u, p.b_p)
+        x = g.pack([v.cpu().numpy() for v in xu[i]], xp[i].cpu().numpy())
+        assert max(direct.relative_error(g, x, direct.solve(g, M, b))) <= 1e-8
+    sb.close()
