@@ -316,3 +316,52 @@ def test_stacked_batch_helper_mixed_sizes(S):
         x = g.pack([v.cpu().numpy() for v in xu[i]], xp[i].cpu().numpy())
         assert max(direct.relative_error(g, x, direct.solve(g, M, b))) <= 1e-8
     sb.close()
+
+
+@pytest.mark.parametrize("n,bc", GRIDS[:2])
+def test_stacked_entry_points_per_instance(S, n, bc):
+    """The other calls on a stacked handle act on each instance as alone:
+    the two V-cycles, repeated V-cycles per subsolve (P1..P5, 2 + 3 cycles,
+    sweeping coarsest level), the pressure mean removal and the
+    backward-Euler right-hand side, bitwise; the V-cycles with the default
+    coarsest solve to 1e-12."""
+    theta = 1.0
+    prs = _instances(n, bc, 3, seed=91, theta=theta)
+    st, bu, bp, singles = _stack(S, prs)
+    # V-cycles (default parameters)
+    xu = [torch.zeros_like(v) for v in bu]
+    xp = torch.zeros_like(bp)
+    S.stk_velocity_vcycle(st.handle, bu, xu)
+    S.stk_pressure_vcycle(st.handle, bp - bp.mean(dim=(1, 2), keepdim=True), xp)
+    for i, sv in enumerate(singles):
+        zu, zp = sv.zeros()
+        S.stk_velocity_vcycle(sv.handle, _slice(bu, i), zu)
+        rp = (bp[i] - bp[i].mean()).reshape(zp.shape).contiguous()
+        S.stk_pressure_vcycle(sv.handle, rp, zp)
+        for a, b in zip(zu + [zp], _slice(xu, i) + [xp[i]]):
+            a, b = a.reshape(-1), b.reshape(-1)
+            assert torch.linalg.norm(a - b) <= 1e-12 * torch.linalg.norm(a)
+    # repeated V-cycles per subsolve
+    for which in (1, 2, 3, 4, 5):
+        xu, xp = st.apply_preconditioner(which, bu, bp, ncoarse=6, vcycles_u=2, vcycles_p=3)
+        for i, sv in enumerate(singles):
+            zu, zp = sv.apply_preconditioner(which, _slice(bu, i), bp[i], ncoarse=6, vcycles_u=2,
+                                             vcycles_p=3)
+            assert _eqv(zu, _slice(xu, i)) and _eq(zp, xp[i]), which
+    # mean removal
+    yp = torch.empty_like(bp)
+    S.stk_remove_mean(st.handle, bp, yp)
+    for i, sv in enumerate(singles):
+        zp = torch.empty_like(bp[i])
+        S.stk_remove_mean(sv.handle, bp[i].contiguous(), zp)
+        assert _eq(zp, yp[i])
+    # backward-Euler right-hand side
+    fu = [torch.randn_like(v) for v in bu]
+    ou = [torch.empty_like(v) for v in bu]
+    S.stk_backward_euler_rhs(st.handle, bu, fu, ou)
+    for i, sv in enumerate(singles):
+        zu = [torch.empty_like(v) for v in _slice(bu, i)]
+        S.stk_backward_euler_rhs(sv.handle, [v.contiguous() for v in _slice(bu, i)],
+                                 [v.contiguous() for v in _slice(fu, i)], zu)
+        assert _eqv(zu, _slice(ou, i))
+    _close(st, singles)
