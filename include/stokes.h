@@ -120,10 +120,12 @@ int stk_create(int dim, const int* n, double h, const int* bc, stk_handle** out)
  * of a V-cycle, of the operator and of the preconditioner runs once over
  * all instances, the reductions and the GMRES least-squares problems
  * (Sec. 3.2) per instance, and an instance's results equal those of a
- * handle made by stk_create for it alone (bitwise for the operator,
- * V-cycles and preconditioners when the coarsest level sweeps, i.e.
- * ncoarse != 8; the single handle applies a precomputed coarse-solve matrix
- * for ncoarse = 8).  stk_solve on the handle solves every instance, one
+ * handle made by stk_create for it alone: bitwise for the operator,
+ * V-cycles, preconditioners and solves whenever the coarsest level runs in
+ * the coarse-level kernel (as in the default schedules: each instance then
+ * applies its own precomputed coarse-solve matrix, like a single handle) or
+ * sweeps (ncoarse != 8); to rounding when a stacked handle sweeps a
+ * coarsest level that a single handle applies as a matrix.  stk_solve on the handle solves every instance, one
  * CUDA graph launch per GMRES cycle for all of them; an instance that has
  * converged sits out the rest of the solve and its solution is final.  The
  * solve's info summarises the instances (iterations, restarts, residuals
