@@ -202,14 +202,27 @@ def traffic_per_launch(family, form, workload):
     return None
 
 
+# kernel families that pool launches on grids of every size (the per-level
+# smoothers below the finest level, the first sweeps from zero on every
+# level, the coarse-level kernels): not one kernel configuration, so never
+# "the dominant kernel" of a roofline
+MULTI_LEVEL_FAMILIES = {"vel_smooth_colour", "cell_smooth_colour", "vel_smooth_pair",
+                        "cell_smooth_pair", "vel_smooth_first", "cell_smooth_first", "coarse_levels"}
+
+
 def roofline_of(fams, form, peaks, family=None, workload=TRAFFIC_WORKLOAD):
-    """Roofline of the dominant kernel family of a solve (largest device
-    time), or of `family`.  FP64 Gauss-Seidel kernels are bound by the FP64 pipe (about 0.19
+    """Roofline of the dominant kernel of a solve -- the family with the
+    largest device time among those that are one kernel configuration
+    (MULTI_LEVEL_FAMILIES pool many grid sizes and are left out) -- or of
+    `family`.  FP64 Gauss-Seidel kernels are bound by the FP64 pipe (about 0.19
     FLOP per byte, at the GB300 balance of 1.25 TFLOP/s over 6.8 TB/s, with
     the pipe 80-89 % busy under ncu): reported as "alu" in TFLOP/s.  The rest
     is reported against HBM bandwidth."""
-    dom = max(fams, key=lambda f: f["ms"]) if family is None else \
-        next(f for f in fams if f["name"] == family)
+    if family is None:
+        single = [f for f in fams if f["name"] not in MULTI_LEVEL_FAMILIES]
+        dom = max(single or fams, key=lambda f: f["ms"])
+    else:
+        dom = next(f for f in fams if f["name"] == family)
     secs = dom["ms"] * 1e-3
     per_launch_us = dom["ms"] * 1e3 / dom["launches"]
     traffic = traffic_per_launch(dom["name"], form, workload) if dom["name"].endswith("_l0") else None

@@ -29,3 +29,13 @@ def test_roofline_alu_and_hbm_fractions():
     m = bench.roofline_of(fams, "mixed", peaks, "vel_smooth_colour_l0", "other")
     assert m["bound"] == "hbm" and m["peak"] == 6790.3
     assert abs(m["achieved"] - 10 * 134217728.0 / 0.4e-3 / 1e9) < 1e-9
+
+
+def test_dominant_kernel_is_one_kernel_configuration():
+    """A family that pools launches on every grid size (the smoothers below
+    the finest level) is not the dominant kernel even with the most time."""
+    fams = [{"name": "vel_smooth_colour", "launches": 900, "ms": 9.0, "bytes": 1e9, "flops": 1e9},
+            {"name": "vel_smooth_colour_l0", "launches": 200, "ms": 8.0, "bytes": 2e10, "flops": 4e9},
+            {"name": "arnoldi_update", "launches": 100, "ms": 5.0, "bytes": 2e10, "flops": 0.0}]
+    r = bench.roofline_of(fams, "fp64", {"hbm_gbs": 6790.3}, workload="other")
+    assert r["kernel"] == "vel_smooth_colour_l0"
