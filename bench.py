@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--quick", action="store_true",
                     help="profiling runs: only the timed solves of --form, no baseline/e2e/profile passes")
     ap.add_argument("--form", default="both", choices=["both", "fp64", "mixed"])
+    ap.add_argument("--batched-forms", default="",
+                    help="--workload c4: comma-separated forms to time (e.g. stacked_mixed; for "
+                         "profilers), else every form")
     ap.add_argument("--no-graphs", action="store_true",
                     help="quick mode: launch every kernel from the host (for profilers)")
     ap.add_argument("--schedule", default="",
@@ -533,7 +536,7 @@ def run_ours(args):
     return 0
 
 
-def measure_batched(steps, warmup, e2e=True):
+def measure_batched(steps, warmup, e2e=True, only=None):
     """64 independent 2D periodic unsteady instances of {64..512}^2 (sizes
     drawn by seed), mu contrast 1e3, P1: one after another with the FP64
     solver; all together with stk_solve_batched over one handle per instance
@@ -646,13 +649,6 @@ def measure_batched(steps, warmup, e2e=True):
             times.append(e0.elapsed_time(e1))
         return statistics.mean(times), infos
 
-    for _ in range(warmup):
-        sequential(S.STK_FP64)
-        batched(S.STK_FP64)
-        batched(S.STK_MIXED)
-        for prec in (S.STK_FP64, S.STK_MIXED):
-            stacked(prec)
-            stacked_batched(prec)
     res = {}
     forms = (("sequential_fp64", sequential, S.STK_FP64),
              ("batched_fp64", batched, S.STK_FP64),
@@ -662,12 +658,18 @@ def measure_batched(steps, warmup, e2e=True):
              ("stacked_mixed", stacked, S.STK_MIXED),
              ("stacked_batched_fp64", stacked_batched, S.STK_FP64),
              ("stacked_batched_mixed", stacked_batched, S.STK_MIXED))
+    if only:   # a subset (profiling runs): no comparison solves, no e2e
+        forms = tuple(f for f in forms if f[0] in only)
+        e2e = False
+    for _ in range(warmup):
+        for name, fn, prec in forms:
+            fn(prec)
     for name, fn, prec in forms:
         ms, infos = timed(fn, prec, steps)
         res[name] = {"ms": ms, "iterations_total": int(sum(i["iterations"] for i in infos)),
                      "max_true_residual": max(i["true_residual"] for i in infos),
                      "all_converged": all(i["converged"] for i in infos)}
-        if name.startswith("stacked"):
+        if name.startswith("stacked") and not only:
             # every instance against its own-handle solution of the same form
             ref = batched(prec)
             diff = 0.0
@@ -677,12 +679,15 @@ def measure_batched(steps, warmup, e2e=True):
                     b = torch.cat([v.reshape(-1) for v in xus[i]] + [xps[i].reshape(-1)])
                     diff = max(diff, float(torch.linalg.norm(a - b) / torch.linalg.norm(b)))
             res[name]["max_rel_diff_vs_per_handle_solution"] = diff
-    best = min((n for n in res if n.startswith(("batched", "stacked"))), key=lambda n: res[n]["ms"])
+    best = min((n for n in res if n.startswith(("batched", "stacked"))), key=lambda n: res[n]["ms"],
+               default=min(res, key=lambda n: res[n]["ms"]))
+    seq = res.get("sequential_fp64")
     out = {"forms": res, "sizes_histogram": {str(n): sizes.count(n) for n in sorted(set(sizes))},
            "cells": int(sum(n * n for n in sizes)), "fastest_batched_form": best,
            "stacked_groups": {str(gr["n"]): len(gr["idx"]) for gr in groups},
-           "speedup_batched_mixed_vs_sequential_fp64": res["sequential_fp64"]["ms"] / res["batched_mixed"]["ms"],
-           "speedup_fastest_vs_sequential_fp64": res["sequential_fp64"]["ms"] / res[best]["ms"]}
+           "speedup_batched_mixed_vs_sequential_fp64":
+               seq["ms"] / res["batched_mixed"]["ms"] if seq and "batched_mixed" in res else None,
+           "speedup_fastest_vs_sequential_fp64": seq["ms"] / res[best]["ms"] if seq else None}
     fns = {name: (fn, prec) for name, fn, prec in forms}
     if e2e:
         # the fastest form from pinned host buffers: the per-handle forms copy
@@ -838,7 +843,8 @@ def other_configs(steps, warmup, peaks):
 
 
 def run_batched(args):
-    r = measure_batched(args.steps, args.warmup)
+    only = set(f for f in args.batched_forms.split(",") if f) or None
+    r = measure_batched(args.steps, args.warmup, only=only)
     res = r["forms"]
     best = r["fastest_batched_form"]
     line = {"metric": METRIC, "value": res[best]["ms"], "unit": UNIT, "n_gpus": 1,
