@@ -59,7 +59,8 @@ def parse():
                     help="--workload c4: comma-separated forms to time (e.g. stacked_mixed; for "
                          "profilers), else every form")
     ap.add_argument("--no-graphs", action="store_true",
-                    help="quick mode: launch every kernel from the host (for profilers)")
+                    help="quick mode and the stacked forms of --workload c4: launch every kernel "
+                         "from the host (for profilers)")
     ap.add_argument("--schedule", default="",
                     help="quick mode: coarse_level,threads,pair_level instead of the tuned schedule")
     ap.add_argument("--big", action="store_true",
@@ -536,7 +537,7 @@ def run_ours(args):
     return 0
 
 
-def measure_batched(steps, warmup, e2e=True, only=None):
+def measure_batched(steps, warmup, e2e=True, only=None, graphs=True):
     """64 independent 2D periodic unsteady instances of {64..512}^2 (sizes
     drawn by seed), mu contrast 1e3, P1: one after another with the FP64
     solver; all together with stk_solve_batched over one handle per instance
@@ -583,6 +584,8 @@ def measure_batched(steps, warmup, e2e=True, only=None):
         bu = [stk([prs[i].b_u[a] for i in idx], sv.face_shape(a)) for a in range(2)]
         bp = stk([prs[i].b_p for i in idx], sv.cell_shape())
         xu, xp = sv.zeros(dev)
+        if not graphs:   # every kernel launched from the host (for profilers)
+            S.stk_set_graphs(sv.handle, 0)
         groups.append({"n": n, "idx": idx, "sv": sv, "bu": bu, "bp": bp, "xu": xu, "xp": xp})
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -844,7 +847,7 @@ def other_configs(steps, warmup, peaks):
 
 def run_batched(args):
     only = set(f for f in args.batched_forms.split(",") if f) or None
-    r = measure_batched(args.steps, args.warmup, only=only)
+    r = measure_batched(args.steps, args.warmup, only=only, graphs=not args.no_graphs)
     res = r["forms"]
     best = r["fastest_batched_form"]
     line = {"metric": METRIC, "value": res[best]["ms"], "unit": UNIT, "n_gpus": 1,
