@@ -446,7 +446,7 @@ void launch_sum_sl(int n, int nsl, const T* x, double* scratch, double* out, int
 // out = in - sum[y * stride + 1] per instance y (in == out allowed)
 template <typename T>
 void launch_sub_mean_sl(int n, int nsl, const T* in, T* out, const double* sum, int stride, cudaStream_t s);
-// h[i] = <w, V_i> for i <= j and h[j+1] = <w, w>;  V = array of j+1 device pointers
+// j = 0: h[0] = <w, V[0]>; j = -1: h[0] = <w, w> (V unused)
 void launch_multidot(int n, int j, const double* const* V, const double* w, double* scratch,
                      double* h, unsigned* cnt, cudaStream_t s);
 // modified Gram-Schmidt step: w -= h[k] vk, then out[0] = <w, u> (u = null: <w, w>)

@@ -622,13 +622,29 @@ __device__ __forceinline__ void finish_sum(const double* part, int n, double* ou
     }
 }
 
+// s + x[i] + x[i + st] + ... over i < n, added in that order; the loads of
+// eight steps are issued before their adds (a thread of a reduction grid
+// has tens of steps, each a dependent FP64 add)
+template <typename T>
+__device__ __forceinline__ double strided_sum(const T* __restrict__ x, int i, int n, int st) {
+    constexpr int U = 8;
+    double s = 0.0;
+    for (; i < n - (U - 1) * st; i += U * st) {
+        T v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = x[i + u * st];
+#pragma unroll
+        for (int u = 0; u < U; ++u) s += double(v[u]);
+    }
+    for (; i < n; i += st) s += double(x[i]);
+    return s;
+}
+
 template <typename T>
 __global__ void k_sum_partials(int n, const T* __restrict__ x, double* part, double* out, unsigned* cnt) {
     pdl_entry();
     __shared__ double sh[32];
-    double s = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        s += double(x[i]);
+    double s = strided_sum(x, blockIdx.x * blockDim.x + threadIdx.x, n, gridDim.x * blockDim.x);
     s = block_sum(s, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
     finish_sum(part, n, out, cnt);
@@ -676,9 +692,7 @@ __global__ void k_sum_partials_sl(int n, const T* __restrict__ x, double* part, 
     pdl_entry();
     __shared__ double sh[32];
     const T* xs = x + (size_t)blockIdx.y * n;
-    double s = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        s += double(xs[i]);
+    double s = strided_sum(xs, blockIdx.x * blockDim.x + threadIdx.x, n, gridDim.x * blockDim.x);
     s = block_sum(s, sh);
     double* p = part + (size_t)blockIdx.y * gridDim.x;
     if (threadIdx.x == 0) p[blockIdx.x] = s;

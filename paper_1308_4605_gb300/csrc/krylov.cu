@@ -87,35 +87,101 @@ __device__ __forceinline__ bool finish_last(const double* part, int nb, double* 
     return true;
 }
 
-// h[i] = <w, V_i> (i <= J) and h[J+1] = <w, w>
+// Number of grid-stride steps whose loads a read-only pass issues before
+// using any of them (its adds keep the order of the steps).
+constexpr int LOOKAHEAD = 4;
+
+// The partial sums of pass J of thread pair index t, stride st, over the
+// pairs t < n2: acc[i] += <w, V_i> (i <= J), or acc[0] += <w, w> for J = -1,
+// pair after pair.  `pair(t)` maps a step to its pair of values.
+template <int J, typename PairOf>
+__device__ __forceinline__ void dot_pass(const PtrArr& V, const double2* __restrict__ w2, int t, int n2,
+                                         int st, PairOf pair, double (&acc)[J >= 0 ? J + 1 : 1]) {
+    for (; t < n2 - (LOOKAHEAD - 1) * st; t += LOOKAHEAD * st) {
+        int p[LOOKAHEAD];
+        double2 a[LOOKAHEAD];
+#pragma unroll
+        for (int u = 0; u < LOOKAHEAD; ++u) {
+            p[u] = pair(t + u * st);
+            a[u] = w2[p[u]];
+        }
+        if constexpr (J < 0) {
+#pragma unroll
+            for (int u = 0; u < LOOKAHEAD; ++u) {
+                acc[0] = fma(a[u].x, a[u].x, acc[0]);
+                acc[0] = fma(a[u].y, a[u].y, acc[0]);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i <= J; ++i) {
+                double2 v[LOOKAHEAD];
+#pragma unroll
+                for (int u = 0; u < LOOKAHEAD; ++u) v[u] = reinterpret_cast<const double2*>(V.p[i])[p[u]];
+#pragma unroll
+                for (int u = 0; u < LOOKAHEAD; ++u) {
+                    acc[i] = fma(a[u].x, v[u].x, acc[i]);
+                    acc[i] = fma(a[u].y, v[u].y, acc[i]);
+                }
+            }
+        }
+    }
+    for (; t < n2; t += st) {
+        const int p = pair(t);
+        const double2 a = w2[p];
+        if constexpr (J < 0) {
+            acc[0] = fma(a.x, a.x, acc[0]);
+            acc[0] = fma(a.y, a.y, acc[0]);
+        } else {
+#pragma unroll
+            for (int i = 0; i <= J; ++i) {
+                const double2 v = reinterpret_cast<const double2*>(V.p[i])[p];
+                acc[i] = fma(a.x, v.x, acc[i]);
+                acc[i] = fma(a.y, v.y, acc[i]);
+            }
+        }
+    }
+}
+
+// The sum over the float4 steps i, i + st, ... < n4 of each step's four
+// values (summed in FP32 in pairs, widened once), step after step.
+__device__ __forceinline__ double sum4_pass(const float4* __restrict__ x4, int i, int n4, int st) {
+    double s = 0.0;
+    for (; i < n4 - (LOOKAHEAD - 1) * st; i += LOOKAHEAD * st) {
+        float4 v[LOOKAHEAD];
+#pragma unroll
+        for (int u = 0; u < LOOKAHEAD; ++u) v[u] = x4[i + u * st];
+#pragma unroll
+        for (int u = 0; u < LOOKAHEAD; ++u) s += double((v[u].x + v[u].y) + (v[u].z + v[u].w));
+    }
+    for (; i < n4; i += st) {
+        const float4 v = x4[i];
+        s += double((v.x + v.y) + (v.z + v.w));
+    }
+    return s;
+}
+
+// h[i] = <w, V_i> (i <= J); for J = -1, h[0] = <w, w>
 template <int J>
 __global__ void __launch_bounds__(KT) k_mdot(int n, PtrArr V, const double* __restrict__ w,
                                               double* __restrict__ part, double* out, unsigned* cnt) {
+    constexpr int NV = J >= 0 ? J + 1 : 1;
     pdl_entry();
-    double acc[J + 2];
+    double acc[NV];
 #pragma unroll
-    for (int i = 0; i < J + 2; ++i) acc[i] = 0.0;
-    const int n2 = n >> 1;
-    const double2* w2 = reinterpret_cast<const double2*>(w);
-    for (int t = blockIdx.x * KT + threadIdx.x; t < n2; t += gridDim.x * KT) {
-        const double2 a = w2[t];
-#pragma unroll
-        for (int i = 0; i <= J; ++i) {
-            const double2 v = reinterpret_cast<const double2*>(V.p[i])[t];
-            acc[i] = fma(a.x, v.x, acc[i]);
-            acc[i] = fma(a.y, v.y, acc[i]);
-        }
-        acc[J + 1] = fma(a.x, a.x, acc[J + 1]);
-        acc[J + 1] = fma(a.y, a.y, acc[J + 1]);
-    }
+    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    dot_pass<J>(V, reinterpret_cast<const double2*>(w), blockIdx.x * KT + threadIdx.x, n >> 1, gridDim.x * KT,
+                [](int t) { return t; }, acc);
     if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
         const double a = w[n - 1];
+        if constexpr (J < 0) {
+            acc[0] = fma(a, a, acc[0]);
+        } else {
 #pragma unroll
-        for (int i = 0; i <= J; ++i) acc[i] = fma(a, static_cast<const double*>(V.p[i])[n - 1], acc[i]);
-        acc[J + 1] = fma(a, a, acc[J + 1]);
+            for (int i = 0; i <= J; ++i) acc[i] = fma(a, static_cast<const double*>(V.p[i])[n - 1], acc[i]);
+        }
     }
-    block_sums<J + 2>(acc, part, gridDim.x);
-    finish_last<J + 2>(part, gridDim.x, out, cnt);
+    block_sums<NV>(acc, part, gridDim.x);
+    finish_last<NV>(part, gridDim.x, out, cnt);
 }
 
 // One modified Gram-Schmidt step: w -= h[k] v_k, then the block partials
@@ -249,28 +315,17 @@ template <int J>
 __global__ void __launch_bounds__(KT) k_mdot_sl(SliceMap m, PtrArr V, const double* __restrict__ w,
                                                  double* __restrict__ part, double* out, int ostride,
                                                  unsigned* cnt) {
+    constexpr int NV = J >= 0 ? J + 1 : 1;
     const int nbu = gridDim.x;
     pdl_entry();
     const int y = blockIdx.y;
-    double acc[J + 2];
+    double acc[NV];
 #pragma unroll
-    for (int i = 0; i < J + 2; ++i) acc[i] = 0.0;
-    const int n2 = m.nl >> 1;
-    const double2* w2 = reinterpret_cast<const double2*>(w);
-    for (int t = blockIdx.x * KT + threadIdx.x; t < n2; t += gridDim.x * KT) {
-        const int p = sl_pair(m, y, t);
-        const double2 a = w2[p];
-#pragma unroll
-        for (int i = 0; i <= J; ++i) {
-            const double2 v = reinterpret_cast<const double2*>(V.p[i])[p];
-            acc[i] = fma(a.x, v.x, acc[i]);
-            acc[i] = fma(a.y, v.y, acc[i]);
-        }
-        acc[J + 1] = fma(a.x, a.x, acc[J + 1]);
-        acc[J + 1] = fma(a.y, a.y, acc[J + 1]);
-    }
-    block_sums<J + 2>(acc, part + (size_t)y * (J + 2) * nbu, nbu);
-    finish_last<J + 2>(part + (size_t)y * (J + 2) * nbu, nbu, out + (size_t)y * ostride, cnt + y);
+    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    dot_pass<J>(V, reinterpret_cast<const double2*>(w), blockIdx.x * KT + threadIdx.x, m.nl >> 1,
+                gridDim.x * KT, [&m, y](int t) { return sl_pair(m, y, t); }, acc);
+    block_sums<NV>(acc, part + (size_t)y * NV * nbu, nbu);
+    finish_last<NV>(part + (size_t)y * NV * nbu, nbu, out + (size_t)y * ostride, cnt + y);
 }
 
 __global__ void __launch_bounds__(KT) k_mgs_step_sl(SliceMap m, const double* __restrict__ vk,
@@ -360,11 +415,7 @@ __global__ void __launch_bounds__(KT) k_sum_f32x4_sl(int n, const float* __restr
     const float* xs = x + (size_t)blockIdx.y * n;
     const int n4 = n >> 2;
     const float4* x4 = reinterpret_cast<const float4*>(xs);
-    double acc[1] = {0.0};
-    for (int i = blockIdx.x * KT + threadIdx.x; i < n4; i += gridDim.x * KT) {
-        const float4 v = x4[i];
-        acc[0] += double((v.x + v.y) + (v.z + v.w));
-    }
+    double acc[1] = {sum4_pass(x4, blockIdx.x * KT + threadIdx.x, n4, gridDim.x * KT)};
     if (blockIdx.x == 0 && threadIdx.x < (n & 3)) acc[0] += double(xs[4 * n4 + threadIdx.x]);
     block_sums<1>(acc, part + (size_t)blockIdx.y * nbu, nbu);
     double* o = out + (size_t)blockIdx.y * ostride;
@@ -400,11 +451,7 @@ __global__ void __launch_bounds__(KT) k_sum_f32x4(int n, const float* __restrict
     pdl_entry();
     const int n4 = n >> 2;
     const float4* x4 = reinterpret_cast<const float4*>(x);
-    double acc[1] = {0.0};
-    for (int i = blockIdx.x * KT + threadIdx.x; i < n4; i += gridDim.x * KT) {
-        const float4 v = x4[i];
-        acc[0] += double((v.x + v.y) + (v.z + v.w));
-    }
+    double acc[1] = {sum4_pass(x4, blockIdx.x * KT + threadIdx.x, n4, gridDim.x * KT)};
     if (blockIdx.x == 0 && threadIdx.x < (n & 3)) acc[0] += double(x[4 * n4 + threadIdx.x]);
     block_sums<1>(acc, part, gridDim.x);
     if (finish_last<1>(part, gridDim.x, out, cnt) && threadIdx.x == 0) out[1] = out[0] / n;
@@ -422,15 +469,10 @@ void launch_sum_f32x4(int n, const float* x, double* scratch, double* out, unsig
 
 void launch_multidot(int n, int j, const double* const* V, const double* w, double* scratch,
                      double* h, unsigned* cnt, cudaStream_t s) {
-    PtrArr pa = pack(reinterpret_cast<const void* const*>(V), j + 1);
+    PtrArr pa = pack(reinterpret_cast<const void* const*>(V), j < 0 ? 0 : 1);
     const int nb = kry_blocks(n >> 1);
-    switch (j) {
-    case -1: launch_pdl(k_mdot<-1>, dim3(nb), dim3(KT), s, n, pa, w, scratch, h, cnt); break;
-#define X(J) case J: launch_pdl(k_mdot<J>, dim3(nb), dim3(KT), s, n, pa, w, scratch, h, cnt); break;
-    STK_J_CASES(X)
-#undef X
-    default: return;
-    }
+    if (j < 0) launch_pdl(k_mdot<-1>, dim3(nb), dim3(KT), s, n, pa, w, scratch, h, cnt);
+    else launch_pdl(k_mdot<0>, dim3(nb), dim3(KT), s, n, pa, w, scratch, h, cnt);
 }
 
 template <typename TV>
@@ -468,15 +510,10 @@ void launch_sum_f32x4_sl(int n, int nsl, const float* x, double* scratch, double
 
 void launch_multidot_sl(const SliceMap& m, int nsl, int j, const double* const* V, const double* w,
                         double* scratch, double* h, int hstride, unsigned* cnt, cudaStream_t s) {
-    PtrArr pa = pack(reinterpret_cast<const void* const*>(V), j + 1);
+    PtrArr pa = pack(reinterpret_cast<const void* const*>(V), j < 0 ? 0 : 1);
     const dim3 gr(kry_blocks(m.nl >> 1), nsl);
-    switch (j) {
-    case -1: launch_pdl(k_mdot_sl<-1>, gr, dim3(KT), s, m, pa, w, scratch, h, hstride, cnt); break;
-#define X(J) case J: launch_pdl(k_mdot_sl<J>, gr, dim3(KT), s, m, pa, w, scratch, h, hstride, cnt); break;
-    STK_J_CASES(X)
-#undef X
-    default: return;
-    }
+    if (j < 0) launch_pdl(k_mdot_sl<-1>, gr, dim3(KT), s, m, pa, w, scratch, h, hstride, cnt);
+    else launch_pdl(k_mdot_sl<0>, gr, dim3(KT), s, m, pa, w, scratch, h, hstride, cnt);
 }
 
 void launch_mgs_step_sl(const SliceMap& m, int nsl, const double* vk, const double* u, const double* h,
