@@ -1,16 +1,18 @@
 // Krylov vector kernels of the GMRES core (Sec. 3.2): modified Gram-Schmidt
 // steps (w -= h_k v_k fused with the next projection <w, v_{k+1}>, or with
-// ||w||^2 after the last one), classical multi-dot / update passes (norms,
-// and the projections of a vector on several others), the solution update
-// x += sum y_i z_i and scalings.
+// ||w||^2 after the last one), the first projection <w, v_0> and norms, the
+// solution update x += sum y_i z_i and scalings.
 //
 // These are streaming kernels over packed Stokes vectors of N doubles.  The
-// number of basis vectors is a template parameter (dispatched at run time),
-// loads are 16-byte, the grid is a function of the vector length alone
-// (about four pairs of values per thread, at most KRY_BLOCKS blocks = 8 per
-// SM; kry_blocks) and every reduction sums its block partials in a fixed
-// order, so results are bitwise reproducible.  On GB300 the FP64 FMA rate (about 1.2 TFLOP/s) caps a
-// pass at about one FMA per 8 bytes read.
+// number of basis vectors of an update is a template parameter (dispatched
+// at run time), loads are 16-byte, the grid is a function of the vector
+// length alone (about four pairs of values per thread, at most KRY_BLOCKS
+// blocks = 8 per SM; kry_blocks) and every reduction sums its block partials
+// in a fixed order, so results are bitwise reproducible.  On GB300 the FP64
+// FMA rate (about 1.2 TFLOP/s) caps a pass at about one FMA per 8 bytes
+// read; the passes that only read issue the loads of LOOKAHEAD steps before
+// their FMAs, so that a thread's chain of dependent FMAs does not also wait
+// for one load at a time.
 #include "internal.cuh"
 
 namespace stk {
