@@ -39,3 +39,29 @@ def test_dominant_kernel_is_one_kernel_configuration():
             {"name": "arnoldi_update", "launches": 100, "ms": 5.0, "bytes": 2e10, "flops": 0.0}]
     r = bench.roofline_of(fams, "fp64", {"hbm_gbs": 6790.3}, workload="other")
     assert r["kernel"] == "vel_smooth_colour_l0"
+
+
+def test_traffic_dropped_once_the_sources_change(tmp_path, monkeypatch):
+    """A traffic line counts only while stencil.cuh + kernels.cu + pair.cu
+    hash to its recorded `sources` value: editing any of them makes the
+    figure null until the counters are taken again."""
+    import hashlib
+    csrc = tmp_path / "paper_1308_4605_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    files = {"stencil.cuh": b"// stencils\n", "kernels.cu": b"// kernels\n", "pair.cu": b"// pairs\n"}
+    for name, text in files.items():
+        (csrc / name).write_bytes(text)
+    h = hashlib.sha256()
+    for name in ("stencil.cuh", "kernels.cu", "pair.cu"):
+        h.update(files[name])
+    src = h.hexdigest()[:16]
+    (tmp_path / "profiles" / "kernels_3d_unsteady_periodic_128.md").write_text(
+        f"traffic: vel_smooth_colour_l0 fp64 143510016 sources {src}\n"
+        f"traffic: vel_smooth_colour_l0 mixed 67484416 sources 0000000000000000\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    w = bench.TRAFFIC_WORKLOAD
+    assert bench.traffic_per_launch("vel_smooth_colour_l0", "fp64", w) == 143510016.0
+    assert bench.traffic_per_launch("vel_smooth_colour_l0", "mixed", w) is None   # other sources
+    (csrc / "kernels.cu").write_bytes(b"// kernels, edited\n")
+    assert bench.traffic_per_launch("vel_smooth_colour_l0", "fp64", w) is None
