@@ -91,7 +91,7 @@ def test_autograd_matches_oracle_gradient(S, cfg, precision):
     b = g.pack(pr.b_u, pr.b_p)
     Lr, glogmu, grho, _, _ = gradient.loss_and_gradient(
         g, pr.rho, pr.mu, pr.theta, b, u_t, lambda M, r: direct.solve(g, M, r))
-    assert abs(float(L) - Lr) <= 1e-8 * abs(Lr)
+    assert abs(float(L.detach()) - Lr) <= 1e-8 * abs(Lr)
     gm = log_mu.grad.cpu().numpy().ravel()
     assert np.linalg.norm(gm - glogmu) <= 1e-6 * np.linalg.norm(glogmu)
     if pr.theta != 0.0:
